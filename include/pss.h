@@ -1,0 +1,268 @@
+/*
+ * pss.h -- C ABI of libpss, a GB300 (sm_103a) library for the per-DM-trial
+ * pulsar periodicity search: incoherent dedispersion over a DM plan, a real
+ * FFT of every dedispersed series, block-median whitening, an f-fdot
+ * (Fourier-domain acceleration) plane, harmonic summing with a sigma
+ * threshold, and sifting into a candidate list.
+ *
+ * The paper ("A PRESTO-based Parallel Pulsar Search Pipeline Used for FAST
+ * Drift Scan Data") describes this pipeline as a sequence of programs run
+ * once per DM value (Sect. 2, steps 1-7; Sect. 1, the five steps of a pulsar
+ * search) with DM plans of the form of Tables 2 and 3.  Each call below
+ * names the step it implements.
+ *
+ * Conventions (all calls):
+ *  - Every call returns a pss_status; on failure pss_last_error() returns a
+ *    message for the calling thread.  No call aborts the process.
+ *  - Pointers documented as "device" must be CUDA device (or managed)
+ *    memory of the context's device; "host" pointers are ordinary host
+ *    memory (pinned memory makes uploads faster but is not required).
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the context's
+ *    own stream.  Calls that return results on the host synchronise that
+ *    stream before they return; calls that only write device memory are
+ *    asynchronous with respect to the host.
+ *  - The caller owns every buffer it passes.  The library owns pss_ctx,
+ *    pss_plan and pss_server objects until the matching destroy/free call.
+ *  - A pss_ctx may be used by one host thread at a time.
+ */
+#ifndef PSS_H
+#define PSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PSS_OK = 0,
+    PSS_EINVAL = -1,     /* invalid argument (message says which)            */
+    PSS_ENOMEM = -2,     /* a device or host allocation failed               */
+    PSS_ECAP = -3,       /* output capacity too small; *n_out = count needed */
+    PSS_ETIMEOUT = -4,   /* a bounded wait expired                           */
+    PSS_ECUDA = -5,      /* a CUDA runtime call failed                       */
+    PSS_EBUSY = -6,      /* object in use                                    */
+    PSS_ENOTREADY = -7   /* result not ready yet                             */
+} pss_status;
+
+typedef struct pss_ctx pss_ctx;
+typedef struct pss_plan pss_plan;
+
+/* A search-mode filterbank in memory (the paper's test files, Table 1).
+ *  nchan, nsamp: channels and time samples.  tsamp_s: sampling time.
+ *  fch0_mhz: centre frequency of channel 0; foff_mhz: signed spacing, so
+ *  channel c is centred at fch0 + c*foff.
+ *  nbits: 8 (one uint8 per sample) or 1 (8 channels per byte, channel c at
+ *  bit 7 - c%8 of byte c/8, i.e. most significant bit first; nchan % 8 == 0).
+ *  layout: 0 = time-major, file order: sample t of channel c at byte
+ *  t*nchan + c (8-bit) or bit as above in row t of nchan/8 bytes (1-bit);
+ *  1 = channel-major uint8 [nchan][nsamp] (8-bit only).
+ *  chan_mask: optional host array of nchan bytes, nonzero = keep; NULL keeps
+ *  every channel (the paper masks RFI with rfifind, Sect. 2 step 1; only a
+ *  static mask is supported here). */
+typedef struct {
+    int32_t nchan;
+    int32_t nbits;
+    int64_t nsamp;
+    double tsamp_s;
+    double fch0_mhz;
+    double foff_mhz;
+    int32_t layout;
+    int32_t reserved;
+    const uint8_t* chan_mask;
+} pss_fil_desc;
+
+/* One row of a dedispersion plan (columns of the paper's Tables 2-3):
+ * n_dm trials DM_i = dm_lo + i*dm_step (computed directly in FP64, not by
+ * accumulation), the dedispersed series downsampled by ds.  ds must be a
+ * power of two between 1 and 1024. */
+typedef struct {
+    double dm_lo;
+    double dm_step;
+    int32_t n_dm;
+    int32_t ds;
+} pss_dd_stage;
+
+/* Search parameters (the paper sets zmax for accelsearch, Sect. 3.2).
+ *  zmax: largest |z| (Fourier drift in bins over the series span); 0 = no
+ *  acceleration search.  dz: z step; zmax must be a multiple of dz.
+ *  numharm: largest harmonic sum (power of two, 1..32).
+ *  sigma_thr: single-trial Gaussian-equivalent threshold.
+ *  f_lo_hz: lowest fundamental frequency searched.
+ *  whiten_block: bins per whitening block (power of two, 64..4096, and a
+ *  divisor of nfft/2).  halfwidth_extra: m(z) = ceil(|z|/2) + extra taps
+ *  each side (1..64).  min_dm_hits: sifted groups seen in fewer DM trials
+ *  are dropped. */
+typedef struct {
+    int32_t zmax;
+    int32_t numharm;
+    double dz;
+    double sigma_thr;
+    double f_lo_hz;
+    int32_t whiten_block;
+    int32_t halfwidth_extra;
+    int32_t min_dm_hits;
+    int32_t reserved;
+} pss_search_cfg;
+
+/* A raw (unsifted) detection: plane point (h half-bins, row j) at harmonic
+ * stage numharm of DM trial dm_idx, with harmonic-summed power `power`. */
+typedef struct {
+    int32_t dm_idx;
+    int32_t numharm;
+    int32_t h;
+    int32_t j;
+    float power;
+    int32_t reserved;
+} pss_raw_cand;
+
+/* A sifted candidate: fundamental r (bins of the series span T), z (bins),
+ * f_hz = r / T, the harmonic stage, summed power, sigma, and the number of
+ * DM trials in which the same signal was detected. */
+typedef struct {
+    int32_t dm_idx;
+    int32_t numharm;
+    double dm;
+    double r;
+    double z;
+    double f_hz;
+    double sigma;
+    float power;
+    int32_t dm_hits;
+    int32_t h;
+    int32_t j;
+} pss_cand;
+
+/* ---- context ---------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`: its own stream and a device
+ * workspace that grows on demand and is freed by pss_ctx_destroy. */
+pss_status pss_ctx_create(int device, pss_ctx** out);
+void pss_ctx_destroy(pss_ctx* ctx);
+/* Message of the last failed call made by this thread ("" if none). */
+const char* pss_last_error(void);
+/* Library version string. */
+const char* pss_version(void);
+
+/* Per-stage device-time accounting (tracing).  While enabled, every kernel
+ * launch of the search path is bracketed by CUDA events on the stream it is
+ * launched on.  Stages: 0 unpack/transpose, 1 dedisperse, 2 FFT passes,
+ * 3 R2C + whitening, 4 f-fdot plane, 5 harmonic sum + compaction.
+ * pss_ctx_profile(ctx, 1) enables and resets; (ctx, 0) disables.
+ * pss_ctx_profile_read synchronises the recorded events and returns the
+ * summed milliseconds and launch counts of each stage (arrays of
+ * PSS_NPROF_STAGES), then resets the records.  The paper reports only
+ * whole-pipeline wall-clock times (Table 4, Fig. 1); this has no
+ * counterpart there. */
+#define PSS_NPROF_STAGES 6
+pss_status pss_ctx_profile(pss_ctx* ctx, int enable);
+pss_status pss_ctx_profile_read(pss_ctx* ctx, double* ms, int64_t* launches);
+
+/* ---- plan (DDplan; Sect. 3.1, Tables 2-3) ------------------------------- */
+
+/* Build the DM grid and the integer delay table of a plan:
+ * d[dm][c] = round_half_away(((K*DM) * (1/(f_c*f_c) - 1/(f_ref*f_ref))) / tsamp)
+ * evaluated in FP64 in that order, K = 4.148808e3 s MHz^2 pc^-1 cm^3,
+ * f_ref = the highest channel frequency.  D = the largest delay; every
+ * trial of stage s has N_v = floor((nsamp - D) / ds_s) valid samples and is
+ * transformed with nfft = the next power of two >= N_v.
+ * Errors: PSS_EINVAL for nsamp <= D, empty stages, bad ds. */
+pss_status pss_dd_plan(const pss_fil_desc* fil, const pss_dd_stage* stages, int nstages,
+                       pss_plan** out);
+/* ndm (total trials) and max_delay (D).  dms (nullable, host, ndm doubles)
+ * receives the DM values; delays (nullable, host, ndm*nchan int32,
+ * row-major [dm][channel], all channels including masked ones). */
+pss_status pss_plan_info(const pss_plan* plan, int64_t* ndm, int64_t* max_delay,
+                         double* dms, int32_t* delays);
+/* Stage of DM index `dm_idx` and its N_v, nfft, ds. */
+pss_status pss_plan_trial_info(const pss_plan* plan, int64_t dm_idx, int32_t* stage,
+                               int64_t* nv, int64_t* nfft, int32_t* ds);
+void pss_plan_free(pss_plan* plan);
+
+/* ---- dedispersion (Sect. 2 step 2, prepdata/prepsubband) ---------------- */
+
+/* Exact int32 dedispersion of DM trials [dm_begin, dm_end):
+ * s[t] = sum over kept channels c of x[c][t + d_c], t < nsamp - D, then
+ * s_ds[j] = sum_{k<ds} s[j*ds + k] for j < N_v.
+ * data: the file bytes (host if data_on_device == 0, else device).
+ * out: device int32; trial i's N_v values start at element
+ * sum_{dm_begin <= k < i} N_v(k) (rows packed back to back). */
+pss_status pss_dedisperse(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil,
+                          const void* data, int data_on_device, int64_t dm_begin,
+                          int64_t dm_end, int32_t* out, void* stream);
+
+/* ---- spectra (Sect. 2 step 3, realfft) ---------------------------------- */
+
+/* Whitened half spectrum of DM trials [dm_begin, dm_end): the dedispersed
+ * series minus its mean, zero-padded to nfft, transformed
+ * A_k = sum_n y_n exp(-2 pi i k n / nfft) for k < nfft/2, DC set to 0, and
+ * every block of whiten_block bins scaled by sqrt(ln 2 / med_b) where med_b
+ * is the lower median of |A_k|^2 over the block (DC excluded); a block with
+ * median 0 is zeroed.  out: device, interleaved (re, im) float pairs, rows of
+ * nfft/2 complex values packed back to back as in pss_dedisperse. */
+pss_status pss_spectrum(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil,
+                        const void* data, int data_on_device, const pss_search_cfg* cfg,
+                        int64_t dm_begin, int64_t dm_end, float* out, void* stream);
+
+/* ---- f-fdot power plane (Sect. 2 step 4 / Sect. 3.2, accelsearch zmax) --- */
+
+/* Normalised power plane P[j][h] = |A(h/2, z_j)|^2 of DM trials
+ * [dm_begin, dm_end), z_j = -zmax + j*dz, h in [0, nfft), with
+ * A(r, z) = sum_{k=floor(r)-m+1}^{floor(r)+m} A'_k conj(rho(r-k, z)) / sqrt(E),
+ * rho(q, z) = integral_0^1 exp(2 pi i ((q - z/2) u + z u^2/2)) du the response
+ * of a linearly drifting sinusoid, E the energy of the 2m taps and bins
+ * outside [0, nfft/2) taken as 0.  out: device float, per trial n_z*nfft
+ * values (row-major [j][h]) packed back to back. */
+pss_status pss_power_plane(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil,
+                           const void* data, int data_on_device, const pss_search_cfg* cfg,
+                           int64_t dm_begin, int64_t dm_end, float* out, void* stream);
+
+/* ---- search (Sect. 2 steps 2-4 fused) ----------------------------------- */
+
+/* Raw detections of DM trials [dm_begin, dm_end): for every harmonic stage
+ * n in {1, 2, 4, .., numharm}, S_n(h, j) = sum_{k=1..n} P[j_k][h_k] with
+ * h_k = floor((2kh + n) / (2n)), j_k = Z + sgn(j-Z) floor((2k|j-Z| + n)/(2n)),
+ * Z = zmax/dz; a point is reported when S_n >= S_thr(n) (the power whose
+ * Gamma(n,1) tail probability equals the Gaussian tail at sigma_thr), its
+ * fundamental h/(2nT) >= f_lo_hz, and S_n beats all in-plane neighbours of
+ * its 3x3 window (exact ties go to the lower linear index j*nfft + h).
+ * out: host array of cap entries, sorted by (dm_idx, numharm, j, h).
+ * *n_out: the number found; PSS_ECAP (nothing written) if it exceeds cap. */
+pss_status pss_search_raw(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil,
+                          const void* data, int data_on_device, const pss_search_cfg* cfg,
+                          int64_t dm_begin, int64_t dm_end, pss_raw_cand* out, int64_t cap,
+                          int64_t* n_out, void* stream);
+
+/* Sifting (Sect. 2 step 5, ACCEL_sift) of raw detections, host only.
+ * Each raw point moves to its fundamental r = h/(2n), z = (j-Z) dz / n;
+ * within a DM trial, points with |dr| <= 1 and |dz'| <= dz are linked
+ * (single linkage) and the highest-sigma member kept (ties: lower n, r, z,
+ * DM index); the survivors of all trials are linked the same way, keeping
+ * one per group with dm_hits = distinct trials in the group; groups with
+ * dm_hits < min_dm_hits are dropped.  Output sorted by (dm_idx, numharm, r, z).
+ * PSS_ECAP with *n_out = count needed if cap is too small. */
+pss_status pss_sift(const pss_plan* plan, const pss_search_cfg* cfg, const pss_raw_cand* raw,
+                    int64_t n_raw, pss_cand* out, int64_t cap, int64_t* n_out);
+
+/* The whole search of DM trials [dm_begin, dm_end) of one file:
+ * pss_search_raw followed by pss_sift.  out: host, cap entries. */
+pss_status pss_search_dm_batch(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil,
+                               const void* data, int data_on_device, const pss_search_cfg* cfg,
+                               int64_t dm_begin, int64_t dm_end, pss_cand* out, int64_t cap,
+                               int64_t* n_out, void* stream);
+
+/* Evaluate rho(q_i, z_i) (see pss_power_plane) on the context's GPU in FP64.
+ * q, z: host arrays of n doubles; out: host array of 2n doubles (re, im).
+ * Exposes the template arithmetic so that it can be checked directly. */
+pss_status pss_response(pss_ctx* ctx, const double* q, const double* z, int64_t n, double* out);
+
+/* Significance of a harmonic sum: -Phi^-1(Q(n, S)) with
+ * Q(n, S) = exp(-S) sum_{j<n} S^j / j!, and its inverse (the threshold). */
+double pss_sigma_of_power(int32_t numharm, double power);
+double pss_power_threshold(int32_t numharm, double sigma);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSS_H */

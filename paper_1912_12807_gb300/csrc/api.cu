@@ -1,0 +1,668 @@
+// C-ABI entry points of libpss: context, plan, and the search path
+// dedisperse -> FFT -> whiten -> f-fdot plane -> harmonic sum -> sift
+// (paper Sect. 2, steps 2-5).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <vector>
+
+#include "pss_internal.h"
+#include "response.cuh"
+
+namespace pss {
+
+pss_status DevBuf::ensure(size_t want) {
+    if (want <= bytes) return PSS_OK;
+    release();
+    size_t sz = want + want / 8 + 256;
+    cudaError_t e = cudaMalloc(&p, sz);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        bytes = 0;
+        cudaGetLastError();
+        return fail(PSS_ENOMEM, std::string("device allocation of ") + std::to_string(sz) + " bytes failed: " +
+                                    cudaGetErrorString(e));
+    }
+    bytes = sz;
+    return PSS_OK;
+}
+
+void DevBuf::release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+}
+
+ProfScope::ProfScope(Ctx* ctx, int st, cudaStream_t str) : c(ctx), stage(st), s(str) {
+    if (!c->prof_on) return;
+    for (int i = 0; i < 2; ++i) {
+        cudaEvent_t e = nullptr;
+        if (!c->prof_pool.empty()) {
+            e = c->prof_pool.back();
+            c->prof_pool.pop_back();
+        } else if (cudaEventCreate(&e) != cudaSuccess) {
+            e = nullptr;
+        }
+        (i == 0 ? a : b) = e;
+    }
+    if (a) cudaEventRecord(a, s);
+}
+
+ProfScope::~ProfScope() {
+    if (!a || !b) return;
+    cudaEventRecord(b, s);
+    c->prof_recs.push_back({stage, a, b});
+}
+
+namespace {
+
+cudaStream_t pick_stream(pss_ctx* ctx, void* stream) {
+    return stream ? (cudaStream_t)stream : ctx->stream;
+}
+
+pss_status check_common(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const void* data,
+                        int64_t dm_begin, int64_t dm_end) {
+    if (!ctx || !plan || !fil || !data) return fail(PSS_EINVAL, "null ctx, plan, descriptor or data");
+    if (fil->nchan != plan->nchan || fil->nsamp != plan->nsamp)
+        return fail(PSS_EINVAL, "descriptor does not match the plan (nchan/nsamp)");
+    if (fil->nbits != 8 && fil->nbits != 1) return fail(PSS_EINVAL, "nbits must be 8 or 1");
+    if (fil->nbits == 1 && (fil->nchan % 8) != 0) return fail(PSS_EINVAL, "1-bit data needs nchan % 8 == 0");
+    if (fil->layout != 0 && fil->layout != 1) return fail(PSS_EINVAL, "layout must be 0 or 1");
+    if (fil->layout == 1 && fil->nbits != 8) return fail(PSS_EINVAL, "channel-major layout is 8-bit only");
+    if (dm_begin < 0 || dm_end > plan->ndm() || dm_begin > dm_end)
+        return fail(PSS_EINVAL, "DM range outside the plan");
+    return PSS_OK;
+}
+
+int64_t file_bytes(const pss_fil_desc* fil) {
+    if (fil->nbits == 8) return (int64_t)fil->nchan * fil->nsamp;
+    return (int64_t)(fil->nchan / 8) * fil->nsamp;
+}
+
+std::vector<int32_t> kept_channels(const pss_fil_desc* fil) {
+    std::vector<int32_t> keep;
+    for (int c = 0; c < fil->nchan; ++c)
+        if (!fil->chan_mask || fil->chan_mask[c]) keep.push_back(c);
+    return keep;
+}
+
+// delays of the kept channels, [dm_end - dm_begin][keep.size()]
+std::vector<int32_t> compact_delays(const pss_plan* plan, const std::vector<int32_t>& keep, int64_t dm_begin,
+                                    int64_t dm_end) {
+    const size_t ck = keep.size();
+    std::vector<int32_t> hd((size_t)(dm_end - dm_begin) * ck);
+    for (int64_t i = 0; i < dm_end - dm_begin; ++i)
+        for (size_t r = 0; r < ck; ++r)
+            hd[(size_t)i * ck + r] = plan->delays[(size_t)(dm_begin + i) * plan->nchan + keep[r]];
+    return hd;
+}
+
+// Upload (if needed) and unpack/transpose the file into ctx->xcm; upload
+// the kept channels' delays of [dm_begin, dm_end) into ctx->delays_dev.
+pss_status stage_input(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const void* data,
+                       int on_device, int64_t dm_begin, int64_t dm_end, cudaStream_t s, int32_t* ck_out,
+                       int64_t* pitch_out) {
+    const int64_t nbytes = file_bytes(fil);
+    const uint8_t* src = (const uint8_t*)data;
+    if (!on_device) {
+        PSS_TRY(ctx->fil_dev.ensure((size_t)nbytes));
+        PSS_CUDA(cudaMemcpyAsync(ctx->fil_dev.p, data, (size_t)nbytes, cudaMemcpyHostToDevice, s));
+        src = (const uint8_t*)ctx->fil_dev.p;
+    }
+    const std::vector<int32_t> keep = kept_channels(fil);
+    const int32_t ck = (int32_t)keep.size();
+    if (ck == 0) return fail(PSS_EINVAL, "channel mask removes every channel");
+    const int TN = dedisp_tile_samples();
+    const int64_t pitch = ((fil->nsamp + TN + 256) + 63) / 64 * 64;
+    // keep list + compacted delays in one upload
+    const std::vector<int32_t> hd = compact_delays(plan, keep, dm_begin, dm_end);
+    std::vector<int32_t> host((size_t)ck + hd.size());
+    memcpy(host.data(), keep.data(), sizeof(int32_t) * ck);
+    if (!hd.empty()) memcpy(host.data() + ck, hd.data(), sizeof(int32_t) * hd.size());
+    PSS_TRY(ctx->delays_dev.ensure(host.size() * sizeof(int32_t)));
+    PSS_CUDA(cudaMemcpyAsync(ctx->delays_dev.p, host.data(), host.size() * sizeof(int32_t),
+                             cudaMemcpyHostToDevice, s));
+    PSS_TRY(ctx->xcm.ensure((size_t)ck * pitch + 64));
+    PrepArgs pa;
+    pa.src = src;
+    pa.nchan = fil->nchan;
+    pa.nbits = fil->nbits;
+    pa.layout = fil->layout;
+    pa.nsamp = fil->nsamp;
+    pa.keep = (const int32_t*)ctx->delays_dev.p;
+    pa.ck = ck;
+    pa.xcm = (uint8_t*)ctx->xcm.p;
+    pa.pitch = pitch;
+    {
+        ProfScope ps(ctx, 0, s);
+        PSS_CUDA(launch_prep(pa, s));
+    }
+    // the host vector must outlive the async copy
+    PSS_CUDA(cudaStreamSynchronize(s));
+    *ck_out = ck;
+    *pitch_out = pitch;
+    return PSS_OK;
+}
+
+// max over consecutive groups of 8 trials and channels of (dmax - dmin)
+int32_t delay_spread(const int32_t* d, int64_t nb, int32_t ck) {
+    int32_t sp = 0;
+    for (int64_t g = 0; g < nb; g += 8) {
+        const int64_t ge = std::min<int64_t>(nb, g + 8);
+        for (int32_t c = 0; c < ck; ++c) {
+            int32_t lo = d[g * ck + c], hi = lo;
+            for (int64_t i = g + 1; i < ge; ++i) {
+                lo = std::min(lo, d[i * ck + c]);
+                hi = std::max(hi, d[i * ck + c]);
+            }
+            sp = std::max(sp, hi - lo);
+        }
+    }
+    return sp;
+}
+
+enum Mode { MODE_SPECTRUM, MODE_PLANE, MODE_SEARCH };
+
+struct Outputs {
+    float* spec = nullptr;   // MODE_SPECTRUM: user device buffer
+    float* plane = nullptr;  // MODE_PLANE: user device buffer
+};
+
+pss_status check_cfg(const pss_search_cfg* cfg, const Plan& P) {
+    if (!cfg) return fail(PSS_EINVAL, "null search cfg");
+    if (cfg->zmax < 0) return fail(PSS_EINVAL, "zmax must be >= 0");
+    if (cfg->zmax > 0) {
+        if (!(cfg->dz > 0)) return fail(PSS_EINVAL, "dz must be > 0");
+        const double r = cfg->zmax / cfg->dz;
+        if (fabs(r - llround(r)) > 1e-9) return fail(PSS_EINVAL, "zmax must be a multiple of dz");
+        if (cfg->zmax > 1200) return fail(PSS_EINVAL, "zmax above 1200 is not supported");
+    }
+    const int nh = cfg->numharm;
+    if (nh < 1 || nh > 32 || (nh & (nh - 1))) return fail(PSS_EINVAL, "numharm must be a power of two in [1, 32]");
+    const int W = cfg->whiten_block;
+    if (W < 64 || W > 4096 || (W & (W - 1))) return fail(PSS_EINVAL, "whiten_block must be a power of two in [64, 4096]");
+    if (cfg->halfwidth_extra < 1 || cfg->halfwidth_extra > 64)
+        return fail(PSS_EINVAL, "halfwidth_extra must be in [1, 64]");
+    for (const auto& st : P.stages)
+        if ((st.nfft / 2) % W != 0 || st.nfft / 2 < 64)
+            return fail(PSS_EINVAL, "whiten_block must divide nfft/2 (and nfft >= 128) for every stage");
+    return PSS_OK;
+}
+
+int nz_of(const pss_search_cfg* cfg) { return cfg->zmax ? (int)llround(2.0 * cfg->zmax / cfg->dz) + 1 : 1; }
+
+// Build (or reuse) the response templates of cfg in ctx->taps.
+pss_status ensure_templates(pss_ctx* ctx, const pss_search_cfg* cfg, cudaStream_t s) {
+    const double dz = cfg->zmax ? cfg->dz : 1.0;
+    if (ctx->tap_zmax == cfg->zmax && ctx->tap_extra == cfg->halfwidth_extra && ctx->tap_dz == dz) return PSS_OK;
+    const int nz = nz_of(cfg);
+    std::vector<int32_t> off(2 * nz), m(nz);
+    int32_t total = 0;
+    for (int j = 0; j < nz; ++j) {
+        const double z = cfg->zmax ? -(double)cfg->zmax + (double)j * dz : 0.0;
+        m[j] = (int32_t)ceil(fabs(z) / 2.0) + cfg->halfwidth_extra;
+        off[2 * j] = total;
+        total += 2 * m[j];
+        off[2 * j + 1] = total;
+        total += 2 * m[j];
+    }
+    PSS_TRY(ctx->taps.ensure((size_t)total * sizeof(float2)));
+    PSS_TRY(ctx->tapinfo.ensure((size_t)(2 * nz + nz + 2 * nz) * sizeof(int32_t)));
+    int32_t* info = (int32_t*)ctx->tapinfo.p;
+    std::vector<int32_t> hinfo(3 * nz);
+    for (int i = 0; i < 2 * nz; ++i) hinfo[i] = off[i];
+    for (int j = 0; j < nz; ++j) hinfo[2 * nz + j] = m[j];
+    PSS_CUDA(cudaMemcpyAsync(info, hinfo.data(), hinfo.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    TemplateArgs ta;
+    ta.nz = nz;
+    ta.zmax = cfg->zmax;
+    ta.extra = cfg->halfwidth_extra;
+    ta.dz = dz;
+    ta.taps = (float2*)ctx->taps.p;
+    ta.tap_off = info;
+    ta.tap_m = info + 2 * nz;
+    ta.tap_scale = (float*)(info + 3 * nz);
+    ta.total = total;
+    PSS_CUDA(launch_templates(ta, s));
+    PSS_CUDA(cudaStreamSynchronize(s));
+    ctx->tap_zmax = cfg->zmax;
+    ctx->tap_extra = cfg->halfwidth_extra;
+    ctx->tap_dz = dz;
+    return PSS_OK;
+}
+
+// Thresholds in FP32, rounded up so that S_f >= thr_f implies S_f >= thr.
+float thr_f32(int n, double sigma) {
+    const double t = power_threshold(n, sigma);
+    float f = (float)t;
+    if ((double)f < t) f = nextafterf(f, INFINITY);
+    return f;
+}
+
+// Run the path over [dm_begin, dm_end) in batches within each plan stage.
+pss_status run_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const void* data, int on_dev,
+                    const pss_search_cfg* cfg, int64_t dm_begin, int64_t dm_end, Mode mode, Outputs outs,
+                    cudaStream_t s, int64_t dev_cap) {
+    int32_t ck = 0;
+    int64_t pitch = 0;
+    PSS_TRY(stage_input(ctx, plan, fil, data, on_dev, dm_begin, dm_end, s, &ck, &pitch));
+    if (dm_end == dm_begin) return PSS_OK;
+    PSS_TRY(ensure_templates(ctx, cfg, s));
+    const int nz = nz_of(cfg);
+    const int Z = cfg->zmax ? (int)llround(cfg->zmax / cfg->dz) : 0;
+    const int32_t* dtab = (const int32_t*)ctx->delays_dev.p + ck;
+    // host copy of the compacted delays for the spread computation
+    const std::vector<int32_t> hd = compact_delays(plan, kept_channels(fil), dm_begin, dm_end);
+    const int nstages = (int)log2((double)cfg->numharm) + 1;
+    if (mode == MODE_SEARCH) {
+        PSS_TRY(ctx->cands.ensure((size_t)dev_cap * sizeof(pss_raw_cand)));
+        PSS_TRY(ctx->counter.ensure(sizeof(unsigned long long)));
+        PSS_CUDA(cudaMemsetAsync(ctx->counter.p, 0, sizeof(unsigned long long), s));
+    }
+    int64_t out_off = 0;  // packed output offset (elements) for spectrum/plane modes
+    for (size_t si = 0; si < plan->stages.size(); ++si) {
+        const StageInfo& st = plan->stages[si];
+        const int64_t lo = std::max<int64_t>(dm_begin, st.first);
+        const int64_t hi = std::min<int64_t>(dm_end, st.first + st.n_dm);
+        if (lo >= hi) continue;
+        const int64_t nfft = st.nfft, M = nfft / 2;
+        const size_t per_dm = (size_t)nfft * 4 + (size_t)M * 8 * 3 + (mode == MODE_PLANE ? 0 : (size_t)nz * nfft * 4);
+        int64_t B = (int64_t)((size_t)6 << 30) / (int64_t)per_dm;
+        B = std::max<int64_t>(1, std::min<int64_t>(B, 1024));
+        B = std::min<int64_t>(B, hi - lo);
+        PSS_TRY(ctx->series.ensure((size_t)B * nfft * 4));
+        PSS_TRY(ctx->sums.ensure((size_t)B * 8));
+        PSS_TRY(ctx->fftA.ensure((size_t)B * M * 8));
+        PSS_TRY(ctx->fftB.ensure((size_t)B * M * 8));
+        if (mode != MODE_SPECTRUM) PSS_TRY(ctx->spec.ensure((size_t)B * M * 8));
+        if (mode == MODE_SEARCH) PSS_TRY(ctx->plane.ensure((size_t)B * nz * nfft * 4));
+        const double T = (double)(nfft * (int64_t)st.ds) * plan->tsamp;
+        HarmArgs ha{};
+        for (int k = 0; k < nstages; ++k) {
+            const int n = 1 << k;
+            ha.thr[k] = thr_f32(n, cfg->sigma_thr);
+            ha.hmin[k] = (int32_t)std::min<double>(ceil((double)(2 * n) * T * cfg->f_lo_hz), 2e9);
+        }
+        for (int64_t b0 = lo; b0 < hi; b0 += B) {
+            const int32_t nb = (int32_t)std::min<int64_t>(B, hi - b0);
+            const int32_t* drow = dtab + (b0 - dm_begin) * ck;
+            DedispArgs da;
+            da.xcm = (const uint8_t*)ctx->xcm.p;
+            da.pitch = pitch;
+            da.ck = ck;
+            da.delays = drow;
+            da.nb = nb;
+            da.nv = st.nv;
+            da.ds = st.ds;
+            da.out_f = (float*)ctx->series.p;
+            da.out_i = nullptr;
+            da.out_stride = nfft;
+            da.sums = (unsigned long long*)ctx->sums.p;
+            da.spread = delay_spread(hd.data() + (size_t)(b0 - dm_begin) * ck, nb, ck);
+            PSS_CUDA(cudaMemsetAsync(ctx->sums.p, 0, (size_t)nb * 8, s));
+            {
+                ProfScope ps(ctx, 1, s);
+                PSS_CUDA(launch_dedisp(da, ctx->num_sms, s));
+            }
+            FftArgs fa;
+            fa.series = (const float*)ctx->series.p;
+            fa.series_stride = nfft;
+            fa.sums = (const unsigned long long*)ctx->sums.p;
+            fa.nv = st.nv;
+            fa.nfft = nfft;
+            fa.nb = nb;
+            fa.bufA = (float2*)ctx->fftA.p;
+            fa.bufB = (float2*)ctx->fftB.p;
+            float2* spec = (mode == MODE_SPECTRUM) ? (float2*)(outs.spec) + out_off : (float2*)ctx->spec.p;
+            fa.spec_out = spec;
+            fa.spec_stride = M;
+            fa.whiten_block = cfg->whiten_block;
+            PSS_CUDA(launch_fft_whiten(fa, s, ctx));
+            if (mode == MODE_SPECTRUM) {
+                out_off += (int64_t)nb * M;
+                continue;
+            }
+            PlaneArgs pl;
+            pl.spec = spec;
+            pl.spec_stride = M;
+            pl.nfft = nfft;
+            pl.nb = nb;
+            pl.plane = (mode == MODE_PLANE) ? outs.plane + out_off : (float*)ctx->plane.p;
+            pl.plane_stride = (int64_t)nz * nfft;
+            pl.zmax = cfg->zmax;
+            pl.dz = cfg->zmax ? cfg->dz : 1.0;
+            pl.extra = cfg->halfwidth_extra;
+            pl.taps = (const float2*)ctx->taps.p;
+            const int32_t* info = (const int32_t*)ctx->tapinfo.p;
+            pl.tap_off = info;
+            pl.tap_m = info + 2 * nz;
+            pl.tap_scale = (const float*)(info + 3 * nz);
+            {
+                ProfScope ps(ctx, 4, s);
+                PSS_CUDA(launch_plane(pl, s));
+            }
+            if (mode == MODE_PLANE) {
+                out_off += (int64_t)nb * nz * nfft;
+                continue;
+            }
+            ha.plane = pl.plane;
+            ha.plane_stride = pl.plane_stride;
+            ha.nfft = nfft;
+            ha.nz = nz;
+            ha.Z = Z;
+            ha.nb = nb;
+            ha.dm0 = (int32_t)b0;
+            ha.nstages = nstages;
+            ha.out = (pss_raw_cand*)ctx->cands.p;
+            ha.counter = (unsigned long long*)ctx->counter.p;
+            ha.cap = dev_cap;
+            {
+                ProfScope ps(ctx, 5, s);
+                PSS_CUDA(launch_harm(ha, s));
+            }
+        }
+    }
+    return PSS_OK;
+}
+
+bool raw_less(const pss_raw_cand& a, const pss_raw_cand& b) {
+    if (a.dm_idx != b.dm_idx) return a.dm_idx < b.dm_idx;
+    if (a.numharm != b.numharm) return a.numharm < b.numharm;
+    if (a.j != b.j) return a.j < b.j;
+    return a.h < b.h;
+}
+
+pss_status search_raw_vec(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const void* data, int on_dev,
+                          const pss_search_cfg* cfg, int64_t dm_begin, int64_t dm_end, std::vector<pss_raw_cand>* out,
+                          cudaStream_t s) {
+    PSS_TRY(check_common(ctx, plan, fil, data, dm_begin, dm_end));
+    PSS_TRY(check_cfg(cfg, *plan));
+    int64_t cap = ctx->cands.bytes ? (int64_t)(ctx->cands.bytes / sizeof(pss_raw_cand)) : (int64_t)1 << 20;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        PSS_TRY(run_path(ctx, plan, fil, data, on_dev, cfg, dm_begin, dm_end, MODE_SEARCH, Outputs(), s, cap));
+        unsigned long long cnt = 0;
+        if (dm_end > dm_begin)
+            PSS_CUDA(cudaMemcpyAsync(&cnt, ctx->counter.p, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+        PSS_CUDA(cudaStreamSynchronize(s));
+        if ((int64_t)cnt <= cap) {
+            out->resize(cnt);
+            if (cnt)
+                PSS_CUDA(cudaMemcpy(out->data(), ctx->cands.p, cnt * sizeof(pss_raw_cand), cudaMemcpyDeviceToHost));
+            std::sort(out->begin(), out->end(), raw_less);
+            return PSS_OK;
+        }
+        cap = (int64_t)cnt + 1024;  // overflowed the device buffer: grow and redo
+    }
+    return fail(PSS_ECAP, "candidate buffer overflow persisted after resizing");
+}
+
+}  // namespace
+}  // namespace pss
+
+using namespace pss;
+
+extern "C" {
+
+const char* pss_version(void) { return "pss 0.1 (sm_103a)"; }
+
+pss_status pss_ctx_create(int device, pss_ctx** out) {
+    if (!out) return fail(PSS_EINVAL, "pss_ctx_create: null out");
+    *out = nullptr;
+    int n = 0;
+    PSS_CUDA(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return fail(PSS_EINVAL, "pss_ctx_create: no such device");
+    PSS_CUDA(cudaSetDevice(device));
+    pss_ctx* c = new pss_ctx();
+    c->device = device;
+    cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "cudaStreamCreate");
+    }
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    *out = c;
+    return PSS_OK;
+}
+
+void pss_ctx_destroy(pss_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    DevBuf* bufs[] = {&c->fil_dev, &c->xcm, &c->delays_dev, &c->series, &c->sums, &c->fftA, &c->fftB,
+                      &c->spec, &c->plane, &c->cands, &c->counter, &c->taps, &c->tapinfo, &c->int_out};
+    for (DevBuf* b : bufs) b->release();
+    for (auto& r : c->prof_recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : c->prof_pool) cudaEventDestroy(e);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+pss_status pss_ctx_profile(pss_ctx* ctx, int enable) {
+    if (!ctx) return fail(PSS_EINVAL, "pss_ctx_profile: null ctx");
+    PSS_CUDA(cudaSetDevice(ctx->device));
+    for (auto& r : ctx->prof_recs) {
+        ctx->prof_pool.push_back(r.a);
+        ctx->prof_pool.push_back(r.b);
+    }
+    ctx->prof_recs.clear();
+    ctx->prof_on = enable != 0;
+    return PSS_OK;
+}
+
+pss_status pss_ctx_profile_read(pss_ctx* ctx, double* ms, int64_t* launches) {
+    if (!ctx || !ms || !launches) return fail(PSS_EINVAL, "pss_ctx_profile_read: null argument");
+    PSS_CUDA(cudaSetDevice(ctx->device));
+    for (int i = 0; i < PSS_NPROF_STAGES; ++i) {
+        ms[i] = 0.0;
+        launches[i] = 0;
+    }
+    for (auto& r : ctx->prof_recs) {
+        PSS_CUDA(cudaEventSynchronize(r.b));
+        float t = 0.f;
+        PSS_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+        ms[r.stage] += t;
+        launches[r.stage] += 1;
+        ctx->prof_pool.push_back(r.a);
+        ctx->prof_pool.push_back(r.b);
+    }
+    ctx->prof_recs.clear();
+    return PSS_OK;
+}
+
+pss_status pss_dd_plan(const pss_fil_desc* fil, const pss_dd_stage* stages, int nstages, pss_plan** out) {
+    if (!out) return fail(PSS_EINVAL, "pss_dd_plan: null out");
+    *out = nullptr;
+    pss_plan* p = new pss_plan();
+    pss_status st = build_plan(fil, stages, nstages, p);
+    if (st != PSS_OK) {
+        delete p;
+        return st;
+    }
+    *out = p;
+    return PSS_OK;
+}
+
+pss_status pss_plan_info(const pss_plan* plan, int64_t* ndm, int64_t* max_delay, double* dms, int32_t* delays) {
+    if (!plan) return fail(PSS_EINVAL, "pss_plan_info: null plan");
+    if (ndm) *ndm = plan->ndm();
+    if (max_delay) *max_delay = plan->max_delay;
+    if (dms) memcpy(dms, plan->dms.data(), sizeof(double) * plan->dms.size());
+    if (delays) memcpy(delays, plan->delays.data(), sizeof(int32_t) * plan->delays.size());
+    return PSS_OK;
+}
+
+pss_status pss_plan_trial_info(const pss_plan* plan, int64_t dm_idx, int32_t* stage, int64_t* nv, int64_t* nfft,
+                               int32_t* ds) {
+    if (!plan) return fail(PSS_EINVAL, "pss_plan_trial_info: null plan");
+    if (dm_idx < 0 || dm_idx >= plan->ndm()) return fail(PSS_EINVAL, "pss_plan_trial_info: dm_idx out of range");
+    const int s = plan->stage_of[dm_idx];
+    const StageInfo& si = plan->stages[s];
+    if (stage) *stage = s;
+    if (nv) *nv = si.nv;
+    if (nfft) *nfft = si.nfft;
+    if (ds) *ds = si.ds;
+    return PSS_OK;
+}
+
+void pss_plan_free(pss_plan* plan) { delete plan; }
+
+pss_status pss_dedisperse(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const void* data,
+                          int data_on_device, int64_t dm_begin, int64_t dm_end, int32_t* out, void* stream) {
+    PSS_TRY(check_common(ctx, plan, fil, data, dm_begin, dm_end));
+    if (!out && dm_end > dm_begin) return fail(PSS_EINVAL, "pss_dedisperse: null out");
+    PSS_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = pick_stream(ctx, stream);
+    int32_t ck = 0;
+    int64_t pitch = 0;
+    PSS_TRY(stage_input(ctx, plan, fil, data, data_on_device, dm_begin, dm_end, s, &ck, &pitch));
+    const int32_t* dtab = (const int32_t*)ctx->delays_dev.p + ck;
+    const std::vector<int32_t> hd = compact_delays(plan, kept_channels(fil), dm_begin, dm_end);
+    int64_t off = 0;
+    for (size_t si = 0; si < plan->stages.size(); ++si) {
+        const StageInfo& st = plan->stages[si];
+        const int64_t lo = std::max<int64_t>(dm_begin, st.first);
+        const int64_t hi = std::min<int64_t>(dm_end, st.first + st.n_dm);
+        if (lo >= hi) continue;
+        for (int64_t b0 = lo; b0 < hi; b0 += 1024) {
+            const int32_t nb = (int32_t)std::min<int64_t>(1024, hi - b0);
+            DedispArgs da;
+            da.xcm = (const uint8_t*)ctx->xcm.p;
+            da.pitch = pitch;
+            da.ck = ck;
+            da.delays = dtab + (b0 - dm_begin) * ck;
+            da.nb = nb;
+            da.nv = st.nv;
+            da.ds = st.ds;
+            da.out_f = nullptr;
+            da.out_i = out + off;
+            da.out_stride = st.nv;
+            da.sums = nullptr;
+            da.spread = delay_spread(hd.data() + (size_t)(b0 - dm_begin) * ck, nb, ck);
+            {
+                ProfScope ps(ctx, 1, s);
+                PSS_CUDA(launch_dedisp(da, ctx->num_sms, s));
+            }
+            off += (int64_t)nb * st.nv;
+        }
+    }
+    return PSS_OK;
+}
+
+pss_status pss_spectrum(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const void* data,
+                        int data_on_device, const pss_search_cfg* cfg, int64_t dm_begin, int64_t dm_end, float* out,
+                        void* stream) {
+    PSS_TRY(check_common(ctx, plan, fil, data, dm_begin, dm_end));
+    PSS_TRY(check_cfg(cfg, *plan));
+    if (!out && dm_end > dm_begin) return fail(PSS_EINVAL, "pss_spectrum: null out");
+    PSS_CUDA(cudaSetDevice(ctx->device));
+    Outputs o;
+    o.spec = out;
+    return run_path(ctx, plan, fil, data, data_on_device, cfg, dm_begin, dm_end, MODE_SPECTRUM, o,
+                    pick_stream(ctx, stream), 0);
+}
+
+pss_status pss_power_plane(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const void* data,
+                           int data_on_device, const pss_search_cfg* cfg, int64_t dm_begin, int64_t dm_end,
+                           float* out, void* stream) {
+    PSS_TRY(check_common(ctx, plan, fil, data, dm_begin, dm_end));
+    PSS_TRY(check_cfg(cfg, *plan));
+    if (!out && dm_end > dm_begin) return fail(PSS_EINVAL, "pss_power_plane: null out");
+    PSS_CUDA(cudaSetDevice(ctx->device));
+    Outputs o;
+    o.plane = out;
+    return run_path(ctx, plan, fil, data, data_on_device, cfg, dm_begin, dm_end, MODE_PLANE, o,
+                    pick_stream(ctx, stream), 0);
+}
+
+pss_status pss_search_raw(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const void* data,
+                          int data_on_device, const pss_search_cfg* cfg, int64_t dm_begin, int64_t dm_end,
+                          pss_raw_cand* out, int64_t cap, int64_t* n_out, void* stream) {
+    if (!n_out) return fail(PSS_EINVAL, "pss_search_raw: null n_out");
+    *n_out = 0;
+    if (ctx) PSS_CUDA(cudaSetDevice(ctx->device));
+    std::vector<pss_raw_cand> v;
+    PSS_TRY(search_raw_vec(ctx, plan, fil, data, data_on_device, cfg, dm_begin, dm_end, &v,
+                           ctx ? pick_stream(ctx, stream) : nullptr));
+    *n_out = (int64_t)v.size();
+    if ((int64_t)v.size() > cap) return fail(PSS_ECAP, "pss_search_raw: output capacity too small");
+    if (!v.empty()) {
+        if (!out) return fail(PSS_EINVAL, "pss_search_raw: null out");
+        memcpy(out, v.data(), v.size() * sizeof(pss_raw_cand));
+    }
+    return PSS_OK;
+}
+
+pss_status pss_sift(const pss_plan* plan, const pss_search_cfg* cfg, const pss_raw_cand* raw, int64_t n_raw,
+                    pss_cand* out, int64_t cap, int64_t* n_out) {
+    if (!plan || !cfg || !n_out || (n_raw > 0 && !raw)) return fail(PSS_EINVAL, "pss_sift: null argument");
+    *n_out = 0;
+    if (cfg->zmax > 0 && !(cfg->dz > 0)) return fail(PSS_EINVAL, "pss_sift: dz must be > 0");
+    std::vector<pss_cand> v;
+    PSS_TRY(sift(*plan, *cfg, raw, n_raw, &v));
+    *n_out = (int64_t)v.size();
+    if ((int64_t)v.size() > cap) return fail(PSS_ECAP, "pss_sift: output capacity too small");
+    if (!v.empty()) {
+        if (!out) return fail(PSS_EINVAL, "pss_sift: null out");
+        memcpy(out, v.data(), v.size() * sizeof(pss_cand));
+    }
+    return PSS_OK;
+}
+
+pss_status pss_search_dm_batch(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const void* data,
+                               int data_on_device, const pss_search_cfg* cfg, int64_t dm_begin, int64_t dm_end,
+                               pss_cand* out, int64_t cap, int64_t* n_out, void* stream) {
+    if (!n_out) return fail(PSS_EINVAL, "pss_search_dm_batch: null n_out");
+    *n_out = 0;
+    if (ctx) PSS_CUDA(cudaSetDevice(ctx->device));
+    std::vector<pss_raw_cand> raw;
+    PSS_TRY(search_raw_vec(ctx, plan, fil, data, data_on_device, cfg, dm_begin, dm_end, &raw,
+                           ctx ? pick_stream(ctx, stream) : nullptr));
+    std::vector<pss_cand> v;
+    PSS_TRY(sift(*plan, *cfg, raw.data(), (int64_t)raw.size(), &v));
+    *n_out = (int64_t)v.size();
+    if ((int64_t)v.size() > cap) return fail(PSS_ECAP, "pss_search_dm_batch: output capacity too small");
+    if (!v.empty()) {
+        if (!out) return fail(PSS_EINVAL, "pss_search_dm_batch: null out");
+        memcpy(out, v.data(), v.size() * sizeof(pss_cand));
+    }
+    return PSS_OK;
+}
+
+}  // extern "C"
+
+namespace pss {
+namespace {
+__global__ void k_response(const double* q, const double* z, int64_t n, double* out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const cplx r = rho_resp(q[i], z[i]);
+    out[2 * i] = r.re;
+    out[2 * i + 1] = r.im;
+}
+}  // namespace
+}  // namespace pss
+
+extern "C" pss_status pss_response(pss_ctx* ctx, const double* q, const double* z, int64_t n, double* out) {
+    if (!ctx || (n > 0 && (!q || !z || !out)) || n < 0) return fail(PSS_EINVAL, "pss_response: bad arguments");
+    if (n == 0) return PSS_OK;
+    PSS_CUDA(cudaSetDevice(ctx->device));
+    double* d = nullptr;
+    PSS_CUDA(cudaMalloc(&d, (size_t)n * 4 * sizeof(double)));
+    cudaStream_t s = ctx->stream;
+    cudaError_t e = cudaMemcpyAsync(d, q, n * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d + n, z, n * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        k_response<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(d, d + n, n, d + 2 * n);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d + 2 * n, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "pss_response");
+    return PSS_OK;
+}

@@ -1,0 +1,210 @@
+// Internal declarations shared by the libpss translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pss.h"
+
+namespace pss {
+
+// ---- errors ---------------------------------------------------------------
+void set_error(const std::string& msg);
+pss_status fail(pss_status st, const std::string& msg);
+pss_status cuda_fail(cudaError_t e, const char* what);
+
+#define PSS_CUDA(call)                                          \
+    do {                                                        \
+        cudaError_t _e = (call);                                \
+        if (_e != cudaSuccess) return pss::cuda_fail(_e, #call); \
+    } while (0)
+
+#define PSS_TRY(call)                      \
+    do {                                   \
+        pss_status _s = (call);            \
+        if (_s != PSS_OK) return _s;       \
+    } while (0)
+
+// ---- plan -----------------------------------------------------------------
+struct StageInfo {
+    double dm_lo, dm_step;
+    int32_t n_dm, ds;
+    int64_t first;  // index of the stage's first trial
+    int64_t nv, nfft;
+};
+
+struct Plan {
+    int32_t nchan = 0;
+    int64_t nsamp = 0;
+    double tsamp = 0, fch0 = 0, foff = 0;
+    std::vector<double> freqs;
+    std::vector<StageInfo> stages;
+    std::vector<double> dms;
+    std::vector<int32_t> stage_of;
+    std::vector<int32_t> delays;  // [ndm][nchan]
+    int64_t max_delay = 0;
+    int64_t ndm() const { return (int64_t)dms.size(); }
+    double t_span(int64_t dm) const {
+        const StageInfo& s = stages[stage_of[dm]];
+        return (double)(s.nfft * (int64_t)s.ds) * tsamp;
+    }
+};
+
+pss_status build_plan(const pss_fil_desc* fil, const pss_dd_stage* st, int nst, Plan* out);
+
+// ---- statistics (host) ----------------------------------------------------
+double log_q(int n, double S);
+double sigma_from_logp(double logp);
+double sigma_of_power(int n, double S);
+double power_threshold(int n, double sigma);
+
+// ---- sift (host) ----------------------------------------------------------
+pss_status sift(const Plan& P, const pss_search_cfg& cfg, const pss_raw_cand* raw, int64_t n,
+                std::vector<pss_cand>* out);
+
+// ---- device workspace -----------------------------------------------------
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    pss_status ensure(size_t want);
+    void release();
+};
+
+struct Ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    DevBuf fil_dev;      // uploaded file bytes
+    DevBuf xcm;          // channel-major uint8 [Ck][pitch]
+    DevBuf delays_dev;   // int32 [ndm][Ck] (kept channels)
+    DevBuf series;       // float [B][nfft]
+    DevBuf sums;         // unsigned long long [B]
+    DevBuf fftA, fftB;   // float2 [B][M]
+    DevBuf spec;         // float2 [B][M]  whitened spectrum
+    DevBuf plane;        // float [B][nz][nfft]
+    DevBuf cands;        // pss_raw_cand [cap]
+    DevBuf counter;      // unsigned long long
+    DevBuf taps;         // float2 templates
+    DevBuf tapinfo;      // per row tap info
+    DevBuf int_out;      // int32 scratch
+    void* host_pinned = nullptr;
+    size_t host_pinned_bytes = 0;
+    // (zmax, extra, dz) of the templates currently in `taps`
+    int32_t tap_zmax = -1, tap_extra = -1;
+    double tap_dz = 0.0;
+    // per-stage event timing (pss_ctx_profile)
+    bool prof_on = false;
+    struct ProfRec {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    std::vector<ProfRec> prof_recs;
+    std::vector<cudaEvent_t> prof_pool;
+};
+
+// RAII pair of events around one launch when profiling is on.
+struct ProfScope {
+    Ctx* c;
+    int stage;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(Ctx* ctx, int st, cudaStream_t str);
+    ~ProfScope();
+};
+
+// ---- kernel launchers (each returns cudaGetLastError of its launch) -------
+struct PrepArgs {
+    const uint8_t* src;   // file bytes on device
+    int32_t nchan, nbits, layout;
+    int64_t nsamp;
+    const int32_t* keep;  // device [Ck] source channel index of each kept row
+    int32_t ck;
+    uint8_t* xcm;
+    int64_t pitch;        // bytes per channel-major row (multiple of 64)
+};
+cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
+
+struct DedispArgs {
+    const uint8_t* xcm;
+    int64_t pitch;
+    int32_t ck;
+    const int32_t* delays;  // [nb][ck] for this batch
+    int32_t nb;             // trials in this batch
+    int64_t nv;             // outputs per trial
+    int32_t ds;
+    float* out_f;           // [nb][out_stride] or null
+    int32_t* out_i;         // [nb][out_stride] or null (packed rows use stride nv)
+    int64_t out_stride;
+    unsigned long long* sums;  // [nb] or null
+    int32_t spread;         // max over groups/channels of (dmax - dmin)
+};
+int dedisp_tile_samples();
+cudaError_t launch_dedisp(const DedispArgs& a, int num_sms, cudaStream_t s);
+
+struct FftArgs {
+    const float* series;              // [nb][series_stride] raw sums (float, exact)
+    int64_t series_stride;
+    const unsigned long long* sums;   // [nb]
+    int64_t nv;
+    int64_t nfft;
+    int32_t nb;
+    float2* bufA;
+    float2* bufB;                     // [nb][nfft/2] each
+    float2* spec_out;                 // [nb][spec_stride]
+    int64_t spec_stride;
+    int32_t whiten_block;
+};
+cudaError_t launch_fft_whiten(const FftArgs& a, cudaStream_t s, Ctx* prof_ctx);
+
+struct PlaneArgs {
+    const float2* spec;  // [nb][spec_stride] whitened half spectrum (M = nfft/2)
+    int64_t spec_stride;
+    int64_t nfft;
+    int32_t nb;
+    float* plane;        // [nb][plane_stride]; row j at j*nfft
+    int64_t plane_stride;
+    int32_t zmax;
+    double dz;
+    int32_t extra;
+    const float2* taps;  // device template table (zmax > 0)
+    const int32_t* tap_off;  // [nz*2] offsets into taps
+    const int32_t* tap_m;    // [nz] half-widths
+    const float* tap_scale;  // [nz*2] 1/sqrt(E)
+};
+cudaError_t launch_plane(const PlaneArgs& a, cudaStream_t s);
+
+struct TemplateArgs {
+    int32_t nz, zmax, extra;
+    double dz;
+    float2* taps;       // out
+    int32_t* tap_off;   // in (host-computed layout, device copy)
+    int32_t* tap_m;
+    float* tap_scale;   // out
+    int32_t total;
+};
+cudaError_t launch_templates(const TemplateArgs& a, cudaStream_t s);
+
+struct HarmArgs {
+    const float* plane;
+    int64_t plane_stride;
+    int64_t nfft;
+    int32_t nz;
+    int32_t Z;
+    int32_t nb;
+    int32_t dm0;        // dm index of batch row 0
+    int32_t nstages;    // log2(numharm) + 1
+    float thr[6];       // per stage
+    int32_t hmin[6];    // per stage
+    pss_raw_cand* out;
+    unsigned long long* counter;
+    int64_t cap;
+};
+cudaError_t launch_harm(const HarmArgs& a, cudaStream_t s);
+
+}  // namespace pss
+
+struct pss_ctx : public pss::Ctx {};
+struct pss_plan : public pss::Plan {};

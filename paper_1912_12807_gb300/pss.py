@@ -1,0 +1,350 @@
+"""ctypes binding of libpss (declared in include/pss.h).
+
+Argument marshalling only: every step of the search runs in the CUDA
+library.  Device buffers are torch tensors on the context's GPU; host
+buffers are numpy arrays.  The functions keep the C names.  If the shared
+library has not been built, importing this module raises -- there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libpss.so")
+
+PSS_OK, PSS_EINVAL, PSS_ENOMEM, PSS_ECAP, PSS_ETIMEOUT, PSS_ECUDA, PSS_EBUSY, PSS_ENOTREADY = 0, -1, -2, -3, -4, -5, -6, -7
+_NAMES = {0: "PSS_OK", -1: "PSS_EINVAL", -2: "PSS_ENOMEM", -3: "PSS_ECAP", -4: "PSS_ETIMEOUT", -5: "PSS_ECUDA",
+          -6: "PSS_EBUSY", -7: "PSS_ENOTREADY"}
+
+
+class PssError(RuntimeError):
+    def __init__(self, status: int, msg: str, needed: Optional[int] = None):
+        super().__init__("%s: %s" % (_NAMES.get(status, status), msg))
+        self.status = status
+        self.needed = needed
+
+
+class pss_fil_desc(C.Structure):
+    _fields_ = [("nchan", C.c_int32), ("nbits", C.c_int32), ("nsamp", C.c_int64), ("tsamp_s", C.c_double),
+                ("fch0_mhz", C.c_double), ("foff_mhz", C.c_double), ("layout", C.c_int32),
+                ("reserved", C.c_int32), ("chan_mask", C.POINTER(C.c_uint8))]
+
+
+class pss_dd_stage(C.Structure):
+    _fields_ = [("dm_lo", C.c_double), ("dm_step", C.c_double), ("n_dm", C.c_int32), ("ds", C.c_int32)]
+
+
+class pss_search_cfg(C.Structure):
+    _fields_ = [("zmax", C.c_int32), ("numharm", C.c_int32), ("dz", C.c_double), ("sigma_thr", C.c_double),
+                ("f_lo_hz", C.c_double), ("whiten_block", C.c_int32), ("halfwidth_extra", C.c_int32),
+                ("min_dm_hits", C.c_int32), ("reserved", C.c_int32)]
+
+
+RAW_DTYPE = np.dtype([("dm_idx", "<i4"), ("numharm", "<i4"), ("h", "<i4"), ("j", "<i4"), ("power", "<f4"),
+                      ("reserved", "<i4")])
+CAND_DTYPE = np.dtype([("dm_idx", "<i4"), ("numharm", "<i4"), ("dm", "<f8"), ("r", "<f8"), ("z", "<f8"),
+                       ("f_hz", "<f8"), ("sigma", "<f8"), ("power", "<f4"), ("dm_hits", "<i4"), ("h", "<i4"),
+                       ("j", "<i4")], align=True)
+
+# every symbol include/pss.h declares
+EXPORTS = ["pss_ctx_create", "pss_ctx_destroy", "pss_last_error", "pss_version", "pss_dd_plan", "pss_plan_info",
+           "pss_plan_trial_info", "pss_plan_free", "pss_dedisperse", "pss_spectrum", "pss_power_plane",
+           "pss_search_raw", "pss_sift", "pss_search_dm_batch", "pss_response", "pss_sigma_of_power",
+           "pss_power_threshold", "pss_ctx_profile", "pss_ctx_profile_read"]
+PROFILE_STAGES = ["unpack", "dedisperse", "fft", "whiten", "plane", "harmsum"]
+
+_lib = None
+
+
+def lib():
+    """The loaded libpss (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libpss.so not built (run python -m paper_1912_12807_gb300.build): " + LIB_PATH)
+    L = C.CDLL(LIB_PATH)
+    vp, i64, i32, st = C.c_void_p, C.c_int64, C.c_int32, C.c_int
+    P = C.POINTER
+    sig = {
+        "pss_ctx_create": (st, [C.c_int, P(vp)]),
+        "pss_ctx_destroy": (None, [vp]),
+        "pss_last_error": (C.c_char_p, []),
+        "pss_version": (C.c_char_p, []),
+        "pss_dd_plan": (st, [P(pss_fil_desc), P(pss_dd_stage), C.c_int, P(vp)]),
+        "pss_plan_info": (st, [vp, P(i64), P(i64), vp, vp]),
+        "pss_plan_trial_info": (st, [vp, i64, P(i32), P(i64), P(i64), P(i32)]),
+        "pss_plan_free": (None, [vp]),
+        "pss_dedisperse": (st, [vp, vp, P(pss_fil_desc), vp, C.c_int, i64, i64, vp, vp]),
+        "pss_spectrum": (st, [vp, vp, P(pss_fil_desc), vp, C.c_int, P(pss_search_cfg), i64, i64, vp, vp]),
+        "pss_power_plane": (st, [vp, vp, P(pss_fil_desc), vp, C.c_int, P(pss_search_cfg), i64, i64, vp, vp]),
+        "pss_search_raw": (st, [vp, vp, P(pss_fil_desc), vp, C.c_int, P(pss_search_cfg), i64, i64, vp, i64,
+                                P(i64), vp]),
+        "pss_sift": (st, [vp, P(pss_search_cfg), vp, i64, vp, i64, P(i64)]),
+        "pss_search_dm_batch": (st, [vp, vp, P(pss_fil_desc), vp, C.c_int, P(pss_search_cfg), i64, i64, vp, i64,
+                                     P(i64), vp]),
+        "pss_response": (st, [vp, vp, vp, i64, vp]),
+        "pss_ctx_profile": (st, [vp, C.c_int]),
+        "pss_ctx_profile_read": (st, [vp, vp, vp]),
+        "pss_sigma_of_power": (C.c_double, [i32, C.c_double]),
+        "pss_power_threshold": (C.c_double, [i32, C.c_double]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int, needed: Optional[int] = None):
+    if status != PSS_OK:
+        raise PssError(status, lib().pss_last_error().decode(), needed)
+
+
+# ---------------------------------------------------------------------------
+# descriptors
+# ---------------------------------------------------------------------------
+
+class FilDesc:
+    """Keeps a pss_fil_desc and the arrays it points to alive."""
+
+    def __init__(self, nchan, nsamp, tsamp_s, fch0_mhz, foff_mhz, nbits=8, layout=0, chan_mask=None):
+        self.mask = None if chan_mask is None else np.ascontiguousarray(chan_mask, dtype=np.uint8)
+        self.c = pss_fil_desc(int(nchan), int(nbits), int(nsamp), float(tsamp_s), float(fch0_mhz),
+                              float(foff_mhz), int(layout), 0,
+                              None if self.mask is None else self.mask.ctypes.data_as(C.POINTER(C.c_uint8)))
+
+    @classmethod
+    def of(cls, fil, chan_mask=None, layout=0):
+        return cls(fil.nchan, fil.nsamp, fil.tsamp_s, fil.fch0_mhz, fil.foff_mhz, fil.nbits, layout, chan_mask)
+
+
+def stages_array(stages) -> "C.Array":
+    arr = (pss_dd_stage * len(stages))()
+    for i, s in enumerate(stages):
+        arr[i] = pss_dd_stage(float(s.dm_lo), float(s.dm_step), int(s.n_dm), int(s.ds))
+    return arr
+
+
+def search_cfg(zmax=0, dz=2.0, numharm=8, sigma_thr=6.0, f_lo_hz=1.0, whiten_block=1024, halfwidth_extra=16,
+               min_dm_hits=1) -> pss_search_cfg:
+    return pss_search_cfg(int(zmax), int(numharm), float(dz), float(sigma_thr), float(f_lo_hz), int(whiten_block),
+                          int(halfwidth_extra), int(min_dm_hits), 0)
+
+
+def cfg_of(c) -> pss_search_cfg:
+    return search_cfg(c.zmax, c.dz, c.numharm, c.sigma_thr, c.f_lo_hz, c.whiten_block, c.halfwidth_extra,
+                      c.min_dm_hits)
+
+
+# ---------------------------------------------------------------------------
+# objects
+# ---------------------------------------------------------------------------
+
+class Context:
+    def __init__(self, device: int = 0):
+        h = C.c_void_p()
+        _check(lib().pss_ctx_create(int(device), C.byref(h)))
+        self.h = h
+        self.device = device
+
+    def profile(self, enable: bool = True):
+        _check(lib().pss_ctx_profile(self.h, int(enable)))
+
+    def profile_read(self):
+        """{stage: (ms, launches)} since the last enable/read (synchronises)."""
+        ms = np.zeros(len(PROFILE_STAGES), dtype=np.float64)
+        n = np.zeros(len(PROFILE_STAGES), dtype=np.int64)
+        _check(lib().pss_ctx_profile_read(self.h, ms.ctypes.data, n.ctypes.data))
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(PROFILE_STAGES)}
+
+    def close(self):
+        if self.h:
+            lib().pss_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Plan:
+    def __init__(self, desc: FilDesc, stages):
+        self.desc = desc
+        self._st = stages_array(stages)
+        h = C.c_void_p()
+        _check(lib().pss_dd_plan(C.byref(desc.c), self._st, len(stages), C.byref(h)))
+        self.h = h
+        ndm, dmax = C.c_int64(), C.c_int64()
+        _check(lib().pss_plan_info(h, C.byref(ndm), C.byref(dmax), None, None))
+        self.ndm, self.max_delay = ndm.value, dmax.value
+
+    def dms(self) -> np.ndarray:
+        out = np.empty(self.ndm, dtype=np.float64)
+        _check(lib().pss_plan_info(self.h, None, None, out.ctypes.data, None))
+        return out
+
+    def delays(self) -> np.ndarray:
+        out = np.empty((self.ndm, self.desc.c.nchan), dtype=np.int32)
+        _check(lib().pss_plan_info(self.h, None, None, None, out.ctypes.data))
+        return out
+
+    def trial(self, dm_idx: int):
+        s, nv, nfft, ds = C.c_int32(), C.c_int64(), C.c_int64(), C.c_int32()
+        _check(lib().pss_plan_trial_info(self.h, int(dm_idx), C.byref(s), C.byref(nv), C.byref(nfft), C.byref(ds)))
+        return dict(stage=s.value, nv=nv.value, nfft=nfft.value, ds=ds.value)
+
+    def close(self):
+        if self.h:
+            lib().pss_plan_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _data_arg(data):
+    """(pointer, on_device, keepalive) for a numpy array or a torch tensor."""
+    try:
+        import torch
+        if isinstance(data, torch.Tensor):
+            if not data.is_contiguous():
+                raise ValueError("data must be contiguous")
+            return C.c_void_p(data.data_ptr()), int(data.is_cuda), data
+    except ImportError:
+        pass
+    arr = np.ascontiguousarray(data)
+    return C.c_void_p(arr.ctypes.data), 0, arr
+
+
+def _stream(stream):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return None
+
+
+def _rows(plan: Plan, dm_begin: int, dm_end: int, key: str):
+    return [plan.trial(i)[key] for i in range(dm_begin, dm_end)]
+
+
+# ---------------------------------------------------------------------------
+# calls (C names)
+# ---------------------------------------------------------------------------
+
+def pss_dedisperse(ctx: Context, plan: Plan, data, dm_begin: int, dm_end: int, out=None, stream=None):
+    """int32 device tensor of the packed dedispersed series of [dm_begin, dm_end)."""
+    import torch
+    total = int(sum(_rows(plan, dm_begin, dm_end, "nv")))
+    if out is None:
+        out = torch.empty(max(total, 1), dtype=torch.int32, device="cuda:%d" % ctx.device)
+    p, dev, keep = _data_arg(data)
+    _check(lib().pss_dedisperse(ctx.h, plan.h, C.byref(plan.desc.c), p, dev, dm_begin, dm_end,
+                                C.c_void_p(out.data_ptr()), _stream(stream)))
+    return out[:total]
+
+
+def pss_spectrum(ctx: Context, plan: Plan, data, cfg: pss_search_cfg, dm_begin: int, dm_end: int, stream=None):
+    """complex64 device tensor: whitened half spectra, rows packed back to back."""
+    import torch
+    total = int(sum(n // 2 for n in _rows(plan, dm_begin, dm_end, "nfft")))
+    out = torch.empty(2 * max(total, 1), dtype=torch.float32, device="cuda:%d" % ctx.device)
+    p, dev, keep = _data_arg(data)
+    _check(lib().pss_spectrum(ctx.h, plan.h, C.byref(plan.desc.c), p, dev, C.byref(cfg), dm_begin, dm_end,
+                              C.c_void_p(out.data_ptr()), _stream(stream)))
+    return torch.view_as_complex(out[: 2 * total].view(-1, 2))
+
+
+def n_z(cfg: pss_search_cfg) -> int:
+    return int(round(2 * cfg.zmax / cfg.dz)) + 1 if cfg.zmax else 1
+
+
+def pss_power_plane(ctx: Context, plan: Plan, data, cfg: pss_search_cfg, dm_begin: int, dm_end: int, stream=None):
+    """float32 device tensor: planes [n_z][nfft] of [dm_begin, dm_end) packed back to back."""
+    import torch
+    nz = n_z(cfg)
+    total = int(sum(nz * n for n in _rows(plan, dm_begin, dm_end, "nfft")))
+    out = torch.empty(max(total, 1), dtype=torch.float32, device="cuda:%d" % ctx.device)
+    p, dev, keep = _data_arg(data)
+    _check(lib().pss_power_plane(ctx.h, plan.h, C.byref(plan.desc.c), p, dev, C.byref(cfg), dm_begin, dm_end,
+                                 C.c_void_p(out.data_ptr()), _stream(stream)))
+    return out[:total]
+
+
+def pss_search_raw(ctx: Context, plan: Plan, data, cfg: pss_search_cfg, dm_begin: int, dm_end: int,
+                   cap: int = 1 << 16, stream=None) -> np.ndarray:
+    p, dev, keep = _data_arg(data)
+    n = C.c_int64()
+    while True:
+        out = np.zeros(cap, dtype=RAW_DTYPE)
+        st = lib().pss_search_raw(ctx.h, plan.h, C.byref(plan.desc.c), p, dev, C.byref(cfg), dm_begin, dm_end,
+                                  out.ctypes.data, cap, C.byref(n), _stream(stream))
+        if st == PSS_ECAP:
+            cap = n.value
+            continue
+        _check(st)
+        return out[: n.value]
+
+
+def pss_sift(plan: Plan, cfg: pss_search_cfg, raw: np.ndarray, cap: int = 1 << 14) -> np.ndarray:
+    raw = np.ascontiguousarray(raw, dtype=RAW_DTYPE)
+    n = C.c_int64()
+    while True:
+        out = np.zeros(cap, dtype=CAND_DTYPE)
+        st = lib().pss_sift(plan.h, C.byref(cfg), raw.ctypes.data, raw.shape[0], out.ctypes.data, cap, C.byref(n))
+        if st == PSS_ECAP:
+            cap = n.value
+            continue
+        _check(st)
+        return out[: n.value]
+
+
+def pss_search_dm_batch(ctx: Context, plan: Plan, data, cfg: pss_search_cfg, dm_begin: int, dm_end: int,
+                        cap: int = 1 << 14, stream=None) -> np.ndarray:
+    p, dev, keep = _data_arg(data)
+    n = C.c_int64()
+    while True:
+        out = np.zeros(cap, dtype=CAND_DTYPE)
+        st = lib().pss_search_dm_batch(ctx.h, plan.h, C.byref(plan.desc.c), p, dev, C.byref(cfg), dm_begin, dm_end,
+                                       out.ctypes.data, cap, C.byref(n), _stream(stream))
+        if st == PSS_ECAP:
+            cap = n.value
+            continue
+        _check(st)
+        return out[: n.value]
+
+
+def pss_response(ctx: Context, q: Sequence[float], z: Sequence[float]) -> np.ndarray:
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    out = np.empty(2 * q.shape[0], dtype=np.float64)
+    _check(lib().pss_response(ctx.h, q.ctypes.data, z.ctypes.data, q.shape[0], out.ctypes.data))
+    return out[0::2] + 1j * out[1::2]
+
+
+def pss_sigma_of_power(numharm: int, power: float) -> float:
+    return lib().pss_sigma_of_power(int(numharm), float(power))
+
+
+def pss_power_threshold(numharm: int, sigma: float) -> float:
+    return lib().pss_power_threshold(int(numharm), float(sigma))
+
+
+def pss_version() -> str:
+    return lib().pss_version().decode()

@@ -1,0 +1,169 @@
+"""Host-side checks of libpss that need no GPU: the shared library loads,
+exports every symbol include/pss.h declares, has the struct layout the
+binding assumes, and its host-only calls (plan, statistics, sift) agree
+with the oracle."""
+import os
+import re
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import plan as OP
+from oracle import sift as OS
+from oracle import stats as OST
+from paper_1912_12807_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1912_12807_gb300 import build, pss
+    if not os.path.exists(pss.LIB_PATH):
+        build.build()
+    return pss
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "pss.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(pss_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(L):
+    lib = L.lib()
+    names = _declared()
+    assert len(names) >= 17
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(L.EXPORTS) == names
+
+
+def test_struct_layout_matches_binding(L):
+    import ctypes as C
+    src = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "pss.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(pss_fil_desc), sizeof(pss_dd_stage), sizeof(pss_search_cfg),
+         sizeof(pss_raw_cand), sizeof(pss_cand), offsetof(pss_cand, power), offsetof(pss_fil_desc, chan_mask));
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write(src)
+        exe = os.path.join(d, "t")
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        got = [int(x) for x in subprocess.check_output([exe]).split()]
+    want = [C.sizeof(L.pss_fil_desc), C.sizeof(L.pss_dd_stage), C.sizeof(L.pss_search_cfg),
+            L.RAW_DTYPE.itemsize, L.CAND_DTYPE.itemsize, L.CAND_DTYPE.fields["power"][1],
+            L.pss_fil_desc.chan_mask.offset]
+    assert got == want
+
+
+def test_version_and_no_device_error(L):
+    assert "sm_103a" in L.pss_version()
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    with pytest.raises(L.PssError) as e:
+        L.Context(0)
+    assert e.value.status in (L.PSS_ECUDA, L.PSS_EINVAL)
+
+
+@pytest.mark.parametrize("wl", ["small", "drift", "pmps"])
+def test_plan_delay_table_bit_exact(L, wl):
+    shapes = {
+        "small": (64, 1 << 16, 2e-4, 1200.0, 1500.0, [synth.Stage(0.0, 1.0, 101, 1)]),
+        "drift": (256, 1 << 18, 2e-4, 1050.0, 1450.0, [synth.Stage(0.0, 0.5, 1001, 1)]),
+        "pmps": (96, 1 << 23, 2.5e-4, 1230.0, 1518.0, synth.stages_from_table(
+            [(0.0, 200.0, 0.5, 1), (200.0, 600.0, 1.0, 2), (600.0, 2000.0, 5.0, 4)], True)),
+    }
+    nchan, nsamp, ts, lo, hi, stages = shapes[wl]
+    fch0, foff = synth.band(lo, hi, nchan)
+    desc = L.FilDesc(nchan, nsamp, ts, fch0, foff, 8 if wl != "pmps" else 1)
+    p = L.Plan(desc, stages)
+    op = OP.Plan(nchan, nsamp, ts, fch0, foff, stages)
+    np.testing.assert_array_equal(p.dms(), op.dms)
+    np.testing.assert_array_equal(p.delays(), op.delays)
+    assert p.max_delay == op.max_delay
+    for i in (0, p.ndm // 2, p.ndm - 1):
+        t = p.trial(i)
+        nv, nfft = op.nv_nfft(i)
+        assert (t["nv"], t["nfft"], t["ds"]) == (nv, nfft, int(op.ds_of[i]))
+
+
+def test_plan_rejects_bad_input(L):
+    desc = L.FilDesc(64, 1000, 2e-4, 1202.34375, 4.6875)
+    with pytest.raises(L.PssError) as e:
+        L.Plan(desc, [synth.Stage(0.0, 1.0, 2000, 1)])  # delays exceed the file
+    assert e.value.status == L.PSS_EINVAL
+    with pytest.raises(L.PssError):
+        L.Plan(desc, [synth.Stage(0.0, 1.0, 10, 3)])     # ds not a power of two
+    with pytest.raises(L.PssError):
+        L.Plan(desc, [synth.Stage(0.0, 1.0, 0, 1)])      # empty stage
+
+
+def test_sigma_and_threshold_match_oracle(L):
+    for n in (1, 2, 4, 8, 16, 32):
+        # (S well below n gives p ~ 1, where log Q itself cancels; no detection lives there)
+        for S in (1.0, 8.0, 25.0, 60.0, 300.0, 2000.0, 12000.0):
+            if S < 2 * n + 5:
+                continue
+            a = L.pss_sigma_of_power(n, S)
+            b = OST.sigma_of(n, S)
+            assert abs(a - b) <= 1e-9 * max(1.0, abs(b)), (n, S, a, b)
+        assert abs(L.pss_power_threshold(n, 6.0) - OST.power_threshold(n, 6.0)) < 1e-8
+
+
+def _random_raw(rng, ndm, per_dm, nfft, nz):
+    rows = []
+    for d in range(ndm):
+        for _ in range(per_dm):
+            n = int(2 ** rng.integers(0, 4))
+            h = int(rng.integers(0, 400))
+            j = int(rng.integers(0, nz))
+            rows.append((d, n, h, j, np.float32(rng.uniform(20, 80)), 0))
+    return np.array(rows, dtype=[("dm_idx", "<i4"), ("numharm", "<i4"), ("h", "<i4"), ("j", "<i4"),
+                                 ("power", "<f4"), ("reserved", "<i4")])
+
+
+@pytest.mark.parametrize("zmax,min_hits", [(0, 1), (20, 1), (20, 2)])
+def test_sift_matches_oracle(L, zmax, min_hits):
+    rng = np.random.default_rng(zmax + min_hits)
+    nchan, nsamp = 64, 1 << 14
+    fch0, foff = synth.band(1200.0, 1500.0, nchan)
+    stages = [synth.Stage(0.0, 1.0, 12, 1)]
+    desc = L.FilDesc(nchan, nsamp, 2e-4, fch0, foff)
+    p = L.Plan(desc, stages)
+    op = OP.Plan(nchan, nsamp, 2e-4, fch0, foff, stages)
+    dz = 2.0
+    nz = int(2 * zmax / dz) + 1 if zmax else 1
+    Z = int(zmax / dz)
+    raw = _random_raw(rng, 12, 40, 8192, nz)
+    cfg = L.search_cfg(zmax=zmax, dz=dz, numharm=8, min_dm_hits=min_hits)
+    got = L.pss_sift(p, cfg, raw)
+    by_dm = {}
+    for c in raw:
+        n, h, j = int(c["numharm"]), int(c["h"]), int(c["j"])
+        r, z = OS.fundamental(n, h, j, Z, dz)
+        by_dm.setdefault(int(c["dm_idx"]), []).append(dict(
+            dm_idx=int(c["dm_idx"]), numharm=n, h=h, j=j, r=r, z=z, power=float(c["power"]),
+            sigma=OST.sigma_of(n, float(c["power"]))))
+    ref = OS.sift(by_dm, dz, min_hits)
+    assert len(got) == len(ref)
+    for g, r in zip(got, ref):
+        assert (int(g["dm_idx"]), int(g["numharm"]), int(g["h"]), int(g["j"]), int(g["dm_hits"])) == \
+               (r["dm_idx"], r["numharm"], r["h"], r["j"], r["dm_hits"])
+        assert g["r"] == r["r"] and g["z"] == r["z"]
+        assert abs(g["sigma"] - r["sigma"]) < 1e-9 * r["sigma"]
+        assert g["dm"] == op.dms[r["dm_idx"]]
+        assert abs(g["f_hz"] - r["r"] / op.t_span(r["dm_idx"])) < 1e-12 * g["f_hz"] + 1e-15
