@@ -200,7 +200,7 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    wl = synth.workload_driftscan(seed=1002 + rank)
+    wl = synth.workload_driftscan(seed=1002 + rank, n_dm=args.dm_trials)
     fil = wl.fil
     ctx = pss.Context(local_rank)
     plan = pss.Plan(pss.FilDesc.of(fil), wl.stages)
@@ -298,7 +298,7 @@ def run_ours(args, rank, world, local_rank):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "i32+f32", "data": "synthetic",
-            "config": _config(), "files_per_s": world * 1e3 / ms, "s_per_file": ms / 1e3,
+            "config": _config({"dm_trials": ndm}), "files_per_s": world * 1e3 / ms, "s_per_file": ms / 1e3,
             "realtime_budget_s": REALTIME_S, "realtime_factor": REALTIME_S / (ms / 1e3),
             "roofline": roof,
             "e2e": {"value": world * ndm / (e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": bi,
@@ -322,6 +322,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dm-trials", type=int, default=1001,
+                    help="DM trials of the plan (0.5 step from DM 0); smaller values make profiling cases")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -17,10 +17,11 @@
  *  - Pointers documented as "device" must be CUDA device (or managed)
  *    memory of the context's device; "host" pointers are ordinary host
  *    memory (pinned memory makes uploads faster but is not required).
- *  - `stream` is a cudaStream_t passed as void*; NULL means the context's
- *    own stream.  Calls that return results on the host synchronise that
- *    stream before they return; calls that only write device memory are
- *    asynchronous with respect to the host.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the CUDA
+ *    legacy default stream (as for CUDA library calls).  Calls that return
+ *    results on the host synchronise that stream before they return; calls
+ *    that only write device memory are asynchronous with respect to the
+ *    host and ordered on `stream`.
  *  - The caller owns every buffer it passes.  The library owns pss_ctx,
  *    pss_plan and pss_server objects until the matching destroy/free call.
  *  - A pss_ctx may be used by one host thread at a time.
@@ -136,8 +137,8 @@ typedef struct {
 
 /* ---- context ---------------------------------------------------------- */
 
-/* Create a context on CUDA device `device`: its own stream and a device
- * workspace that grows on demand and is freed by pss_ctx_destroy. */
+/* Create a context on CUDA device `device` with a device workspace that
+ * grows on demand and is freed by pss_ctx_destroy. */
 pss_status pss_ctx_create(int device, pss_ctx** out);
 void pss_ctx_destroy(pss_ctx* ctx);
 /* Message of the last failed call made by this thread ("" if none). */

@@ -5,7 +5,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "pss_internal.h"
@@ -58,8 +60,25 @@ ProfScope::~ProfScope() {
 
 namespace {
 
+// Host phase timing, printed to stderr when PSS_TIMING is set in the
+// environment (tracing of the host side of a call).
+struct HostTimer {
+    bool on;
+    std::chrono::steady_clock::time_point t;
+    HostTimer() : on(getenv("PSS_TIMING") != nullptr), t(std::chrono::steady_clock::now()) {}
+    void mark(const char* what) {
+        if (!on) return;
+        auto n = std::chrono::steady_clock::now();
+        fprintf(stderr, "[pss] %-14s %8.3f ms\n", what, std::chrono::duration<double>(n - t).count() * 1e3);
+        t = n;
+    }
+};
+
+// NULL selects the legacy default stream (stream handle 0 in a library
+// compiled without per-thread default streams).
 cudaStream_t pick_stream(pss_ctx* ctx, void* stream) {
-    return stream ? (cudaStream_t)stream : ctx->stream;
+    (void)ctx;
+    return (cudaStream_t)stream;
 }
 
 pss_status check_common(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const void* data,
@@ -247,7 +266,9 @@ pss_status run_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil,
                     cudaStream_t s, int64_t dev_cap) {
     int32_t ck = 0;
     int64_t pitch = 0;
+    HostTimer tm;
     PSS_TRY(stage_input(ctx, plan, fil, data, on_dev, dm_begin, dm_end, s, &ck, &pitch));
+    tm.mark("stage_input");
     if (dm_end == dm_begin) return PSS_OK;
     PSS_TRY(ensure_templates(ctx, cfg, s));
     const int nz = nz_of(cfg);
@@ -367,30 +388,30 @@ pss_status run_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil,
     return PSS_OK;
 }
 
-bool raw_less(const pss_raw_cand& a, const pss_raw_cand& b) {
-    if (a.dm_idx != b.dm_idx) return a.dm_idx < b.dm_idx;
-    if (a.numharm != b.numharm) return a.numharm < b.numharm;
-    if (a.j != b.j) return a.j < b.j;
-    return a.h < b.h;
-}
-
 pss_status search_raw_vec(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const void* data, int on_dev,
                           const pss_search_cfg* cfg, int64_t dm_begin, int64_t dm_end, std::vector<pss_raw_cand>* out,
-                          cudaStream_t s) {
+                          cudaStream_t s, bool sorted) {
     PSS_TRY(check_common(ctx, plan, fil, data, dm_begin, dm_end));
     PSS_TRY(check_cfg(cfg, *plan));
     int64_t cap = ctx->cands.bytes ? (int64_t)(ctx->cands.bytes / sizeof(pss_raw_cand)) : (int64_t)1 << 20;
+    HostTimer tm;
     for (int attempt = 0; attempt < 2; ++attempt) {
         PSS_TRY(run_path(ctx, plan, fil, data, on_dev, cfg, dm_begin, dm_end, MODE_SEARCH, Outputs(), s, cap));
+        tm.mark("enqueue");
         unsigned long long cnt = 0;
         if (dm_end > dm_begin)
             PSS_CUDA(cudaMemcpyAsync(&cnt, ctx->counter.p, sizeof(cnt), cudaMemcpyDeviceToHost, s));
         PSS_CUDA(cudaStreamSynchronize(s));
+        tm.mark("gpu");
         if ((int64_t)cnt <= cap) {
             out->resize(cnt);
             if (cnt)
-                PSS_CUDA(cudaMemcpy(out->data(), ctx->cands.p, cnt * sizeof(pss_raw_cand), cudaMemcpyDeviceToHost));
-            std::sort(out->begin(), out->end(), raw_less);
+                PSS_CUDA(cudaMemcpyAsync(out->data(), ctx->cands.p, cnt * sizeof(pss_raw_cand),
+                                         cudaMemcpyDeviceToHost, s));
+            PSS_CUDA(cudaStreamSynchronize(s));
+            tm.mark("download");
+            if (sorted) sort_raw(out, plan->ndm());
+            tm.mark("sort");
             return PSS_OK;
         }
         cap = (int64_t)cnt + 1024;  // overflowed the device buffer: grow and redo
@@ -587,7 +608,7 @@ pss_status pss_search_raw(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc
     if (ctx) PSS_CUDA(cudaSetDevice(ctx->device));
     std::vector<pss_raw_cand> v;
     PSS_TRY(search_raw_vec(ctx, plan, fil, data, data_on_device, cfg, dm_begin, dm_end, &v,
-                           ctx ? pick_stream(ctx, stream) : nullptr));
+                           ctx ? pick_stream(ctx, stream) : nullptr, true));
     *n_out = (int64_t)v.size();
     if ((int64_t)v.size() > cap) return fail(PSS_ECAP, "pss_search_raw: output capacity too small");
     if (!v.empty()) {
@@ -621,9 +642,11 @@ pss_status pss_search_dm_batch(pss_ctx* ctx, const pss_plan* plan, const pss_fil
     if (ctx) PSS_CUDA(cudaSetDevice(ctx->device));
     std::vector<pss_raw_cand> raw;
     PSS_TRY(search_raw_vec(ctx, plan, fil, data, data_on_device, cfg, dm_begin, dm_end, &raw,
-                           ctx ? pick_stream(ctx, stream) : nullptr));
+                           ctx ? pick_stream(ctx, stream) : nullptr, false));
     std::vector<pss_cand> v;
+    HostTimer tm;
     PSS_TRY(sift(*plan, *cfg, raw.data(), (int64_t)raw.size(), &v));
+    tm.mark("sift");
     *n_out = (int64_t)v.size();
     if ((int64_t)v.size() > cap) return fail(PSS_ECAP, "pss_search_dm_batch: output capacity too small");
     if (!v.empty()) {

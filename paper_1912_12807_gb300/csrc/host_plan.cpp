@@ -108,9 +108,10 @@ pss_status build_plan(const pss_fil_desc* fil, const pss_dd_stage* st, int nst, 
 
 double log_q(int n, double S) {
     if (S <= 0) return 0.0;
+    if (n > 64) n = 64;
     const double lS = log(S);
     double mx = -1e300;
-    std::vector<double> t(n);
+    double t[64];
     for (int j = 0; j < n; ++j) {
         t[j] = j * lS - S - lgamma((double)j + 1.0);
         mx = std::max(mx, t[j]);

@@ -77,27 +77,87 @@ std::vector<std::vector<int>> link_groups(const std::vector<Item>& it, double dz
     return groups;
 }
 
+// Representative of a linked group: the highest sigma (ties: lower n, r, z,
+// DM index).  sigma is strictly increasing in S for a fixed n, so only the
+// largest-S member of each harmonic stage can win; sigma is evaluated for
+// those alone (items with sigma < 0 have not been evaluated yet).
+int pick_rep(std::vector<Item>& items, const std::vector<int>& g) {
+    int best_of_n[8];
+    for (int i = 0; i < 8; ++i) best_of_n[i] = -1;
+    for (int k : g) {
+        const Item& a = items[k];
+        int li = 0;
+        while ((1 << li) < a.n && li < 7) ++li;
+        int& b = best_of_n[li];
+        if (b < 0) {
+            b = k;
+            continue;
+        }
+        const Item& c = items[b];
+        if (a.power > c.power || (a.power == c.power && (a.r < c.r || (a.r == c.r && (a.z < c.z || (a.z == c.z && a.dm_idx < c.dm_idx))))))
+            b = k;
+    }
+    int best = -1;
+    for (int i = 0; i < 8; ++i) {
+        const int k = best_of_n[i];
+        if (k < 0) continue;
+        if (items[k].sigma < 0) items[k].sigma = sigma_of_power(items[k].n, (double)items[k].power);
+        if (best < 0 || rep_less(items[k], items[best])) best = k;
+    }
+    return best;
+}
+
 }  // namespace
+
+void bucket_by_dm(const pss_raw_cand* raw, int64_t n, int64_t ndm, std::vector<int64_t>* order,
+                  std::vector<std::pair<int64_t, int64_t>>* buckets) {
+    std::vector<int64_t> cnt((size_t)ndm + 1, 0);
+    for (int64_t i = 0; i < n; ++i) cnt[(size_t)raw[i].dm_idx + 1]++;
+    for (int64_t d = 0; d < ndm; ++d) cnt[(size_t)d + 1] += cnt[(size_t)d];
+    order->assign((size_t)n, 0);
+    std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
+    for (int64_t i = 0; i < n; ++i) (*order)[(size_t)pos[(size_t)raw[i].dm_idx]++] = i;
+    buckets->clear();
+    for (int64_t d = 0; d < ndm; ++d)
+        if (cnt[(size_t)d + 1] > cnt[(size_t)d]) buckets->push_back({cnt[(size_t)d], cnt[(size_t)d + 1]});
+}
+
+void sort_raw(std::vector<pss_raw_cand>* v, int64_t ndm) {
+    std::vector<int64_t> order;
+    std::vector<std::pair<int64_t, int64_t>> bk;
+    bucket_by_dm(v->data(), (int64_t)v->size(), ndm, &order, &bk);
+    std::vector<pss_raw_cand> out(v->size());
+    for (size_t i = 0; i < order.size(); ++i) out[i] = (*v)[(size_t)order[i]];
+    parallel_for((int64_t)bk.size(), 8, [&](int64_t b) {
+        std::sort(out.begin() + bk[(size_t)b].first, out.begin() + bk[(size_t)b].second,
+                  [](const pss_raw_cand& x, const pss_raw_cand& y) {
+                      if (x.numharm != y.numharm) return x.numharm < y.numharm;
+                      if (x.j != y.j) return x.j < y.j;
+                      return x.h < y.h;
+                  });
+    });
+    v->swap(out);
+}
 
 pss_status sift(const Plan& P, const pss_search_cfg& cfg, const pss_raw_cand* raw, int64_t n,
                 std::vector<pss_cand>* out) {
     out->clear();
     const int Z = cfg.zmax ? (int)llround(cfg.zmax / cfg.dz) : 0;
     const double dz = cfg.dz;
-    // bucket by DM trial
-    std::vector<int64_t> idx(n);
-    std::iota(idx.begin(), idx.end(), 0);
-    std::stable_sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) { return raw[a].dm_idx < raw[b].dm_idx; });
-    std::vector<Item> survivors;
-    int64_t p = 0;
-    while (p < n) {
-        int64_t q = p;
-        const int32_t dm = raw[idx[p]].dm_idx;
-        if (dm < 0 || dm >= P.ndm()) return fail(PSS_EINVAL, "pss_sift: dm_idx out of range");
+    for (int64_t i = 0; i < n; ++i) {
+        if (raw[i].dm_idx < 0 || raw[i].dm_idx >= P.ndm()) return fail(PSS_EINVAL, "pss_sift: dm_idx out of range");
+        if (raw[i].numharm < 1 || raw[i].numharm > 64 || (raw[i].numharm & (raw[i].numharm - 1))) return fail(PSS_EINVAL, "pss_sift: numharm must be a power of two in [1, 64]");
+    }
+    std::vector<int64_t> order;
+    std::vector<std::pair<int64_t, int64_t>> bk;
+    bucket_by_dm(raw, n, P.ndm(), &order, &bk);
+    // within each DM trial (independent: in parallel)
+    std::vector<std::vector<Item>> surv(bk.size());
+    parallel_for((int64_t)bk.size(), 4, [&](int64_t b) {
         std::vector<Item> items;
-        while (q < n && raw[idx[q]].dm_idx == dm) {
-            const pss_raw_cand& c = raw[idx[q]];
-            if (c.numharm < 1) return fail(PSS_EINVAL, "pss_sift: numharm < 1");
+        items.reserve((size_t)(bk[(size_t)b].second - bk[(size_t)b].first));
+        for (int64_t q = bk[(size_t)b].first; q < bk[(size_t)b].second; ++q) {
+            const pss_raw_cand& c = raw[order[(size_t)q]];
             Item it;
             it.dm_idx = c.dm_idx;
             it.n = c.numharm;
@@ -106,25 +166,19 @@ pss_status sift(const Plan& P, const pss_search_cfg& cfg, const pss_raw_cand* ra
             it.power = c.power;
             it.r = (double)c.h / (double)(2 * c.numharm);
             it.z = (double)(c.j - Z) * dz / (double)c.numharm;
-            it.sigma = sigma_of_power(c.numharm, (double)c.power);
+            it.sigma = -1.0;  // evaluated on demand by pick_rep
             items.push_back(it);
-            ++q;
         }
-        for (auto& g : link_groups(items, dz)) {
-            int best = g[0];
-            for (int k : g)
-                if (rep_less(items[k], items[best])) best = k;
-            survivors.push_back(items[best]);
-        }
-        p = q;
-    }
+        for (auto& g : link_groups(items, dz)) surv[(size_t)b].push_back(items[pick_rep(items, g)]);
+    });
+    std::vector<Item> survivors;
+    for (auto& v : surv) survivors.insert(survivors.end(), v.begin(), v.end());
+
+    // across DM trials
     for (auto& g : link_groups(survivors, dz)) {
-        int best = g[0];
+        const int best = pick_rep(survivors, g);
         std::vector<int32_t> dms;
-        for (int k : g) {
-            if (rep_less(survivors[k], survivors[best])) best = k;
-            dms.push_back(survivors[k].dm_idx);
-        }
+        for (int k : g) dms.push_back(survivors[k].dm_idx);
         std::sort(dms.begin(), dms.end());
         int hits = (int)(std::unique(dms.begin(), dms.end()) - dms.begin());
         if (hits < cfg.min_dm_hits) continue;

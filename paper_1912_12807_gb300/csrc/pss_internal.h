@@ -4,7 +4,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <atomic>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/pss.h"
@@ -60,6 +63,39 @@ double log_q(int n, double S);
 double sigma_from_logp(double logp);
 double sigma_of_power(int n, double S);
 double power_threshold(int n, double sigma);
+
+// ---- host parallel loop -----------------------------------------------------
+// f(i) for i in [0, n) on up to hardware_concurrency threads (dynamic
+// scheduling in chunks of `grain`).
+template <class F>
+void parallel_for(int64_t n, int64_t grain, F&& f) {
+    unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    if (n <= grain || nt == 1) {
+        for (int64_t i = 0; i < n; ++i) f(i);
+        return;
+    }
+    nt = (unsigned)std::min<int64_t>(nt, (n + grain - 1) / grain);
+    std::atomic<int64_t> next{0};
+    auto body = [&]() {
+        for (;;) {
+            const int64_t b = next.fetch_add(grain);
+            if (b >= n) break;
+            const int64_t e = std::min(n, b + grain);
+            for (int64_t i = b; i < e; ++i) f(i);
+        }
+    };
+    std::vector<std::thread> th;
+    for (unsigned t = 1; t < nt; ++t) th.emplace_back(body);
+    body();
+    for (auto& t : th) t.join();
+}
+
+// Stable counting sort of raw detections by DM index: returns the order
+// and, for each DM present, [begin, end) into it.
+void bucket_by_dm(const pss_raw_cand* raw, int64_t n, int64_t ndm, std::vector<int64_t>* order,
+                  std::vector<std::pair<int64_t, int64_t>>* buckets);
+// Sort raw detections by (dm_idx, numharm, j, h) in place.
+void sort_raw(std::vector<pss_raw_cand>* v, int64_t ndm);
 
 // ---- sift (host) ----------------------------------------------------------
 pss_status sift(const Plan& P, const pss_search_cfg& cfg, const pss_raw_cand* raw, int64_t n,
