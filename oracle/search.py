@@ -42,7 +42,7 @@ def search_trial(x_cm, P: _plan.Plan, dm_idx: int, cfg, thr: Optional[dict] = No
     for n, h, j, S in _hs.raw_candidates(plane, cfg.numharm, Z, thr, T, cfg.f_lo_hz):
         r, z = _sift.fundamental(n, h, j, Z, cfg.dz)
         out.append(dict(dm_idx=int(dm_idx), dm=float(P.dms[dm_idx]), numharm=n, h=h, j=j,
-                        power=S, sigma=_st.sigma_of(n, S), r=r, z=z, f_hz=r / T))
+                        power=S, sigma=_st.sigma_of(n, S), r=r, z=z, zq=_sift.zq(n, j, Z), f_hz=r / T))
     return out
 
 

@@ -3,9 +3,11 @@
 The paper names the step only.  Reading used here:
 
 * Each raw candidate is moved to its fundamental: r = h / (2n) bins,
-  z = (j - Z) dz / n (both exact in FP64 for power-of-two n).
+  z = (j - Z) dz / n.
 * Within one DM trial, candidates are linked when |dr| <= 1 bin and
   |dz| <= dz (single linkage); each linked group keeps one representative.
+  Both conditions are evaluated exactly, on rationals (r = h/(2n) and
+  z/dz = (j - Z)/n), not on rounded floating-point values.
 * Survivors of all DM trials are linked again the same way; each group
   keeps one representative and records dm_hits, the number of distinct DM
   trials in the group; groups with dm_hits < min_dm_hits are dropped.
@@ -15,6 +17,7 @@ The paper names the step only.  Reading used here:
 """
 from __future__ import annotations
 
+from fractions import Fraction
 from typing import Dict, List
 
 
@@ -25,15 +28,24 @@ def _find(par, i):
     return i
 
 
+def _rz(c: Dict, dz: float):
+    """Exact (r, z/dz): from (h, j, n, Z) when the candidate carries them,
+    else from its (binary-exact) floats."""
+    if "zq" in c:
+        return Fraction(c["h"], 2 * c["numharm"]), c["zq"]
+    return Fraction(c["r"]), Fraction(c["z"]) / Fraction(dz)
+
+
 def _groups(items: List[Dict], dz: float) -> List[List[int]]:
-    order = sorted(range(len(items)), key=lambda i: (items[i]["r"], items[i]["z"], i))
+    ex = [_rz(c, dz) for c in items]
+    order = sorted(range(len(items)), key=lambda i: (ex[i][0], ex[i][1], i))
     par = list(range(len(items)))
     for a_pos, a in enumerate(order):
-        ra, za = items[a]["r"], items[a]["z"]
+        ra, za = ex[a]
         for b in order[a_pos + 1:]:
-            if items[b]["r"] - ra > 1.0:
+            if ex[b][0] - ra > 1:
                 break
-            if abs(items[b]["z"] - za) <= dz:
+            if abs(ex[b][1] - za) <= 1:
                 pa, pb = _find(par, a), _find(par, b)
                 if pa != pb:
                     par[max(pa, pb)] = min(pa, pb)
@@ -48,7 +60,12 @@ def _rep_key(c: Dict):
 
 
 def fundamental(n: int, h: int, j: int, Z: int, dz: float):
+    """(r, z) of the fundamental as floats; zq(n, j, Z) gives z/dz exactly."""
     return float(h) / float(2 * n), float(j - Z) * dz / float(n)
+
+
+def zq(n: int, j: int, Z: int) -> Fraction:
+    return Fraction(j - Z, n)
 
 
 def sift_within(cands: List[Dict], dz: float) -> List[Dict]:

@@ -9,6 +9,9 @@
 // lower z, lower DM index.  Output is sorted by (DM index, n, r, z).
 #include <math.h>
 
+#include <stdint.h>
+#include <stdlib.h>
+
 #include <algorithm>
 #include <numeric>
 #include <vector>
@@ -23,6 +26,7 @@ struct Item {
     int32_t dm_idx, n, h, j;
     float power;
     double r, z, sigma;
+    int64_t kr, kz;  // exact link coordinates: 64 r and 32 z / dz
 };
 
 int find_root(std::vector<int>& par, int i) {
@@ -41,38 +45,100 @@ bool rep_less(const Item& a, const Item& b) {
     return a.dm_idx < b.dm_idx;
 }
 
-// Group indices [0, items.size()) by single linkage in (r, z).
-std::vector<std::vector<int>> link_groups(const std::vector<Item>& it, double dz) {
+// Group indices [0, items.size()) by single linkage: i and j are linked
+// when |r_i - r_j| <= 1 and |z_i - z_j| <= dz.  The test runs on exact
+// integers: kr = 64 r = h (32/n) and kz = 32 z / dz = (j - Z)(32/n), so the
+// conditions are |dkr| <= 64 and |dkz| <= 32.  Items are bucketed into cells
+// of 64 x 32 units: two items of one cell always link, so a cell is one
+// union-find node, and only the 4 forward-neighbouring cells need pair tests
+// (skipped when their bounding boxes are too far apart or they are already
+// joined).
+struct Cell {
+    int64_t cr, cz;
+    int begin, end;  // range in the sorted order
+    int64_t r_lo, r_hi, z_lo, z_hi;
+};
+
+std::vector<std::vector<int>> link_groups(const std::vector<Item>& it, double /*dz*/) {
     const int n = (int)it.size();
+    auto fdiv = [](int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); };
     std::vector<int> order(n);
     std::iota(order.begin(), order.end(), 0);
+    std::vector<int64_t> cr(n), cz(n);
+    for (int i = 0; i < n; ++i) {
+        cr[i] = fdiv(it[i].kr, 64);
+        cz[i] = fdiv(it[i].kz, 32);
+    }
     std::sort(order.begin(), order.end(), [&](int a, int b) {
-        if (it[a].r != it[b].r) return it[a].r < it[b].r;
-        if (it[a].z != it[b].z) return it[a].z < it[b].z;
+        if (cr[a] != cr[b]) return cr[a] < cr[b];
+        if (cz[a] != cz[b]) return cz[a] < cz[b];
         return a < b;
     });
-    std::vector<int> par(n);
+    std::vector<Cell> cells;
+    for (int p = 0; p < n;) {
+        int q = p;
+        Cell c{cr[order[p]], cz[order[p]], p, p, INT64_MAX, INT64_MIN, INT64_MAX, INT64_MIN};
+        while (q < n && cr[order[q]] == c.cr && cz[order[q]] == c.cz) {
+            const Item& x = it[order[q]];
+            c.r_lo = std::min(c.r_lo, x.kr);
+            c.r_hi = std::max(c.r_hi, x.kr);
+            c.z_lo = std::min(c.z_lo, x.kz);
+            c.z_hi = std::max(c.z_hi, x.kz);
+            ++q;
+        }
+        c.end = q;
+        cells.push_back(c);
+        p = q;
+    }
+    const int nc = (int)cells.size();
+    std::vector<int> par(nc);
     std::iota(par.begin(), par.end(), 0);
-    for (int p = 0; p < n; ++p) {
-        const Item& a = it[order[p]];
-        for (int q = p + 1; q < n; ++q) {
-            const Item& b = it[order[q]];
-            if (b.r - a.r > 1.0) break;
-            if (fabs(b.z - a.z) <= dz) {
-                int ra = find_root(par, order[p]), rb = find_root(par, order[q]);
-                if (ra != rb) par[std::max(ra, rb)] = std::min(ra, rb);
+    auto find_cell = [&](int64_t r, int64_t z) -> int {
+        int lo = 0, hi = nc;
+        while (lo < hi) {
+            const int mid = (lo + hi) / 2;
+            if (cells[mid].cr < r || (cells[mid].cr == r && cells[mid].cz < z)) lo = mid + 1;
+            else hi = mid;
+        }
+        return (lo < nc && cells[lo].cr == r && cells[lo].cz == z) ? lo : -1;
+    };
+    const int64_t nb[4][2] = {{0, 1}, {1, -1}, {1, 0}, {1, 1}};
+    for (int a = 0; a < nc; ++a) {
+        const Cell& A = cells[a];
+        for (auto& d : nb) {
+            const int b = find_cell(A.cr + d[0], A.cz + d[1]);
+            if (b < 0) continue;
+            const Cell& B = cells[b];
+            if (find_root(par, a) == find_root(par, b)) continue;
+            // bounding-box gap larger than the link distance: no pair can link
+            if (B.r_lo - A.r_hi > 64 || A.r_lo - B.r_hi > 64 || B.z_lo - A.z_hi > 32 || A.z_lo - B.z_hi > 32)
+                continue;
+            bool linked = false;
+            for (int p = A.begin; p < A.end && !linked; ++p) {
+                const Item& x = it[order[p]];
+                for (int q = B.begin; q < B.end; ++q) {
+                    const Item& y = it[order[q]];
+                    if (std::llabs(x.kr - y.kr) <= 64 && std::llabs(x.kz - y.kz) <= 32) {
+                        linked = true;
+                        break;
+                    }
+                }
+            }
+            if (linked) {
+                const int ra = find_root(par, a), rb = find_root(par, b);
+                par[std::max(ra, rb)] = std::min(ra, rb);
             }
         }
     }
     std::vector<std::vector<int>> groups;
-    std::vector<int> slot(n, -1);
-    for (int i = 0; i < n; ++i) {
-        int r = find_root(par, i);
+    std::vector<int> slot(nc, -1);
+    for (int c = 0; c < nc; ++c) {
+        const int r = find_root(par, c);
         if (slot[r] < 0) {
             slot[r] = (int)groups.size();
             groups.emplace_back();
         }
-        groups[slot[r]].push_back(i);
+        for (int p = cells[c].begin; p < cells[c].end; ++p) groups[slot[r]].push_back(order[p]);
     }
     return groups;
 }
@@ -146,7 +212,7 @@ pss_status sift(const Plan& P, const pss_search_cfg& cfg, const pss_raw_cand* ra
     const double dz = cfg.dz;
     for (int64_t i = 0; i < n; ++i) {
         if (raw[i].dm_idx < 0 || raw[i].dm_idx >= P.ndm()) return fail(PSS_EINVAL, "pss_sift: dm_idx out of range");
-        if (raw[i].numharm < 1 || raw[i].numharm > 64 || (raw[i].numharm & (raw[i].numharm - 1))) return fail(PSS_EINVAL, "pss_sift: numharm must be a power of two in [1, 64]");
+        if (raw[i].numharm < 1 || raw[i].numharm > 32 || (raw[i].numharm & (raw[i].numharm - 1))) return fail(PSS_EINVAL, "pss_sift: numharm must be a power of two in [1, 32]");
     }
     std::vector<int64_t> order;
     std::vector<std::pair<int64_t, int64_t>> bk;
@@ -167,6 +233,8 @@ pss_status sift(const Plan& P, const pss_search_cfg& cfg, const pss_raw_cand* ra
             it.r = (double)c.h / (double)(2 * c.numharm);
             it.z = (double)(c.j - Z) * dz / (double)c.numharm;
             it.sigma = -1.0;  // evaluated on demand by pick_rep
+            it.kr = (int64_t)c.h * (32 / c.numharm);
+            it.kz = (int64_t)(c.j - Z) * (32 / c.numharm);
             items.push_back(it);
         }
         for (auto& g : link_groups(items, dz)) surv[(size_t)b].push_back(items[pick_rep(items, g)]);

@@ -136,8 +136,8 @@ def _random_raw(rng, ndm, per_dm, nfft, nz):
                                  ("power", "<f4"), ("reserved", "<i4")])
 
 
-@pytest.mark.parametrize("zmax,min_hits", [(0, 1), (20, 1), (20, 2)])
-def test_sift_matches_oracle(L, zmax, min_hits):
+@pytest.mark.parametrize("zmax,min_hits,dz", [(0, 1, 2.0), (20, 1, 2.0), (20, 2, 2.0), (6, 1, 0.3)])
+def test_sift_matches_oracle(L, zmax, min_hits, dz):
     rng = np.random.default_rng(zmax + min_hits)
     nchan, nsamp = 64, 1 << 14
     fch0, foff = synth.band(1200.0, 1500.0, nchan)
@@ -145,9 +145,8 @@ def test_sift_matches_oracle(L, zmax, min_hits):
     desc = L.FilDesc(nchan, nsamp, 2e-4, fch0, foff)
     p = L.Plan(desc, stages)
     op = OP.Plan(nchan, nsamp, 2e-4, fch0, foff, stages)
-    dz = 2.0
-    nz = int(2 * zmax / dz) + 1 if zmax else 1
-    Z = int(zmax / dz)
+    nz = int(round(2 * zmax / dz)) + 1 if zmax else 1
+    Z = int(round(zmax / dz))
     raw = _random_raw(rng, 12, 40, 8192, nz)
     cfg = L.search_cfg(zmax=zmax, dz=dz, numharm=8, min_dm_hits=min_hits)
     got = L.pss_sift(p, cfg, raw)
@@ -156,7 +155,7 @@ def test_sift_matches_oracle(L, zmax, min_hits):
         n, h, j = int(c["numharm"]), int(c["h"]), int(c["j"])
         r, z = OS.fundamental(n, h, j, Z, dz)
         by_dm.setdefault(int(c["dm_idx"]), []).append(dict(
-            dm_idx=int(c["dm_idx"]), numharm=n, h=h, j=j, r=r, z=z, power=float(c["power"]),
+            dm_idx=int(c["dm_idx"]), numharm=n, h=h, j=j, r=r, z=z, zq=OS.zq(n, j, Z), power=float(c["power"]),
             sigma=OST.sigma_of(n, float(c["power"]))))
     ref = OS.sift(by_dm, dz, min_hits)
     assert len(got) == len(ref)
