@@ -193,6 +193,33 @@ pss_status pss_dedisperse(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc
                           const void* data, int data_on_device, int64_t dm_begin,
                           int64_t dm_end, int32_t* out, void* stream);
 
+/* Dedispersion for callers that cannot allocate device memory (the paper
+ * has no counterpart to this call).  A real-time ingest thread must not call
+ * cudaMalloc or cudaFree, which can synchronise the whole device and take
+ * unbounded time, and a process whose device memory is already fully reserved
+ * by another allocator has none to give; such callers pass their own input
+ * and output buffers and this call allocates nothing.
+ * Same result and output layout as pss_dedisperse (no context needed), with
+ * these differences:
+ *  - data_dev must be device memory (there is no upload buffer);
+ *  - its scratch (kept-channel list, delays of the requested trials, and a
+ *    channel-major copy of the file: about nchan_kept * (nsamp + 1280) bytes
+ *    plus 4 * nchan_kept * (dm_end - dm_begin + 1)) lives in one static
+ *    device array of PSS_NOALLOC_SCRATCH_BYTES; larger requests return
+ *    PSS_EINVAL with the size needed.  Every GPU that loads the library
+ *    holds that array until the process exits;
+ *  - the first call on a device looks up the array's device address (set-up
+ *    per device, under the current device); make that first call before any
+ *    stream capture;
+ *  - every call shares the one array: calls that overlap on the GPU (other
+ *    streams, other host threads) race and corrupt each other's results.
+ *    Each call overwrites all of the scratch it reads, so nothing carries
+ *    over from the previous call;
+ *  - it synchronises `stream` before returning. */
+#define PSS_NOALLOC_SCRATCH_BYTES (32u << 20)
+pss_status pss_dedisperse_noalloc(const pss_plan* plan, const pss_fil_desc* fil, const void* data_dev,
+                                  int64_t dm_begin, int64_t dm_end, int32_t* out, void* stream);
+
 /* ---- spectra (Sect. 2 step 3, realfft) ---------------------------------- */
 
 /* Whitened half spectrum of DM trials [dm_begin, dm_end): the dedispersed

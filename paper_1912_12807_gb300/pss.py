@@ -55,7 +55,7 @@ CAND_DTYPE = np.dtype([("dm_idx", "<i4"), ("numharm", "<i4"), ("dm", "<f8"), ("r
 EXPORTS = ["pss_ctx_create", "pss_ctx_destroy", "pss_last_error", "pss_version", "pss_dd_plan", "pss_plan_info",
            "pss_plan_trial_info", "pss_plan_free", "pss_dedisperse", "pss_spectrum", "pss_power_plane",
            "pss_search_raw", "pss_sift", "pss_search_dm_batch", "pss_response", "pss_sigma_of_power",
-           "pss_power_threshold", "pss_ctx_profile", "pss_ctx_profile_read"]
+           "pss_power_threshold", "pss_ctx_profile", "pss_ctx_profile_read", "pss_dedisperse_noalloc"]
 PROFILE_STAGES = ["unpack", "dedisperse", "fft", "whiten", "plane", "harmsum"]
 
 _lib = None
@@ -89,6 +89,7 @@ def lib():
         "pss_search_dm_batch": (st, [vp, vp, P(pss_fil_desc), vp, C.c_int, P(pss_search_cfg), i64, i64, vp, i64,
                                      P(i64), vp]),
         "pss_response": (st, [vp, vp, vp, i64, vp]),
+        "pss_dedisperse_noalloc": (st, [vp, P(pss_fil_desc), vp, i64, i64, vp, vp]),
         "pss_ctx_profile": (st, [vp, C.c_int]),
         "pss_ctx_profile_read": (st, [vp, vp, vp]),
         "pss_sigma_of_power": (C.c_double, [i32, C.c_double]),
@@ -257,6 +258,21 @@ def pss_dedisperse(ctx: Context, plan: Plan, data, dm_begin: int, dm_end: int, o
     p, dev, keep = _data_arg(data)
     _check(lib().pss_dedisperse(ctx.h, plan.h, C.byref(plan.desc.c), p, dev, dm_begin, dm_end,
                                 C.c_void_p(out.data_ptr()), _stream(stream)))
+    return out[:total]
+
+
+def pss_dedisperse_noalloc(plan: Plan, data_dev, dm_begin: int, dm_end: int, out=None, stream=None):
+    """pss_dedisperse without device allocation inside the call: data_dev is
+    a CUDA tensor, `out` (allocated here if not given, before the call) an
+    int32 CUDA tensor of at least sum N_v elements."""
+    import torch
+    total = int(sum(_rows(plan, dm_begin, dm_end, "nv")))
+    if out is None:
+        out = torch.empty(max(total, 1), dtype=torch.int32, device=data_dev.device)
+    if not (isinstance(data_dev, torch.Tensor) and data_dev.is_cuda):
+        raise ValueError("data_dev must be a CUDA tensor")
+    _check(lib().pss_dedisperse_noalloc(plan.h, C.byref(plan.desc.c), C.c_void_p(data_dev.data_ptr()), dm_begin,
+                                        dm_end, C.c_void_p(out.data_ptr()), _stream(stream)))
     return out[:total]
 
 
