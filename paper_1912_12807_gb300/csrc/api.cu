@@ -144,6 +144,10 @@ pss_status stage_input(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* f
     PSS_CUDA(cudaMemcpyAsync(ctx->delays_dev.p, host.data(), host.size() * sizeof(int32_t),
                              cudaMemcpyHostToDevice, s));
     PSS_TRY(ctx->xcm.ensure((size_t)ck * pitch + 64));
+    if (!ctx->errflag.p) {
+        PSS_TRY(ctx->errflag.ensure(sizeof(int)));
+        PSS_CUDA(cudaMemsetAsync(ctx->errflag.p, 0, sizeof(int), s));
+    }
     PrepArgs pa;
     pa.src = src;
     pa.nchan = fil->nchan;
@@ -322,6 +326,7 @@ pss_status run_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil,
             da.out_stride = nfft;
             da.sums = (unsigned long long*)ctx->sums.p;
             da.spread = delay_spread(hd.data() + (size_t)(b0 - dm_begin) * ck, nb, ck);
+            da.err = (int*)ctx->errflag.p;
             PSS_CUDA(cudaMemsetAsync(ctx->sums.p, 0, (size_t)nb * 8, s));
             {
                 ProfScope ps(ctx, 1, s);
@@ -388,6 +393,20 @@ pss_status run_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil,
     return PSS_OK;
 }
 
+// A kernel's bounded wait expired since the flag was last cleared: report it
+// (and clear it).
+pss_status check_errflag(pss_ctx* ctx, cudaStream_t s) {
+    if (!ctx->errflag.p) return PSS_OK;
+    int flag = 0;
+    PSS_CUDA(cudaMemcpyAsync(&flag, ctx->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PSS_CUDA(cudaStreamSynchronize(s));
+    if (flag) {
+        PSS_CUDA(cudaMemsetAsync(ctx->errflag.p, 0, sizeof(int), s));
+        return fail(PSS_ETIMEOUT, "a kernel's bounded wait on its staging barrier expired; results discarded");
+    }
+    return PSS_OK;
+}
+
 pss_status search_raw_vec(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const void* data, int on_dev,
                           const pss_search_cfg* cfg, int64_t dm_begin, int64_t dm_end, std::vector<pss_raw_cand>* out,
                           cudaStream_t s, bool sorted) {
@@ -403,6 +422,7 @@ pss_status search_raw_vec(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc
             PSS_CUDA(cudaMemcpyAsync(&cnt, ctx->counter.p, sizeof(cnt), cudaMemcpyDeviceToHost, s));
         PSS_CUDA(cudaStreamSynchronize(s));
         tm.mark("gpu");
+        PSS_TRY(check_errflag(ctx, s));
         if ((int64_t)cnt <= cap) {
             out->resize(cnt);
             if (cnt)
@@ -452,7 +472,7 @@ void pss_ctx_destroy(pss_ctx* c) {
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     DevBuf* bufs[] = {&c->fil_dev, &c->xcm, &c->delays_dev, &c->series, &c->sums, &c->fftA, &c->fftB,
-                      &c->spec, &c->plane, &c->cands, &c->counter, &c->taps, &c->tapinfo, &c->int_out};
+                      &c->spec, &c->plane, &c->cands, &c->counter, &c->taps, &c->tapinfo, &c->errflag};
     for (DevBuf* b : bufs) b->release();
     for (auto& r : c->prof_recs) {
         cudaEventDestroy(r.a);
@@ -564,6 +584,7 @@ pss_status pss_dedisperse(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc
             da.out_stride = st.nv;
             da.sums = nullptr;
             da.spread = delay_spread(hd.data() + (size_t)(b0 - dm_begin) * ck, nb, ck);
+            da.err = (int*)ctx->errflag.p;
             {
                 ProfScope ps(ctx, 1, s);
                 PSS_CUDA(launch_dedisp(da, ctx->num_sms, s));

@@ -106,14 +106,35 @@ pss_status build_plan(const pss_fil_desc* fil, const pss_dd_stage* st, int nst, 
 // Noise powers are Exp(1); a sum of n of them is Gamma(n, 1) with tail
 // Q(n, S) = exp(-S) sum_{j<n} S^j / j!.  sigma = -Phi^-1(Q).
 
+namespace {
+// lgamma(j + 1) for j < 64
+struct LogFactorials {
+    double v[64];
+    LogFactorials() {
+        for (int j = 0; j < 64; ++j) v[j] = lgamma((double)j + 1.0);
+    }
+};
+const LogFactorials kLogFact;
+}  // namespace
+
 double log_q(int n, double S) {
     if (S <= 0) return 0.0;
     if (n > 64) n = 64;
     const double lS = log(S);
+    if (S >= n) {
+        // The terms grow with j up to j = n - 1; relative to the last one,
+        // term_j / term_{n-1} = prod_{i=j+1}^{n-1} i / S <= 1.
+        double ratio = 1.0, acc = 1.0;
+        for (int j = n - 2; j >= 0; --j) {
+            ratio *= (double)(j + 1) / S;
+            acc += ratio;
+        }
+        return (n - 1) * lS - S - kLogFact.v[n - 1] + log(acc);
+    }
     double mx = -1e300;
     double t[64];
     for (int j = 0; j < n; ++j) {
-        t[j] = j * lS - S - lgamma((double)j + 1.0);
+        t[j] = j * lS - S - kLogFact.v[j];
         mx = std::max(mx, t[j]);
     }
     double acc = 0;

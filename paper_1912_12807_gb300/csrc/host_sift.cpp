@@ -25,9 +25,20 @@ namespace {
 struct Item {
     int32_t dm_idx, n, h, j;
     float power;
-    double r, z, sigma;
+    double r, z;
+    double logp;   // log Q(n, S); NAN until evaluated
+    double sigma;  // -Phi^-1(Q); < 0 until evaluated
     int64_t kr, kz;  // exact link coordinates: 64 r and 32 z / dz
 };
+
+double item_logp(Item& x) {
+    if (x.logp != x.logp) x.logp = log_q(x.n, (double)x.power);
+    return x.logp;
+}
+double item_sigma(Item& x) {
+    if (x.sigma < 0) x.sigma = sigma_of_power(x.n, (double)x.power);
+    return x.sigma;
+}
 
 int find_root(std::vector<int>& par, int i) {
     while (par[i] != i) {
@@ -59,8 +70,33 @@ struct Cell {
     int64_t r_lo, r_hi, z_lo, z_hi;
 };
 
-std::vector<std::vector<int>> link_groups(const std::vector<Item>& it, double /*dz*/) {
+// Flattened groups: members of group g are order[start[g] .. start[g+1]).
+struct Groups {
+    std::vector<int> start, members;
+    int count() const { return (int)start.size() - 1; }
+};
+
+Groups link_groups(const std::vector<Item>& it, double /*dz*/) {
     const int n = (int)it.size();
+    bool one_row = true;
+    for (int i = 1; i < n && one_row; ++i) one_row = it[i].kz == it[0].kz;
+    if (one_row) {
+        // all z equal (zmax = 0): sort by r; consecutive items closer than
+        // one bin link, so groups are the runs of the sorted order
+        Groups G;
+        std::vector<uint64_t> key(n);
+        for (int i = 0; i < n; ++i) key[i] = ((uint64_t)it[i].kr << 32) | (uint32_t)i;
+        std::sort(key.begin(), key.end());
+        G.members.resize(n);
+        G.start.push_back(0);
+        for (int p = 0; p < n; ++p) {
+            G.members[p] = (int)(key[p] & 0xFFFFFFFFu);
+            if (p > 0 && (int64_t)(key[p] >> 32) - (int64_t)(key[p - 1] >> 32) > 64) G.start.push_back(p);
+        }
+        G.start.push_back(n);
+        if (n == 0) G.start.resize(1);
+        return G;
+    }
     auto fdiv = [](int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); };
     std::vector<int> order(n);
     std::iota(order.begin(), order.end(), 0);
@@ -130,27 +166,40 @@ std::vector<std::vector<int>> link_groups(const std::vector<Item>& it, double /*
             }
         }
     }
-    std::vector<std::vector<int>> groups;
-    std::vector<int> slot(nc, -1);
+    // roots in order of first appearance; counting sort of cells by root
+    std::vector<int> slot(nc, -1), cnt;
+    int ng = 0;
     for (int c = 0; c < nc; ++c) {
         const int r = find_root(par, c);
         if (slot[r] < 0) {
-            slot[r] = (int)groups.size();
-            groups.emplace_back();
+            slot[r] = ng++;
+            cnt.push_back(0);
         }
-        for (int p = cells[c].begin; p < cells[c].end; ++p) groups[slot[r]].push_back(order[p]);
+        cnt[slot[r]] += cells[c].end - cells[c].begin;
     }
-    return groups;
+    Groups G;
+    G.start.assign(ng + 1, 0);
+    for (int g = 0; g < ng; ++g) G.start[g + 1] = G.start[g] + cnt[g];
+    G.members.resize(n);
+    std::vector<int> fill(G.start.begin(), G.start.end() - 1);
+    for (int c = 0; c < nc; ++c) {
+        const int g = slot[find_root(par, c)];
+        for (int p = cells[c].begin; p < cells[c].end; ++p) G.members[fill[g]++] = order[p];
+    }
+    return G;
 }
 
 // Representative of a linked group: the highest sigma (ties: lower n, r, z,
 // DM index).  sigma is strictly increasing in S for a fixed n, so only the
-// largest-S member of each harmonic stage can win; sigma is evaluated for
-// those alone (items with sigma < 0 have not been evaluated yet).
-int pick_rep(std::vector<Item>& items, const std::vector<int>& g) {
+// largest-S member of each harmonic stage can win.  sigma is a decreasing
+// function of log Q, so those few members are ranked by log Q; sigma itself
+// is evaluated only where two log Q values are too close (1e-12 relative) for
+// their order to decide the order of the sigmas, and for the winner.
+int pick_rep(std::vector<Item>& items, const int* mem, int nm) {
     int best_of_n[8];
     for (int i = 0; i < 8; ++i) best_of_n[i] = -1;
-    for (int k : g) {
+    for (int q = 0; q < nm; ++q) {
+        const int k = mem[q];
         const Item& a = items[k];
         int li = 0;
         while ((1 << li) < a.n && li < 7) ++li;
@@ -167,9 +216,20 @@ int pick_rep(std::vector<Item>& items, const std::vector<int>& g) {
     for (int i = 0; i < 8; ++i) {
         const int k = best_of_n[i];
         if (k < 0) continue;
-        if (items[k].sigma < 0) items[k].sigma = sigma_of_power(items[k].n, (double)items[k].power);
-        if (best < 0 || rep_less(items[k], items[best])) best = k;
+        if (best < 0) {
+            best = k;
+            continue;
+        }
+        const double lk = item_logp(items[k]), lb = item_logp(items[best]);
+        if (fabs(lk - lb) > 1e-12 * std::max(fabs(lk), fabs(lb))) {
+            if (lk < lb) best = k;
+        } else {
+            item_sigma(items[k]);
+            item_sigma(items[best]);
+            if (rep_less(items[k], items[best])) best = k;
+        }
     }
+    item_sigma(items[best]);
     return best;
 }
 
@@ -233,20 +293,27 @@ pss_status sift(const Plan& P, const pss_search_cfg& cfg, const pss_raw_cand* ra
             it.r = (double)c.h / (double)(2 * c.numharm);
             it.z = (double)(c.j - Z) * dz / (double)c.numharm;
             it.sigma = -1.0;  // evaluated on demand by pick_rep
+            it.logp = NAN;
             it.kr = (int64_t)c.h * (32 / c.numharm);
             it.kz = (int64_t)(c.j - Z) * (32 / c.numharm);
             items.push_back(it);
         }
-        for (auto& g : link_groups(items, dz)) surv[(size_t)b].push_back(items[pick_rep(items, g)]);
+        const Groups G = link_groups(items, dz);
+        for (int g = 0; g < G.count(); ++g)
+            surv[(size_t)b].push_back(
+                items[pick_rep(items, G.members.data() + G.start[g], G.start[g + 1] - G.start[g])]);
     });
     std::vector<Item> survivors;
     for (auto& v : surv) survivors.insert(survivors.end(), v.begin(), v.end());
 
     // across DM trials
-    for (auto& g : link_groups(survivors, dz)) {
-        const int best = pick_rep(survivors, g);
+    const Groups G = link_groups(survivors, dz);
+    for (int g = 0; g < G.count(); ++g) {
+        const int* mem = G.members.data() + G.start[g];
+        const int nm = G.start[g + 1] - G.start[g];
+        const int best = pick_rep(survivors, mem, nm);
         std::vector<int32_t> dms;
-        for (int k : g) dms.push_back(survivors[k].dm_idx);
+        for (int q = 0; q < nm; ++q) dms.push_back(survivors[mem[q]].dm_idx);
         std::sort(dms.begin(), dms.end());
         int hits = (int)(std::unique(dms.begin(), dms.end()) - dms.begin());
         if (hits < cfg.min_dm_hits) continue;

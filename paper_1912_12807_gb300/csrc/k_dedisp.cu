@@ -2,75 +2,194 @@
 // exact in integers:  s[t] = sum_c x[c][t + d_c],  s_ds[j] = sum_{k<ds} s[j*ds+k].
 //
 // Work decomposition.  A CTA owns G = 8 consecutive DM trials (one warp
-// each) and a tile of TN = 1024 native-rate output samples.  Channels are
-// processed in chunks of CC: for every channel of the chunk the bytes
-// [t0 + min_d, t0 + max_d + TN) that the 8 trials need are staged once in
-// shared memory and reused by all 8 warps.  Each row is stored as four
-// copies shifted by 0..3 bytes, so any delay is served by aligned 32-bit
-// shared-memory reads (consecutive lanes read consecutive words: no bank
-// conflicts).
+// each) and a tile of TN = 1024 native-rate output samples, and walks the
+// channels in chunks of CC.  For each channel of a chunk the bytes
+// [t0 + min_d, t0 + max_d + TN) that the 8 trials need are fetched once from
+// global memory by the bulk-copy (TMA) engine into a shared-memory staging
+// area, while the warps are still summing the previous chunk; an mbarrier
+// with a byte count signals arrival.  The staged row is then expanded into
+// four copies shifted by 0..3 bytes, so every delay is served by aligned
+// 32-bit shared-memory reads (consecutive lanes read consecutive words: no
+// bank conflicts) and the 8 warps reuse the staged bytes.
 //
 // Arithmetic is SWAR: a 32-bit word holds 4 consecutive 8-bit samples of one
-// channel; (w & 0x00FF00FF) and (w >> 8) & 0x00FF00FF split it into two
-// pairs of 16-bit lanes that are added with ordinary 32-bit adds.  A 16-bit
-// lane holds at most 257 * 255 < 65536, so the lanes are widened into 32-bit
-// accumulators every 256 channels.  The result is the exact integer sum.
+// channel; (w & 0x00FF00FF) and byte-permute(w) split it into two pairs of
+// 16-bit lanes that are added with 32-bit adds.  The adds are issued as
+// integer multiply-adds (x * one + acc, `one` a run-time 1) so that they run
+// on the FMA pipe while the masks use the integer ALU pipe.  A 16-bit lane
+// holds at most 257 * 255 < 65536, so with more than 256 channels the lanes
+// are widened into 32-bit accumulators every 256 channels.  The result is the
+// exact integer sum.
+//
+// Every wait on the mbarrier is bounded; on expiry the CTA sets the error
+// flag, waits (bounded) for its copies in flight, and exits without writing.
 #include "pss_internal.h"
 
 namespace pss {
 
 namespace {
 
-constexpr int G = 8;            // DM trials per CTA (one per warp)
-constexpr int KW = 8;           // 32-bit words per lane
-constexpr int TN = 32 * 4 * KW; // native samples per tile (1024)
+constexpr int G = 8;             // DM trials per CTA (one per warp)
+constexpr int KW = 8;            // 32-bit words per lane
+constexpr int TN = 32 * 4 * KW;  // native samples per tile (1024)
+constexpr int NT = 32 * G;
+constexpr int WAIT_LIMIT = 1 << 22;
 
-__device__ __forceinline__ uint32_t hi_pairs(uint32_t w) {
-    // bytes 1 and 3 of w into the low bytes of two 16-bit lanes
-    return __byte_perm(w, 0u, 0x4341);
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-template <bool INT_OUT>
-__global__ void __launch_bounds__(256) k_dedisp(DedispArgs a, int RW, int CC) {
-    extern __shared__ __align__(16) uint32_t smem[];
-    // smem layout: [CC][4 copies][RW words] staged rows, then per-channel a16
-    int64_t* row_start = reinterpret_cast<int64_t*>(smem + (size_t)CC * 4 * RW);
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (int i = 0; i < WAIT_LIMIT; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t madd(uint32_t x, uint32_t one, uint32_t acc) {
+    uint32_t r;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(x), "r"(one), "r"(acc));
+    return r;
+}
+
+struct Smem {
+    uint32_t* copies;  // [CC][4][RW]
+    uint8_t* raw;      // [CC][RAWB]
+    int64_t* rs;       // [2][CC] 16-byte-aligned first staged byte of each row
+    int32_t* offs;     // [2][G][CC] byte offset of t0 + d into the staged row
+    uint64_t* bar;
+};
+
+// Shared-memory layout (byte offsets); the same function sizes the launch.
+struct Layout {
+    size_t copies, raw, rs, offs, bar, total;
+};
+__host__ __device__ inline Layout layout_of(int RW, int CC) {
+    Layout L;
+    const size_t cp = (size_t)CC * 16 * RW, ep = (size_t)G * TN * 4;  // copies / epilogue scratch
+    L.copies = 0;
+    L.raw = cp > ep ? cp : ep;
+    L.rs = L.raw + (size_t)CC * (4 * RW + 16);
+    L.offs = L.rs + 2 * (size_t)CC * 8;
+    L.bar = (L.offs + 2 * (size_t)G * CC * 4 + 7) & ~(size_t)7;
+    L.total = L.bar + 8;
+    return L;
+}
+
+template <bool INT_OUT, bool WIDE>
+__global__ void __launch_bounds__(NT) k_dedisp(DedispArgs a, int RW, int CC, uint32_t one) {
+    extern __shared__ __align__(128) uint8_t smraw[];
+    const int RAWB = 4 * RW + 16;
+    const Layout Lo = layout_of(RW, CC);
+    Smem S;
+    S.copies = reinterpret_cast<uint32_t*>(smraw + Lo.copies);
+    S.raw = smraw + Lo.raw;
+    S.rs = reinterpret_cast<int64_t*>(smraw + Lo.rs);
+    S.offs = reinterpret_cast<int32_t*>(smraw + Lo.offs);
+    S.bar = reinterpret_cast<uint64_t*>(smraw + Lo.bar);
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int64_t t0 = (int64_t)blockIdx.x * TN;
     const int g0 = blockIdx.y * G;
     const int gn = min(G, a.nb - g0);
-    const int my = g0 + warp;  // this warp's trial in the batch
+    const int my = g0 + warp;
     const bool active = warp < gn;
-    const int32_t* drow = a.delays + (int64_t)(active ? my : g0) * a.ck;
+    const int nchunks = (a.ck + CC - 1) / CC;
 
-    uint32_t lo[KW], hi[KW];
-    uint32_t wide[4 * KW];
-#pragma unroll
-    for (int k = 0; k < KW; ++k) lo[k] = hi[k] = 0u;
-#pragma unroll
-    for (int k = 0; k < 4 * KW; ++k) wide[k] = 0u;
-    int since_flush = 0;
+    if (threadIdx.x == 0) {
+        mbar_init(S.bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
 
-    const int qn = RW / 4;  // 16-byte chunks per copy row
-    for (int cb = 0; cb < a.ck; cb += CC) {
+    // per-chunk bookkeeping: row starts and each warp's offsets
+    auto prepare = [&](int c, int slot) {
+        const int cb = c * CC;
         const int cn = min(CC, a.ck - cb);
-        // per-channel first staged byte (16-byte aligned)
-        for (int i = threadIdx.x; i < cn; i += blockDim.x) {
+        for (int i = threadIdx.x; i < cn; i += NT) {
             const int32_t* dcol = a.delays + (int64_t)g0 * a.ck + cb + i;
             int32_t dmin = dcol[0];
             for (int g = 1; g < gn; ++g) dmin = min(dmin, dcol[(int64_t)g * a.ck]);
-            row_start[i] = (t0 + dmin) & ~int64_t(15);
+            S.rs[slot * CC + i] = (t0 + dmin) & ~int64_t(15);
         }
         __syncthreads();
-        // stage: 4 byte-shifted copies of each row
-        for (int it = threadIdx.x; it < cn * qn; it += blockDim.x) {
+        for (int x = threadIdx.x; x < gn * cn; x += NT) {
+            const int g = x / cn, i = x - g * cn;
+            const int32_t d = a.delays[(int64_t)(g0 + g) * a.ck + cb + i];
+            S.offs[(slot * G + g) * CC + i] = (int32_t)(t0 + d - S.rs[slot * CC + i]);
+        }
+    };
+    auto issue = [&](int c, int slot) {
+        // warp 0: one bulk copy per row of the chunk
+        if (warp == 0) {
+            const int cb = c * CC;
+            const int cn = min(CC, a.ck - cb);
+            if (lane == 0) mbar_expect_tx(S.bar, (uint32_t)(cn * RAWB));
+            __syncwarp();
+            // order this CTA's earlier generic-proxy reads of the staging area
+            // before the bulk copies overwrite it
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            for (int i = lane; i < cn; i += 32) {
+                const uint8_t* src = a.xcm + (int64_t)(cb + i) * a.pitch + S.rs[slot * CC + i];
+                bulk_g2s(S.raw + (size_t)i * RAWB, src, (uint32_t)RAWB, S.bar);
+            }
+        }
+    };
+
+    uint32_t lo[KW], hi[KW];
+    uint32_t wide[WIDE ? 4 * KW : 1];
+#pragma unroll
+    for (int k = 0; k < KW; ++k) lo[k] = hi[k] = 0u;
+#pragma unroll
+    for (int k = 0; k < (WIDE ? 4 * KW : 1); ++k) wide[k] = 0u;
+    int since_flush = 0;
+
+    prepare(0, 0);
+    __syncthreads();
+    issue(0, 0);
+    const int qn = RW / 4;
+    int failed_at = -1;
+    for (int c = 0; c < nchunks; ++c) {
+        const int slot = c & 1;
+        const int cb = c * CC;
+        const int cn = min(CC, a.ck - cb);
+        const bool ok = mbar_wait(S.bar, (uint32_t)(c & 1));
+        if (__syncthreads_or(!ok)) {
+            failed_at = c;
+            break;
+        }
+        if (c + 1 < nchunks) prepare(c + 1, slot ^ 1);
+        // expand the staged rows into 4 byte-shifted copies
+        for (int it = threadIdx.x; it < cn * qn; it += NT) {
             const int i = it / qn, q = it - i * qn;
-            const uint8_t* src = a.xcm + (int64_t)(cb + i) * a.pitch + row_start[i] + 16 * q;
-            const uint4 v = __ldg(reinterpret_cast<const uint4*>(src));
-            const uint32_t w4 = __ldg(reinterpret_cast<const uint32_t*>(src + 16));
-            uint32_t* base = smem + (size_t)i * 4 * RW + 4 * q;
+            const uint8_t* src = S.raw + (size_t)i * RAWB + 16 * q;
+            const uint4 v = *reinterpret_cast<const uint4*>(src);
+            const uint32_t w4 = *reinterpret_cast<const uint32_t*>(src + 16);
+            uint32_t* base = S.copies + (size_t)i * 4 * RW + 4 * q;
             const uint32_t W[5] = {v.x, v.y, v.z, v.w, w4};
 #pragma unroll
             for (int s = 0; s < 4; ++s) {
@@ -83,43 +202,61 @@ __global__ void __launch_bounds__(256) k_dedisp(DedispArgs a, int RW, int CC) {
             }
         }
         __syncthreads();
-        if (since_flush + cn > 256) {
+        if (c + 1 < nchunks) issue(c + 1, slot ^ 1);
+        if constexpr (WIDE) {
+            if (since_flush + cn > 256) {
 #pragma unroll
-            for (int k = 0; k < KW; ++k) {
-                wide[4 * k + 0] += lo[k] & 0xFFFFu;
-                wide[4 * k + 2] += lo[k] >> 16;
-                wide[4 * k + 1] += hi[k] & 0xFFFFu;
-                wide[4 * k + 3] += hi[k] >> 16;
-                lo[k] = hi[k] = 0u;
+                for (int k = 0; k < KW; ++k) {
+                    wide[4 * k + 0] += lo[k] & 0xFFFFu;
+                    wide[4 * k + 2] += lo[k] >> 16;
+                    wide[4 * k + 1] += hi[k] & 0xFFFFu;
+                    wide[4 * k + 3] += hi[k] >> 16;
+                    lo[k] = hi[k] = 0u;
+                }
+                since_flush = 0;
             }
-            since_flush = 0;
         }
         if (active) {
+            const int32_t* offs = S.offs + (slot * G + warp) * CC;
+#pragma unroll 2
             for (int i = 0; i < cn; ++i) {
-                const int64_t o = t0 + drow[cb + i] - row_start[i];
-                const uint32_t* p = smem + ((size_t)i * 4 + (o & 3)) * RW + (o >> 2) + lane;
+                const int o = offs[i];
+                const uint32_t* p = S.copies + ((size_t)i * 4 + (o & 3)) * RW + (o >> 2) + lane;
 #pragma unroll
                 for (int k = 0; k < KW; ++k) {
                     const uint32_t w = p[32 * k];
-                    lo[k] += w & 0x00FF00FFu;
-                    hi[k] += hi_pairs(w);
+                    lo[k] = madd(w & 0x00FF00FFu, one, lo[k]);
+                    hi[k] = madd(__byte_perm(w, 0u, 0x4341), one, hi[k]);
                 }
             }
         }
         since_flush += cn;
         __syncthreads();
     }
+    if (failed_at >= 0) {
+        if (threadIdx.x == 0 && a.err) atomicExch(a.err, 1);
+        // let the copies still in flight land before the CTA's shared memory is released
+        mbar_wait(S.bar, (uint32_t)(failed_at & 1));
+        return;
+    }
+    uint32_t tot[4 * KW];
 #pragma unroll
     for (int k = 0; k < KW; ++k) {
-        wide[4 * k + 0] += lo[k] & 0xFFFFu;
-        wide[4 * k + 2] += lo[k] >> 16;
-        wide[4 * k + 1] += hi[k] & 0xFFFFu;
-        wide[4 * k + 3] += hi[k] >> 16;
+        tot[4 * k + 0] = lo[k] & 0xFFFFu;
+        tot[4 * k + 2] = lo[k] >> 16;
+        tot[4 * k + 1] = hi[k] & 0xFFFFu;
+        tot[4 * k + 3] = hi[k] >> 16;
+        if constexpr (WIDE) {
+            tot[4 * k + 0] += wide[4 * k + 0];
+            tot[4 * k + 2] += wide[4 * k + 2];
+            tot[4 * k + 1] += wide[4 * k + 1];
+            tot[4 * k + 3] += wide[4 * k + 3];
+        }
     }
     if (!active) return;
 
     // Epilogue.  Lane owns native samples t0 + 4*(lane + 32k) + {0..3}.
-    const int64_t j0 = t0 / a.ds;  // first output of this tile
+    const int64_t j0 = t0 / a.ds;
     unsigned long long part = 0ull;
     if (a.ds == 1) {
         float* of = INT_OUT ? nullptr : a.out_f + (int64_t)my * a.out_stride;
@@ -127,23 +264,29 @@ __global__ void __launch_bounds__(256) k_dedisp(DedispArgs a, int RW, int CC) {
 #pragma unroll
         for (int k = 0; k < KW; ++k) {
             const int64_t j = j0 + 4 * (lane + 32 * k);
+            if (!INT_OUT && j + 3 < a.nv) {
+                part += (unsigned long long)tot[4 * k] + tot[4 * k + 1] + tot[4 * k + 2] + tot[4 * k + 3];
+                *reinterpret_cast<float4*>(of + j) =
+                    make_float4((float)tot[4 * k], (float)tot[4 * k + 1], (float)tot[4 * k + 2], (float)tot[4 * k + 3]);
+                continue;
+            }
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 if (j + e < a.nv) {
-                    part += wide[4 * k + e];
-                    if (INT_OUT) oi[j + e] = (int32_t)wide[4 * k + e];
-                    else of[j + e] = (float)wide[4 * k + e];
+                    part += tot[4 * k + e];
+                    if (INT_OUT) oi[j + e] = (int32_t)tot[4 * k + e];
+                    else of[j + e] = (float)tot[4 * k + e];
                 }
             }
         }
     } else {
-        // boxcar by ds through shared memory (the staging area is free now;
-        // each warp uses its own TN-word slice, so a warp barrier suffices)
-        uint32_t* nat = smem + (size_t)warp * TN;
+        // boxcar by ds through shared memory: every warp is past the last
+        // __syncthreads, so the copy area is free; each warp uses its own slice
+        uint32_t* nat = S.copies + (size_t)warp * TN;
 #pragma unroll
         for (int k = 0; k < KW; ++k)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) nat[4 * (lane + 32 * k) + e] = wide[4 * k + e];
+            for (int e = 0; e < 4; ++e) nat[4 * (lane + 32 * k) + e] = tot[4 * k + e];
         __syncwarp();
         const int nout = TN / a.ds;
         for (int oo = lane; oo < nout; oo += 32) {
@@ -163,33 +306,35 @@ __global__ void __launch_bounds__(256) k_dedisp(DedispArgs a, int RW, int CC) {
     }
 }
 
+template <bool I, bool W>
+cudaError_t launch_t(const DedispArgs& a, dim3 grid, size_t shm, int RW, int CC, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(k_dedisp<I, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    if (e != cudaSuccess) return e;
+    k_dedisp<I, W><<<grid, NT, shm, s>>>(a, RW, CC, 1u);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 int dedisp_tile_samples() { return TN; }
 
 cudaError_t launch_dedisp(const DedispArgs& a, int num_sms, cudaStream_t s) {
     (void)num_sms;
-    // staged row: 256 words read per lane sweep plus the delay spread and
+    // staged row: the 256 words a lane sweep reads plus the delay spread and
     // the 16-byte alignment slack, in whole 16-byte chunks
     int RW = 32 * KW + (15 + a.spread) / 4 + 1;
     RW = (RW + 3) & ~3;
-    const size_t per_chan = (size_t)4 * RW * 4;
-    int CC = (int)((96 * 1024) / per_chan);
+    const size_t per_chan = (size_t)16 * RW + (4 * RW + 16);
+    int CC = (int)((64 * 1024) / per_chan);
     if (CC > 32) CC = 32;
     if (CC < 1) CC = 1;
-    size_t shm = (size_t)CC * per_chan + (size_t)CC * sizeof(int64_t);
-    if (shm < (size_t)G * TN * 4 + CC * sizeof(int64_t)) shm = (size_t)G * TN * 4 + CC * sizeof(int64_t);
-    if (shm > 200 * 1024) return cudaErrorInvalidValue;
+    const size_t shm = layout_of(RW, CC).total;
+    if (shm > 220 * 1024) return cudaErrorInvalidValue;
     const int64_t L = a.nv * a.ds;
     dim3 grid((unsigned)((L + TN - 1) / TN), (unsigned)((a.nb + G - 1) / G));
-    if (a.out_i) {
-        cudaFuncSetAttribute(k_dedisp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-        k_dedisp<true><<<grid, 256, shm, s>>>(a, RW, CC);
-    } else {
-        cudaFuncSetAttribute(k_dedisp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-        k_dedisp<false><<<grid, 256, shm, s>>>(a, RW, CC);
-    }
-    return cudaGetLastError();
+    const bool wide = a.ck > 256;
+    if (a.out_i) return wide ? launch_t<true, true>(a, grid, shm, RW, CC, s) : launch_t<true, false>(a, grid, shm, RW, CC, s);
+    return wide ? launch_t<false, true>(a, grid, shm, RW, CC, s) : launch_t<false, false>(a, grid, shm, RW, CC, s);
 }
 
 }  // namespace pss

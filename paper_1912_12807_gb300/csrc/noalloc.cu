@@ -136,6 +136,7 @@ extern "C" pss_status pss_dedisperse_noalloc(const pss_plan* plan, const pss_fil
             da.out_stride = st.nv;
             da.sums = nullptr;
             da.spread = spread;
+            da.err = nullptr;
             PSS_CUDA(launch_dedisp(da, 0, s));
             off += (int64_t)nb * st.nv;
         }

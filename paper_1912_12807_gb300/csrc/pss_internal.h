@@ -125,7 +125,7 @@ struct Ctx {
     DevBuf counter;      // unsigned long long
     DevBuf taps;         // float2 templates
     DevBuf tapinfo;      // per row tap info
-    DevBuf int_out;      // int32 scratch
+    DevBuf errflag;      // int: a kernel's bounded wait expired
     void* host_pinned = nullptr;
     size_t host_pinned_bytes = 0;
     // (zmax, extra, dz) of the templates currently in `taps`
@@ -176,6 +176,7 @@ struct DedispArgs {
     int64_t out_stride;
     unsigned long long* sums;  // [nb] or null
     int32_t spread;         // max over groups/channels of (dmax - dmin)
+    int* err;               // set to 1 if a bounded wait expires (nullable)
 };
 int dedisp_tile_samples();
 cudaError_t launch_dedisp(const DedispArgs& a, int num_sms, cudaStream_t s);
