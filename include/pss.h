@@ -205,9 +205,10 @@ pss_status pss_dedisperse(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc
  *  - its scratch (kept-channel list, delays of the requested trials, and a
  *    channel-major copy of the file: about nchan_kept * (nsamp + 1280) bytes
  *    plus 4 * nchan_kept * (dm_end - dm_begin + 1)) lives in one static
- *    device array of PSS_NOALLOC_SCRATCH_BYTES; larger requests return
- *    PSS_EINVAL with the size needed.  Every GPU that loads the library
- *    holds that array until the process exits;
+ *    device array of PSS_NOALLOC_SCRATCH_BYTES (next to a static 4-byte
+ *    error flag); larger requests return PSS_EINVAL with the size needed.
+ *    Every GPU that loads the library holds that array until the process
+ *    exits;
  *  - the first call on a device looks up the array's device address (set-up
  *    per device, under the current device); make that first call before any
  *    stream capture;

@@ -169,11 +169,13 @@ pss_status stage_input(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* f
     return PSS_OK;
 }
 
-// max over consecutive groups of 8 trials and channels of (dmax - dmin)
+// max over the dedispersion kernel's groups of consecutive trials and over
+// channels of (dmax - dmin)
 int32_t delay_spread(const int32_t* d, int64_t nb, int32_t ck) {
+    const int G = dedisp_group_trials();
     int32_t sp = 0;
-    for (int64_t g = 0; g < nb; g += 8) {
-        const int64_t ge = std::min<int64_t>(nb, g + 8);
+    for (int64_t g = 0; g < nb; g += G) {
+        const int64_t ge = std::min<int64_t>(nb, g + G);
         for (int32_t c = 0; c < ck; ++c) {
             int32_t lo = d[g * ck + c], hi = lo;
             for (int64_t i = g + 1; i < ge; ++i) {
@@ -286,6 +288,14 @@ pss_status run_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil,
         PSS_TRY(ctx->counter.ensure(sizeof(unsigned long long)));
         PSS_CUDA(cudaMemsetAsync(ctx->counter.p, 0, sizeof(unsigned long long), s));
     }
+    // twiddle table covering every stage's nfft (powers of two: the largest suffices)
+    int64_t nfft_max = 0;
+    for (const auto& st : plan->stages) nfft_max = std::max<int64_t>(nfft_max, st.nfft);
+    if (ctx->twid_n < nfft_max) {
+        PSS_TRY(ctx->twid.ensure((size_t)nfft_max * sizeof(float2)));
+        PSS_CUDA(launch_twiddles((float2*)ctx->twid.p, nfft_max, s));
+        ctx->twid_n = nfft_max;
+    }
     int64_t out_off = 0;  // packed output offset (elements) for spectrum/plane modes
     for (size_t si = 0; si < plan->stages.size(); ++si) {
         const StageInfo& st = plan->stages[si];
@@ -345,6 +355,8 @@ pss_status run_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil,
             fa.spec_out = spec;
             fa.spec_stride = M;
             fa.whiten_block = cfg->whiten_block;
+            fa.tw = (const float2*)ctx->twid.p;
+            fa.twM = ctx->twid_n;
             PSS_CUDA(launch_fft_whiten(fa, s, ctx));
             if (mode == MODE_SPECTRUM) {
                 out_off += (int64_t)nb * M;
@@ -402,7 +414,8 @@ pss_status check_errflag(pss_ctx* ctx, cudaStream_t s) {
     PSS_CUDA(cudaStreamSynchronize(s));
     if (flag) {
         PSS_CUDA(cudaMemsetAsync(ctx->errflag.p, 0, sizeof(int), s));
-        return fail(PSS_ETIMEOUT, "a kernel's bounded wait on its staging barrier expired; results discarded");
+        if (flag == 1) return fail(PSS_ETIMEOUT, "a kernel's bounded wait on its staging barrier expired; results discarded");
+        return fail(PSS_EINVAL, "dedispersion refused a delay spread larger than its launch was sized for; results discarded");
     }
     return PSS_OK;
 }
@@ -472,7 +485,7 @@ void pss_ctx_destroy(pss_ctx* c) {
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     DevBuf* bufs[] = {&c->fil_dev, &c->xcm, &c->delays_dev, &c->series, &c->sums, &c->fftA, &c->fftB,
-                      &c->spec, &c->plane, &c->cands, &c->counter, &c->taps, &c->tapinfo, &c->errflag};
+                      &c->spec, &c->plane, &c->cands, &c->counter, &c->taps, &c->tapinfo, &c->errflag, &c->twid};
     for (DevBuf* b : bufs) b->release();
     for (auto& r : c->prof_recs) {
         cudaEventDestroy(r.a);

@@ -1,16 +1,17 @@
 // Incoherent dedispersion (paper Sect. 2 step 2: one prepdata run per DM),
 // exact in integers:  s[t] = sum_c x[c][t + d_c],  s_ds[j] = sum_{k<ds} s[j*ds+k].
 //
-// Work decomposition.  A CTA owns G = 8 consecutive DM trials (one warp
+// Work decomposition.  A CTA owns G = 16 consecutive DM trials (one warp
 // each) and a tile of TN = 1024 native-rate output samples, and walks the
 // channels in chunks of CC.  For each channel of a chunk the bytes
-// [t0 + min_d, t0 + max_d + TN) that the 8 trials need are fetched once from
+// [t0 + min_d, t0 + max_d + TN) that the 16 trials need are fetched once from
 // global memory by the bulk-copy (TMA) engine into a shared-memory staging
 // area, while the warps are still summing the previous chunk; an mbarrier
 // with a byte count signals arrival.  The staged row is then expanded into
 // four copies shifted by 0..3 bytes, so every delay is served by aligned
 // 32-bit shared-memory reads (consecutive lanes read consecutive words: no
-// bank conflicts) and the 8 warps reuse the staged bytes.
+// bank conflicts) and the 16 warps reuse the staged bytes.  Row starts and
+// every warp's offsets for all channels are computed once per tile.
 //
 // Arithmetic is SWAR: a 32-bit word holds 4 consecutive 8-bit samples of one
 // channel; (w & 0x00FF00FF) and byte-permute(w) split it into two pairs of
@@ -29,7 +30,7 @@ namespace pss {
 
 namespace {
 
-constexpr int G = 8;             // DM trials per CTA (one per warp)
+constexpr int G = 16;            // DM trials per CTA (one per warp)
 constexpr int KW = 8;            // 32-bit words per lane
 constexpr int TN = 32 * 4 * KW;  // native samples per tile (1024)
 constexpr int NT = 32 * G;
@@ -79,8 +80,8 @@ __device__ __forceinline__ uint32_t madd(uint32_t x, uint32_t one, uint32_t acc)
 struct Smem {
     uint32_t* copies;  // [CC][4][RW]
     uint8_t* raw;      // [CC][RAWB]
-    int64_t* rs;       // [2][CC] 16-byte-aligned first staged byte of each row
-    int32_t* offs;     // [2][G][CC] byte offset of t0 + d into the staged row
+    int32_t* rs;       // [ck] first staged byte of each row, relative to t0 (16-byte aligned absolute)
+    uint16_t* offs;    // [G][ck] byte offset of t0 + d into the staged row
     uint64_t* bar;
 };
 
@@ -88,14 +89,14 @@ struct Smem {
 struct Layout {
     size_t copies, raw, rs, offs, bar, total;
 };
-__host__ __device__ inline Layout layout_of(int RW, int CC) {
+__host__ __device__ inline Layout layout_of(int RW, int CC, int ck) {
     Layout L;
     const size_t cp = (size_t)CC * 16 * RW, ep = (size_t)G * TN * 4;  // copies / epilogue scratch
     L.copies = 0;
     L.raw = cp > ep ? cp : ep;
     L.rs = L.raw + (size_t)CC * (4 * RW + 16);
-    L.offs = L.rs + 2 * (size_t)CC * 8;
-    L.bar = (L.offs + 2 * (size_t)G * CC * 4 + 7) & ~(size_t)7;
+    L.offs = L.rs + (size_t)ck * 4;
+    L.bar = (L.offs + (size_t)G * ck * 2 + 7) & ~(size_t)7;
     L.total = L.bar + 8;
     return L;
 }
@@ -104,12 +105,12 @@ template <bool INT_OUT, bool WIDE>
 __global__ void __launch_bounds__(NT) k_dedisp(DedispArgs a, int RW, int CC, uint32_t one) {
     extern __shared__ __align__(128) uint8_t smraw[];
     const int RAWB = 4 * RW + 16;
-    const Layout Lo = layout_of(RW, CC);
+    const Layout Lo = layout_of(RW, CC, a.ck);
     Smem S;
     S.copies = reinterpret_cast<uint32_t*>(smraw + Lo.copies);
     S.raw = smraw + Lo.raw;
-    S.rs = reinterpret_cast<int64_t*>(smraw + Lo.rs);
-    S.offs = reinterpret_cast<int32_t*>(smraw + Lo.offs);
+    S.rs = reinterpret_cast<int32_t*>(smraw + Lo.rs);
+    S.offs = reinterpret_cast<uint16_t*>(smraw + Lo.offs);
     S.bar = reinterpret_cast<uint64_t*>(smraw + Lo.bar);
 
     const int lane = threadIdx.x & 31;
@@ -126,24 +127,28 @@ __global__ void __launch_bounds__(NT) k_dedisp(DedispArgs a, int RW, int CC, uin
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
 
-    // per-chunk bookkeeping: row starts and each warp's offsets
-    auto prepare = [&](int c, int slot) {
-        const int cb = c * CC;
-        const int cn = min(CC, a.ck - cb);
-        for (int i = threadIdx.x; i < cn; i += NT) {
-            const int32_t* dcol = a.delays + (int64_t)g0 * a.ck + cb + i;
-            int32_t dmin = dcol[0];
-            for (int g = 1; g < gn; ++g) dmin = min(dmin, dcol[(int64_t)g * a.ck]);
-            S.rs[slot * CC + i] = (t0 + dmin) & ~int64_t(15);
+    // row starts and each warp's offsets for every channel of the tile; an
+    // offset past what the staged row holds (a spread larger than the launch
+    // was sized for) is refused rather than read out of bounds
+    const int omax = 4 * (RW - 32 * KW);
+    bool bad = false;
+    for (int c = threadIdx.x; c < a.ck; c += NT) {
+        const int32_t* dcol = a.delays + (int64_t)g0 * a.ck + c;
+        int32_t dmin = dcol[0];
+        for (int g = 1; g < gn; ++g) dmin = min(dmin, dcol[(int64_t)g * a.ck]);
+        const int64_t st = (t0 + dmin) & ~int64_t(15);
+        S.rs[c] = (int32_t)(st - t0);
+        for (int g = 0; g < gn; ++g) {
+            const int64_t o = t0 + dcol[(int64_t)g * a.ck] - st;
+            bad |= (o >= omax);
+            S.offs[g * a.ck + c] = (uint16_t)(bad ? 0 : o);
         }
-        __syncthreads();
-        for (int x = threadIdx.x; x < gn * cn; x += NT) {
-            const int g = x / cn, i = x - g * cn;
-            const int32_t d = a.delays[(int64_t)(g0 + g) * a.ck + cb + i];
-            S.offs[(slot * G + g) * CC + i] = (int32_t)(t0 + d - S.rs[slot * CC + i]);
-        }
-    };
-    auto issue = [&](int c, int slot) {
+    }
+    if (__syncthreads_or(bad)) {
+        if (threadIdx.x == 0 && a.err) atomicExch(a.err, 2);
+        return;
+    }
+    auto issue = [&](int c) {
         // warp 0: one bulk copy per row of the chunk
         if (warp == 0) {
             const int cb = c * CC;
@@ -154,7 +159,7 @@ __global__ void __launch_bounds__(NT) k_dedisp(DedispArgs a, int RW, int CC, uin
             // before the bulk copies overwrite it
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             for (int i = lane; i < cn; i += 32) {
-                const uint8_t* src = a.xcm + (int64_t)(cb + i) * a.pitch + S.rs[slot * CC + i];
+                const uint8_t* src = a.xcm + (int64_t)(cb + i) * a.pitch + t0 + S.rs[cb + i];
                 bulk_g2s(S.raw + (size_t)i * RAWB, src, (uint32_t)RAWB, S.bar);
             }
         }
@@ -168,13 +173,11 @@ __global__ void __launch_bounds__(NT) k_dedisp(DedispArgs a, int RW, int CC, uin
     for (int k = 0; k < (WIDE ? 4 * KW : 1); ++k) wide[k] = 0u;
     int since_flush = 0;
 
-    prepare(0, 0);
     __syncthreads();
-    issue(0, 0);
+    issue(0);
     const int qn = RW / 4;
     int failed_at = -1;
     for (int c = 0; c < nchunks; ++c) {
-        const int slot = c & 1;
         const int cb = c * CC;
         const int cn = min(CC, a.ck - cb);
         const bool ok = mbar_wait(S.bar, (uint32_t)(c & 1));
@@ -182,7 +185,6 @@ __global__ void __launch_bounds__(NT) k_dedisp(DedispArgs a, int RW, int CC, uin
             failed_at = c;
             break;
         }
-        if (c + 1 < nchunks) prepare(c + 1, slot ^ 1);
         // expand the staged rows into 4 byte-shifted copies
         for (int it = threadIdx.x; it < cn * qn; it += NT) {
             const int i = it / qn, q = it - i * qn;
@@ -202,7 +204,7 @@ __global__ void __launch_bounds__(NT) k_dedisp(DedispArgs a, int RW, int CC, uin
             }
         }
         __syncthreads();
-        if (c + 1 < nchunks) issue(c + 1, slot ^ 1);
+        if (c + 1 < nchunks) issue(c + 1);
         if constexpr (WIDE) {
             if (since_flush + cn > 256) {
 #pragma unroll
@@ -217,7 +219,7 @@ __global__ void __launch_bounds__(NT) k_dedisp(DedispArgs a, int RW, int CC, uin
             }
         }
         if (active) {
-            const int32_t* offs = S.offs + (slot * G + warp) * CC;
+            const uint16_t* offs = S.offs + warp * a.ck + cb;
 #pragma unroll 2
             for (int i = 0; i < cn; ++i) {
                 const int o = offs[i];
@@ -317,6 +319,7 @@ cudaError_t launch_t(const DedispArgs& a, dim3 grid, size_t shm, int RW, int CC,
 }  // namespace
 
 int dedisp_tile_samples() { return TN; }
+int dedisp_group_trials() { return G; }
 
 cudaError_t launch_dedisp(const DedispArgs& a, int num_sms, cudaStream_t s) {
     (void)num_sms;
@@ -328,7 +331,8 @@ cudaError_t launch_dedisp(const DedispArgs& a, int num_sms, cudaStream_t s) {
     int CC = (int)((64 * 1024) / per_chan);
     if (CC > 32) CC = 32;
     if (CC < 1) CC = 1;
-    const size_t shm = layout_of(RW, CC).total;
+    if (15 + a.spread > 65535 - 4 * RW) return cudaErrorInvalidValue;  // offsets are 16-bit
+    const size_t shm = layout_of(RW, CC, a.ck).total;
     if (shm > 220 * 1024) return cudaErrorInvalidValue;
     const int64_t L = a.nv * a.ds;
     dim3 grid((unsigned)((L + TN - 1) / TN), (unsigned)((a.nb + G - 1) / G));

@@ -7,13 +7,17 @@
 // is formed in the whitening kernel.
 //
 // The complex FFT is a Stockham auto-sort FFT with a few large-radix passes
-// (radix R = 64..1024, product = M).  In the pass with running length Ns,
-// element j + r*M/R (r < R) of each of M/R columns is multiplied by
+// (radix R = 32..1024, product = M).  In the pass with running length Ns,
+// element j + r*M/R (r < R) of each of the M/R columns is multiplied by
 // exp(-2 pi i r (j mod Ns) / (Ns R)), transformed by an R-point DFT and
 // written to (j / Ns) * Ns * R + (j mod Ns) + r * Ns.  A CTA owns TJ = 8
-// consecutive columns, reads them with contiguous 64-byte rows, does the
-// R-point DFT in shared memory with radix-4 (and one radix-2) Stockham
-// sub-stages, and writes contiguous rows.  Two passes cover M <= 2^20.
+// consecutive columns, reads them as contiguous 64-byte rows, does the
+// R-point DFT in shared memory with radix-8 Stockham sub-stages (one radix-2
+// or radix-4 sub-stage first when log2 R is not a multiple of 3), in place
+// (inputs of a sub-stage are held in registers across a barrier), and writes
+// contiguous rows.  Two passes cover M <= 2^20, three up to 2^24.  All twiddle factors
+// come from one table exp(-2 pi i t / Mt) (t < Mt, computed in FP64 and
+// rounded to FP32), read with stride Mt / P for a P-th root of unity.
 //
 // The first pass also subtracts the series mean (exact integer sum / N_v,
 // split into an integer and a fractional part so the FP32 subtraction is
@@ -26,96 +30,108 @@ namespace pss {
 
 namespace {
 
-constexpr int TJ = 8;       // columns per CTA
-constexpr int TJP = TJ + 1; // padded shared-memory row (bank spread)
-constexpr int NT = 256;     // threads per CTA
+constexpr int TJ = 8;        // columns per CTA
+constexpr int TJP = TJ + 1;  // padded shared-memory row (bank spread)
+constexpr int NT = 256;      // threads per CTA
+constexpr float R2 = 0.70710678118654752440f;
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-// multiply by -i
-__device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }
+__device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }  // * (-i)
 
-// exp(-2 pi i num / den) for integers 0 <= num < den, den a power of two
-__device__ __forceinline__ float2 twiddle(int64_t num, int64_t den) {
-    float s, c;
-    sincospif(-2.0f * (float)num / (float)den, &s, &c);
-    return make_float2(c, s);
+// forward DFTs of length 2, 4, 8 in registers (x[k] = sum_n x[n] e^{-2 pi i nk/L})
+__device__ __forceinline__ void dft2(float2* x) {
+    const float2 a = x[0], b = x[1];
+    x[0] = cadd(a, b);
+    x[1] = csub(a, b);
+}
+__device__ __forceinline__ void dft4(float2& y0, float2& y1, float2& y2, float2& y3) {
+    const float2 s02 = cadd(y0, y2), d02 = csub(y0, y2);
+    const float2 s13 = cadd(y1, y3), d13 = mul_mi(csub(y1, y3));
+    y0 = cadd(s02, s13);
+    y2 = csub(s02, s13);
+    const float2 t1 = cadd(d02, d13), t3 = csub(d02, d13);
+    y1 = t1;
+    y3 = t3;
+}
+__device__ __forceinline__ void dft4v(float2* x) { dft4(x[0], x[1], x[2], x[3]); }
+__device__ __forceinline__ void dft8(float2* x) {
+    float2 a0 = cadd(x[0], x[4]), b0 = csub(x[0], x[4]);
+    float2 a1 = cadd(x[1], x[5]), b1 = csub(x[1], x[5]);
+    float2 a2 = cadd(x[2], x[6]), b2 = csub(x[2], x[6]);
+    float2 a3 = cadd(x[3], x[7]), b3 = csub(x[3], x[7]);
+    // b_m *= w^m, w = exp(-2 pi i / 8)
+    b1 = make_float2((b1.x + b1.y) * R2, (b1.y - b1.x) * R2);
+    b2 = mul_mi(b2);
+    b3 = make_float2((b3.y - b3.x) * R2, -(b3.x + b3.y) * R2);
+    dft4(a0, a1, a2, a3);
+    dft4(b0, b1, b2, b3);
+    x[0] = a0; x[2] = a1; x[4] = a2; x[6] = a3;
+    x[1] = b0; x[3] = b1; x[5] = b2; x[7] = b3;
 }
 
-// In-place R-point DFT of TJ columns held in shared memory as
-// buf[r * TJP + jj], by Stockham sub-stages of radix 4 (and one of radix 2
-// when log2 R is odd).
+template <int RR>
+__device__ __forceinline__ void dft_small(float2* x) {
+    if constexpr (RR == 2) dft2(x);
+    else if constexpr (RR == 4) dft4v(x);
+    else dft8(x);
+}
+
+// One Stockham sub-stage of radix RR on the R-point DFTs of TJ columns,
+// in place in shared memory ([r * TJP + jj]), running span ns: every thread
+// reads its butterflies' inputs into registers, the block synchronises, and
+// the results are written back.  The twiddle exp(-2 pi i q k / (RR ns)) is
+// tws[q k R / (RR ns)], tws[t] = exp(-2 pi i t / R).
+template <int R, int RR>
+__device__ __forceinline__ void substage(float2* buf, const float2* tws, int ns) {
+    constexpr int NB = R / RR * TJ;
+    constexpr int PER = (NB + NT - 1) / NT;
+    float2 x[PER][RR];
+    int dst[PER];
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int e = threadIdx.x + p * NT;
+        if (NB % NT == 0 || e < NB) {
+            const int jj = e % TJ, b = e / TJ;
+            const int k = b % ns;
+            const int tstep = k * (R / RR / ns);
+#pragma unroll
+            for (int q = 0; q < RR; ++q) {
+                x[p][q] = buf[(b + q * (R / RR)) * TJP + jj];
+                if (q && k) x[p][q] = cmul(x[p][q], tws[q * tstep]);
+            }
+            dst[p] = ((b / ns) * ns * RR + k) * TJP + jj;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int e = threadIdx.x + p * NT;
+        if (NB % NT == 0 || e < NB) {
+            dft_small<RR>(x[p]);
+#pragma unroll
+            for (int q = 0; q < RR; ++q) buf[dst[p] + q * ns * TJP] = x[p][q];
+        }
+    }
+    __syncthreads();
+}
+
+// R-point DFTs of TJ columns held in buf (in place).
 template <int R>
-__device__ void smem_dft(float2* buf) {
+__device__ void smem_dft(float2* buf, const float2* tws) {
     constexpr int LOG = (R == 32) ? 5 : (R == 64) ? 6 : (R == 128) ? 7 : (R == 256) ? 8 : (R == 512) ? 9 : 10;
     int ns = 1;
-    if (LOG & 1) {
-        // radix-2 sub-stage first
-        constexpr int NB = R / 2 * TJ;
-        constexpr int PER = (NB + NT - 1) / NT;
-        float2 v[PER][2];
-        int dst[PER];
-#pragma unroll
-        for (int p = 0; p < PER; ++p) {
-            const int e = threadIdx.x + p * NT;
-            if (e < NB) {
-                const int jj = e % TJ, b = e / TJ;
-                v[p][0] = buf[b * TJP + jj];
-                v[p][1] = buf[(b + R / 2) * TJP + jj];
-                dst[p] = (2 * b) * TJP + jj;  // ns = 1: idxD = 2b
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int p = 0; p < PER; ++p) {
-            const int e = threadIdx.x + p * NT;
-            if (e < NB) {
-                buf[dst[p]] = cadd(v[p][0], v[p][1]);
-                buf[dst[p] + TJP] = csub(v[p][0], v[p][1]);
-            }
-        }
-        __syncthreads();
-        ns = 2;
+    if constexpr (LOG % 3 == 1) {
+        substage<R, 2>(buf, tws, ns);
+        ns *= 2;
+    } else if constexpr (LOG % 3 == 2) {
+        substage<R, 4>(buf, tws, ns);
+        ns *= 4;
     }
-    for (; ns < R; ns *= 4) {
-        constexpr int NB = R / 4 * TJ;
-        constexpr int PER = (NB + NT - 1) / NT;
-        float2 v[PER][4];
-        int dst[PER];
-#pragma unroll
-        for (int p = 0; p < PER; ++p) {
-            const int e = threadIdx.x + p * NT;
-            if (e < NB) {
-                const int jj = e % TJ, b = e / TJ;
-                const int k = b % ns;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    float2 x = buf[(b + q * (R / 4)) * TJP + jj];
-                    if (q && k) x = cmul(x, twiddle((int64_t)q * k, 4 * ns));
-                    v[p][q] = x;
-                }
-                dst[p] = ((b / ns) * ns * 4 + k) * TJP + jj;
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int p = 0; p < PER; ++p) {
-            const int e = threadIdx.x + p * NT;
-            if (e < NB) {
-                const float2 a0 = v[p][0], a1 = v[p][1], a2 = v[p][2], a3 = v[p][3];
-                const float2 s02 = cadd(a0, a2), d02 = csub(a0, a2);
-                const float2 s13 = cadd(a1, a3), d13 = mul_mi(csub(a1, a3));
-                buf[dst[p]] = cadd(s02, s13);
-                buf[dst[p] + ns * TJP] = cadd(d02, d13);
-                buf[dst[p] + 2 * ns * TJP] = csub(s02, s13);
-                buf[dst[p] + 3 * ns * TJP] = csub(d02, d13);
-            }
-        }
-        __syncthreads();
-    }
+    for (; ns < R; ns *= 8) substage<R, 8>(buf, tws, ns);
 }
 
 struct PassArgs {
@@ -129,53 +145,69 @@ struct PassArgs {
     int64_t out_stride;
     int64_t M;
     int64_t Ns;
+    const float2* tw;          // exp(-2 pi i t / twM)
+    int64_t twM;
 };
 
 template <int R>
-__global__ void __launch_bounds__(NT) k_fft_pass(PassArgs a) {
-    extern __shared__ float2 buf[];
+__global__ void __launch_bounds__(NT) k_fft_pass(const __grid_constant__ PassArgs a) {
+    extern __shared__ float2 sm[];
+    float2* bufA = sm;
+    float2* tws = sm + R * TJP;
     const int b = blockIdx.y;
     const int64_t ncol = a.M / R;
     const int64_t j0 = (int64_t)blockIdx.x * TJ;
     const bool first = (a.series != nullptr);
+    const int64_t tstride = a.twM / R;
+    for (int t = threadIdx.x; t < R; t += NT) tws[t] = a.tw[(int64_t)t * tstride];
 
-    float mu_i = 0.f, mu_f = 0.f;
     if (first) {
         // mean = sum / N_v in FP64, split as integer + fraction
         const double mu = (double)a.sums[b] / (double)a.nv;
         const double mi = rint(mu);
-        mu_i = (float)mi;
-        mu_f = (float)(mu - mi);
-    }
-    // load with twiddles
-    for (int e = threadIdx.x; e < R * TJ; e += NT) {
-        const int jj = e % TJ, r = e / TJ;
-        const int64_t j = j0 + jj;
-        float2 x = make_float2(0.f, 0.f);
-        if (j < ncol) {
-            const int64_t n = j + (int64_t)r * ncol;
-            if (first) {
-                const float* s = a.series + (int64_t)b * a.series_stride;
-                const int64_t m0 = 2 * n, m1 = 2 * n + 1;
-                x.x = (m0 < a.nv) ? (s[m0] - mu_i) - mu_f : 0.f;
-                x.y = (m1 < a.nv) ? (s[m1] - mu_i) - mu_f : 0.f;
-            } else {
-                x = a.in[(int64_t)b * a.in_stride + n];
-                const int64_t k = j % a.Ns;
-                if (k && r) x = cmul(x, twiddle(((int64_t)r * k) % (a.Ns * R), a.Ns * R));
+        const float mu_i = (float)mi, mu_f = (float)(mu - mi);
+        const float* s = a.series + (int64_t)b * a.series_stride;
+#pragma unroll
+        for (int e = threadIdx.x; e < R * TJ; e += NT) {
+            const int jj = e % TJ, r = e / TJ;
+            const int64_t j = j0 + jj;
+            float2 x = make_float2(0.f, 0.f);
+            if (j < ncol) {
+                const int64_t n = j + (int64_t)r * ncol;
+                if (2 * n + 1 < a.nv) {
+                    const float2 v = *reinterpret_cast<const float2*>(s + 2 * n);
+                    x = make_float2((v.x - mu_i) - mu_f, (v.y - mu_i) - mu_f);
+                } else if (2 * n < a.nv) {
+                    x.x = (s[2 * n] - mu_i) - mu_f;
+                }
             }
+            bufA[r * TJP + jj] = x;
         }
-        buf[r * TJP + jj] = x;
+    } else {
+        const int64_t ostride = a.twM / (a.Ns * R);
+        const float2* in = a.in + (int64_t)b * a.in_stride;
+#pragma unroll
+        for (int e = threadIdx.x; e < R * TJ; e += NT) {
+            const int jj = e % TJ, r = e / TJ;
+            const int64_t j = j0 + jj;
+            float2 x = make_float2(0.f, 0.f);
+            if (j < ncol) {
+                x = in[j + (int64_t)r * ncol];
+                const int64_t k = j % a.Ns;
+                if (k && r) x = cmul(x, a.tw[(int64_t)r * k * ostride]);
+            }
+            bufA[r * TJP + jj] = x;
+        }
     }
     __syncthreads();
-    smem_dft<R>(buf);
-    // store
+    smem_dft<R>(bufA, tws);
+    const float2* res = bufA;
     float2* o = a.out + (int64_t)b * a.out_stride;
     if (a.Ns == 1) {
         for (int e = threadIdx.x; e < R * TJ; e += NT) {
             const int r = e % R, jj = e / R;
             const int64_t j = j0 + jj;
-            if (j < ncol) o[j * R + r] = buf[r * TJP + jj];
+            if (j < ncol) o[j * R + r] = res[r * TJP + jj];
         }
     } else {
         for (int e = threadIdx.x; e < R * TJ; e += NT) {
@@ -183,7 +215,7 @@ __global__ void __launch_bounds__(NT) k_fft_pass(PassArgs a) {
             const int64_t j = j0 + jj;
             if (j < ncol) {
                 const int64_t k = j % a.Ns;
-                o[(j / a.Ns) * a.Ns * R + k + (int64_t)r * a.Ns] = buf[r * TJP + jj];
+                o[(j / a.Ns) * a.Ns * R + k + (int64_t)r * a.Ns] = res[r * TJP + jj];
             }
         }
     }
@@ -191,8 +223,9 @@ __global__ void __launch_bounds__(NT) k_fft_pass(PassArgs a) {
 
 template <int R>
 cudaError_t run_pass(const PassArgs& p, int nb, cudaStream_t s) {
-    const size_t shm = (size_t)R * TJP * sizeof(float2);
-    cudaFuncSetAttribute(k_fft_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    const size_t shm = (size_t)(R * TJP + R) * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(k_fft_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((p.M / R + TJ - 1) / TJ), (unsigned)nb);
     k_fft_pass<R><<<grid, NT, shm, s>>>(p);
     return cudaGetLastError();
@@ -210,87 +243,161 @@ cudaError_t dispatch_pass(int R, const PassArgs& p, int nb, cudaStream_t s) {
     }
 }
 
+__global__ void k_twiddles(float2* tw, int64_t n) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    double s, c;
+    sincospi(-2.0 * (double)t / (double)n, &s, &c);
+    tw[t] = make_float2((float)c, (float)s);
+}
+
 // ---- real-to-complex post-processing + whitening ---------------------------
 // One CTA per whitening block [bW, (b+1)W).  The lower median of |A_k|^2 is
-// found exactly by a 4-digit radix select on the float bit patterns (which
-// order like the values for non-negative floats).
+// selected exactly on the float bit patterns (which order like the values for
+// non-negative floats): a 2048-bin histogram of bits 30..20 locates the bin
+// holding the wanted rank; the (few) values in that bin are gathered and the
+// one of the right rank is found by counting, ties broken by position.  If
+// that bin holds more than NCAND values, three further 8/8/4-bit histogram
+// rounds on the remaining bits finish the selection instead.
+constexpr int NBIN = 2048;
+constexpr int NCAND = 256;
+
 template <int EPT>
-__global__ void __launch_bounds__(256) k_r2c_whiten(const float2* Zall, int64_t z_stride, int64_t M,
-                                                    int W, float2* out, int64_t out_stride) {
+__global__ void __launch_bounds__(256) k_r2c_whiten(const float2* Zall, int64_t z_stride, int64_t M, int W,
+                                                    float2* out, int64_t out_stride, const float2* tw, int64_t twM) {
     extern __shared__ uint32_t sh[];
-    uint32_t* key = sh;             // [W]
-    uint32_t* hist = sh + W;        // [256]
-    __shared__ uint32_t s_digit, s_rank;
+    uint32_t* key = sh;              // [W]
+    uint32_t* hist = sh + W;         // [NBIN]
+    uint32_t* cand = hist + NBIN;    // [NCAND] values
+    uint32_t* cpos = cand + NCAND;   // [NCAND] positions
+    __shared__ uint32_t s_part[8], s_bin, s_rank, s_cnt, s_val;
     const int b = blockIdx.y;
     const int64_t k0 = (int64_t)blockIdx.x * W;
     const float2* Z = Zall + (int64_t)b * z_stride;
     float2* O = out + (int64_t)b * out_stride;
+    const int nt = blockDim.x;
+    const int64_t wstride = twM / (2 * M);  // exp(-2 pi i k / nfft)
+    for (int i = threadIdx.x; i < NBIN; i += nt) hist[i] = 0u;
+    if (threadIdx.x == 0) s_cnt = 0u;
     float2 A[EPT];
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
-        const int64_t k = k0 + threadIdx.x + (int64_t)e * blockDim.x;
+        const int64_t k = k0 + threadIdx.x + (int64_t)e * nt;
         const float2 zk = Z[k];
         const float2 zm = Z[(M - k) & (M - 1)];
         const float2 zc = make_float2(zm.x, -zm.y);
         const float2 sum = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y + zc.y));
         const float2 dif = make_float2(0.5f * (zk.x - zc.x), 0.5f * (zk.y - zc.y));
-        // -(i) * w * dif,  w = exp(-2 pi i k / nfft) = exp(-pi i k / M)
-        float s, c;
-        sincospif(-(float)k / (float)M, &s, &c);
-        const float2 wd = make_float2(c * dif.x - s * dif.y, c * dif.y + s * dif.x);
-        float2 a = make_float2(sum.x + wd.y, sum.y - wd.x);
+        const float2 w = tw[k * wstride];
+        const float2 wd = cmul(w, dif);
+        float2 a = make_float2(sum.x + wd.y, sum.y - wd.x);  // sum - i * w * dif
         if (k == 0) a = make_float2(0.f, 0.f);
         A[e] = a;
         const float p = a.x * a.x + a.y * a.y;
-        key[threadIdx.x + e * blockDim.x] = (k == 0) ? 0xFFFFFFFFu : __float_as_uint(p);
+        key[threadIdx.x + e * nt] = (k == 0) ? 0xFFFFFFFFu : __float_as_uint(p);
     }
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+        const uint32_t kk = key[threadIdx.x + e * nt];
+        if (kk != 0xFFFFFFFFu) atomicAdd(&hist[kk >> 20], 1u);
+    }
+    __syncthreads();
     const int m = (k0 == 0) ? W - 1 : W;
-    uint32_t rank = (uint32_t)((m - 1) / 2);
-    uint32_t prefix = 0u, mask = 0u;
-    for (int pass = 0; pass < 4; ++pass) {
-        const int shift = 24 - 8 * pass;
-        for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0u;
+    const uint32_t rank0 = (uint32_t)((m - 1) / 2);
+    // block scan over NBIN bins: thread t owns bins [t*BPT, (t+1)*BPT)
+    const int BPT = NBIN / nt;
+    {
+        uint32_t tot = 0;
+        for (int i = 0; i < BPT; ++i) tot += hist[threadIdx.x * BPT + i];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        uint32_t incl = tot;
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += v;
+        }
+        if (lane == 31 || threadIdx.x == nt - 1) s_part[wid] = incl;
         __syncthreads();
+        uint32_t before = incl - tot;
+        for (int w2 = 0; w2 < wid; ++w2) before += s_part[w2];
+        for (int i = 0; i < BPT; ++i) {
+            const uint32_t c = hist[threadIdx.x * BPT + i];
+            if (rank0 >= before && rank0 < before + c) {
+                s_bin = (uint32_t)(threadIdx.x * BPT + i);
+                s_rank = rank0 - before;
+            }
+            before += c;
+        }
+    }
+    __syncthreads();
+    const uint32_t bin = s_bin, rank = s_rank;
+    const uint32_t nin = hist[bin];
+    uint32_t med_bits;
+    if (nin <= (uint32_t)NCAND) {
+        // gather the bin's values, then count ranks (ties by position)
 #pragma unroll
         for (int e = 0; e < EPT; ++e) {
-            const uint32_t kk = key[threadIdx.x + e * blockDim.x];
-            if (kk != 0xFFFFFFFFu && (kk & mask) == prefix) atomicAdd(&hist[(kk >> shift) & 255u], 1u);
+            const int pos = threadIdx.x + e * nt;
+            const uint32_t kk = key[pos];
+            if (kk != 0xFFFFFFFFu && (kk >> 20) == bin) {
+                const uint32_t slot = atomicAdd(&s_cnt, 1u);
+                cand[slot] = kk;
+                cpos[slot] = (uint32_t)pos;
+            }
         }
         __syncthreads();
-        if (threadIdx.x < 32) {
-            // warp 0 scans the 256 bins (8 per lane) to find the digit
-            const int lane = threadIdx.x;
-            uint32_t loc[8], tot = 0;
-            for (int i = 0; i < 8; ++i) {
-                loc[i] = hist[lane * 8 + i];
-                tot += loc[i];
+        for (uint32_t i = threadIdx.x; i < nin; i += nt) {
+            const uint32_t v = cand[i], pv = cpos[i];
+            uint32_t r = 0;
+            for (uint32_t q = 0; q < nin; ++q) {
+                const uint32_t u = cand[q];
+                r += (u < v) || (u == v && cpos[q] < pv);
             }
-            uint32_t incl = tot;
-            for (int off = 1; off < 32; off <<= 1) {
-                const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
-                if (lane >= off) incl += v;
+            if (r == rank) s_val = v;
+        }
+        __syncthreads();
+        med_bits = s_val;
+    } else {
+        // many values share the top bits: finish with radix rounds on bits 19..0
+        uint32_t prefix = bin << 20, mask = 0xFFF00000u, rk = rank;
+        const int shifts[3] = {12, 4, 0};
+        const int widths[3] = {8, 8, 4};
+        for (int pass = 0; pass < 3; ++pass) {
+            const int shift = shifts[pass];
+            const uint32_t dmask = (1u << widths[pass]) - 1u;
+            __syncthreads();
+            for (int i = threadIdx.x; i < 256; i += nt) hist[i] = 0u;
+            __syncthreads();
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) {
+                const uint32_t kk = key[threadIdx.x + e * nt];
+                if (kk != 0xFFFFFFFFu && (kk & mask) == prefix) atomicAdd(&hist[(kk >> shift) & dmask], 1u);
             }
-            uint32_t before = incl - tot;
-            for (int i = 0; i < 8; ++i) {
-                if (rank >= before && rank < before + loc[i]) {
-                    s_digit = (uint32_t)(lane * 8 + i);
-                    s_rank = rank - before;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                uint32_t before = 0;
+                for (uint32_t d = 0; d <= dmask; ++d) {
+                    if (rk < before + hist[d]) {
+                        s_bin = d;
+                        s_rank = rk - before;
+                        break;
+                    }
+                    before += hist[d];
                 }
-                before += loc[i];
             }
+            __syncthreads();
+            prefix |= s_bin << shift;
+            mask |= dmask << shift;
+            rk = s_rank;
         }
-        __syncthreads();
-        prefix |= s_digit << shift;
-        mask |= 255u << shift;
-        rank = s_rank;
-        __syncthreads();
+        med_bits = prefix;
     }
-    const float med = __uint_as_float(prefix);
+    const float med = __uint_as_float(med_bits);
     float scale = 0.f;
     if (med > 0.f) scale = (float)sqrt(0.69314718055994530942 / (double)med);
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
-        const int64_t k = k0 + threadIdx.x + (int64_t)e * blockDim.x;
+        const int64_t k = k0 + threadIdx.x + (int64_t)e * nt;
         O[k] = make_float2(A[e].x * scale, A[e].y * scale);
     }
 }
@@ -310,9 +417,15 @@ void radix_plan(int64_t M, int* rad, int* np) {
 
 }  // namespace
 
+cudaError_t launch_twiddles(float2* tw, int64_t n, cudaStream_t s) {
+    k_twiddles<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tw, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fft_whiten(const FftArgs& a, cudaStream_t s, Ctx* prof_ctx) {
     const int64_t M = a.nfft / 2;
     if (M < 64 || (M & (M - 1)) != 0) return cudaErrorInvalidValue;
+    if (!a.tw || a.twM < a.nfft || a.twM % a.nfft) return cudaErrorInvalidValue;
     int rad[4], np = 0;
     radix_plan(M, rad, &np);
     for (int i = 0; i < np; ++i)
@@ -321,6 +434,8 @@ cudaError_t launch_fft_whiten(const FftArgs& a, cudaStream_t s, Ctx* prof_ctx) {
     p.M = M;
     p.nv = a.nv;
     p.sums = a.sums;
+    p.tw = a.tw;
+    p.twM = a.twM;
     int64_t Ns = 1;
     const float2* in = nullptr;
     float2* bufs[2] = {a.bufA, a.bufB};
@@ -343,15 +458,18 @@ cudaError_t launch_fft_whiten(const FftArgs& a, cudaStream_t s, Ctx* prof_ctx) {
     const int W = a.whiten_block;
     if (W < 64 || W > 4096 || (W & (W - 1)) != 0 || M % W != 0) return cudaErrorInvalidValue;
     const int nt = W < 256 ? W : 256;
-    const size_t shm = (size_t)(W + 256) * sizeof(uint32_t);
+    const size_t shm = (size_t)(W + NBIN + 2 * NCAND) * sizeof(uint32_t);
     dim3 grid((unsigned)(M / W), (unsigned)a.nb);
     ProfScope ps(prof_ctx, 3, s);
     switch (W / nt) {
-#define PSS_WHITEN(E)                                                                            \
-    case E:                                                                                      \
-        cudaFuncSetAttribute(k_r2c_whiten<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm); \
-        k_r2c_whiten<E><<<grid, nt, shm, s>>>(in, M, M, W, a.spec_out, a.spec_stride);           \
-        break;
+#define PSS_WHITEN(E)                                                                                       \
+    case E: {                                                                                               \
+        cudaError_t e = cudaFuncSetAttribute(k_r2c_whiten<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                             (int)shm);                                                     \
+        if (e != cudaSuccess) return e;                                                                     \
+        k_r2c_whiten<E><<<grid, nt, shm, s>>>(in, M, M, W, a.spec_out, a.spec_stride, a.tw, a.twM);         \
+        break;                                                                                              \
+    }
         PSS_WHITEN(1)
         PSS_WHITEN(2)
         PSS_WHITEN(4)

@@ -26,129 +26,173 @@ namespace {
 
 constexpr int NT = 256;
 
-__global__ void __launch_bounds__(NT) k_harm(HarmArgs a, int TR, int TH) {
-    extern __shared__ float S[];  // [(TR+2) * (TH+2)], row r <-> j = j0 - 1 + r
-    __shared__ float s_thr[8];
-    __shared__ int s_hmin[8];
-    if (threadIdx.x < 8) {
-        const int i = threadIdx.x < a.nstages ? threadIdx.x : 0;
-        s_thr[threadIdx.x] = a.thr[i];
-        s_hmin[threadIdx.x] = a.hmin[i];
-    }
-    const int SW = TH + 2;
-    const int b = blockIdx.z;
-    const int h0 = blockIdx.x * TH;
-    const int j0 = blockIdx.y * TR;
-    const int nfft = (int)a.nfft;
-    const float* P = a.plane + (int64_t)b * a.plane_stride;
-    // rows of the plane present in tile + halo
-    const int jlo = max(j0 - 1, 0), jhi = min(j0 + TR + 1, a.nz);
-    const int r0 = jlo - (j0 - 1);
-    const int nrows = jhi - jlo;
-    const int halo_n = nrows * SW;
-    const int lane = threadIdx.x & 31;
+struct Tile {
+    int h0, j0, jlo, r0, halo_n, nfft, lane, b;
+    const float* P;
+};
 
-    for (int si = 0; si < a.nstages; ++si) {
-        const int n = 1 << si;
-        const int sh = si + 1;
-        for (int x = threadIdx.x; x < halo_n; x += NT) {
-            const int rr = x / SW, hc = x - rr * SW;
-            const int j = jlo + rr;
-            const int h = h0 - 1 + hc;
-            float* dst = S + (r0 + rr) * SW + hc;
-            if (h < 0 || h >= nfft) {
-                *dst = -INFINITY;
-                continue;
-            }
-            const int d = j - a.Z;
-            const int ad = d < 0 ? -d : d;
-            float acc;
-            if (si == 0) {
-                acc = __ldg(P + (int64_t)j * nfft + h);
+// Stage SI (n = 2^SI): add the odd harmonics to the sums held in S, then
+// test and compact the tile's points.  TR x TH is the tile; ONE_ROW is the
+// zmax = 0 case (a single plane row, no row arithmetic).
+template <int SI, int TR, int TH, bool ONE_ROW>
+__device__ __forceinline__ void harm_stage(const HarmArgs& a, const Tile& t, float* S, const float* s_thr,
+                                           const int* s_hmin) {
+    constexpr int n = 1 << SI;
+    constexpr int sh = SI + 1;
+    constexpr int SW = TH + 2;
+    for (int x = threadIdx.x; x < t.halo_n; x += NT) {
+        const int rr = ONE_ROW ? 0 : x / SW;
+        const int hc = ONE_ROW ? x : x - rr * SW;
+        const int j = t.jlo + rr;
+        const int h = t.h0 - 1 + hc;
+        float* dst = S + (t.r0 + rr) * SW + hc;
+        if (h < 0 || h >= t.nfft) {
+            *dst = -INFINITY;
+            continue;
+        }
+        float acc;
+        if constexpr (SI == 0) {
+            acc = __ldg(t.P + (ONE_ROW ? 0 : j * t.nfft) + h);
+        } else {
+            // the n/2 odd harmonics: independent loads, issued together
+            float v[n / 2];
+            const int h2 = 2 * h;
+            if constexpr (ONE_ROW) {
+#pragma unroll
+                for (int q = 0; q < n / 2; ++q) v[q] = __ldg(t.P + (((2 * q + 1) * h2 + n) >> sh));
             } else {
-                acc = *dst;
-                for (int k = 1; k < n; k += 2) {
-                    const int hk = (2 * k * h + n) >> sh;
-                    const int dk = (2 * k * ad + n) >> sh;
+                const int d = j - a.Z;
+                const int ad2 = 2 * (d < 0 ? -d : d);
+#pragma unroll
+                for (int q = 0; q < n / 2; ++q) {
+                    const int k = 2 * q + 1;
+                    const int dk = (k * ad2 + n) >> sh;
                     const int jk = d < 0 ? a.Z - dk : a.Z + dk;
-                    acc += __ldg(P + (int64_t)jk * nfft + hk);
+                    v[q] = __ldg(t.P + jk * t.nfft + ((k * h2 + n) >> sh));
                 }
             }
-            *dst = acc;
+            acc = *dst;
+#pragma unroll
+            for (int q = 0; q < n / 2; ++q) acc += v[q];
         }
-        __syncthreads();
-        const float thr = s_thr[si];
-        const int hmin = s_hmin[si];
-        const int npts = TR * TH;
-        for (int base = 0; base < npts; base += NT) {
-            const int p = base + threadIdx.x;
-            bool hit = false;
-            int j = 0, h = 0;
-            float s = 0.f;
-            if (p < npts) {
-                const int jr = p / TH, hc = p - jr * TH;
-                j = j0 + jr;
-                h = h0 + hc;
-                if (j < a.nz && h < nfft && h >= hmin) {
-                    const int x = (jr + 1) * SW + hc + 1;
-                    s = S[x];
-                    if (s >= thr) {
-                        hit = true;
+        *dst = acc;
+    }
+    __syncthreads();
+    const float thr = s_thr[SI];
+    const int hmin = s_hmin[SI];
+    constexpr int npts = TR * TH;
+#pragma unroll 1
+    for (int base = 0; base < npts; base += NT) {
+        const int p = base + threadIdx.x;
+        bool hit = false;
+        int j = 0, h = 0;
+        float s = 0.f;
+        if (p < npts) {
+            const int jr = p / TH, hc = p - jr * TH;
+            j = t.j0 + jr;
+            h = t.h0 + hc;
+            if (j < a.nz && h < t.nfft && h >= hmin) {
+                const int x = (jr + 1) * SW + hc + 1;
+                s = S[x];
+                if (s >= thr) {
+                    hit = true;
 #pragma unroll
-                        for (int dj = -1; dj <= 1; ++dj) {
-                            if (j + dj < 0 || j + dj >= a.nz) continue;
+                    for (int dj = -1; dj <= 1; ++dj) {
+                        if (ONE_ROW && dj != 0) continue;
+                        if (j + dj < 0 || j + dj >= a.nz) continue;
 #pragma unroll
-                            for (int dh = -1; dh <= 1; ++dh) {
-                                if (dj == 0 && dh == 0) continue;
-                                const float nb = S[x + dj * SW + dh];
-                                // the neighbour's linear index is larger iff (dj, dh) > (0, 0)
-                                const bool nb_later = (dj > 0) || (dj == 0 && dh > 0);
-                                if (!(s > nb || (s == nb && nb_later))) hit = false;
-                            }
+                        for (int dh = -1; dh <= 1; ++dh) {
+                            if (dj == 0 && dh == 0) continue;
+                            const float nb = S[x + dj * SW + dh];
+                            // the neighbour's linear index is larger iff (dj, dh) > (0, 0)
+                            const bool nb_later = (dj > 0) || (dj == 0 && dh > 0);
+                            if (!(s > nb || (s == nb && nb_later))) hit = false;
                         }
                     }
                 }
             }
-            const unsigned m = __ballot_sync(0xffffffffu, hit);
-            if (m) {
-                unsigned long long slot0 = 0ull;
-                if (lane == 0) slot0 = atomicAdd(a.counter, (unsigned long long)__popc(m));
-                slot0 = __shfl_sync(0xffffffffu, slot0, 0);
-                if (hit) {
-                    const unsigned long long slot = slot0 + __popc(m & ((1u << lane) - 1u));
-                    if ((int64_t)slot < a.cap) {
-                        pss_raw_cand c;
-                        c.dm_idx = a.dm0 + b;
-                        c.numharm = n;
-                        c.h = h;
-                        c.j = j;
-                        c.power = s;
-                        c.reserved = 0;
-                        a.out[slot] = c;
-                    }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (m) {
+            unsigned long long slot0 = 0ull;
+            if (t.lane == 0) slot0 = atomicAdd(a.counter, (unsigned long long)__popc(m));
+            slot0 = __shfl_sync(0xffffffffu, slot0, 0);
+            if (hit) {
+                const unsigned long long slot = slot0 + __popc(m & ((1u << t.lane) - 1u));
+                if ((int64_t)slot < a.cap) {
+                    pss_raw_cand c;
+                    c.dm_idx = a.dm0 + t.b;
+                    c.numharm = n;
+                    c.h = h;
+                    c.j = j;
+                    c.power = s;
+                    c.reserved = 0;
+                    a.out[slot] = c;
                 }
             }
         }
-        __syncthreads();
     }
+    __syncthreads();
+}
+
+template <int SI, int NSTAGES, int TR, int TH, bool ONE_ROW>
+__device__ __forceinline__ void harm_stages(const HarmArgs& a, const Tile& t, float* S, const float* s_thr,
+                                            const int* s_hmin) {
+    if constexpr (SI < NSTAGES) {
+        harm_stage<SI, TR, TH, ONE_ROW>(a, t, S, s_thr, s_hmin);
+        harm_stages<SI + 1, NSTAGES, TR, TH, ONE_ROW>(a, t, S, s_thr, s_hmin);
+    }
+}
+
+template <int NSTAGES, int TR, int TH, bool ONE_ROW>
+__global__ void __launch_bounds__(NT) k_harm(const __grid_constant__ HarmArgs a) {
+    __shared__ float S[(TR + 2) * (TH + 2)];  // row r <-> j = j0 - 1 + r
+    __shared__ float s_thr[8];
+    __shared__ int s_hmin[8];
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+        if (threadIdx.x == q) {  // constant indices keep the parameter block out of local memory
+            s_thr[q] = a.thr[q];
+            s_hmin[q] = a.hmin[q];
+        }
+    Tile t;
+    t.b = blockIdx.z;
+    t.h0 = blockIdx.x * TH;
+    t.j0 = blockIdx.y * TR;
+    t.nfft = (int)a.nfft;
+    t.P = a.plane + (int64_t)t.b * a.plane_stride;
+    // rows of the plane present in tile + halo
+    t.jlo = ONE_ROW ? 0 : max(t.j0 - 1, 0);
+    const int jhi = ONE_ROW ? 1 : min(t.j0 + TR + 1, a.nz);
+    t.r0 = t.jlo - (t.j0 - 1);
+    t.halo_n = (jhi - t.jlo) * (TH + 2);
+    t.lane = threadIdx.x & 31;
+    __syncthreads();
+    harm_stages<0, NSTAGES, TR, TH, ONE_ROW>(a, t, S, s_thr, s_hmin);
+}
+
+template <int TR, int TH, bool ONE_ROW>
+cudaError_t launch_variant(const HarmArgs& a, cudaStream_t s) {
+    dim3 grid((unsigned)((a.nfft + TH - 1) / TH), (unsigned)((a.nz + TR - 1) / TR), (unsigned)a.nb);
+    switch (a.nstages) {
+        case 1: k_harm<1, TR, TH, ONE_ROW><<<grid, NT, 0, s>>>(a); break;
+        case 2: k_harm<2, TR, TH, ONE_ROW><<<grid, NT, 0, s>>>(a); break;
+        case 3: k_harm<3, TR, TH, ONE_ROW><<<grid, NT, 0, s>>>(a); break;
+        case 4: k_harm<4, TR, TH, ONE_ROW><<<grid, NT, 0, s>>>(a); break;
+        case 5: k_harm<5, TR, TH, ONE_ROW><<<grid, NT, 0, s>>>(a); break;
+        case 6: k_harm<6, TR, TH, ONE_ROW><<<grid, NT, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_harm(const HarmArgs& a, cudaStream_t s) {
     if (a.nfft > (int64_t(1) << 24) || a.nstages > 6) return cudaErrorInvalidValue;
-    int TR, TH;
-    if (a.nz == 1) {
-        TR = 1;
-        TH = 2048;
-    } else {
-        TR = 4;
-        TH = 256;
-    }
-    const size_t shm = (size_t)(TR + 2) * (TH + 2) * sizeof(float);
-    dim3 grid((unsigned)((a.nfft + TH - 1) / TH), (unsigned)((a.nz + TR - 1) / TR), (unsigned)a.nb);
-    k_harm<<<grid, NT, shm, s>>>(a, TR, TH);
-    return cudaGetLastError();
+    if ((int64_t)a.nz * a.nfft > (int64_t(1) << 31)) return cudaErrorInvalidValue;  // 32-bit plane offsets
+    if (a.nz == 1) return launch_variant<1, 2048, true>(a, s);
+    return launch_variant<4, 256, false>(a, s);
 }
 
 }  // namespace pss

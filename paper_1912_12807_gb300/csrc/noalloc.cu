@@ -21,23 +21,30 @@ namespace {
 
 // Shared by every call on a device; held until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[PSS_NOALLOC_SCRATCH_BYTES];
+// Error flag the kernels set when they refuse or abandon work.
+static __device__ int g_noalloc_err;
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 void* g_scratch_addr[kMaxDevices] = {nullptr};
+void* g_err_addr[kMaxDevices] = {nullptr};
 
 // Device address of the static array on the current device (looked up once
 // per device; the first call on a device does this set-up).
-pss_status scratch_address(int dev, void** out) {
+pss_status scratch_address(int dev, void** out, int** err) {
     if (dev < 0 || dev >= kMaxDevices) return fail(PSS_EINVAL, "pss_dedisperse_noalloc: device index too large");
     std::lock_guard<std::mutex> lk(g_setup_mu);
     if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
+        void *p = nullptr, *q = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        e = cudaGetSymbolAddress(&q, g_noalloc_err);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_err)");
         g_scratch_addr[dev] = p;
+        g_err_addr[dev] = q;
     }
     *out = g_scratch_addr[dev];
+    *err = (int*)g_err_addr[dev];
     return PSS_OK;
 }
 
@@ -81,7 +88,9 @@ extern "C" pss_status pss_dedisperse_noalloc(const pss_plan* plan, const pss_fil
                                     std::to_string((size_t)PSS_NOALLOC_SCRATCH_BYTES) +
                                     " (use pss_dedisperse, or fewer channels, samples or DM trials)");
     void* base = nullptr;
-    PSS_TRY(scratch_address(dev, &base));
+    int* d_err = nullptr;
+    PSS_TRY(scratch_address(dev, &base, &d_err));
+    PSS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), s));
     int32_t* d_keep = (int32_t*)base;
     uint8_t* d_xcm = (uint8_t*)base + table_bytes;
 
@@ -112,12 +121,13 @@ extern "C" pss_status pss_dedisperse_noalloc(const pss_plan* plan, const pss_fil
         for (int64_t b0 = lo; b0 < hi; b0 += 1024) {
             const int32_t nb = (int32_t)std::min<int64_t>(1024, hi - b0);
             const int32_t* hrow = host.data() + (size_t)ck * (1 + (b0 - dm_begin));
-            // largest delay spread over groups of 8 consecutive trials
+            // largest delay spread over the kernel's groups of consecutive trials
+            const int32_t G = dedisp_group_trials();
             int32_t spread = 0;
-            for (int32_t g = 0; g < nb; g += 8)
+            for (int32_t g = 0; g < nb; g += G)
                 for (int32_t c = 0; c < ck; ++c) {
                     int32_t mn = hrow[(size_t)g * ck + c], mx = mn;
-                    for (int32_t i = g + 1; i < std::min(nb, g + 8); ++i) {
+                    for (int32_t i = g + 1; i < std::min(nb, g + G); ++i) {
                         mn = std::min(mn, hrow[(size_t)i * ck + c]);
                         mx = std::max(mx, hrow[(size_t)i * ck + c]);
                     }
@@ -136,12 +146,15 @@ extern "C" pss_status pss_dedisperse_noalloc(const pss_plan* plan, const pss_fil
             da.out_stride = st.nv;
             da.sums = nullptr;
             da.spread = spread;
-            da.err = nullptr;
+            da.err = d_err;
             PSS_CUDA(launch_dedisp(da, 0, s));
             off += (int64_t)nb * st.nv;
         }
     }
+    int flag = 0;
+    PSS_CUDA(cudaMemcpyAsync(&flag, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     // the delay upload reads `host`, which goes out of scope on return
     PSS_CUDA(cudaStreamSynchronize(s));
+    if (flag) return fail(flag == 1 ? PSS_ETIMEOUT : PSS_EINVAL, "pss_dedisperse_noalloc: the kernel refused or abandoned its work");
     return PSS_OK;
 }

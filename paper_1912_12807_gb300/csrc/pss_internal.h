@@ -126,6 +126,8 @@ struct Ctx {
     DevBuf taps;         // float2 templates
     DevBuf tapinfo;      // per row tap info
     DevBuf errflag;      // int: a kernel's bounded wait expired
+    DevBuf twid;         // float2 twiddle table exp(-2 pi i t / twid_n)
+    int64_t twid_n = 0;
     void* host_pinned = nullptr;
     size_t host_pinned_bytes = 0;
     // (zmax, extra, dz) of the templates currently in `taps`
@@ -179,6 +181,7 @@ struct DedispArgs {
     int* err;               // set to 1 if a bounded wait expires (nullable)
 };
 int dedisp_tile_samples();
+int dedisp_group_trials();  // consecutive trials sharing one staged tile
 cudaError_t launch_dedisp(const DedispArgs& a, int num_sms, cudaStream_t s);
 
 struct FftArgs {
@@ -193,7 +196,10 @@ struct FftArgs {
     float2* spec_out;                 // [nb][spec_stride]
     int64_t spec_stride;
     int32_t whiten_block;
+    const float2* tw;                 // exp(-2 pi i t / twM), t < twM; twM a multiple of nfft
+    int64_t twM;
 };
+cudaError_t launch_twiddles(float2* tw, int64_t n, cudaStream_t s);
 cudaError_t launch_fft_whiten(const FftArgs& a, cudaStream_t s, Ctx* prof_ctx);
 
 struct PlaneArgs {
