@@ -1,11 +1,16 @@
-"""Benchmark: DM-trials searched per second on the drift-scan-shaped file.
+"""Benchmark: DM-trials searched per second.
 
-Workload (one step): the full periodicity search of one synthetic
-256-channel, 2^18-sample (52.4 s at 0.2 ms) 8-bit file over DM 0-500 in
-steps of 0.5 (1001 trials), zmax 0, harmonic sums up to 16, 6 sigma:
-unpack/transpose, dedispersion, FFT, whitening, power plane, harmonic
-sums with thresholding, candidate download and sifting -- one call of
-pss_search_dm_batch with the file already resident on the GPU.
+Default workload (one step): the full periodicity search of one synthetic
+256-channel, 2^18-sample (52.4 s at 0.2 ms) 8-bit drift-scan-shaped file
+over DM 0-500 in steps of 0.5 (1001 trials), zmax 0, harmonic sums up to 16,
+6 sigma: unpack/transpose, dedispersion, FFT, whitening, power plane,
+harmonic sums with thresholding, candidate download and sifting -- one call
+of pss_search_dm_batch with the file already resident on the GPU.
+
+Other workloads (--workload): accel (same file shape, DM 0-300 step 1,
+zmax 200, dz 2, numharm 8), pmps (96-channel 1-bit 2^23-sample file, staged
+plan of 1081 trials, zmax 0, numharm 16), pmps50 (the same with zmax 50),
+small (64 channels, 2^16 samples, 101 trials).
 
 `e2e` repeats the step through the same C call with the file in pinned
 host memory (upload and candidate download inside the timed region).
@@ -14,9 +19,9 @@ Multi-GPU (torchrun): every rank searches its own file (independent
 problems, weak scaling, no collective); value = all ranks' DM trials /
 the slowest rank's time.
 
-`--impl reference` times the FP64 CPU oracle (the only reference there
-is: the paper's pipeline is PRESTO on CPUs, not available here) on the
-host cores, on a bounded sample of the same workload's DM trials.
+`--impl reference` times the FP64 CPU oracle (the only reference there is:
+the paper's pipeline is PRESTO on CPUs, not available here) on the host
+cores, on a bounded sample of the same workload's DM trials.
 """
 from __future__ import annotations
 
@@ -36,14 +41,39 @@ sys.path.insert(0, ROOT)
 
 METRIC = "DM-trials searched/s and files/s vs 26 s realtime; batched vs plain; p99 lat"
 UNIT = "DM-trials/s"
-WORKLOAD = "driftscan_256ch_2^18_8bit_dm0-500x0.5_1001trials_zmax0_numharm16"
 REALTIME_S = 26.0
 
+WORKLOADS = {
+    "driftscan": "driftscan_256ch_2^18_8bit_dm0-500x0.5_1001trials_zmax0_numharm16",
+    "accel": "accel_256ch_2^18_8bit_dm0-300x1_301trials_zmax200_dz2_numharm8",
+    "pmps": "pmps_96ch_1bit_2^23_staged1081trials_zmax0_numharm16",
+    "pmps50": "pmps_96ch_1bit_2^23_staged1081trials_zmax50_numharm16",
+    "small": "small_64ch_2^16_8bit_dm0-100x1_101trials_zmax0_numharm8",
+}
 
-def _config(extra=None):
-    c = {"workload": WORKLOAD, "nchan": 256, "nsamp": 1 << 18, "tsamp_s": 2e-4, "band_mhz": [1050, 1450],
-         "dm_trials": 1001, "zmax": 0, "numharm": 16, "sigma_thr": 6.0,
-         "l2": "256 MiB buffer written between timed steps (input 64 MiB < L2)"}
+
+def make_workload(name: str, n_dm=None, seed_offset: int = 0):
+    from paper_1912_12807_gb300 import synth
+    if name == "driftscan":
+        return synth.workload_driftscan(seed=1002 + seed_offset, n_dm=n_dm or 1001)
+    if name == "accel":
+        return synth.workload_accel(seed=1003 + seed_offset, n_dm=n_dm or 301)
+    if name == "pmps":
+        return synth.workload_pmps(seed=1004 + seed_offset, zmax=0)
+    if name == "pmps50":
+        return synth.workload_pmps(seed=1004 + seed_offset, zmax=50)
+    if name == "small":
+        return synth.workload_small(seed=1001 + seed_offset)
+    raise ValueError(name)
+
+
+def _config(wl, name, extra=None):
+    f = wl.fil
+    c = {"workload": WORKLOADS[name], "nchan": f.nchan, "nsamp": f.nsamp, "nbits": f.nbits,
+         "tsamp_s": f.tsamp_s, "dm_trials": int(sum(s.n_dm for s in wl.stages)),
+         "stages": [[s.dm_lo, s.dm_step, s.n_dm, s.ds] for s in wl.stages],
+         "zmax": wl.cfg.zmax, "dz": wl.cfg.dz, "numharm": wl.cfg.numharm, "sigma_thr": wl.cfg.sigma_thr,
+         "l2": "256 MiB buffer written between timed steps"}
     if extra:
         c.update(extra)
     return c
@@ -53,64 +83,72 @@ def _config(extra=None):
 _W = {}
 
 
-def _worker_init():
-    from paper_1912_12807_gb300 import synth
+def _worker_init(name):
     from oracle import dedisperse as OD
     from oracle import plan as OP
     from oracle import stats as OST
-    wl = synth.workload_driftscan()
+    wl = make_workload(name)
     _W["wl"] = wl
     _W["P"] = OP.Plan.for_file(wl.fil, wl.stages)
-    _W["x"] = OD.channel_major(wl.fil.data, wl.fil.nchan, 8)
+    _W["x"] = OD.channel_major(wl.fil.data, wl.fil.nchan, wl.fil.nbits)
     _W["thr"] = OST.thresholds(wl.cfg.numharm, wl.cfg.sigma_thr)
 
 
 def _worker_trial(i):
     from oracle import search as OSr
-    return len(OSr.search_trial(_W["x"], _W["P"], int(i), _W["wl"].cfg, _W["thr"]))
+    method = "fftconv" if _W["wl"].cfg.zmax > 0 else "direct"
+    return len(OSr.search_trial(_W["x"], _W["P"], int(i), _W["wl"].cfg, _W["thr"], plane_method=method))
 
 
-def _oracle_pool(cores):
+def _oracle_pool(cores, name):
     ctx = mp.get_context("spawn")
-    return ctx.Pool(cores, initializer=_worker_init)
+    return ctx.Pool(cores, initializer=_worker_init, initargs=(name,))
 
 
-def oracle_rate(pool, cores, n_trials, ndm=1001, offset=0):
+def oracle_rate(pool, n_trials, ndm, offset=0):
     """Time the oracle over n_trials DM trials spread over the plan."""
     idx = [int((offset + k * ndm / n_trials)) % ndm for k in range(n_trials)]
     t0 = time.perf_counter()
     pool.map(_worker_trial, idx, chunksize=1)
     dt = time.perf_counter() - t0
-    return n_trials / dt, dt, idx
+    return n_trials / dt, dt
 
 
-def cpu_baseline_block(value, cores, n, dt):
+def cpu_baseline_block(value, cores, n, ndm, dt):
     return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d of the 1001 DM trials (evenly spaced), each searched end to end by the FP64 "
-                      "NumPy oracle in a spawn pool of %d processes; %.1f s wall" % (n, cores, dt)}
+            "sample": "%d of the %d DM trials (evenly spaced), each searched end to end by the FP64 "
+                      "NumPy oracle in a spawn pool of %d processes; %.1f s wall" % (n, ndm, cores, dt)}
+
+
+def _per_step_trials(name, cores):
+    # keep a sample near 10-30 s of CPU work
+    per_core = {"driftscan": 8, "small": 40, "accel": 1, "pmps": 1, "pmps50": 1}[name]
+    return max(2, per_core * cores)
 
 
 def run_reference(args, rank):
     if rank != 0:
         return
+    name = args.workload
+    wl = make_workload(name)
+    ndm = int(sum(s.n_dm for s in wl.stages))
     cores = os.cpu_count() or 1
-    pool = _oracle_pool(cores)
-    pool.map(_worker_trial, list(range(cores)), chunksize=1)  # warm the workers (imports, file)
-    per_step = 4 * cores
+    pool = _oracle_pool(cores, name)
+    pool.map(_worker_trial, list(range(min(cores, ndm))), chunksize=1)  # warm the workers
+    per_step = max(1, _per_step_trials(name, cores) // 2)
     for w in range(args.warmup):
-        oracle_rate(pool, cores, cores, offset=w * 7)
-    rates, dts = [], []
+        oracle_rate(pool, max(1, cores // 2), ndm, offset=w * 7)
+    dts = []
     for k in range(args.steps):
-        r, dt, _ = oracle_rate(pool, cores, per_step, offset=13 + k * 31)
-        rates.append(r)
+        _, dt = oracle_rate(pool, per_step, ndm, offset=13 + k * 31)
         dts.append(dt)
     pool.close()
     value = per_step * args.steps / sum(dts)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * sum(dts) / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": _config({"step": "%d DM trials per step (bounded sample)" % per_step}),
-            "cpu_baseline": cpu_baseline_block(value, cores, per_step * args.steps, sum(dts)),
+            "config": _config(wl, name, {"step": "%d DM trials per step (bounded sample)" % per_step}),
+            "cpu_baseline": cpu_baseline_block(value, cores, per_step * args.steps, ndm, sum(dts)),
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -169,7 +207,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.samples)}
 
 
-# ---------------------------------------------------------------- GPU arm
+# ---------------------------------------------------------------- rooflines
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -178,29 +216,94 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def stage_work(plan, wl, fil_nbytes):
+    """Algorithmic work of one step per profiled stage: (bound, amount, unit).
+
+    dedisperse: kept channels x output samples x ds additions (each output
+    sample sums one 8-bit sample per channel per native sample);
+    unpack: file read + channel-major write; fft: every pass reads and writes
+    8 bytes per complex point; whiten: spectrum read + write; plane: for
+    zmax 0 the spectrum read + plane write, for zmax > 0 the 8 flops of every
+    complex tap of the correlation; harmsum: one read of the plane."""
+    ndm = plan.ndm
+    cfg = wl.cfg
+    nz = int(round(2 * cfg.zmax / cfg.dz)) + 1 if cfg.zmax else 1
+    adds = 0.0
+    fft_b = whiten_b = plane_b = harm_b = 0.0
+    plane_flops = 0.0
+    for i in range(ndm):
+        t = plan.trial(i)
+        nv, nfft, ds = t["nv"], t["nfft"], t["ds"]
+        M = nfft // 2
+        adds += float(wl.fil.nchan) * nv * ds
+        passes = max(1, int(math.ceil(math.log2(M) / 10)))
+        fft_b += passes * 2 * 8.0 * M
+        whiten_b += 2 * 8.0 * M
+        harm_b += 4.0 * nz * nfft
+        if cfg.zmax == 0:
+            plane_b += 8.0 * M + 4.0 * nfft
+        else:
+            for j in range(nz):
+                z = -cfg.zmax + j * cfg.dz
+                m = int(math.ceil(abs(z) / 2)) + cfg.halfwidth_extra
+                plane_flops += 2 * (2 * m) * 8.0 * M
+    return {"unpack": ("hbm", 2.0 * fil_nbytes, "bytes"),
+            "dedisperse": ("alu", adds, "channel-adds"),
+            "fft": ("hbm", fft_b, "bytes"),
+            "whiten": ("hbm", whiten_b, "bytes"),
+            "plane": ("hbm", plane_b, "bytes") if cfg.zmax == 0 else ("alu", plane_flops, "flops"),
+            "harmsum": ("hbm", harm_b, "bytes")}
+
+
+def roofline_of(stage, bound, amount, unit, ms, launches, peaks, peak_kind):
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    per_launch = amount / max(launches, 1)
+    t = (ms / max(launches, 1)) / 1e3
+    ach = per_launch / t if t > 0 else 0.0
+    if bound == "hbm":
+        peak = hbm * 1e9
+        return {"kernel": stage, "bound": "hbm", "achieved": ach / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": ach / peak, "traffic": None, "peak_source": "hbm_gbs (%s)" % peak_kind}
+    if unit == "channel-adds":
+        # 152 SMs x 64 integer-ALU lanes x 2 sixteen-bit additions per 32-bit add
+        peak = 152 * 64 * 2 * sm_mhz * 1e6
+        return {"kernel": stage, "bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12,
+                "unit": "T channel-adds/s", "frac": ach / peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x 64 INT lanes x 2 (16-bit SWAR) x %.0f MHz (%s clock)"
+                               % (sm_mhz, peak_kind)}
+    peak = 152 * 128 * 2 * sm_mhz * 1e6  # FP32 FMA lanes
+    return {"kernel": stage, "bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+            "frac": ach / peak, "traffic": None,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x %.0f MHz (%s clock)" % (sm_mhz, peak_kind)}
+
+
+# ---------------------------------------------------------------- GPU arm
 def run_ours(args, rank, world, local_rank):
-    import numpy as np
     import torch
 
-    from paper_1912_12807_gb300 import pss, synth
+    from paper_1912_12807_gb300 import pss
 
+    name = args.workload
     # CPU baseline first (spawn pool, before any CUDA call), rank 0 at N=1 only
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        wl0 = make_workload(name)
+        ndm0 = int(sum(s.n_dm for s in wl0.stages))
         cores = os.cpu_count() or 1
-        pool = _oracle_pool(cores)
-        pool.map(_worker_trial, list(range(cores)), chunksize=1)
-        n = 8 * cores
-        r, dt, _ = oracle_rate(pool, cores, n, offset=5)
+        pool = _oracle_pool(cores, name)
+        pool.map(_worker_trial, list(range(min(cores, ndm0))), chunksize=1)
+        n = _per_step_trials(name, cores)
+        r, dt = oracle_rate(pool, n, ndm0, offset=5)
         pool.close()
-        cpu = cpu_baseline_block(r, cores, n, dt)
+        cpu = cpu_baseline_block(r, cores, n, ndm0, dt)
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    wl = synth.workload_driftscan(seed=1002 + rank, n_dm=args.dm_trials)
+    wl = make_workload(name, n_dm=args.dm_trials, seed_offset=rank)
     fil = wl.fil
     ctx = pss.Context(local_rank)
     plan = pss.Plan(pss.FilDesc.of(fil), wl.stages)
@@ -212,11 +315,10 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
 
     def step(on_device=True):
-        src = data_dev if on_device else data_host
         if on_device:
-            return pss.pss_search_dm_batch(ctx, plan, src, cfg, 0, ndm, stream=stream.cuda_stream)
+            return pss.pss_search_dm_batch(ctx, plan, data_dev, cfg, 0, ndm, stream=stream.cuda_stream)
         # a numpy view of the pinned tensor: the library uploads it inside the call
-        return pss.pss_search_dm_batch(ctx, plan, src.numpy(), cfg, 0, ndm, stream=stream.cuda_stream)
+        return pss.pss_search_dm_batch(ctx, plan, data_host.numpy(), cfg, 0, ndm, stream=stream.cuda_stream)
 
     for _ in range(args.warmup):
         cands = step()
@@ -259,7 +361,7 @@ def run_ours(args, rank, world, local_rank):
         flush.fill_((k + 1) & 0xFF)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        c2 = step(on_device=False)
+        step(on_device=False)
         t1 = time.perf_counter()
         e2e_ms.append(1e3 * (t1 - t0))
     e2e = statistics.mean(e2e_ms)
@@ -276,36 +378,30 @@ def run_ours(args, rank, world, local_rank):
         return
     value = world * ndm / (ms / 1e3)
     peaks, peak_kind = measured_peaks()
-    d_ms, d_n = prof["dedisperse"]
+    work = stage_work(plan, wl, fil.nbytes())
+    rooflines = {}
+    for st, (ms_st, n_st) in prof.items():
+        if n_st == 0:
+            continue
+        bound, amount, unit = work[st]
+        rooflines[st] = roofline_of(st, bound, amount * args.steps, unit, ms_st, n_st, peaks, peak_kind)
+    dominant = max(prof, key=lambda k: prof[k][0])
     launches_per_step = sum(n for _, n in prof.values()) / args.steps
-    # dedispersion: C_kept * N_v channel additions per trial (one 8-bit sample
-    # added per channel per output sample), all trials of the step in d_n launches
-    nv = plan.trial(0)["nv"]
-    adds = float(fil.nchan) * nv * ndm
-    per_launch_adds = adds * args.steps / max(d_n, 1)
-    d_avg_s = (d_ms / max(d_n, 1)) / 1e3
-    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    # ALU ceiling of the SWAR scheme: 152 SMs x 64 integer-ALU lanes per clock
-    # x 2 sixteen-bit additions per 32-bit add, at the maximum SM clock
-    alu_peak = 152 * 64 * 2 * sm_mhz * 1e6
-    achieved = per_launch_adds / d_avg_s if d_avg_s > 0 else 0.0
-    roof = {"kernel": "k_dedisp", "bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12,
-            "unit": "T channel-adds/s", "frac": achieved / alu_peak, "traffic": None,
-            "peak_source": "derived: 152 SMs x 64 INT lanes x 2 (16-bit SWAR) x %.0f MHz (%s clock)"
-                           % (sm_mhz, peak_kind)}
     bi = fil.nbytes()
     bo = int(len(cands)) * pss.CAND_DTYPE.itemsize
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "i32+f32", "data": "synthetic",
-            "config": _config({"dm_trials": ndm}), "files_per_s": world * 1e3 / ms, "s_per_file": ms / 1e3,
-            "realtime_budget_s": REALTIME_S, "realtime_factor": REALTIME_S / (ms / 1e3),
-            "roofline": roof,
+            "config": _config(wl, name, {"dm_trials": ndm}), "files_per_s": world * 1e3 / ms,
+            "s_per_file": ms / 1e3, "realtime_budget_s": REALTIME_S, "realtime_factor": REALTIME_S / (ms / 1e3),
+            "roofline": rooflines[dominant],
             "e2e": {"value": world * ndm / (e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": bi,
                     "d2h_bytes_per_step": bo, "ms_per_step": e2e},
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
             "stage_launches_per_step": {k: v[1] / args.steps for k, v in prof.items()},
+            "stage_rooflines": {k: {"bound": v["bound"], "frac": v["frac"], "achieved": v["achieved"],
+                                    "unit": v["unit"]} for k, v in rooflines.items()},
             "clocks": clocks.summary(), "wall_s_timed": t_wall, "candidates": int(len(cands)),
             "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
@@ -321,9 +417,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="driftscan", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--dm-trials", type=int, default=1001,
-                    help="DM trials of the plan (0.5 step from DM 0); smaller values make profiling cases")
+    ap.add_argument("--dm-trials", type=int, default=None,
+                    help="DM trials of a single-stage plan (driftscan/accel); smaller values make profiling cases")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

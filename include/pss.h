@@ -281,6 +281,44 @@ pss_status pss_search_dm_batch(pss_ctx* ctx, const pss_plan* plan, const pss_fil
                                int64_t dm_begin, int64_t dm_end, pss_cand* out, int64_t cap,
                                int64_t* n_out, void* stream);
 
+/* ---- candidate refinement (no counterpart in the paper, which folds) ---- */
+
+/* A point of the refinement objective: the trial dm_idx supplies the series
+ * span T, nfft and the whitening gains; (dm, r, z) are continuous. */
+typedef struct {
+    int32_t dm_idx;
+    int32_t numharm;
+    double dm;
+    double r;
+    double z;
+} pss_refine_point;
+
+/* Prepare refinement for plan stage `stage`: the mean-subtracted spectrum
+ * of every kept channel alone (same N_v, ds and nfft as the stage's trials)
+ * and the whitening gains ln 2 / med_b of every trial of the stage are kept
+ * on the device in the context until the next prepare. */
+pss_status pss_refine_prepare(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const void* data,
+                              int data_on_device, const pss_search_cfg* cfg, int32_t stage, void* stream);
+
+/* Objective and gradient at n points (host arrays) of the prepared stage:
+ *   P_h(DM, r, z) = sum_{k=1..h} g(floor(kr)) |F_k|^2 / E_k,
+ *   F_k = sum_c exp(i 2 pi (k r) DM dtau_c / T) sum_q A^c_q conj(rho(kr - q, kz)),
+ * q over the 2m(kz) bins nearest kr (as for pss_power_plane), E_k the energy
+ * of those taps, dtau_c = K (f_c^-2 - f_ref^-2) the delay per unit DM,
+ * g the block's whitening gain in trial dm_idx.  power: n doubles;
+ * grad (nullable): 3n doubles (dP/dDM, dP/dr, dP/dz), analytic. */
+pss_status pss_refine_eval(pss_ctx* ctx, const pss_plan* plan, const pss_refine_point* pts, int64_t n,
+                           double* power, double* grad, void* stream);
+
+/* Gradient ascent (Adam, `iters` steps of size lr in cell units: DM step of
+ * the candidate's stage, one bin in r, dz in z; z stays fixed when zmax is
+ * 0; at most two cells from the start) on P_h for each candidate (host
+ * array).  Each candidate is replaced by the best point visited: dm, r, z,
+ * f_hz, power = P_h and its sigma. */
+pss_status pss_refine_candidates(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const void* data,
+                                 int data_on_device, const pss_search_cfg* cfg, pss_cand* inout, int64_t n,
+                                 int32_t iters, double lr, void* stream);
+
 /* Evaluate rho(q_i, z_i) (see pss_power_plane) on the context's GPU in FP64.
  * q, z: host arrays of n doubles; out: host array of 2n doubles (re, im).
  * Exposes the template arithmetic so that it can be checked directly. */

@@ -82,7 +82,7 @@ class Objective:
         m = _resp.halfwidth(zk, self.cfg.halfwidth_extra)
         k0 = int(math.floor(rk))
         qs = np.arange(k0 - m + 1, k0 + m + 1)
-        rho = np.array([_resp.rho_quad(rk - q, zk) for q in qs])
+        rho = np.array([_resp.rho(rk - q, zk) for q in qs])
         E = float(np.sum(np.abs(rho) ** 2))
         ok = (qs >= 0) & (qs < M)
         G = self.Ac[:, qs[ok]] @ np.conj(rho[ok])          # [C]

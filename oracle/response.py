@@ -51,6 +51,17 @@ def rho_quad(q: float, z: float) -> complex:
     return complex(np.sum(w * np.cos(ph)), np.sum(w * np.sin(ph)))
 
 
+def rho(q: float, z: float) -> complex:
+    """rho(q, z): the sinc closed form at z = 0 (pinned to the quadrature by
+    the tests), the quadrature of the defining integral otherwise."""
+    if z == 0.0:
+        q = float(q)
+        if q == 0.0:
+            return 1.0 + 0.0j
+        return complex(math.cos(math.pi * q), math.sin(math.pi * q)) * (math.sin(math.pi * q) / (math.pi * q))
+    return rho_quad(q, z)
+
+
 def halfwidth(z: float, extra: int = 16) -> int:
     return int(math.ceil(abs(z) / 2.0)) + int(extra)
 

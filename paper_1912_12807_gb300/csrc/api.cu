@@ -188,11 +188,12 @@ int32_t delay_spread(const int32_t* d, int64_t nb, int32_t ck) {
     return sp;
 }
 
-enum Mode { MODE_SPECTRUM, MODE_PLANE, MODE_SEARCH };
+enum Mode { MODE_SPECTRUM, MODE_PLANE, MODE_SEARCH, MODE_GAINS };
 
 struct Outputs {
     float* spec = nullptr;   // MODE_SPECTRUM: user device buffer
     float* plane = nullptr;  // MODE_PLANE: user device buffer
+    float* gains = nullptr;  // MODE_GAINS: device [trial - dm_begin][blocks]
 };
 
 pss_status check_cfg(const pss_search_cfg* cfg, const Plan& P) {
@@ -303,7 +304,8 @@ pss_status run_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil,
         const int64_t hi = std::min<int64_t>(dm_end, st.first + st.n_dm);
         if (lo >= hi) continue;
         const int64_t nfft = st.nfft, M = nfft / 2;
-        const size_t per_dm = (size_t)nfft * 4 + (size_t)M * 8 * 3 + (mode == MODE_PLANE ? 0 : (size_t)nz * nfft * 4);
+        const size_t per_dm = (size_t)nfft * 4 + (size_t)M * 8 * 3 +
+                              ((mode == MODE_PLANE || mode == MODE_GAINS) ? 0 : (size_t)nz * nfft * 4);
         int64_t B = (int64_t)((size_t)6 << 30) / (int64_t)per_dm;
         B = std::max<int64_t>(1, std::min<int64_t>(B, 1024));
         B = std::min<int64_t>(B, hi - lo);
@@ -312,6 +314,7 @@ pss_status run_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil,
         PSS_TRY(ctx->fftA.ensure((size_t)B * M * 8));
         PSS_TRY(ctx->fftB.ensure((size_t)B * M * 8));
         if (mode != MODE_SPECTRUM) PSS_TRY(ctx->spec.ensure((size_t)B * M * 8));
+        const int64_t lo_first = dm_begin;
         if (mode == MODE_SEARCH) PSS_TRY(ctx->plane.ensure((size_t)B * nz * nfft * 4));
         const double T = (double)(nfft * (int64_t)st.ds) * plan->tsamp;
         HarmArgs ha{};
@@ -357,11 +360,19 @@ pss_status run_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil,
             fa.whiten_block = cfg->whiten_block;
             fa.tw = (const float2*)ctx->twid.p;
             fa.twM = ctx->twid_n;
+            fa.whiten = 1;
+            fa.gains_out = nullptr;
+            fa.gains_stride = 0;
+            if (mode == MODE_GAINS) {
+                fa.gains_out = outs.gains + (b0 - lo_first) * (M / cfg->whiten_block);
+                fa.gains_stride = M / cfg->whiten_block;
+            }
             PSS_CUDA(launch_fft_whiten(fa, s, ctx));
             if (mode == MODE_SPECTRUM) {
                 out_off += (int64_t)nb * M;
                 continue;
             }
+            if (mode == MODE_GAINS) continue;
             PlaneArgs pl;
             pl.spec = spec;
             pl.spec_stride = M;
@@ -485,7 +496,8 @@ void pss_ctx_destroy(pss_ctx* c) {
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     DevBuf* bufs[] = {&c->fil_dev, &c->xcm, &c->delays_dev, &c->series, &c->sums, &c->fftA, &c->fftB,
-                      &c->spec, &c->plane, &c->cands, &c->counter, &c->taps, &c->tapinfo, &c->errflag, &c->twid};
+                      &c->spec, &c->plane, &c->cands, &c->counter, &c->taps, &c->tapinfo, &c->errflag, &c->twid, &c->chan_spec, &c->refine_gains,
+                      &c->refine_dtau, &c->refine_pts, &c->refine_out};
     for (DevBuf* b : bufs) b->release();
     for (auto& r : c->prof_recs) {
         cudaEventDestroy(r.a);
@@ -721,5 +733,208 @@ extern "C" pss_status pss_response(pss_ctx* ctx, const double* q, const double* 
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(d);
     if (e != cudaSuccess) return cuda_fail(e, "pss_response");
+    return PSS_OK;
+}
+
+// ---- candidate refinement --------------------------------------------------
+
+namespace pss {
+namespace {
+
+const double K_DISP_REFINE = 4.148808e3;  // s MHz^2 pc^-1 cm^3
+
+pss_status refine_prepare(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const void* data, int on_dev,
+                          const pss_search_cfg* cfg, int32_t stage, cudaStream_t s) {
+    if (stage < 0 || stage >= (int)plan->stages.size()) return fail(PSS_EINVAL, "pss_refine_prepare: bad stage");
+    const StageInfo& st = plan->stages[stage];
+    const int64_t nfft = st.nfft, M = nfft / 2;
+    // whitening gains of every trial of the stage (also stages the input)
+    const int64_t nblocks = M / cfg->whiten_block;
+    PSS_TRY(ctx->refine_gains.ensure((size_t)st.n_dm * nblocks * sizeof(float)));
+    Outputs o;
+    o.gains = (float*)ctx->refine_gains.p;
+    PSS_TRY(run_path(ctx, plan, fil, data, on_dev, cfg, st.first, st.first + st.n_dm, MODE_GAINS, o, s, 0));
+    // per-channel series (channel-major copy already staged by run_path) and spectra
+    const std::vector<int32_t> keep = kept_channels(fil);
+    const int32_t ck = (int32_t)keep.size();
+    const int TN = dedisp_tile_samples();
+    const int64_t pitch = ((fil->nsamp + TN + 256) + 63) / 64 * 64;
+    PSS_TRY(ctx->series.ensure((size_t)ck * nfft * 4));
+    PSS_TRY(ctx->sums.ensure((size_t)ck * 8));
+    PSS_TRY(ctx->fftA.ensure((size_t)ck * M * 8));
+    PSS_TRY(ctx->fftB.ensure((size_t)ck * M * 8));
+    PSS_TRY(ctx->chan_spec.ensure((size_t)ck * M * 8));
+    PSS_CUDA(cudaMemsetAsync(ctx->sums.p, 0, (size_t)ck * 8, s));
+    PSS_CUDA(launch_chan_series((const uint8_t*)ctx->xcm.p, pitch, ck, st.nv, st.ds, (float*)ctx->series.p, nfft,
+                                (unsigned long long*)ctx->sums.p, s));
+    FftArgs fa;
+    fa.series = (const float*)ctx->series.p;
+    fa.series_stride = nfft;
+    fa.sums = (const unsigned long long*)ctx->sums.p;
+    fa.nv = st.nv;
+    fa.nfft = nfft;
+    fa.nb = ck;
+    fa.bufA = (float2*)ctx->fftA.p;
+    fa.bufB = (float2*)ctx->fftB.p;
+    fa.spec_out = (float2*)ctx->chan_spec.p;
+    fa.spec_stride = M;
+    fa.whiten_block = cfg->whiten_block;
+    fa.tw = (const float2*)ctx->twid.p;
+    fa.twM = ctx->twid_n;
+    fa.whiten = 0;
+    fa.gains_out = nullptr;
+    fa.gains_stride = 0;
+    PSS_CUDA(launch_fft_whiten(fa, s, ctx));
+    // delay per unit DM of each kept channel, relative to the top channel
+    double fmax = -1e300;
+    for (double f : plan->freqs) fmax = std::max(fmax, f);
+    std::vector<double> dt(ck);
+    for (int32_t r = 0; r < ck; ++r) {
+        const double f = plan->freqs[keep[r]];
+        dt[r] = K_DISP_REFINE * (1.0 / (f * f) - 1.0 / (fmax * fmax));
+    }
+    PSS_TRY(ctx->refine_dtau.ensure((size_t)ck * sizeof(double)));
+    PSS_CUDA(cudaMemcpyAsync(ctx->refine_dtau.p, dt.data(), ck * sizeof(double), cudaMemcpyHostToDevice, s));
+    PSS_CUDA(cudaStreamSynchronize(s));
+    ctx->refine_plan = plan;
+    ctx->refine_stage = stage;
+    ctx->refine_ck = ck;
+    ctx->refine_nfft = nfft;
+    ctx->refine_first = st.first;
+    ctx->refine_ntrials = st.n_dm;
+    ctx->refine_nblocks = nblocks;
+    ctx->refine_extra = cfg->halfwidth_extra;
+    ctx->refine_block = cfg->whiten_block;
+    ctx->refine_T = (double)(nfft * (int64_t)st.ds) * plan->tsamp;
+    return PSS_OK;
+}
+
+pss_status refine_eval(pss_ctx* ctx, const pss_plan* plan, const pss_refine_point* pts, int64_t n, double* power,
+                       double* grad, cudaStream_t s) {
+    if (ctx->refine_plan != plan || ctx->refine_stage < 0)
+        return fail(PSS_EINVAL, "pss_refine_eval: call pss_refine_prepare for this plan first");
+    std::vector<RefinePt> hp((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t t = (int64_t)pts[i].dm_idx - ctx->refine_first;
+        if (t < 0 || t >= ctx->refine_ntrials)
+            return fail(PSS_EINVAL, "pss_refine_eval: point outside the prepared stage");
+        if (pts[i].numharm < 1 || pts[i].numharm > 32) return fail(PSS_EINVAL, "pss_refine_eval: bad numharm");
+        if (!(pts[i].r >= 0.0) || !(pts[i].r * pts[i].numharm < ctx->refine_nfft / 2))
+            return fail(PSS_EINVAL, "pss_refine_eval: r outside the spectrum");
+        if ((int)ceil(fabs(pts[i].z * pts[i].numharm) / 2.0) + ctx->refine_extra > refine_max_taps() / 2)
+            return fail(PSS_EINVAL, "pss_refine_eval: |z| too large");
+        hp[(size_t)i] = RefinePt{(int32_t)t, pts[i].numharm, pts[i].dm, pts[i].r, pts[i].z};
+    }
+    if (n == 0) return PSS_OK;
+    PSS_TRY(ctx->refine_pts.ensure((size_t)n * sizeof(RefinePt)));
+    PSS_TRY(ctx->refine_out.ensure((size_t)n * 4 * sizeof(double)));
+    PSS_CUDA(cudaMemcpyAsync(ctx->refine_pts.p, hp.data(), n * sizeof(RefinePt), cudaMemcpyHostToDevice, s));
+    RefineArgs a;
+    a.pts = (const RefinePt*)ctx->refine_pts.p;
+    a.chan_spec = (const float2*)ctx->chan_spec.p;
+    a.dtau = (const double*)ctx->refine_dtau.p;
+    a.gains = (const float*)ctx->refine_gains.p;
+    a.nfft = ctx->refine_nfft;
+    a.ck = ctx->refine_ck;
+    a.extra = ctx->refine_extra;
+    a.whiten_block = ctx->refine_block;
+    a.nblocks = ctx->refine_nblocks;
+    a.T = ctx->refine_T;
+    a.power = (double*)ctx->refine_out.p;
+    a.grad = (double*)ctx->refine_out.p + n;
+    PSS_CUDA(launch_refine_eval(a, n, s));
+    PSS_CUDA(cudaMemcpyAsync(power, a.power, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (grad) PSS_CUDA(cudaMemcpyAsync(grad, a.grad, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    PSS_CUDA(cudaStreamSynchronize(s));
+    return PSS_OK;
+}
+
+}  // namespace
+}  // namespace pss
+
+extern "C" pss_status pss_refine_prepare(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const void* data,
+                                         int data_on_device, const pss_search_cfg* cfg, int32_t stage, void* stream) {
+    PSS_TRY(check_common(ctx, plan, fil, data, 0, 0));
+    PSS_TRY(check_cfg(cfg, *plan));
+    PSS_CUDA(cudaSetDevice(ctx->device));
+    return refine_prepare(ctx, plan, fil, data, data_on_device, cfg, stage, pick_stream(ctx, stream));
+}
+
+extern "C" pss_status pss_refine_eval(pss_ctx* ctx, const pss_plan* plan, const pss_refine_point* pts, int64_t n,
+                                      double* power, double* grad, void* stream) {
+    if (!ctx || !plan || (n > 0 && (!pts || !power)) || n < 0) return fail(PSS_EINVAL, "pss_refine_eval: bad arguments");
+    PSS_CUDA(cudaSetDevice(ctx->device));
+    return refine_eval(ctx, plan, pts, n, power, grad, pick_stream(ctx, stream));
+}
+
+extern "C" pss_status pss_refine_candidates(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil,
+                                            const void* data, int data_on_device, const pss_search_cfg* cfg,
+                                            pss_cand* inout, int64_t n, int32_t iters, double lr, void* stream) {
+    PSS_TRY(check_common(ctx, plan, fil, data, 0, 0));
+    PSS_TRY(check_cfg(cfg, *plan));
+    if (n < 0 || (n > 0 && !inout) || iters < 0 || !(lr > 0)) return fail(PSS_EINVAL, "pss_refine_candidates: bad arguments");
+    PSS_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = pick_stream(ctx, stream);
+    for (int64_t i = 0; i < n; ++i)
+        if (inout[i].dm_idx < 0 || inout[i].dm_idx >= plan->ndm())
+            return fail(PSS_EINVAL, "pss_refine_candidates: dm_idx outside the plan");
+    const double dzc = cfg->zmax ? cfg->dz : 0.0;  // z moves only in an acceleration search
+    for (size_t stg = 0; stg < plan->stages.size(); ++stg) {
+        std::vector<int64_t> idx;
+        for (int64_t i = 0; i < n; ++i)
+            if (plan->stage_of[inout[i].dm_idx] == (int32_t)stg) idx.push_back(i);
+        if (idx.empty()) continue;
+        PSS_TRY(refine_prepare(ctx, plan, fil, data, data_on_device, cfg, (int32_t)stg, s));
+        const double dm_cell = plan->stages[stg].dm_step > 0 ? plan->stages[stg].dm_step : 1.0;
+        const size_t m = idx.size();
+        // Adam on cell-normalised coordinates u = (DM / dm_step, r, z / dz)
+        std::vector<pss_refine_point> cur(m), best(m);
+        std::vector<double> bestP(m, -1.0), P(m), G(3 * m), mom(3 * m, 0.0), vel(3 * m, 0.0);
+        std::vector<double> u0(3 * m);
+        for (size_t q = 0; q < m; ++q) {
+            const pss_cand& c = inout[idx[q]];
+            cur[q] = pss_refine_point{c.dm_idx, c.numharm, c.dm, c.r, c.z};
+            u0[3 * q] = c.dm / dm_cell;
+            u0[3 * q + 1] = c.r;
+            u0[3 * q + 2] = dzc > 0 ? c.z / dzc : 0.0;
+        }
+        const double b1 = 0.9, b2 = 0.999, eps = 1e-12;
+        for (int it = 0; it <= iters; ++it) {
+            PSS_TRY(refine_eval(ctx, plan, cur.data(), (int64_t)m, P.data(), G.data(), s));
+            for (size_t q = 0; q < m; ++q) {
+                if (P[q] > bestP[q]) {
+                    bestP[q] = P[q];
+                    best[q] = cur[q];
+                }
+            }
+            if (it == iters) break;
+            for (size_t q = 0; q < m; ++q) {
+                const double gu[3] = {G[3 * q] * dm_cell, G[3 * q + 1], dzc > 0 ? G[3 * q + 2] * dzc : 0.0};
+                double u[3] = {cur[q].dm / dm_cell, cur[q].r, dzc > 0 ? cur[q].z / dzc : 0.0};
+                for (int d = 0; d < 3; ++d) {
+                    double& mo = mom[3 * q + d];
+                    double& ve = vel[3 * q + d];
+                    mo = b1 * mo + (1 - b1) * gu[d];
+                    ve = b2 * ve + (1 - b2) * gu[d] * gu[d];
+                    const double mh = mo / (1 - pow(b1, it + 1)), vh = ve / (1 - pow(b2, it + 1));
+                    u[d] += lr * mh / (sqrt(vh) + eps);  // ascent
+                    // stay within two cells of the detection
+                    u[d] = std::min(std::max(u[d], u0[3 * q + d] - 2.0), u0[3 * q + d] + 2.0);
+                }
+                cur[q].dm = std::max(0.0, u[0] * dm_cell);
+                cur[q].r = std::max(0.5, u[1]);
+                cur[q].z = dzc > 0 ? u[2] * dzc : 0.0;
+            }
+        }
+        for (size_t q = 0; q < m; ++q) {
+            pss_cand& c = inout[idx[q]];
+            c.dm = best[q].dm;
+            c.r = best[q].r;
+            c.z = best[q].z;
+            c.f_hz = best[q].r / ctx->refine_T;
+            c.power = (float)bestP[q];
+            c.sigma = sigma_of_power(c.numharm, bestP[q]);
+        }
+    }
     return PSS_OK;
 }

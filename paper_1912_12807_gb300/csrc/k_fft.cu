@@ -264,7 +264,8 @@ constexpr int NCAND = 256;
 
 template <int EPT>
 __global__ void __launch_bounds__(256) k_r2c_whiten(const float2* Zall, int64_t z_stride, int64_t M, int W,
-                                                    float2* out, int64_t out_stride, const float2* tw, int64_t twM) {
+                                                    float2* out, int64_t out_stride, const float2* tw, int64_t twM,
+                                                    int whiten, float* gains, int64_t gains_stride) {
     extern __shared__ uint32_t sh[];
     uint32_t* key = sh;              // [W]
     uint32_t* hist = sh + W;         // [NBIN]
@@ -295,6 +296,11 @@ __global__ void __launch_bounds__(256) k_r2c_whiten(const float2* Zall, int64_t 
         A[e] = a;
         const float p = a.x * a.x + a.y * a.y;
         key[threadIdx.x + e * nt] = (k == 0) ? 0xFFFFFFFFu : __float_as_uint(p);
+    }
+    if (!whiten && !gains) {
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) O[k0 + threadIdx.x + (int64_t)e * nt] = A[e];
+        return;
     }
     __syncthreads();
 #pragma unroll
@@ -395,6 +401,9 @@ __global__ void __launch_bounds__(256) k_r2c_whiten(const float2* Zall, int64_t 
     const float med = __uint_as_float(med_bits);
     float scale = 0.f;
     if (med > 0.f) scale = (float)sqrt(0.69314718055994530942 / (double)med);
+    if (gains && threadIdx.x == 0)
+        gains[(int64_t)b * gains_stride + blockIdx.x] = med > 0.f ? (float)(0.69314718055994530942 / (double)med) : 0.f;
+    if (!whiten) scale = 1.f;
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
         const int64_t k = k0 + threadIdx.x + (int64_t)e * nt;
@@ -467,7 +476,8 @@ cudaError_t launch_fft_whiten(const FftArgs& a, cudaStream_t s, Ctx* prof_ctx) {
         cudaError_t e = cudaFuncSetAttribute(k_r2c_whiten<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                              (int)shm);                                                     \
         if (e != cudaSuccess) return e;                                                                     \
-        k_r2c_whiten<E><<<grid, nt, shm, s>>>(in, M, M, W, a.spec_out, a.spec_stride, a.tw, a.twM);         \
+        k_r2c_whiten<E><<<grid, nt, shm, s>>>(in, M, M, W, a.spec_out, a.spec_stride, a.tw, a.twM, a.whiten, \
+                                              a.gains_out, a.gains_stride);                                 \
         break;                                                                                              \
     }
         PSS_WHITEN(1)

@@ -128,6 +128,12 @@ struct Ctx {
     DevBuf errflag;      // int: a kernel's bounded wait expired
     DevBuf twid;         // float2 twiddle table exp(-2 pi i t / twid_n)
     int64_t twid_n = 0;
+    // refinement state (pss_refine_prepare)
+    DevBuf chan_spec, refine_gains, refine_dtau, refine_pts, refine_out;
+    const void* refine_plan = nullptr;
+    int32_t refine_stage = -1, refine_ck = 0, refine_extra = 16, refine_block = 1024;
+    int64_t refine_nfft = 0, refine_first = 0, refine_ntrials = 0, refine_nblocks = 0;
+    double refine_T = 0.0;
     void* host_pinned = nullptr;
     size_t host_pinned_bytes = 0;
     // (zmax, extra, dz) of the templates currently in `taps`
@@ -198,6 +204,9 @@ struct FftArgs {
     int32_t whiten_block;
     const float2* tw;                 // exp(-2 pi i t / twM), t < twM; twM a multiple of nfft
     int64_t twM;
+    int32_t whiten;                   // 0: output the raw half spectrum (DC still zeroed)
+    float* gains_out;                 // nullable [nb][gains_stride]: ln 2 / med_b per block
+    int64_t gains_stride;
 };
 cudaError_t launch_twiddles(float2* tw, int64_t n, cudaStream_t s);
 cudaError_t launch_fft_whiten(const FftArgs& a, cudaStream_t s, Ctx* prof_ctx);
@@ -246,6 +255,30 @@ struct HarmArgs {
     int64_t cap;
 };
 cudaError_t launch_harm(const HarmArgs& a, cudaStream_t s);
+
+struct RefinePt {
+    int32_t trial;    // index into the prepared stage's gains table
+    int32_t numharm;
+    double dm, r, z;
+};
+struct RefineArgs {
+    const RefinePt* pts;
+    const float2* chan_spec;  // [ck][nfft/2] raw per-channel spectra
+    const double* dtau;       // [ck] delay per unit DM, seconds
+    const float* gains;       // [trials][nblocks] ln 2 / median power
+    int64_t nfft;
+    int32_t ck;
+    int32_t extra;
+    int32_t whiten_block;
+    int64_t nblocks;
+    double T;
+    double* power;            // [n]
+    double* grad;             // [n][3]: d/dDM, d/dr, d/dz
+};
+cudaError_t launch_chan_series(const uint8_t* xcm, int64_t pitch, int32_t ck, int64_t nv, int32_t ds, float* out,
+                               int64_t out_stride, unsigned long long* sums, cudaStream_t s);
+cudaError_t launch_refine_eval(const RefineArgs& a, int64_t n, cudaStream_t s);
+int refine_max_taps();
 
 }  // namespace pss
 

@@ -102,20 +102,24 @@ PSS_HD void fresnel_cs(double x, double* C, double* S) {
     *S = s;
 }
 
-// Moments I_n(q) = integral_0^1 u^n e^{2 pi i q u} du, n = 0..6: by the
-// power series of the exponential for |q| < 0.5, else by the upward
-// recurrence I_n = (e^{ia} - n I_{n-1}) / (i a), a = 2 pi q (stable there).
-PSS_HD void moments(double q, cplx* I) {
+// Moments I_n(q) = integral_0^1 u^n e^{2 pi i q u} du, n = 0..NM-1: by the
+// power series of the exponential for |q| < 0.5 (or |q| < NM/4 when more
+// moments are needed), else by the upward recurrence
+// I_n = (e^{ia} - n I_{n-1}) / (i a), a = 2 pi q, whose error grows like
+// n!/a^n and so stays small for a > n.
+template <int NM>
+PSS_HD void moments_n(double q, cplx* I) {
     const double a = 2.0 * M_PI * q;
-    if (fabs(q) < 0.5) {
+    if (fabs(q) < 0.5 || fabs(a) < 1.5 * NM) {
         cplx t = {1.0, 0.0};
-        for (int n = 0; n <= 6; ++n) I[n] = {0.0, 0.0};
-        for (int m = 0; m < 40; ++m) {
-            for (int n = 0; n <= 6; ++n) {
+        for (int n = 0; n < NM; ++n) I[n] = {0.0, 0.0};
+        for (int m = 0; m < 80; ++m) {
+            for (int n = 0; n < NM; ++n) {
                 I[n].re += t.re / (n + m + 1);
                 I[n].im += t.im / (n + m + 1);
             }
             t = c_mul(t, cplx{0.0, a / (m + 1)});
+            if (fabs(t.re) + fabs(t.im) < 1e-18) break;
         }
         return;
     }
@@ -123,8 +127,10 @@ PSS_HD void moments(double q, cplx* I) {
     pss_sincospi(2.0 * q, &sn, &cs);
     const cplx inv_ia = {0.0, -1.0 / a};
     I[0] = c_mul(cplx{cs - 1.0, sn}, inv_ia);
-    for (int n = 1; n <= 6; ++n) I[n] = c_mul(cplx{cs - n * I[n - 1].re, sn - n * I[n - 1].im}, inv_ia);
+    for (int n = 1; n < NM; ++n) I[n] = c_mul(cplx{cs - n * I[n - 1].re, sn - n * I[n - 1].im}, inv_ia);
 }
+
+PSS_HD void moments(double q, cplx* I) { moments_n<7>(q, I); }
 
 PSS_HD cplx rho_resp(double q, double z) {
     if (z == 0.0) {
@@ -167,6 +173,75 @@ PSS_HD cplx rho_resp(double q, double z) {
     double sn, cs;
     pss_sincospi(-(qq * qq) / z, &sn, &cs);
     return c_mul(cplx{cs, sn}, cplx{dC, dS});
+}
+
+// rho(q, z) and its partial derivatives
+//   rho_q = d rho / dq = 2 pi i M1,  rho_z = d rho / dz = pi i (M2 - M1),
+// M_p = integral_0^1 u^p exp(2 pi i [(q - z/2) u + z u^2 / 2]) du.
+// For |z| >= 0.05 the moments follow from rho by integrating by parts
+// (a = q - z/2, e = exp(2 pi i q)):
+//   a rho + z M1 = (e - 1) / (2 pi i),   a M1 + z M2 = (e - rho) / (2 pi i).
+// (below that the division by z loses digits); for smaller |z| everything
+// comes from the Taylor series in z (terms fall as (pi |z| / 4)^n / n!) of
+//   rho = sum_n (i pi z)^n / n! * integral (u^2 - u)^n e^{2 pi i q u} du
+// (n <= 4), whose terms are moments I_p(q) of u^p; (u^2 - u)^n =
+// sum_j C(n,j) (-1)^(n-j) u^(n+j).
+PSS_HD void rho_derivs(double q, double z, cplx* r, cplx* rq, cplx* rz) {
+    if (fabs(z) < 0.05) {
+        cplx I[11];
+        moments_n<11>(q, I);
+        cplx rho = {0, 0}, dq = {0, 0}, dz = {0, 0};
+        cplx c = {1.0, 0.0};  // (i pi z)^n / n!
+        cplx cz = {0.0, 0.0}; // d/dz of (i pi z)^n / n! = (i pi)^n z^(n-1) / (n-1)!
+        double binom[5] = {1, 0, 0, 0, 0};
+        for (int n = 0; n <= 4; ++n) {
+            if (n > 0) {
+                // Pascal row n
+                for (int j = n; j > 0; --j) binom[j] += binom[j - 1];
+            }
+            cplx Mn = {0, 0}, MUn = {0, 0};
+            for (int j = 0; j <= n; ++j) {
+                const double co = ((n - j) & 1 ? -1.0 : 1.0) * binom[j];
+                Mn.re += co * I[n + j].re;
+                Mn.im += co * I[n + j].im;
+                MUn.re += co * I[n + j + 1].re;
+                MUn.im += co * I[n + j + 1].im;
+            }
+            if (n > 0) {
+                // c_n = c_{n-1} * (i pi z) / n ; cz_n = c_{n-1} * (i pi) (since d/dz z^n/n! = z^(n-1)/(n-1)!)
+                const cplx ipi = {0.0, M_PI};
+                cz = c_mul(c, ipi);
+                c = c_mul(c, cplx{0.0, M_PI * z / n});
+            }
+            const cplx t0 = c_mul(c, Mn);
+            rho.re += t0.re;
+            rho.im += t0.im;
+            const cplx t1 = c_mul(c, c_mul(cplx{0.0, 2.0 * M_PI}, MUn));
+            dq.re += t1.re;
+            dq.im += t1.im;
+            if (n > 0) {
+                const cplx t2 = c_mul(cz, Mn);
+                dz.re += t2.re;
+                dz.im += t2.im;
+            }
+        }
+        *r = rho;
+        *rq = dq;
+        *rz = dz;
+        return;
+    }
+    const cplx rho = rho_resp(q, z);
+    double sn, cs;
+    pss_sincospi(2.0 * q, &sn, &cs);
+    const double a = q - 0.5 * z;
+    const cplx inv2pii = {0.0, -1.0 / (2.0 * M_PI)};
+    const cplx t1 = c_mul(cplx{cs - 1.0, sn}, inv2pii);
+    const cplx M1 = {(t1.re - a * rho.re) / z, (t1.im - a * rho.im) / z};
+    const cplx t2 = c_mul(cplx{cs - rho.re, sn - rho.im}, inv2pii);
+    const cplx M2 = {(t2.re - a * M1.re) / z, (t2.im - a * M1.im) / z};
+    *r = rho;
+    *rq = c_mul(cplx{0.0, 2.0 * M_PI}, M1);
+    *rz = c_mul(cplx{0.0, M_PI}, cplx{M2.re - M1.re, M2.im - M1.im});
 }
 
 }  // namespace pss

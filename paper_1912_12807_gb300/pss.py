@@ -45,6 +45,12 @@ class pss_search_cfg(C.Structure):
                 ("min_dm_hits", C.c_int32), ("reserved", C.c_int32)]
 
 
+class pss_refine_point(C.Structure):
+    _fields_ = [("dm_idx", C.c_int32), ("numharm", C.c_int32), ("dm", C.c_double), ("r", C.c_double),
+                ("z", C.c_double)]
+
+
+REFINE_DTYPE = np.dtype([("dm_idx", "<i4"), ("numharm", "<i4"), ("dm", "<f8"), ("r", "<f8"), ("z", "<f8")])
 RAW_DTYPE = np.dtype([("dm_idx", "<i4"), ("numharm", "<i4"), ("h", "<i4"), ("j", "<i4"), ("power", "<f4"),
                       ("reserved", "<i4")])
 CAND_DTYPE = np.dtype([("dm_idx", "<i4"), ("numharm", "<i4"), ("dm", "<f8"), ("r", "<f8"), ("z", "<f8"),
@@ -55,7 +61,8 @@ CAND_DTYPE = np.dtype([("dm_idx", "<i4"), ("numharm", "<i4"), ("dm", "<f8"), ("r
 EXPORTS = ["pss_ctx_create", "pss_ctx_destroy", "pss_last_error", "pss_version", "pss_dd_plan", "pss_plan_info",
            "pss_plan_trial_info", "pss_plan_free", "pss_dedisperse", "pss_spectrum", "pss_power_plane",
            "pss_search_raw", "pss_sift", "pss_search_dm_batch", "pss_response", "pss_sigma_of_power",
-           "pss_power_threshold", "pss_ctx_profile", "pss_ctx_profile_read", "pss_dedisperse_noalloc"]
+           "pss_power_threshold", "pss_ctx_profile", "pss_ctx_profile_read", "pss_dedisperse_noalloc",
+           "pss_refine_prepare", "pss_refine_eval", "pss_refine_candidates"]
 PROFILE_STAGES = ["unpack", "dedisperse", "fft", "whiten", "plane", "harmsum"]
 
 _lib = None
@@ -90,6 +97,10 @@ def lib():
                                      P(i64), vp]),
         "pss_response": (st, [vp, vp, vp, i64, vp]),
         "pss_dedisperse_noalloc": (st, [vp, P(pss_fil_desc), vp, i64, i64, vp, vp]),
+        "pss_refine_prepare": (st, [vp, vp, P(pss_fil_desc), vp, C.c_int, P(pss_search_cfg), i32, vp]),
+        "pss_refine_eval": (st, [vp, vp, vp, i64, vp, vp, vp]),
+        "pss_refine_candidates": (st, [vp, vp, P(pss_fil_desc), vp, C.c_int, P(pss_search_cfg), vp, i64, i32,
+                                       C.c_double, vp]),
         "pss_ctx_profile": (st, [vp, C.c_int]),
         "pss_ctx_profile_read": (st, [vp, vp, vp]),
         "pss_sigma_of_power": (C.c_double, [i32, C.c_double]),
@@ -344,6 +355,61 @@ def pss_search_dm_batch(ctx: Context, plan: Plan, data, cfg: pss_search_cfg, dm_
             continue
         _check(st)
         return out[: n.value]
+
+
+def pss_refine_prepare(ctx: Context, plan: Plan, data, cfg: pss_search_cfg, stage: int, stream=None):
+    p, dev, keep = _data_arg(data)
+    _check(lib().pss_refine_prepare(ctx.h, plan.h, C.byref(plan.desc.c), p, dev, C.byref(cfg), int(stage),
+                                    _stream(stream)))
+
+
+def pss_refine_eval(ctx: Context, plan: Plan, points, stream=None):
+    """(power [n], grad [n][3]) at refinement points (REFINE_DTYPE array)."""
+    pts = np.ascontiguousarray(points, dtype=REFINE_DTYPE)
+    n = pts.shape[0]
+    power = np.zeros(n, dtype=np.float64)
+    grad = np.zeros((n, 3), dtype=np.float64)
+    _check(lib().pss_refine_eval(ctx.h, plan.h, pts.ctypes.data, n, power.ctypes.data, grad.ctypes.data,
+                                 _stream(stream)))
+    return power, grad
+
+
+def pss_refine_candidates(ctx: Context, plan: Plan, data, cfg: pss_search_cfg, cands: np.ndarray, iters: int = 40,
+                          lr: float = 0.05, stream=None) -> np.ndarray:
+    out = np.ascontiguousarray(cands, dtype=CAND_DTYPE).copy()
+    p, dev, keep = _data_arg(data)
+    _check(lib().pss_refine_candidates(ctx.h, plan.h, C.byref(plan.desc.c), p, dev, C.byref(cfg), out.ctypes.data,
+                                       out.shape[0], int(iters), float(lr), _stream(stream)))
+    return out
+
+
+def refine_power_function():
+    """torch.autograd.Function computing P_h(DM, r, z) on the GPU (after
+    pss_refine_prepare) with the library's analytic gradient."""
+    import torch
+
+    class RefinePower(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, dm, r, z, ctx_, plan, dm_idx, numharm):
+            pts = np.zeros(dm.numel(), dtype=REFINE_DTYPE)
+            pts["dm_idx"] = np.asarray(dm_idx).reshape(-1)
+            pts["numharm"] = np.asarray(numharm).reshape(-1)
+            pts["dm"] = dm.detach().cpu().double().numpy().reshape(-1)
+            pts["r"] = r.detach().cpu().double().numpy().reshape(-1)
+            pts["z"] = z.detach().cpu().double().numpy().reshape(-1)
+            power, grad = pss_refine_eval(ctx_, plan, pts)
+            g = torch.from_numpy(grad).to(dm.device)
+            fctx.save_for_backward(g)
+            return torch.from_numpy(power).to(dm.device).reshape(dm.shape)
+
+        @staticmethod
+        def backward(fctx, gp):
+            (g,) = fctx.saved_tensors
+            gp = gp.reshape(-1).double()
+            return ((gp * g[:, 0]).reshape(gp.shape), (gp * g[:, 1]).reshape(gp.shape),
+                    (gp * g[:, 2]).reshape(gp.shape), None, None, None, None)
+
+    return RefinePower
 
 
 def pss_response(ctx: Context, q: Sequence[float], z: Sequence[float]) -> np.ndarray:

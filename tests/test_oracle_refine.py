@@ -1,0 +1,73 @@
+"""Pins for the refinement objective (oracle/refine.py)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import refine as RF
+from oracle import response as R
+from paper_1912_12807_gb300 import synth
+
+
+def _tone_file(nchan, nsamp, r0, amp=40.0, seed=0):
+    # every channel carries the same undispersed tone at r0 bins of the span
+    rng = np.random.default_rng(seed)
+    t = np.arange(nsamp)
+    x = 128 + amp * np.cos(2 * np.pi * r0 * t / nsamp)[:, None] + rng.normal(0, 2.0, (nsamp, nchan))
+    data = np.clip(np.rint(x), 0, 255).astype(np.uint8)
+    fch0, foff = synth.band(1200.0, 1500.0, nchan)
+    return synth.Filterbank(nchan, nsamp, 2e-4, fch0, foff, 8, data, [])
+
+
+def test_rho_closed_form_matches_quadrature():
+    for q in (0.0, 0.5, -2.25, 7.0):
+        assert abs(R.rho(q, 0.0) - R.rho_quad(q, 0.0)) < 1e-13
+    assert R.rho(1.5, 3.0) == R.rho_quad(1.5, 3.0)
+
+
+def test_single_channel_peak_and_zero_gradient_at_tone():
+    # One channel, one undispersed tone at a half-integer bin r0 of the span:
+    # the 2m taps around r0 are symmetric about it, so the objective is
+    # (up to the tone's negative-frequency image and 8-bit rounding) even in
+    # r - r0: its maximum is at r0 and its slope there vanishes.
+    nsamp = 4096
+    r0 = 300.5
+    fil = _tone_file(1, nsamp, r0, amp=60.0, seed=1)
+    fil.data[:] = np.clip(np.rint(128 + 60.0 * np.cos(2 * np.pi * r0 * np.arange(nsamp) / nsamp)),
+                          0, 255).astype(np.uint8)[:, None]
+    cfg = synth.SearchCfg(zmax=0, numharm=1, whiten_block=64)
+    obj = RF.Objective(fil, [synth.Stage(0.0, 1.0, 3, 1)], cfg, dm_idx=0)
+    assert obj.nfft == nsamp and obj.nv == nsamp
+    best = obj.grid_max(0.0, r0, 0.0, 1, 1.0, 0.0)
+    assert abs(best[2] - r0) < 1e-9
+    h = 1e-3
+    g = (obj(0.0, r0 + h, 0.0, 1) - obj(0.0, r0 - h, 0.0, 1)) / (2 * h)
+    d = 0.05
+    curv = (obj(0.0, r0 + d, 0.0, 1) - 2 * obj(0.0, r0, 0.0, 1) + obj(0.0, r0 - d, 0.0, 1)) / d ** 2
+    assert curv < 0
+    assert abs(g) < 1e-2 * abs(curv)
+
+
+def test_integer_bins_reduce_to_phased_channel_sum():
+    # z = 0 and integer k r: the response is a delta, E = 1, so
+    # P_h = sum_k gain * |sum_c exp(i phi_ck) A^c_{kr}|^2
+    wl = synth.workload_small(nsamp=1 << 14)
+    cfg = wl.cfg
+    obj = RF.Objective(wl.fil, [synth.Stage(40.0, 1.0, 21, 1)], cfg, dm_idx=10)
+    dm, r = 50.0, 123.0
+    ref = 0.0
+    for k in range(1, 5):
+        rk = k * r
+        phi = 2 * math.pi * rk * dm * obj.dtau / obj.T
+        F = np.sum(np.exp(1j * phi) * obj.Ac[:, int(rk)])
+        ref += obj.gain[int(rk) // cfg.whiten_block] * abs(F) ** 2
+    assert abs(obj(dm, r, 0.0, 4) - ref) < 1e-9 * ref
+
+
+def test_dispersed_pulsar_prefers_its_dm():
+    wl = synth.workload_small(nsamp=1 << 14)
+    obj = RF.Objective(wl.fil, [synth.Stage(40.0, 1.0, 21, 1)], wl.cfg, dm_idx=10)
+    r = (1 / 0.0333) * obj.T  # fundamental of the injected 33.3 ms pulsar
+    at = max(obj(50.0, r + d, 0.0, 8) for d in np.arange(-1, 1.01, 0.125))
+    off = max(obj(20.0, r + d, 0.0, 8) for d in np.arange(-1, 1.01, 0.125))
+    assert at > 4 * off
