@@ -324,6 +324,59 @@ pss_status pss_refine_candidates(pss_ctx* ctx, const pss_plan* plan, const pss_f
  * Exposes the template arithmetic so that it can be checked directly. */
 pss_status pss_response(pss_ctx* ctx, const double* q, const double* z, int64_t n, double* out);
 
+/* ---- batched search: one graph launch per file (no paper counterpart) --- */
+
+/* A search prepared for files of one shape (descriptor, plan, cfg): its own
+ * context and stream, every device buffer allocated, and the whole kernel
+ * sequence of pss_search_dm_batch over all trials of the plan captured into
+ * one CUDA graph.  The plan and descriptor are copied; `fil->chan_mask` too. */
+typedef struct pss_batch pss_batch;
+pss_status pss_batch_create(int device, const pss_plan* plan, const pss_fil_desc* fil, const pss_search_cfg* cfg,
+                            pss_batch** out);
+/* Search one file of the batch's shape (data: host or device bytes): copy it
+ * in, launch the graph, download the detections, sift on the host.  Same
+ * result as pss_search_dm_batch over all trials.  gpu_ms (nullable): device
+ * time of copy + graph.  Not thread-safe for one batch. */
+pss_status pss_batch_run(pss_batch* b, const void* data, int data_on_device, pss_cand* out, int64_t cap,
+                         int64_t* n_out, double* gpu_ms);
+/* Device bytes held by the batch. */
+size_t pss_batch_footprint(const pss_batch* b);
+/* Device bytes a batch for this shape will hold, computed on the host
+ * without a device (what the server admits files by).  PSS_EINVAL for the
+ * arguments pss_batch_create would reject. */
+pss_status pss_search_footprint(const pss_plan* plan, const pss_fil_desc* fil, const pss_search_cfg* cfg,
+                                size_t* bytes);
+void pss_batch_free(pss_batch* b);
+
+/* ---- serving: continuous batching of files as they arrive --------------- */
+
+/* A request loop on one device (the paper's drift-scan files arrive one per
+ * ~26 s and must each be searched within that budget, Sect. 1).  Up to
+ * max_slots files are in flight at once, each on its own stream and batch
+ * (kernels of different files overlap on the device); a queued file is
+ * admitted when a slot is free and its device footprint fits in what is
+ * left of hbm_budget_bytes (FIFO; a file larger than the whole budget fails
+ * with PSS_ENOMEM).  Slots keep their prepared batch for the next file of
+ * the same shape.  Thread-safe. */
+typedef struct pss_server pss_server;
+typedef struct pss_result pss_result;
+pss_status pss_server_create(int device, size_t hbm_budget_bytes, int max_slots, pss_server** out);
+/* Queue a file (host bytes, copied before return) with its plan stages and
+ * search cfg; *ticket identifies the result. */
+pss_status pss_submit_file(pss_server* srv, const pss_fil_desc* fil, const void* host_data,
+                           const pss_dd_stage* stages, int nstages, const pss_search_cfg* cfg, uint64_t* ticket);
+/* Wait up to timeout_ms for a ticket's result: PSS_ENOTREADY if timeout_ms
+ * is 0 and it is not ready, PSS_ETIMEOUT if the wait expires.  The result is
+ * handed over once (free it with pss_result_free). */
+pss_status pss_poll(pss_server* srv, uint64_t ticket, int timeout_ms, pss_result** out);
+/* The file's outcome (PSS_OK or the error it met), its sifted candidates
+ * (valid until pss_result_free), and submit-to-ready latency in seconds. */
+pss_status pss_result_cands(const pss_result* r, const pss_cand** c, int64_t* n, double* latency_s);
+void pss_result_free(pss_result* r);
+/* Completed files, and the 50th / 99th percentile latency over them (s). */
+pss_status pss_server_stats(pss_server* srv, int64_t* completed, double* p50_s, double* p99_s, size_t* bytes_in_use);
+void pss_server_destroy(pss_server* srv);
+
 /* Significance of a harmonic sum: -Phi^-1(Q(n, S)) with
  * Q(n, S) = exp(-S) sum_{j<n} S^j / j!, and its inverse (the threshold). */
 double pss_sigma_of_power(int32_t numharm, double power);

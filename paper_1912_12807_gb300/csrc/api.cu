@@ -118,18 +118,11 @@ std::vector<int32_t> compact_delays(const pss_plan* plan, const std::vector<int3
     return hd;
 }
 
-// Upload (if needed) and unpack/transpose the file into ctx->xcm; upload
-// the kept channels' delays of [dm_begin, dm_end) into ctx->delays_dev.
-pss_status stage_input(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const void* data,
-                       int on_device, int64_t dm_begin, int64_t dm_end, cudaStream_t s, int32_t* ck_out,
-                       int64_t* pitch_out) {
-    const int64_t nbytes = file_bytes(fil);
-    const uint8_t* src = (const uint8_t*)data;
-    if (!on_device) {
-        PSS_TRY(ctx->fil_dev.ensure((size_t)nbytes));
-        PSS_CUDA(cudaMemcpyAsync(ctx->fil_dev.p, data, (size_t)nbytes, cudaMemcpyHostToDevice, s));
-        src = (const uint8_t*)ctx->fil_dev.p;
-    }
+// Host-side set-up for a file: the kept channels, their delays for
+// [dm_begin, dm_end) uploaded to ctx->delays_dev, and the channel-major
+// buffer.  Synchronises `s` (the delay upload reads a host vector).
+pss_status setup_input(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, int64_t dm_begin,
+                       int64_t dm_end, cudaStream_t s, int32_t* ck_out, int64_t* pitch_out) {
     const std::vector<int32_t> keep = kept_channels(fil);
     const int32_t ck = (int32_t)keep.size();
     if (ck == 0) return fail(PSS_EINVAL, "channel mask removes every channel");
@@ -148,6 +141,27 @@ pss_status stage_input(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* f
         PSS_TRY(ctx->errflag.ensure(sizeof(int)));
         PSS_CUDA(cudaMemsetAsync(ctx->errflag.p, 0, sizeof(int), s));
     }
+    PSS_CUDA(cudaStreamSynchronize(s));
+    *ck_out = ck;
+    *pitch_out = pitch;
+    return PSS_OK;
+}
+
+// Upload a host file into ctx->fil_dev (device data is used in place).
+pss_status upload_input(pss_ctx* ctx, const pss_fil_desc* fil, const void* data, int on_device, cudaStream_t s,
+                        const uint8_t** src) {
+    *src = (const uint8_t*)data;
+    if (on_device) return PSS_OK;
+    const int64_t nbytes = file_bytes(fil);
+    PSS_TRY(ctx->fil_dev.ensure((size_t)nbytes));
+    PSS_CUDA(cudaMemcpyAsync(ctx->fil_dev.p, data, (size_t)nbytes, cudaMemcpyHostToDevice, s));
+    *src = (const uint8_t*)ctx->fil_dev.p;
+    return PSS_OK;
+}
+
+// Unpack/transpose the file into ctx->xcm (kernel launch only).
+pss_status enqueue_prep(pss_ctx* ctx, const pss_fil_desc* fil, const uint8_t* src, int32_t ck, int64_t pitch,
+                        cudaStream_t s) {
     PrepArgs pa;
     pa.src = src;
     pa.nchan = fil->nchan;
@@ -158,15 +172,19 @@ pss_status stage_input(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* f
     pa.ck = ck;
     pa.xcm = (uint8_t*)ctx->xcm.p;
     pa.pitch = pitch;
-    {
-        ProfScope ps(ctx, 0, s);
-        PSS_CUDA(launch_prep(pa, s));
-    }
-    // the host vector must outlive the async copy
-    PSS_CUDA(cudaStreamSynchronize(s));
-    *ck_out = ck;
-    *pitch_out = pitch;
+    ProfScope ps(ctx, 0, s);
+    PSS_CUDA(launch_prep(pa, s));
     return PSS_OK;
+}
+
+// Old entry used by pss_dedisperse: set-up, upload and unpack in one go.
+pss_status stage_input(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const void* data,
+                       int on_device, int64_t dm_begin, int64_t dm_end, cudaStream_t s, int32_t* ck_out,
+                       int64_t* pitch_out) {
+    PSS_TRY(setup_input(ctx, plan, fil, dm_begin, dm_end, s, ck_out, pitch_out));
+    const uint8_t* src = nullptr;
+    PSS_TRY(upload_input(ctx, fil, data, on_device, s, &src));
+    return enqueue_prep(ctx, fil, src, *ck_out, *pitch_out, s);
 }
 
 // max over the dedispersion kernel's groups of consecutive trials and over
@@ -267,27 +285,55 @@ float thr_f32(int n, double sigma) {
     return f;
 }
 
-// Run the path over [dm_begin, dm_end) in batches within each plan stage.
-pss_status run_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const void* data, int on_dev,
-                    const pss_search_cfg* cfg, int64_t dm_begin, int64_t dm_end, Mode mode, Outputs outs,
-                    cudaStream_t s, int64_t dev_cap) {
+// One batch of consecutive trials within a plan stage.
+struct BatchDesc {
+    int32_t stage;
+    int64_t b0;        // first trial
+    int32_t nb;        // trials
+    int32_t spread;    // delay spread the dedispersion launch is sized for
+    int64_t out_off;   // packed output offset (spectrum / plane modes)
+};
+
+// Everything the kernel sequence needs, computed on the host once.
+struct PathSetup {
     int32_t ck = 0;
     int64_t pitch = 0;
-    HostTimer tm;
-    PSS_TRY(stage_input(ctx, plan, fil, data, on_dev, dm_begin, dm_end, s, &ck, &pitch));
-    tm.mark("stage_input");
+    int nz = 1, Z = 0, nstages = 1;
+    std::vector<BatchDesc> batches;
+    std::vector<HarmArgs> harm;  // per stage: thresholds and f_lo cuts
+    int64_t dev_cap = 0;
+};
+
+// Trials per batch for a stage of nfft-point spectra: as many as fit in
+// 6 GiB of per-trial buffers (series, three spectra, and the plane when
+// searching), at most 1024 and at most the n trials there are.
+int64_t batch_trials(int64_t nfft, int nz, Mode mode, int64_t n) {
+    const size_t per_dm = (size_t)nfft * 4 + (size_t)(nfft / 2) * 8 * 3 +
+                          ((mode == MODE_PLANE || mode == MODE_GAINS) ? 0 : (size_t)nz * nfft * 4);
+    int64_t B = (int64_t)((size_t)6 << 30) / (int64_t)per_dm;
+    B = std::max<int64_t>(1, std::min<int64_t>(B, 1024));
+    return std::min<int64_t>(B, n);
+}
+
+// Host set-up of the path over [dm_begin, dm_end): input tables, every
+// device buffer at its final size, templates and twiddles.  After this the
+// kernel sequence (enqueue_path) allocates nothing and never waits on the
+// host, so it can be captured into a CUDA graph.
+pss_status setup_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const pss_search_cfg* cfg,
+                      int64_t dm_begin, int64_t dm_end, Mode mode, cudaStream_t s, int64_t dev_cap, PathSetup* P) {
+    PSS_TRY(setup_input(ctx, plan, fil, dm_begin, dm_end, s, &P->ck, &P->pitch));
+    P->batches.clear();
+    P->harm.clear();
+    P->dev_cap = dev_cap;
     if (dm_end == dm_begin) return PSS_OK;
     PSS_TRY(ensure_templates(ctx, cfg, s));
-    const int nz = nz_of(cfg);
-    const int Z = cfg->zmax ? (int)llround(cfg->zmax / cfg->dz) : 0;
-    const int32_t* dtab = (const int32_t*)ctx->delays_dev.p + ck;
-    // host copy of the compacted delays for the spread computation
+    P->nz = nz_of(cfg);
+    P->Z = cfg->zmax ? (int)llround(cfg->zmax / cfg->dz) : 0;
+    P->nstages = (int)log2((double)cfg->numharm) + 1;
     const std::vector<int32_t> hd = compact_delays(plan, kept_channels(fil), dm_begin, dm_end);
-    const int nstages = (int)log2((double)cfg->numharm) + 1;
     if (mode == MODE_SEARCH) {
         PSS_TRY(ctx->cands.ensure((size_t)dev_cap * sizeof(pss_raw_cand)));
         PSS_TRY(ctx->counter.ensure(sizeof(unsigned long long)));
-        PSS_CUDA(cudaMemsetAsync(ctx->counter.p, 0, sizeof(unsigned long long), s));
     }
     // twiddle table covering every stage's nfft (powers of two: the largest suffices)
     int64_t nfft_max = 0;
@@ -297,123 +343,153 @@ pss_status run_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil,
         PSS_CUDA(launch_twiddles((float2*)ctx->twid.p, nfft_max, s));
         ctx->twid_n = nfft_max;
     }
-    int64_t out_off = 0;  // packed output offset (elements) for spectrum/plane modes
+    size_t need_series = 0, need_fft = 0, need_sums = 0, need_plane = 0;
+    int64_t out_off = 0;
     for (size_t si = 0; si < plan->stages.size(); ++si) {
         const StageInfo& st = plan->stages[si];
         const int64_t lo = std::max<int64_t>(dm_begin, st.first);
         const int64_t hi = std::min<int64_t>(dm_end, st.first + st.n_dm);
-        if (lo >= hi) continue;
-        const int64_t nfft = st.nfft, M = nfft / 2;
-        const size_t per_dm = (size_t)nfft * 4 + (size_t)M * 8 * 3 +
-                              ((mode == MODE_PLANE || mode == MODE_GAINS) ? 0 : (size_t)nz * nfft * 4);
-        int64_t B = (int64_t)((size_t)6 << 30) / (int64_t)per_dm;
-        B = std::max<int64_t>(1, std::min<int64_t>(B, 1024));
-        B = std::min<int64_t>(B, hi - lo);
-        PSS_TRY(ctx->series.ensure((size_t)B * nfft * 4));
-        PSS_TRY(ctx->sums.ensure((size_t)B * 8));
-        PSS_TRY(ctx->fftA.ensure((size_t)B * M * 8));
-        PSS_TRY(ctx->fftB.ensure((size_t)B * M * 8));
-        if (mode != MODE_SPECTRUM) PSS_TRY(ctx->spec.ensure((size_t)B * M * 8));
-        const int64_t lo_first = dm_begin;
-        if (mode == MODE_SEARCH) PSS_TRY(ctx->plane.ensure((size_t)B * nz * nfft * 4));
-        const double T = (double)(nfft * (int64_t)st.ds) * plan->tsamp;
         HarmArgs ha{};
-        for (int k = 0; k < nstages; ++k) {
+        const double T = (double)(st.nfft * (int64_t)st.ds) * plan->tsamp;
+        for (int k = 0; k < P->nstages; ++k) {
             const int n = 1 << k;
             ha.thr[k] = thr_f32(n, cfg->sigma_thr);
             ha.hmin[k] = (int32_t)std::min<double>(ceil((double)(2 * n) * T * cfg->f_lo_hz), 2e9);
         }
+        P->harm.push_back(ha);
+        if (lo >= hi) continue;
+        const int64_t nfft = st.nfft, M = nfft / 2;
+        const int64_t B = batch_trials(nfft, P->nz, mode, hi - lo);
+        need_series = std::max(need_series, (size_t)B * nfft * 4);
+        need_sums = std::max(need_sums, (size_t)B * 8);
+        need_fft = std::max(need_fft, (size_t)B * M * 8);
+        if (mode == MODE_SEARCH) need_plane = std::max(need_plane, (size_t)B * P->nz * nfft * 4);
         for (int64_t b0 = lo; b0 < hi; b0 += B) {
-            const int32_t nb = (int32_t)std::min<int64_t>(B, hi - b0);
-            const int32_t* drow = dtab + (b0 - dm_begin) * ck;
-            DedispArgs da;
-            da.xcm = (const uint8_t*)ctx->xcm.p;
-            da.pitch = pitch;
-            da.ck = ck;
-            da.delays = drow;
-            da.nb = nb;
-            da.nv = st.nv;
-            da.ds = st.ds;
-            da.out_f = (float*)ctx->series.p;
-            da.out_i = nullptr;
-            da.out_stride = nfft;
-            da.sums = (unsigned long long*)ctx->sums.p;
-            da.spread = delay_spread(hd.data() + (size_t)(b0 - dm_begin) * ck, nb, ck);
-            da.err = (int*)ctx->errflag.p;
-            PSS_CUDA(cudaMemsetAsync(ctx->sums.p, 0, (size_t)nb * 8, s));
-            {
-                ProfScope ps(ctx, 1, s);
-                PSS_CUDA(launch_dedisp(da, ctx->num_sms, s));
-            }
-            FftArgs fa;
-            fa.series = (const float*)ctx->series.p;
-            fa.series_stride = nfft;
-            fa.sums = (const unsigned long long*)ctx->sums.p;
-            fa.nv = st.nv;
-            fa.nfft = nfft;
-            fa.nb = nb;
-            fa.bufA = (float2*)ctx->fftA.p;
-            fa.bufB = (float2*)ctx->fftB.p;
-            float2* spec = (mode == MODE_SPECTRUM) ? (float2*)(outs.spec) + out_off : (float2*)ctx->spec.p;
-            fa.spec_out = spec;
-            fa.spec_stride = M;
-            fa.whiten_block = cfg->whiten_block;
-            fa.tw = (const float2*)ctx->twid.p;
-            fa.twM = ctx->twid_n;
-            fa.whiten = 1;
-            fa.gains_out = nullptr;
-            fa.gains_stride = 0;
-            if (mode == MODE_GAINS) {
-                fa.gains_out = outs.gains + (b0 - lo_first) * (M / cfg->whiten_block);
-                fa.gains_stride = M / cfg->whiten_block;
-            }
-            PSS_CUDA(launch_fft_whiten(fa, s, ctx));
-            if (mode == MODE_SPECTRUM) {
-                out_off += (int64_t)nb * M;
-                continue;
-            }
-            if (mode == MODE_GAINS) continue;
-            PlaneArgs pl;
-            pl.spec = spec;
-            pl.spec_stride = M;
-            pl.nfft = nfft;
-            pl.nb = nb;
-            pl.plane = (mode == MODE_PLANE) ? outs.plane + out_off : (float*)ctx->plane.p;
-            pl.plane_stride = (int64_t)nz * nfft;
-            pl.zmax = cfg->zmax;
-            pl.dz = cfg->zmax ? cfg->dz : 1.0;
-            pl.extra = cfg->halfwidth_extra;
-            pl.taps = (const float2*)ctx->taps.p;
-            const int32_t* info = (const int32_t*)ctx->tapinfo.p;
-            pl.tap_off = info;
-            pl.tap_m = info + 2 * nz;
-            pl.tap_scale = (const float*)(info + 3 * nz);
-            {
-                ProfScope ps(ctx, 4, s);
-                PSS_CUDA(launch_plane(pl, s));
-            }
-            if (mode == MODE_PLANE) {
-                out_off += (int64_t)nb * nz * nfft;
-                continue;
-            }
-            ha.plane = pl.plane;
-            ha.plane_stride = pl.plane_stride;
-            ha.nfft = nfft;
-            ha.nz = nz;
-            ha.Z = Z;
-            ha.nb = nb;
-            ha.dm0 = (int32_t)b0;
-            ha.nstages = nstages;
-            ha.out = (pss_raw_cand*)ctx->cands.p;
-            ha.counter = (unsigned long long*)ctx->counter.p;
-            ha.cap = dev_cap;
-            {
-                ProfScope ps(ctx, 5, s);
-                PSS_CUDA(launch_harm(ha, s));
-            }
+            BatchDesc d;
+            d.stage = (int32_t)si;
+            d.b0 = b0;
+            d.nb = (int32_t)std::min<int64_t>(B, hi - b0);
+            d.spread = delay_spread(hd.data() + (size_t)(b0 - dm_begin) * P->ck, d.nb, P->ck);
+            d.out_off = out_off;
+            out_off += (mode == MODE_SPECTRUM) ? (int64_t)d.nb * M : (mode == MODE_PLANE) ? (int64_t)d.nb * P->nz * nfft : 0;
+            P->batches.push_back(d);
+        }
+    }
+    PSS_TRY(ctx->series.ensure(need_series));
+    PSS_TRY(ctx->sums.ensure(need_sums));
+    PSS_TRY(ctx->fftA.ensure(need_fft));
+    PSS_TRY(ctx->fftB.ensure(need_fft));
+    if (mode != MODE_SPECTRUM) PSS_TRY(ctx->spec.ensure(need_fft));
+    if (mode == MODE_SEARCH) PSS_TRY(ctx->plane.ensure(need_plane));
+    return PSS_OK;
+}
+
+// The kernel sequence of the path (no allocation, no host waits): unpack,
+// then per batch dedisperse, FFT + whiten, plane, harmonic sums.
+pss_status enqueue_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const uint8_t* src,
+                        const pss_search_cfg* cfg, int64_t dm_begin, const PathSetup& P, Mode mode, Outputs outs,
+                        cudaStream_t s) {
+    PSS_TRY(enqueue_prep(ctx, fil, src, P.ck, P.pitch, s));
+    if (P.batches.empty()) return PSS_OK;
+    const int32_t* dtab = (const int32_t*)ctx->delays_dev.p + P.ck;
+    if (mode == MODE_SEARCH) PSS_CUDA(cudaMemsetAsync(ctx->counter.p, 0, sizeof(unsigned long long), s));
+    for (const BatchDesc& d : P.batches) {
+        const StageInfo& st = plan->stages[d.stage];
+        const int64_t nfft = st.nfft, M = nfft / 2;
+        DedispArgs da;
+        da.xcm = (const uint8_t*)ctx->xcm.p;
+        da.pitch = P.pitch;
+        da.ck = P.ck;
+        da.delays = dtab + (d.b0 - dm_begin) * P.ck;
+        da.nb = d.nb;
+        da.nv = st.nv;
+        da.ds = st.ds;
+        da.out_f = (float*)ctx->series.p;
+        da.out_i = nullptr;
+        da.out_stride = nfft;
+        da.sums = (unsigned long long*)ctx->sums.p;
+        da.spread = d.spread;
+        da.err = (int*)ctx->errflag.p;
+        PSS_CUDA(cudaMemsetAsync(ctx->sums.p, 0, (size_t)d.nb * 8, s));
+        {
+            ProfScope ps(ctx, 1, s);
+            PSS_CUDA(launch_dedisp(da, ctx->num_sms, s));
+        }
+        FftArgs fa;
+        fa.series = (const float*)ctx->series.p;
+        fa.series_stride = nfft;
+        fa.sums = (const unsigned long long*)ctx->sums.p;
+        fa.nv = st.nv;
+        fa.nfft = nfft;
+        fa.nb = d.nb;
+        fa.bufA = (float2*)ctx->fftA.p;
+        fa.bufB = (float2*)ctx->fftB.p;
+        float2* spec = (mode == MODE_SPECTRUM) ? (float2*)(outs.spec) + d.out_off : (float2*)ctx->spec.p;
+        fa.spec_out = spec;
+        fa.spec_stride = M;
+        fa.whiten_block = cfg->whiten_block;
+        fa.tw = (const float2*)ctx->twid.p;
+        fa.twM = ctx->twid_n;
+        fa.whiten = 1;
+        fa.gains_out = nullptr;
+        fa.gains_stride = 0;
+        if (mode == MODE_GAINS) {
+            fa.gains_out = outs.gains + (d.b0 - dm_begin) * (M / cfg->whiten_block);
+            fa.gains_stride = M / cfg->whiten_block;
+        }
+        PSS_CUDA(launch_fft_whiten(fa, s, ctx));
+        if (mode == MODE_SPECTRUM || mode == MODE_GAINS) continue;
+        PlaneArgs pl;
+        pl.spec = spec;
+        pl.spec_stride = M;
+        pl.nfft = nfft;
+        pl.nb = d.nb;
+        pl.plane = (mode == MODE_PLANE) ? outs.plane + d.out_off : (float*)ctx->plane.p;
+        pl.plane_stride = (int64_t)P.nz * nfft;
+        pl.zmax = cfg->zmax;
+        pl.dz = cfg->zmax ? cfg->dz : 1.0;
+        pl.extra = cfg->halfwidth_extra;
+        pl.taps = (const float2*)ctx->taps.p;
+        const int32_t* info = (const int32_t*)ctx->tapinfo.p;
+        pl.tap_off = info;
+        pl.tap_m = info + 2 * P.nz;
+        pl.tap_scale = (const float*)(info + 3 * P.nz);
+        {
+            ProfScope ps(ctx, 4, s);
+            PSS_CUDA(launch_plane(pl, s));
+        }
+        if (mode == MODE_PLANE) continue;
+        HarmArgs ha = P.harm[d.stage];
+        ha.plane = pl.plane;
+        ha.plane_stride = pl.plane_stride;
+        ha.nfft = nfft;
+        ha.nz = P.nz;
+        ha.Z = P.Z;
+        ha.nb = d.nb;
+        ha.dm0 = (int32_t)d.b0;
+        ha.nstages = P.nstages;
+        ha.out = (pss_raw_cand*)ctx->cands.p;
+        ha.counter = (unsigned long long*)ctx->counter.p;
+        ha.cap = P.dev_cap;
+        {
+            ProfScope ps(ctx, 5, s);
+            PSS_CUDA(launch_harm(ha, s));
         }
     }
     return PSS_OK;
+}
+
+// Run the path over [dm_begin, dm_end) in batches within each plan stage.
+pss_status run_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const void* data, int on_dev,
+                    const pss_search_cfg* cfg, int64_t dm_begin, int64_t dm_end, Mode mode, Outputs outs,
+                    cudaStream_t s, int64_t dev_cap) {
+    HostTimer tm;
+    PathSetup P;
+    PSS_TRY(setup_path(ctx, plan, fil, cfg, dm_begin, dm_end, mode, s, dev_cap, &P));
+    const uint8_t* src = nullptr;
+    PSS_TRY(upload_input(ctx, fil, data, on_dev, s, &src));
+    tm.mark("setup");
+    return enqueue_path(ctx, plan, fil, src, cfg, dm_begin, P, mode, outs, s);
 }
 
 // A kernel's bounded wait expired since the flag was last cleared: report it
@@ -937,4 +1013,217 @@ extern "C" pss_status pss_refine_candidates(pss_ctx* ctx, const pss_plan* plan, 
         }
     }
     return PSS_OK;
+}
+
+// ---- prepared, graph-captured search of one file shape ---------------------
+
+struct pss_batch {
+    pss_ctx* ctx = nullptr;
+    pss::Plan plan;
+    pss_fil_desc fil{};
+    std::vector<uint8_t> mask;
+    pss_search_cfg cfg{};
+    pss::PathSetup P;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    size_t footprint = 0;
+};
+
+namespace pss {
+namespace {
+
+size_t ctx_bytes(const pss_ctx* c) {
+    const DevBuf* bufs[] = {&c->fil_dev, &c->xcm, &c->delays_dev, &c->series, &c->sums, &c->fftA, &c->fftB,
+                            &c->spec, &c->plane, &c->cands, &c->counter, &c->taps, &c->tapinfo, &c->errflag,
+                            &c->twid};
+    size_t t = 0;
+    for (const DevBuf* b : bufs) t += b->bytes;
+    return t;
+}
+
+void batch_release_graph(pss_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+// (Re)build the set-up for the full DM range with candidate capacity `cap`
+// and capture the kernel sequence into a graph (input: ctx->fil_dev).
+pss_status batch_build(pss_batch* b, int64_t cap) {
+    pss_ctx* ctx = b->ctx;
+    cudaStream_t s = ctx->stream;
+    batch_release_graph(b);
+    PSS_TRY(setup_path(ctx, static_cast<const pss_plan*>(&b->plan), &b->fil, &b->cfg, 0, b->plan.ndm(), MODE_SEARCH,
+                       s, cap, &b->P));
+    PSS_TRY(ctx->fil_dev.ensure((size_t)file_bytes(&b->fil)));
+    // one eager pass sets every kernel attribute before capture
+    PSS_TRY(enqueue_path(ctx, static_cast<const pss_plan*>(&b->plan), &b->fil, (const uint8_t*)ctx->fil_dev.p,
+                         &b->cfg, 0, b->P, MODE_SEARCH, Outputs(), s));
+    PSS_CUDA(cudaStreamSynchronize(s));
+    // relaxed: the launchers call cudaFuncSetAttribute, which is not a stream operation
+    PSS_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    pss_status st = enqueue_path(ctx, static_cast<const pss_plan*>(&b->plan), &b->fil, (const uint8_t*)ctx->fil_dev.p,
+                                 &b->cfg, 0, b->P, MODE_SEARCH, Outputs(), s);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (st != PSS_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    b->graph = g;
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (e != cudaSuccess) {
+        batch_release_graph(b);
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    b->footprint = ctx_bytes(ctx);
+    return PSS_OK;
+}
+
+}  // namespace
+}  // namespace pss
+
+extern "C" pss_status pss_batch_create(int device, const pss_plan* plan, const pss_fil_desc* fil,
+                                       const pss_search_cfg* cfg, pss_batch** out) {
+    if (!out || !plan || !fil || !cfg) return fail(PSS_EINVAL, "pss_batch_create: null argument");
+    *out = nullptr;
+    PSS_TRY(check_common(reinterpret_cast<pss_ctx*>(1), plan, fil, fil, 0, 0));
+    PSS_TRY(check_cfg(cfg, *plan));
+    pss_batch* b = new pss_batch();
+    pss_status st = pss_ctx_create(device, &b->ctx);
+    if (st != PSS_OK) {
+        delete b;
+        return st;
+    }
+    b->plan = *plan;
+    b->fil = *fil;
+    if (fil->chan_mask) {
+        b->mask.assign(fil->chan_mask, fil->chan_mask + fil->nchan);
+        b->fil.chan_mask = b->mask.data();
+    }
+    b->cfg = *cfg;
+    st = batch_build(b, kBatchInitialCap);
+    if (st != PSS_OK) {
+        const std::string msg = pss_last_error();
+        pss_batch_free(b);
+        return fail(st, msg);
+    }
+    *out = b;
+    return PSS_OK;
+}
+
+namespace pss {
+
+// Device bytes a pss_batch of this shape will hold (the DevBuf sizes
+// setup_path and the templates ask for, with DevBuf's slack), computed on
+// the host without touching the device: the server admits files by it.
+pss_status validate_search(const pss_plan* plan, const pss_fil_desc* fil, const pss_search_cfg* cfg) {
+    PSS_TRY(check_common(reinterpret_cast<pss_ctx*>(1), plan, fil, fil, 0, 0));
+    return check_cfg(cfg, *plan);
+}
+
+size_t search_footprint(const Plan& plan, const pss_fil_desc* fil, const pss_search_cfg* cfg, int64_t dev_cap) {
+    auto buf = [](size_t want) { return want ? want + want / 8 + 256 : (size_t)0; };
+    const std::vector<int32_t> keep = kept_channels(fil);
+    const int64_t ck = (int64_t)keep.size();
+    const int64_t pitch = ((fil->nsamp + dedisp_tile_samples() + 256) + 63) / 64 * 64;
+    const int nz = nz_of(cfg);
+    size_t t = buf((size_t)file_bytes(fil)) + buf((size_t)ck * pitch + 64) +
+               buf((size_t)(ck + plan.ndm() * ck) * sizeof(int32_t)) + buf(sizeof(int)) +
+               buf((size_t)dev_cap * sizeof(pss_raw_cand)) + buf(sizeof(unsigned long long));
+    int64_t nfft_max = 0, total_taps = 0;
+    size_t need_series = 0, need_fft = 0, need_sums = 0, need_plane = 0;
+    for (const auto& st : plan.stages) {
+        nfft_max = std::max<int64_t>(nfft_max, st.nfft);
+        if (st.n_dm <= 0) continue;
+        const int64_t B = batch_trials(st.nfft, nz, MODE_SEARCH, st.n_dm);
+        need_series = std::max(need_series, (size_t)B * st.nfft * 4);
+        need_sums = std::max(need_sums, (size_t)B * 8);
+        need_fft = std::max(need_fft, (size_t)B * (st.nfft / 2) * 8);
+        need_plane = std::max(need_plane, (size_t)B * nz * st.nfft * 4);
+    }
+    for (int j = 0; j < nz; ++j) {
+        const double z = cfg->zmax ? -(double)cfg->zmax + (double)j * cfg->dz : 0.0;
+        total_taps += 4 * ((int64_t)ceil(fabs(z) / 2.0) + cfg->halfwidth_extra);
+    }
+    t += buf((size_t)nfft_max * sizeof(float2)) + buf(need_series) + buf(need_sums) + 3 * buf(need_fft) +
+         buf(need_plane) + buf((size_t)total_taps * sizeof(float2)) + buf((size_t)5 * nz * sizeof(int32_t));
+    return t;
+}
+
+}  // namespace pss
+
+extern "C" pss_status pss_search_footprint(const pss_plan* plan, const pss_fil_desc* fil, const pss_search_cfg* cfg,
+                                           size_t* bytes) {
+    if (!bytes) return fail(PSS_EINVAL, "pss_search_footprint: null argument");
+    PSS_TRY(validate_search(plan, fil, cfg));
+    *bytes = search_footprint(*plan, fil, cfg, kBatchInitialCap);
+    return PSS_OK;
+}
+
+extern "C" size_t pss_batch_footprint(const pss_batch* b) { return b ? b->footprint : 0; }
+
+extern "C" pss_status pss_batch_run(pss_batch* b, const void* data, int data_on_device, pss_cand* out, int64_t cap,
+                                    int64_t* n_out, double* gpu_ms) {
+    if (!b || !data || !n_out) return fail(PSS_EINVAL, "pss_batch_run: null argument");
+    *n_out = 0;
+    pss_ctx* ctx = b->ctx;
+    PSS_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    const size_t nbytes = (size_t)file_bytes(&b->fil);
+    std::vector<pss_raw_cand> raw;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (gpu_ms) {
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            cudaEventRecord(e0, s);
+        }
+        PSS_CUDA(cudaMemcpyAsync(ctx->fil_dev.p, data, nbytes,
+                                 data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        PSS_CUDA(cudaGraphLaunch(b->exec, s));
+        unsigned long long cnt = 0;
+        PSS_CUDA(cudaMemcpyAsync(&cnt, ctx->counter.p, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+        if (gpu_ms) cudaEventRecord(e1, s);
+        PSS_CUDA(cudaStreamSynchronize(s));
+        if (gpu_ms) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            *gpu_ms = ms;
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+        }
+        PSS_TRY(check_errflag(ctx, s));
+        if ((int64_t)cnt <= b->P.dev_cap) {
+            raw.resize(cnt);
+            if (cnt)
+                PSS_CUDA(cudaMemcpyAsync(raw.data(), ctx->cands.p, cnt * sizeof(pss_raw_cand), cudaMemcpyDeviceToHost, s));
+            PSS_CUDA(cudaStreamSynchronize(s));
+            break;
+        }
+        // the candidate buffer overflowed: rebuild with room for all of them and redo
+        PSS_TRY(batch_build(b, (int64_t)cnt + 1024));
+        if (attempt == 1) return fail(PSS_ECAP, "pss_batch_run: candidate buffer overflow persisted after resizing");
+    }
+    std::vector<pss_cand> v;
+    PSS_TRY(sift(b->plan, b->cfg, raw.data(), (int64_t)raw.size(), &v));
+    *n_out = (int64_t)v.size();
+    if ((int64_t)v.size() > cap) return fail(PSS_ECAP, "pss_batch_run: output capacity too small");
+    if (!v.empty()) {
+        if (!out) return fail(PSS_EINVAL, "pss_batch_run: null out");
+        memcpy(out, v.data(), v.size() * sizeof(pss_cand));
+    }
+    return PSS_OK;
+}
+
+extern "C" void pss_batch_free(pss_batch* b) {
+    if (!b) return;
+    if (b->ctx) {
+        cudaSetDevice(b->ctx->device);
+        batch_release_graph(b);
+        pss_ctx_destroy(b->ctx);
+    }
+    delete b;
 }

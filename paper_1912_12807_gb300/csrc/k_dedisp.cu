@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(NT) k_dedisp(DedispArgs a, int RW, int CC, uin
 
 template <bool I, bool W>
 cudaError_t launch_t(const DedispArgs& a, dim3 grid, size_t shm, int RW, int CC, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(k_dedisp<I, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    cudaError_t e = allow_smem((const void*)k_dedisp<I, W>, shm);
     if (e != cudaSuccess) return e;
     k_dedisp<I, W><<<grid, NT, shm, s>>>(a, RW, CC, 1u);
     return cudaGetLastError();

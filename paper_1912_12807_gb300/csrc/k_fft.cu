@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(NT) k_fft_pass(const __grid_constant__ PassArg
 template <int R>
 cudaError_t run_pass(const PassArgs& p, int nb, cudaStream_t s) {
     const size_t shm = (size_t)(R * TJP + R) * sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(k_fft_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    cudaError_t e = allow_smem((const void*)k_fft_pass<R>, shm);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((p.M / R + TJ - 1) / TJ), (unsigned)nb);
     k_fft_pass<R><<<grid, NT, shm, s>>>(p);
@@ -473,8 +473,7 @@ cudaError_t launch_fft_whiten(const FftArgs& a, cudaStream_t s, Ctx* prof_ctx) {
     switch (W / nt) {
 #define PSS_WHITEN(E)                                                                                       \
     case E: {                                                                                               \
-        cudaError_t e = cudaFuncSetAttribute(k_r2c_whiten<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                             (int)shm);                                                     \
+        cudaError_t e = allow_smem((const void*)k_r2c_whiten<E>, shm);                               \
         if (e != cudaSuccess) return e;                                                                     \
         k_r2c_whiten<E><<<grid, nt, shm, s>>>(in, M, M, W, a.spec_out, a.spec_stride, a.tw, a.twM, a.whiten, \
                                               a.gains_out, a.gains_stride);                                 \

@@ -122,7 +122,10 @@ cudaError_t launch_plane(const PlaneArgs& a, cudaStream_t s) {
     const int nz = a.zmax ? (int)llround(2.0 * a.zmax / a.dz) + 1 : 1;
     const int mmax = (int)ceil(a.zmax / 2.0) + a.extra;
     const size_t shm = (size_t)(KB + 2 * mmax - 1 + 4 * mmax) * sizeof(float2);
-    cudaFuncSetAttribute(k_plane, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    {
+        cudaError_t e = allow_smem((const void*)k_plane, shm);
+        if (e != cudaSuccess) return e;
+    }
     dim3 grid((unsigned)((M + KB - 1) / KB), (unsigned)nz, (unsigned)a.nb);
     k_plane<<<grid, NT, shm, s>>>(a);
     return cudaGetLastError();

@@ -171,6 +171,23 @@ struct PrepArgs {
 };
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
 
+// Let kernel `fn` launch with as much dynamic shared memory as the device
+// allows next to its static shared memory (error if `shm` exceeds that).
+// Always setting the one maximum, not the launch's own size, keeps
+// concurrent host threads that launch the same kernel with different sizes
+// from undoing each other's setting.
+inline cudaError_t allow_smem(const void* fn, size_t shm) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    const size_t room = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+    if (shm > room) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)room);
+}
+
 struct DedispArgs {
     const uint8_t* xcm;
     int64_t pitch;
@@ -284,3 +301,13 @@ int refine_max_taps();
 
 struct pss_ctx : public pss::Ctx {};
 struct pss_plan : public pss::Plan {};
+
+namespace pss {
+// Raw-detection capacity a pss_batch starts with (it grows on overflow).
+constexpr int64_t kBatchInitialCap = (int64_t)1 << 18;
+// Argument checks of a whole-file search (pss_batch_create's).
+pss_status validate_search(const pss_plan* plan, const pss_fil_desc* fil, const pss_search_cfg* cfg);
+// Device bytes a pss_batch for this shape holds with room for dev_cap raw
+// detections; host arithmetic only.
+size_t search_footprint(const Plan& plan, const pss_fil_desc* fil, const pss_search_cfg* cfg, int64_t dev_cap);
+}  // namespace pss

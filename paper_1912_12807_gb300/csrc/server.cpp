@@ -1,0 +1,332 @@
+// Serving: continuous batching of filterbank files on one device.
+//
+// The paper processes a drift-scan survey whose files arrive every ~26 s and
+// must each be searched within that time (Sect. 1); on CPUs it keeps up by
+// running up to a "parallel number" of PRESTO processes at once and starting
+// a new one as soon as a slot frees (its V3 scheme, Sect. 2).  Here each of
+// max_slots worker threads owns a slot: a prepared, graph-captured search
+// (pss_batch) on its own stream.  A queued file is admitted, in arrival
+// order, as soon as a slot is idle and the file's device footprint fits in
+// what is left of the budget; the kernels of the files in flight overlap on
+// the GPU and each slot sifts its file on the host while the others compute.
+// A slot keeps its batch for the next file of the same shape; an idle slot
+// drops its batch when the file at the head of the queue needs the memory.
+#include <math.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <sstream>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "pss_internal.h"
+
+struct pss_result {
+    pss_status status = PSS_OK;
+    std::string err;
+    std::vector<pss_cand> cands;
+    double latency_s = 0.0;
+};
+
+namespace pss {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    uint64_t ticket = 0;
+    std::vector<uint8_t> data;
+    pss_fil_desc fil{};
+    std::vector<uint8_t> mask;
+    std::vector<pss_dd_stage> stages;
+    pss_search_cfg cfg{};
+    pss_plan* plan = nullptr;
+    size_t estimate = 0;
+    std::string key;
+    Clock::time_point t_submit;
+    ~Request() {
+        if (plan) pss_plan_free(plan);
+    }
+};
+
+std::string shape_key(const pss_fil_desc& f, const std::vector<uint8_t>& mask, const std::vector<pss_dd_stage>& st,
+                      const pss_search_cfg& c) {
+    std::ostringstream o;
+    o.precision(17);
+    o << f.nchan << '/' << f.nbits << '/' << f.nsamp << '/' << f.tsamp_s << '/' << f.fch0_mhz << '/' << f.foff_mhz
+      << '/' << f.layout << '|';
+    for (uint8_t m : mask) o << (m ? '1' : '0');
+    o << '|';
+    for (const auto& s : st) o << s.dm_lo << ',' << s.dm_step << ',' << s.n_dm << ',' << s.ds << ';';
+    o << '|' << c.zmax << ',' << c.numharm << ',' << c.dz << ',' << c.sigma_thr << ',' << c.f_lo_hz << ','
+      << c.whiten_block << ',' << c.halfwidth_extra << ',' << c.min_dm_hits;
+    return o.str();
+}
+
+struct Slot {
+    pss_batch* batch = nullptr;
+    std::string key;
+    size_t held = 0;  // bytes accounted to this slot's batch
+};
+
+}  // namespace
+}  // namespace pss
+
+using namespace pss;
+
+struct pss_server {
+    int device = 0;
+    size_t budget = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request*> queue;
+    std::unordered_map<uint64_t, pss_result*> done;
+    std::unordered_map<uint64_t, bool> known;  // submitted and not yet handed out
+    uint64_t next_ticket = 1;
+    size_t in_use = 0;
+    bool stop = false;
+    std::vector<Slot> slots;
+    std::vector<std::thread> workers;
+    std::vector<double> latencies;
+
+    void finish(Request* r, pss_result* res) {
+        res->latency_s = std::chrono::duration<double>(Clock::now() - r->t_submit).count();
+        std::lock_guard<std::mutex> lk(mu);
+        done[r->ticket] = res;
+        latencies.push_back(res->latency_s);
+        cv_done.notify_all();
+        cv_work.notify_all();
+    }
+
+    void worker(int si) {
+        Slot& slot = slots[si];
+        cudaSetDevice(device);
+        std::unique_lock<std::mutex> lk(mu);
+        for (;;) {
+            Request* r = nullptr;
+            while (!stop) {
+                if (!queue.empty()) {
+                    Request* h = queue.front();
+                    if (h->estimate > budget) {
+                        queue.pop_front();
+                        lk.unlock();
+                        pss_result* res = new pss_result();
+                        res->status = PSS_ENOMEM;
+                        res->err = "file needs more device memory than the server budget";
+                        finish(h, res);
+                        delete h;
+                        lk.lock();
+                        continue;
+                    }
+                    const bool same = slot.batch && slot.key == h->key;
+                    const size_t after = same ? in_use : in_use - slot.held + h->estimate;
+                    if (after <= budget) {
+                        queue.pop_front();
+                        in_use = after;
+                        if (!same) slot.held = h->estimate;
+                        r = h;
+                        break;
+                    }
+                    if (slot.batch && !same) {
+                        // make room: drop this idle slot's prepared batch
+                        pss_batch* old = slot.batch;
+                        slot.batch = nullptr;
+                        slot.key.clear();
+                        in_use -= slot.held;
+                        slot.held = 0;
+                        lk.unlock();
+                        pss_batch_free(old);
+                        lk.lock();
+                        cv_work.notify_all();
+                        continue;
+                    }
+                }
+                cv_work.wait(lk);
+            }
+            if (!r) return;  // stopping
+            lk.unlock();
+            pss_result* res = new pss_result();
+            try {
+                if (!slot.batch || slot.key != r->key) {
+                    if (slot.batch) pss_batch_free(slot.batch);
+                    slot.batch = nullptr;
+                    slot.key.clear();
+                    pss_status st = pss_batch_create(device, r->plan, &r->fil, &r->cfg, &slot.batch);
+                    if (st != PSS_OK) {
+                        res->status = st;
+                        res->err = pss_last_error();
+                    } else {
+                        slot.key = r->key;
+                        const size_t actual = pss_batch_footprint(slot.batch);
+                        std::lock_guard<std::mutex> g(mu);
+                        in_use = in_use - slot.held + actual;
+                        slot.held = actual;
+                    }
+                }
+                if (res->status == PSS_OK) {
+                    int64_t n = 0;
+                    std::vector<pss_cand> buf(1024);
+                    pss_status st = pss_batch_run(slot.batch, r->data.data(), 0, buf.data(), (int64_t)buf.size(), &n,
+                                                  nullptr);
+                    if (st == PSS_ECAP) {
+                        buf.resize((size_t)n);
+                        st = pss_batch_run(slot.batch, r->data.data(), 0, buf.data(), (int64_t)buf.size(), &n, nullptr);
+                    }
+                    if (st != PSS_OK) {
+                        res->status = st;
+                        res->err = pss_last_error();
+                    } else {
+                        buf.resize((size_t)n);
+                        res->cands.swap(buf);
+                    }
+                }
+            } catch (const std::bad_alloc&) {
+                res->status = PSS_ENOMEM;
+                res->err = "host allocation failed";
+            }
+            if (res->status != PSS_OK && slot.batch) {
+                // a failed batch is not reused
+                pss_batch_free(slot.batch);
+                slot.batch = nullptr;
+                slot.key.clear();
+                std::lock_guard<std::mutex> g(mu);
+                in_use -= slot.held;
+                slot.held = 0;
+            } else if (res->status != PSS_OK) {
+                std::lock_guard<std::mutex> g(mu);
+                in_use -= slot.held;
+                slot.held = 0;
+            }
+            finish(r, res);
+            delete r;
+            lk.lock();
+        }
+    }
+};
+
+extern "C" pss_status pss_server_create(int device, size_t hbm_budget_bytes, int max_slots, pss_server** out) {
+    if (!out || max_slots < 1 || max_slots > 64 || hbm_budget_bytes == 0)
+        return fail(PSS_EINVAL, "pss_server_create: bad arguments");
+    *out = nullptr;
+    int n = 0;
+    PSS_CUDA(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return fail(PSS_EINVAL, "pss_server_create: no such device");
+    pss_server* s = new pss_server();
+    s->device = device;
+    s->budget = hbm_budget_bytes;
+    s->slots.resize((size_t)max_slots);
+    for (int i = 0; i < max_slots; ++i) s->workers.emplace_back([s, i] { s->worker(i); });
+    *out = s;
+    return PSS_OK;
+}
+
+extern "C" pss_status pss_submit_file(pss_server* srv, const pss_fil_desc* fil, const void* host_data,
+                                      const pss_dd_stage* stages, int nstages, const pss_search_cfg* cfg,
+                                      uint64_t* ticket) {
+    if (!srv || !fil || !host_data || !stages || nstages <= 0 || !cfg || !ticket)
+        return fail(PSS_EINVAL, "pss_submit_file: null argument");
+    Request* r = new Request();
+    r->fil = *fil;
+    if (fil->chan_mask) {
+        r->mask.assign(fil->chan_mask, fil->chan_mask + fil->nchan);
+        r->fil.chan_mask = r->mask.data();
+    }
+    r->stages.assign(stages, stages + nstages);
+    r->cfg = *cfg;
+    pss_status st = pss_dd_plan(&r->fil, r->stages.data(), nstages, &r->plan);
+    if (st != PSS_OK) {
+        delete r;
+        return st;
+    }
+    st = validate_search(r->plan, &r->fil, &r->cfg);
+    if (st != PSS_OK) {
+        delete r;
+        return st;
+    }
+    r->estimate = search_footprint(*r->plan, &r->fil, &r->cfg, kBatchInitialCap);
+    const size_t nbytes = fil->nbits == 8 ? (size_t)fil->nchan * fil->nsamp : (size_t)(fil->nchan / 8) * fil->nsamp;
+    try {
+        r->data.assign((const uint8_t*)host_data, (const uint8_t*)host_data + nbytes);
+    } catch (const std::bad_alloc&) {
+        delete r;
+        return fail(PSS_ENOMEM, "pss_submit_file: cannot copy the file");
+    }
+    r->key = shape_key(r->fil, r->mask, r->stages, r->cfg);
+    r->t_submit = Clock::now();
+    std::lock_guard<std::mutex> lk(srv->mu);
+    r->ticket = srv->next_ticket++;
+    *ticket = r->ticket;
+    srv->known[r->ticket] = true;
+    srv->queue.push_back(r);
+    srv->cv_work.notify_all();
+    return PSS_OK;
+}
+
+extern "C" pss_status pss_poll(pss_server* srv, uint64_t ticket, int timeout_ms, pss_result** out) {
+    if (!srv || !out) return fail(PSS_EINVAL, "pss_poll: null argument");
+    *out = nullptr;
+    std::unique_lock<std::mutex> lk(srv->mu);
+    if (!srv->known.count(ticket)) return fail(PSS_EINVAL, "pss_poll: unknown ticket (or already handed out)");
+    auto ready = [&] { return srv->done.count(ticket) > 0; };
+    if (!ready()) {
+        if (timeout_ms == 0) return fail(PSS_ENOTREADY, "pss_poll: not ready");
+        if (timeout_ms < 0) srv->cv_done.wait(lk, ready);
+        else if (!srv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
+            return fail(PSS_ETIMEOUT, "pss_poll: wait expired");
+    }
+    *out = srv->done[ticket];
+    srv->done.erase(ticket);
+    srv->known.erase(ticket);
+    return PSS_OK;
+}
+
+extern "C" pss_status pss_result_cands(const pss_result* r, const pss_cand** c, int64_t* n, double* latency_s) {
+    if (!r) return fail(PSS_EINVAL, "pss_result_cands: null result");
+    if (c) *c = r->cands.empty() ? nullptr : r->cands.data();
+    if (n) *n = (int64_t)r->cands.size();
+    if (latency_s) *latency_s = r->latency_s;
+    if (r->status != PSS_OK) set_error(r->err);
+    return r->status;
+}
+
+extern "C" void pss_result_free(pss_result* r) { delete r; }
+
+extern "C" pss_status pss_server_stats(pss_server* srv, int64_t* completed, double* p50_s, double* p99_s,
+                                       size_t* bytes_in_use) {
+    if (!srv) return fail(PSS_EINVAL, "pss_server_stats: null server");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    std::vector<double> v = srv->latencies;
+    std::sort(v.begin(), v.end());
+    auto pct = [&](double p) {
+        if (v.empty()) return 0.0;
+        // nearest-rank percentile
+        size_t i = (size_t)ceil(p / 100.0 * (double)v.size());
+        if (i < 1) i = 1;
+        return v[i - 1];
+    };
+    if (completed) *completed = (int64_t)v.size();
+    if (p50_s) *p50_s = pct(50.0);
+    if (p99_s) *p99_s = pct(99.0);
+    if (bytes_in_use) *bytes_in_use = srv->in_use;
+    return PSS_OK;
+}
+
+extern "C" void pss_server_destroy(pss_server* srv) {
+    if (!srv) return;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->stop = true;
+        srv->cv_work.notify_all();
+    }
+    for (auto& t : srv->workers) t.join();
+    for (auto& sl : srv->slots)
+        if (sl.batch) pss_batch_free(sl.batch);
+    for (Request* r : srv->queue) delete r;
+    for (auto& kv : srv->done) delete kv.second;
+    delete srv;
+}

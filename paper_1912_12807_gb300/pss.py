@@ -62,7 +62,9 @@ EXPORTS = ["pss_ctx_create", "pss_ctx_destroy", "pss_last_error", "pss_version",
            "pss_plan_trial_info", "pss_plan_free", "pss_dedisperse", "pss_spectrum", "pss_power_plane",
            "pss_search_raw", "pss_sift", "pss_search_dm_batch", "pss_response", "pss_sigma_of_power",
            "pss_power_threshold", "pss_ctx_profile", "pss_ctx_profile_read", "pss_dedisperse_noalloc",
-           "pss_refine_prepare", "pss_refine_eval", "pss_refine_candidates"]
+           "pss_refine_prepare", "pss_refine_eval", "pss_refine_candidates", "pss_batch_create", "pss_batch_run",
+           "pss_batch_footprint", "pss_batch_free", "pss_search_footprint", "pss_server_create", "pss_submit_file", "pss_poll",
+           "pss_result_cands", "pss_result_free", "pss_server_stats", "pss_server_destroy"]
 PROFILE_STAGES = ["unpack", "dedisperse", "fft", "whiten", "plane", "harmsum"]
 
 _lib = None
@@ -103,6 +105,19 @@ def lib():
                                        C.c_double, vp]),
         "pss_ctx_profile": (st, [vp, C.c_int]),
         "pss_ctx_profile_read": (st, [vp, vp, vp]),
+        "pss_batch_create": (st, [C.c_int, vp, P(pss_fil_desc), P(pss_search_cfg), P(vp)]),
+        "pss_batch_run": (st, [vp, vp, C.c_int, vp, i64, P(i64), P(C.c_double)]),
+        "pss_batch_footprint": (C.c_size_t, [vp]),
+        "pss_batch_free": (None, [vp]),
+        "pss_search_footprint": (st, [vp, P(pss_fil_desc), P(pss_search_cfg), P(C.c_size_t)]),
+        "pss_server_create": (st, [C.c_int, C.c_size_t, C.c_int, P(vp)]),
+        "pss_submit_file": (st, [vp, P(pss_fil_desc), vp, P(pss_dd_stage), C.c_int, P(pss_search_cfg),
+                                 P(C.c_uint64)]),
+        "pss_poll": (st, [vp, C.c_uint64, C.c_int, P(vp)]),
+        "pss_result_cands": (st, [vp, P(vp), P(i64), P(C.c_double)]),
+        "pss_result_free": (None, [vp]),
+        "pss_server_stats": (st, [vp, P(i64), P(C.c_double), P(C.c_double), P(C.c_size_t)]),
+        "pss_server_destroy": (None, [vp]),
         "pss_sigma_of_power": (C.c_double, [i32, C.c_double]),
         "pss_power_threshold": (C.c_double, [i32, C.c_double]),
     }
@@ -355,6 +370,119 @@ def pss_search_dm_batch(ctx: Context, plan: Plan, data, cfg: pss_search_cfg, dm_
             continue
         _check(st)
         return out[: n.value]
+
+
+class Batch:
+    """A search prepared for files of one shape and captured into a CUDA
+    graph (pss_batch_*); run() searches one file per call."""
+
+    def __init__(self, plan: Plan, cfg: pss_search_cfg, device: int = 0):
+        h = C.c_void_p()
+        _check(lib().pss_batch_create(int(device), plan.h, C.byref(plan.desc.c), C.byref(cfg), C.byref(h)))
+        self.h, self.plan, self.cfg = h, plan, cfg
+
+    @property
+    def footprint(self) -> int:
+        return int(lib().pss_batch_footprint(self.h))
+
+    def run(self, data, cap: int = 1 << 14, timing: bool = False):
+        """Sifted candidates of one file (host array or device tensor; a device
+        tensor must be complete: the batch copies it on its own stream)."""
+        p, dev, keep = _data_arg(data)
+        if dev:
+            import torch
+            torch.cuda.current_stream().synchronize()
+        n, ms = C.c_int64(), C.c_double()
+        while True:
+            out = np.zeros(cap, dtype=CAND_DTYPE)
+            st = lib().pss_batch_run(self.h, p, dev, out.ctypes.data, cap, C.byref(n),
+                                     C.byref(ms) if timing else None)
+            if st == PSS_ECAP:
+                cap = n.value
+                continue
+            _check(st)
+            return (out[: n.value], ms.value) if timing else out[: n.value]
+
+    def close(self):
+        if self.h:
+            lib().pss_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pss_batch_create(plan: Plan, cfg: pss_search_cfg, device: int = 0) -> Batch:
+    return Batch(plan, cfg, device)
+
+
+def pss_search_footprint(plan: Plan, cfg: pss_search_cfg) -> int:
+    """Device bytes a Batch (or a server slot) for this shape holds."""
+    b = C.c_size_t()
+    _check(lib().pss_search_footprint(plan.h, C.byref(plan.desc.c), C.byref(cfg), C.byref(b)))
+    return int(b.value)
+
+
+def pss_batch_run(batch: Batch, data, cap: int = 1 << 14) -> np.ndarray:
+    return batch.run(data, cap)
+
+
+class Server:
+    """Request loop over files (pss_server_*): submit() queues a file and
+    returns a ticket; poll() hands over its candidates once."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 2, device: int = 0):
+        h = C.c_void_p()
+        _check(lib().pss_server_create(int(device), C.c_size_t(int(hbm_budget_bytes)), int(max_slots), C.byref(h)))
+        self.h = h
+
+    def submit(self, desc: FilDesc, data, stages, cfg: pss_search_cfg) -> int:
+        arr = np.ascontiguousarray(data, dtype=np.uint8)
+        st_arr = stages_array(stages)
+        t = C.c_uint64()
+        _check(lib().pss_submit_file(self.h, C.byref(desc.c), arr.ctypes.data, st_arr, len(stages), C.byref(cfg),
+                                     C.byref(t)))
+        return int(t.value)
+
+    def poll(self, ticket: int, timeout_ms: int = -1):
+        """(candidates, latency_s) of a finished file; raises PssError with
+        PSS_ENOTREADY / PSS_ETIMEOUT while it is not ready, or the error the
+        file met."""
+        r = C.c_void_p()
+        _check(lib().pss_poll(self.h, C.c_uint64(int(ticket)), int(timeout_ms), C.byref(r)))
+        try:
+            cp, n, lat = C.c_void_p(), C.c_int64(), C.c_double()
+            st = lib().pss_result_cands(r, C.byref(cp), C.byref(n), C.byref(lat))
+            _check(st)
+            out = np.zeros(n.value, dtype=CAND_DTYPE)
+            if n.value:
+                C.memmove(out.ctypes.data, cp.value, n.value * CAND_DTYPE.itemsize)
+            return out, float(lat.value)
+        finally:
+            lib().pss_result_free(r)
+
+    def stats(self):
+        done, p50, p99, used = C.c_int64(), C.c_double(), C.c_double(), C.c_size_t()
+        _check(lib().pss_server_stats(self.h, C.byref(done), C.byref(p50), C.byref(p99), C.byref(used)))
+        return dict(completed=done.value, p50_s=p50.value, p99_s=p99.value, bytes_in_use=int(used.value))
+
+    def close(self):
+        if self.h:
+            lib().pss_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pss_server_create(hbm_budget_bytes: int, max_slots: int = 2, device: int = 0) -> Server:
+    return Server(hbm_budget_bytes, max_slots, device)
 
 
 def pss_refine_prepare(ctx: Context, plan: Plan, data, cfg: pss_search_cfg, stage: int, stream=None):

@@ -77,6 +77,33 @@ def test_version_and_no_device_error(L):
     with pytest.raises(L.PssError) as e:
         L.Context(0)
     assert e.value.status in (L.PSS_ECUDA, L.PSS_EINVAL)
+    desc = L.FilDesc(64, 1 << 14, 2e-4, 1202.34375, 4.6875)
+    plan = L.Plan(desc, [synth.Stage(0.0, 1.0, 8, 1)])
+    with pytest.raises(L.PssError) as e:
+        L.Batch(plan, L.search_cfg())
+    assert e.value.status in (L.PSS_ECUDA, L.PSS_EINVAL)
+    with pytest.raises(L.PssError) as e:
+        L.Server(1 << 30, 2)
+    assert e.value.status in (L.PSS_ECUDA, L.PSS_EINVAL)
+
+
+def test_search_footprint_is_host_arithmetic(L):
+    """The admission estimate: at least the buffers one batch of trials
+    needs (file, series, three spectra, plane), within 15 % + 64 MiB of
+    them, growing with zmax; the checks pss_batch_create makes."""
+    nchan, nsamp, nfft = 256, 1 << 18, 1 << 18
+    desc = L.FilDesc(nchan, nsamp, 2e-4, *synth.band(1050.0, 1450.0, nchan))
+    plan = L.Plan(desc, [synth.Stage(0.0, 0.5, 1001, 1)])
+    got0 = L.pss_search_footprint(plan, L.search_cfg(zmax=0, numharm=16))
+    B = 1024  # trials per batch: 6 GiB / (20 + 4 nz) bytes per point, at most 1024
+    base = nchan * nsamp + B * nfft * 4 + 3 * B * (nfft // 2) * 8
+    assert base + B * nfft * 4 <= got0 <= 1.15 * (base + B * nfft * 4) + (64 << 20)
+    got50 = L.pss_search_footprint(plan, L.search_cfg(zmax=50, dz=2.0, numharm=16))
+    B50 = (6 << 30) // (nfft * (20 + 4 * 51))
+    assert got50 >= nchan * nsamp + B50 * 51 * nfft * 4
+    with pytest.raises(L.PssError) as e:
+        L.pss_search_footprint(plan, L.search_cfg(numharm=3))
+    assert e.value.status == L.PSS_EINVAL
 
 
 @pytest.mark.parametrize("wl", ["small", "drift", "pmps"])
