@@ -14,6 +14,10 @@ small (64 channels, 2^16 samples, 101 trials).
 
 `e2e` repeats the step through the same C call with the file in pinned
 host memory (upload and candidate download inside the timed region).
+`batched` runs the same file through a prepared, graph-captured search
+(pss_batch); `serve` streams files of the same shape through the request
+loop (pss_server): saturated throughput, and p50/p99 latency at paced
+arrivals.
 
 Multi-GPU (torchrun): every rank searches its own file (independent
 problems, weak scaling, no collective); value = all ranks' DM trials /
@@ -371,6 +375,12 @@ def run_ours(args, rank, world, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e = float(t.item())
 
+    batched = served = None
+    if not args.no_serve:
+        batched = run_batched(pss, plan, cfg, data_dev, ndm, max(3, args.steps), flush)
+        if rank == 0:
+            served = run_served(pss, name, wl, args, local_rank)
+
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
@@ -403,12 +413,84 @@ def run_ours(args, rank, world, local_rank):
             "stage_rooflines": {k: {"bound": v["bound"], "frac": v["frac"], "achieved": v["achieved"],
                                     "unit": v["unit"]} for k, v in rooflines.items()},
             "clocks": clocks.summary(), "wall_s_timed": t_wall, "candidates": int(len(cands)),
-            "cpu_baseline": cpu}
+            "batched": batched, "serve": served, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_batched(pss, plan, cfg, data_dev, ndm, steps, flush):
+    """The same file through a prepared, graph-captured pss_batch: one graph
+    launch per file (device time from the batch's own events; wall time
+    includes the candidate download and the host sift)."""
+    import torch
+    b = pss.Batch(plan, cfg)
+    for _ in range(3):
+        b.run(data_dev)
+    gpu, wall = [], []
+    for k in range(steps):
+        flush.fill_((k + 7) & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, g = b.run(data_dev, timing=True)
+        wall.append(time.perf_counter() - t0)
+        gpu.append(g)
+    fp = b.footprint
+    b.close()
+    g, w = statistics.mean(gpu), statistics.mean(wall)
+    return {"value": ndm / (g / 1e3), "unit": UNIT, "gpu_ms_per_file": g, "wall_ms_per_file": 1e3 * w,
+            "wall_dm_trials_per_s": ndm / w, "launches_per_file": "1 graph", "device_bytes": fp}
+
+
+def run_served(pss, name, wl, args, device):
+    """A stream of files of the workload's shape (distinct contents) through the
+    request loop (pss_server): (a) all submitted at once, for throughput
+    with the host sift of one file overlapping the kernels of the next;
+    (b) paced arrivals, for submit-to-result latency percentiles."""
+    import numpy as np
+    n_distinct, n_files = 4, max(16, 4 * args.steps)
+    # distinct contents of one shape: the file rotated in time
+    datas = [np.ascontiguousarray(np.roll(wl.fil.data, 40503 * i, axis=0)) for i in range(n_distinct)]
+    desc = pss.FilDesc.of(wl.fil)
+    cfg = pss.cfg_of(wl.cfg)
+    ndm = int(sum(s.n_dm for s in wl.stages))
+    slots = args.serve_slots
+    srv = pss.Server(int(args.serve_budget_gib * (1 << 30)), max_slots=slots, device=device)
+    # warm-up at the same queue depth: batches prepared, pinned staging pool grown
+    for t in [srv.submit(desc, datas[i % n_distinct], wl.stages, cfg) for i in range(n_files)]:
+        srv.poll(t)
+    t0 = time.perf_counter()
+    ts = [srv.submit(desc, datas[i % n_distinct], wl.stages, cfg) for i in range(n_files)]
+    t_sub = time.perf_counter() - t0
+    for t in ts:
+        srv.poll(t)
+    dt = time.perf_counter() - t0
+    srv.close()
+    # paced: arrivals every `gap` seconds (about half the measured capacity)
+    gap = 2.0 * dt / n_files
+    srv = pss.Server(int(args.serve_budget_gib * (1 << 30)), max_slots=slots, device=device)
+    for t in [srv.submit(desc, d, wl.stages, cfg) for d in datas[:slots]]:
+        srv.poll(t)
+    lat = []
+    tick = time.perf_counter()
+    pending = []
+    for i in range(n_files):
+        while time.perf_counter() < tick + i * gap:
+            time.sleep(gap / 20)
+        pending.append(srv.submit(desc, datas[i % n_distinct], wl.stages, cfg))
+    for t in pending:
+        lat.append(srv.poll(t)[1])
+    srv.close()
+    lat.sort()
+    pct = lambda q: lat[max(0, math.ceil(q / 100.0 * len(lat)) - 1)]
+    return {"slots": slots, "files": n_files, "distinct_files": n_distinct,
+            "saturated": {"value": n_files * ndm / dt, "unit": UNIT, "files_per_s": n_files / dt,
+                          "realtime_factor": REALTIME_S * n_files / dt, "submit_ms_per_file": 1e3 * t_sub / n_files},
+            "paced": {"arrival_gap_ms": 1e3 * gap, "p50_ms": 1e3 * pct(50), "p99_ms": 1e3 * pct(99),
+                      "max_ms": 1e3 * lat[-1]},
+            "budget_gib": args.serve_budget_gib}
 
 
 def main():
@@ -419,6 +501,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="driftscan", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the batched and served measurements")
+    ap.add_argument("--serve-slots", type=int, default=2)
+    ap.add_argument("--serve-budget-gib", type=float, default=64.0)
     ap.add_argument("--dm-trials", type=int, default=None,
                     help="DM trials of a single-stage plan (driftscan/accel); smaller values make profiling cases")
     args = ap.parse_args()

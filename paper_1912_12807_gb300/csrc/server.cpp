@@ -38,9 +38,68 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// Page-locked host buffers that hold queued files: the copy into one at
+// submit is a plain memcpy (split over threads), and the slot's upload from
+// it is an asynchronous DMA instead of the driver's staged pageable copy.
+// At most `cap` bytes are kept; past that, files wait in ordinary memory.
+class PinnedPool {
+  public:
+    explicit PinnedPool(size_t cap) : cap_(cap) {}
+    ~PinnedPool() {
+        for (auto& b : free_) cudaFreeHost(b.second);
+    }
+    // a buffer of at least n bytes, or nullptr (then the caller uses pageable memory)
+    void* take(size_t n) {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            for (size_t i = 0; i < free_.size(); ++i)
+                if (free_[i].first >= n) {
+                    void* p = free_[i].second;
+                    size_[p] = free_[i].first;
+                    free_.erase(free_.begin() + (long)i);
+                    return p;
+                }
+            if (held_ + n > cap_) return nullptr;
+            held_ += n;
+        }
+        void* p = nullptr;
+        if (cudaHostAlloc(&p, n, cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();
+            std::lock_guard<std::mutex> lk(mu_);
+            held_ -= n;
+            return nullptr;
+        }
+        std::lock_guard<std::mutex> lk(mu_);
+        size_[p] = n;
+        return p;
+    }
+    void give(void* p) {
+        if (!p) return;
+        std::lock_guard<std::mutex> lk(mu_);
+        free_.emplace_back(size_[p], p);
+        size_.erase(p);
+    }
+
+  private:
+    size_t cap_, held_ = 0;
+    std::mutex mu_;
+    std::vector<std::pair<size_t, void*>> free_;
+    std::unordered_map<void*, size_t> size_;
+};
+
+void copy_parallel(uint8_t* dst, const uint8_t* src, size_t n) {
+    const size_t chunk = (size_t)8 << 20;
+    parallel_for((int64_t)((n + chunk - 1) / chunk), 1, [&](int64_t i) {
+        const size_t b = (size_t)i * chunk, e = std::min(n, b + chunk);
+        memcpy(dst + b, src + b, e - b);
+    });
+}
+
 struct Request {
     uint64_t ticket = 0;
-    std::vector<uint8_t> data;
+    PinnedPool* pool = nullptr;
+    void* pinned = nullptr;
+    std::vector<uint8_t> data;  // used when no pinned buffer was available
     pss_fil_desc fil{};
     std::vector<uint8_t> mask;
     std::vector<pss_dd_stage> stages;
@@ -49,7 +108,14 @@ struct Request {
     size_t estimate = 0;
     std::string key;
     Clock::time_point t_submit;
+    const void* bytes() const { return pinned ? pinned : (const void*)data.data(); }
+    void release_data() {
+        if (pinned) pool->give(pinned);
+        pinned = nullptr;
+        std::vector<uint8_t>().swap(data);
+    }
     ~Request() {
+        release_data();
         if (plan) pss_plan_free(plan);
     }
 };
@@ -82,6 +148,7 @@ using namespace pss;
 struct pss_server {
     int device = 0;
     size_t budget = 0;
+    PinnedPool pinned{(size_t)4 << 30};
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<Request*> queue;
@@ -171,11 +238,11 @@ struct pss_server {
                 if (res->status == PSS_OK) {
                     int64_t n = 0;
                     std::vector<pss_cand> buf(1024);
-                    pss_status st = pss_batch_run(slot.batch, r->data.data(), 0, buf.data(), (int64_t)buf.size(), &n,
-                                                  nullptr);
+                    pss_status st =
+                        pss_batch_run(slot.batch, r->bytes(), 0, buf.data(), (int64_t)buf.size(), &n, nullptr);
                     if (st == PSS_ECAP) {
                         buf.resize((size_t)n);
-                        st = pss_batch_run(slot.batch, r->data.data(), 0, buf.data(), (int64_t)buf.size(), &n, nullptr);
+                        st = pss_batch_run(slot.batch, r->bytes(), 0, buf.data(), (int64_t)buf.size(), &n, nullptr);
                     }
                     if (st != PSS_OK) {
                         res->status = st;
@@ -202,6 +269,7 @@ struct pss_server {
                 in_use -= slot.held;
                 slot.held = 0;
             }
+            r->release_data();
             finish(r, res);
             delete r;
             lk.lock();
@@ -250,8 +318,16 @@ extern "C" pss_status pss_submit_file(pss_server* srv, const pss_fil_desc* fil, 
     }
     r->estimate = search_footprint(*r->plan, &r->fil, &r->cfg, kBatchInitialCap);
     const size_t nbytes = fil->nbits == 8 ? (size_t)fil->nchan * fil->nsamp : (size_t)(fil->nchan / 8) * fil->nsamp;
+    cudaSetDevice(srv->device);
+    r->pool = &srv->pinned;
+    r->pinned = srv->pinned.take(nbytes);
     try {
-        r->data.assign((const uint8_t*)host_data, (const uint8_t*)host_data + nbytes);
+        if (r->pinned) {
+            copy_parallel((uint8_t*)r->pinned, (const uint8_t*)host_data, nbytes);
+        } else {
+            r->data.resize(nbytes);
+            copy_parallel(r->data.data(), (const uint8_t*)host_data, nbytes);
+        }
     } catch (const std::bad_alloc&) {
         delete r;
         return fail(PSS_ENOMEM, "pss_submit_file: cannot copy the file");
