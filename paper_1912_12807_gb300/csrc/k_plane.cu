@@ -110,6 +110,61 @@ __global__ void __launch_bounds__(NT) k_plane(PlaneArgs a) {
     }
 }
 
+// Odd half-bin tap i of the z = 0 template with 2m = NTAP taps: the
+// imaginary part of conj(rho(1/2 - t, 0)) with t = i - (m - 1), which is
+// 1 / (pi (t - 1/2)) (its real part is zero), rounded to FP32 at compile time.
+template <int NTAP>
+__host__ __device__ constexpr float z0_tap(int i) {
+    return (float)(1.0 / (3.14159265358979323846 * ((double)(i - (NTAP / 2 - 1)) - 0.5)));
+}
+
+// zmax = 0 plane with 2m = NTAP taps: each thread computes R consecutive
+// bins from a register window over a shared-memory tile (one padding slot
+// every 8 entries keeps the strided 8-byte reads free of bank conflicts);
+// the taps are compile-time constants.  Same arithmetic and order per
+// output as k_plane's z = 0 rows.
+template <int NTAP, int R>
+__global__ void __launch_bounds__(NT) k_plane_z0(PlaneArgs a) {
+    constexpr int KB0 = NT * R;
+    constexpr int H = NTAP / 2 - 1;  // taps t = -H .. H+1 around the bin
+    constexpr int TW = KB0 + NTAP - 1;
+    __shared__ float2 tile[TW + TW / 8 + 1];
+    const int b = blockIdx.y;
+    const int64_t M = a.nfft / 2;
+    const int64_t k0 = (int64_t)blockIdx.x * KB0;
+    const float2* Ap = a.spec + (int64_t)b * a.spec_stride;
+    for (int i = threadIdx.x; i < TW; i += NT) {
+        const int64_t k = k0 - H + i;
+        tile[i + (i >> 3)] = (k >= 0 && k < M) ? Ap[k] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const float s1 = a.tap_scale[1];
+    float re[R], im[R], p0[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) re[i] = im[i] = p0[i] = 0.f;
+    const float2* w = tile + threadIdx.x * (R + R / 8);
+#pragma unroll
+    for (int j = 0; j < R + NTAP - 1; ++j) {
+        const float2 x = w[j + (j >> 3)];
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const int ti = j - i;
+            if (ti >= 0 && ti < NTAP) {
+                re[i] = fmaf(x.x, z0_tap<NTAP>(ti), re[i]);
+                im[i] = fmaf(x.y, z0_tap<NTAP>(ti), im[i]);
+            }
+            if (ti == H) p0[i] = x.x * x.x + x.y * x.y;
+        }
+    }
+    float2* P = reinterpret_cast<float2*>(a.plane + (int64_t)b * a.plane_stride);
+    const int64_t kb = k0 + (int64_t)threadIdx.x * R;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const float r = re[i] * s1, q = im[i] * s1;
+        if (kb + i < M) P[kb + i] = make_float2(p0[i], r * r + q * q);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_templates(const TemplateArgs& a, cudaStream_t s) {
@@ -119,6 +174,12 @@ cudaError_t launch_templates(const TemplateArgs& a, cudaStream_t s) {
 
 cudaError_t launch_plane(const PlaneArgs& a, cudaStream_t s) {
     const int64_t M = a.nfft / 2;
+    if (a.zmax == 0 && a.extra == 16) {
+        constexpr int R = 8;
+        dim3 grid((unsigned)((M + NT * R - 1) / (NT * R)), (unsigned)a.nb);
+        k_plane_z0<32, R><<<grid, NT, 0, s>>>(a);
+        return cudaGetLastError();
+    }
     const int nz = a.zmax ? (int)llround(2.0 * a.zmax / a.dz) + 1 : 1;
     const int mmax = (int)ceil(a.zmax / 2.0) + a.extra;
     const size_t shm = (size_t)(KB + 2 * mmax - 1 + 4 * mmax) * sizeof(float2);
