@@ -81,7 +81,7 @@ struct Smem {
     uint32_t* copies;  // [CC][4][RW]
     uint8_t* raw;      // [CC][RAWB]
     int32_t* rs;       // [ck] first staged byte of each row, relative to t0 (16-byte aligned absolute)
-    uint16_t* offs;    // [G][ck] byte offset of t0 + d into the staged row
+    uint16_t* offs;    // [G][ck] word index of t0 + d in the row's four shifted copies
     uint64_t* bar;
 };
 
@@ -141,7 +141,8 @@ __global__ void __launch_bounds__(NT) k_dedisp(DedispArgs a, int RW, int CC, uin
         for (int g = 0; g < gn; ++g) {
             const int64_t o = t0 + dcol[(int64_t)g * a.ck] - st;
             bad |= (o >= omax);
-            S.offs[g * a.ck + c] = (uint16_t)(bad ? 0 : o);
+            // word index into the channel's four copies: copy (o & 3), word (o >> 2)
+            S.offs[g * a.ck + c] = (uint16_t)(bad ? 0 : (o & 3) * RW + (o >> 2));
         }
     }
     if (__syncthreads_or(bad)) {
@@ -222,8 +223,7 @@ __global__ void __launch_bounds__(NT) k_dedisp(DedispArgs a, int RW, int CC, uin
             const uint16_t* offs = S.offs + warp * a.ck + cb;
 #pragma unroll 2
             for (int i = 0; i < cn; ++i) {
-                const int o = offs[i];
-                const uint32_t* p = S.copies + ((size_t)i * 4 + (o & 3)) * RW + (o >> 2) + lane;
+                const uint32_t* p = S.copies + (size_t)i * 4 * RW + offs[i] + lane;
 #pragma unroll
                 for (int k = 0; k < KW; ++k) {
                     const uint32_t w = p[32 * k];

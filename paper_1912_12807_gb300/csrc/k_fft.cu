@@ -162,10 +162,16 @@ __global__ void __launch_bounds__(NT) k_fft_pass(const __grid_constant__ PassArg
     for (int t = threadIdx.x; t < R; t += NT) tws[t] = a.tw[(int64_t)t * tstride];
 
     if (first) {
-        // mean = sum / N_v in FP64, split as integer + fraction
-        const double mu = (double)a.sums[b] / (double)a.nv;
-        const double mi = rint(mu);
-        const float mu_i = (float)mi, mu_f = (float)(mu - mi);
+        // mean = sum / N_v in FP64 (once per CTA: FP64 is slow), split as integer + fraction
+        __shared__ float s_mu[2];
+        if (threadIdx.x == 0) {
+            const double mu = (double)a.sums[b] / (double)a.nv;
+            const double mi = rint(mu);
+            s_mu[0] = (float)mi;
+            s_mu[1] = (float)(mu - mi);
+        }
+        __syncthreads();
+        const float mu_i = s_mu[0], mu_f = s_mu[1];
         const float* s = a.series + (int64_t)b * a.series_stride;
 #pragma unroll
         for (int e = threadIdx.x; e < R * TJ; e += NT) {
@@ -398,12 +404,16 @@ __global__ void __launch_bounds__(256) k_r2c_whiten(const float2* Zall, int64_t 
         }
         med_bits = prefix;
     }
-    const float med = __uint_as_float(med_bits);
-    float scale = 0.f;
-    if (med > 0.f) scale = (float)sqrt(0.69314718055994530942 / (double)med);
-    if (gains && threadIdx.x == 0)
-        gains[(int64_t)b * gains_stride + blockIdx.x] = med > 0.f ? (float)(0.69314718055994530942 / (double)med) : 0.f;
-    if (!whiten) scale = 1.f;
+    // scale sqrt(ln 2 / med) and gain ln 2 / med in FP64, once per CTA (FP64 is slow)
+    __shared__ float s_scale;
+    if (threadIdx.x == 0) {
+        const float med = __uint_as_float(med_bits);
+        const double g = med > 0.f ? 0.69314718055994530942 / (double)med : 0.0;
+        s_scale = whiten ? (float)sqrt(g) : 1.f;
+        if (gains) gains[(int64_t)b * gains_stride + blockIdx.x] = (float)g;
+    }
+    __syncthreads();
+    const float scale = s_scale;
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
         const int64_t k = k0 + threadIdx.x + (int64_t)e * nt;
