@@ -270,6 +270,23 @@ pss_status ensure_templates(pss_ctx* ctx, const pss_search_cfg* cfg, cudaStream_
     ta.tap_scale = (float*)(info + 3 * nz);
     ta.total = total;
     PSS_CUDA(launch_templates(ta, s));
+    // template spectra for the overlap-save plane (any spectrum of >= L bins)
+    ctx->ftap_ok = false;
+    if (plane_fft_usable(cfg->zmax, cfg->halfwidth_extra, PLANE_FFT_L)) {
+        const int mmax = (cfg->zmax + 1) / 2 + cfg->halfwidth_extra;
+        PSS_TRY(ctx->ftaps.ensure((size_t)nz * 2 * PLANE_FFT_L * sizeof(float2)));
+        FftTemplateArgs fa;
+        fa.nz = nz;
+        fa.zmax = cfg->zmax;
+        fa.extra = cfg->halfwidth_extra;
+        fa.dz = dz;
+        fa.tap_m = info + 2 * nz;
+        fa.ftaps = (float2*)ctx->ftaps.p;
+        fa.L = PLANE_FFT_L;
+        fa.M0 = mmax - 1;
+        PSS_CUDA(launch_fft_templates(fa, s));
+        ctx->ftap_ok = true;
+    }
     PSS_CUDA(cudaStreamSynchronize(s));
     ctx->tap_zmax = cfg->zmax;
     ctx->tap_extra = cfg->halfwidth_extra;
@@ -454,6 +471,16 @@ pss_status enqueue_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* 
         pl.tap_off = info;
         pl.tap_m = info + 2 * P.nz;
         pl.tap_scale = (const float*)(info + 3 * P.nz);
+        pl.ftaps = nullptr;
+        if (ctx->ftap_ok && plane_fft_usable(cfg->zmax, cfg->halfwidth_extra, M)) {
+            const int mmax = (cfg->zmax + 1) / 2 + cfg->halfwidth_extra;
+            pl.ftaps = (const float2*)ctx->ftaps.p;
+            pl.fL = PLANE_FFT_L;
+            pl.fM0 = mmax - 1;
+            pl.fV = PLANE_FFT_L - 2 * mmax + 1;
+            pl.tw = (const float2*)ctx->twid.p;
+            pl.twM = ctx->twid_n;
+        }
         {
             ProfScope ps(ctx, 4, s);
             PSS_CUDA(launch_plane(pl, s));
@@ -572,8 +599,8 @@ void pss_ctx_destroy(pss_ctx* c) {
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     DevBuf* bufs[] = {&c->fil_dev, &c->xcm, &c->delays_dev, &c->series, &c->sums, &c->fftA, &c->fftB,
-                      &c->spec, &c->plane, &c->cands, &c->counter, &c->taps, &c->tapinfo, &c->errflag, &c->twid, &c->chan_spec, &c->refine_gains,
-                      &c->refine_dtau, &c->refine_pts, &c->refine_out};
+                      &c->spec, &c->plane, &c->cands, &c->counter, &c->taps, &c->ftaps, &c->tapinfo, &c->errflag,
+                      &c->twid, &c->chan_spec, &c->refine_gains, &c->refine_dtau, &c->refine_pts, &c->refine_out};
     for (DevBuf* b : bufs) b->release();
     for (auto& r : c->prof_recs) {
         cudaEventDestroy(r.a);
@@ -1034,8 +1061,8 @@ namespace {
 
 size_t ctx_bytes(const pss_ctx* c) {
     const DevBuf* bufs[] = {&c->fil_dev, &c->xcm, &c->delays_dev, &c->series, &c->sums, &c->fftA, &c->fftB,
-                            &c->spec, &c->plane, &c->cands, &c->counter, &c->taps, &c->tapinfo, &c->errflag,
-                            &c->twid};
+                            &c->spec, &c->plane, &c->cands, &c->counter, &c->taps, &c->ftaps, &c->tapinfo,
+                            &c->errflag, &c->twid};
     size_t t = 0;
     for (const DevBuf* b : bufs) t += b->bytes;
     return t;
@@ -1148,6 +1175,8 @@ size_t search_footprint(const Plan& plan, const pss_fil_desc* fil, const pss_sea
         const double z = cfg->zmax ? -(double)cfg->zmax + (double)j * cfg->dz : 0.0;
         total_taps += 4 * ((int64_t)ceil(fabs(z) / 2.0) + cfg->halfwidth_extra);
     }
+    if (plane_fft_usable(cfg->zmax, cfg->halfwidth_extra, PLANE_FFT_L))
+        t += buf((size_t)nz * 2 * PLANE_FFT_L * sizeof(float2));
     t += buf((size_t)nfft_max * sizeof(float2)) + buf(need_series) + buf(need_sums) + 3 * buf(need_fft) +
          buf(need_plane) + buf((size_t)total_taps * sizeof(float2)) + buf((size_t)5 * nz * sizeof(int32_t));
     return t;

@@ -24,6 +24,7 @@
 // exact up to one rounding) and zero-pads past N_v.
 #include <math.h>
 
+#include "fft_small.cuh"
 #include "pss_internal.h"
 
 namespace pss {
@@ -33,52 +34,6 @@ namespace {
 constexpr int TJ = 8;        // columns per CTA
 constexpr int TJP = TJ + 1;  // padded shared-memory row (bank spread)
 constexpr int NT = 256;      // threads per CTA
-constexpr float R2 = 0.70710678118654752440f;
-
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }  // * (-i)
-
-// forward DFTs of length 2, 4, 8 in registers (x[k] = sum_n x[n] e^{-2 pi i nk/L})
-__device__ __forceinline__ void dft2(float2* x) {
-    const float2 a = x[0], b = x[1];
-    x[0] = cadd(a, b);
-    x[1] = csub(a, b);
-}
-__device__ __forceinline__ void dft4(float2& y0, float2& y1, float2& y2, float2& y3) {
-    const float2 s02 = cadd(y0, y2), d02 = csub(y0, y2);
-    const float2 s13 = cadd(y1, y3), d13 = mul_mi(csub(y1, y3));
-    y0 = cadd(s02, s13);
-    y2 = csub(s02, s13);
-    const float2 t1 = cadd(d02, d13), t3 = csub(d02, d13);
-    y1 = t1;
-    y3 = t3;
-}
-__device__ __forceinline__ void dft4v(float2* x) { dft4(x[0], x[1], x[2], x[3]); }
-__device__ __forceinline__ void dft8(float2* x) {
-    float2 a0 = cadd(x[0], x[4]), b0 = csub(x[0], x[4]);
-    float2 a1 = cadd(x[1], x[5]), b1 = csub(x[1], x[5]);
-    float2 a2 = cadd(x[2], x[6]), b2 = csub(x[2], x[6]);
-    float2 a3 = cadd(x[3], x[7]), b3 = csub(x[3], x[7]);
-    // b_m *= w^m, w = exp(-2 pi i / 8)
-    b1 = make_float2((b1.x + b1.y) * R2, (b1.y - b1.x) * R2);
-    b2 = mul_mi(b2);
-    b3 = make_float2((b3.y - b3.x) * R2, -(b3.x + b3.y) * R2);
-    dft4(a0, a1, a2, a3);
-    dft4(b0, b1, b2, b3);
-    x[0] = a0; x[2] = a1; x[4] = a2; x[6] = a3;
-    x[1] = b0; x[3] = b1; x[5] = b2; x[7] = b3;
-}
-
-template <int RR>
-__device__ __forceinline__ void dft_small(float2* x) {
-    if constexpr (RR == 2) dft2(x);
-    else if constexpr (RR == 4) dft4v(x);
-    else dft8(x);
-}
 
 // One Stockham sub-stage of radix RR on the R-point DFTs of TJ columns,
 // in place in shared memory ([r * TJP + jj]), running span ns: every thread

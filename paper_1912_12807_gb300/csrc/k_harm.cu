@@ -186,41 +186,48 @@ cudaError_t launch_variant(const HarmArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// ---- single-row plane (zmax = 0): register-blocked variant ----------------
+// ---- register-blocked variant ------------------------------------------------
 //
-// A warp owns WR = 32 R consecutive half-bins; lane l holds the sums of the
-// points h = hw + l + 32 i (i < R) in registers.  For stage n and odd
-// harmonic k, point h reads half-bin (2kh + n) >> (s+1); stepping h by 32
-// steps that index by exactly 32k/n (an integer for n <= 32), so one index
-// computation per harmonic serves all R points and the loads use
-// compile-time offsets, each coalesced across the warp.  Additions happen
-// in the order of k_harm (stage by stage, odd k increasing), so the sums
-// are bit-identical.  Threshold tests run on the lane's maximum; the rare
-// warp with a point above threshold takes its neighbours from adjacent
-// lanes, or recomputes the sum outside the warp's run from the plane.
+// A warp owns WR = 32 R consecutive half-bins of one plane row j; lane l
+// holds the sums of the points h = hw + l + 32 i (i < R) in registers.  For
+// stage n and odd harmonic k, point (h, j) reads row j_k (the same for the
+// whole warp) at half-bin (2kh + n) >> (s+1); stepping h by 32 steps that
+// index by exactly 32k/n (an integer for n <= 32), so one index computation
+// per harmonic serves all R points and the loads use compile-time offsets,
+// each coalesced across the warp.  Additions happen in the order of k_harm
+// (stage by stage, odd k increasing), so the sums are bit-identical.
+// Threshold tests run on the lane's maximum; a warp with a point above
+// threshold takes same-row neighbours from adjacent lanes and recomputes any
+// other neighbour (warp edges, rows j +- 1) from the plane.
 
-// S_n at half-bin h from the plane (the same additions in the same order).
+// S_n at (h, j) from the plane (the same additions in the same order).
 template <int SI>
-__device__ float harm_sum_at(const float* P, int h, int nfft) {
-    if (h < 0 || h >= nfft) return -INFINITY;
-    float acc = __ldg(P + h);
+__device__ float harm_sum_at(const float* P, int h, int j, int nfft, int nz, int Z) {
+    if (h < 0 || h >= nfft || j < 0 || j >= nz) return -INFINITY;
+    float acc = __ldg(P + j * nfft + h);
+    const int d = j - Z, ad2 = 2 * (d < 0 ? -d : d);
 #pragma unroll
     for (int s = 1; s <= SI; ++s) {
         const int n = 1 << s;
-        for (int q = 0; q < n / 2; ++q) acc += __ldg(P + ((2 * (2 * q + 1) * h + n) >> (s + 1)));
+        for (int q = 0; q < n / 2; ++q) {
+            const int k = 2 * q + 1;
+            const int dk = (k * ad2 + n) >> (s + 1);
+            const int jk = d < 0 ? Z - dk : Z + dk;
+            acc += __ldg(P + jk * nfft + ((2 * k * h + n) >> (s + 1)));
+        }
     }
     return acc;
 }
 
 template <int SI, int R>
-__device__ __forceinline__ void row_test(const HarmArgs& a, const float* P, const float (&acc)[R], int hw, int lane,
-                                         int b) {
+__device__ __forceinline__ void reg_test(const HarmArgs& a, const float* P, const float (&acc)[R], int hw, int j,
+                                         int lane, int b) {
     const float thr = a.thr[SI];
     float mx = acc[0];
 #pragma unroll
     for (int i = 1; i < R; ++i) mx = fmaxf(mx, acc[i]);
     if (!__any_sync(0xffffffffu, mx >= thr)) return;
-    const int nfft = (int)a.nfft, hmin = a.hmin[SI];
+    const int nfft = (int)a.nfft, hmin = a.hmin[SI], nz = a.nz, Z = a.Z;
 #pragma unroll
     for (int i = 0; i < R; ++i) {
         float left = __shfl_up_sync(0xffffffffu, acc[i], 1);
@@ -230,17 +237,26 @@ __device__ __forceinline__ void row_test(const HarmArgs& a, const float* P, cons
         const float s = acc[i];
         const int h = hw + lane + 32 * i;
         if (s >= thr && h >= hmin) {
-            if (lane == 0) left = i > 0 ? l31 : harm_sum_at<SI>(P, hw - 1, nfft);
-            if (lane == 31) right = i < R - 1 ? r0 : harm_sum_at<SI>(P, hw + 32 * R, nfft);
-            // strictly above the earlier neighbour, ties to the lower index against the later one
-            if (s > left && s >= right) {
+            if (lane == 0) left = i > 0 ? l31 : harm_sum_at<SI>(P, hw - 1, j, nfft, nz, Z);
+            if (lane == 31) right = i < R - 1 ? r0 : harm_sum_at<SI>(P, hw + 32 * R, j, nfft, nz, Z);
+            // strictly above every earlier neighbour, ties to the lower index against later ones
+            bool hit = s > left && s >= right;
+            if (nz > 1) {
+#pragma unroll
+                for (int dh = -1; dh <= 1; ++dh) {
+                    if (!hit) break;
+                    hit = s > harm_sum_at<SI>(P, h + dh, j - 1, nfft, nz, Z) &&
+                          s >= harm_sum_at<SI>(P, h + dh, j + 1, nfft, nz, Z);
+                }
+            }
+            if (hit) {
                 const unsigned long long slot = atomicAdd(a.counter, 1ull);
                 if ((int64_t)slot < a.cap) {
                     pss_raw_cand c;
                     c.dm_idx = a.dm0 + b;
                     c.numharm = 1 << SI;
                     c.h = h;
-                    c.j = 0;
+                    c.j = j;
                     c.power = s;
                     c.reserved = 0;
                     a.out[slot] = c;
@@ -251,47 +267,52 @@ __device__ __forceinline__ void row_test(const HarmArgs& a, const float* P, cons
 }
 
 template <int SI, int NSTAGES, int R>
-__device__ __forceinline__ void row_stages(const HarmArgs& a, const float* P, float (&acc)[R], int hw, int lane,
-                                           int b) {
+__device__ __forceinline__ void reg_stages(const HarmArgs& a, const float* P, float (&acc)[R], int hw, int j,
+                                           int lane, int b) {
     if constexpr (SI < NSTAGES) {
         if constexpr (SI > 0) {
             constexpr int n = 1 << SI;
+            const int d = j - a.Z, ad2 = 2 * (d < 0 ? -d : d);
 #pragma unroll
             for (int q = 0; q < n / 2; ++q) {
                 const int k = 2 * q + 1;
-                const float* p = P + ((2 * k * (hw + lane) + n) >> (SI + 1));
+                const int dk = (k * ad2 + n) >> (SI + 1);
+                const int jk = d < 0 ? a.Z - dk : a.Z + dk;
+                const float* p = P + jk * (int)a.nfft + ((2 * k * (hw + lane) + n) >> (SI + 1));
 #pragma unroll
                 for (int i = 0; i < R; ++i) acc[i] += __ldg(p + (32 / n) * k * i);
             }
         }
-        row_test<SI, R>(a, P, acc, hw, lane, b);
-        row_stages<SI + 1, NSTAGES, R>(a, P, acc, hw, lane, b);
+        reg_test<SI, R>(a, P, acc, hw, j, lane, b);
+        reg_stages<SI + 1, NSTAGES, R>(a, P, acc, hw, j, lane, b);
     }
 }
 
-constexpr int ROW_NT = 128;
+constexpr int REG_NT = 128;
 
 template <int NSTAGES, int R>
-__global__ void __launch_bounds__(ROW_NT) k_harm_row(const __grid_constant__ HarmArgs a) {
+__global__ void __launch_bounds__(REG_NT) k_harm_reg(const __grid_constant__ HarmArgs a) {
     const int lane = threadIdx.x & 31;
-    const int b = blockIdx.y;
-    const int hw = (blockIdx.x * (ROW_NT / 32) + (threadIdx.x >> 5)) * 32 * R;
+    const int j = blockIdx.y;
+    const int b = blockIdx.z;
+    const int hw = (blockIdx.x * (REG_NT / 32) + (threadIdx.x >> 5)) * 32 * R;
     const float* P = a.plane + (int64_t)b * a.plane_stride;
     float acc[R];
+    const float* row = P + j * (int)a.nfft;
 #pragma unroll
-    for (int i = 0; i < R; ++i) acc[i] = __ldg(P + hw + lane + 32 * i);
-    row_stages<0, NSTAGES, R>(a, P, acc, hw, lane, b);
+    for (int i = 0; i < R; ++i) acc[i] = __ldg(row + hw + lane + 32 * i);
+    reg_stages<0, NSTAGES, R>(a, P, acc, hw, j, lane, b);
 }
 
 template <int R>
-cudaError_t launch_row(const HarmArgs& a, cudaStream_t s) {
-    dim3 grid((unsigned)(a.nfft / (ROW_NT * R)), (unsigned)a.nb);
+cudaError_t launch_reg(const HarmArgs& a, cudaStream_t s) {
+    dim3 grid((unsigned)(a.nfft / (REG_NT * R)), (unsigned)a.nz, (unsigned)a.nb);
     switch (a.nstages) {
-        case 1: k_harm_row<1, R><<<grid, ROW_NT, 0, s>>>(a); break;
-        case 2: k_harm_row<2, R><<<grid, ROW_NT, 0, s>>>(a); break;
-        case 3: k_harm_row<3, R><<<grid, ROW_NT, 0, s>>>(a); break;
-        case 4: k_harm_row<4, R><<<grid, ROW_NT, 0, s>>>(a); break;
-        case 5: k_harm_row<5, R><<<grid, ROW_NT, 0, s>>>(a); break;
+        case 1: k_harm_reg<1, R><<<grid, REG_NT, 0, s>>>(a); break;
+        case 2: k_harm_reg<2, R><<<grid, REG_NT, 0, s>>>(a); break;
+        case 3: k_harm_reg<3, R><<<grid, REG_NT, 0, s>>>(a); break;
+        case 4: k_harm_reg<4, R><<<grid, REG_NT, 0, s>>>(a); break;
+        case 5: k_harm_reg<5, R><<<grid, REG_NT, 0, s>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -302,8 +323,8 @@ cudaError_t launch_row(const HarmArgs& a, cudaStream_t s) {
 cudaError_t launch_harm(const HarmArgs& a, cudaStream_t s) {
     if (a.nfft > (int64_t(1) << 24) || a.nstages > 6) return cudaErrorInvalidValue;
     if ((int64_t)a.nz * a.nfft > (int64_t(1) << 31)) return cudaErrorInvalidValue;  // 32-bit plane offsets
-    // register-blocked single-row kernel: up to 16 harmonics, whole warps of 32 x 16 points
-    if (a.nz == 1 && a.nstages <= 5 && a.nfft % (ROW_NT * 16) == 0) return launch_row<16>(a, s);
+    // register-blocked kernel: up to 16 harmonics, whole warps of 32 x 16 points
+    if (a.nstages <= 5 && a.nfft % (REG_NT * 16) == 0 && a.nz <= 65535) return launch_reg<16>(a, s);
     if (a.nz == 1) return launch_variant<1, 2048, true>(a, s);
     return launch_variant<4, 256, false>(a, s);
 }

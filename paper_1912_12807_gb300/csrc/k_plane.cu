@@ -8,10 +8,18 @@
 // with 1/sqrt(E).  They depend only on (zmax, dz, extra) and are cached by
 // the context.
 //
-// Plane: one CTA per (tile of KB bins, row, trial) stages the spectrum tile
-// with its +-m halo and the row's taps in shared memory and correlates.  For
-// the z = 0 row the even half-bins are |A'_k|^2 exactly and the odd ones use
-// the purely imaginary sinc taps, i.e. a real-weight FIR.
+// Plane, direct form: one CTA per (tile of KB bins, row, trial) stages the
+// spectrum tile with its +-m halo and the row's taps in shared memory and
+// correlates.  For the z = 0 row the even half-bins are |A'_k|^2 exactly and
+// the odd ones use the purely imaginary sinc taps, i.e. a real-weight FIR.
+//
+// Plane, overlap-save form (zmax > 0): the correlation of a row is a
+// convolution of the spectrum with that row's taps, so it is done with
+// L-point FFTs: a CTA transforms one segment of L spectrum bins once, then
+// for every (row, parity) multiplies by the FFT of the taps, transforms back
+// and keeps the L - 2 m_max + 1 outputs that the circular wrap does not
+// touch.  About 70 flops per plane value instead of 16 m(z).
+#include "fft_small.cuh"
 #include "pss_internal.h"
 #include "response.cuh"
 
@@ -165,7 +173,177 @@ __global__ void __launch_bounds__(NT) k_plane_z0(PlaneArgs a) {
     }
 }
 
+// ---- overlap-save plane ------------------------------------------------------
+
+// Template spectra, FP64: for row z_j and parity p the taps
+// g[t] = conj(rho(p/2 - t, z_j)), t = -m+1..m, sit at circular position
+// s = t + M0 (M0 = m_max - 1), and
+//   T[f] = (1 / (L sqrt(E))) sum_t g[t] exp(+2 pi i f s / L),
+// so that FFT(conj(X T)) of a segment's spectrum X is conj(L) times the
+// circular correlation with g / sqrt(E): its squared magnitude at u is the
+// plane value of the segment's u-th valid bin.  One CTA per (row, parity).
+__global__ void k_fft_templates(FftTemplateArgs a) {
+    extern __shared__ double2 fts[];
+    double2* g = fts;              // [2 m]
+    double2* W = fts + 2 * 1024;   // [L] exp(+2 pi i n / L)
+    __shared__ double red[256];
+    const int row = blockIdx.x >> 1, par = blockIdx.x & 1;
+    const double z = -(double)a.zmax + (double)row * a.dz;
+    const int m = a.tap_m[row];
+    double e = 0.0;
+    for (int i = threadIdx.x; i < 2 * m; i += blockDim.x) {
+        const int t = i - m + 1;
+        const cplx r = rho_resp(0.5 * par - (double)t, z);
+        g[i] = make_double2(r.re, -r.im);
+        e += r.re * r.re + r.im * r.im;
+    }
+    for (int n = threadIdx.x; n < a.L; n += blockDim.x) {
+        double sn, cs;
+        sincospi(2.0 * (double)n / (double)a.L, &sn, &cs);
+        W[n] = make_double2(cs, sn);
+    }
+    red[threadIdx.x] = e;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    const double scale = 1.0 / ((double)a.L * sqrt(red[0]));
+    float2* out = a.ftaps + (int64_t)blockIdx.x * a.L;
+    for (int f = threadIdx.x; f < a.L; f += blockDim.x) {
+        double re = 0.0, im = 0.0;
+        for (int i = 0; i < 2 * m; ++i) {
+            const int s = i - m + 1 + a.M0;  // 0 <= s < L
+            const double2 w = W[(f * s) & (a.L - 1)];  // L is a power of two
+            re += g[i].x * w.x - g[i].y * w.y;
+            im += g[i].x * w.y + g[i].y * w.x;
+        }
+        out[f] = make_float2((float)(re * scale), (float)(im * scale));
+    }
+}
+
+constexpr int FNT = 256;
+
+// padded shared-memory index: one spare slot per 8 keeps the strided
+// butterfly writes free of bank conflicts
+__device__ __forceinline__ int fp(int i) { return i + (i >> 3); }
+
+// One in-place Stockham sub-stage of radix RR of an L-point forward FFT held
+// in shared memory (natural order in and out after all sub-stages).
+template <int L, int RR>
+__device__ __forceinline__ void fft_substage(float2* buf, const float2* tws, int ns) {
+    constexpr int NB = L / RR;
+    constexpr int PER = NB / FNT;
+    float2 x[PER][RR];
+    int dst[PER];
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int b = threadIdx.x + p * FNT;
+        const int k = b & (ns - 1);
+        const int tstep = k * (L / RR / ns);
+#pragma unroll
+        for (int q = 0; q < RR; ++q) {
+            x[p][q] = buf[fp(b + q * NB)];
+            if (q && k) x[p][q] = cmul(x[p][q], tws[q * tstep]);
+        }
+        dst[p] = (b - k) * RR + k;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        dft_small<RR>(x[p]);
+#pragma unroll
+        for (int q = 0; q < RR; ++q) buf[fp(dst[p] + q * ns)] = x[p][q];
+    }
+    __syncthreads();
+}
+
+// L = 2048 = 4 * 8 * 8 * 8
+__device__ __forceinline__ void fft2048(float2* buf, const float2* tws) {
+    fft_substage<2048, 4>(buf, tws, 1);
+    fft_substage<2048, 8>(buf, tws, 4);
+    fft_substage<2048, 8>(buf, tws, 32);
+    fft_substage<2048, 8>(buf, tws, 256);
+}
+
+__global__ void __launch_bounds__(FNT) k_plane_fft(const __grid_constant__ PlaneArgs a) {
+    constexpr int L = PLANE_FFT_L;
+    constexpr int PADL = L + L / 8;
+    constexpr int NE = L / FNT;
+    extern __shared__ float2 fsm[];
+    float2* X = fsm;             // segment spectrum (kept)
+    float2* Y = fsm + PADL;      // work
+    float2* tws = fsm + 2 * PADL;
+    const int b = blockIdx.y;
+    const int64_t M = a.nfft / 2;
+    const int V = a.fV, M0 = a.fM0;
+    const int64_t k0 = (int64_t)blockIdx.x * V;
+    const float2* Ap = a.spec + (int64_t)b * a.spec_stride;
+    const int64_t tstride = a.twM / L;
+    for (int t = threadIdx.x; t < L; t += FNT) tws[t] = a.tw[t * tstride];
+    for (int i = threadIdx.x; i < L; i += FNT) {
+        const int64_t k = k0 - M0 + i;
+        X[fp(i)] = (k >= 0 && k < M) ? Ap[k] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    fft2048(X, tws);
+    const int nz = (int)llround(2.0 * a.zmax / a.dz) + 1;
+    float2* P = reinterpret_cast<float2*>(a.plane + (int64_t)b * a.plane_stride);
+    for (int j = 0; j < nz; ++j) {
+        const bool zrow0 = (-(double)a.zmax + (double)j * a.dz == 0.0);
+        float pw[2][NE];
+#pragma unroll
+        for (int par = 0; par < 2; ++par) {
+            if (par == 0 && zrow0) {
+                // integer half-bins of the z = 0 row: the raw powers, exactly
+#pragma unroll
+                for (int e = 0; e < NE; ++e) {
+                    const int u = threadIdx.x + e * FNT;
+                    const int64_t k = k0 + u;
+                    pw[0][e] = 0.f;
+                    if (u < V && k < M) {
+                        const float2 c = Ap[k];
+                        pw[0][e] = c.x * c.x + c.y * c.y;
+                    }
+                }
+                continue;
+            }
+            const float2* T = a.ftaps + ((int64_t)j * 2 + par) * L;
+#pragma unroll
+            for (int e = 0; e < NE; ++e) {
+                const int i = threadIdx.x + e * FNT;
+                const float2 y = cmul(X[fp(i)], __ldg(T + i));
+                Y[fp(i)] = make_float2(y.x, -y.y);
+            }
+            __syncthreads();
+            fft2048(Y, tws);
+#pragma unroll
+            for (int e = 0; e < NE; ++e) {
+                const float2 y = Y[fp(threadIdx.x + e * FNT)];
+                pw[par][e] = y.x * y.x + y.y * y.y;
+            }
+            __syncthreads();
+        }
+        float2* row = P + (int64_t)j * M;
+#pragma unroll
+        for (int e = 0; e < NE; ++e) {
+            const int u = threadIdx.x + e * FNT;
+            const int64_t k = k0 + u;
+            if (u < V && k < M) row[k] = make_float2(pw[0][e], pw[1][e]);
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_fft_templates(const FftTemplateArgs& a, cudaStream_t s) {
+    if (a.L != PLANE_FFT_L) return cudaErrorInvalidValue;
+    const size_t shm = (size_t)(2 * 1024 + a.L) * sizeof(double2);
+    cudaError_t e = allow_smem((const void*)k_fft_templates, shm);
+    if (e != cudaSuccess) return e;
+    k_fft_templates<<<a.nz * 2, 256, shm, s>>>(a);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_templates(const TemplateArgs& a, cudaStream_t s) {
     k_templates<<<a.nz * 2, 256, 0, s>>>(a);
@@ -181,6 +359,16 @@ cudaError_t launch_plane(const PlaneArgs& a, cudaStream_t s) {
         return cudaGetLastError();
     }
     const int nz = a.zmax ? (int)llround(2.0 * a.zmax / a.dz) + 1 : 1;
+    if (a.ftaps) {
+        if (a.fL != PLANE_FFT_L || a.fV <= 0 || a.twM % PLANE_FFT_L) return cudaErrorInvalidValue;
+        constexpr int PADL = PLANE_FFT_L + PLANE_FFT_L / 8;
+        const size_t shm = (size_t)(2 * PADL + PLANE_FFT_L) * sizeof(float2);
+        cudaError_t e = allow_smem((const void*)k_plane_fft, shm);
+        if (e != cudaSuccess) return e;
+        dim3 grid((unsigned)((M + a.fV - 1) / a.fV), (unsigned)a.nb);
+        k_plane_fft<<<grid, FNT, shm, s>>>(a);
+        return cudaGetLastError();
+    }
     const int mmax = (int)ceil(a.zmax / 2.0) + a.extra;
     const size_t shm = (size_t)(KB + 2 * mmax - 1 + 4 * mmax) * sizeof(float2);
     {

@@ -124,6 +124,7 @@ struct Ctx {
     DevBuf cands;        // pss_raw_cand [cap]
     DevBuf counter;      // unsigned long long
     DevBuf taps;         // float2 templates
+    DevBuf ftaps;        // float2 [nz][2][L] template spectra (overlap-save plane)
     DevBuf tapinfo;      // per row tap info
     DevBuf errflag;      // int: a kernel's bounded wait expired
     DevBuf twid;         // float2 twiddle table exp(-2 pi i t / twid_n)
@@ -139,6 +140,7 @@ struct Ctx {
     // (zmax, extra, dz) of the templates currently in `taps`
     int32_t tap_zmax = -1, tap_extra = -1;
     double tap_dz = 0.0;
+    bool ftap_ok = false;  // ftaps hold the spectra of the current templates
     // per-stage event timing (pss_ctx_profile)
     bool prof_on = false;
     struct ProfRec {
@@ -242,8 +244,30 @@ struct PlaneArgs {
     const int32_t* tap_off;  // [nz*2] offsets into taps
     const int32_t* tap_m;    // [nz] half-widths
     const float* tap_scale;  // [nz*2] 1/sqrt(E)
+    // overlap-save form (zmax > 0): per (row, parity) the spectrum of the
+    // taps, [nz][2][fL]; null when the direct form is used
+    const float2* ftaps;
+    int32_t fL, fV, fM0;     // segment length, valid outputs per segment, lead
+    const float2* tw;        // exp(-2 pi i t / twM)
+    int64_t twM;
 };
 cudaError_t launch_plane(const PlaneArgs& a, cudaStream_t s);
+
+// Overlap-save plane: segment length, and whether it serves (zmax, extra)
+// for spectra of M bins (the direct form is used otherwise).
+constexpr int PLANE_FFT_L = 2048;
+inline bool plane_fft_usable(int32_t zmax, int32_t extra, int64_t M) {
+    const int mmax = (zmax + 1) / 2 + extra;
+    return zmax > 0 && 4 * mmax <= PLANE_FFT_L && M >= PLANE_FFT_L;
+}
+struct FftTemplateArgs {
+    int32_t nz, zmax, extra;
+    double dz;
+    const int32_t* tap_m;  // [nz] half-widths
+    float2* ftaps;         // out [nz][2][L]
+    int32_t L, M0;
+};
+cudaError_t launch_fft_templates(const FftTemplateArgs& a, cudaStream_t s);
 
 struct TemplateArgs {
     int32_t nz, zmax, extra;

@@ -169,6 +169,23 @@ def test_accel_plane(L, ctx, zmax, dz):
         check_powers(got[k * nz * nfft:(k + 1) * nz * nfft].reshape(nz, nfft), ref, "accel plane DM %d" % i)
 
 
+def test_accel_plane_direct_form(L, ctx):
+    # a spectrum shorter than the overlap-save segment (1024 bins) takes the direct form
+    fil = synth.make_8bit(32, 2000, 2e-4, 1200.0, 1500.0,
+                          [synth.Pulsar(0.01, 20.0, 0.05, 0.3, z_direct=5.0)], seed=4)
+    stages = [synth.Stage(10.0, 5.0, 3, 1)]
+    wl = synth.Workload("t", fil, stages, synth.SearchCfg(zmax=12, dz=2.0, numharm=4, whiten_block=128))
+    cfg = _cfg(L, wl)
+    plan = L.Plan(L.FilDesc.of(fil), stages)
+    op = OP.Plan.for_file(fil, stages)
+    x = OD.channel_major(fil.data, fil.nchan, 8)
+    nfft = op.nv_nfft(1)[1]
+    assert nfft // 2 < 2048
+    got = L.pss_power_plane(ctx, plan, _torch_dev(fil.data), cfg, 1, 2).cpu().numpy()
+    _, _, ref = oracle_plane(x, op, 1, wl.cfg)
+    check_powers(got.reshape(L.n_z(cfg), nfft), ref, "direct-form accel plane")
+
+
 # ---------------------------------------------------------------- candidates
 def test_search_raw_small_parity(L, ctx, small):
     fil = small.fil
