@@ -275,11 +275,18 @@ pss_status pss_sift(const pss_plan* plan, const pss_search_cfg* cfg, const pss_r
                     int64_t n_raw, pss_cand* out, int64_t cap, int64_t* n_out);
 
 /* The whole search of DM trials [dm_begin, dm_end) of one file:
- * pss_search_raw followed by pss_sift.  out: host, cap entries. */
+ * pss_search_raw followed by pss_sift.  out: host, cap entries.  The sifted
+ * list is also kept in the context (until its next search), so that after
+ * PSS_ECAP a caller fetches it with pss_ctx_take_cands instead of searching
+ * again. */
 pss_status pss_search_dm_batch(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil,
                                const void* data, int data_on_device, const pss_search_cfg* cfg,
                                int64_t dm_begin, int64_t dm_end, pss_cand* out, int64_t cap,
                                int64_t* n_out, void* stream);
+/* Copy the sifted candidates of the context's last pss_search_dm_batch
+ * (host `out`, cap entries); PSS_ECAP with *n_out = count if cap is too
+ * small, PSS_EINVAL if the context has searched nothing. */
+pss_status pss_ctx_take_cands(pss_ctx* ctx, pss_cand* out, int64_t cap, int64_t* n_out);
 
 /* ---- candidate refinement (no counterpart in the paper, which folds) ---- */
 
@@ -339,6 +346,10 @@ pss_status pss_batch_create(int device, const pss_plan* plan, const pss_fil_desc
  * time of copy + graph.  Not thread-safe for one batch. */
 pss_status pss_batch_run(pss_batch* b, const void* data, int data_on_device, pss_cand* out, int64_t cap,
                          int64_t* n_out, double* gpu_ms);
+/* The sifted candidates of the batch's last pss_batch_run (kept after
+ * PSS_ECAP so that they need not be searched again); errors as
+ * pss_ctx_take_cands. */
+pss_status pss_batch_take_cands(pss_batch* b, pss_cand* out, int64_t cap, int64_t* n_out);
 /* Device bytes held by the batch. */
 size_t pss_batch_footprint(const pss_batch* b);
 /* Device bytes a batch for this shape will hold, computed on the host

@@ -480,6 +480,10 @@ pss_status enqueue_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* 
             pl.fV = PLANE_FFT_L - 2 * mmax + 1;
             pl.tw = (const float2*)ctx->twid.p;
             pl.twM = ctx->twid_n;
+            pl.nz = P.nz;
+            pl.zrow0 = -1;
+            for (int j = 0; j < P.nz; ++j)
+                if (-(double)cfg->zmax + (double)j * pl.dz == 0.0) pl.zrow0 = j;
         }
         {
             ProfScope ps(ctx, 4, s);
@@ -518,6 +522,20 @@ pss_status run_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil,
     tm.mark("setup");
     return enqueue_path(ctx, plan, fil, src, cfg, dm_begin, P, mode, outs, s);
 }
+
+}  // namespace
+
+pss_status take_cands(const std::vector<pss_cand>& v, pss_cand* out, int64_t cap, int64_t* n_out) {
+    *n_out = (int64_t)v.size();
+    if ((int64_t)v.size() > cap) return fail(PSS_ECAP, "output capacity too small (count in *n_out)");
+    if (!v.empty()) {
+        if (!out) return fail(PSS_EINVAL, "null output buffer");
+        memcpy(out, v.data(), v.size() * sizeof(pss_cand));
+    }
+    return PSS_OK;
+}
+
+namespace {
 
 // A kernel's bounded wait expired since the flag was last cleared: report it
 // (and clear it).
@@ -792,17 +810,20 @@ pss_status pss_search_dm_batch(pss_ctx* ctx, const pss_plan* plan, const pss_fil
     std::vector<pss_raw_cand> raw;
     PSS_TRY(search_raw_vec(ctx, plan, fil, data, data_on_device, cfg, dm_begin, dm_end, &raw,
                            ctx ? pick_stream(ctx, stream) : nullptr, false));
-    std::vector<pss_cand> v;
+    ctx->has_last = false;
+    ctx->last_cands.clear();
     HostTimer tm;
-    PSS_TRY(sift(*plan, *cfg, raw.data(), (int64_t)raw.size(), &v));
+    PSS_TRY(sift(*plan, *cfg, raw.data(), (int64_t)raw.size(), &ctx->last_cands));
     tm.mark("sift");
-    *n_out = (int64_t)v.size();
-    if ((int64_t)v.size() > cap) return fail(PSS_ECAP, "pss_search_dm_batch: output capacity too small");
-    if (!v.empty()) {
-        if (!out) return fail(PSS_EINVAL, "pss_search_dm_batch: null out");
-        memcpy(out, v.data(), v.size() * sizeof(pss_cand));
-    }
-    return PSS_OK;
+    ctx->has_last = true;
+    return take_cands(ctx->last_cands, out, cap, n_out);
+}
+
+pss_status pss_ctx_take_cands(pss_ctx* ctx, pss_cand* out, int64_t cap, int64_t* n_out) {
+    if (!ctx || !n_out) return fail(PSS_EINVAL, "pss_ctx_take_cands: null argument");
+    *n_out = 0;
+    if (!ctx->has_last) return fail(PSS_EINVAL, "pss_ctx_take_cands: the context holds no search result");
+    return take_cands(ctx->last_cands, out, cap, n_out);
 }
 
 }  // extern "C"
@@ -1051,6 +1072,8 @@ struct pss_batch {
     std::vector<uint8_t> mask;
     pss_search_cfg cfg{};
     pss::PathSetup P;
+    std::vector<pss_cand> last;  // sifted candidates of the last run
+    bool has_last = false;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     size_t footprint = 0;
@@ -1236,15 +1259,18 @@ extern "C" pss_status pss_batch_run(pss_batch* b, const void* data, int data_on_
         PSS_TRY(batch_build(b, (int64_t)cnt + 1024));
         if (attempt == 1) return fail(PSS_ECAP, "pss_batch_run: candidate buffer overflow persisted after resizing");
     }
-    std::vector<pss_cand> v;
-    PSS_TRY(sift(b->plan, b->cfg, raw.data(), (int64_t)raw.size(), &v));
-    *n_out = (int64_t)v.size();
-    if ((int64_t)v.size() > cap) return fail(PSS_ECAP, "pss_batch_run: output capacity too small");
-    if (!v.empty()) {
-        if (!out) return fail(PSS_EINVAL, "pss_batch_run: null out");
-        memcpy(out, v.data(), v.size() * sizeof(pss_cand));
-    }
-    return PSS_OK;
+    b->has_last = false;
+    b->last.clear();
+    PSS_TRY(sift(b->plan, b->cfg, raw.data(), (int64_t)raw.size(), &b->last));
+    b->has_last = true;
+    return take_cands(b->last, out, cap, n_out);
+}
+
+extern "C" pss_status pss_batch_take_cands(pss_batch* b, pss_cand* out, int64_t cap, int64_t* n_out) {
+    if (!b || !n_out) return fail(PSS_EINVAL, "pss_batch_take_cands: null argument");
+    *n_out = 0;
+    if (!b->has_last) return fail(PSS_EINVAL, "pss_batch_take_cands: the batch holds no search result");
+    return take_cands(b->last, out, cap, n_out);
 }
 
 extern "C" void pss_batch_free(pss_batch* b) {

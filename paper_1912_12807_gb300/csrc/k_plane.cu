@@ -224,113 +224,137 @@ __global__ void k_fft_templates(FftTemplateArgs a) {
 
 constexpr int FNT = 256;
 
-// padded shared-memory index: one spare slot per 8 keeps the strided
-// butterfly writes free of bank conflicts
-__device__ __forceinline__ int fp(int i) { return i + (i >> 3); }
+// Swizzled shared-memory index for 8-byte elements: within each run of 16
+// (one 128-byte line) the slot is XORed with a function of the run number,
+// chosen so that every access of the 8-8-8-4 sub-stage order (16 consecutive
+// elements; or 8 runs of 2 at stride 8; or 2 runs of 8 at stride 64) hits 16
+// different bank pairs per half-warp.
+__device__ __forceinline__ int fp(int i) {
+    const int r = i >> 4;
+    const int g = (r & 7) | ((r & 4) << 1);
+    return (i & ~15) | ((i & 15) ^ g);
+}
 
-// One in-place Stockham sub-stage of radix RR of an L-point forward FFT held
-// in shared memory (natural order in and out after all sub-stages).
-template <int L, int RR>
-__device__ __forceinline__ void fft_substage(float2* buf, const float2* tws, int ns) {
+// Twiddles of the sub-stages with running span NS: table [q][k] =
+// exp(-2 pi i q k / (RR NS)) (q-major, so lanes with consecutive k read
+// consecutive words).  Offsets of the three tables of L = 2048 = 8*8*8*4.
+constexpr int TW2 = 0;            // RR 8, NS 8:   8 x 8
+constexpr int TW3 = TW2 + 64;     // RR 8, NS 64:  8 x 64
+constexpr int TW4 = TW3 + 512;    // RR 4, NS 512: 4 x 512
+constexpr int TWN = TW4 + 2048;
+
+// One in-place Stockham sub-stage of radix RR and running span NS of two
+// L-point forward FFTs held in shared memory (natural order in and out after
+// all sub-stages); each thread runs the same butterflies on both.
+template <int L, int RR, int NS>
+__device__ __forceinline__ void fft_substage2(float2* b0, float2* b1, const float2* twt) {
     constexpr int NB = L / RR;
     constexpr int PER = NB / FNT;
-    float2 x[PER][RR];
+    float2 x0[PER][RR], x1[PER][RR];
     int dst[PER];
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
         const int b = threadIdx.x + p * FNT;
-        const int k = b & (ns - 1);
-        const int tstep = k * (L / RR / ns);
+        const int k = b & (NS - 1);
 #pragma unroll
         for (int q = 0; q < RR; ++q) {
-            x[p][q] = buf[fp(b + q * NB)];
-            if (q && k) x[p][q] = cmul(x[p][q], tws[q * tstep]);
+            x0[p][q] = b0[fp(b + q * NB)];
+            x1[p][q] = b1[fp(b + q * NB)];
+            if (NS > 1 && q) {
+                const float2 w = twt[q * NS + k];
+                x0[p][q] = cmul(x0[p][q], w);
+                x1[p][q] = cmul(x1[p][q], w);
+            }
         }
         dst[p] = (b - k) * RR + k;
     }
     __syncthreads();
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
-        dft_small<RR>(x[p]);
+        dft_small<RR>(x0[p]);
+        dft_small<RR>(x1[p]);
 #pragma unroll
-        for (int q = 0; q < RR; ++q) buf[fp(dst[p] + q * ns)] = x[p][q];
+        for (int q = 0; q < RR; ++q) {
+            b0[fp(dst[p] + q * NS)] = x0[p][q];
+            b1[fp(dst[p] + q * NS)] = x1[p][q];
+        }
     }
     __syncthreads();
 }
 
-// L = 2048 = 4 * 8 * 8 * 8
-__device__ __forceinline__ void fft2048(float2* buf, const float2* tws) {
-    fft_substage<2048, 4>(buf, tws, 1);
-    fft_substage<2048, 8>(buf, tws, 4);
-    fft_substage<2048, 8>(buf, tws, 32);
-    fft_substage<2048, 8>(buf, tws, 256);
+__device__ __forceinline__ void fft2048x2(float2* b0, float2* b1, const float2* twt) {
+    fft_substage2<2048, 8, 1>(b0, b1, twt);
+    fft_substage2<2048, 8, 8>(b0, b1, twt + TW2);
+    fft_substage2<2048, 8, 64>(b0, b1, twt + TW3);
+    fft_substage2<2048, 4, 512>(b0, b1, twt + TW4);
 }
 
-__global__ void __launch_bounds__(FNT) k_plane_fft(const __grid_constant__ PlaneArgs a) {
+__global__ void __launch_bounds__(FNT, 3) k_plane_fft(const __grid_constant__ PlaneArgs a) {
     constexpr int L = PLANE_FFT_L;
-    constexpr int PADL = L + L / 8;
+    static_assert(L == 2048, "sub-stage tables are laid out for 2048 points");
+    constexpr int PADL = L;
     constexpr int NE = L / FNT;
     extern __shared__ float2 fsm[];
-    float2* X = fsm;             // segment spectrum (kept)
-    float2* Y = fsm + PADL;      // work
-    float2* tws = fsm + 2 * PADL;
+    float2* Y0 = fsm;             // work, parity 0 (first: the segment)
+    float2* Y1 = fsm + PADL;      // work, parity 1
+    float2* twt = fsm + 2 * PADL;
     const int b = blockIdx.y;
     const int64_t M = a.nfft / 2;
     const int V = a.fV, M0 = a.fM0;
     const int64_t k0 = (int64_t)blockIdx.x * V;
     const float2* Ap = a.spec + (int64_t)b * a.spec_stride;
-    const int64_t tstride = a.twM / L;
-    for (int t = threadIdx.x; t < L; t += FNT) tws[t] = a.tw[t * tstride];
+    const int64_t tstride = a.twM / L;  // global table: exp(-2 pi i t / twM)
+    for (int i = threadIdx.x; i < TWN; i += FNT) {
+        int rr, ns, o;
+        if (i < TW3) { rr = 8; ns = 8; o = i - TW2; }
+        else if (i < TW4) { rr = 8; ns = 64; o = i - TW3; }
+        else { rr = 4; ns = 512; o = i - TW4; }
+        const int q = o / ns, k = o - q * ns;
+        twt[i] = a.tw[(int64_t)(q * k * (L / (rr * ns))) * tstride];
+    }
     for (int i = threadIdx.x; i < L; i += FNT) {
         const int64_t k = k0 - M0 + i;
-        X[fp(i)] = (k >= 0 && k < M) ? Ap[k] : make_float2(0.f, 0.f);
+        Y0[fp(i)] = (k >= 0 && k < M) ? Ap[k] : make_float2(0.f, 0.f);
+        Y1[fp(i)] = make_float2(0.f, 0.f);
     }
     __syncthreads();
-    fft2048(X, tws);
-    const int nz = (int)llround(2.0 * a.zmax / a.dz) + 1;
+    fft2048x2(Y0, Y1, twt);  // the segment's spectrum (the second transform is idle)
+    float2 X[NE];            // each thread keeps the bins it multiplies
+#pragma unroll
+    for (int e = 0; e < NE; ++e) X[e] = Y0[fp(threadIdx.x + e * FNT)];
+    __syncthreads();
+    const int nz = a.nz;
     float2* P = reinterpret_cast<float2*>(a.plane + (int64_t)b * a.plane_stride);
     for (int j = 0; j < nz; ++j) {
-        const bool zrow0 = (-(double)a.zmax + (double)j * a.dz == 0.0);
-        float pw[2][NE];
+        const bool zrow0 = (j == a.zrow0);
+        const float2* T0 = a.ftaps + (int64_t)j * 2 * L;
+        const float2* T1 = T0 + L;
 #pragma unroll
-        for (int par = 0; par < 2; ++par) {
-            if (par == 0 && zrow0) {
-                // integer half-bins of the z = 0 row: the raw powers, exactly
-#pragma unroll
-                for (int e = 0; e < NE; ++e) {
-                    const int u = threadIdx.x + e * FNT;
-                    const int64_t k = k0 + u;
-                    pw[0][e] = 0.f;
-                    if (u < V && k < M) {
-                        const float2 c = Ap[k];
-                        pw[0][e] = c.x * c.x + c.y * c.y;
-                    }
-                }
-                continue;
-            }
-            const float2* T = a.ftaps + ((int64_t)j * 2 + par) * L;
-#pragma unroll
-            for (int e = 0; e < NE; ++e) {
-                const int i = threadIdx.x + e * FNT;
-                const float2 y = cmul(X[fp(i)], __ldg(T + i));
-                Y[fp(i)] = make_float2(y.x, -y.y);
-            }
-            __syncthreads();
-            fft2048(Y, tws);
-#pragma unroll
-            for (int e = 0; e < NE; ++e) {
-                const float2 y = Y[fp(threadIdx.x + e * FNT)];
-                pw[par][e] = y.x * y.x + y.y * y.y;
-            }
-            __syncthreads();
+        for (int e = 0; e < NE; ++e) {
+            const int i = threadIdx.x + e * FNT;
+            const float2 y0 = cmul(X[e], __ldg(T0 + i)), y1 = cmul(X[e], __ldg(T1 + i));
+            Y0[fp(i)] = make_float2(y0.x, -y0.y);
+            Y1[fp(i)] = make_float2(y1.x, -y1.y);
         }
+        __syncthreads();
+        fft2048x2(Y0, Y1, twt);
         float2* row = P + (int64_t)j * M;
 #pragma unroll
         for (int e = 0; e < NE; ++e) {
             const int u = threadIdx.x + e * FNT;
             const int64_t k = k0 + u;
-            if (u < V && k < M) row[k] = make_float2(pw[0][e], pw[1][e]);
+            if (u < V && k < M) {
+                const float2 y0 = Y0[fp(u)], y1 = Y1[fp(u)];
+                float p0 = y0.x * y0.x + y0.y * y0.y;
+                if (zrow0) {
+                    // integer half-bins of the z = 0 row: the raw powers, exactly
+                    const float2 c = Ap[k];
+                    p0 = c.x * c.x + c.y * c.y;
+                }
+                row[k] = make_float2(p0, y1.x * y1.x + y1.y * y1.y);
+            }
         }
+        __syncthreads();
     }
 }
 
@@ -361,8 +385,7 @@ cudaError_t launch_plane(const PlaneArgs& a, cudaStream_t s) {
     const int nz = a.zmax ? (int)llround(2.0 * a.zmax / a.dz) + 1 : 1;
     if (a.ftaps) {
         if (a.fL != PLANE_FFT_L || a.fV <= 0 || a.twM % PLANE_FFT_L) return cudaErrorInvalidValue;
-        constexpr int PADL = PLANE_FFT_L + PLANE_FFT_L / 8;
-        const size_t shm = (size_t)(2 * PADL + PLANE_FFT_L) * sizeof(float2);
+        const size_t shm = (size_t)(2 * PLANE_FFT_L + TWN) * sizeof(float2);
         cudaError_t e = allow_smem((const void*)k_plane_fft, shm);
         if (e != cudaSuccess) return e;
         dim3 grid((unsigned)((M + a.fV - 1) / a.fV), (unsigned)a.nb);

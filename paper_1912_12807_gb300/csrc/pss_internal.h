@@ -97,6 +97,9 @@ void bucket_by_dm(const pss_raw_cand* raw, int64_t n, int64_t ndm, std::vector<i
 // Sort raw detections by (dm_idx, numharm, j, h) in place.
 void sort_raw(std::vector<pss_raw_cand>* v, int64_t ndm);
 
+// Copy a kept candidate list to a caller's buffer (PSS_ECAP if it does not fit).
+pss_status take_cands(const std::vector<pss_cand>& v, pss_cand* out, int64_t cap, int64_t* n_out);
+
 // ---- sift (host) ----------------------------------------------------------
 pss_status sift(const Plan& P, const pss_search_cfg& cfg, const pss_raw_cand* raw, int64_t n,
                 std::vector<pss_cand>* out);
@@ -141,6 +144,9 @@ struct Ctx {
     int32_t tap_zmax = -1, tap_extra = -1;
     double tap_dz = 0.0;
     bool ftap_ok = false;  // ftaps hold the spectra of the current templates
+    // sifted candidates of the last whole-file search (pss_ctx_take_cands)
+    std::vector<pss_cand> last_cands;
+    bool has_last = false;
     // per-stage event timing (pss_ctx_profile)
     bool prof_on = false;
     struct ProfRec {
@@ -248,6 +254,7 @@ struct PlaneArgs {
     // taps, [nz][2][fL]; null when the direct form is used
     const float2* ftaps;
     int32_t fL, fV, fM0;     // segment length, valid outputs per segment, lead
+    int32_t nz, zrow0;       // rows, and the row with z = 0 exactly (-1: none)
     const float2* tw;        // exp(-2 pi i t / twM)
     int64_t twM;
 };

@@ -242,7 +242,7 @@ struct pss_server {
                         pss_batch_run(slot.batch, r->bytes(), 0, buf.data(), (int64_t)buf.size(), &n, nullptr);
                     if (st == PSS_ECAP) {
                         buf.resize((size_t)n);
-                        st = pss_batch_run(slot.batch, r->bytes(), 0, buf.data(), (int64_t)buf.size(), &n, nullptr);
+                        st = pss_batch_take_cands(slot.batch, buf.data(), (int64_t)buf.size(), &n);
                     }
                     if (st != PSS_OK) {
                         res->status = st;

@@ -63,7 +63,8 @@ EXPORTS = ["pss_ctx_create", "pss_ctx_destroy", "pss_last_error", "pss_version",
            "pss_search_raw", "pss_sift", "pss_search_dm_batch", "pss_response", "pss_sigma_of_power",
            "pss_power_threshold", "pss_ctx_profile", "pss_ctx_profile_read", "pss_dedisperse_noalloc",
            "pss_refine_prepare", "pss_refine_eval", "pss_refine_candidates", "pss_batch_create", "pss_batch_run",
-           "pss_batch_footprint", "pss_batch_free", "pss_search_footprint", "pss_server_create", "pss_submit_file", "pss_poll",
+           "pss_batch_footprint", "pss_batch_free", "pss_search_footprint", "pss_ctx_take_cands",
+           "pss_batch_take_cands", "pss_server_create", "pss_submit_file", "pss_poll",
            "pss_result_cands", "pss_result_free", "pss_server_stats", "pss_server_destroy"]
 PROFILE_STAGES = ["unpack", "dedisperse", "fft", "whiten", "plane", "harmsum"]
 
@@ -109,6 +110,8 @@ def lib():
         "pss_batch_run": (st, [vp, vp, C.c_int, vp, i64, P(i64), P(C.c_double)]),
         "pss_batch_footprint": (C.c_size_t, [vp]),
         "pss_batch_free": (None, [vp]),
+        "pss_ctx_take_cands": (st, [vp, vp, i64, P(i64)]),
+        "pss_batch_take_cands": (st, [vp, vp, i64, P(i64)]),
         "pss_search_footprint": (st, [vp, P(pss_fil_desc), P(pss_search_cfg), P(C.c_size_t)]),
         "pss_server_create": (st, [C.c_int, C.c_size_t, C.c_int, P(vp)]),
         "pss_submit_file": (st, [vp, P(pss_fil_desc), vp, P(pss_dd_stage), C.c_int, P(pss_search_cfg),
@@ -361,15 +364,14 @@ def pss_search_dm_batch(ctx: Context, plan: Plan, data, cfg: pss_search_cfg, dm_
                         cap: int = 1 << 14, stream=None) -> np.ndarray:
     p, dev, keep = _data_arg(data)
     n = C.c_int64()
-    while True:
-        out = np.zeros(cap, dtype=CAND_DTYPE)
-        st = lib().pss_search_dm_batch(ctx.h, plan.h, C.byref(plan.desc.c), p, dev, C.byref(cfg), dm_begin, dm_end,
-                                       out.ctypes.data, cap, C.byref(n), _stream(stream))
-        if st == PSS_ECAP:
-            cap = n.value
-            continue
-        _check(st)
-        return out[: n.value]
+    out = np.zeros(cap, dtype=CAND_DTYPE)
+    st = lib().pss_search_dm_batch(ctx.h, plan.h, C.byref(plan.desc.c), p, dev, C.byref(cfg), dm_begin, dm_end,
+                                   out.ctypes.data, cap, C.byref(n), _stream(stream))
+    if st == PSS_ECAP:  # the context kept the list: fetch it without searching again
+        out = np.zeros(n.value, dtype=CAND_DTYPE)
+        st = lib().pss_ctx_take_cands(ctx.h, out.ctypes.data, n.value, C.byref(n))
+    _check(st)
+    return out[: n.value]
 
 
 class Batch:
@@ -393,15 +395,13 @@ class Batch:
             import torch
             torch.cuda.current_stream().synchronize()
         n, ms = C.c_int64(), C.c_double()
-        while True:
-            out = np.zeros(cap, dtype=CAND_DTYPE)
-            st = lib().pss_batch_run(self.h, p, dev, out.ctypes.data, cap, C.byref(n),
-                                     C.byref(ms) if timing else None)
-            if st == PSS_ECAP:
-                cap = n.value
-                continue
-            _check(st)
-            return (out[: n.value], ms.value) if timing else out[: n.value]
+        out = np.zeros(cap, dtype=CAND_DTYPE)
+        st = lib().pss_batch_run(self.h, p, dev, out.ctypes.data, cap, C.byref(n), C.byref(ms) if timing else None)
+        if st == PSS_ECAP:  # the batch kept the list: fetch it without searching again
+            out = np.zeros(n.value, dtype=CAND_DTYPE)
+            st = lib().pss_batch_take_cands(self.h, out.ctypes.data, n.value, C.byref(n))
+        _check(st)
+        return (out[: n.value], ms.value) if timing else out[: n.value]
 
     def close(self):
         if self.h:

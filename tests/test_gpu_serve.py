@@ -159,3 +159,26 @@ def test_server_poll_states_and_bad_requests(L, ctx):
             srv.poll(t, timeout_ms=0)
         assert e.value.status == L.PSS_EINVAL
     srv.close()
+
+
+def test_take_cands_after_ecap_needs_no_second_search(L, ctx):
+    import ctypes as C
+    a = _case_a(1001)
+    ref = _alone(L, ctx, a)
+    assert ref.shape[0] > 1
+    plan = L.Plan(L.FilDesc.of(a.fil), a.stages)
+    cfg = L.cfg_of(a.cfg)
+    one = np.zeros(1, dtype=L.CAND_DTYPE)
+    n = C.c_int64()
+    st = L.lib().pss_search_dm_batch(ctx.h, plan.h, C.byref(plan.desc.c), C.c_void_p(a.fil.data.ctypes.data), 0,
+                                     C.byref(cfg), 0, plan.ndm, one.ctypes.data, 1, C.byref(n), None)
+    assert st == L.PSS_ECAP and n.value == ref.shape[0]
+    out = np.zeros(n.value, dtype=L.CAND_DTYPE)
+    assert L.lib().pss_ctx_take_cands(ctx.h, out.ctypes.data, n.value, C.byref(n)) == L.PSS_OK
+    assert _same(out, ref)
+    b = L.Batch(plan, cfg)
+    assert _same(b.run(a.fil.data, cap=1), ref)
+    b.close()
+    fresh = L.Context(0)
+    assert L.lib().pss_ctx_take_cands(fresh.h, out.ctypes.data, n.value, C.byref(n)) == L.PSS_EINVAL
+    fresh.close()
