@@ -10,9 +10,11 @@
 #include <math.h>
 
 #include <stdint.h>
+#include <stdio.h>
 #include <stdlib.h>
 
 #include <algorithm>
+#include <chrono>
 #include <numeric>
 #include <vector>
 
@@ -99,17 +101,36 @@ Groups link_groups(const std::vector<Item>& it, double /*dz*/) {
     }
     auto fdiv = [](int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); };
     std::vector<int> order(n);
-    std::iota(order.begin(), order.end(), 0);
     std::vector<int64_t> cr(n), cz(n);
+    int64_t cr0 = INT64_MAX, cr1 = INT64_MIN, cz0 = INT64_MAX, cz1 = INT64_MIN;
     for (int i = 0; i < n; ++i) {
         cr[i] = fdiv(it[i].kr, 64);
         cz[i] = fdiv(it[i].kz, 32);
+        cr0 = std::min(cr0, cr[i]);
+        cr1 = std::max(cr1, cr[i]);
+        cz0 = std::min(cz0, cz[i]);
+        cz1 = std::max(cz1, cz[i]);
     }
-    std::sort(order.begin(), order.end(), [&](int a, int b) {
-        if (cr[a] != cr[b]) return cr[a] < cr[b];
-        if (cz[a] != cz[b]) return cz[a] < cz[b];
-        return a < b;
-    });
+    // order by (cell r, cell z, index): one packed 64-bit key when the ranges fit
+    int bz = 1, bi = 1;
+    while ((int64_t(1) << bz) <= cz1 - cz0) ++bz;
+    while ((int64_t(1) << bi) < n) ++bi;
+    int br = 1;
+    while (n > 0 && (int64_t(1) << br) <= cr1 - cr0) ++br;
+    if (n > 0 && br + bz + bi <= 63) {
+        std::vector<uint64_t> key(n);
+        for (int i = 0; i < n; ++i)
+            key[i] = ((uint64_t)(cr[i] - cr0) << (bz + bi)) | ((uint64_t)(cz[i] - cz0) << bi) | (uint64_t)i;
+        std::sort(key.begin(), key.end());
+        for (int p = 0; p < n; ++p) order[p] = (int)(key[p] & ((uint64_t(1) << bi) - 1));
+    } else {
+        std::iota(order.begin(), order.end(), 0);
+        std::sort(order.begin(), order.end(), [&](int a, int b) {
+            if (cr[a] != cr[b]) return cr[a] < cr[b];
+            if (cz[a] != cz[b]) return cz[a] < cz[b];
+            return a < b;
+        });
+    }
     std::vector<Cell> cells;
     for (int p = 0; p < n;) {
         int q = p;
@@ -129,20 +150,20 @@ Groups link_groups(const std::vector<Item>& it, double /*dz*/) {
     const int nc = (int)cells.size();
     std::vector<int> par(nc);
     std::iota(par.begin(), par.end(), 0);
-    auto find_cell = [&](int64_t r, int64_t z) -> int {
-        int lo = 0, hi = nc;
-        while (lo < hi) {
-            const int mid = (lo + hi) / 2;
-            if (cells[mid].cr < r || (cells[mid].cr == r && cells[mid].cz < z)) lo = mid + 1;
-            else hi = mid;
-        }
-        return (lo < nc && cells[lo].cr == r && cells[lo].cz == z) ? lo : -1;
-    };
-    const int64_t nb[4][2] = {{0, 1}, {1, -1}, {1, 0}, {1, 1}};
+    // forward neighbours (cr, cz+1), (cr+1, cz-1), (cr+1, cz), (cr+1, cz+1):
+    // cells are sorted by (cr, cz), so a cursor into row cr+1 only moves forward
+    int cur = 0;
     for (int a = 0; a < nc; ++a) {
         const Cell& A = cells[a];
-        for (auto& d : nb) {
-            const int b = find_cell(A.cr + d[0], A.cz + d[1]);
+        int nbr[4] = {-1, -1, -1, -1};
+        if (a + 1 < nc && cells[a + 1].cr == A.cr && cells[a + 1].cz == A.cz + 1) nbr[0] = a + 1;
+        if (cur < a + 1) cur = a + 1;
+        while (cur < nc && (cells[cur].cr < A.cr + 1 || (cells[cur].cr == A.cr + 1 && cells[cur].cz < A.cz - 1))) ++cur;
+        for (int c = cur, d = 1; c < nc && cells[c].cr == A.cr + 1 && cells[c].cz <= A.cz + 1; ++c) {
+            d = (int)(cells[c].cz - A.cz) + 2;  // 1, 2, 3
+            nbr[d] = c;
+        }
+        for (int b : nbr) {
             if (b < 0) continue;
             const Cell& B = cells[b];
             if (find_root(par, a) == find_root(par, b)) continue;
@@ -274,12 +295,27 @@ pss_status sift(const Plan& P, const pss_search_cfg& cfg, const pss_raw_cand* ra
         if (raw[i].dm_idx < 0 || raw[i].dm_idx >= P.ndm()) return fail(PSS_EINVAL, "pss_sift: dm_idx out of range");
         if (raw[i].numharm < 1 || raw[i].numharm > 32 || (raw[i].numharm & (raw[i].numharm - 1))) return fail(PSS_EINVAL, "pss_sift: numharm must be a power of two in [1, 32]");
     }
+    const bool dbg = getenv("PSS_TIMING") != nullptr;  // phase times on stderr
+    auto t0 = std::chrono::steady_clock::now();
+    auto lap = [&](const char* what) {
+        if (!dbg) return;
+        auto t1 = std::chrono::steady_clock::now();
+        fprintf(stderr, "[pss] sift.%-10s %8.3f ms\n", what, std::chrono::duration<double, std::milli>(t1 - t0).count());
+        t0 = t1;
+    };
     std::vector<int64_t> order;
     std::vector<std::pair<int64_t, int64_t>> bk;
     bucket_by_dm(raw, n, P.ndm(), &order, &bk);
-    // within each DM trial (independent: in parallel)
+    lap("bucket");
+    // within each DM trial (independent: in parallel, largest trials first)
     std::vector<std::vector<Item>> surv(bk.size());
-    parallel_for((int64_t)bk.size(), 4, [&](int64_t b) {
+    std::vector<int64_t> by_size(bk.size());
+    std::iota(by_size.begin(), by_size.end(), 0);
+    std::stable_sort(by_size.begin(), by_size.end(), [&](int64_t x, int64_t y) {
+        return bk[(size_t)x].second - bk[(size_t)x].first > bk[(size_t)y].second - bk[(size_t)y].first;
+    });
+    parallel_for((int64_t)bk.size(), 1, [&](int64_t bi) {
+        const int64_t b = by_size[(size_t)bi];
         std::vector<Item> items;
         items.reserve((size_t)(bk[(size_t)b].second - bk[(size_t)b].first));
         for (int64_t q = bk[(size_t)b].first; q < bk[(size_t)b].second; ++q) {
@@ -305,9 +341,12 @@ pss_status sift(const Plan& P, const pss_search_cfg& cfg, const pss_raw_cand* ra
     });
     std::vector<Item> survivors;
     for (auto& v : surv) survivors.insert(survivors.end(), v.begin(), v.end());
+    lap("within");
+    if (dbg) fprintf(stderr, "[pss] sift: %lld raw, %zu survive their trial\n", (long long)n, survivors.size());
 
     // across DM trials
     const Groups G = link_groups(survivors, dz);
+    lap("link");
     for (int g = 0; g < G.count(); ++g) {
         const int* mem = G.members.data() + G.start[g];
         const int nm = G.start[g + 1] - G.start[g];
@@ -332,6 +371,7 @@ pss_status sift(const Plan& P, const pss_search_cfg& cfg, const pss_raw_cand* ra
         c.j = b.j;
         out->push_back(c);
     }
+    lap("reps");
     std::sort(out->begin(), out->end(), [](const pss_cand& a, const pss_cand& b) {
         if (a.dm_idx != b.dm_idx) return a.dm_idx < b.dm_idx;
         if (a.numharm != b.numharm) return a.numharm < b.numharm;
