@@ -292,10 +292,12 @@ constexpr int REG_NT = 128;
 
 template <int NSTAGES, int R>
 __global__ void __launch_bounds__(REG_NT) k_harm_reg(const __grid_constant__ HarmArgs a) {
+    // blocks of consecutive launch order take the same h range of successive
+    // rows, so the harmonic rows they read overlap while they are in L2
     const int lane = threadIdx.x & 31;
-    const int j = blockIdx.y;
+    const int j = blockIdx.x;
     const int b = blockIdx.z;
-    const int hw = (blockIdx.x * (REG_NT / 32) + (threadIdx.x >> 5)) * 32 * R;
+    const int hw = (blockIdx.y * (REG_NT / 32) + (threadIdx.x >> 5)) * 32 * R;
     const float* P = a.plane + (int64_t)b * a.plane_stride;
     float acc[R];
     const float* row = P + j * (int)a.nfft;
@@ -306,7 +308,7 @@ __global__ void __launch_bounds__(REG_NT) k_harm_reg(const __grid_constant__ Har
 
 template <int R>
 cudaError_t launch_reg(const HarmArgs& a, cudaStream_t s) {
-    dim3 grid((unsigned)(a.nfft / (REG_NT * R)), (unsigned)a.nz, (unsigned)a.nb);
+    dim3 grid((unsigned)a.nz, (unsigned)(a.nfft / (REG_NT * R)), (unsigned)a.nb);
     switch (a.nstages) {
         case 1: k_harm_reg<1, R><<<grid, REG_NT, 0, s>>>(a); break;
         case 2: k_harm_reg<2, R><<<grid, REG_NT, 0, s>>>(a); break;
@@ -324,7 +326,8 @@ cudaError_t launch_harm(const HarmArgs& a, cudaStream_t s) {
     if (a.nfft > (int64_t(1) << 24) || a.nstages > 6) return cudaErrorInvalidValue;
     if ((int64_t)a.nz * a.nfft > (int64_t(1) << 31)) return cudaErrorInvalidValue;  // 32-bit plane offsets
     // register-blocked kernel: up to 16 harmonics, whole warps of 32 x 16 points
-    if (a.nstages <= 5 && a.nfft % (REG_NT * 16) == 0 && a.nz <= 65535) return launch_reg<16>(a, s);
+    if (a.nstages <= 5 && a.nfft % (REG_NT * 16) == 0 && a.nfft / (REG_NT * 16) <= 65535 && a.nb <= 65535)
+        return launch_reg<16>(a, s);
     if (a.nz == 1) return launch_variant<1, 2048, true>(a, s);
     return launch_variant<4, 256, false>(a, s);
 }

@@ -220,6 +220,30 @@ def make_8bit(nchan: int, nsamp: int, tsamp: float, lo: float, hi: float,
                       list(pulsars), tuple(rfi_chans), burst_t_s)
 
 
+def make_8bit_chunked(nchan: int, nsamp: int, tsamp: float, lo: float, hi: float,
+                      pulsars: Sequence[Pulsar], seed: int, chunk: int = 1 << 15) -> Filterbank:
+    """The make_8bit recipe (noise clip(round_half_even(128 + 16 g)) plus
+    dispersed pulses) generated in FP32 blocks of `chunk` samples, for files
+    too large to hold in FP64 at once (the noise realisation differs from
+    make_8bit's for the same seed)."""
+    rng = np.random.default_rng(seed)
+    fch0, foff = band(lo, hi, nchan)
+    freqs = fch0 + np.arange(nchan) * foff
+    f_top = float(freqs.max())
+    t_span = nsamp * tsamp
+    out = np.empty((nsamp, nchan), dtype=np.uint8)
+    dl = [_sim_delay_s(p.dm, freqs, f_top) for p in pulsars]
+    for s0 in range(0, nsamp, chunk):
+        s1 = min(nsamp, s0 + chunk)
+        x = rng.standard_normal((s1 - s0, nchan), dtype=np.float32)
+        for p, d in zip(pulsars, dl):
+            _inject(x, s0, tsamp, p, d, t_span, p.amp)
+        np.rint(x * 16.0 + 128.0, out=x)
+        np.clip(x, 0, 255, out=x)
+        out[s0:s1] = x.astype(np.uint8)
+    return Filterbank(nchan, nsamp, tsamp, fch0, foff, 8, out, list(pulsars))
+
+
 def make_1bit(nchan: int, nsamp: int, tsamp: float, lo: float, hi: float,
               pulsars: Sequence[Pulsar], seed: int, chunk: int = 1 << 18,
               ) -> Filterbank:
@@ -343,6 +367,6 @@ def stream_files(n_files: int = 64, seed0: int = 5000, mean_gap_s: float = 26.0,
         npsr = int(rng.integers(0, 4))
         prng = np.random.default_rng(seed0 + f + 100000)
         psrs = _drift_pulsars(prng, npsr, nchan, nsamp)
-        fil = make_8bit(nchan, nsamp, 2e-4, 1050.0, 1450.0, psrs, seed0 + f)
+        fil = make_8bit_chunked(nchan, nsamp, 2e-4, 1050.0, 1450.0, psrs, seed0 + f)
         yield t, Workload("stream_file_%d" % f, fil, [Stage(0.0, 1.0, 501, 1)],
                           SearchCfg(zmax=100, dz=2.0, numharm=8))
