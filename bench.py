@@ -493,17 +493,101 @@ def run_served(pss, name, wl, args, device):
             "budget_gib": args.serve_budget_gib}
 
 
+def run_stream(args, rank, world, local_rank):
+    """Mixed-shape drift-scan stream (128-1024 channels, 2^17-2^19 samples,
+    0-3 pulsars, DM 0-500 step 1, zmax 100, numharm 8; Poisson arrivals with
+    a 26 s mean replayed faster by --stream-speedup): the plain per-file loop
+    (pss_search_dm_batch on host data, one file after another), then the
+    request loop (pss_server) saturated (all files queued at once) and paced
+    at the replayed arrival times, with submit-to-result latencies."""
+    import numpy as np
+    import torch
+
+    from paper_1912_12807_gb300 import pss, synth
+    if rank != 0:
+        return
+    torch.cuda.set_device(local_rank)
+    t0 = time.perf_counter()
+    files = list(synth.stream_files(args.stream_files, speedup=args.stream_speedup))
+    t_gen = time.perf_counter() - t0
+    ndm = int(sum(st.n_dm for st in files[0][1].stages))
+    shapes = sorted({(w.fil.nchan, w.fil.nsamp) for _, w in files})
+    descs = [pss.FilDesc.of(w.fil) for _, w in files]
+    cfg = pss.cfg_of(files[0][1].cfg)
+    stages = files[0][1].stages
+    # plain loop: one context, one file after another (each shape warmed once first)
+    ctx = pss.Context(local_rank)
+    plans = {}
+    for (_, w), d in zip(files, descs):
+        key = (w.fil.nchan, w.fil.nsamp)
+        if key not in plans:
+            plans[key] = pss.Plan(d, stages)
+            pss.pss_search_dm_batch(ctx, plans[key], w.fil.data, cfg, 0, ndm)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n_plain = 0
+    for (_, w) in files:
+        c = pss.pss_search_dm_batch(ctx, plans[(w.fil.nchan, w.fil.nsamp)], w.fil.data, cfg, 0, ndm)
+        n_plain += len(c)
+    t_plain = time.perf_counter() - t0
+    ctx.close()
+    budget = int(args.serve_budget_gib * (1 << 30))
+    # served, saturated: every file queued at once (after one warm pass that prepares the batches)
+    srv = pss.Server(budget, max_slots=args.serve_slots, device=local_rank)
+    for t in [srv.submit(d, w.fil.data, stages, cfg) for (_, w), d in zip(files, descs)]:
+        srv.poll(t)
+    t0 = time.perf_counter()
+    ts = [srv.submit(d, w.fil.data, stages, cfg) for (_, w), d in zip(files, descs)]
+    n_served = sum(len(srv.poll(t)[0]) for t in ts)
+    t_sat = time.perf_counter() - t0
+    # served, paced at the replayed arrival times
+    tick = time.perf_counter()
+    pending = []
+    for (ta, w), d in zip(files, descs):
+        while time.perf_counter() < tick + ta:
+            time.sleep(0.001)
+        pending.append(srv.submit(d, w.fil.data, stages, cfg))
+    lat = sorted(srv.poll(t)[1] for t in pending)
+    t_paced = time.perf_counter() - tick
+    srv.close()
+    clocks.stop()
+    pct = lambda q: lat[max(0, math.ceil(q / 100.0 * len(lat)) - 1)]
+    n = len(files)
+    value = n * ndm / t_sat
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": n, "warmup": n,
+            "ms_per_step": 1e3 * t_sat / n, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "i32+f32", "data": "synthetic",
+            "config": {"workload": "stream_%dfiles_128-1024ch_2^17-2^19_dm0-500x1_zmax100_numharm8" % n,
+                       "files": n, "shapes": [list(x) for x in shapes], "dm_trials_per_file": ndm,
+                       "zmax": cfg.zmax, "numharm": cfg.numharm, "arrival_mean_s": 26.0,
+                       "replay_speedup": args.stream_speedup, "slots": args.serve_slots,
+                       "budget_gib": args.serve_budget_gib, "input": "host memory (copied at submit)"},
+            "files_per_s": n / t_sat, "realtime_factor": REALTIME_S * n / t_sat,
+            "plain": {"value": n * ndm / t_plain, "unit": UNIT, "files_per_s": n / t_plain,
+                      "s_per_file": t_plain / n},
+            "served_saturated": {"value": value, "unit": UNIT, "files_per_s": n / t_sat, "s_per_file": t_sat / n},
+            "served_paced": {"p50_ms": 1e3 * pct(50), "p99_ms": 1e3 * pct(99), "max_ms": 1e3 * lat[-1],
+                             "wall_s": t_paced, "realtime_budget_s": REALTIME_S},
+            "candidates": {"plain": n_plain, "served": n_served},
+            "clocks": clocks.summary(), "generation_s": t_gen}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="driftscan", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="driftscan", choices=sorted(WORKLOADS) + ["stream"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the batched and served measurements")
     ap.add_argument("--serve-slots", type=int, default=2)
     ap.add_argument("--serve-budget-gib", type=float, default=64.0)
+    ap.add_argument("--stream-files", type=int, default=64)
+    ap.add_argument("--stream-speedup", type=float, default=50.0)
     ap.add_argument("--dm-trials", type=int, default=None,
                     help="DM trials of a single-stage plan (driftscan/accel); smaller values make profiling cases")
     args = ap.parse_args()
@@ -512,6 +596,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.workload == "stream":
+        run_stream(args, rank, world, local_rank)
         return
     run_ours(args, rank, world, local_rank)
 

@@ -365,10 +365,11 @@ void pss_batch_free(pss_batch* b);
  * ~26 s and must each be searched within that budget, Sect. 1).  Up to
  * max_slots files are in flight at once, each on its own stream and batch
  * (kernels of different files overlap on the device); a queued file is
- * admitted when a slot is free and its device footprint fits in what is
- * left of hbm_budget_bytes (FIFO; a file larger than the whole budget fails
- * with PSS_ENOMEM).  Slots keep their prepared batch for the next file of
- * the same shape.  Thread-safe. */
+ * admitted, FIFO, when a slot is free and either an idle prepared batch of
+ * its shape exists or its device footprint (pss_search_footprint) fits in
+ * what is left of hbm_budget_bytes, least recently used idle batches of
+ * other shapes being freed to make room (a file larger than the whole
+ * budget fails with PSS_ENOMEM).  Thread-safe. */
 typedef struct pss_server pss_server;
 typedef struct pss_result pss_result;
 pss_status pss_server_create(int device, size_t hbm_budget_bytes, int max_slots, pss_server** out);

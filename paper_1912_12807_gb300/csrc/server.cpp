@@ -4,13 +4,15 @@
 // must each be searched within that time (Sect. 1); on CPUs it keeps up by
 // running up to a "parallel number" of PRESTO processes at once and starting
 // a new one as soon as a slot frees (its V3 scheme, Sect. 2).  Here each of
-// max_slots worker threads owns a slot: a prepared, graph-captured search
-// (pss_batch) on its own stream.  A queued file is admitted, in arrival
-// order, as soon as a slot is idle and the file's device footprint fits in
-// what is left of the budget; the kernels of the files in flight overlap on
-// the GPU and each slot sifts its file on the host while the others compute.
-// A slot keeps its batch for the next file of the same shape; an idle slot
-// drops its batch when the file at the head of the queue needs the memory.
+// max_slots worker threads is a slot that runs one file at a time through a
+// prepared, graph-captured search (pss_batch, its own stream).  A queued
+// file is admitted in arrival order as soon as a slot is free: it reuses an
+// idle prepared batch of its shape (descriptor, plan, search parameters) if
+// there is one, otherwise a new batch is prepared when the file's estimated
+// device footprint fits in what is left of the budget, evicting least
+// recently used idle batches of other shapes to make room.  The kernels of
+// the files in flight overlap on the GPU, and each slot sifts its file on
+// the host while the others compute.
 #include <math.h>
 
 #include <algorithm>
@@ -134,10 +136,12 @@ std::string shape_key(const pss_fil_desc& f, const std::vector<uint8_t>& mask, c
     return o.str();
 }
 
-struct Slot {
-    pss_batch* batch = nullptr;
+// A prepared batch not in use, with the time it was last used.
+struct Idle {
+    pss_batch* batch;
     std::string key;
-    size_t held = 0;  // bytes accounted to this slot's batch
+    size_t bytes;
+    uint64_t stamp;
 };
 
 }  // namespace
@@ -157,7 +161,8 @@ struct pss_server {
     uint64_t next_ticket = 1;
     size_t in_use = 0;
     bool stop = false;
-    std::vector<Slot> slots;
+    std::vector<Idle> idle;  // prepared batches no slot is using (any shape)
+    uint64_t clock = 0;
     std::vector<std::thread> workers;
     std::vector<double> latencies;
 
@@ -170,79 +175,94 @@ struct pss_server {
         cv_work.notify_all();
     }
 
-    void worker(int si) {
-        Slot& slot = slots[si];
+    // Admission of the file at the head of the queue (FIFO), under `mu`:
+    // reuse an idle batch of its shape; else prepare a new one if its
+    // estimated footprint fits in what is left of the budget; else free the
+    // least recently used idle batch and try again; else wait for a running
+    // file to finish.  Returns the request, with *batch set when one was
+    // reused (and *reserved = bytes set aside for a new batch otherwise).
+    Request* admit(std::unique_lock<std::mutex>& lk, pss_batch** batch, size_t* reserved) {
+        while (!stop) {
+            if (queue.empty()) {
+                cv_work.wait(lk);
+                continue;
+            }
+            Request* h = queue.front();
+            if (h->estimate > budget) {
+                queue.pop_front();
+                lk.unlock();
+                pss_result* res = new pss_result();
+                res->status = PSS_ENOMEM;
+                res->err = "file needs more device memory than the server budget";
+                finish(h, res);
+                delete h;
+                lk.lock();
+                continue;
+            }
+            for (size_t i = 0; i < idle.size(); ++i)
+                if (idle[i].key == h->key) {
+                    *batch = idle[i].batch;
+                    *reserved = 0;
+                    idle.erase(idle.begin() + (long)i);
+                    queue.pop_front();
+                    return h;
+                }
+            if (in_use + h->estimate <= budget) {
+                in_use += h->estimate;
+                *batch = nullptr;
+                *reserved = h->estimate;
+                queue.pop_front();
+                return h;
+            }
+            if (!idle.empty()) {
+                size_t lru = 0;
+                for (size_t i = 1; i < idle.size(); ++i)
+                    if (idle[i].stamp < idle[lru].stamp) lru = i;
+                Idle v = idle[lru];
+                idle.erase(idle.begin() + (long)lru);
+                in_use -= v.bytes;
+                lk.unlock();
+                pss_batch_free(v.batch);
+                lk.lock();
+                continue;
+            }
+            cv_work.wait(lk);
+        }
+        return nullptr;
+    }
+
+    void worker(int) {
         cudaSetDevice(device);
         std::unique_lock<std::mutex> lk(mu);
         for (;;) {
-            Request* r = nullptr;
-            while (!stop) {
-                if (!queue.empty()) {
-                    Request* h = queue.front();
-                    if (h->estimate > budget) {
-                        queue.pop_front();
-                        lk.unlock();
-                        pss_result* res = new pss_result();
-                        res->status = PSS_ENOMEM;
-                        res->err = "file needs more device memory than the server budget";
-                        finish(h, res);
-                        delete h;
-                        lk.lock();
-                        continue;
-                    }
-                    const bool same = slot.batch && slot.key == h->key;
-                    const size_t after = same ? in_use : in_use - slot.held + h->estimate;
-                    if (after <= budget) {
-                        queue.pop_front();
-                        in_use = after;
-                        if (!same) slot.held = h->estimate;
-                        r = h;
-                        break;
-                    }
-                    if (slot.batch && !same) {
-                        // make room: drop this idle slot's prepared batch
-                        pss_batch* old = slot.batch;
-                        slot.batch = nullptr;
-                        slot.key.clear();
-                        in_use -= slot.held;
-                        slot.held = 0;
-                        lk.unlock();
-                        pss_batch_free(old);
-                        lk.lock();
-                        cv_work.notify_all();
-                        continue;
-                    }
-                }
-                cv_work.wait(lk);
-            }
+            pss_batch* batch = nullptr;
+            size_t held = 0;
+            Request* r = admit(lk, &batch, &held);
             if (!r) return;  // stopping
+            if (batch) held = pss_batch_footprint(batch);
             lk.unlock();
             pss_result* res = new pss_result();
             try {
-                if (!slot.batch || slot.key != r->key) {
-                    if (slot.batch) pss_batch_free(slot.batch);
-                    slot.batch = nullptr;
-                    slot.key.clear();
-                    pss_status st = pss_batch_create(device, r->plan, &r->fil, &r->cfg, &slot.batch);
+                if (!batch) {
+                    pss_status st = pss_batch_create(device, r->plan, &r->fil, &r->cfg, &batch);
                     if (st != PSS_OK) {
+                        batch = nullptr;
                         res->status = st;
                         res->err = pss_last_error();
                     } else {
-                        slot.key = r->key;
-                        const size_t actual = pss_batch_footprint(slot.batch);
+                        const size_t actual = pss_batch_footprint(batch);
                         std::lock_guard<std::mutex> g(mu);
-                        in_use = in_use - slot.held + actual;
-                        slot.held = actual;
+                        in_use = in_use - held + actual;
+                        held = actual;
                     }
                 }
                 if (res->status == PSS_OK) {
                     int64_t n = 0;
                     std::vector<pss_cand> buf(1024);
-                    pss_status st =
-                        pss_batch_run(slot.batch, r->bytes(), 0, buf.data(), (int64_t)buf.size(), &n, nullptr);
+                    pss_status st = pss_batch_run(batch, r->bytes(), 0, buf.data(), (int64_t)buf.size(), &n, nullptr);
                     if (st == PSS_ECAP) {
                         buf.resize((size_t)n);
-                        st = pss_batch_take_cands(slot.batch, buf.data(), (int64_t)buf.size(), &n);
+                        st = pss_batch_take_cands(batch, buf.data(), (int64_t)buf.size(), &n);
                     }
                     if (st != PSS_OK) {
                         res->status = st;
@@ -256,18 +276,18 @@ struct pss_server {
                 res->status = PSS_ENOMEM;
                 res->err = "host allocation failed";
             }
-            if (res->status != PSS_OK && slot.batch) {
+            // the run's footprint may have grown (a candidate buffer resized on overflow)
+            if (batch && res->status == PSS_OK) {
+                const size_t actual = pss_batch_footprint(batch);
+                std::lock_guard<std::mutex> g(mu);
+                in_use = in_use - held + actual;
+                held = actual;
+                idle.push_back(Idle{batch, r->key, held, ++clock});
+            } else {
                 // a failed batch is not reused
-                pss_batch_free(slot.batch);
-                slot.batch = nullptr;
-                slot.key.clear();
+                if (batch) pss_batch_free(batch);
                 std::lock_guard<std::mutex> g(mu);
-                in_use -= slot.held;
-                slot.held = 0;
-            } else if (res->status != PSS_OK) {
-                std::lock_guard<std::mutex> g(mu);
-                in_use -= slot.held;
-                slot.held = 0;
+                in_use -= held;
             }
             r->release_data();
             finish(r, res);
@@ -287,7 +307,6 @@ extern "C" pss_status pss_server_create(int device, size_t hbm_budget_bytes, int
     pss_server* s = new pss_server();
     s->device = device;
     s->budget = hbm_budget_bytes;
-    s->slots.resize((size_t)max_slots);
     for (int i = 0; i < max_slots; ++i) s->workers.emplace_back([s, i] { s->worker(i); });
     *out = s;
     return PSS_OK;
@@ -400,8 +419,7 @@ extern "C" void pss_server_destroy(pss_server* srv) {
         srv->cv_work.notify_all();
     }
     for (auto& t : srv->workers) t.join();
-    for (auto& sl : srv->slots)
-        if (sl.batch) pss_batch_free(sl.batch);
+    for (auto& v : srv->idle) pss_batch_free(v.batch);
     for (Request* r : srv->queue) delete r;
     for (auto& kv : srv->done) delete kv.second;
     delete srv;

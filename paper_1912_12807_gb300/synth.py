@@ -220,28 +220,52 @@ def make_8bit(nchan: int, nsamp: int, tsamp: float, lo: float, hi: float,
                       list(pulsars), tuple(rfi_chans), burst_t_s)
 
 
-def make_8bit_chunked(nchan: int, nsamp: int, tsamp: float, lo: float, hi: float,
-                      pulsars: Sequence[Pulsar], seed: int, chunk: int = 1 << 15) -> Filterbank:
-    """The make_8bit recipe (noise clip(round_half_even(128 + 16 g)) plus
-    dispersed pulses) generated in FP32 blocks of `chunk` samples, for files
-    too large to hold in FP64 at once (the noise realisation differs from
-    make_8bit's for the same seed)."""
+_QTAB = None
+
+
+def _quantised_gauss_table() -> np.ndarray:
+    """uint8 [65536]: a uniform 16-bit index maps to clip(round(128 + 16 g),
+    0, 255) with the probabilities of g ~ N(0, 1) (to 2^-16)."""
+    global _QTAB
+    if _QTAB is None:
+        v = np.arange(256)
+        edges = (v[:-1] + 0.5 - 128.0) / 16.0                  # upper edge of each value
+        cdf = 0.5 * (1.0 + np.array([math.erf(e / math.sqrt(2.0)) for e in edges]))
+        cut = np.rint(cdf * 65536.0).astype(np.int64)          # first index of value v+1
+        tab = np.searchsorted(cut, np.arange(65536), side="right").astype(np.uint8)
+        _QTAB = tab
+    return _QTAB
+
+
+def make_8bit_stream(nchan: int, nsamp: int, tsamp: float, lo: float, hi: float,
+                     pulsars: Sequence[Pulsar], seed: int) -> Filterbank:
+    """A fast stand-in for make_8bit for the many large files of a served
+    stream: the noise values are drawn directly with the distribution of the
+    quantised Gaussian (a 16-bit lookup table), and each pulsar's pulse train
+    (Gaussian profile, FWHM duty * P) is added in the quantised domain
+    (stochastically rounded to 1/16 sd, so its mean is kept) at the channel's
+    dispersion delay rounded to a whole sample."""
     rng = np.random.default_rng(seed)
     fch0, foff = band(lo, hi, nchan)
     freqs = fch0 + np.arange(nchan) * foff
     f_top = float(freqs.max())
-    t_span = nsamp * tsamp
-    out = np.empty((nsamp, nchan), dtype=np.uint8)
-    dl = [_sim_delay_s(p.dm, freqs, f_top) for p in pulsars]
-    for s0 in range(0, nsamp, chunk):
-        s1 = min(nsamp, s0 + chunk)
-        x = rng.standard_normal((s1 - s0, nchan), dtype=np.float32)
-        for p, d in zip(pulsars, dl):
-            _inject(x, s0, tsamp, p, d, t_span, p.amp)
-        np.rint(x * 16.0 + 128.0, out=x)
-        np.clip(x, 0, 255, out=x)
-        out[s0:s1] = x.astype(np.uint8)
-    return Filterbank(nchan, nsamp, tsamp, fch0, foff, 8, out, list(pulsars))
+    q = _quantised_gauss_table()[rng.integers(0, 65536, (nsamp, nchan), dtype=np.uint16)]
+    t = np.arange(nsamp, dtype=np.float64) * tsamp
+    for p in pulsars:
+        ph = p.phase0 + t / p.period_s
+        v = 16.0 * p.amp * _gauss_profile(ph, p.duty)
+        nz = np.nonzero(v > 1e-3)[0]
+        if nz.size == 0:
+            continue
+        sh = np.rint(_sim_delay_s(p.dm, freqs, f_top) / tsamp).astype(np.int64)
+        for c in range(nchan):
+            idx = nz + sh[c]
+            keep = idx < nsamp
+            # stochastic rounding keeps the mean of a sub-level pulse
+            inc = np.floor(v[nz[keep]] + rng.random(int(keep.sum()))).astype(np.int16)
+            col = q[idx[keep], c].astype(np.int16) + inc
+            q[idx[keep], c] = np.clip(col, 0, 255).astype(np.uint8)
+    return Filterbank(nchan, nsamp, tsamp, fch0, foff, 8, q, list(pulsars))
 
 
 def make_1bit(nchan: int, nsamp: int, tsamp: float, lo: float, hi: float,
@@ -367,6 +391,6 @@ def stream_files(n_files: int = 64, seed0: int = 5000, mean_gap_s: float = 26.0,
         npsr = int(rng.integers(0, 4))
         prng = np.random.default_rng(seed0 + f + 100000)
         psrs = _drift_pulsars(prng, npsr, nchan, nsamp)
-        fil = make_8bit_chunked(nchan, nsamp, 2e-4, 1050.0, 1450.0, psrs, seed0 + f)
+        fil = make_8bit_stream(nchan, nsamp, 2e-4, 1050.0, 1450.0, psrs, seed0 + f)
         yield t, Workload("stream_file_%d" % f, fil, [Stage(0.0, 1.0, 501, 1)],
                           SearchCfg(zmax=100, dz=2.0, numharm=8))
