@@ -177,6 +177,12 @@ __global__ void __launch_bounds__(NT) k_dedisp(DedispArgs a, int RW, int CC, uin
     __syncthreads();
     issue(0);
     const int qn = RW / 4;
+    // expansion work split: qn 16-byte chunks per row, x_rows rows per sweep
+    // (rows longer than NT chunks: one row per sweep, chunks strided by NT)
+    const int x_rows = qn <= NT ? NT / qn : 1;
+    const int x_qstep = qn <= NT ? qn : NT;
+    const int x_row = qn <= NT ? (threadIdx.x < x_rows * qn ? (int)threadIdx.x / qn : (1 << 30)) : 0;
+    const int x_q = qn <= NT ? (int)threadIdx.x - ((int)threadIdx.x / qn) * qn : (int)threadIdx.x;
     int failed_at = -1;
     for (int c = 0; c < nchunks; ++c) {
         const int cb = c * CC;
@@ -186,9 +192,10 @@ __global__ void __launch_bounds__(NT) k_dedisp(DedispArgs a, int RW, int CC, uin
             failed_at = c;
             break;
         }
-        // expand the staged rows into 4 byte-shifted copies
-        for (int it = threadIdx.x; it < cn * qn; it += NT) {
-            const int i = it / qn, q = it - i * qn;
+        // expand the staged rows into 4 byte-shifted copies (thread -> (row, 16-byte
+        // chunk) split computed once per launch: no division in the loop)
+        for (int i = x_row; i < cn; i += x_rows)
+        for (int q = x_q; q < qn; q += x_qstep) {
             const uint8_t* src = S.raw + (size_t)i * RAWB + 16 * q;
             const uint4 v = *reinterpret_cast<const uint4*>(src);
             const uint32_t w4 = *reinterpret_cast<const uint32_t*>(src + 16);
@@ -221,7 +228,7 @@ __global__ void __launch_bounds__(NT) k_dedisp(DedispArgs a, int RW, int CC, uin
         }
         if (active) {
             const uint16_t* offs = S.offs + warp * a.ck + cb;
-#pragma unroll 2
+#pragma unroll 4
             for (int i = 0; i < cn; ++i) {
                 const uint32_t* p = S.copies + (size_t)i * 4 * RW + offs[i] + lane;
 #pragma unroll
@@ -328,7 +335,7 @@ cudaError_t launch_dedisp(const DedispArgs& a, int num_sms, cudaStream_t s) {
     int RW = 32 * KW + (15 + a.spread) / 4 + 1;
     RW = (RW + 3) & ~3;
     const size_t per_chan = (size_t)16 * RW + (4 * RW + 16);
-    int CC = (int)((64 * 1024) / per_chan);
+    int CC = (int)((96 * 1024) / per_chan);  // two CTAs per SM fit beside the rest
     if (CC > 32) CC = 32;
     if (CC < 1) CC = 1;
     if (15 + a.spread > 65535 - 4 * RW) return cudaErrorInvalidValue;  // offsets are 16-bit
