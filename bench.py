@@ -46,6 +46,7 @@ sys.path.insert(0, ROOT)
 METRIC = "DM-trials searched/s and files/s vs 26 s realtime; batched vs plain; p99 lat"
 UNIT = "DM-trials/s"
 REALTIME_S = 26.0
+OLA_L = 2048  # overlap-save segment of the zmax > 0 plane
 
 WORKLOADS = {
     "driftscan": "driftscan_256ch_2^18_8bit_dm0-500x0.5_1001trials_zmax0_numharm16",
@@ -227,8 +228,10 @@ def stage_work(plan, wl, fil_nbytes):
     sample sums one 8-bit sample per channel per native sample);
     unpack: file read + channel-major write; fft: every pass reads and writes
     8 bytes per complex point; whiten: spectrum read + write; plane: for
-    zmax 0 the spectrum read + plane write, for zmax > 0 the 8 flops of every
-    complex tap of the correlation; harmsum: one read of the plane."""
+    zmax 0 the spectrum read + plane write, for zmax > 0 the flops of the
+    overlap-save correlation (5 L log2 L per L-point FFT, 6 per complex
+    product) or, where the direct form runs, the 8 flops of every complex tap;
+    harmsum: one read of the plane."""
     ndm = plan.ndm
     cfg = wl.cfg
     nz = int(round(2 * cfg.zmax / cfg.dz)) + 1 if cfg.zmax else 1
@@ -247,10 +250,18 @@ def stage_work(plan, wl, fil_nbytes):
         if cfg.zmax == 0:
             plane_b += 8.0 * M + 4.0 * nfft
         else:
-            for j in range(nz):
-                z = -cfg.zmax + j * cfg.dz
-                m = int(math.ceil(abs(z) / 2)) + cfg.halfwidth_extra
-                plane_flops += 2 * (2 * m) * 8.0 * M
+            mmax = (cfg.zmax + 1) // 2 + cfg.halfwidth_extra
+            if 4 * mmax <= OLA_L and M >= OLA_L:
+                # overlap-save: per segment of OLA_L bins, one forward FFT, then per
+                # row two pointwise products and two FFTs (5 L log2 L flops each)
+                V = OLA_L - 2 * mmax + 1
+                fft = 5.0 * OLA_L * math.log2(OLA_L)
+                plane_flops += math.ceil(M / V) * (fft + nz * 2 * (6.0 * OLA_L + fft))
+            else:
+                for j in range(nz):
+                    z = -cfg.zmax + j * cfg.dz
+                    m = int(math.ceil(abs(z) / 2)) + cfg.halfwidth_extra
+                    plane_flops += 2 * (2 * m) * 8.0 * M
     return {"unpack": ("hbm", 2.0 * fil_nbytes, "bytes"),
             "dedisperse": ("alu", adds, "channel-adds"),
             "fft": ("hbm", fft_b, "bytes"),
