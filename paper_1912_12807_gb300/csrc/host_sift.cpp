@@ -215,8 +215,9 @@ Groups link_groups(const std::vector<Item>& it, double /*dz*/) {
 // largest-S member of each harmonic stage can win.  sigma is a decreasing
 // function of log Q, so those few members are ranked by log Q; sigma itself
 // is evaluated only where two log Q values are too close (1e-12 relative) for
-// their order to decide the order of the sigmas, and for the winner.
-int pick_rep(std::vector<Item>& items, const int* mem, int nm) {
+// their order to decide the order of the sigmas, and for the winner when the
+// caller needs it (the final, across-trial representatives).
+int pick_rep(std::vector<Item>& items, const int* mem, int nm, bool need_sigma) {
     int best_of_n[8];
     for (int i = 0; i < 8; ++i) best_of_n[i] = -1;
     for (int q = 0; q < nm; ++q) {
@@ -250,7 +251,7 @@ int pick_rep(std::vector<Item>& items, const int* mem, int nm) {
             if (rep_less(items[k], items[best])) best = k;
         }
     }
-    item_sigma(items[best]);
+    if (need_sigma) item_sigma(items[best]);
     return best;
 }
 
@@ -337,7 +338,7 @@ pss_status sift(const Plan& P, const pss_search_cfg& cfg, const pss_raw_cand* ra
         const Groups G = link_groups(items, dz);
         for (int g = 0; g < G.count(); ++g)
             surv[(size_t)b].push_back(
-                items[pick_rep(items, G.members.data() + G.start[g], G.start[g + 1] - G.start[g])]);
+                items[pick_rep(items, G.members.data() + G.start[g], G.start[g + 1] - G.start[g], false)]);
     });
     std::vector<Item> survivors;
     for (auto& v : surv) survivors.insert(survivors.end(), v.begin(), v.end());
@@ -350,7 +351,7 @@ pss_status sift(const Plan& P, const pss_search_cfg& cfg, const pss_raw_cand* ra
     for (int g = 0; g < G.count(); ++g) {
         const int* mem = G.members.data() + G.start[g];
         const int nm = G.start[g + 1] - G.start[g];
-        const int best = pick_rep(survivors, mem, nm);
+        const int best = pick_rep(survivors, mem, nm, true);
         std::vector<int32_t> dms;
         for (int q = 0; q < nm; ++q) dms.push_back(survivors[mem[q]].dm_idx);
         std::sort(dms.begin(), dms.end());
