@@ -302,6 +302,44 @@ float thr_f32(int n, double sigma) {
     return f;
 }
 
+// Inter-pass twiddle tables of the M-point FFT (built once per size, after
+// the global twiddle table; outside any graph capture).
+pss_status ensure_passtw(pss_ctx* ctx, int64_t M, cudaStream_t s) {
+    for (const auto& t : ctx->passtw)
+        if (t.M == M) return PSS_OK;
+    int rad[4] = {0, 0, 0, 0};
+    const int np = fft_pass_plan(M, rad);
+    Ctx::PassTw t;
+    t.M = M;
+    t.twM = ctx->twid_n;
+    int64_t total = 0, Ns = rad[0];
+    for (int i = 1; i < np; ++i) {
+        t.off[i] = total;
+        total += (int64_t)rad[i] * Ns;
+        Ns *= rad[i];
+    }
+    if (total > 0) {
+        PSS_TRY(t.buf.ensure((size_t)total * sizeof(float2)));
+        Ns = rad[0];
+        for (int i = 1; i < np; ++i) {
+            PSS_CUDA(launch_pass_twiddles((float2*)t.buf.p + t.off[i], (const float2*)ctx->twid.p, ctx->twid_n,
+                                          rad[i], Ns, s));
+            Ns *= rad[i];
+        }
+    }
+    ctx->passtw.push_back(t);
+    return PSS_OK;
+}
+
+// Point the FftArgs at the inter-pass tables of its size (ensure_passtw first).
+void set_passtw(const pss_ctx* ctx, FftArgs* fa) {
+    for (int i = 0; i < 4; ++i) fa->ptw[i] = nullptr;
+    const int64_t M = fa->nfft / 2;
+    for (const auto& t : ctx->passtw)
+        if (t.M == M && t.buf.p)
+            for (int i = 1; i < 4; ++i) fa->ptw[i] = (const float2*)t.buf.p + t.off[i];
+}
+
 // One batch of consecutive trials within a plan stage.
 struct BatchDesc {
     int32_t stage;
@@ -360,6 +398,8 @@ pss_status setup_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fi
         PSS_CUDA(launch_twiddles((float2*)ctx->twid.p, nfft_max, s));
         ctx->twid_n = nfft_max;
     }
+    for (const auto& st : plan->stages)
+        if (st.n_dm > 0) PSS_TRY(ensure_passtw(ctx, st.nfft / 2, s));
     size_t need_series = 0, need_fft = 0, need_sums = 0, need_plane = 0;
     int64_t out_off = 0;
     for (size_t si = 0; si < plan->stages.size(); ++si) {
@@ -447,6 +487,7 @@ pss_status enqueue_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* 
         fa.whiten_block = cfg->whiten_block;
         fa.tw = (const float2*)ctx->twid.p;
         fa.twM = ctx->twid_n;
+        set_passtw(ctx, &fa);
         fa.whiten = 1;
         fa.gains_out = nullptr;
         fa.gains_stride = 0;
@@ -620,6 +661,7 @@ void pss_ctx_destroy(pss_ctx* c) {
                       &c->spec, &c->plane, &c->cands, &c->counter, &c->taps, &c->ftaps, &c->tapinfo, &c->errflag,
                       &c->twid, &c->chan_spec, &c->refine_gains, &c->refine_dtau, &c->refine_pts, &c->refine_out};
     for (DevBuf* b : bufs) b->release();
+    for (auto& t : c->passtw) t.buf.release();
     for (auto& r : c->prof_recs) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -905,6 +947,8 @@ pss_status refine_prepare(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc
     fa.whiten_block = cfg->whiten_block;
     fa.tw = (const float2*)ctx->twid.p;
     fa.twM = ctx->twid_n;
+    PSS_TRY(ensure_passtw(ctx, M, s));
+    set_passtw(ctx, &fa);
     fa.whiten = 0;
     fa.gains_out = nullptr;
     fa.gains_stride = 0;
@@ -1088,6 +1132,7 @@ size_t ctx_bytes(const pss_ctx* c) {
                             &c->errflag, &c->twid};
     size_t t = 0;
     for (const DevBuf* b : bufs) t += b->bytes;
+    for (const auto& p : c->passtw) t += p.buf.bytes;
     return t;
 }
 
@@ -1185,9 +1230,14 @@ size_t search_footprint(const Plan& plan, const pss_fil_desc* fil, const pss_sea
                buf((size_t)dev_cap * sizeof(pss_raw_cand)) + buf(sizeof(unsigned long long));
     int64_t nfft_max = 0, total_taps = 0;
     size_t need_series = 0, need_fft = 0, need_sums = 0, need_plane = 0;
+    std::vector<int64_t> sizes;
     for (const auto& st : plan.stages) {
         nfft_max = std::max<int64_t>(nfft_max, st.nfft);
         if (st.n_dm <= 0) continue;
+        if (std::find(sizes.begin(), sizes.end(), st.nfft) == sizes.end()) {
+            sizes.push_back(st.nfft);
+            t += buf((size_t)(st.nfft / 2) * sizeof(float2));  // inter-pass twiddles (at most M entries)
+        }
         const int64_t B = batch_trials(st.nfft, nz, MODE_SEARCH, st.n_dm);
         need_series = std::max(need_series, (size_t)B * st.nfft * 4);
         need_sums = std::max(need_sums, (size_t)B * 8);

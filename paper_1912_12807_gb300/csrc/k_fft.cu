@@ -39,9 +39,10 @@ constexpr int NT = 256;      // threads per CTA
 // in place in shared memory ([r * TJP + jj]), running span ns: every thread
 // reads its butterflies' inputs into registers, the block synchronises, and
 // the results are written back.  The twiddle exp(-2 pi i q k / (RR ns)) is
-// tws[q k R / (RR ns)], tws[t] = exp(-2 pi i t / R).
+// twt[q ns + k] (a table per sub-stage, q-major so that the lanes of a warp,
+// which hold consecutive k, read consecutive words).
 template <int R, int RR>
-__device__ __forceinline__ void substage(float2* buf, const float2* tws, int ns) {
+__device__ __forceinline__ void substage(float2* buf, const float2* twt, int ns) {
     constexpr int NB = R / RR * TJ;
     constexpr int PER = (NB + NT - 1) / NT;
     float2 x[PER][RR];
@@ -51,14 +52,13 @@ __device__ __forceinline__ void substage(float2* buf, const float2* tws, int ns)
         const int e = threadIdx.x + p * NT;
         if (NB % NT == 0 || e < NB) {
             const int jj = e % TJ, b = e / TJ;
-            const int k = b % ns;
-            const int tstep = k * (R / RR / ns);
+            const int k = b & (ns - 1);
 #pragma unroll
             for (int q = 0; q < RR; ++q) {
                 x[p][q] = buf[(b + q * (R / RR)) * TJP + jj];
-                if (q && k) x[p][q] = cmul(x[p][q], tws[q * tstep]);
+                if (q && k) x[p][q] = cmul(x[p][q], twt[q * ns + k]);
             }
-            dst[p] = ((b / ns) * ns * RR + k) * TJP + jj;
+            dst[p] = ((b - k) * RR + k) * TJP + jj;
         }
     }
     __syncthreads();
@@ -74,19 +74,47 @@ __device__ __forceinline__ void substage(float2* buf, const float2* tws, int ns)
     __syncthreads();
 }
 
+// Sub-stage plan of an R-point DFT: one radix-2 or radix-4 sub-stage first
+// when log2 R is not a multiple of 3, then radix 8.  Sub-stages after the
+// first have running span ns > 1 and a twiddle table of RR * ns entries.
+template <int R>
+struct SubPlan {
+    static constexpr int LOG = (R == 32) ? 5 : (R == 64) ? 6 : (R == 128) ? 7 : (R == 256) ? 8 : (R == 512) ? 9 : 10;
+    static constexpr int FIRST = (LOG % 3 == 1) ? 2 : (LOG % 3 == 2) ? 4 : 8;
+    // total twiddle-table entries: sum of 8 ns over the radix-8 sub-stages with ns > 1
+    static constexpr int table_size() {
+        int t = 0;
+        for (int ns = FIRST; ns < R; ns *= 8) t += 8 * ns;
+        return t;
+    }
+};
+
+// Fill the sub-stage twiddle tables from the global table exp(-2 pi i t / twM).
+template <int R>
+__device__ void load_subtables(float2* twt, const float2* tw, int64_t twM) {
+    const int64_t tstride = twM / R;
+    int off = 0;
+    for (int ns = SubPlan<R>::FIRST; ns < R; ns *= 8) {
+        for (int i = threadIdx.x; i < 8 * ns; i += NT) {
+            const int q = i / ns, k = i - q * ns;
+            twt[off + i] = tw[(int64_t)(q * k * (R / (8 * ns))) * tstride];
+        }
+        off += 8 * ns;
+    }
+}
+
 // R-point DFTs of TJ columns held in buf (in place).
 template <int R>
-__device__ void smem_dft(float2* buf, const float2* tws) {
-    constexpr int LOG = (R == 32) ? 5 : (R == 64) ? 6 : (R == 128) ? 7 : (R == 256) ? 8 : (R == 512) ? 9 : 10;
-    int ns = 1;
-    if constexpr (LOG % 3 == 1) {
-        substage<R, 2>(buf, tws, ns);
-        ns *= 2;
-    } else if constexpr (LOG % 3 == 2) {
-        substage<R, 4>(buf, tws, ns);
-        ns *= 4;
+__device__ void smem_dft(float2* buf, const float2* twt) {
+    constexpr int FIRST = SubPlan<R>::FIRST;
+    if constexpr (FIRST == 2) substage<R, 2>(buf, twt, 1);
+    else if constexpr (FIRST == 4) substage<R, 4>(buf, twt, 1);
+    else substage<R, 8>(buf, twt, 1);
+    int off = 0;
+    for (int ns = FIRST; ns < R; ns *= 8) {
+        substage<R, 8>(buf, twt + off, ns);
+        off += 8 * ns;
     }
-    for (; ns < R; ns *= 8) substage<R, 8>(buf, tws, ns);
 }
 
 struct PassArgs {
@@ -102,19 +130,19 @@ struct PassArgs {
     int64_t Ns;
     const float2* tw;          // exp(-2 pi i t / twM)
     int64_t twM;
+    const float2* ptw;         // later passes: [R][Ns] inter-pass twiddles tw[r k twM / (Ns R)]
 };
 
 template <int R>
 __global__ void __launch_bounds__(NT) k_fft_pass(const __grid_constant__ PassArgs a) {
     extern __shared__ float2 sm[];
     float2* bufA = sm;
-    float2* tws = sm + R * TJP;
+    float2* twt = sm + R * TJP;  // sub-stage twiddle tables
     const int b = blockIdx.y;
     const int64_t ncol = a.M / R;
     const int64_t j0 = (int64_t)blockIdx.x * TJ;
     const bool first = (a.series != nullptr);
-    const int64_t tstride = a.twM / R;
-    for (int t = threadIdx.x; t < R; t += NT) tws[t] = a.tw[(int64_t)t * tstride];
+    load_subtables<R>(twt, a.tw, a.twM);
 
     if (first) {
         // mean = sum / N_v in FP64 (once per CTA: FP64 is slow), split as integer + fraction
@@ -145,7 +173,6 @@ __global__ void __launch_bounds__(NT) k_fft_pass(const __grid_constant__ PassArg
             bufA[r * TJP + jj] = x;
         }
     } else {
-        const int64_t ostride = a.twM / (a.Ns * R);
         const float2* in = a.in + (int64_t)b * a.in_stride;
 #pragma unroll
         for (int e = threadIdx.x; e < R * TJ; e += NT) {
@@ -155,13 +182,14 @@ __global__ void __launch_bounds__(NT) k_fft_pass(const __grid_constant__ PassArg
             if (j < ncol) {
                 x = in[j + (int64_t)r * ncol];
                 const int64_t k = j % a.Ns;
-                if (k && r) x = cmul(x, a.tw[(int64_t)r * k * ostride]);
+                // table laid out like the data: consecutive columns read consecutive words
+                if (k && r) x = cmul(x, a.ptw[(int64_t)r * a.Ns + k]);
             }
             bufA[r * TJP + jj] = x;
         }
     }
     __syncthreads();
-    smem_dft<R>(bufA, tws);
+    smem_dft<R>(bufA, twt);
     const float2* res = bufA;
     float2* o = a.out + (int64_t)b * a.out_stride;
     if (a.Ns == 1) {
@@ -184,7 +212,7 @@ __global__ void __launch_bounds__(NT) k_fft_pass(const __grid_constant__ PassArg
 
 template <int R>
 cudaError_t run_pass(const PassArgs& p, int nb, cudaStream_t s) {
-    const size_t shm = (size_t)(R * TJP + R) * sizeof(float2);
+    const size_t shm = (size_t)(R * TJP + SubPlan<R>::table_size()) * sizeof(float2);
     cudaError_t e = allow_smem((const void*)k_fft_pass<R>, shm);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((p.M / R + TJ - 1) / TJ), (unsigned)nb);
@@ -391,6 +419,28 @@ void radix_plan(int64_t M, int* rad, int* np) {
 
 }  // namespace
 
+int fft_pass_plan(int64_t M, int* rad) {
+    int np = 0;
+    radix_plan(M, rad, &np);
+    return np;
+}
+
+namespace {
+// inter-pass twiddles of a later pass: out[r Ns + k] = tw[r k twM / (Ns R)]
+__global__ void k_pass_twiddles(float2* out, const float2* tw, int64_t twM, int R, int64_t Ns) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)R * Ns) return;
+    const int64_t r = i / Ns, k = i - r * Ns;
+    out[i] = tw[r * k * (twM / (Ns * R))];
+}
+}  // namespace
+
+cudaError_t launch_pass_twiddles(float2* out, const float2* tw, int64_t twM, int R, int64_t Ns, cudaStream_t s) {
+    const int64_t n = (int64_t)R * Ns;
+    k_pass_twiddles<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, tw, twM, R, Ns);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_twiddles(float2* tw, int64_t n, cudaStream_t s) {
     k_twiddles<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tw, n);
     return cudaGetLastError();
@@ -423,6 +473,8 @@ cudaError_t launch_fft_whiten(const FftArgs& a, cudaStream_t s, Ctx* prof_ctx) {
         p.out = cur;
         p.out_stride = M;
         p.Ns = Ns;
+        p.ptw = a.ptw[i];
+        if (i > 0 && !p.ptw) return cudaErrorInvalidValue;
         ProfScope ps(prof_ctx, 2, s);
         cudaError_t e = dispatch_pass(rad[i], p, a.nb, s);
         if (e != cudaSuccess) return e;

@@ -132,6 +132,13 @@ struct Ctx {
     DevBuf errflag;      // int: a kernel's bounded wait expired
     DevBuf twid;         // float2 twiddle table exp(-2 pi i t / twid_n)
     int64_t twid_n = 0;
+    // inter-pass twiddle tables of each FFT size in use (later passes, laid out like their data)
+    struct PassTw {
+        int64_t M = 0, twM = 0;
+        DevBuf buf;
+        int64_t off[4] = {0, 0, 0, 0};
+    };
+    std::vector<PassTw> passtw;
     // refinement state (pss_refine_prepare)
     DevBuf chan_spec, refine_gains, refine_dtau, refine_pts, refine_out;
     const void* refine_plan = nullptr;
@@ -232,8 +239,12 @@ struct FftArgs {
     int32_t whiten;                   // 0: output the raw half spectrum (DC still zeroed)
     float* gains_out;                 // nullable [nb][gains_stride]: ln 2 / med_b per block
     int64_t gains_stride;
+    const float2* ptw[4];             // inter-pass twiddle tables of passes 1.. (fft_pass_plan)
 };
 cudaError_t launch_twiddles(float2* tw, int64_t n, cudaStream_t s);
+// Radices of the passes of an M-point FFT (returns the pass count, <= 3).
+int fft_pass_plan(int64_t M, int* rad);
+cudaError_t launch_pass_twiddles(float2* out, const float2* tw, int64_t twM, int R, int64_t Ns, cudaStream_t s);
 cudaError_t launch_fft_whiten(const FftArgs& a, cudaStream_t s, Ctx* prof_ctx);
 
 struct PlaneArgs {
