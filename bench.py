@@ -449,10 +449,12 @@ def run_batched(pss, plan, cfg, data_dev, ndm, steps, flush):
         wall.append(time.perf_counter() - t0)
         gpu.append(g)
     fp = b.footprint
+    tuning = b.tuning
     b.close()
     g, w = statistics.mean(gpu), statistics.mean(wall)
     return {"value": ndm / (g / 1e3), "unit": UNIT, "gpu_ms_per_file": g, "wall_ms_per_file": 1e3 * w,
-            "wall_dm_trials_per_s": ndm / w, "launches_per_file": "1 graph", "device_bytes": fp}
+            "wall_dm_trials_per_s": ndm / w, "launches_per_file": "1 graph", "device_bytes": fp,
+            "tuning": tuning}
 
 
 def run_served(pss, name, wl, args, device):

@@ -334,9 +334,12 @@ pss_status pss_response(pss_ctx* ctx, const double* q, const double* z, int64_t 
 /* ---- batched search: one graph launch per file (no paper counterpart) --- */
 
 /* A search prepared for files of one shape (descriptor, plan, cfg): its own
- * context and stream, every device buffer allocated, and the whole kernel
- * sequence of pss_search_dm_batch over all trials of the plan captured into
- * one CUDA graph.  The plan and descriptor are copied; `fil->chan_mask` too. */
+ * context and stream, launch shapes picked by timing (pss_batch_tuning),
+ * every device buffer allocated, and the whole kernel sequence of
+ * pss_search_dm_batch over all trials of the plan captured into one CUDA
+ * graph.  The plan and descriptor are copied; `fil->chan_mask` too.  With a
+ * tuned FFT pass split the powers differ from the untuned call's by FP32
+ * rounding only. */
 typedef struct pss_batch pss_batch;
 pss_status pss_batch_create(int device, const pss_plan* plan, const pss_fil_desc* fil, const pss_search_cfg* cfg,
                             pss_batch** out);
@@ -352,6 +355,14 @@ pss_status pss_batch_run(pss_batch* b, const void* data, int data_on_device, pss
 pss_status pss_batch_take_cands(pss_batch* b, pss_cand* out, int64_t cap, int64_t* n_out);
 /* Device bytes held by the batch. */
 size_t pss_batch_footprint(const pss_batch* b);
+/* Launch shapes the batch's autotuner chose (pss_batch_create times each
+ * choice on the first <= 128 trials of the shape and keeps the fastest;
+ * the choice is remembered per shape for the life of the process;
+ * environment PSS_AUTOTUNE=0 keeps the defaults 0 / 16 / 96):
+ * fft_split: FFT pass-split variant (0 = even split), harm_run: points per
+ * lane of the harmonic sum (16 or 8), dedisp_kb: shared memory for staged
+ * channel chunks (KiB).  Pointers are nullable. */
+pss_status pss_batch_tuning(const pss_batch* b, int32_t* fft_split, int32_t* harm_run, int32_t* dedisp_kb);
 /* Device bytes a batch for this shape will hold, computed on the host
  * without a device (what the server admits files by).  PSS_EINVAL for the
  * arguments pss_batch_create would reject. */

@@ -8,6 +8,9 @@
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
+#include <map>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "pss_internal.h"
@@ -304,13 +307,15 @@ float thr_f32(int n, double sigma) {
 
 // Inter-pass twiddle tables of the M-point FFT (built once per size, after
 // the global twiddle table; outside any graph capture).
-pss_status ensure_passtw(pss_ctx* ctx, int64_t M, cudaStream_t s) {
+pss_status ensure_passtw(pss_ctx* ctx, int64_t M, int variant, cudaStream_t s) {
     for (const auto& t : ctx->passtw)
-        if (t.M == M) return PSS_OK;
+        if (t.M == M && t.variant == variant) return PSS_OK;
     int rad[4] = {0, 0, 0, 0};
-    const int np = fft_pass_plan(M, rad);
+    const int np = fft_pass_plan(M, variant, rad);
+    if (np == 0) return fail(PSS_EINVAL, "no such FFT pass split");
     Ctx::PassTw t;
     t.M = M;
+    t.variant = variant;
     t.twM = ctx->twid_n;
     int64_t total = 0, Ns = rad[0];
     for (int i = 1; i < np; ++i) {
@@ -336,7 +341,7 @@ void set_passtw(const pss_ctx* ctx, FftArgs* fa) {
     for (int i = 0; i < 4; ++i) fa->ptw[i] = nullptr;
     const int64_t M = fa->nfft / 2;
     for (const auto& t : ctx->passtw)
-        if (t.M == M && t.buf.p)
+        if (t.M == M && t.variant == fa->fft_variant && t.buf.p)
             for (int i = 1; i < 4; ++i) fa->ptw[i] = (const float2*)t.buf.p + t.off[i];
 }
 
@@ -399,7 +404,7 @@ pss_status setup_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fi
         ctx->twid_n = nfft_max;
     }
     for (const auto& st : plan->stages)
-        if (st.n_dm > 0) PSS_TRY(ensure_passtw(ctx, st.nfft / 2, s));
+        if (st.n_dm > 0) PSS_TRY(ensure_passtw(ctx, st.nfft / 2, ctx->tune.fft_variant, s));
     size_t need_series = 0, need_fft = 0, need_sums = 0, need_plane = 0;
     int64_t out_off = 0;
     for (size_t si = 0; si < plan->stages.size(); ++si) {
@@ -453,7 +458,7 @@ pss_status enqueue_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* 
     for (const BatchDesc& d : P.batches) {
         const StageInfo& st = plan->stages[d.stage];
         const int64_t nfft = st.nfft, M = nfft / 2;
-        DedispArgs da;
+        DedispArgs da{};
         da.xcm = (const uint8_t*)ctx->xcm.p;
         da.pitch = P.pitch;
         da.ck = P.ck;
@@ -467,12 +472,13 @@ pss_status enqueue_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* 
         da.sums = (unsigned long long*)ctx->sums.p;
         da.spread = d.spread;
         da.err = (int*)ctx->errflag.p;
+        da.chunk_kb = ctx->tune.dedisp_kb;
         PSS_CUDA(cudaMemsetAsync(ctx->sums.p, 0, (size_t)d.nb * 8, s));
         {
             ProfScope ps(ctx, 1, s);
             PSS_CUDA(launch_dedisp(da, ctx->num_sms, s));
         }
-        FftArgs fa;
+        FftArgs fa{};
         fa.series = (const float*)ctx->series.p;
         fa.series_stride = nfft;
         fa.sums = (const unsigned long long*)ctx->sums.p;
@@ -487,6 +493,7 @@ pss_status enqueue_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* 
         fa.whiten_block = cfg->whiten_block;
         fa.tw = (const float2*)ctx->twid.p;
         fa.twM = ctx->twid_n;
+        fa.fft_variant = ctx->tune.fft_variant;
         set_passtw(ctx, &fa);
         fa.whiten = 1;
         fa.gains_out = nullptr;
@@ -532,6 +539,7 @@ pss_status enqueue_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* 
         }
         if (mode == MODE_PLANE) continue;
         HarmArgs ha = P.harm[d.stage];
+        ha.run = ctx->tune.harm_run;
         ha.plane = pl.plane;
         ha.plane_stride = pl.plane_stride;
         ha.nfft = nfft;
@@ -759,7 +767,7 @@ pss_status pss_dedisperse(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc
         if (lo >= hi) continue;
         for (int64_t b0 = lo; b0 < hi; b0 += 1024) {
             const int32_t nb = (int32_t)std::min<int64_t>(1024, hi - b0);
-            DedispArgs da;
+            DedispArgs da{};
             da.xcm = (const uint8_t*)ctx->xcm.p;
             da.pitch = pitch;
             da.ck = ck;
@@ -933,7 +941,7 @@ pss_status refine_prepare(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc
     PSS_CUDA(cudaMemsetAsync(ctx->sums.p, 0, (size_t)ck * 8, s));
     PSS_CUDA(launch_chan_series((const uint8_t*)ctx->xcm.p, pitch, ck, st.nv, st.ds, (float*)ctx->series.p, nfft,
                                 (unsigned long long*)ctx->sums.p, s));
-    FftArgs fa;
+    FftArgs fa{};
     fa.series = (const float*)ctx->series.p;
     fa.series_stride = nfft;
     fa.sums = (const unsigned long long*)ctx->sums.p;
@@ -947,7 +955,8 @@ pss_status refine_prepare(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc
     fa.whiten_block = cfg->whiten_block;
     fa.tw = (const float2*)ctx->twid.p;
     fa.twM = ctx->twid_n;
-    PSS_TRY(ensure_passtw(ctx, M, s));
+    fa.fft_variant = 0;
+    PSS_TRY(ensure_passtw(ctx, M, 0, s));
     set_passtw(ctx, &fa);
     fa.whiten = 0;
     fa.gains_out = nullptr;
@@ -1143,6 +1152,104 @@ void batch_release_graph(pss_batch* b) {
     b->graph = nullptr;
 }
 
+// ---- autotuner ----------------------------------------------------------------
+//
+// A prepared batch picks its launch shapes by timing them: on the first
+// min(ndm, 128) trials of its file shape (the input in ctx->fil_dev), each
+// choice is tried in turn (FFT pass split, then harmonic-sum points per
+// lane, then the dedispersion chunk budget), each candidate run once to warm
+// and once timed with CUDA events over the whole kernel sequence, and the
+// fastest kept.  The result is remembered per shape for the life of the
+// process, so every batch of a shape (and so every file of that shape in a
+// server) runs the same kernels.  PSS_AUTOTUNE=0 disables it.
+
+std::string tune_key(const Plan& plan, const pss_fil_desc* f, const pss_search_cfg* c) {
+    std::string k;
+    char buf[256];
+    snprintf(buf, sizeof buf, "%d/%d/%lld/%.17g/%.17g/%.17g/%d|", f->nchan, f->nbits, (long long)f->nsamp,
+             f->tsamp_s, f->fch0_mhz, f->foff_mhz, f->layout);
+    k += buf;
+    for (int i = 0; i < f->nchan; ++i) k += (f->chan_mask && !f->chan_mask[i]) ? '0' : '1';
+    for (const auto& st : plan.stages) {
+        snprintf(buf, sizeof buf, "|%.17g,%.17g,%d,%d", st.dm_lo, st.dm_step, st.n_dm, st.ds);
+        k += buf;
+    }
+    snprintf(buf, sizeof buf, "|%d,%d,%.17g,%.17g,%.17g,%d,%d,%d", c->zmax, c->numharm, c->dz, c->sigma_thr,
+             c->f_lo_hz, c->whiten_block, c->halfwidth_extra, c->min_dm_hits);
+    k += buf;
+    return k;
+}
+
+std::mutex g_tune_mu;
+std::map<std::string, Tune> g_tuned;
+
+pss_status autotune(pss_ctx* ctx, const Plan& plan, const pss_fil_desc* fil, const pss_search_cfg* cfg) {
+    const char* env = getenv("PSS_AUTOTUNE");
+    if (env && env[0] == '0') return PSS_OK;
+    const std::string key = tune_key(plan, fil, cfg);
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            ctx->tune = it->second;
+            return PSS_OK;
+        }
+    }
+    cudaStream_t s = ctx->stream;
+    const int64_t nt = std::min<int64_t>(plan.ndm(), 128);
+    const pss_plan* pp = static_cast<const pss_plan*>(&plan);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PSS_CUDA(cudaEventCreate(&e0));
+    PSS_CUDA(cudaEventCreate(&e1));
+    auto measure = [&](float* ms) -> pss_status {
+        PathSetup T;
+        PSS_TRY(setup_path(ctx, pp, fil, cfg, 0, nt, MODE_SEARCH, s, kBatchInitialCap, &T));
+        const uint8_t* src = (const uint8_t*)ctx->fil_dev.p;
+        PSS_TRY(enqueue_path(ctx, pp, fil, src, cfg, 0, T, MODE_SEARCH, Outputs(), s));
+        PSS_CUDA(cudaEventRecord(e0, s));
+        PSS_TRY(enqueue_path(ctx, pp, fil, src, cfg, 0, T, MODE_SEARCH, Outputs(), s));
+        PSS_CUDA(cudaEventRecord(e1, s));
+        PSS_CUDA(cudaEventSynchronize(e1));
+        PSS_CUDA(cudaEventElapsedTime(ms, e0, e1));
+        return check_errflag(ctx, s);
+    };
+    auto sweep = [&](int* field, const std::vector<int>& cands, const char* what) -> pss_status {
+        int best = *field;
+        float best_ms = 1e30f;
+        for (int v : cands) {
+            *field = v;
+            float ms = 0.f;
+            PSS_TRY(measure(&ms));
+            if (getenv("PSS_TIMING")) fprintf(stderr, "[pss] tune %-10s %5d: %8.3f ms\n", what, v, ms);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = v;
+            }
+        }
+        *field = best;
+        return PSS_OK;
+    };
+    pss_status st = PSS_OK;
+    {
+        // FFT pass splits of the first stage's size
+        std::vector<int> fv;
+        int rad[4];
+        for (int v = 0; v < 6 && fft_pass_plan(plan.stages[0].nfft / 2, v, rad) > 0; ++v) fv.push_back(v);
+        st = sweep(&ctx->tune.fft_variant, fv, "fft split");
+        if (st == PSS_OK) st = sweep(&ctx->tune.harm_run, {16, 8}, "harm run");
+        if (st == PSS_OK) st = sweep(&ctx->tune.dedisp_kb, {96, 64}, "dedisp kb");
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != PSS_OK) {
+        ctx->tune = Tune();
+        return st;
+    }
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tuned.emplace(key, ctx->tune);
+    return PSS_OK;
+}
+
 // (Re)build the set-up for the full DM range with candidate capacity `cap`
 // and capture the kernel sequence into a graph (input: ctx->fil_dev).
 pss_status batch_build(pss_batch* b, int64_t cap) {
@@ -1199,7 +1306,13 @@ extern "C" pss_status pss_batch_create(int device, const pss_plan* plan, const p
         b->fil.chan_mask = b->mask.data();
     }
     b->cfg = *cfg;
-    st = batch_build(b, kBatchInitialCap);
+    st = b->ctx->fil_dev.ensure((size_t)file_bytes(&b->fil));
+    if (st == PSS_OK) {
+        // tune on a constant file (the kernels' work does not depend on the values)
+        cudaError_t e = cudaMemsetAsync(b->ctx->fil_dev.p, 0x80, (size_t)file_bytes(&b->fil), b->ctx->stream);
+        st = e == cudaSuccess ? autotune(b->ctx, b->plan, &b->fil, &b->cfg) : cuda_fail(e, "cudaMemsetAsync");
+    }
+    if (st == PSS_OK) st = batch_build(b, kBatchInitialCap);
     if (st != PSS_OK) {
         const std::string msg = pss_last_error();
         pss_batch_free(b);
@@ -1266,6 +1379,14 @@ extern "C" pss_status pss_search_footprint(const pss_plan* plan, const pss_fil_d
 }
 
 extern "C" size_t pss_batch_footprint(const pss_batch* b) { return b ? b->footprint : 0; }
+
+extern "C" pss_status pss_batch_tuning(const pss_batch* b, int32_t* fft_split, int32_t* harm_run, int32_t* dedisp_kb) {
+    if (!b) return fail(PSS_EINVAL, "pss_batch_tuning: null batch");
+    if (fft_split) *fft_split = b->ctx->tune.fft_variant;
+    if (harm_run) *harm_run = b->ctx->tune.harm_run;
+    if (dedisp_kb) *dedisp_kb = b->ctx->tune.dedisp_kb;
+    return PSS_OK;
+}
 
 extern "C" pss_status pss_batch_run(pss_batch* b, const void* data, int data_on_device, pss_cand* out, int64_t cap,
                                     int64_t* n_out, double* gpu_ms) {

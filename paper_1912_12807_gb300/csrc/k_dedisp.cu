@@ -335,7 +335,8 @@ cudaError_t launch_dedisp(const DedispArgs& a, int num_sms, cudaStream_t s) {
     int RW = 32 * KW + (15 + a.spread) / 4 + 1;
     RW = (RW + 3) & ~3;
     const size_t per_chan = (size_t)16 * RW + (4 * RW + 16);
-    int CC = (int)((96 * 1024) / per_chan);  // two CTAs per SM fit beside the rest
+    const int kb = a.chunk_kb > 0 ? a.chunk_kb : 96;  // 96 KiB: two CTAs per SM fit beside the rest
+    int CC = (int)(((size_t)kb * 1024) / per_chan);
     if (CC > 32) CC = 32;
     if (CC < 1) CC = 1;
     if (15 + a.spread > 65535 - 4 * RW) return cudaErrorInvalidValue;  // offsets are 16-bit

@@ -404,24 +404,50 @@ __global__ void __launch_bounds__(256) k_r2c_whiten(const float2* Zall, int64_t 
     }
 }
 
-void radix_plan(int64_t M, int* rad, int* np) {
+// Pass radices of an M-point FFT, M = 2^L: the fewest passes of radix
+// 2^5 .. 2^10 (ceil(L / 10)); variant 0 splits L evenly, larger parts
+// first; variants 1.. are the other splits of L into that many parts within
+// [5, 10] (used by the autotuner).  Returns false past the last variant.
+bool radix_variant(int64_t M, int variant, int* rad, int* np) {
     int L = 0;
     while ((int64_t(1) << L) < M) ++L;
     int p = (L + 9) / 10;
     if (p < 1) p = 1;
-    // split L into p parts, larger ones first
-    for (int i = 0; i < p; ++i) {
-        int li = L / p + (i < L % p ? 1 : 0);
-        rad[i] = 1 << li;
+    int parts[4];
+    for (int i = 0; i < p; ++i) parts[i] = L / p + (i < L % p ? 1 : 0);
+    int v = 0;
+    if (variant > 0) {
+        // enumerate compositions of L into p parts in [5, 10], skipping the even split
+        int c[4] = {5, 5, 5, 5};
+        bool found = false;
+        while (!found) {
+            int sum = 0;
+            for (int i = 0; i < p; ++i) sum += c[i];
+            bool even = true;
+            for (int i = 0; i < p; ++i) even &= (c[i] == parts[i]);
+            if (sum == L && !even && ++v == variant) {
+                for (int i = 0; i < p; ++i) parts[i] = c[i];
+                found = true;
+                break;
+            }
+            int i = p - 1;
+            while (i >= 0 && c[i] == 10) c[i--] = 5;
+            if (i < 0) return false;
+            ++c[i];
+        }
     }
+    for (int i = 0; i < p; ++i) rad[i] = 1 << parts[i];
     *np = p;
+    return true;
 }
+
+void radix_plan(int64_t M, int* rad, int* np) { radix_variant(M, 0, rad, np); }
 
 }  // namespace
 
-int fft_pass_plan(int64_t M, int* rad) {
+int fft_pass_plan(int64_t M, int variant, int* rad) {
     int np = 0;
-    radix_plan(M, rad, &np);
+    if (!radix_variant(M, variant, rad, &np)) return 0;
     return np;
 }
 
@@ -451,7 +477,7 @@ cudaError_t launch_fft_whiten(const FftArgs& a, cudaStream_t s, Ctx* prof_ctx) {
     if (M < 64 || (M & (M - 1)) != 0) return cudaErrorInvalidValue;
     if (!a.tw || a.twM < a.nfft || a.twM % a.nfft) return cudaErrorInvalidValue;
     int rad[4], np = 0;
-    radix_plan(M, rad, &np);
+    if (!radix_variant(M, a.fft_variant, rad, &np)) return cudaErrorInvalidValue;
     for (int i = 0; i < np; ++i)
         if (rad[i] < 32 || rad[i] > 1024) return cudaErrorInvalidValue;
     PassArgs p{};

@@ -326,6 +326,9 @@ cudaError_t launch_harm(const HarmArgs& a, cudaStream_t s) {
     if (a.nfft > (int64_t(1) << 24) || a.nstages > 6) return cudaErrorInvalidValue;
     if ((int64_t)a.nz * a.nfft > (int64_t(1) << 31)) return cudaErrorInvalidValue;  // 32-bit plane offsets
     // register-blocked kernel: up to 16 harmonics, whole warps of 32 x 16 points
+    if (a.run == 8 && a.nstages <= 5 && a.nfft % (REG_NT * 8) == 0 && a.nfft / (REG_NT * 8) <= 65535 &&
+        a.nb <= 65535)
+        return launch_reg<8>(a, s);
     if (a.nstages <= 5 && a.nfft % (REG_NT * 16) == 0 && a.nfft / (REG_NT * 16) <= 65535 && a.nb <= 65535)
         return launch_reg<16>(a, s);
     if (a.nz == 1) return launch_variant<1, 2048, true>(a, s);

@@ -133,7 +133,7 @@ extern "C" pss_status pss_dedisperse_noalloc(const pss_plan* plan, const pss_fil
                     }
                     spread = std::max(spread, mx - mn);
                 }
-            DedispArgs da;
+            DedispArgs da{};
             da.xcm = d_xcm;
             da.pitch = pitch;
             da.ck = ck;

@@ -112,6 +112,14 @@ struct DevBuf {
     void release();
 };
 
+// Launch-shape choices the autotuner may change (pss_batch_create); the
+// defaults are what untuned calls use.
+struct Tune {
+    int fft_variant = 0;   // FFT pass split
+    int harm_run = 16;     // harmonic-sum points per lane
+    int dedisp_kb = 96;    // dedispersion chunk staging budget
+};
+
 struct Ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -135,6 +143,7 @@ struct Ctx {
     // inter-pass twiddle tables of each FFT size in use (later passes, laid out like their data)
     struct PassTw {
         int64_t M = 0, twM = 0;
+        int variant = 0;
         DevBuf buf;
         int64_t off[4] = {0, 0, 0, 0};
     };
@@ -151,6 +160,7 @@ struct Ctx {
     int32_t tap_zmax = -1, tap_extra = -1;
     double tap_dz = 0.0;
     bool ftap_ok = false;  // ftaps hold the spectra of the current templates
+    Tune tune;             // launch shapes (set by the autotuner of a prepared batch)
     // sifted candidates of the last whole-file search (pss_ctx_take_cands)
     std::vector<pss_cand> last_cands;
     bool has_last = false;
@@ -217,6 +227,7 @@ struct DedispArgs {
     unsigned long long* sums;  // [nb] or null
     int32_t spread;         // max over groups/channels of (dmax - dmin)
     int* err;               // set to 1 if a bounded wait expires (nullable)
+    int32_t chunk_kb;       // shared memory for staged channel chunks (0: default)
 };
 int dedisp_tile_samples();
 int dedisp_group_trials();  // consecutive trials sharing one staged tile
@@ -240,10 +251,12 @@ struct FftArgs {
     float* gains_out;                 // nullable [nb][gains_stride]: ln 2 / med_b per block
     int64_t gains_stride;
     const float2* ptw[4];             // inter-pass twiddle tables of passes 1.. (fft_pass_plan)
+    int32_t fft_variant;              // pass split (fft_pass_plan variant)
 };
 cudaError_t launch_twiddles(float2* tw, int64_t n, cudaStream_t s);
-// Radices of the passes of an M-point FFT (returns the pass count, <= 3).
-int fft_pass_plan(int64_t M, int* rad);
+// Radices of the passes of an M-point FFT for split `variant` (0 = default);
+// returns the pass count (<= 3), or 0 past the last variant.
+int fft_pass_plan(int64_t M, int variant, int* rad);
 cudaError_t launch_pass_twiddles(float2* out, const float2* tw, int64_t twM, int R, int64_t Ns, cudaStream_t s);
 cudaError_t launch_fft_whiten(const FftArgs& a, cudaStream_t s, Ctx* prof_ctx);
 
@@ -312,8 +325,10 @@ struct HarmArgs {
     pss_raw_cand* out;
     unsigned long long* counter;
     int64_t cap;
+    int32_t run;        // points per lane of the register-blocked kernel (16 or 8; 0: 16)
 };
 cudaError_t launch_harm(const HarmArgs& a, cudaStream_t s);
+
 
 struct RefinePt {
     int32_t trial;    // index into the prepared stage's gains table

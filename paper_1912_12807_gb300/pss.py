@@ -64,7 +64,7 @@ EXPORTS = ["pss_ctx_create", "pss_ctx_destroy", "pss_last_error", "pss_version",
            "pss_power_threshold", "pss_ctx_profile", "pss_ctx_profile_read", "pss_dedisperse_noalloc",
            "pss_refine_prepare", "pss_refine_eval", "pss_refine_candidates", "pss_batch_create", "pss_batch_run",
            "pss_batch_footprint", "pss_batch_free", "pss_search_footprint", "pss_ctx_take_cands",
-           "pss_batch_take_cands", "pss_server_create", "pss_submit_file", "pss_poll",
+           "pss_batch_take_cands", "pss_batch_tuning", "pss_server_create", "pss_submit_file", "pss_poll",
            "pss_result_cands", "pss_result_free", "pss_server_stats", "pss_server_destroy"]
 PROFILE_STAGES = ["unpack", "dedisperse", "fft", "whiten", "plane", "harmsum"]
 
@@ -112,6 +112,7 @@ def lib():
         "pss_batch_free": (None, [vp]),
         "pss_ctx_take_cands": (st, [vp, vp, i64, P(i64)]),
         "pss_batch_take_cands": (st, [vp, vp, i64, P(i64)]),
+        "pss_batch_tuning": (st, [vp, P(i32), P(i32), P(i32)]),
         "pss_search_footprint": (st, [vp, P(pss_fil_desc), P(pss_search_cfg), P(C.c_size_t)]),
         "pss_server_create": (st, [C.c_int, C.c_size_t, C.c_int, P(vp)]),
         "pss_submit_file": (st, [vp, P(pss_fil_desc), vp, P(pss_dd_stage), C.c_int, P(pss_search_cfg),
@@ -386,6 +387,13 @@ class Batch:
     @property
     def footprint(self) -> int:
         return int(lib().pss_batch_footprint(self.h))
+
+    @property
+    def tuning(self):
+        """{fft_split, harm_run, dedisp_kb} chosen by the batch's autotuner."""
+        f, h, d = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(lib().pss_batch_tuning(self.h, C.byref(f), C.byref(h), C.byref(d)))
+        return {"fft_split": f.value, "harm_run": h.value, "dedisp_kb": d.value}
 
     def run(self, data, cap: int = 1 << 14, timing: bool = False):
         """Sifted candidates of one file (host array or device tensor; a device

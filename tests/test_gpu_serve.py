@@ -11,6 +11,13 @@ from paper_1912_12807_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 
+@pytest.fixture(autouse=True)
+def untuned(monkeypatch):
+    # byte-for-byte comparisons with the untuned plain call: keep the default
+    # launch shapes (the tuned FFT split changes FP32 rounding only)
+    monkeypatch.setenv("PSS_AUTOTUNE", "0")
+
+
 @pytest.fixture(scope="module")
 def L():
     from paper_1912_12807_gb300 import pss
@@ -182,3 +189,35 @@ def test_take_cands_after_ecap_needs_no_second_search(L, ctx):
     fresh = L.Context(0)
     assert L.lib().pss_ctx_take_cands(fresh.h, out.ctypes.data, n.value, C.byref(n)) == L.PSS_EINVAL
     fresh.close()
+
+
+def test_autotuned_batch_and_server(L, ctx, monkeypatch):
+    monkeypatch.setenv("PSS_AUTOTUNE", "1")
+    a, c = _case_a(1001), _case_a(5151)
+    plan = L.Plan(L.FilDesc.of(a.fil), a.stages)
+    cfg = L.cfg_of(a.cfg)
+    b = L.Batch(plan, cfg)
+    t = b.tuning
+    assert t["harm_run"] in (8, 16) and t["dedisp_kb"] in (64, 96) and t["fft_split"] >= 0
+    got, ref = b.run(a.fil.data), _alone(L, ctx, a)
+    # same detections; powers within the parity tolerance of the untuned search
+    key = lambda x: set(zip(x["dm_idx"].tolist(), x["numharm"].tolist(), x["h"].tolist(), x["j"].tolist()))
+    assert len(key(got) ^ key(ref)) <= max(2, len(ref) // 50)
+    common = {k: p for k, p in zip(zip(ref["dm_idx"].tolist(), ref["numharm"].tolist(), ref["h"].tolist(),
+                                       ref["j"].tolist()), ref["power"].tolist())}
+    for row in got:
+        k = (int(row["dm_idx"]), int(row["numharm"]), int(row["h"]), int(row["j"]))
+        if k in common:
+            assert abs(row["power"] - common[k]) <= 1e-4 * max(common[k], 1.0)
+    b2 = L.Batch(plan, cfg)
+    assert b2.tuning == t  # remembered per shape
+    b2.close()
+    b.close()
+    # served: alone and in a mix give the same bytes (one tuning per shape)
+    srv = L.Server(8 << 30, max_slots=2)
+    desc = L.FilDesc.of(a.fil)
+    alone = srv.poll(srv.submit(desc, a.fil.data, a.stages, cfg), 120000)[0]
+    ts = [srv.submit(L.FilDesc.of(w.fil), w.fil.data, w.stages, L.cfg_of(w.cfg)) for w in (c, a, _case_b(), a)]
+    outs = [srv.poll(t, 120000)[0] for t in ts]
+    assert _same(outs[1], alone) and _same(outs[3], alone)
+    srv.close()
