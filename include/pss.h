@@ -356,13 +356,16 @@ pss_status pss_batch_take_cands(pss_batch* b, pss_cand* out, int64_t cap, int64_
 /* Device bytes held by the batch. */
 size_t pss_batch_footprint(const pss_batch* b);
 /* Launch shapes the batch's autotuner chose (pss_batch_create times each
- * choice on the first <= 128 trials of the shape and keeps the fastest;
+ * choice on the first <= 256 trials of the shape, timing the stage it
+ * changes, and keeps the fastest;
  * the choice is remembered per shape for the life of the process;
- * environment PSS_AUTOTUNE=0 keeps the defaults 0 / 16 / 96):
+ * environment PSS_AUTOTUNE=0 keeps the defaults 0 / 16 / 96 / 0):
  * fft_split: FFT pass-split variant (0 = even split), harm_run: points per
  * lane of the harmonic sum (16 or 8), dedisp_kb: shared memory for staged
- * channel chunks (KiB).  Pointers are nullable. */
-pss_status pss_batch_tuning(const pss_batch* b, int32_t* fft_split, int32_t* harm_run, int32_t* dedisp_kb);
+ * channel chunks (KiB), whiten_form: whitening median per CTA (0) or per
+ * warp (1).  Pointers are nullable. */
+pss_status pss_batch_tuning(const pss_batch* b, int32_t* fft_split, int32_t* harm_run, int32_t* dedisp_kb,
+                            int32_t* whiten_form);
 /* Device bytes a batch for this shape will hold, computed on the host
  * without a device (what the server admits files by).  PSS_EINVAL for the
  * arguments pss_batch_create would reject. */

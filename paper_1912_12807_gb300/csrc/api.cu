@@ -494,6 +494,7 @@ pss_status enqueue_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* 
         fa.tw = (const float2*)ctx->twid.p;
         fa.twM = ctx->twid_n;
         fa.fft_variant = ctx->tune.fft_variant;
+        fa.whiten_form = ctx->tune.whiten_form;
         set_passtw(ctx, &fa);
         fa.whiten = 1;
         fa.gains_out = nullptr;
@@ -1155,13 +1156,14 @@ void batch_release_graph(pss_batch* b) {
 // ---- autotuner ----------------------------------------------------------------
 //
 // A prepared batch picks its launch shapes by timing them: on the first
-// min(ndm, 128) trials of its file shape (the input in ctx->fil_dev), each
-// choice is tried in turn (FFT pass split, then harmonic-sum points per
-// lane, then the dedispersion chunk budget), each candidate run once to warm
-// and once timed with CUDA events over the whole kernel sequence, and the
+// min(ndm, 256) trials of its file shape (the input in ctx->fil_dev), each
+// choice is tried in turn (FFT pass split, harmonic-sum points per lane,
+// dedispersion chunk budget, whitening form), each candidate run once to
+// warm and once with the stage it changes timed by CUDA events, and the
 // fastest kept.  The result is remembered per shape for the life of the
 // process, so every batch of a shape (and so every file of that shape in a
-// server) runs the same kernels.  PSS_AUTOTUNE=0 disables it.
+// server) runs the same kernels.  PSS_AUTOTUNE=0 disables it; PSS_TUNE pins
+// the choices.
 
 std::string tune_key(const Plan& plan, const pss_fil_desc* f, const pss_search_cfg* c) {
     std::string k;
@@ -1184,6 +1186,18 @@ std::mutex g_tune_mu;
 std::map<std::string, Tune> g_tuned;
 
 pss_status autotune(pss_ctx* ctx, const Plan& plan, const pss_fil_desc* fil, const pss_search_cfg* cfg) {
+    // PSS_TUNE="fft,harm,dedisp,whiten" pins the launch shapes instead (not remembered)
+    if (const char* pin = getenv("PSS_TUNE")) {
+        Tune t;
+        if (sscanf(pin, "%d,%d,%d,%d", &t.fft_variant, &t.harm_run, &t.dedisp_kb, &t.whiten_form) != 4)
+            return fail(PSS_EINVAL, "PSS_TUNE must be four integers: fft split, harm run, dedisp KiB, whiten form");
+        int rad[4];
+        if (fft_pass_plan(plan.stages[0].nfft / 2, t.fft_variant, rad) == 0 || (t.harm_run != 8 && t.harm_run != 16) ||
+            t.dedisp_kb < 16 || t.dedisp_kb > 200 || (t.whiten_form != 0 && t.whiten_form != 1))
+            return fail(PSS_EINVAL, "PSS_TUNE value out of range");
+        ctx->tune = t;
+        return PSS_OK;
+    }
     const char* env = getenv("PSS_AUTOTUNE");
     if (env && env[0] == '0') return PSS_OK;
     const std::string key = tune_key(plan, fil, cfg);
@@ -1196,30 +1210,32 @@ pss_status autotune(pss_ctx* ctx, const Plan& plan, const pss_fil_desc* fil, con
         }
     }
     cudaStream_t s = ctx->stream;
-    const int64_t nt = std::min<int64_t>(plan.ndm(), 128);
+    const int64_t nt = std::min<int64_t>(plan.ndm(), 256);
     const pss_plan* pp = static_cast<const pss_plan*>(&plan);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    PSS_CUDA(cudaEventCreate(&e0));
-    PSS_CUDA(cudaEventCreate(&e1));
-    auto measure = [&](float* ms) -> pss_status {
+    // time of profiler stage `stage` (1 dedisperse, 2 FFT, 3 whiten, 5 harmonic sum) over one
+    // warm pass; the kernels of the other stages do not change with the choice being tuned
+    auto measure = [&](int stage, float* ms) -> pss_status {
         PathSetup T;
         PSS_TRY(setup_path(ctx, pp, fil, cfg, 0, nt, MODE_SEARCH, s, kBatchInitialCap, &T));
         const uint8_t* src = (const uint8_t*)ctx->fil_dev.p;
         PSS_TRY(enqueue_path(ctx, pp, fil, src, cfg, 0, T, MODE_SEARCH, Outputs(), s));
-        PSS_CUDA(cudaEventRecord(e0, s));
+        PSS_TRY(pss_ctx_profile(ctx, 1));
         PSS_TRY(enqueue_path(ctx, pp, fil, src, cfg, 0, T, MODE_SEARCH, Outputs(), s));
-        PSS_CUDA(cudaEventRecord(e1, s));
-        PSS_CUDA(cudaEventSynchronize(e1));
-        PSS_CUDA(cudaEventElapsedTime(ms, e0, e1));
+        double st_ms[PSS_NPROF_STAGES];
+        int64_t n[PSS_NPROF_STAGES];
+        pss_status r = pss_ctx_profile_read(ctx, st_ms, n);
+        pss_ctx_profile(ctx, 0);
+        PSS_TRY(r);
+        *ms = (float)st_ms[stage];
         return check_errflag(ctx, s);
     };
-    auto sweep = [&](int* field, const std::vector<int>& cands, const char* what) -> pss_status {
+    auto sweep = [&](int* field, const std::vector<int>& cands, int stage, const char* what) -> pss_status {
         int best = *field;
         float best_ms = 1e30f;
         for (int v : cands) {
             *field = v;
             float ms = 0.f;
-            PSS_TRY(measure(&ms));
+            PSS_TRY(measure(stage, &ms));
             if (getenv("PSS_TIMING")) fprintf(stderr, "[pss] tune %-10s %5d: %8.3f ms\n", what, v, ms);
             if (ms < best_ms) {
                 best_ms = ms;
@@ -1235,12 +1251,11 @@ pss_status autotune(pss_ctx* ctx, const Plan& plan, const pss_fil_desc* fil, con
         std::vector<int> fv;
         int rad[4];
         for (int v = 0; v < 6 && fft_pass_plan(plan.stages[0].nfft / 2, v, rad) > 0; ++v) fv.push_back(v);
-        st = sweep(&ctx->tune.fft_variant, fv, "fft split");
-        if (st == PSS_OK) st = sweep(&ctx->tune.harm_run, {16, 8}, "harm run");
-        if (st == PSS_OK) st = sweep(&ctx->tune.dedisp_kb, {96, 64}, "dedisp kb");
+        st = sweep(&ctx->tune.fft_variant, fv, 2, "fft split");
+        if (st == PSS_OK) st = sweep(&ctx->tune.harm_run, {16, 8}, 5, "harm run");
+        if (st == PSS_OK) st = sweep(&ctx->tune.dedisp_kb, {96, 64}, 1, "dedisp kb");
+        if (st == PSS_OK) st = sweep(&ctx->tune.whiten_form, {0, 1}, 3, "whiten");
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     if (st != PSS_OK) {
         ctx->tune = Tune();
         return st;
@@ -1380,11 +1395,13 @@ extern "C" pss_status pss_search_footprint(const pss_plan* plan, const pss_fil_d
 
 extern "C" size_t pss_batch_footprint(const pss_batch* b) { return b ? b->footprint : 0; }
 
-extern "C" pss_status pss_batch_tuning(const pss_batch* b, int32_t* fft_split, int32_t* harm_run, int32_t* dedisp_kb) {
+extern "C" pss_status pss_batch_tuning(const pss_batch* b, int32_t* fft_split, int32_t* harm_run, int32_t* dedisp_kb,
+                                       int32_t* whiten_form) {
     if (!b) return fail(PSS_EINVAL, "pss_batch_tuning: null batch");
     if (fft_split) *fft_split = b->ctx->tune.fft_variant;
     if (harm_run) *harm_run = b->ctx->tune.harm_run;
     if (dedisp_kb) *dedisp_kb = b->ctx->tune.dedisp_kb;
+    if (whiten_form) *whiten_form = b->ctx->tune.whiten_form;
     return PSS_OK;
 }
 

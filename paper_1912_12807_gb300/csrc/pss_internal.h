@@ -118,6 +118,7 @@ struct Tune {
     int fft_variant = 0;   // FFT pass split
     int harm_run = 16;     // harmonic-sum points per lane
     int dedisp_kb = 96;    // dedispersion chunk staging budget
+    int whiten_form = 0;   // whitening kernel form
 };
 
 struct Ctx {
@@ -252,6 +253,7 @@ struct FftArgs {
     int64_t gains_stride;
     const float2* ptw[4];             // inter-pass twiddle tables of passes 1.. (fft_pass_plan)
     int32_t fft_variant;              // pass split (fft_pass_plan variant)
+    int32_t whiten_form;              // 0: block-per-CTA median, 1: warp-per-block median
 };
 cudaError_t launch_twiddles(float2* tw, int64_t n, cudaStream_t s);
 // Radices of the passes of an M-point FFT for split `variant` (0 = default);
