@@ -221,6 +221,22 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def recorded_traffic(workload, stage):
+    """DRAM bytes per launch of a stage's kernel from the committed ncu capture
+    (profiles/dram_traffic.json), or None when there is none or the kernel
+    source has changed since it was taken."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        rec = json.load(open(p))[workload][stage]
+        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+    except (OSError, KeyError, ValueError):
+        return None
+    if hashlib.sha1(src).hexdigest() != rec["source_sha1"]:
+        return None
+    return float(rec["dram_read_bytes"]) + float(rec["dram_write_bytes"])
+
+
 def stage_work(plan, wl, fil_nbytes):
     """Algorithmic work of one step per profiled stage: (bound, amount, unit).
 
@@ -406,6 +422,8 @@ def run_ours(args, rank, world, local_rank):
             continue
         bound, amount, unit = work[st]
         rooflines[st] = roofline_of(st, bound, amount * args.steps, unit, ms_st, n_st, peaks, peak_kind)
+        if args.dm_trials is None:
+            rooflines[st]["traffic"] = recorded_traffic(name, st)
     dominant = max(prof, key=lambda k: prof[k][0])
     launches_per_step = sum(n for _, n in prof.values()) / args.steps
     bi = fil.nbytes()
