@@ -380,7 +380,8 @@ int64_t batch_trials(int64_t nfft, int nz, Mode mode, int64_t n) {
 // kernel sequence (enqueue_path) allocates nothing and never waits on the
 // host, so it can be captured into a CUDA graph.
 pss_status setup_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const pss_search_cfg* cfg,
-                      int64_t dm_begin, int64_t dm_end, Mode mode, cudaStream_t s, int64_t dev_cap, PathSetup* P) {
+                      int64_t dm_begin, int64_t dm_end, Mode mode, cudaStream_t s, int64_t dev_cap, PathSetup* P,
+                      int64_t max_b = 0) {
     PSS_TRY(setup_input(ctx, plan, fil, dm_begin, dm_end, s, &P->ck, &P->pitch));
     P->batches.clear();
     P->harm.clear();
@@ -421,7 +422,8 @@ pss_status setup_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fi
         P->harm.push_back(ha);
         if (lo >= hi) continue;
         const int64_t nfft = st.nfft, M = nfft / 2;
-        const int64_t B = batch_trials(nfft, P->nz, mode, hi - lo);
+        int64_t B = batch_trials(nfft, P->nz, mode, hi - lo);
+        if (max_b > 0) B = std::min(B, max_b);
         need_series = std::max(need_series, (size_t)B * nfft * 4);
         need_sums = std::max(need_sums, (size_t)B * 8);
         need_fft = std::max(need_fft, (size_t)B * M * 8);
@@ -450,7 +452,7 @@ pss_status setup_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fi
 // then per batch dedisperse, FFT + whiten, plane, harmonic sums.
 pss_status enqueue_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const uint8_t* src,
                         const pss_search_cfg* cfg, int64_t dm_begin, const PathSetup& P, Mode mode, Outputs outs,
-                        cudaStream_t s) {
+                        cudaStream_t s, bool snapshots = false) {
     PSS_TRY(enqueue_prep(ctx, fil, src, P.ck, P.pitch, s));
     if (P.batches.empty()) return PSS_OK;
     const int32_t* dtab = (const int32_t*)ctx->delays_dev.p + P.ck;
@@ -556,6 +558,20 @@ pss_status enqueue_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* 
             ProfScope ps(ctx, 5, s);
             PSS_CUDA(launch_harm(ha, s));
         }
+        if (snapshots) {
+            // detection count after this batch, then an event the host can wait on
+            const size_t bi = (size_t)(&d - P.batches.data());
+            PSS_CUDA(cudaMemcpyAsync(ctx->batch_cnt + bi, ctx->counter.p, sizeof(unsigned long long),
+                                     cudaMemcpyDeviceToHost, s));
+            // under stream capture the record must be external (an event-record node the host can
+            // wait on); outside capture that flag is refused
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            PSS_CUDA(cudaStreamIsCapturing(s, &cs));
+            if (cs == cudaStreamCaptureStatusActive)
+                PSS_CUDA(cudaEventRecordWithFlags(ctx->batch_ev[bi], s, cudaEventRecordExternal));
+            else
+                PSS_CUDA(cudaEventRecord(ctx->batch_ev[bi], s));
+        }
     }
     return PSS_OK;
 }
@@ -600,6 +616,105 @@ pss_status check_errflag(pss_ctx* ctx, cudaStream_t s) {
         return fail(PSS_EINVAL, "dedispersion refused a delay spread larger than its launch was sized for; results discarded");
     }
     return PSS_OK;
+}
+
+// Events and pinned count slots for n DM batches, and a stream for downloads.
+pss_status ensure_snapshots(pss_ctx* ctx, int n) {
+    if (!ctx->stream2) PSS_CUDA(cudaStreamCreateWithFlags(&ctx->stream2, cudaStreamNonBlocking));
+    while ((int)ctx->batch_ev.size() < n) {
+        cudaEvent_t e = nullptr;
+        PSS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ctx->batch_ev.push_back(e);
+    }
+    if (ctx->batch_cnt_n < n) {
+        if (ctx->batch_cnt) cudaFreeHost(ctx->batch_cnt);
+        ctx->batch_cnt = nullptr;
+        ctx->batch_cnt_n = 0;
+        PSS_CUDA(cudaHostAlloc((void**)&ctx->batch_cnt, (size_t)n * sizeof(unsigned long long), cudaHostAllocDefault));
+        ctx->batch_cnt_n = n;
+    }
+    return PSS_OK;
+}
+
+pss_status ensure_raw_pinned(pss_ctx* ctx, size_t n) {
+    if (ctx->raw_pinned_n >= n) return PSS_OK;
+    if (ctx->raw_pinned) cudaFreeHost(ctx->raw_pinned);
+    ctx->raw_pinned = nullptr;
+    ctx->raw_pinned_n = 0;
+    const size_t want = n + n / 4 + 4096;
+    PSS_CUDA(cudaHostAlloc((void**)&ctx->raw_pinned, want * sizeof(pss_raw_cand), cudaHostAllocDefault));
+    ctx->raw_pinned_n = want;
+    return PSS_OK;
+}
+
+// After the kernels of a search were enqueued with per-batch snapshots:
+// wait for each DM batch in turn, download its detections on the second
+// stream and run the within-trial sift on the host while the device works
+// on the later batches.  *overflow: a batch's count passed `cap` (its
+// detections are incomplete; the caller redoes the search larger).
+pss_status drain_batches(pss_ctx* ctx, const pss_plan* plan, const pss_search_cfg* cfg, size_t nbatches,
+                         int64_t cap, std::vector<SiftItem>* surv, bool* overflow, unsigned long long* total) {
+    *overflow = false;
+    unsigned long long prev = 0;
+    for (size_t i = 0; i < nbatches; ++i) {
+        PSS_CUDA(cudaEventSynchronize(ctx->batch_ev[i]));
+        const unsigned long long cnt = ctx->batch_cnt[i];
+        *total = cnt;
+        if (*overflow) continue;
+        if ((int64_t)cnt > cap) {
+            *overflow = true;
+            continue;
+        }
+        if (cnt > prev) {
+            PSS_TRY(ensure_raw_pinned(ctx, (size_t)(cnt - prev)));
+            PSS_CUDA(cudaStreamWaitEvent(ctx->stream2, ctx->batch_ev[i], 0));
+            PSS_CUDA(cudaMemcpyAsync(ctx->raw_pinned, (const pss_raw_cand*)ctx->cands.p + prev,
+                                     (size_t)(cnt - prev) * sizeof(pss_raw_cand), cudaMemcpyDeviceToHost,
+                                     ctx->stream2));
+            PSS_CUDA(cudaStreamSynchronize(ctx->stream2));
+            PSS_TRY(sift_within(*plan, *cfg, ctx->raw_pinned, (int64_t)(cnt - prev), surv));
+        }
+        prev = cnt;
+    }
+    return PSS_OK;
+}
+
+// The whole search of [dm_begin, dm_end) with its sift.  The trials run in
+// at least two DM batches so that the within-trial sift of the first ones
+// overlaps the device work of the later ones.
+pss_status search_pipelined(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const void* data, int on_dev,
+                            const pss_search_cfg* cfg, int64_t dm_begin, int64_t dm_end, cudaStream_t s,
+                            std::vector<pss_cand>* out) {
+    PSS_TRY(check_common(ctx, plan, fil, data, dm_begin, dm_end));
+    PSS_TRY(check_cfg(cfg, *plan));
+    out->clear();
+    if (dm_end == dm_begin) return PSS_OK;
+    int64_t cap = ctx->cands.bytes ? (int64_t)(ctx->cands.bytes / sizeof(pss_raw_cand)) : (int64_t)1 << 20;
+    const int64_t n = dm_end - dm_begin;
+    HostTimer tm;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        PathSetup P;
+        PSS_TRY(setup_path(ctx, plan, fil, cfg, dm_begin, dm_end, MODE_SEARCH, s, cap, &P, n >= 64 ? (n + 1) / 2 : 0));
+        const uint8_t* src = nullptr;
+        PSS_TRY(upload_input(ctx, fil, data, on_dev, s, &src));
+        PSS_TRY(ensure_snapshots(ctx, (int)P.batches.size()));
+        PSS_TRY(enqueue_path(ctx, plan, fil, src, cfg, dm_begin, P, MODE_SEARCH, Outputs(), s, true));
+        tm.mark("enqueue");
+        std::vector<SiftItem> surv;
+        bool overflow = false;
+        unsigned long long total = 0;
+        PSS_TRY(drain_batches(ctx, plan, cfg, P.batches.size(), cap, &surv, &overflow, &total));
+        PSS_CUDA(cudaStreamSynchronize(s));
+        tm.mark("gpu+within");
+        PSS_TRY(check_errflag(ctx, s));
+        if (!overflow) {
+            PSS_TRY(sift_across(*plan, *cfg, surv, out));
+            tm.mark("across");
+            return PSS_OK;
+        }
+        cap = (int64_t)total + 1024;  // overflowed the device buffer: grow and redo
+    }
+    return fail(PSS_ECAP, "candidate buffer overflow persisted after resizing");
 }
 
 pss_status search_raw_vec(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const void* data, int on_dev,
@@ -671,6 +786,10 @@ void pss_ctx_destroy(pss_ctx* c) {
                       &c->twid, &c->chan_spec, &c->refine_gains, &c->refine_dtau, &c->refine_pts, &c->refine_out};
     for (DevBuf* b : bufs) b->release();
     for (auto& t : c->passtw) t.buf.release();
+    for (cudaEvent_t e : c->batch_ev) cudaEventDestroy(e);
+    if (c->batch_cnt) cudaFreeHost(c->batch_cnt);
+    if (c->raw_pinned) cudaFreeHost(c->raw_pinned);
+    if (c->stream2) cudaStreamDestroy(c->stream2);
     for (auto& r : c->prof_recs) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -858,14 +977,10 @@ pss_status pss_search_dm_batch(pss_ctx* ctx, const pss_plan* plan, const pss_fil
     if (!n_out) return fail(PSS_EINVAL, "pss_search_dm_batch: null n_out");
     *n_out = 0;
     if (ctx) PSS_CUDA(cudaSetDevice(ctx->device));
-    std::vector<pss_raw_cand> raw;
-    PSS_TRY(search_raw_vec(ctx, plan, fil, data, data_on_device, cfg, dm_begin, dm_end, &raw,
-                           ctx ? pick_stream(ctx, stream) : nullptr, false));
+    if (!ctx) return fail(PSS_EINVAL, "null ctx");
     ctx->has_last = false;
-    ctx->last_cands.clear();
-    HostTimer tm;
-    PSS_TRY(sift(*plan, *cfg, raw.data(), (int64_t)raw.size(), &ctx->last_cands));
-    tm.mark("sift");
+    PSS_TRY(search_pipelined(ctx, plan, fil, data, data_on_device, cfg, dm_begin, dm_end, pick_stream(ctx, stream),
+                             &ctx->last_cands));
     ctx->has_last = true;
     return take_cands(ctx->last_cands, out, cap, n_out);
 }
@@ -1271,17 +1386,19 @@ pss_status batch_build(pss_batch* b, int64_t cap) {
     pss_ctx* ctx = b->ctx;
     cudaStream_t s = ctx->stream;
     batch_release_graph(b);
-    PSS_TRY(setup_path(ctx, static_cast<const pss_plan*>(&b->plan), &b->fil, &b->cfg, 0, b->plan.ndm(), MODE_SEARCH,
-                       s, cap, &b->P));
+    const int64_t n = b->plan.ndm();
+    PSS_TRY(setup_path(ctx, static_cast<const pss_plan*>(&b->plan), &b->fil, &b->cfg, 0, n, MODE_SEARCH, s, cap,
+                       &b->P, n >= 64 ? (n + 1) / 2 : 0));
     PSS_TRY(ctx->fil_dev.ensure((size_t)file_bytes(&b->fil)));
+    PSS_TRY(ensure_snapshots(ctx, (int)b->P.batches.size()));
     // one eager pass sets every kernel attribute before capture
     PSS_TRY(enqueue_path(ctx, static_cast<const pss_plan*>(&b->plan), &b->fil, (const uint8_t*)ctx->fil_dev.p,
-                         &b->cfg, 0, b->P, MODE_SEARCH, Outputs(), s));
+                         &b->cfg, 0, b->P, MODE_SEARCH, Outputs(), s, true));
     PSS_CUDA(cudaStreamSynchronize(s));
     // relaxed: the launchers call cudaFuncSetAttribute, which is not a stream operation
     PSS_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
     pss_status st = enqueue_path(ctx, static_cast<const pss_plan*>(&b->plan), &b->fil, (const uint8_t*)ctx->fil_dev.p,
-                                 &b->cfg, 0, b->P, MODE_SEARCH, Outputs(), s);
+                                 &b->cfg, 0, b->P, MODE_SEARCH, Outputs(), s, true);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(s, &g);
     if (st != PSS_OK) {
@@ -1413,7 +1530,8 @@ extern "C" pss_status pss_batch_run(pss_batch* b, const void* data, int data_on_
     PSS_CUDA(cudaSetDevice(ctx->device));
     cudaStream_t s = ctx->stream;
     const size_t nbytes = (size_t)file_bytes(&b->fil);
-    std::vector<pss_raw_cand> raw;
+    b->has_last = false;
+    b->last.clear();
     for (int attempt = 0; attempt < 2; ++attempt) {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (gpu_ms) {
@@ -1424,9 +1542,13 @@ extern "C" pss_status pss_batch_run(pss_batch* b, const void* data, int data_on_
         PSS_CUDA(cudaMemcpyAsync(ctx->fil_dev.p, data, nbytes,
                                  data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
         PSS_CUDA(cudaGraphLaunch(b->exec, s));
-        unsigned long long cnt = 0;
-        PSS_CUDA(cudaMemcpyAsync(&cnt, ctx->counter.p, sizeof(cnt), cudaMemcpyDeviceToHost, s));
         if (gpu_ms) cudaEventRecord(e1, s);
+        // the within-trial sift of each DM batch runs while the graph does the later ones
+        std::vector<SiftItem> surv;
+        bool overflow = false;
+        unsigned long long total = 0;
+        PSS_TRY(drain_batches(ctx, static_cast<const pss_plan*>(&b->plan), &b->cfg, b->P.batches.size(),
+                              b->P.dev_cap, &surv, &overflow, &total));
         PSS_CUDA(cudaStreamSynchronize(s));
         if (gpu_ms) {
             float ms = 0.f;
@@ -1436,22 +1558,16 @@ extern "C" pss_status pss_batch_run(pss_batch* b, const void* data, int data_on_
             cudaEventDestroy(e1);
         }
         PSS_TRY(check_errflag(ctx, s));
-        if ((int64_t)cnt <= b->P.dev_cap) {
-            raw.resize(cnt);
-            if (cnt)
-                PSS_CUDA(cudaMemcpyAsync(raw.data(), ctx->cands.p, cnt * sizeof(pss_raw_cand), cudaMemcpyDeviceToHost, s));
-            PSS_CUDA(cudaStreamSynchronize(s));
-            break;
+        if (!overflow) {
+            PSS_TRY(sift_across(b->plan, b->cfg, surv, &b->last));
+            b->has_last = true;
+            return take_cands(b->last, out, cap, n_out);
         }
         // the candidate buffer overflowed: rebuild with room for all of them and redo
-        PSS_TRY(batch_build(b, (int64_t)cnt + 1024));
-        if (attempt == 1) return fail(PSS_ECAP, "pss_batch_run: candidate buffer overflow persisted after resizing");
+        if (attempt == 1) break;
+        PSS_TRY(batch_build(b, (int64_t)total + 1024));
     }
-    b->has_last = false;
-    b->last.clear();
-    PSS_TRY(sift(b->plan, b->cfg, raw.data(), (int64_t)raw.size(), &b->last));
-    b->has_last = true;
-    return take_cands(b->last, out, cap, n_out);
+    return fail(PSS_ECAP, "pss_batch_run: candidate buffer overflow persisted after resizing");
 }
 
 extern "C" pss_status pss_batch_take_cands(pss_batch* b, pss_cand* out, int64_t cap, int64_t* n_out) {

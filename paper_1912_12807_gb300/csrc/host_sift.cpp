@@ -24,14 +24,7 @@ namespace pss {
 
 namespace {
 
-struct Item {
-    int32_t dm_idx, n, h, j;
-    float power;
-    double r, z;
-    double logp;   // log Q(n, S); NAN until evaluated
-    double sigma;  // -Phi^-1(Q); < 0 until evaluated
-    int64_t kr, kz;  // exact link coordinates: 64 r and 32 z / dz
-};
+using Item = SiftItem;
 
 double item_logp(Item& x) {
     if (x.logp != x.logp) x.logp = log_q(x.n, (double)x.power);
@@ -287,9 +280,8 @@ void sort_raw(std::vector<pss_raw_cand>* v, int64_t ndm) {
     v->swap(out);
 }
 
-pss_status sift(const Plan& P, const pss_search_cfg& cfg, const pss_raw_cand* raw, int64_t n,
-                std::vector<pss_cand>* out) {
-    out->clear();
+pss_status sift_within(const Plan& P, const pss_search_cfg& cfg, const pss_raw_cand* raw, int64_t n,
+                       std::vector<SiftItem>* out) {
     const int Z = cfg.zmax ? (int)llround(cfg.zmax / cfg.dz) : 0;
     const double dz = cfg.dz;
     for (int64_t i = 0; i < n; ++i) {
@@ -340,13 +332,24 @@ pss_status sift(const Plan& P, const pss_search_cfg& cfg, const pss_raw_cand* ra
             surv[(size_t)b].push_back(
                 items[pick_rep(items, G.members.data() + G.start[g], G.start[g + 1] - G.start[g], false)]);
     });
-    std::vector<Item> survivors;
-    for (auto& v : surv) survivors.insert(survivors.end(), v.begin(), v.end());
+    for (auto& v : surv) out->insert(out->end(), v.begin(), v.end());
     lap("within");
-    if (dbg) fprintf(stderr, "[pss] sift: %lld raw, %zu survive their trial\n", (long long)n, survivors.size());
+    if (dbg) fprintf(stderr, "[pss] sift: %lld raw, %zu survive their trial\n", (long long)n, out->size());
+    return PSS_OK;
+}
 
-    // across DM trials
-    const Groups G = link_groups(survivors, dz);
+pss_status sift_across(const Plan& P, const pss_search_cfg& cfg, std::vector<SiftItem>& survivors,
+                       std::vector<pss_cand>* out) {
+    out->clear();
+    const bool dbg = getenv("PSS_TIMING") != nullptr;
+    auto t0 = std::chrono::steady_clock::now();
+    auto lap = [&](const char* what) {
+        if (!dbg) return;
+        auto t1 = std::chrono::steady_clock::now();
+        fprintf(stderr, "[pss] sift.%-10s %8.3f ms\n", what, std::chrono::duration<double, std::milli>(t1 - t0).count());
+        t0 = t1;
+    };
+    const Groups G = link_groups(survivors, cfg.dz);
     lap("link");
     for (int g = 0; g < G.count(); ++g) {
         const int* mem = G.members.data() + G.start[g];
@@ -380,6 +383,13 @@ pss_status sift(const Plan& P, const pss_search_cfg& cfg, const pss_raw_cand* ra
         return a.z < b.z;
     });
     return PSS_OK;
+}
+
+pss_status sift(const Plan& P, const pss_search_cfg& cfg, const pss_raw_cand* raw, int64_t n,
+                std::vector<pss_cand>* out) {
+    std::vector<SiftItem> survivors;
+    PSS_TRY(sift_within(P, cfg, raw, n, &survivors));
+    return sift_across(P, cfg, survivors, out);
 }
 
 }  // namespace pss

@@ -103,6 +103,21 @@ pss_status take_cands(const std::vector<pss_cand>& v, pss_cand* out, int64_t cap
 // ---- sift (host) ----------------------------------------------------------
 pss_status sift(const Plan& P, const pss_search_cfg& cfg, const pss_raw_cand* raw, int64_t n,
                 std::vector<pss_cand>* out);
+// The two halves of sift: survivors of the within-trial linkage (appended to
+// *out; raw detections of one DM trial must all be in one call), then the
+// across-trial linkage of all survivors.
+struct SiftItem {
+    int32_t dm_idx, n, h, j;
+    float power;
+    double r, z;
+    double logp;     // log Q(n, S); NAN until evaluated
+    double sigma;    // -Phi^-1(Q); < 0 until evaluated
+    int64_t kr, kz;  // exact link coordinates: 64 r and 32 z / dz
+};
+pss_status sift_within(const Plan& P, const pss_search_cfg& cfg, const pss_raw_cand* raw, int64_t n,
+                       std::vector<SiftItem>* out);
+pss_status sift_across(const Plan& P, const pss_search_cfg& cfg, std::vector<SiftItem>& survivors,
+                       std::vector<pss_cand>* out);
 
 // ---- device workspace -----------------------------------------------------
 struct DevBuf {
@@ -162,6 +177,14 @@ struct Ctx {
     double tap_dz = 0.0;
     bool ftap_ok = false;  // ftaps hold the spectra of the current templates
     Tune tune;             // launch shapes (set by the autotuner of a prepared batch)
+    // pipelined search: a second stream for candidate downloads, one event and
+    // one pinned detection-count slot per DM batch
+    cudaStream_t stream2 = nullptr;
+    std::vector<cudaEvent_t> batch_ev;
+    unsigned long long* batch_cnt = nullptr;  // pinned host [batch_cnt_n]
+    int batch_cnt_n = 0;
+    pss_raw_cand* raw_pinned = nullptr;       // pinned host staging of downloaded detections
+    size_t raw_pinned_n = 0;
     // sifted candidates of the last whole-file search (pss_ctx_take_cands)
     std::vector<pss_cand> last_cands;
     bool has_last = false;
