@@ -498,12 +498,8 @@ def run_served(pss, name, wl, args, device):
     for t in ts:
         srv.poll(t)
     dt = time.perf_counter() - t0
-    srv.close()
-    # paced: arrivals every `gap` seconds (about half the measured capacity)
+    # paced (same server, batches prepared): arrivals every `gap` seconds (about half the measured capacity)
     gap = 2.0 * dt / n_files
-    srv = pss.Server(int(args.serve_budget_gib * (1 << 30)), max_slots=slots, device=device)
-    for t in [srv.submit(desc, d, wl.stages, cfg) for d in datas[:slots]]:
-        srv.poll(t)
     lat = []
     tick = time.perf_counter()
     pending = []

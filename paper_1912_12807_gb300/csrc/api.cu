@@ -618,6 +618,11 @@ pss_status check_errflag(pss_ctx* ctx, cudaStream_t s) {
     return PSS_OK;
 }
 
+// Trials per DM batch of a pipelined search of n trials: four batches (at
+// least 64 trials each), so that the host sift of all but the last overlaps
+// the device work.
+int64_t pipeline_batch(int64_t n) { return n >= 256 ? (n + 3) / 4 : (n >= 64 ? (n + 1) / 2 : 0); }
+
 // Events and pinned count slots for n DM batches, and a stream for downloads.
 pss_status ensure_snapshots(pss_ctx* ctx, int n) {
     if (!ctx->stream2) PSS_CUDA(cudaStreamCreateWithFlags(&ctx->stream2, cudaStreamNonBlocking));
@@ -694,7 +699,7 @@ pss_status search_pipelined(pss_ctx* ctx, const pss_plan* plan, const pss_fil_de
     HostTimer tm;
     for (int attempt = 0; attempt < 2; ++attempt) {
         PathSetup P;
-        PSS_TRY(setup_path(ctx, plan, fil, cfg, dm_begin, dm_end, MODE_SEARCH, s, cap, &P, n >= 64 ? (n + 1) / 2 : 0));
+        PSS_TRY(setup_path(ctx, plan, fil, cfg, dm_begin, dm_end, MODE_SEARCH, s, cap, &P, pipeline_batch(n)));
         const uint8_t* src = nullptr;
         PSS_TRY(upload_input(ctx, fil, data, on_dev, s, &src));
         PSS_TRY(ensure_snapshots(ctx, (int)P.batches.size()));
@@ -1388,7 +1393,7 @@ pss_status batch_build(pss_batch* b, int64_t cap) {
     batch_release_graph(b);
     const int64_t n = b->plan.ndm();
     PSS_TRY(setup_path(ctx, static_cast<const pss_plan*>(&b->plan), &b->fil, &b->cfg, 0, n, MODE_SEARCH, s, cap,
-                       &b->P, n >= 64 ? (n + 1) / 2 : 0));
+                       &b->P, pipeline_batch(n)));
     PSS_TRY(ctx->fil_dev.ensure((size_t)file_bytes(&b->fil)));
     PSS_TRY(ensure_snapshots(ctx, (int)b->P.batches.size()));
     // one eager pass sets every kernel attribute before capture
