@@ -221,6 +221,22 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def max_over_ranks(x, world, device=None):
+    """The largest value of x over all ranks (the slowest rank's time)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, trials_per_rank, ms):
+    """Whole-job DM-trials/s: every rank searches its own file (weak scaling)."""
+    return world * trials_per_rank / (ms / 1e3)
+
+
 def recorded_traffic(workload, stage):
     """DRAM bytes per launch of a stage's kernel from the committed ncu capture
     (profiles/dram_traffic.json), or None when there is none or the kernel
@@ -379,12 +395,7 @@ def run_ours(args, rank, world, local_rank):
     ctx.profile(False)
     clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = sum(step_ms) / len(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(sum(step_ms) / len(step_ms), world, dev)
 
     # e2e through the same call with the file in pinned host memory
     e2e_ms = []
@@ -395,12 +406,11 @@ def run_ours(args, rank, world, local_rank):
         step(on_device=False)
         t1 = time.perf_counter()
         e2e_ms.append(1e3 * (t1 - t0))
-    e2e = statistics.mean(e2e_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = float(t.item())
+    e2e = max_over_ranks(statistics.mean(e2e_ms), world, dev)
+
+    refine = None
+    if wl.cfg.zmax > 0 and rank == 0 and len(cands):
+        refine = run_refine(pss, ctx, plan, data_dev, cfg, cands, args.refine_top)
 
     batched = served = None
     if not args.no_serve:
@@ -413,7 +423,7 @@ def run_ours(args, rank, world, local_rank):
             import torch.distributed as dist
             dist.destroy_process_group()
         return
-    value = world * ndm / (ms / 1e3)
+    value = job_value(world, ndm, ms)
     peaks, peak_kind = measured_peaks()
     work = stage_work(plan, wl, fil.nbytes())
     rooflines = {}
@@ -434,7 +444,7 @@ def run_ours(args, rank, world, local_rank):
             "config": _config(wl, name, {"dm_trials": ndm}), "files_per_s": world * 1e3 / ms,
             "s_per_file": ms / 1e3, "realtime_budget_s": REALTIME_S, "realtime_factor": REALTIME_S / (ms / 1e3),
             "roofline": rooflines[dominant],
-            "e2e": {"value": world * ndm / (e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": bi,
+            "e2e": {"value": job_value(world, ndm, e2e), "unit": UNIT, "h2d_bytes_per_step": bi,
                     "d2h_bytes_per_step": bo, "ms_per_step": e2e},
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
@@ -442,12 +452,32 @@ def run_ours(args, rank, world, local_rank):
             "stage_rooflines": {k: {"bound": v["bound"], "frac": v["frac"], "achieved": v["achieved"],
                                     "unit": v["unit"]} for k, v in rooflines.items()},
             "clocks": clocks.summary(), "wall_s_timed": t_wall, "candidates": int(len(cands)),
-            "batched": batched, "serve": served, "cpu_baseline": cpu}
+            "batched": batched, "serve": served, "refine": refine, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_refine(pss, ctx, plan, data_dev, cfg, cands, top, iters=40):
+    """Continuous (DM, r, z) refinement of the `top` highest-sigma candidates
+    by gradient ascent (pss_refine_candidates): wall time of the call (which
+    prepares the per-channel spectra of each candidate stage, then runs the
+    ascent), and how much the refined power exceeds the search's."""
+    import numpy as np
+    import torch
+    sel = cands[np.argsort(-cands["sigma"], kind="stable")[:top]]
+    pss.pss_refine_candidates(ctx, plan, data_dev, cfg, sel[: min(8, len(sel))], iters=2)  # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = pss.pss_refine_candidates(ctx, plan, data_dev, cfg, sel, iters=iters)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    gain = out["power"] / np.maximum(sel["power"], 1e-30)
+    return {"candidates": int(len(sel)), "iters": iters, "s": dt, "cands_per_s": len(sel) / dt,
+            "power_gain_median": float(np.median(gain)), "power_gain_min": float(gain.min()),
+            "stages_prepared": int(len(np.unique([plan.trial(int(i))["stage"] for i in sel["dm_idx"]])))}
 
 
 def run_batched(pss, plan, cfg, data_dev, ndm, steps, flush):
@@ -614,6 +644,7 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=2)
     ap.add_argument("--serve-budget-gib", type=float, default=64.0)
     ap.add_argument("--stream-files", type=int, default=64)
+    ap.add_argument("--refine-top", type=int, default=4096, help="candidates refined after a zmax > 0 search")
     ap.add_argument("--stream-speedup", type=float, default=50.0)
     ap.add_argument("--dm-trials", type=int, default=None,
                     help="DM trials of a single-stage plan (driftscan/accel); smaller values make profiling cases")
