@@ -359,13 +359,16 @@ size_t pss_batch_footprint(const pss_batch* b);
  * choice on the first <= 256 trials of the shape, timing the stage it
  * changes, and keeps the fastest;
  * the choice is remembered per shape for the life of the process;
- * environment PSS_AUTOTUNE=0 keeps the defaults 0 / 16 / 96 / 0):
+ * environment PSS_AUTOTUNE=0 keeps the defaults 0 / 16 / 96 / 0 / 1):
  * fft_split: FFT pass-split variant (0 = even split), harm_run: points per
  * lane of the harmonic sum (16 or 8), dedisp_kb: shared memory for staged
  * channel chunks (KiB), whiten_form: whitening median per CTA (0) or per
- * warp (1).  Pointers are nullable. */
+ * warp (1), fused: for zmax 0 and nfft 2^18, FFT + whitening + plane in one
+ * thread-block-cluster launch (1) or as separate kernels (0); the fused
+ * path is used only where the device can run 16-CTA clusters.  Pointers
+ * are nullable. */
 pss_status pss_batch_tuning(const pss_batch* b, int32_t* fft_split, int32_t* harm_run, int32_t* dedisp_kb,
-                            int32_t* whiten_form);
+                            int32_t* whiten_form, int32_t* fused);
 /* Device bytes a batch for this shape will hold, computed on the host
  * without a device (what the server admits files by).  PSS_EINVAL for the
  * arguments pss_batch_create would reject. */

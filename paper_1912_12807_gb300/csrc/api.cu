@@ -480,71 +480,93 @@ pss_status enqueue_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* 
             ProfScope ps(ctx, 1, s);
             PSS_CUDA(launch_dedisp(da, ctx->num_sms, s));
         }
-        FftArgs fa{};
-        fa.series = (const float*)ctx->series.p;
-        fa.series_stride = nfft;
-        fa.sums = (const unsigned long long*)ctx->sums.p;
-        fa.nv = st.nv;
-        fa.nfft = nfft;
-        fa.nb = d.nb;
-        fa.bufA = (float2*)ctx->fftA.p;
-        fa.bufB = (float2*)ctx->fftB.p;
-        float2* spec = (mode == MODE_SPECTRUM) ? (float2*)(outs.spec) + d.out_off : (float2*)ctx->spec.p;
-        fa.spec_out = spec;
-        fa.spec_stride = M;
-        fa.whiten_block = cfg->whiten_block;
-        fa.tw = (const float2*)ctx->twid.p;
-        fa.twM = ctx->twid_n;
-        fa.fft_variant = ctx->tune.fft_variant;
-        fa.whiten_form = ctx->tune.whiten_form;
-        set_passtw(ctx, &fa);
-        fa.whiten = 1;
-        fa.gains_out = nullptr;
-        fa.gains_stride = 0;
-        if (mode == MODE_GAINS) {
-            fa.gains_out = outs.gains + (d.b0 - dm_begin) * (M / cfg->whiten_block);
-            fa.gains_stride = M / cfg->whiten_block;
-        }
-        PSS_CUDA(launch_fft_whiten(fa, s, ctx));
-        if (mode == MODE_SPECTRUM || mode == MODE_GAINS) continue;
-        PlaneArgs pl;
-        pl.spec = spec;
-        pl.spec_stride = M;
-        pl.nfft = nfft;
-        pl.nb = d.nb;
-        pl.plane = (mode == MODE_PLANE) ? outs.plane + d.out_off : (float*)ctx->plane.p;
-        pl.plane_stride = (int64_t)P.nz * nfft;
-        pl.zmax = cfg->zmax;
-        pl.dz = cfg->zmax ? cfg->dz : 1.0;
-        pl.extra = cfg->halfwidth_extra;
-        pl.taps = (const float2*)ctx->taps.p;
-        const int32_t* info = (const int32_t*)ctx->tapinfo.p;
-        pl.tap_off = info;
-        pl.tap_m = info + 2 * P.nz;
-        pl.tap_scale = (const float*)(info + 3 * P.nz);
-        pl.ftaps = nullptr;
-        if (ctx->ftap_ok && plane_fft_usable(cfg->zmax, cfg->halfwidth_extra, M)) {
-            const int mmax = (cfg->zmax + 1) / 2 + cfg->halfwidth_extra;
-            pl.ftaps = (const float2*)ctx->ftaps.p;
-            pl.fL = PLANE_FFT_L;
-            pl.fM0 = mmax - 1;
-            pl.fV = PLANE_FFT_L - 2 * mmax + 1;
-            pl.tw = (const float2*)ctx->twid.p;
-            pl.twM = ctx->twid_n;
-            pl.nz = P.nz;
-            pl.zrow0 = -1;
-            for (int j = 0; j < P.nz; ++j)
-                if (-(double)cfg->zmax + (double)j * pl.dz == 0.0) pl.zrow0 = j;
-        }
-        {
-            ProfScope ps(ctx, 4, s);
-            PSS_CUDA(launch_plane(pl, s));
+        const bool fused = (mode == MODE_SEARCH || mode == MODE_PLANE) && cfg->zmax == 0 && nfft == (int64_t(1) << 18) &&
+                           cfg->whiten_block == 1024 && cfg->halfwidth_extra == 16 && ctx->tune.fused &&
+                           spec_cluster_usable();
+        float* plane_out = (mode == MODE_PLANE) ? outs.plane + d.out_off : (float*)ctx->plane.p;
+        if (fused) {
+            // FFT, whitening and the zmax 0 plane in one cluster launch (k_specfused.cu)
+            SpecArgs sa;
+            sa.series = (const float*)ctx->series.p;
+            sa.series_stride = nfft;
+            sa.sums = (const unsigned long long*)ctx->sums.p;
+            sa.nv = st.nv;
+            sa.nfft = nfft;
+            sa.nb = d.nb;
+            sa.plane = plane_out;
+            sa.plane_stride = (int64_t)P.nz * nfft;
+            sa.tw = (const float2*)ctx->twid.p;
+            sa.twM = ctx->twid_n;
+            sa.tap_scale1 = (const float*)((const int32_t*)ctx->tapinfo.p + 3 * P.nz) + 1;
+            ProfScope ps(ctx, 2, s);
+            PSS_CUDA(launch_spec_cluster(sa, s));
+        } else {
+            FftArgs fa{};
+            fa.series = (const float*)ctx->series.p;
+            fa.series_stride = nfft;
+            fa.sums = (const unsigned long long*)ctx->sums.p;
+            fa.nv = st.nv;
+            fa.nfft = nfft;
+            fa.nb = d.nb;
+            fa.bufA = (float2*)ctx->fftA.p;
+            fa.bufB = (float2*)ctx->fftB.p;
+            float2* spec = (mode == MODE_SPECTRUM) ? (float2*)(outs.spec) + d.out_off : (float2*)ctx->spec.p;
+            fa.spec_out = spec;
+            fa.spec_stride = M;
+            fa.whiten_block = cfg->whiten_block;
+            fa.tw = (const float2*)ctx->twid.p;
+            fa.twM = ctx->twid_n;
+            fa.fft_variant = ctx->tune.fft_variant;
+            fa.whiten_form = ctx->tune.whiten_form;
+            set_passtw(ctx, &fa);
+            fa.whiten = 1;
+            fa.gains_out = nullptr;
+            fa.gains_stride = 0;
+            if (mode == MODE_GAINS) {
+                fa.gains_out = outs.gains + (d.b0 - dm_begin) * (M / cfg->whiten_block);
+                fa.gains_stride = M / cfg->whiten_block;
+            }
+            PSS_CUDA(launch_fft_whiten(fa, s, ctx));
+            if (mode == MODE_SPECTRUM || mode == MODE_GAINS) continue;
+            PlaneArgs pl;
+            pl.spec = spec;
+            pl.spec_stride = M;
+            pl.nfft = nfft;
+            pl.nb = d.nb;
+            pl.plane = (mode == MODE_PLANE) ? outs.plane + d.out_off : (float*)ctx->plane.p;
+            pl.plane_stride = (int64_t)P.nz * nfft;
+            pl.zmax = cfg->zmax;
+            pl.dz = cfg->zmax ? cfg->dz : 1.0;
+            pl.extra = cfg->halfwidth_extra;
+            pl.taps = (const float2*)ctx->taps.p;
+            const int32_t* info = (const int32_t*)ctx->tapinfo.p;
+            pl.tap_off = info;
+            pl.tap_m = info + 2 * P.nz;
+            pl.tap_scale = (const float*)(info + 3 * P.nz);
+            pl.ftaps = nullptr;
+            if (ctx->ftap_ok && plane_fft_usable(cfg->zmax, cfg->halfwidth_extra, M)) {
+                const int mmax = (cfg->zmax + 1) / 2 + cfg->halfwidth_extra;
+                pl.ftaps = (const float2*)ctx->ftaps.p;
+                pl.fL = PLANE_FFT_L;
+                pl.fM0 = mmax - 1;
+                pl.fV = PLANE_FFT_L - 2 * mmax + 1;
+                pl.tw = (const float2*)ctx->twid.p;
+                pl.twM = ctx->twid_n;
+                pl.nz = P.nz;
+                pl.zrow0 = -1;
+                for (int j = 0; j < P.nz; ++j)
+                    if (-(double)cfg->zmax + (double)j * pl.dz == 0.0) pl.zrow0 = j;
+            }
+            {
+                ProfScope ps(ctx, 4, s);
+                PSS_CUDA(launch_plane(pl, s));
+            }
         }
         if (mode == MODE_PLANE) continue;
         HarmArgs ha = P.harm[d.stage];
         ha.run = ctx->tune.harm_run;
-        ha.plane = pl.plane;
-        ha.plane_stride = pl.plane_stride;
+        ha.plane = plane_out;
+        ha.plane_stride = (int64_t)P.nz * nfft;
         ha.nfft = nfft;
         ha.nz = P.nz;
         ha.Z = P.Z;
@@ -778,6 +800,8 @@ pss_status pss_ctx_create(int device, pss_ctx** out) {
         return cuda_fail(e, "cudaStreamCreate");
     }
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    // PSS_FUSED=1: the cluster-fused FFT / whitening / plane kernel where it applies
+    if (const char* f = getenv("PSS_FUSED")) c->tune.fused = f[0] == '1';
     *out = c;
     return PSS_OK;
 }
@@ -1309,8 +1333,12 @@ pss_status autotune(pss_ctx* ctx, const Plan& plan, const pss_fil_desc* fil, con
     // PSS_TUNE="fft,harm,dedisp,whiten" pins the launch shapes instead (not remembered)
     if (const char* pin = getenv("PSS_TUNE")) {
         Tune t;
-        if (sscanf(pin, "%d,%d,%d,%d", &t.fft_variant, &t.harm_run, &t.dedisp_kb, &t.whiten_form) != 4)
-            return fail(PSS_EINVAL, "PSS_TUNE must be four integers: fft split, harm run, dedisp KiB, whiten form");
+        const int got = sscanf(pin, "%d,%d,%d,%d,%d", &t.fft_variant, &t.harm_run, &t.dedisp_kb, &t.whiten_form,
+                               &t.fused);
+        if (got != 4 && got != 5)
+            return fail(PSS_EINVAL,
+                        "PSS_TUNE must be four or five integers: fft split, harm run, dedisp KiB, whiten form[, fused]");
+        if (t.fused != 0 && t.fused != 1) return fail(PSS_EINVAL, "PSS_TUNE value out of range");
         int rad[4];
         if (fft_pass_plan(plan.stages[0].nfft / 2, t.fft_variant, rad) == 0 || (t.harm_run != 8 && t.harm_run != 16) ||
             t.dedisp_kb < 16 || t.dedisp_kb > 200 || (t.whiten_form != 0 && t.whiten_form != 1))
@@ -1334,7 +1362,7 @@ pss_status autotune(pss_ctx* ctx, const Plan& plan, const pss_fil_desc* fil, con
     const pss_plan* pp = static_cast<const pss_plan*>(&plan);
     // time of profiler stage `stage` (1 dedisperse, 2 FFT, 3 whiten, 5 harmonic sum) over one
     // warm pass; the kernels of the other stages do not change with the choice being tuned
-    auto measure = [&](int stage, float* ms) -> pss_status {
+    auto measure = [&](unsigned stages, float* ms) -> pss_status {
         PathSetup T;
         PSS_TRY(setup_path(ctx, pp, fil, cfg, 0, nt, MODE_SEARCH, s, kBatchInitialCap, &T));
         const uint8_t* src = (const uint8_t*)ctx->fil_dev.p;
@@ -1346,10 +1374,12 @@ pss_status autotune(pss_ctx* ctx, const Plan& plan, const pss_fil_desc* fil, con
         pss_status r = pss_ctx_profile_read(ctx, st_ms, n);
         pss_ctx_profile(ctx, 0);
         PSS_TRY(r);
-        *ms = (float)st_ms[stage];
+        *ms = 0.f;
+        for (int i = 0; i < PSS_NPROF_STAGES; ++i)
+            if (stages & (1u << i)) *ms += (float)st_ms[i];
         return check_errflag(ctx, s);
     };
-    auto sweep = [&](int* field, const std::vector<int>& cands, int stage, const char* what) -> pss_status {
+    auto sweep = [&](int* field, const std::vector<int>& cands, unsigned stage, const char* what) -> pss_status {
         int best = *field;
         float best_ms = 1e30f;
         for (int v : cands) {
@@ -1371,10 +1401,17 @@ pss_status autotune(pss_ctx* ctx, const Plan& plan, const pss_fil_desc* fil, con
         std::vector<int> fv;
         int rad[4];
         for (int v = 0; v < 6 && fft_pass_plan(plan.stages[0].nfft / 2, v, rad) > 0; ++v) fv.push_back(v);
-        st = sweep(&ctx->tune.fft_variant, fv, 2, "fft split");
-        if (st == PSS_OK) st = sweep(&ctx->tune.harm_run, {16, 8}, 5, "harm run");
-        if (st == PSS_OK) st = sweep(&ctx->tune.dedisp_kb, {96, 64}, 1, "dedisp kb");
-        if (st == PSS_OK) st = sweep(&ctx->tune.whiten_form, {0, 1}, 3, "whiten");
+        // stage bits of the profiler: 1 dedisperse, 2 FFT (and the fused kernel), 3 whiten, 4 plane, 5 harmonic sum
+        const bool fusable = cfg->zmax == 0 && plan.stages.size() == 1 && plan.stages[0].nfft == (int64_t(1) << 18) &&
+                             cfg->whiten_block == 1024 && cfg->halfwidth_extra == 16 && spec_cluster_usable();
+        if (fusable) st = sweep(&ctx->tune.fused, {1, 0}, (1u << 2) | (1u << 3) | (1u << 4), "fused");
+        else ctx->tune.fused = 0;
+        if (st == PSS_OK && !ctx->tune.fused) {
+            st = sweep(&ctx->tune.fft_variant, fv, 1u << 2, "fft split");
+            if (st == PSS_OK) st = sweep(&ctx->tune.whiten_form, {0, 1}, 1u << 3, "whiten");
+        }
+        if (st == PSS_OK) st = sweep(&ctx->tune.harm_run, {16, 8}, 1u << 5, "harm run");
+        if (st == PSS_OK) st = sweep(&ctx->tune.dedisp_kb, {96, 64}, 1u << 1, "dedisp kb");
     }
     if (st != PSS_OK) {
         ctx->tune = Tune();
@@ -1518,12 +1555,13 @@ extern "C" pss_status pss_search_footprint(const pss_plan* plan, const pss_fil_d
 extern "C" size_t pss_batch_footprint(const pss_batch* b) { return b ? b->footprint : 0; }
 
 extern "C" pss_status pss_batch_tuning(const pss_batch* b, int32_t* fft_split, int32_t* harm_run, int32_t* dedisp_kb,
-                                       int32_t* whiten_form) {
+                                       int32_t* whiten_form, int32_t* fused) {
     if (!b) return fail(PSS_EINVAL, "pss_batch_tuning: null batch");
     if (fft_split) *fft_split = b->ctx->tune.fft_variant;
     if (harm_run) *harm_run = b->ctx->tune.harm_run;
     if (dedisp_kb) *dedisp_kb = b->ctx->tune.dedisp_kb;
     if (whiten_form) *whiten_form = b->ctx->tune.whiten_form;
+    if (fused) *fused = b->ctx->tune.fused;
     return PSS_OK;
 }
 

@@ -53,4 +53,24 @@ __device__ __forceinline__ void dft_small(float2* x) {
     else dft8(x);
 }
 
+// Swizzled shared-memory index for 8-byte elements: within each run of 16
+// (one 128-byte line) the slot is XORed with a function of the run number,
+// chosen so that every access of the 8-8-8-4 sub-stage order (16 consecutive
+// elements; or 8 runs of 2 at stride 8; or 2 runs of 8 at stride 64) hits 16
+// different bank pairs per half-warp.
+__host__ __device__ __forceinline__ int fp(int i) {
+    const int r = i >> 4;
+    const int g = (r & 7) | ((r & 4) << 1);
+    return (i & ~15) | ((i & 15) ^ g);
+}
+
+
+// Odd half-bin tap i of the z = 0 template with 2m = NTAP taps: the
+// imaginary part of conj(rho(1/2 - t, 0)) with t = i - (m - 1), which is
+// 1 / (pi (t - 1/2)) (its real part is zero), rounded to FP32 at compile time.
+template <int NTAP>
+__host__ __device__ constexpr float z0_tap(int i) {
+    return (float)(1.0 / (3.14159265358979323846 * ((double)(i - (NTAP / 2 - 1)) - 0.5)));
+}
+
 }  // namespace pss

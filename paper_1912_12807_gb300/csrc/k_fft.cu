@@ -25,6 +25,7 @@
 #include <math.h>
 
 #include "fft_small.cuh"
+#include "whiten.cuh"
 #include "pss_internal.h"
 
 namespace pss {
@@ -248,8 +249,6 @@ __global__ void k_twiddles(float2* tw, int64_t n) {
 // one of the right rank is found by counting, ties broken by position.  If
 // that bin holds more than NCAND values, three further 8/8/4-bit histogram
 // rounds on the remaining bits finish the selection instead.
-constexpr int NBIN = 2048;
-constexpr int NCAND = 256;
 
 template <int EPT>
 __global__ void __launch_bounds__(256) k_r2c_whiten(const float2* Zall, int64_t z_stride, int64_t M, int W,
@@ -413,146 +412,6 @@ __global__ void __launch_bounds__(256) k_r2c_whiten(const float2* Zall, int64_t 
 constexpr int WW = 4;  // warps per CTA
 
 template <int VPL>
-__device__ __forceinline__ void whiten_block(float2 (&A)[VPL], int64_t k0, int lane, int m, uint32_t* hist,
-                                             uint32_t* cand, uint32_t* cpos, int whiten, float* gain_out,
-                                             float2* O) {
-    auto keyof = [&](int i) -> uint32_t {
-        return (k0 == 0 && lane == 0 && i == 0) ? 0xFFFFFFFFu : __float_as_uint(A[i].x * A[i].x + A[i].y * A[i].y);
-    };
-    __syncwarp();
-    for (int i = lane; i < NBIN; i += 32) hist[i] = 0u;
-    __syncwarp();
-#pragma unroll
-    for (int i = 0; i < VPL; ++i) {
-        const uint32_t kk = keyof(i);
-        if (kk != 0xFFFFFFFFu) atomicAdd(&hist[kk >> 20], 1u);
-    }
-    __syncwarp();
-    const uint32_t rank0 = (uint32_t)((m - 1) / 2);
-    // the bin holding rank0: lane l owns bins [l * NBIN/32, (l+1) * NBIN/32)
-    constexpr int BPL = NBIN / 32;
-    uint32_t tot = 0;
-#pragma unroll 8
-    for (int i = 0; i < BPL; ++i) tot += hist[lane * BPL + i];
-    uint32_t incl = tot;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
-        if (lane >= off) incl += v;
-    }
-    const uint32_t before0 = incl - tot;
-    const bool mine = rank0 >= before0 && rank0 < incl;
-    const int owner = __ffs(__ballot_sync(0xffffffffu, mine)) - 1;
-    uint32_t bin = 0, rank = 0;
-    if (lane == owner) {
-        uint32_t before = before0;
-        for (int i = 0; i < BPL; ++i) {
-            const uint32_t c = hist[lane * BPL + i];
-            if (rank0 < before + c) {
-                bin = (uint32_t)(lane * BPL + i);
-                rank = rank0 - before;
-                break;
-            }
-            before += c;
-        }
-    }
-    bin = __shfl_sync(0xffffffffu, bin, owner);
-    rank = __shfl_sync(0xffffffffu, rank, owner);
-    const uint32_t nin = hist[bin];
-    uint32_t med_bits = 0;
-    if (nin <= (uint32_t)NCAND) {
-        // gather the bin's values with their positions, then count ranks (ties by position)
-        uint32_t base = 0;
-#pragma unroll
-        for (int i = 0; i < VPL; ++i) {
-            const uint32_t kk = keyof(i);
-            const bool in = kk != 0xFFFFFFFFu && (kk >> 20) == bin;
-            const unsigned bal = __ballot_sync(0xffffffffu, in);
-            if (in) {
-                const uint32_t slot = base + __popc(bal & ((1u << lane) - 1u));
-                cand[slot] = kk;
-                cpos[slot] = (uint32_t)(lane + 32 * i);
-            }
-            base += __popc(bal);
-        }
-        __syncwarp();
-        uint32_t found = 0;
-        bool have = false;
-        for (uint32_t c = lane; c < nin; c += 32) {
-            const uint32_t v = cand[c], pv = cpos[c];
-            uint32_t r = 0;
-            for (uint32_t q = 0; q < nin; ++q) {
-                const uint32_t u = cand[q];
-                r += (u < v) || (u == v && cpos[q] < pv);
-            }
-            if (r == rank) {
-                found = v;
-                have = true;
-            }
-        }
-        const int who = __ffs(__ballot_sync(0xffffffffu, have)) - 1;
-        med_bits = __shfl_sync(0xffffffffu, found, who < 0 ? 0 : who);
-    } else {
-        // many values share the top bits: radix rounds on bits 19..0 (8, 8, 4)
-        uint32_t prefix = bin << 20, mask = 0xFFF00000u, rk = rank;
-#pragma unroll
-        for (int pass = 0; pass < 3; ++pass) {
-            const int shift = pass == 0 ? 12 : (pass == 1 ? 4 : 0);
-            const uint32_t dmask = pass == 2 ? 15u : 255u;
-            __syncwarp();
-            for (int i = lane; i < 256; i += 32) hist[i] = 0u;
-            __syncwarp();
-#pragma unroll
-            for (int i = 0; i < VPL; ++i) {
-                const uint32_t kk = keyof(i);
-                if (kk != 0xFFFFFFFFu && (kk & mask) == prefix) atomicAdd(&hist[(kk >> shift) & dmask], 1u);
-            }
-            __syncwarp();
-            uint32_t dsel = 0, rsel = 0;
-            if (lane == 0) {
-                uint32_t before = 0;
-                for (uint32_t d = 0; d <= dmask; ++d) {
-                    if (rk < before + hist[d]) {
-                        dsel = d;
-                        rsel = rk - before;
-                        break;
-                    }
-                    before += hist[d];
-                }
-            }
-            dsel = __shfl_sync(0xffffffffu, dsel, 0);
-            rsel = __shfl_sync(0xffffffffu, rsel, 0);
-            prefix |= dsel << shift;
-            mask |= dmask << shift;
-            rk = rsel;
-        }
-        med_bits = prefix;
-    }
-    // scale sqrt(ln 2 / med) and gain ln 2 / med in FP64, once per warp (FP64 is slow)
-    float scale = 1.f;
-    if (lane == 0) {
-        const float med = __uint_as_float(med_bits);
-        const double g = med > 0.f ? 0.69314718055994530942 / (double)med : 0.0;
-        scale = whiten ? (float)sqrt(g) : 1.f;
-        if (gain_out) *gain_out = (float)g;
-    }
-    scale = __shfl_sync(0xffffffffu, scale, 0);
-#pragma unroll
-    for (int i = 0; i < VPL; ++i) O[k0 + lane + 32 * i] = make_float2(A[i].x * scale, A[i].y * scale);
-}
-
-// A_k = (Z_k + conj Z_{M-k}) / 2 - (i/2) e^{-2 pi i k / nfft} (Z_k - conj Z_{M-k}), A_0 = 0
-__device__ __forceinline__ float2 r2c_bin(float2 zk, float2 zm, float2 w, int64_t k) {
-    const float2 zc = make_float2(zm.x, -zm.y);
-    const float2 sum = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y + zc.y));
-    const float2 dif = make_float2(0.5f * (zk.x - zc.x), 0.5f * (zk.y - zc.y));
-    const float2 wd = cmul(w, dif);
-    float2 a = make_float2(sum.x + wd.y, sum.y - wd.x);  // sum - i * w * dif
-    if (k == 0) a = make_float2(0.f, 0.f);
-    return a;
-}
-
-template <int VPL>
 __global__ void __launch_bounds__(32 * WW) k_whiten_warp(const float2* Zall, int64_t z_stride, int64_t M,
                                                          float2* out, int64_t out_stride, const float2* tw,
                                                          int64_t twM, int whiten, float* gains,
@@ -580,7 +439,7 @@ __global__ void __launch_bounds__(32 * WW) k_whiten_warp(const float2* Zall, int
         return;
     }
     float* g = gains ? gains + (int64_t)b * gains_stride + blk : nullptr;
-    whiten_block<VPL>(A, k0, lane, k0 == 0 ? W - 1 : W, s_hist[wq], s_cand[wq], s_cpos[wq], whiten, g, O);
+    whiten_block<VPL>(A, k0, lane, k0 == 0 ? W - 1 : W, s_hist[wq], s_cand[wq], s_cpos[wq], whiten, g, O + k0);
 }
 
 // Pass radices of an M-point FFT, M = 2^L: the fewest passes of radix
@@ -619,8 +478,6 @@ bool radix_variant(int64_t M, int variant, int* rad, int* np) {
     *np = p;
     return true;
 }
-
-void radix_plan(int64_t M, int* rad, int* np) { radix_variant(M, 0, rad, np); }
 
 }  // namespace
 

@@ -118,14 +118,6 @@ __global__ void __launch_bounds__(NT) k_plane(PlaneArgs a) {
     }
 }
 
-// Odd half-bin tap i of the z = 0 template with 2m = NTAP taps: the
-// imaginary part of conj(rho(1/2 - t, 0)) with t = i - (m - 1), which is
-// 1 / (pi (t - 1/2)) (its real part is zero), rounded to FP32 at compile time.
-template <int NTAP>
-__host__ __device__ constexpr float z0_tap(int i) {
-    return (float)(1.0 / (3.14159265358979323846 * ((double)(i - (NTAP / 2 - 1)) - 0.5)));
-}
-
 // zmax = 0 plane with 2m = NTAP taps: each thread computes R consecutive
 // bins from a register window over a shared-memory tile (one padding slot
 // every 8 entries keeps the strided 8-byte reads free of bank conflicts);
@@ -223,17 +215,6 @@ __global__ void k_fft_templates(FftTemplateArgs a) {
 }
 
 constexpr int FNT = 256;
-
-// Swizzled shared-memory index for 8-byte elements: within each run of 16
-// (one 128-byte line) the slot is XORed with a function of the run number,
-// chosen so that every access of the 8-8-8-4 sub-stage order (16 consecutive
-// elements; or 8 runs of 2 at stride 8; or 2 runs of 8 at stride 64) hits 16
-// different bank pairs per half-warp.
-__device__ __forceinline__ int fp(int i) {
-    const int r = i >> 4;
-    const int g = (r & 7) | ((r & 4) << 1);
-    return (i & ~15) | ((i & 15) ^ g);
-}
 
 // Twiddles of the sub-stages with running span NS: table [q][k] =
 // exp(-2 pi i q k / (RR NS)) (q-major, so lanes with consecutive k read

@@ -134,6 +134,7 @@ struct Tune {
     int harm_run = 16;     // harmonic-sum points per lane
     int dedisp_kb = 96;    // dedispersion chunk staging budget
     int whiten_form = 0;   // whitening kernel form
+    int fused = 0;         // zmax 0, nfft 2^18: cluster-fused FFT + whitening + plane (where the device allows)
 };
 
 struct Ctx {
@@ -284,6 +285,24 @@ cudaError_t launch_twiddles(float2* tw, int64_t n, cudaStream_t s);
 int fft_pass_plan(int64_t M, int variant, int* rad);
 cudaError_t launch_pass_twiddles(float2* out, const float2* tw, int64_t twM, int R, int64_t Ns, cudaStream_t s);
 cudaError_t launch_fft_whiten(const FftArgs& a, cudaStream_t s, Ctx* prof_ctx);
+
+// Fused spectrum (k_specfused.cu): series -> whitened spectrum -> zmax = 0
+// plane for nfft = 2^18, on 16-CTA clusters, one cluster per trial.
+struct SpecArgs {
+    const float* series;              // [nb][series_stride] raw sums (float, exact)
+    int64_t series_stride;
+    const unsigned long long* sums;   // [nb]
+    int64_t nv;
+    int64_t nfft;                     // must be 2^18
+    int32_t nb;
+    float* plane;                     // [nb][plane_stride] half-bin powers
+    int64_t plane_stride;
+    const float2* tw;                 // exp(-2 pi i t / twM)
+    int64_t twM;
+    const float* tap_scale1;          // device: 1/sqrt(E) of the z = 0 odd half-bin taps
+};
+bool spec_cluster_usable();
+cudaError_t launch_spec_cluster(const SpecArgs& a, cudaStream_t s);
 
 struct PlaneArgs {
     const float2* spec;  // [nb][spec_stride] whitened half spectrum (M = nfft/2)

@@ -112,7 +112,7 @@ def lib():
         "pss_batch_free": (None, [vp]),
         "pss_ctx_take_cands": (st, [vp, vp, i64, P(i64)]),
         "pss_batch_take_cands": (st, [vp, vp, i64, P(i64)]),
-        "pss_batch_tuning": (st, [vp, P(i32), P(i32), P(i32), P(i32)]),
+        "pss_batch_tuning": (st, [vp, P(i32), P(i32), P(i32), P(i32), P(i32)]),
         "pss_search_footprint": (st, [vp, P(pss_fil_desc), P(pss_search_cfg), P(C.c_size_t)]),
         "pss_server_create": (st, [C.c_int, C.c_size_t, C.c_int, P(vp)]),
         "pss_submit_file": (st, [vp, P(pss_fil_desc), vp, P(pss_dd_stage), C.c_int, P(pss_search_cfg),
@@ -390,10 +390,11 @@ class Batch:
 
     @property
     def tuning(self):
-        """{fft_split, harm_run, dedisp_kb, whiten_form} chosen by the batch's autotuner."""
-        f, h, d, w = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
-        _check(lib().pss_batch_tuning(self.h, C.byref(f), C.byref(h), C.byref(d), C.byref(w)))
-        return {"fft_split": f.value, "harm_run": h.value, "dedisp_kb": d.value, "whiten_form": w.value}
+        """{fft_split, harm_run, dedisp_kb, whiten_form, fused} chosen by the batch's autotuner."""
+        f, h, d, w, u = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        _check(lib().pss_batch_tuning(self.h, C.byref(f), C.byref(h), C.byref(d), C.byref(w), C.byref(u)))
+        return {"fft_split": f.value, "harm_run": h.value, "dedisp_kb": d.value, "whiten_form": w.value,
+                "fused": u.value}
 
     def run(self, data, cap: int = 1 << 14, timing: bool = False):
         """Sifted candidates of one file (host array or device tensor; a device

@@ -186,6 +186,40 @@ def test_accel_plane_direct_form(L, ctx):
     check_powers(got.reshape(L.n_z(cfg), nfft), ref, "direct-form accel plane")
 
 
+def test_fused_cluster_spectrum_parity(L, ctx, monkeypatch):
+    # nfft = 2^18 at zmax 0 with PSS_FUSED=1 runs the 16-CTA cluster kernel
+    # (FFT, whitening and the half-bin plane in distributed shared memory):
+    # planes against the oracle, the separate kernels against the same
+    # oracle, and the raw detections of the fused path
+    fil = synth.make_8bit(32, 1 << 18, 2e-4, 1200.0, 1500.0,
+                          [synth.Pulsar(0.0213, 1.0, 0.05, 0.08, phase0=0.3)], seed=11)
+    stages = [synth.Stage(0.0, 1.0, 3, 1)]
+    wl = synth.Workload("t", fil, stages, synth.SearchCfg(zmax=0, numharm=8))
+    cfg = _cfg(L, wl)
+    plan = L.Plan(L.FilDesc.of(fil), stages)
+    op = OP.Plan.for_file(fil, stages)
+    assert op.nv_nfft(0)[1] == 1 << 18
+    x = OD.channel_major(fil.data, fil.nchan, 8)
+    dev = _torch_dev(fil.data)
+    monkeypatch.setenv("PSS_FUSED", "1")
+    cf = L.Context(0)
+    got = L.pss_power_plane(cf, plan, dev, cfg, 0, 3).cpu().numpy().reshape(3, 1 << 18)
+    refs = [oracle_plane(x, op, i, wl.cfg)[2] for i in range(3)]
+    for i in range(3):
+        check_powers(got[i:i + 1], refs[i], "fused plane DM %d" % i)
+    sep = L.pss_power_plane(ctx, plan, dev, cfg, 0, 3).cpu().numpy().reshape(3, 1 << 18)
+    for i in range(3):
+        check_powers(sep[i:i + 1], refs[i], "separate-kernel plane DM %d" % i)
+    raw = L.pss_search_raw(cf, plan, dev, cfg, 0, 3)
+    cf.close()
+    n = 0
+    for i in range(3):
+        g, r, e = compare_candidates(raw, refs[i][None, :] if refs[i].ndim == 1 else refs[i], i, 8, 0,
+                                     op.t_span(i), wl.cfg.f_lo_hz, wl.cfg.sigma_thr)
+        n += r
+    assert n > 0
+
+
 # ---------------------------------------------------------------- candidates
 def test_search_raw_small_parity(L, ctx, small):
     fil = small.fil
