@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <functional>
 #include <string>
 #include <thread>
 #include <vector>
@@ -65,29 +66,19 @@ double sigma_of_power(int n, double S);
 double power_threshold(int n, double sigma);
 
 // ---- host parallel loop -----------------------------------------------------
-// f(i) for i in [0, n) on up to hardware_concurrency threads (dynamic
-// scheduling in chunks of `grain`).
+// f(i) for i in [0, n) in chunks of `grain`, run by the calling thread and
+// the workers of a process-wide pool (hardware_concurrency - 1 threads,
+// started on first use).  Several callers (server slots) may run loops at
+// once; each waits only for its own.
+void parallel_for_fn(int64_t n, int64_t grain, const std::function<void(int64_t)>& f);
 template <class F>
 void parallel_for(int64_t n, int64_t grain, F&& f) {
-    unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
-    if (n <= grain || nt == 1) {
+    if (n <= grain) {
         for (int64_t i = 0; i < n; ++i) f(i);
         return;
     }
-    nt = (unsigned)std::min<int64_t>(nt, (n + grain - 1) / grain);
-    std::atomic<int64_t> next{0};
-    auto body = [&]() {
-        for (;;) {
-            const int64_t b = next.fetch_add(grain);
-            if (b >= n) break;
-            const int64_t e = std::min(n, b + grain);
-            for (int64_t i = b; i < e; ++i) f(i);
-        }
-    };
-    std::vector<std::thread> th;
-    for (unsigned t = 1; t < nt; ++t) th.emplace_back(body);
-    body();
-    for (auto& t : th) t.join();
+    const std::function<void(int64_t)> fn = std::forward<F>(f);
+    parallel_for_fn(n, grain, fn);
 }
 
 // Stable counting sort of raw detections by DM index: returns the order
