@@ -359,7 +359,7 @@ size_t pss_batch_footprint(const pss_batch* b);
  * choice on the first <= 256 trials of the shape, timing the stage it
  * changes, and keeps the fastest;
  * the choice is remembered per shape for the life of the process;
- * environment PSS_AUTOTUNE=0 keeps the defaults 0 / 16 / 96 / 0 / 1):
+ * environment PSS_AUTOTUNE=0 keeps the defaults 0 / 8 / 96 / 0 / 0):
  * fft_split: FFT pass-split variant (0 = even split), harm_run: points per
  * lane of the harmonic sum (16 or 8), dedisp_kb: shared memory for staged
  * channel chunks (KiB), whiten_form: whitening median per CTA (0) or per

@@ -136,15 +136,24 @@ pss_status setup_input(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* f
     std::vector<int32_t> host((size_t)ck + hd.size());
     memcpy(host.data(), keep.data(), sizeof(int32_t) * ck);
     if (!hd.empty()) memcpy(host.data() + ck, hd.data(), sizeof(int32_t) * hd.size());
+    // the same tables as the last call (same plan, mask and trials) need no upload and no wait
+    const void* before = ctx->delays_dev.p;
     PSS_TRY(ctx->delays_dev.ensure(host.size() * sizeof(int32_t)));
-    PSS_CUDA(cudaMemcpyAsync(ctx->delays_dev.p, host.data(), host.size() * sizeof(int32_t),
-                             cudaMemcpyHostToDevice, s));
+    const bool same = ctx->delays_dev.p == before && ctx->delays_host == host;
+    if (!same) {
+        ctx->delays_host.clear();
+        PSS_CUDA(cudaMemcpyAsync(ctx->delays_dev.p, host.data(), host.size() * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, s));
+    }
     PSS_TRY(ctx->xcm.ensure((size_t)ck * pitch + 64));
     if (!ctx->errflag.p) {
         PSS_TRY(ctx->errflag.ensure(sizeof(int)));
         PSS_CUDA(cudaMemsetAsync(ctx->errflag.p, 0, sizeof(int), s));
     }
-    PSS_CUDA(cudaStreamSynchronize(s));
+    if (!same) {
+        PSS_CUDA(cudaStreamSynchronize(s));  // `host` is about to go out of scope
+        ctx->delays_host.swap(host);
+    }
     *ck_out = ck;
     *pitch_out = pitch;
     return PSS_OK;
@@ -1410,7 +1419,7 @@ pss_status autotune(pss_ctx* ctx, const Plan& plan, const pss_fil_desc* fil, con
             st = sweep(&ctx->tune.fft_variant, fv, 1u << 2, "fft split");
             if (st == PSS_OK) st = sweep(&ctx->tune.whiten_form, {0, 1}, 1u << 3, "whiten");
         }
-        if (st == PSS_OK) st = sweep(&ctx->tune.harm_run, {16, 8}, 1u << 5, "harm run");
+        if (st == PSS_OK) st = sweep(&ctx->tune.harm_run, {8, 16}, 1u << 5, "harm run");
         if (st == PSS_OK) st = sweep(&ctx->tune.dedisp_kb, {96, 64}, 1u << 1, "dedisp kb");
     }
     if (st != PSS_OK) {

@@ -122,7 +122,7 @@ struct DevBuf {
 // defaults are what untuned calls use.
 struct Tune {
     int fft_variant = 0;   // FFT pass split
-    int harm_run = 16;     // harmonic-sum points per lane
+    int harm_run = 8;      // harmonic-sum points per lane
     int dedisp_kb = 96;    // dedispersion chunk staging budget
     int whiten_form = 0;   // whitening kernel form
     int fused = 0;         // zmax 0, nfft 2^18: cluster-fused FFT + whitening + plane (where the device allows)
@@ -135,6 +135,7 @@ struct Ctx {
     DevBuf fil_dev;      // uploaded file bytes
     DevBuf xcm;          // channel-major uint8 [Ck][pitch]
     DevBuf delays_dev;   // int32 [ndm][Ck] (kept channels)
+    std::vector<int32_t> delays_host;  // what delays_dev holds (keep list + delays), empty if unknown
     DevBuf series;       // float [B][nfft]
     DevBuf sums;         // unsigned long long [B]
     DevBuf fftA, fftB;   // float2 [B][M]

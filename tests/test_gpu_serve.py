@@ -192,13 +192,13 @@ def test_take_cands_after_ecap_needs_no_second_search(L, ctx):
 
 
 def test_alternate_launch_shapes_are_exact(L, ctx, monkeypatch):
-    # 8 points per lane in the harmonic sum, a 64 KiB dedispersion chunk budget
+    # 16 points per lane in the harmonic sum, a 64 KiB dedispersion chunk budget
     # and the warp-per-block whitening median: the same arithmetic, the same bytes
     for case in (_case_a(1001), _case_b()):
-        monkeypatch.setenv("PSS_TUNE", "0,8,64,1,0")
+        monkeypatch.setenv("PSS_TUNE", "0,16,64,1,0")
         plan = L.Plan(L.FilDesc.of(case.fil), case.stages)
         b = L.Batch(plan, L.cfg_of(case.cfg))
-        assert b.tuning == {"fft_split": 0, "harm_run": 8, "dedisp_kb": 64, "whiten_form": 1, "fused": 0}
+        assert b.tuning == {"fft_split": 0, "harm_run": 16, "dedisp_kb": 64, "whiten_form": 1, "fused": 0}
         got = b.run(case.fil.data)
         b.close()
         monkeypatch.delenv("PSS_TUNE")
