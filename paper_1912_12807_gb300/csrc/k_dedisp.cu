@@ -187,7 +187,9 @@ __global__ void __launch_bounds__(NT) k_dedisp(DedispArgs a, int RW, int CC, uin
     for (int c = 0; c < nchunks; ++c) {
         const int cb = c * CC;
         const int cn = min(CC, a.ck - cb);
-        const bool ok = mbar_wait(S.bar, (uint32_t)(c & 1));
+        // one warp polls the mbarrier; the others wait at the block barrier (which
+        // does not take issue slots), and the barrier passes the staged bytes on
+        const bool ok = warp == 0 ? mbar_wait(S.bar, (uint32_t)(c & 1)) : true;
         if (__syncthreads_or(!ok)) {
             failed_at = c;
             break;
