@@ -537,7 +537,7 @@ pss_status enqueue_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* 
             }
             PSS_CUDA(launch_fft_whiten(fa, s, ctx));
             if (mode == MODE_SPECTRUM || mode == MODE_GAINS) continue;
-            PlaneArgs pl;
+            PlaneArgs pl{};
             pl.spec = spec;
             pl.spec_stride = M;
             pl.nfft = nfft;
@@ -562,6 +562,7 @@ pss_status enqueue_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* 
                 pl.tw = (const float2*)ctx->twid.p;
                 pl.twM = ctx->twid_n;
                 pl.nz = P.nz;
+                pl.form = ctx->tune.plane_form;
                 pl.zrow0 = -1;
                 for (int j = 0; j < P.nz; ++j)
                     if (-(double)cfg->zmax + (double)j * pl.dz == 0.0) pl.zrow0 = j;
@@ -811,6 +812,8 @@ pss_status pss_ctx_create(int device, pss_ctx** out) {
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     // PSS_FUSED=1: the cluster-fused FFT / whitening / plane kernel where it applies
     if (const char* f = getenv("PSS_FUSED")) c->tune.fused = f[0] == '1';
+    // PSS_PLANE_FORM=1: the radix 16-16-8 overlap-save plane kernel
+    if (const char* f = getenv("PSS_PLANE_FORM")) c->tune.plane_form = f[0] == '1';
     *out = c;
     return PSS_OK;
 }
@@ -1342,12 +1345,13 @@ pss_status autotune(pss_ctx* ctx, const Plan& plan, const pss_fil_desc* fil, con
     // PSS_TUNE="fft,harm,dedisp,whiten" pins the launch shapes instead (not remembered)
     if (const char* pin = getenv("PSS_TUNE")) {
         Tune t;
-        const int got = sscanf(pin, "%d,%d,%d,%d,%d", &t.fft_variant, &t.harm_run, &t.dedisp_kb, &t.whiten_form,
-                               &t.fused);
-        if (got != 4 && got != 5)
-            return fail(PSS_EINVAL,
-                        "PSS_TUNE must be four or five integers: fft split, harm run, dedisp KiB, whiten form[, fused]");
-        if (t.fused != 0 && t.fused != 1) return fail(PSS_EINVAL, "PSS_TUNE value out of range");
+        const int got = sscanf(pin, "%d,%d,%d,%d,%d,%d", &t.fft_variant, &t.harm_run, &t.dedisp_kb, &t.whiten_form,
+                               &t.fused, &t.plane_form);
+        if (got < 4)
+            return fail(PSS_EINVAL, "PSS_TUNE must be 4 to 6 integers: fft split, harm run, dedisp KiB, whiten form"
+                                    "[, fused[, plane form]]");
+        if ((t.fused != 0 && t.fused != 1) || (t.plane_form != 0 && t.plane_form != 1))
+            return fail(PSS_EINVAL, "PSS_TUNE value out of range");
         int rad[4];
         if (fft_pass_plan(plan.stages[0].nfft / 2, t.fft_variant, rad) == 0 || (t.harm_run != 8 && t.harm_run != 16) ||
             t.dedisp_kb < 16 || t.dedisp_kb > 200 || (t.whiten_form != 0 && t.whiten_form != 1))
@@ -1419,6 +1423,8 @@ pss_status autotune(pss_ctx* ctx, const Plan& plan, const pss_fil_desc* fil, con
             st = sweep(&ctx->tune.fft_variant, fv, 1u << 2, "fft split");
             if (st == PSS_OK) st = sweep(&ctx->tune.whiten_form, {0, 1}, 1u << 3, "whiten");
         }
+        if (st == PSS_OK && cfg->zmax > 0 && plane_fft_usable(cfg->zmax, cfg->halfwidth_extra, plan.stages[0].nfft / 2))
+            st = sweep(&ctx->tune.plane_form, {0, 1}, 1u << 4, "plane form");
         if (st == PSS_OK) st = sweep(&ctx->tune.harm_run, {8, 16}, 1u << 5, "harm run");
         if (st == PSS_OK) st = sweep(&ctx->tune.dedisp_kb, {96, 64}, 1u << 1, "dedisp kb");
     }

@@ -53,6 +53,39 @@ __device__ __forceinline__ void dft_small(float2* x) {
     else dft8(x);
 }
 
+// W_16^m = exp(-2 pi i m / 16)
+__device__ __forceinline__ float2 w16(int m) {
+    constexpr float C[16] = {1.f,          0.92387953f,  0.70710678f,  0.38268343f, 0.f,          -0.38268343f,
+                             -0.70710678f, -0.92387953f, -1.f,         -0.92387953f, -0.70710678f, -0.38268343f,
+                             0.f,          0.38268343f,  0.70710678f,  0.92387953f};
+    return make_float2(C[m & 15], -C[(m + 12) & 15]);  // (cos, -sin): sin(x) = cos(x - pi/2)
+}
+
+// 16-point forward DFT in registers (4 x 4), natural order in and out
+__device__ __forceinline__ void dft16(float2 (&x)[16]) {
+    float2 y[4][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+        float2 t[4] = {x[n2], x[4 + n2], x[8 + n2], x[12 + n2]};
+        dft4v(t);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) y[n2][k1] = (n2 && k1) ? cmul(t[k1], w16(n2 * k1)) : t[k1];
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        float2 t[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
+        dft4v(t);
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) x[k1 + 4 * k2] = t[k2];
+    }
+}
+
+template <int RR>
+__device__ __forceinline__ void dft_any(float2 (&x)[RR]) {
+    if constexpr (RR == 16) dft16(x);
+    else dft_small<RR>(x);
+}
+
 // Swizzled shared-memory index for 8-byte elements: within each run of 16
 // (one 128-byte line) the slot is XORed with a function of the run number,
 // chosen so that every access of the 8-8-8-4 sub-stage order (16 consecutive
@@ -64,6 +97,11 @@ __host__ __device__ __forceinline__ int fp(int i) {
     return (i & ~15) | ((i & 15) ^ g);
 }
 
+
+// A second swizzle for the 16-16-8 sub-stage order (strided writes of 16
+// runs of one element, or 16 consecutive elements): the slot is XORed with
+// the run number.
+__host__ __device__ __forceinline__ int fx(int i) { return (i & ~15) | ((i & 15) ^ ((i >> 4) & 15)); }
 
 // Odd half-bin tap i of the z = 0 template with 2m = NTAP taps: the
 // imaginary part of conj(rho(1/2 - t, 0)) with t = i - (m - 1), which is

@@ -339,6 +339,123 @@ __global__ void __launch_bounds__(FNT, 3) k_plane_fft(const __grid_constant__ Pl
     }
 }
 
+// ---- overlap-save plane, radix 16-16-8 form (an autotuner choice) -------------------
+// The same correlation as k_plane_fft with 128 threads and three in-place
+// sub-stages (radix 16, 16, 8) instead of four: fewer shared-memory passes
+// and barriers per row, at lower thread count.
+constexpr int F16NT = 128;
+constexpr int T16A = 0;             // RR 16, NS 16: 16 x 16
+constexpr int T16B = T16A + 256;    // RR 8, NS 256: 8 x 256
+constexpr int T16N = T16B + 2048;
+
+template <int RR, int NS>
+__device__ __forceinline__ void fft16_substage2(float2* b0, float2* b1, const float2* twt) {
+    constexpr int L = PLANE_FFT_L;
+    constexpr int NB = L / RR;
+    constexpr int PER = NB / F16NT;
+    float2 x0[PER][RR], x1[PER][RR];
+    int dst[PER];
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int b = threadIdx.x + p * F16NT;
+        const int k = b & (NS - 1);
+#pragma unroll
+        for (int q = 0; q < RR; ++q) {
+            x0[p][q] = b0[fx(b + q * NB)];
+            x1[p][q] = b1[fx(b + q * NB)];
+            if (NS > 1 && q) {
+                const float2 w = twt[q * NS + k];
+                x0[p][q] = cmul(x0[p][q], w);
+                x1[p][q] = cmul(x1[p][q], w);
+            }
+        }
+        dst[p] = (b - k) * RR + k;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        dft_any<RR>(x0[p]);
+        dft_any<RR>(x1[p]);
+#pragma unroll
+        for (int q = 0; q < RR; ++q) {
+            b0[fx(dst[p] + q * NS)] = x0[p][q];
+            b1[fx(dst[p] + q * NS)] = x1[p][q];
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void fft2048x2_r16(float2* b0, float2* b1, const float2* twt) {
+    fft16_substage2<16, 1>(b0, b1, twt);
+    fft16_substage2<16, 16>(b0, b1, twt + T16A);
+    fft16_substage2<8, 256>(b0, b1, twt + T16B);
+}
+
+__global__ void __launch_bounds__(F16NT) k_plane_fft16(const __grid_constant__ PlaneArgs a) {
+    constexpr int L = PLANE_FFT_L;
+    constexpr int NE = L / F16NT;  // 16 bins per thread
+    extern __shared__ float2 fsm[];
+    float2* Y0 = fsm;
+    float2* Y1 = fsm + L;
+    float2* twt = fsm + 2 * L;
+    const int b = blockIdx.y;
+    const int64_t M = a.nfft / 2;
+    const int V = a.fV, M0 = a.fM0;
+    const int64_t k0 = (int64_t)blockIdx.x * V;
+    const float2* Ap = a.spec + (int64_t)b * a.spec_stride;
+    const int64_t tstride = a.twM / L;
+    for (int i = threadIdx.x; i < T16N; i += F16NT) {
+        int rr, ns, o;
+        if (i < T16B) { rr = 16; ns = 16; o = i - T16A; }
+        else { rr = 8; ns = 256; o = i - T16B; }
+        const int q = o / ns, k = o - q * ns;
+        twt[i] = a.tw[(int64_t)(q * k * (L / (rr * ns))) * tstride];
+    }
+    for (int i = threadIdx.x; i < L; i += F16NT) {
+        const int64_t k = k0 - M0 + i;
+        Y0[fx(i)] = (k >= 0 && k < M) ? Ap[k] : make_float2(0.f, 0.f);
+        Y1[fx(i)] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    fft2048x2_r16(Y0, Y1, twt);
+    float2 X[NE];
+#pragma unroll
+    for (int e = 0; e < NE; ++e) X[e] = Y0[fx(threadIdx.x + e * F16NT)];
+    __syncthreads();
+    const int nz = a.nz;
+    float2* P = reinterpret_cast<float2*>(a.plane + (int64_t)b * a.plane_stride);
+    for (int j = 0; j < nz; ++j) {
+        const bool zrow0 = (j == a.zrow0);
+        const float2* T0 = a.ftaps + (int64_t)j * 2 * L;
+        const float2* T1 = T0 + L;
+#pragma unroll
+        for (int e = 0; e < NE; ++e) {
+            const int i = threadIdx.x + e * F16NT;
+            const float2 y0 = cmul(X[e], __ldg(T0 + i)), y1 = cmul(X[e], __ldg(T1 + i));
+            Y0[fx(i)] = make_float2(y0.x, -y0.y);
+            Y1[fx(i)] = make_float2(y1.x, -y1.y);
+        }
+        __syncthreads();
+        fft2048x2_r16(Y0, Y1, twt);
+        float2* row = P + (int64_t)j * M;
+#pragma unroll
+        for (int e = 0; e < NE; ++e) {
+            const int u = threadIdx.x + e * F16NT;
+            const int64_t k = k0 + u;
+            if (u < V && k < M) {
+                const float2 y0 = Y0[fx(u)], y1 = Y1[fx(u)];
+                float p0 = y0.x * y0.x + y0.y * y0.y;
+                if (zrow0) {
+                    const float2 c = Ap[k];
+                    p0 = c.x * c.x + c.y * c.y;
+                }
+                row[k] = make_float2(p0, y1.x * y1.x + y1.y * y1.y);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_fft_templates(const FftTemplateArgs& a, cudaStream_t s) {
@@ -364,6 +481,15 @@ cudaError_t launch_plane(const PlaneArgs& a, cudaStream_t s) {
         return cudaGetLastError();
     }
     const int nz = a.zmax ? (int)llround(2.0 * a.zmax / a.dz) + 1 : 1;
+    if (a.ftaps && a.form == 1) {
+        if (a.fL != PLANE_FFT_L || a.fV <= 0 || a.twM % PLANE_FFT_L) return cudaErrorInvalidValue;
+        const size_t shm = (size_t)(2 * PLANE_FFT_L + T16N) * sizeof(float2);
+        cudaError_t e = allow_smem((const void*)k_plane_fft16, shm);
+        if (e != cudaSuccess) return e;
+        dim3 grid((unsigned)((M + a.fV - 1) / a.fV), (unsigned)a.nb);
+        k_plane_fft16<<<grid, F16NT, shm, s>>>(a);
+        return cudaGetLastError();
+    }
     if (a.ftaps) {
         if (a.fL != PLANE_FFT_L || a.fV <= 0 || a.twM % PLANE_FFT_L) return cudaErrorInvalidValue;
         const size_t shm = (size_t)(2 * PLANE_FFT_L + TWN) * sizeof(float2);

@@ -52,33 +52,6 @@ constexpr size_t SMEM_BYTES = OFF_U32 * sizeof(float2) + (size_t)NW * (NBIN + 2 
 
 __device__ __forceinline__ int tp(int i) { return i + (i >> 4); }  // padded FIR tile index
 
-// W_16^m = exp(-2 pi i m / 16)
-__device__ __forceinline__ float2 w16(int m) {
-    constexpr float C[16] = {1.f,          0.92387953f,  0.70710678f,  0.38268343f, 0.f,          -0.38268343f,
-                             -0.70710678f, -0.92387953f, -1.f,         -0.92387953f, -0.70710678f, -0.38268343f,
-                             0.f,          0.38268343f,  0.70710678f,  0.92387953f};
-    return make_float2(C[m & 15], -C[(m + 12) & 15]);  // (cos, -sin): sin(x) = cos(x - pi/2)
-}
-
-// 16-point forward DFT in registers (4 x 4), natural order in and out
-__device__ __forceinline__ void dft16(float2 (&x)[16]) {
-    float2 y[4][4];
-#pragma unroll
-    for (int n2 = 0; n2 < 4; ++n2) {
-        float2 t[4] = {x[n2], x[4 + n2], x[8 + n2], x[12 + n2]};
-        dft4v(t);
-#pragma unroll
-        for (int k1 = 0; k1 < 4; ++k1) y[n2][k1] = (n2 && k1) ? cmul(t[k1], w16(n2 * k1)) : t[k1];
-    }
-#pragma unroll
-    for (int k1 = 0; k1 < 4; ++k1) {
-        float2 t[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
-        dft4v(t);
-#pragma unroll
-        for (int k2 = 0; k2 < 4; ++k2) x[k1 + 4 * k2] = t[k2];
-    }
-}
-
 // exp(-2 pi i t / 8192) = WH[t >> 6] WL[t & 63]
 __device__ __forceinline__ float2 tw8192(const float2* WH, const float2* WL, int t) {
     return cmul(WH[t >> 6], WL[t & 63]);

@@ -126,6 +126,7 @@ struct Tune {
     int dedisp_kb = 96;    // dedispersion chunk staging budget
     int whiten_form = 0;   // whitening kernel form
     int fused = 0;         // zmax 0, nfft 2^18: cluster-fused FFT + whitening + plane (where the device allows)
+    int plane_form = 0;    // overlap-save plane kernel form
 };
 
 struct Ctx {
@@ -315,6 +316,7 @@ struct PlaneArgs {
     const float2* ftaps;
     int32_t fL, fV, fM0;     // segment length, valid outputs per segment, lead
     int32_t nz, zrow0;       // rows, and the row with z = 0 exactly (-1: none)
+    int32_t form;            // overlap-save FFT: 0 radix 8-8-8-4 (256 threads), 1 radix 16-16-8 (128 threads)
     const float2* tw;        // exp(-2 pi i t / twM)
     int64_t twM;
 };

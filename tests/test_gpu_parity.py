@@ -169,6 +169,26 @@ def test_accel_plane(L, ctx, zmax, dz):
         check_powers(got[k * nz * nfft:(k + 1) * nz * nfft].reshape(nz, nfft), ref, "accel plane DM %d" % i)
 
 
+def test_accel_plane_radix16_form(L, monkeypatch):
+    # the radix 16-16-8 overlap-save kernel (an autotuner choice) against the oracle
+    monkeypatch.setenv("PSS_PLANE_FORM", "1")
+    c = L.Context(0)
+    fil = synth.make_8bit(64, 1 << 14, 2e-4, 1200.0, 1500.0,
+                          [synth.Pulsar(0.01, 20.0, 0.05, 0.3, z_direct=9.0)], seed=3)
+    stages = [synth.Stage(10.0, 5.0, 4, 1)]
+    for zmax, dz in ((50, 2.0), (7, 0.5)):
+        wl = synth.Workload("t", fil, stages, synth.SearchCfg(zmax=zmax, dz=dz, numharm=4, whiten_block=256))
+        cfg = _cfg(L, wl)
+        plan = L.Plan(L.FilDesc.of(fil), stages)
+        op = OP.Plan.for_file(fil, stages)
+        x = OD.channel_major(fil.data, fil.nchan, 8)
+        got = L.pss_power_plane(c, plan, _torch_dev(fil.data), cfg, 1, 2).cpu().numpy()
+        nz, nfft = L.n_z(cfg), op.nv_nfft(1)[1]
+        _, _, ref = oracle_plane(x, op, 1, wl.cfg)
+        check_powers(got.reshape(nz, nfft), ref, "radix-16 plane zmax %d" % zmax)
+    c.close()
+
+
 def test_accel_plane_direct_form(L, ctx):
     # a spectrum shorter than the overlap-save segment (1024 bins) takes the direct form
     fil = synth.make_8bit(32, 2000, 2e-4, 1200.0, 1500.0,
