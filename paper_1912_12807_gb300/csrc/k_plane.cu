@@ -391,7 +391,7 @@ __device__ __forceinline__ void fft2048x2_r16(float2* b0, float2* b1, const floa
     fft16_substage2<8, 256>(b0, b1, twt + T16B);
 }
 
-__global__ void __launch_bounds__(F16NT) k_plane_fft16(const __grid_constant__ PlaneArgs a) {
+__global__ void __launch_bounds__(F16NT, 4) k_plane_fft16(const __grid_constant__ PlaneArgs a) {
     constexpr int L = PLANE_FFT_L;
     constexpr int NE = L / F16NT;  // 16 bins per thread
     extern __shared__ float2 fsm[];
