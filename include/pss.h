@@ -359,11 +359,11 @@ size_t pss_batch_footprint(const pss_batch* b);
  * choice on the first <= 256 trials of the shape, timing the stage it
  * changes, and keeps the fastest;
  * the choice is remembered per shape for the life of the process;
- * environment PSS_AUTOTUNE=0 keeps the defaults 0 / 8 / 96 / 0 / 0):
+ * environment PSS_AUTOTUNE=0 keeps the defaults 0 / 8 / 96 / -1 / 0):
  * fft_split: FFT pass-split variant (0 = even split), harm_run: points per
  * lane of the harmonic sum (16 or 8), dedisp_kb: shared memory for staged
- * channel chunks (KiB), whiten_form: whitening median per CTA (0) or per
- * warp (1), fused: for zmax 0 and nfft 2^18, FFT + whitening + plane in one
+ * channel chunks (KiB), whiten_form: whitening median per CTA (0), per
+ * warp (1) or by size (-1: per warp up to 2^18 bins), fused: for zmax 0 and nfft 2^18, FFT + whitening + plane in one
  * thread-block-cluster launch (1) or as separate kernels (0); the fused
  * path is used only where the device can run 16-CTA clusters.  Pointers
  * are nullable. */

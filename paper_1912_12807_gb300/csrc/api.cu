@@ -526,7 +526,7 @@ pss_status enqueue_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* 
             fa.tw = (const float2*)ctx->twid.p;
             fa.twM = ctx->twid_n;
             fa.fft_variant = ctx->tune.fft_variant;
-            fa.whiten_form = ctx->tune.whiten_form;
+            fa.whiten_form = ctx->tune.whiten_form >= 0 ? ctx->tune.whiten_form : (M <= (int64_t(1) << 18) ? 1 : 0);
             set_passtw(ctx, &fa);
             fa.whiten = 1;
             fa.gains_out = nullptr;
@@ -812,7 +812,7 @@ pss_status pss_ctx_create(int device, pss_ctx** out) {
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     // PSS_FUSED=1: the cluster-fused FFT / whitening / plane kernel where it applies
     if (const char* f = getenv("PSS_FUSED")) c->tune.fused = f[0] == '1';
-    // PSS_PLANE_FORM=1: the radix 16-16-8 overlap-save plane kernel
+    // PSS_PLANE_FORM=0 / 1: the radix 8-8-8-4 / 16-16-8 overlap-save plane kernel
     if (const char* f = getenv("PSS_PLANE_FORM")) c->tune.plane_form = f[0] == '1';
     *out = c;
     return PSS_OK;
@@ -1354,7 +1354,7 @@ pss_status autotune(pss_ctx* ctx, const Plan& plan, const pss_fil_desc* fil, con
             return fail(PSS_EINVAL, "PSS_TUNE value out of range");
         int rad[4];
         if (fft_pass_plan(plan.stages[0].nfft / 2, t.fft_variant, rad) == 0 || (t.harm_run != 8 && t.harm_run != 16) ||
-            t.dedisp_kb < 16 || t.dedisp_kb > 200 || (t.whiten_form != 0 && t.whiten_form != 1))
+            t.dedisp_kb < 16 || t.dedisp_kb > 200 || t.whiten_form < -1 || t.whiten_form > 1)
             return fail(PSS_EINVAL, "PSS_TUNE value out of range");
         ctx->tune = t;
         return PSS_OK;
@@ -1422,9 +1422,11 @@ pss_status autotune(pss_ctx* ctx, const Plan& plan, const pss_fil_desc* fil, con
         if (st == PSS_OK && !ctx->tune.fused) {
             st = sweep(&ctx->tune.fft_variant, fv, 1u << 2, "fft split");
             if (st == PSS_OK) st = sweep(&ctx->tune.whiten_form, {0, 1}, 1u << 3, "whiten");
+        } else {
+            ctx->tune.whiten_form = 0;  // not used by the fused kernel
         }
         if (st == PSS_OK && cfg->zmax > 0 && plane_fft_usable(cfg->zmax, cfg->halfwidth_extra, plan.stages[0].nfft / 2))
-            st = sweep(&ctx->tune.plane_form, {0, 1}, 1u << 4, "plane form");
+            st = sweep(&ctx->tune.plane_form, {1, 0}, 1u << 4, "plane form");
         if (st == PSS_OK) st = sweep(&ctx->tune.harm_run, {8, 16}, 1u << 5, "harm run");
         if (st == PSS_OK) st = sweep(&ctx->tune.dedisp_kb, {96, 64}, 1u << 1, "dedisp kb");
     }

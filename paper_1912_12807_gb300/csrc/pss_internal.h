@@ -124,9 +124,9 @@ struct Tune {
     int fft_variant = 0;   // FFT pass split
     int harm_run = 8;      // harmonic-sum points per lane
     int dedisp_kb = 96;    // dedispersion chunk staging budget
-    int whiten_form = 0;   // whitening kernel form
+    int whiten_form = -1;  // whitening kernel form (-1: by size, warp-per-block up to 2^18 bins)
     int fused = 0;         // zmax 0, nfft 2^18: cluster-fused FFT + whitening + plane (where the device allows)
-    int plane_form = 0;    // overlap-save plane kernel form
+    int plane_form = 1;    // overlap-save plane kernel form (1: radix 16-16-8, 0: radix 8-8-8-4)
 };
 
 struct Ctx {

@@ -169,9 +169,10 @@ def test_accel_plane(L, ctx, zmax, dz):
         check_powers(got[k * nz * nfft:(k + 1) * nz * nfft].reshape(nz, nfft), ref, "accel plane DM %d" % i)
 
 
-def test_accel_plane_radix16_form(L, monkeypatch):
-    # the radix 16-16-8 overlap-save kernel (an autotuner choice) against the oracle
-    monkeypatch.setenv("PSS_PLANE_FORM", "1")
+@pytest.mark.parametrize("form", ["0", "1"])
+def test_accel_plane_both_fft_forms(L, monkeypatch, form):
+    # both overlap-save kernels (radix 8-8-8-4 and 16-16-8; an autotuner choice) against the oracle
+    monkeypatch.setenv("PSS_PLANE_FORM", form)
     c = L.Context(0)
     fil = synth.make_8bit(64, 1 << 14, 2e-4, 1200.0, 1500.0,
                           [synth.Pulsar(0.01, 20.0, 0.05, 0.3, z_direct=9.0)], seed=3)
@@ -185,7 +186,7 @@ def test_accel_plane_radix16_form(L, monkeypatch):
         got = L.pss_power_plane(c, plan, _torch_dev(fil.data), cfg, 1, 2).cpu().numpy()
         nz, nfft = L.n_z(cfg), op.nv_nfft(1)[1]
         _, _, ref = oracle_plane(x, op, 1, wl.cfg)
-        check_powers(got.reshape(nz, nfft), ref, "radix-16 plane zmax %d" % zmax)
+        check_powers(got.reshape(nz, nfft), ref, "plane form %s zmax %d" % (form, zmax))
     c.close()
 
 
