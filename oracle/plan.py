@@ -82,20 +82,29 @@ def stage_lengths(nsamp: int, max_delay: int, ds: int):
 
 
 class Plan:
-    """Everything the search needs from the plan, computed once."""
+    """Everything the search needs from the plan, computed once.
 
-    def __init__(self, nchan, nsamp, tsamp_s, fch0_mhz, foff_mhz, stages):
+    subband = (nsub, group) selects the two-stage scheme of
+    `oracle.subband` (self.sub); its largest combined delay then also bounds
+    the valid length (D' = max(D, that delay))."""
+
+    def __init__(self, nchan, nsamp, tsamp_s, fch0_mhz, foff_mhz, stages, subband=None):
         self.nchan, self.nsamp, self.tsamp_s = int(nchan), int(nsamp), float(tsamp_s)
         self.freqs = channel_freqs(nchan, fch0_mhz, foff_mhz)
         self.stages = list(stages)
         self.dms, self.stage_of, self.ds_of = dm_grid(self.stages)
         self.delays = delay_table(self.dms, self.freqs, self.tsamp_s)
         self.max_delay = int(self.delays.max()) if self.delays.size else 0
+        self.sub = None
+        if subband is not None:
+            from .subband import SubbandPlan
+            self.sub = SubbandPlan(self.freqs, self.dms, self.stage_of, self.tsamp_s, *subband)
+            self.max_delay = max(self.max_delay, self.sub.max_comb)
         self.lengths = [stage_lengths(self.nsamp, self.max_delay, int(s.ds)) for s in self.stages]
 
     @classmethod
-    def for_file(cls, fil, stages):
-        return cls(fil.nchan, fil.nsamp, fil.tsamp_s, fil.fch0_mhz, fil.foff_mhz, stages)
+    def for_file(cls, fil, stages, subband=None):
+        return cls(fil.nchan, fil.nsamp, fil.tsamp_s, fil.fch0_mhz, fil.foff_mhz, stages, subband)
 
     def nv_nfft(self, dm_idx: int):
         return self.lengths[int(self.stage_of[dm_idx])]

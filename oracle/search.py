@@ -14,6 +14,7 @@ from . import plan as _plan
 from . import response as _resp
 from . import sift as _sift
 from . import spectrum as _sp
+from . import subband as _sb
 from . import stats as _st
 
 
@@ -21,7 +22,10 @@ def spectrum_of_trial(x_cm, P: _plan.Plan, dm_idx: int, block: int, chan_mask=No
     """(s int64 [N_v], A' complex128 [nfft/2]) for one DM trial."""
     ds = int(P.ds_of[dm_idx])
     nv, nfft = P.nv_nfft(dm_idx)
-    s = _dd.dedisperse(x_cm, P.delays[dm_idx], P.max_delay, ds, chan_mask)
+    if P.sub is None:
+        s = _dd.dedisperse(x_cm, P.delays[dm_idx], P.max_delay, ds, chan_mask)
+    else:
+        s = _sb.dedisperse_subband(x_cm, P.sub, dm_idx, P.max_delay, ds, chan_mask)
     assert s.shape[0] == nv
     y = _sp.real_series(s, nfft)
     A = _sp.half_spectrum(y)
@@ -47,9 +51,10 @@ def search_trial(x_cm, P: _plan.Plan, dm_idx: int, cfg, thr: Optional[dict] = No
 
 
 def search(fil, stages, cfg, dm_indices: Optional[Iterable[int]] = None,
-           plane_method: str = "direct"):
-    """(raw candidates by DM index, sifted list) for a file."""
-    P = _plan.Plan.for_file(fil, stages)
+           plane_method: str = "direct", subband=None):
+    """(raw candidates by DM index, sifted list) for a file; subband =
+    (nsub, group) dedisperses by the two-stage scheme (oracle.subband)."""
+    P = _plan.Plan.for_file(fil, stages, subband)
     x_cm = _dd.channel_major(fil.data, fil.nchan, fil.nbits)
     thr = _st.thresholds(cfg.numharm, cfg.sigma_thr)
     idx = range(len(P.dms)) if dm_indices is None else dm_indices
