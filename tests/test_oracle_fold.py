@@ -1,0 +1,81 @@
+"""Pins for the folding oracle (oracle/fold.py)."""
+import math
+
+import numpy as np
+from scipy import stats
+
+from oracle import fold as FO
+
+
+def test_phase_bins_brute_force():
+    # exact rational phases: f = 3/8 Hz, dt = 1/4 s -> phase j*3/32; bins of 8
+    b = FO.phase_bins(40, 0.25, 0.375, 0.0, 8)
+    ref = [((j * 3) % 32) * 8 // 32 for j in range(40)]
+    assert b.tolist() == ref
+
+
+def test_fold_brute_force_with_drift():
+    rng = np.random.default_rng(1)
+    s = rng.integers(0, 1000, 500)
+    dt, f, fdot, nbin = 1e-3, 37.3, 2.1, 16
+    P, n = FO.fold(s, dt, f, fdot, nbin)
+    Pr, nr = [0] * nbin, [0] * nbin
+    for j in range(500):
+        t = j * dt
+        ph = f * t + 0.5 * fdot * t * t
+        k = int(math.floor((ph - math.floor(ph)) * nbin))
+        Pr[k] += int(s[j])
+        nr[k] += 1
+    assert P.tolist() == Pr and n.tolist() == nr
+    assert int(P.sum()) == int(s.sum()) and int(n.sum()) == 500
+
+
+def test_chi2_of_noise_is_chi2_distributed():
+    # white noise folded at an unrelated frequency: chi2 follows chi2(nbin - 1),
+    # so chi2_red has mean 1 and sd sqrt(2/(nbin-1)); over 200 folds the mean is 1 +- 5 sd/sqrt(200)
+    rng = np.random.default_rng(2)
+    nbin, vals = 32, []
+    for i in range(200):
+        s = np.round(1000 + 30 * rng.standard_normal(4096)).astype(np.int64)
+        mu = s.mean()
+        var = float(((s - mu) ** 2).mean())
+        P, n = FO.fold(s, 1e-3, 7.77 + 0.01 * i, 0.0, nbin)
+        vals.append(FO.chi2_red(P, n, float(s.sum()) / 4096, var))
+    sd = math.sqrt(2.0 / (nbin - 1))
+    assert abs(np.mean(vals) - 1.0) < 5 * sd / math.sqrt(200)
+    # and the distribution itself (Kolmogorov-Smirnov against chi2(nbin-1)/(nbin-1))
+    p = stats.kstest(np.array(vals) * (nbin - 1), "chi2", args=(nbin - 1,)).pvalue
+    assert p > 1e-3
+
+
+def test_fold_search_finds_the_injected_frequency():
+    # a pulse train at f0 = 13.1 Hz folded from a grid started 2 bins off
+    rng = np.random.default_rng(3)
+    N, dt = 1 << 15, 5e-4
+    T = N * dt
+    t = np.arange(N) * dt
+    f0 = 13.1
+    ph = (f0 * t) % 1.0
+    s = np.round(1000 + 30 * rng.standard_normal(N) + 40 * (ph < 0.05)).astype(np.int64)
+    k, fk, c, P, n = FO.fold_search(s, dt, T, f0 + 2.0 / T, 0.0, 64, 9, 0.5)
+    assert k == 0 and abs(fk - f0) < 1e-12            # 2 bins = 4 steps of 0.5 below the centre
+    assert c > 20  # about 38 expected: 5 % duty, 1.3 sigma per sample
+    assert int(np.argmax(P / n)) in (0, 1, 2, 3)      # the pulse sits at phase 0-0.05
+    # the chi2 of a flat series is 0
+    assert FO.fold_search(np.full(1000, 5), dt, T, 3.0, 0.0, 16, 3, 1.0)[2] == 0.0
+
+
+def test_drift_term_realigns_a_chirped_train():
+    # a pulse train whose frequency drifts by 3 bins over the span folds sharply
+    # only with its fdot (a dropped or wrong-signed drift term smears it)
+    rng = np.random.default_rng(4)
+    N, dt = 1 << 15, 5e-4
+    T = N * dt
+    t = np.arange(N) * dt
+    f0, fd = 13.1, 3.0 / T / T
+    ph = (f0 * t + 0.5 * fd * t * t) % 1.0
+    s = np.round(1000 + 30 * rng.standard_normal(N) + 40 * (ph < 0.05)).astype(np.int64)
+    good = FO.fold_search(s, dt, T, f0, fd, 64, 1, 0.0)[2]
+    none = FO.fold_search(s, dt, T, f0, 0.0, 64, 1, 0.0)[2]
+    wrong = FO.fold_search(s, dt, T, f0, -fd, 64, 1, 0.0)[2]
+    assert good > 3 * none and good > 3 * wrong
