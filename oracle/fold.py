@@ -11,7 +11,8 @@ of trial frequencies around the candidate's:
 * Sample j of a series with ds-fold downsampling is at t_j = j * dt,
   dt = ds * tsamp.  Its phase at frequency f and drift fdot (Hz/s) is
   phi_j = f*t_j + (0.5*fdot)*(t_j*t_j), and its bin is
-  floor((phi_j - floor(phi_j)) * nbin) (FP64, in that order).
+  min(floor((phi_j - floor(phi_j)) * nbin), nbin - 1) (FP64, in that order;
+  the product can round up to nbin when the fraction is within an ulp of 1).
 * Profile P_b = sum of s_j over the samples of bin b, n_b their number
   (exact integers).
 * Significance: with mu = S1/N and var = (S2 - S1*S1/N)/N of the series
@@ -32,7 +33,7 @@ def phase_bins(n: int, dt: float, f: float, fdot: float, nbin: int) -> np.ndarra
     t = np.arange(n, dtype=np.float64) * dt
     phi = f * t + (0.5 * fdot) * (t * t)
     frac = phi - np.floor(phi)
-    return np.floor(frac * float(nbin)).astype(np.int64)
+    return np.minimum(np.floor(frac * float(nbin)), float(nbin - 1)).astype(np.int64)
 
 
 def fold(s: np.ndarray, dt: float, f: float, fdot: float, nbin: int):
