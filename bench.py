@@ -412,6 +412,20 @@ def run_ours(args, rank, world, local_rank):
     if wl.cfg.zmax > 0 and rank == 0 and len(cands):
         refine = run_refine(pss, ctx, plan, data_dev, cfg, cands, args.refine_top)
 
+    subband = None
+    if args.subband != "none" and rank == 0:
+        nsub, group = (int(v) for v in args.subband.split(","))
+        subband = run_subband(pss, ctx, wl, data_dev, cfg, ndm, max(3, args.steps), flush, stream, cands,
+                              nsub, group)
+
+    folded = None
+    if args.fold_top > 0 and rank == 0 and len(cands):
+        folded = run_fold(pss, ctx, plan, data_dev, cands, args.fold_top, max(3, args.steps))
+
+    single = None
+    if args.single_pulse and rank == 0:
+        single = run_single_pulse(pss, ctx, plan, data_dev, ndm, max(3, args.steps), flush)
+
     batched = served = None
     if not args.no_serve:
         batched = run_batched(pss, plan, cfg, data_dev, ndm, max(3, args.steps), flush)
@@ -452,7 +466,8 @@ def run_ours(args, rank, world, local_rank):
             "stage_rooflines": {k: {"bound": v["bound"], "frac": v["frac"], "achieved": v["achieved"],
                                     "unit": v["unit"]} for k, v in rooflines.items()},
             "clocks": clocks.summary(), "wall_s_timed": t_wall, "candidates": int(len(cands)),
-            "batched": batched, "serve": served, "refine": refine, "cpu_baseline": cpu}
+            "batched": batched, "serve": served, "refine": refine, "subband": subband, "single_pulse": single, "fold": folded,
+            "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
@@ -478,6 +493,87 @@ def run_refine(pss, ctx, plan, data_dev, cfg, cands, top, iters=40):
     return {"candidates": int(len(sel)), "iters": iters, "s": dt, "cands_per_s": len(sel) / dt,
             "power_gain_median": float(np.median(gain)), "power_gain_min": float(gain.min()),
             "stages_prepared": int(len(np.unique([plan.trial(int(i))["stage"] for i in sel["dm_idx"]])))}
+
+
+def run_subband(pss, ctx, wl, data_dev, cfg, ndm, steps, flush, stream, exact, nsub, group):
+    """The same search on a two-stage (subband) plan of the same DM grid
+    (pss_dd_plan_subband): device time per file (CUDA events, L2 flushed
+    between steps), the dedispersion stage time, and how many of the exact
+    search's sifted candidates it finds again (same frequency within 1.5
+    bins of the span, DM within 2 steps)."""
+    import numpy as np
+    import torch
+    plan = pss.Plan(pss.FilDesc.of(wl.fil), wl.stages, subband=(nsub, group))
+    for _ in range(3):
+        cands = pss.pss_search_dm_batch(ctx, plan, data_dev, cfg, 0, ndm, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_((k + 3) & 0xFF)
+        ev[k][0].record(stream)
+        cands = pss.pss_search_dm_batch(ctx, plan, data_dev, cfg, 0, ndm, stream=stream.cuda_stream)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    dms = plan.dms()
+    step = float(np.min(np.diff(dms))) if len(dms) > 1 else 1.0
+    T = wl.fil.nsamp * wl.fil.tsamp_s
+    found = 0
+    for c in exact:
+        m = (np.abs(cands["f_hz"] - c["f_hz"]) <= 1.5 / T) & (np.abs(cands["dm"] - c["dm"]) <= 2 * step + 1e-9)
+        found += bool(m.any())
+    max_delay = plan.max_delay
+    plan.close()
+    return {"nsub": nsub, "group": group, "value": ndm / (ms / 1e3), "unit": UNIT, "ms_per_file": ms,
+            "stages_ms_per_file": {k: v[0] / steps for k, v in prof.items()},
+            "stage_launches_per_file": {k: v[1] / steps for k, v in prof.items()},
+            "candidates": int(len(cands)), "exact_candidates_found": found, "exact_candidates": int(len(exact)),
+            "max_delay": max_delay}
+
+
+def run_fold(pss, ctx, plan, data_dev, cands, top, steps, nbin=64, nfreq=9, step_bins=0.25):
+    """Folding (pss_fold) of the `top` highest-sigma sifted candidates on a grid
+    of nfreq trial frequencies each: wall time per call, which includes the
+    exact dedispersion of the candidates' trials."""
+    import numpy as np
+    import torch
+    sel = cands[np.argsort(-cands["sigma"], kind="stable")[:top]]
+    fdot = np.array([float(c["z"]) / plan.trial(int(c["dm_idx"]))["nfft"] ** 2 /
+                     (plan.trial(int(c["dm_idx"]))["ds"] * plan.desc.c.tsamp_s) ** 2 for c in sel])
+    args = (ctx, plan, data_dev, sel["dm_idx"], sel["f_hz"], fdot)
+    pss.pss_fold(*args, nbin=nbin, nfreq=nfreq, step_bins=step_bins)
+    dts = []
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, res = pss.pss_fold(*args, nbin=nbin, nfreq=nfreq, step_bins=step_bins)
+        dts.append(time.perf_counter() - t0)
+    w = statistics.mean(dts)
+    return {"candidates": int(len(sel)), "trial_freqs": nfreq, "nbin": nbin, "wall_ms": 1e3 * w,
+            "cands_per_s": len(sel) / w, "distinct_trials": int(len(np.unique(sel["dm_idx"]))),
+            "chi2_red_median": float(np.median(res["chi2_red"]))}
+
+
+def run_single_pulse(pss, ctx, plan, data_dev, ndm, steps, flush):
+    """Single-pulse search (pss_single_pulse: exact int32 dedispersion of every
+    trial, boxcar detection on the device, S/N and pruning on the host) over
+    the whole file: wall time per file with the event download."""
+    import torch
+    pss.pss_single_pulse(ctx, plan, data_dev, 0, ndm)
+    dts, n = [], 0
+    for k in range(steps):
+        flush.fill_((k + 5) & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev = pss.pss_single_pulse(ctx, plan, data_dev, 0, ndm)
+        dts.append(time.perf_counter() - t0)
+        n = len(ev)
+    w = statistics.mean(dts)
+    return {"value": ndm / w, "unit": UNIT, "wall_ms_per_file": 1e3 * w, "events": n,
+            "widths": list(pss.SP_WIDTHS), "sigma_thr": 6.0}
 
 
 def run_batched(pss, plan, cfg, data_dev, ndm, steps, flush):
@@ -646,9 +742,19 @@ def main():
     ap.add_argument("--stream-files", type=int, default=64)
     ap.add_argument("--refine-top", type=int, default=4096, help="candidates refined after a zmax > 0 search")
     ap.add_argument("--stream-speedup", type=float, default=50.0)
+    ap.add_argument("--fold-top", type=int, default=64, help="sifted candidates folded after the search (0: none)")
+    ap.add_argument("--single-pulse", type=int, default=None,
+                    help="1: also time the single-pulse search of every trial (default: 1 for the drift-scan workload)")
+    ap.add_argument("--subband", default=None,
+                    help="'nsub,group' of a two-stage plan searched beside the exact one, or 'none' "
+                         "(default: 16,16 for the drift-scan workload, none otherwise)")
     ap.add_argument("--dm-trials", type=int, default=None,
                     help="DM trials of a single-stage plan (driftscan/accel); smaller values make profiling cases")
     args = ap.parse_args()
+    if args.subband is None:
+        args.subband = "16,16" if args.workload == "driftscan" else "none"
+    if args.single_pulse is None:
+        args.single_pulse = 1 if args.workload == "driftscan" else 0
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -171,6 +171,33 @@ pss_status pss_ctx_profile_read(pss_ctx* ctx, double* ms, int64_t* launches);
  * Errors: PSS_EINVAL for nsamp <= D, empty stages, bad ds. */
 pss_status pss_dd_plan(const pss_fil_desc* fil, const pss_dd_stage* stages, int nstages,
                        pss_plan** out);
+/* A plan for two-stage (subband) dedispersion, the prepsubband scheme the
+ * paper calls faster than one prepdata run per DM (Sect. 5).  Same DM grid
+ * as pss_dd_plan; its dedispersion (pss_dedisperse and every search call
+ * given this plan) computes, with S = nchan / nsub channels per subband,
+ *   stage 1, per group g and subband b:
+ *     u_{g,b}[t] = sum over kept channels c of b of x[c][t + e_c(g)],
+ *     e_c(g) = round(((K*DM_g) * (1/(f_c*f_c) - 1/(f_b*f_b))) / tsamp),
+ *   stage 2, per trial i of group g:
+ *     s[t] = sum_b u_{g,b}[t + D_b(i)],
+ *     D_b(i) = round(((K*DM_i) * (1/(f_b*f_b) - 1/(f_ref*f_ref))) / tsamp),
+ * rounding halves away from zero, then the ds boxcar.  f_b is the highest
+ * centre frequency of subband b (channels [b*S, (b+1)*S)); groups are runs
+ * of `group` consecutive trials of one stage (the last may be shorter), and
+ * DM_g is the DM of a group's middle trial (index first + (n - 1) / 2).
+ * The plan's largest delay is D' = max(D, max over trials and channels of
+ * e_c(g) + D_b(i)), and N_v follows from D' as in pss_dd_plan.  The sums
+ * are exact integers; the scheme approximates each channel's delay (the
+ * error is the within-subband delay at DM_i - DM_g plus roundings).
+ * Errors: PSS_EINVAL as pss_dd_plan, or nsub not dividing nchan, or group
+ * outside [1, 1024].  pss_dedisperse_noalloc refuses such plans. */
+pss_status pss_dd_plan_subband(const pss_fil_desc* fil, const pss_dd_stage* stages, int nstages,
+                               int32_t nsub, int32_t group, pss_plan** out);
+/* The two-stage tables of a plan (nsub == 0 for an exact plan).  Nullable
+ * outputs: group_dm [ngroups] doubles; chan_delays [ngroups][nchan] int32
+ * (e_c(g), every channel); sub_delays [ndm][nsub] int32 (D_b(i)). */
+pss_status pss_plan_subband_info(const pss_plan* plan, int32_t* nsub, int32_t* group, int64_t* ngroups,
+                                 double* group_dm, int32_t* chan_delays, int32_t* sub_delays);
 /* ndm (total trials) and max_delay (D).  dms (nullable, host, ndm doubles)
  * receives the DM values; delays (nullable, host, ndm*nchan int32,
  * row-major [dm][channel], all channels including masked ones). */
@@ -220,6 +247,77 @@ pss_status pss_dedisperse(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc
 #define PSS_NOALLOC_SCRATCH_BYTES (32u << 20)
 pss_status pss_dedisperse_noalloc(const pss_plan* plan, const pss_fil_desc* fil, const void* data_dev,
                                   int64_t dm_begin, int64_t dm_end, int32_t* out, void* stream);
+
+/* ---- single-pulse search (Sect. 2 step 7, single_pulse_search.py) ------- */
+
+/* A single-pulse event: boxcar of `width` samples starting at sample t of
+ * DM trial dm_idx's dedispersed series (samples of the trial's ds), its
+ * exact integer sum and its S/N. */
+typedef struct {
+    int32_t dm_idx;
+    int32_t width;
+    int64_t t;
+    int64_t boxsum;
+    double snr;
+} pss_sp_event;
+
+/* Boxcar matched-filter search of the dedispersed series of DM trials
+ * [dm_begin, dm_end) (the paper ends its pipeline with a single-pulse
+ * search, Sect. 2 step 7; long-period pulsars are found that way, Sect.
+ * 5.3).  Per trial, with N = N_v, S1 = sum s, S2 = sum s^2 (exact):
+ *   mu = S1/N, sigma = sqrt((S2 - S1*S1/N)/N)                    (FP64, in that order)
+ *   B_w[t] = sum_{k<w} s[t+k], 0 <= t <= N - w                   (exact)
+ *   detection: B_w[t] >= w*mu + sigma_thr*sigma*sqrt(w), and B_w[t] >
+ *   B_w[t'] for t - w < t' < t, B_w[t] >= B_w[t'] for t < t' < t + w;
+ *   snr = (B_w[t] - w*mu) / (sigma*sqrt(w));
+ * then per trial the detections by snr (descending; ties: smaller width,
+ * then earlier) are kept when [t, t + w) overlaps none kept before.  A
+ * trial with sigma 0 has no events.  Works with exact and two-stage plans.
+ * widths: host array of nwidths (1..32) widths in [1, 1024].
+ * out: host array of cap events, sorted by (dm_idx, t).  n_out: the number
+ * of events; if it exceeds cap the call returns PSS_ECAP and writes
+ * nothing (call again with cap >= n_out).  Synchronises `stream`. */
+pss_status pss_single_pulse(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const void* data,
+                            int data_on_device, int64_t dm_begin, int64_t dm_end, const int32_t* widths,
+                            int32_t nwidths, double sigma_thr, pss_sp_event* out, int64_t cap, int64_t* n_out,
+                            void* stream);
+
+/* ---- folding (Sect. 2 step 6, prepfold) -------------------------------- */
+
+/* A candidate to fold: DM trial, frequency (Hz) and drift (Hz/s). */
+typedef struct {
+    int32_t dm_idx;
+    int32_t reserved;
+    double f_hz;
+    double fdot_hz_s;
+} pss_fold_req;
+
+/* Result of folding one candidate: the best trial frequency, its reduced
+ * chi-square and its index k in the trial grid. */
+typedef struct {
+    double f_hz;
+    double chi2_red;
+    int32_t best;
+    int32_t reserved;
+} pss_fold_result;
+
+/* Fold each candidate's exact dedispersed series (its DM trial; the paper
+ * folds sifted candidates with prepfold, Sect. 2 step 6).  Sample j is at
+ * t = j*dt, dt = ds*tsamp; at trial frequency
+ *   f_k = f + (k - (nfreq - 1)/2) * (step_bins / T),  k < nfreq,
+ * (T = nfft*ds*tsamp of the trial) its phase is phi = f_k*t + (0.5*fdot)*(t*t)
+ * and its bin min(floor((phi - floor(phi))*nbin), nbin - 1), FP64 in that
+ * order.  P_b / n_b: sum / number of the samples of bin b (exact).  With
+ * mu = S1/N, var = (S2 - S1*S1/N)/N of the series, chi2_red =
+ * sum over bins in order with n_b > 0 of d*d/(n_b*var), d = P_b - n_b*mu,
+ * divided by (those bins - 1); 0 when var is 0.  The result is the trial
+ * with the largest chi2_red (ties: smaller k).
+ * reqs: host [n]; nbin in [2, 1024]; nfreq in [1, 64].
+ * profiles, counts: host int64 [n][nbin] (the best trial's); results: host
+ * [n].  Works with exact and two-stage plans.  Synchronises `stream`. */
+pss_status pss_fold(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const void* data, int data_on_device,
+                    const pss_fold_req* reqs, int64_t n, int32_t nbin, int32_t nfreq, double step_bins,
+                    int64_t* profiles, int64_t* counts, pss_fold_result* results, void* stream);
 
 /* ---- spectra (Sect. 2 step 3, realfft) ---------------------------------- */
 

@@ -103,6 +103,25 @@ int64_t file_bytes(const pss_fil_desc* fil) {
     return (int64_t)(fil->nchan / 8) * fil->nsamp;
 }
 
+// Row pitch of the channel-major copy: the samples, one tile and the copy
+// slack past the end; for a two-stage plan also the furthest stage 1 can
+// read past the file (its rows run to N_v ds + the batch's largest D_b for
+// every subband; what it reads there never reaches an output).
+int64_t xcm_pitch(const Plan& plan, const pss_fil_desc* fil) {
+    int64_t extra = 0;
+    if (plan.nsub > 0) {
+        const int C = plan.nchan, nsub = plan.nsub;
+        for (int64_t i = 0; i < plan.ndm(); ++i) {
+            int32_t emax = 0, dmax = 0;
+            const int32_t* e = &plan.sub_e[(size_t)plan.grp_of[i] * C];
+            for (int c = 0; c < C; ++c) emax = std::max(emax, e[c]);
+            for (int b = 0; b < nsub; ++b) dmax = std::max(dmax, plan.sub_D[(size_t)i * nsub + b]);
+            extra = std::max<int64_t>(extra, (int64_t)emax + dmax - plan.max_delay);
+        }
+    }
+    return ((fil->nsamp + dedisp_tile_samples() + 256 + extra) + 63) / 64 * 64;
+}
+
 std::vector<int32_t> kept_channels(const pss_fil_desc* fil) {
     std::vector<int32_t> keep;
     for (int c = 0; c < fil->nchan; ++c)
@@ -121,21 +140,79 @@ std::vector<int32_t> compact_delays(const pss_plan* plan, const std::vector<int3
     return hd;
 }
 
+// Tables of the two-stage scheme for [dm_begin, dm_end), appended to the
+// keep list in ctx->delays_dev (offsets in int32 elements from its start):
+//   E   [groups][ck]   within-subband delays of the kept channels,
+//   D   [trials][nsub] subband delays,
+//   grp [groups]       (first trial - dm_begin, count),
+//   z   [nsub]         (first kept channel, kept channels) of each subband.
+struct SubTab {
+    bool on = false;
+    int64_t g_begin = 0;  // first group whose rows are uploaded
+    int64_t e_off = 0, d_off = 0, grp_off = 0, z_off = 0;
+    int32_t ckmax = 0;    // most kept channels in one subband
+    std::vector<int32_t> e_host;  // E as uploaded (host copy for launch sizing)
+};
+
+void subband_tables(const pss_plan* plan, const std::vector<int32_t>& keep, int64_t dm_begin, int64_t dm_end,
+                    std::vector<int32_t>* host, SubTab* T) {
+    const int32_t ck = (int32_t)keep.size();
+    const int nsub = plan->nsub, S = plan->sub_S, C = plan->nchan;
+    T->on = true;
+    T->g_begin = dm_end > dm_begin ? plan->grp_of[dm_begin] : 0;
+    const int64_t g_end = dm_end > dm_begin ? plan->grp_of[dm_end - 1] + 1 : T->g_begin;
+    const int64_t ng = g_end - T->g_begin, nt = dm_end - dm_begin;
+    // int2 tables (grp, z) start on 8-byte boundaries: every offset is kept a multiple of 4 elements
+    auto up4 = [](int64_t v) { return (v + 3) & ~int64_t(3); };
+    T->e_off = up4(ck);
+    T->d_off = up4(T->e_off + ng * ck);
+    T->grp_off = up4(T->d_off + nt * nsub);
+    T->z_off = up4(T->grp_off + 2 * ng);
+    host->assign((size_t)(T->z_off + 2 * nsub), 0);
+    int32_t* h = host->data();
+    for (int32_t r = 0; r < ck; ++r) h[r] = keep[r];
+    for (int64_t g = 0; g < ng; ++g)
+        for (int32_t r = 0; r < ck; ++r) h[T->e_off + g * ck + r] = plan->sub_e[(size_t)(T->g_begin + g) * C + keep[r]];
+    for (int64_t i = 0; i < nt; ++i)
+        for (int b = 0; b < nsub; ++b) h[T->d_off + i * nsub + b] = plan->sub_D[(size_t)(dm_begin + i) * nsub + b];
+    for (int64_t g = 0; g < ng; ++g) {
+        h[T->grp_off + 2 * g] = (int32_t)(plan->grp_first[T->g_begin + g] - dm_begin);
+        h[T->grp_off + 2 * g + 1] = plan->grp_n[T->g_begin + g];
+    }
+    T->ckmax = 0;
+    int32_t r = 0;
+    for (int b = 0; b < nsub; ++b) {
+        const int32_t first = r;
+        while (r < ck && keep[r] < (b + 1) * S) ++r;
+        h[T->z_off + 2 * b] = first;
+        h[T->z_off + 2 * b + 1] = r - first;
+        T->ckmax = std::max(T->ckmax, r - first);
+    }
+    T->e_host.assign(h + T->e_off, h + T->e_off + ng * ck);
+}
+
 // Host-side set-up for a file: the kept channels, their delays for
-// [dm_begin, dm_end) uploaded to ctx->delays_dev, and the channel-major
-// buffer.  Synchronises `s` (the delay upload reads a host vector).
+// [dm_begin, dm_end) (or the two-stage tables, `T`) uploaded to
+// ctx->delays_dev, and the channel-major buffer.  Synchronises `s` (the
+// delay upload reads a host vector).
 pss_status setup_input(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, int64_t dm_begin,
-                       int64_t dm_end, cudaStream_t s, int32_t* ck_out, int64_t* pitch_out) {
+                       int64_t dm_end, cudaStream_t s, int32_t* ck_out, int64_t* pitch_out, SubTab* T = nullptr) {
     const std::vector<int32_t> keep = kept_channels(fil);
     const int32_t ck = (int32_t)keep.size();
     if (ck == 0) return fail(PSS_EINVAL, "channel mask removes every channel");
-    const int TN = dedisp_tile_samples();
-    const int64_t pitch = ((fil->nsamp + TN + 256) + 63) / 64 * 64;
-    // keep list + compacted delays in one upload
-    const std::vector<int32_t> hd = compact_delays(plan, keep, dm_begin, dm_end);
-    std::vector<int32_t> host((size_t)ck + hd.size());
-    memcpy(host.data(), keep.data(), sizeof(int32_t) * ck);
-    if (!hd.empty()) memcpy(host.data() + ck, hd.data(), sizeof(int32_t) * hd.size());
+    const int64_t pitch = xcm_pitch(*plan, fil);
+    std::vector<int32_t> host;
+    if (plan->nsub > 0) {
+        if (!T) return fail(PSS_EINVAL, "internal: two-stage plan without its tables");
+        subband_tables(plan, keep, dm_begin, dm_end, &host, T);
+    } else {
+        // keep list + compacted delays in one upload
+        const std::vector<int32_t> hd = compact_delays(plan, keep, dm_begin, dm_end);
+        host.resize((size_t)ck + hd.size());
+        memcpy(host.data(), keep.data(), sizeof(int32_t) * ck);
+        if (!hd.empty()) memcpy(host.data() + ck, hd.data(), sizeof(int32_t) * hd.size());
+        if (T) T->on = false;
+    }
     // the same tables as the last call (same plan, mask and trials) need no upload and no wait
     const void* before = ctx->delays_dev.p;
     PSS_TRY(ctx->delays_dev.ensure(host.size() * sizeof(int32_t)));
@@ -192,8 +269,8 @@ pss_status enqueue_prep(pss_ctx* ctx, const pss_fil_desc* fil, const uint8_t* sr
 // Old entry used by pss_dedisperse: set-up, upload and unpack in one go.
 pss_status stage_input(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const void* data,
                        int on_device, int64_t dm_begin, int64_t dm_end, cudaStream_t s, int32_t* ck_out,
-                       int64_t* pitch_out) {
-    PSS_TRY(setup_input(ctx, plan, fil, dm_begin, dm_end, s, ck_out, pitch_out));
+                       int64_t* pitch_out, SubTab* T) {
+    PSS_TRY(setup_input(ctx, plan, fil, dm_begin, dm_end, s, ck_out, pitch_out, T));
     const uint8_t* src = nullptr;
     PSS_TRY(upload_input(ctx, fil, data, on_device, s, &src));
     return enqueue_prep(ctx, fil, src, *ck_out, *pitch_out, s);
@@ -216,6 +293,185 @@ int32_t delay_spread(const int32_t* d, int64_t nb, int32_t ck) {
         }
     }
     return sp;
+}
+
+// Launch sizes of one two-stage batch: trials [b0, b0 + nb) of a stage.
+struct SubBatch {
+    int64_t g_lo = 0;     // first group touched (global index)
+    int32_t ngb = 0;      // groups touched
+    int64_t len1 = 0;     // stage-1 samples per row: N_v ds + the batch's largest D
+    int64_t stride1 = 0;  // row stride of the stage-1 buffer
+    int32_t spread1 = 0;  // stage 1: within-subband delay spread over rows of 16 groups
+    int32_t spread2 = 0;  // stage 2: subband delay spread within a group
+};
+
+SubBatch sub_batch(const pss_plan* plan, const SubTab& T, int32_t ck, int64_t dm_begin, int64_t b0, int32_t nb,
+                   int64_t nv, int32_t ds) {
+    SubBatch B;
+    const int nsub = plan->nsub;
+    B.g_lo = plan->grp_of[b0];
+    B.ngb = (int32_t)(plan->grp_of[b0 + nb - 1] - B.g_lo + 1);
+    int32_t dmax = 0;
+    for (int64_t i = b0; i < b0 + nb; ++i)
+        for (int b = 0; b < nsub; ++b) dmax = std::max(dmax, plan->sub_D[(size_t)i * nsub + b]);
+    B.len1 = nv * ds + dmax;
+    B.stride1 = (B.len1 + 3) & ~int64_t(3);
+    const int G = dedisp_group_trials();
+    const int32_t* e = T.e_host.data() + (B.g_lo - T.g_begin) * ck;
+    for (int32_t g = 0; g < B.ngb; g += G) {
+        const int32_t ge = std::min<int32_t>(B.ngb, g + G);
+        for (int32_t c = 0; c < ck; ++c) {
+            int32_t lo = e[(int64_t)g * ck + c], hi = lo;
+            for (int32_t k = g + 1; k < ge; ++k) {
+                lo = std::min(lo, e[(int64_t)k * ck + c]);
+                hi = std::max(hi, e[(int64_t)k * ck + c]);
+            }
+            B.spread1 = std::max(B.spread1, hi - lo);
+        }
+    }
+    for (int64_t g = B.g_lo; g < B.g_lo + B.ngb; ++g) {
+        const int64_t lo = std::max<int64_t>(b0, plan->grp_first[g]);
+        const int64_t hi = std::min<int64_t>(b0 + nb, plan->grp_first[g] + plan->grp_n[g]);
+        for (int b = 0; b < nsub; ++b) {
+            int32_t mn = INT32_MAX, mx = INT32_MIN;
+            for (int64_t i = lo; i < hi; ++i) {
+                mn = std::min(mn, plan->sub_D[(size_t)i * nsub + b]);
+                mx = std::max(mx, plan->sub_D[(size_t)i * nsub + b]);
+            }
+            if (hi > lo) B.spread2 = std::max(B.spread2, mx - mn);
+        }
+    }
+    (void)dm_begin;
+    return B;
+}
+
+// Dedisperse trials [b0, b0 + nb) of one stage into rows of out_stride
+// (float out_f with per-trial sums, or int32 out_i): the exact kernel, or,
+// for a two-stage plan, stage 1 into `subu` and stage 2 from it.  `spread`
+// is the exact kernel's delay spread; `SB` the two-stage launch sizes.
+pss_status enqueue_dedisp(pss_ctx* ctx, const pss_plan* plan, int32_t ck, int64_t pitch, const SubTab& T,
+                          const StageInfo& st, int64_t dm_begin, int64_t b0, int32_t nb, int32_t spread,
+                          const SubBatch& SB, void* subu, float* out_f, int32_t* out_i, int64_t out_stride,
+                          unsigned long long* sums, cudaStream_t s) {
+    const int32_t* base = (const int32_t*)ctx->delays_dev.p;
+    if (!T.on) {
+        DedispArgs da{};
+        da.xcm = (const uint8_t*)ctx->xcm.p;
+        da.pitch = pitch;
+        da.ck = ck;
+        da.delays = base + ck + (b0 - dm_begin) * ck;
+        da.nb = nb;
+        da.nv = st.nv;
+        da.ds = st.ds;
+        da.out_f = out_f;
+        da.out_i = out_i;
+        da.out_stride = out_stride;
+        da.sums = sums;
+        da.spread = spread;
+        da.err = (int*)ctx->errflag.p;
+        da.chunk_kb = ctx->tune.dedisp_kb;
+        ProfScope ps(ctx, 1, s);
+        PSS_CUDA(launch_dedisp(da, ctx->num_sms, s));
+        return PSS_OK;
+    }
+    ProfScope ps(ctx, 1, s);
+    DedispArgs da{};
+    da.xcm = (const uint8_t*)ctx->xcm.p;
+    da.pitch = pitch;
+    da.ck = std::max<int32_t>(T.ckmax, 1);
+    da.delays = base + T.e_off + (SB.g_lo - T.g_begin) * ck;
+    da.dstride = ck;
+    da.zsub = (const int2*)(base + T.z_off);
+    da.nz = plan->nsub;
+    da.nb = SB.ngb;
+    da.nv = SB.len1;
+    da.ds = 1;
+    da.out_f = nullptr;
+    da.out_i = (int32_t*)subu;
+    da.out_stride = SB.stride1;
+    da.zout = (int64_t)SB.ngb * SB.stride1;
+    da.sums = nullptr;
+    da.spread = SB.spread1;
+    da.err = (int*)ctx->errflag.p;
+    da.chunk_kb = ctx->tune.dedisp_kb;
+    PSS_CUDA(launch_dedisp(da, ctx->num_sms, s));
+    SubsumArgs sa{};
+    sa.u = (const int32_t*)subu;
+    sa.u_zstride = (int64_t)SB.ngb * SB.stride1;
+    sa.u_rowstride = SB.stride1;
+    sa.u_len = SB.len1;
+    sa.nsub = plan->nsub;
+    sa.D = base + T.d_off + (b0 - dm_begin) * plan->nsub;
+    // group rows relative to the batch: (first - b0, count)
+    sa.grp = (const int2*)(base + T.grp_off) + (SB.g_lo - T.g_begin);
+    sa.ngrp = SB.ngb;
+    sa.nb = nb;
+    sa.nv = st.nv;
+    sa.ds = st.ds;
+    sa.out_f = out_f;
+    sa.out_i = out_i;
+    sa.out_stride = out_stride;
+    sa.sums = sums;
+    sa.spread = SB.spread2;
+    sa.b0rel = (int32_t)(b0 - dm_begin);
+    PSS_CUDA(launch_subsum(sa, s));
+    return PSS_OK;
+}
+
+// Single-pulse events from raw detections: S/N = (B - w mu)/(sigma sqrt(w))
+// with mu, sigma from the trial's exact moments (FP64, the order of the
+// detection kernel); per trial, the detections by S/N (descending; ties:
+// smaller width, then earlier) are kept when their interval [t, t + w)
+// overlaps none kept before.  Output sorted by (trial, t).
+void sp_prune(std::vector<SpRaw>& raw, const std::vector<unsigned long long>& mom, int64_t dm_begin, int64_t dm_end,
+              const pss_plan* plan, std::vector<pss_sp_event>* out) {
+    std::sort(raw.begin(), raw.end(), [](const SpRaw& a, const SpRaw& b) {
+        return a.dm_idx != b.dm_idx ? a.dm_idx < b.dm_idx : (a.w != b.w ? a.w < b.w : a.t < b.t);
+    });
+    const int64_t nt = dm_end - dm_begin;
+    std::vector<size_t> start(nt + 1, raw.size());
+    for (size_t i = raw.size(); i-- > 0;) start[raw[i].dm_idx - dm_begin] = i;
+    for (int64_t i = nt - 1; i >= 0; --i) start[i] = std::min(start[i], start[i + 1]);
+    std::vector<std::vector<pss_sp_event>> per(nt);
+    parallel_for_fn(nt, 8, [&](int64_t i) {
+        const size_t a = start[i], b = start[i + 1];
+        if (a == b) return;
+        const double fS1 = (double)mom[2 * i], fS2 = (double)mom[2 * i + 1];
+        const double fN = (double)plan->stages[plan->stage_of[dm_begin + i]].nv;
+        const double mu = fS1 / fN;
+        double var = (fS2 - fS1 * fS1 / fN) / fN;
+        if (!(var > 0.0)) var = 0.0;
+        const double sigma = sqrt(var);
+        std::vector<pss_sp_event> ev;
+        for (size_t k = a; k < b; ++k) {
+            pss_sp_event e;
+            e.dm_idx = raw[k].dm_idx;
+            e.width = raw[k].w;
+            e.t = raw[k].t;
+            e.boxsum = raw[k].B;
+            const double w = (double)raw[k].w;
+            e.snr = ((double)raw[k].B - w * mu) / (sigma * sqrt(w));
+            ev.push_back(e);
+        }
+        std::sort(ev.begin(), ev.end(), [](const pss_sp_event& x, const pss_sp_event& y) {
+            if (x.snr != y.snr) return x.snr > y.snr;
+            if (x.width != y.width) return x.width < y.width;
+            return x.t < y.t;
+        });
+        std::map<int64_t, int64_t> kept;  // start -> end (exclusive), disjoint
+        std::vector<pss_sp_event> keep;
+        for (const auto& e : ev) {
+            const int64_t s0 = e.t, s1 = e.t + e.width;
+            auto it = kept.lower_bound(s0);
+            if (it != kept.end() && it->first < s1) continue;
+            if (it != kept.begin() && std::prev(it)->second > s0) continue;
+            kept.emplace(s0, s1);
+            keep.push_back(e);
+        }
+        std::sort(keep.begin(), keep.end(), [](const pss_sp_event& x, const pss_sp_event& y) { return x.t < y.t; });
+        per[i].swap(keep);
+    });
+    for (auto& v : per) out->insert(out->end(), v.begin(), v.end());
 }
 
 enum Mode { MODE_SPECTRUM, MODE_PLANE, MODE_SEARCH, MODE_GAINS };
@@ -361,12 +617,14 @@ struct BatchDesc {
     int32_t nb;        // trials
     int32_t spread;    // delay spread the dedispersion launch is sized for
     int64_t out_off;   // packed output offset (spectrum / plane modes)
+    SubBatch sub;      // two-stage launch sizes
 };
 
 // Everything the kernel sequence needs, computed on the host once.
 struct PathSetup {
     int32_t ck = 0;
     int64_t pitch = 0;
+    SubTab sub;  // two-stage tables (sub.on false: exact dedispersion)
     int nz = 1, Z = 0, nstages = 1;
     std::vector<BatchDesc> batches;
     std::vector<HarmArgs> harm;  // per stage: thresholds and f_lo cuts
@@ -391,7 +649,7 @@ int64_t batch_trials(int64_t nfft, int nz, Mode mode, int64_t n) {
 pss_status setup_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const pss_search_cfg* cfg,
                       int64_t dm_begin, int64_t dm_end, Mode mode, cudaStream_t s, int64_t dev_cap, PathSetup* P,
                       int64_t max_b = 0) {
-    PSS_TRY(setup_input(ctx, plan, fil, dm_begin, dm_end, s, &P->ck, &P->pitch));
+    PSS_TRY(setup_input(ctx, plan, fil, dm_begin, dm_end, s, &P->ck, &P->pitch, &P->sub));
     P->batches.clear();
     P->harm.clear();
     P->dev_cap = dev_cap;
@@ -400,7 +658,8 @@ pss_status setup_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fi
     P->nz = nz_of(cfg);
     P->Z = cfg->zmax ? (int)llround(cfg->zmax / cfg->dz) : 0;
     P->nstages = (int)log2((double)cfg->numharm) + 1;
-    const std::vector<int32_t> hd = compact_delays(plan, kept_channels(fil), dm_begin, dm_end);
+    const std::vector<int32_t> hd =
+        P->sub.on ? std::vector<int32_t>() : compact_delays(plan, kept_channels(fil), dm_begin, dm_end);
     if (mode == MODE_SEARCH) {
         PSS_TRY(ctx->cands.ensure((size_t)dev_cap * sizeof(pss_raw_cand)));
         PSS_TRY(ctx->counter.ensure(sizeof(unsigned long long)));
@@ -415,7 +674,7 @@ pss_status setup_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fi
     }
     for (const auto& st : plan->stages)
         if (st.n_dm > 0) PSS_TRY(ensure_passtw(ctx, st.nfft / 2, ctx->tune.fft_variant, s));
-    size_t need_series = 0, need_fft = 0, need_sums = 0, need_plane = 0;
+    size_t need_series = 0, need_fft = 0, need_sums = 0, need_plane = 0, need_subu = 0;
     int64_t out_off = 0;
     for (size_t si = 0; si < plan->stages.size(); ++si) {
         const StageInfo& st = plan->stages[si];
@@ -433,6 +692,8 @@ pss_status setup_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fi
         const int64_t nfft = st.nfft, M = nfft / 2;
         int64_t B = batch_trials(nfft, P->nz, mode, hi - lo);
         if (max_b > 0) B = std::min(B, max_b);
+        // two-stage plans: whole groups per batch where possible
+        if (P->sub.on && B > plan->sub_group) B = B / plan->sub_group * plan->sub_group;
         need_series = std::max(need_series, (size_t)B * nfft * 4);
         need_sums = std::max(need_sums, (size_t)B * 8);
         need_fft = std::max(need_fft, (size_t)B * M * 8);
@@ -442,13 +703,20 @@ pss_status setup_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fi
             d.stage = (int32_t)si;
             d.b0 = b0;
             d.nb = (int32_t)std::min<int64_t>(B, hi - b0);
-            d.spread = delay_spread(hd.data() + (size_t)(b0 - dm_begin) * P->ck, d.nb, P->ck);
+            if (P->sub.on) {
+                d.spread = 0;
+                d.sub = sub_batch(plan, P->sub, P->ck, dm_begin, b0, d.nb, st.nv, st.ds);
+                need_subu = std::max(need_subu, (size_t)plan->nsub * d.sub.ngb * d.sub.stride1 * 4);
+            } else {
+                d.spread = delay_spread(hd.data() + (size_t)(b0 - dm_begin) * P->ck, d.nb, P->ck);
+            }
             d.out_off = out_off;
             out_off += (mode == MODE_SPECTRUM) ? (int64_t)d.nb * M : (mode == MODE_PLANE) ? (int64_t)d.nb * P->nz * nfft : 0;
             P->batches.push_back(d);
         }
     }
     PSS_TRY(ctx->series.ensure(need_series));
+    if (need_subu) PSS_TRY(ctx->subu.ensure(need_subu));
     PSS_TRY(ctx->sums.ensure(need_sums));
     PSS_TRY(ctx->fftA.ensure(need_fft));
     PSS_TRY(ctx->fftB.ensure(need_fft));
@@ -464,31 +732,14 @@ pss_status enqueue_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* 
                         cudaStream_t s, bool snapshots = false) {
     PSS_TRY(enqueue_prep(ctx, fil, src, P.ck, P.pitch, s));
     if (P.batches.empty()) return PSS_OK;
-    const int32_t* dtab = (const int32_t*)ctx->delays_dev.p + P.ck;
     if (mode == MODE_SEARCH) PSS_CUDA(cudaMemsetAsync(ctx->counter.p, 0, sizeof(unsigned long long), s));
     for (const BatchDesc& d : P.batches) {
         const StageInfo& st = plan->stages[d.stage];
         const int64_t nfft = st.nfft, M = nfft / 2;
-        DedispArgs da{};
-        da.xcm = (const uint8_t*)ctx->xcm.p;
-        da.pitch = P.pitch;
-        da.ck = P.ck;
-        da.delays = dtab + (d.b0 - dm_begin) * P.ck;
-        da.nb = d.nb;
-        da.nv = st.nv;
-        da.ds = st.ds;
-        da.out_f = (float*)ctx->series.p;
-        da.out_i = nullptr;
-        da.out_stride = nfft;
-        da.sums = (unsigned long long*)ctx->sums.p;
-        da.spread = d.spread;
-        da.err = (int*)ctx->errflag.p;
-        da.chunk_kb = ctx->tune.dedisp_kb;
         PSS_CUDA(cudaMemsetAsync(ctx->sums.p, 0, (size_t)d.nb * 8, s));
-        {
-            ProfScope ps(ctx, 1, s);
-            PSS_CUDA(launch_dedisp(da, ctx->num_sms, s));
-        }
+        PSS_TRY(enqueue_dedisp(ctx, plan, P.ck, P.pitch, P.sub, st, dm_begin, d.b0, d.nb, d.spread, d.sub,
+                               ctx->subu.p, (float*)ctx->series.p, nullptr, nfft,
+                               (unsigned long long*)ctx->sums.p, s));
         const bool fused = (mode == MODE_SEARCH || mode == MODE_PLANE) && cfg->zmax == 0 && nfft == (int64_t(1) << 18) &&
                            cfg->whiten_block == 1024 && cfg->halfwidth_extra == 16 && ctx->tune.fused &&
                            spec_cluster_usable();
@@ -822,7 +1073,8 @@ void pss_ctx_destroy(pss_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
-    DevBuf* bufs[] = {&c->fil_dev, &c->xcm, &c->delays_dev, &c->series, &c->sums, &c->fftA, &c->fftB,
+    DevBuf* bufs[] = {&c->fil_dev, &c->xcm, &c->delays_dev, &c->subu, &c->sp_series, &c->sp_mom, &c->sp_ev,
+                      &c->fold_buf, &c->series, &c->sums, &c->fftA, &c->fftB,
                       &c->spec, &c->plane, &c->cands, &c->counter, &c->taps, &c->ftaps, &c->tapinfo, &c->errflag,
                       &c->twid, &c->chan_spec, &c->refine_gains, &c->refine_dtau, &c->refine_pts, &c->refine_out};
     for (DevBuf* b : bufs) b->release();
@@ -885,6 +1137,33 @@ pss_status pss_dd_plan(const pss_fil_desc* fil, const pss_dd_stage* stages, int 
     return PSS_OK;
 }
 
+pss_status pss_dd_plan_subband(const pss_fil_desc* fil, const pss_dd_stage* stages, int nstages, int32_t nsub,
+                               int32_t group, pss_plan** out) {
+    if (!out) return fail(PSS_EINVAL, "pss_dd_plan_subband: null out");
+    *out = nullptr;
+    pss_plan* p = new pss_plan();
+    pss_status st = build_plan(fil, stages, nstages, p);
+    if (st == PSS_OK) st = build_subband(p, nsub, group);
+    if (st != PSS_OK) {
+        delete p;
+        return st;
+    }
+    *out = p;
+    return PSS_OK;
+}
+
+pss_status pss_plan_subband_info(const pss_plan* plan, int32_t* nsub, int32_t* group, int64_t* ngroups,
+                                 double* group_dm, int32_t* chan_delays, int32_t* sub_delays) {
+    if (!plan) return fail(PSS_EINVAL, "pss_plan_subband_info: null plan");
+    if (nsub) *nsub = plan->nsub;
+    if (group) *group = plan->sub_group;
+    if (ngroups) *ngroups = (int64_t)plan->grp_first.size();
+    if (group_dm) memcpy(group_dm, plan->grp_dm.data(), sizeof(double) * plan->grp_dm.size());
+    if (chan_delays) memcpy(chan_delays, plan->sub_e.data(), sizeof(int32_t) * plan->sub_e.size());
+    if (sub_delays) memcpy(sub_delays, plan->sub_D.data(), sizeof(int32_t) * plan->sub_D.size());
+    return PSS_OK;
+}
+
 pss_status pss_plan_info(const pss_plan* plan, int64_t* ndm, int64_t* max_delay, double* dms, int32_t* delays) {
     if (!plan) return fail(PSS_EINVAL, "pss_plan_info: null plan");
     if (ndm) *ndm = plan->ndm();
@@ -917,37 +1196,288 @@ pss_status pss_dedisperse(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc
     cudaStream_t s = pick_stream(ctx, stream);
     int32_t ck = 0;
     int64_t pitch = 0;
-    PSS_TRY(stage_input(ctx, plan, fil, data, data_on_device, dm_begin, dm_end, s, &ck, &pitch));
-    const int32_t* dtab = (const int32_t*)ctx->delays_dev.p + ck;
-    const std::vector<int32_t> hd = compact_delays(plan, kept_channels(fil), dm_begin, dm_end);
+    SubTab T;
+    PSS_TRY(stage_input(ctx, plan, fil, data, data_on_device, dm_begin, dm_end, s, &ck, &pitch, &T));
+    const std::vector<int32_t> hd = T.on ? std::vector<int32_t>() : compact_delays(plan, kept_channels(fil), dm_begin, dm_end);
     int64_t off = 0;
     for (size_t si = 0; si < plan->stages.size(); ++si) {
         const StageInfo& st = plan->stages[si];
         const int64_t lo = std::max<int64_t>(dm_begin, st.first);
         const int64_t hi = std::min<int64_t>(dm_end, st.first + st.n_dm);
         if (lo >= hi) continue;
-        for (int64_t b0 = lo; b0 < hi; b0 += 1024) {
-            const int32_t nb = (int32_t)std::min<int64_t>(1024, hi - b0);
-            DedispArgs da{};
-            da.xcm = (const uint8_t*)ctx->xcm.p;
-            da.pitch = pitch;
-            da.ck = ck;
-            da.delays = dtab + (b0 - dm_begin) * ck;
-            da.nb = nb;
-            da.nv = st.nv;
-            da.ds = st.ds;
-            da.out_f = nullptr;
-            da.out_i = out + off;
-            da.out_stride = st.nv;
-            da.sums = nullptr;
-            da.spread = delay_spread(hd.data() + (size_t)(b0 - dm_begin) * ck, nb, ck);
-            da.err = (int*)ctx->errflag.p;
-            {
-                ProfScope ps(ctx, 1, s);
-                PSS_CUDA(launch_dedisp(da, ctx->num_sms, s));
+        int64_t B = 1024;
+        if (T.on) B = std::max<int64_t>(1, std::min<int64_t>(B, 256 / plan->sub_group) * plan->sub_group);
+        for (int64_t b0 = lo; b0 < hi; b0 += B) {
+            const int32_t nb = (int32_t)std::min<int64_t>(B, hi - b0);
+            int32_t spread = 0;
+            SubBatch SB;
+            if (T.on) {
+                SB = sub_batch(plan, T, ck, dm_begin, b0, nb, st.nv, st.ds);
+                PSS_TRY(ctx->subu.ensure((size_t)plan->nsub * SB.ngb * SB.stride1 * 4));
+            } else {
+                spread = delay_spread(hd.data() + (size_t)(b0 - dm_begin) * ck, nb, ck);
             }
+            PSS_TRY(enqueue_dedisp(ctx, plan, ck, pitch, T, st, dm_begin, b0, nb, spread, SB, ctx->subu.p, nullptr,
+                                   out + off, st.nv, nullptr, s));
             off += (int64_t)nb * st.nv;
         }
+    }
+    return PSS_OK;
+}
+
+pss_status pss_single_pulse(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const void* data,
+                            int data_on_device, int64_t dm_begin, int64_t dm_end, const int32_t* widths,
+                            int32_t nwidths, double sigma_thr, pss_sp_event* out, int64_t cap, int64_t* n_out,
+                            void* stream) {
+    if (!n_out) return fail(PSS_EINVAL, "pss_single_pulse: null n_out");
+    *n_out = 0;
+    PSS_TRY(check_common(ctx, plan, fil, data, dm_begin, dm_end));
+    if (!widths || nwidths < 1 || nwidths > SP_MAXW)
+        return fail(PSS_EINVAL, "pss_single_pulse: 1 to 32 widths are required");
+    int32_t wmax = 0;
+    for (int i = 0; i < nwidths; ++i) {
+        if (widths[i] < 1 || widths[i] > SP_MAXWIDTH) return fail(PSS_EINVAL, "pss_single_pulse: widths must be in [1, 1024]");
+        wmax = std::max(wmax, widths[i]);
+    }
+    if (!std::isfinite(sigma_thr)) return fail(PSS_EINVAL, "pss_single_pulse: sigma_thr must be finite");
+    if (!out && cap > 0) return fail(PSS_EINVAL, "pss_single_pulse: null out");
+    PSS_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = pick_stream(ctx, stream);
+    int32_t ck = 0;
+    int64_t pitch = 0;
+    SubTab T;
+    PSS_TRY(stage_input(ctx, plan, fil, data, data_on_device, dm_begin, dm_end, s, &ck, &pitch, &T));
+    const std::vector<int32_t> hd = T.on ? std::vector<int32_t>() : compact_delays(plan, kept_channels(fil), dm_begin, dm_end);
+    PSS_TRY(ctx->counter.ensure(sizeof(unsigned long long)));
+    int64_t devcap = std::max<int64_t>((int64_t)ctx->sp_ev.bytes / (int64_t)sizeof(SpRaw), 1 << 16);
+    PSS_TRY(ctx->sp_ev.ensure((size_t)devcap * sizeof(SpRaw)));
+    std::vector<SpRaw> raw;
+    std::vector<unsigned long long> mom_all((size_t)2 * (dm_end - dm_begin));
+    for (size_t si = 0; si < plan->stages.size(); ++si) {
+        const StageInfo& st = plan->stages[si];
+        const int64_t lo = std::max<int64_t>(dm_begin, st.first);
+        const int64_t hi = std::min<int64_t>(dm_end, st.first + st.n_dm);
+        if (lo >= hi) continue;
+        // trials per batch: up to 1 GiB of int32 series, whole groups for two-stage plans
+        int64_t B = std::max<int64_t>(1, std::min<int64_t>(1024, ((int64_t)1 << 28) / st.nv));
+        if (T.on && B > plan->sub_group) B = B / plan->sub_group * plan->sub_group;
+        PSS_TRY(ctx->sp_series.ensure((size_t)std::min<int64_t>(B, hi - lo) * st.nv * sizeof(int32_t)));
+        PSS_TRY(ctx->sp_mom.ensure((size_t)2 * std::min<int64_t>(B, hi - lo) * sizeof(unsigned long long)));
+        for (int64_t b0 = lo; b0 < hi; b0 += B) {
+            const int32_t nb = (int32_t)std::min<int64_t>(B, hi - b0);
+            int32_t spread = 0;
+            SubBatch SB;
+            if (T.on) {
+                SB = sub_batch(plan, T, ck, dm_begin, b0, nb, st.nv, st.ds);
+                PSS_TRY(ctx->subu.ensure((size_t)plan->nsub * SB.ngb * SB.stride1 * 4));
+            } else {
+                spread = delay_spread(hd.data() + (size_t)(b0 - dm_begin) * ck, nb, ck);
+            }
+            int32_t* ser = (int32_t*)ctx->sp_series.p;
+            PSS_TRY(enqueue_dedisp(ctx, plan, ck, pitch, T, st, dm_begin, b0, nb, spread, SB, ctx->subu.p, nullptr,
+                                   ser, st.nv, nullptr, s));
+            unsigned long long* m1 = (unsigned long long*)ctx->sp_mom.p;
+            unsigned long long* m2 = m1 + nb;
+            PSS_CUDA(cudaMemsetAsync(m1, 0, (size_t)2 * nb * sizeof(unsigned long long), s));
+            PSS_CUDA(cudaMemsetAsync(ctx->counter.p, 0, sizeof(unsigned long long), s));
+            SpArgs sa{};
+            sa.series = ser;
+            sa.stride = st.nv;
+            sa.n = st.nv;
+            sa.nb = nb;
+            sa.dm0 = (int32_t)b0;
+            for (int i = 0; i < nwidths; ++i) sa.w[i] = widths[i];
+            sa.nw = nwidths;
+            sa.wmax = wmax;
+            sa.thr = sigma_thr;
+            sa.s1 = m1;
+            sa.s2 = m2;
+            sa.out = (SpRaw*)ctx->sp_ev.p;
+            sa.count = (unsigned long long*)ctx->counter.p;
+            sa.cap = devcap;
+            PSS_CUDA(launch_single_pulse(sa, m1, m2, s));
+            unsigned long long cnt = 0;
+            PSS_CUDA(cudaMemcpyAsync(&cnt, ctx->counter.p, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+            PSS_CUDA(cudaStreamSynchronize(s));
+            PSS_TRY(check_errflag(ctx, s));
+            if ((int64_t)cnt > devcap) {
+                // grow and detect again (the series and moments are still on the device)
+                devcap = (int64_t)cnt + cnt / 4;
+                PSS_TRY(ctx->sp_ev.ensure((size_t)devcap * sizeof(SpRaw)));
+                sa.out = (SpRaw*)ctx->sp_ev.p;
+                sa.cap = devcap;
+                PSS_CUDA(cudaMemsetAsync(ctx->counter.p, 0, sizeof(unsigned long long), s));
+                PSS_CUDA(launch_sp_detect_only(sa, s));
+                PSS_CUDA(cudaMemcpyAsync(&cnt, ctx->counter.p, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+                PSS_CUDA(cudaStreamSynchronize(s));
+            }
+            const size_t r0 = raw.size();
+            raw.resize(r0 + (size_t)cnt);
+            if (cnt)
+                PSS_CUDA(cudaMemcpyAsync(raw.data() + r0, ctx->sp_ev.p, (size_t)cnt * sizeof(SpRaw),
+                                         cudaMemcpyDeviceToHost, s));
+            PSS_CUDA(cudaMemcpyAsync(mom_all.data() + 2 * (b0 - dm_begin), m1, (size_t)nb * sizeof(unsigned long long),
+                                     cudaMemcpyDeviceToHost, s));
+            PSS_CUDA(cudaMemcpyAsync(mom_all.data() + 2 * (b0 - dm_begin) + nb, m2, (size_t)nb * sizeof(unsigned long long),
+                                     cudaMemcpyDeviceToHost, s));
+            PSS_CUDA(cudaStreamSynchronize(s));
+            // moments were stored as [S1 of the batch][S2 of the batch]; reorder to per-trial pairs below
+            std::vector<unsigned long long> tmp(mom_all.begin() + 2 * (b0 - dm_begin),
+                                                mom_all.begin() + 2 * (b0 - dm_begin) + 2 * nb);
+            for (int32_t i = 0; i < nb; ++i) {
+                mom_all[2 * (b0 - dm_begin + i)] = tmp[i];
+                mom_all[2 * (b0 - dm_begin + i) + 1] = tmp[nb + i];
+            }
+        }
+    }
+    // host: S/N in FP64 and greedy pruning per trial, in the oracle's order
+    std::vector<pss_sp_event> events;
+    sp_prune(raw, mom_all, dm_begin, dm_end, plan, &events);
+    *n_out = (int64_t)events.size();
+    if ((int64_t)events.size() > cap) return fail(PSS_ECAP, "pss_single_pulse: more events than cap (n_out holds the count)");
+    if (!events.empty()) memcpy(out, events.data(), events.size() * sizeof(pss_sp_event));
+    return PSS_OK;
+}
+
+pss_status pss_fold(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const void* data, int data_on_device,
+                    const pss_fold_req* reqs, int64_t n, int32_t nbin, int32_t nfreq, double step_bins,
+                    int64_t* profiles, int64_t* counts, pss_fold_result* results, void* stream) {
+    if (n < 0 || (n > 0 && (!reqs || !profiles || !counts || !results)))
+        return fail(PSS_EINVAL, "pss_fold: null argument");
+    if (nbin < 2 || nbin > 1024) return fail(PSS_EINVAL, "pss_fold: nbin must be in [2, 1024]");
+    if (nfreq < 1 || nfreq > 64) return fail(PSS_EINVAL, "pss_fold: nfreq must be in [1, 64]");
+    if (!std::isfinite(step_bins)) return fail(PSS_EINVAL, "pss_fold: step_bins must be finite");
+    if (n == 0) return PSS_OK;
+    int64_t lo_dm = INT64_MAX, hi_dm = -1;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!std::isfinite(reqs[i].f_hz) || !std::isfinite(reqs[i].fdot_hz_s))
+            return fail(PSS_EINVAL, "pss_fold: non-finite frequency");
+        lo_dm = std::min<int64_t>(lo_dm, reqs[i].dm_idx);
+        hi_dm = std::max<int64_t>(hi_dm, reqs[i].dm_idx);
+    }
+    PSS_TRY(check_common(ctx, plan, fil, data, lo_dm, hi_dm + 1));
+    PSS_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = pick_stream(ctx, stream);
+    int32_t ck = 0;
+    int64_t pitch = 0;
+    SubTab T;
+    PSS_TRY(stage_input(ctx, plan, fil, data, data_on_device, lo_dm, hi_dm + 1, s, &ck, &pitch, &T));
+    const std::vector<int32_t> hd = T.on ? std::vector<int32_t>() : compact_delays(plan, kept_channels(fil), lo_dm, hi_dm + 1);
+    // requests by trial; chunks of at most 256 series rows
+    std::vector<int64_t> order(n);
+    for (int64_t i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return reqs[a].dm_idx < reqs[b].dm_idx; });
+    int64_t nv_max = 0;
+    for (const auto& st : plan->stages) nv_max = std::max<int64_t>(nv_max, st.nv);
+    constexpr int64_t MAXROWS = 256;
+    PSS_TRY(ctx->sp_series.ensure((size_t)MAXROWS * nv_max * sizeof(int32_t)));
+    PSS_TRY(ctx->sp_mom.ensure((size_t)2 * MAXROWS * sizeof(unsigned long long)));
+    size_t q0 = 0;
+    while (q0 < order.size()) {
+        // runs of trials (same stage, gaps of at most 15 trials dedispersed as well) up to MAXROWS rows
+        struct Run { int64_t a, b; int32_t row0; };
+        std::vector<Run> runs;
+        int32_t rows = 0;
+        size_t q = q0;
+        while (q < order.size()) {
+            const int64_t d = reqs[order[q]].dm_idx;
+            if (!runs.empty() && d < runs.back().b) { ++q; continue; }
+            if (!runs.empty() && plan->stage_of[d] == plan->stage_of[runs.back().a] && d - runs.back().b <= 15 &&
+                rows + (d + 1 - runs.back().b) <= MAXROWS) {
+                rows += (int32_t)(d + 1 - runs.back().b);
+                runs.back().b = d + 1;
+            } else if (rows + 1 <= MAXROWS) {
+                runs.push_back({d, d + 1, rows});
+                rows += 1;
+            } else {
+                break;
+            }
+            ++q;
+        }
+        int32_t* ser = (int32_t*)ctx->sp_series.p;
+        unsigned long long* m1 = (unsigned long long*)ctx->sp_mom.p;
+        unsigned long long* m2 = m1 + MAXROWS;
+        PSS_CUDA(cudaMemsetAsync(m1, 0, (size_t)2 * MAXROWS * sizeof(unsigned long long), s));
+        for (const Run& r : runs) {
+            const StageInfo& st = plan->stages[plan->stage_of[r.a]];
+            const int32_t nb = (int32_t)(r.b - r.a);
+            int32_t spread = 0;
+            SubBatch SB;
+            if (T.on) {
+                SB = sub_batch(plan, T, ck, lo_dm, r.a, nb, st.nv, st.ds);
+                PSS_TRY(ctx->subu.ensure((size_t)plan->nsub * SB.ngb * SB.stride1 * 4));
+            } else {
+                spread = delay_spread(hd.data() + (size_t)(r.a - lo_dm) * ck, nb, ck);
+            }
+            int32_t* out = ser + (int64_t)r.row0 * nv_max;
+            PSS_TRY(enqueue_dedisp(ctx, plan, ck, pitch, T, st, lo_dm, r.a, nb, spread, SB, ctx->subu.p, nullptr, out,
+                                   nv_max, nullptr, s));
+            PSS_CUDA(launch_sp_moments(out, nv_max, st.nv, nb, m1 + r.row0, m2 + r.row0, s));
+        }
+        std::vector<unsigned long long> mom((size_t)2 * MAXROWS);
+        PSS_CUDA(cudaMemcpyAsync(mom.data(), m1, mom.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        PSS_CUDA(cudaStreamSynchronize(s));
+        PSS_TRY(check_errflag(ctx, s));
+        // items of this chunk's requests
+        std::vector<FoldItem> items;
+        std::vector<int64_t> which;
+        for (size_t k = q0; k < q; ++k) {
+            const pss_fold_req& rq = reqs[order[k]];
+            int32_t row = -1;
+            for (const Run& r : runs)
+                if (rq.dm_idx >= r.a && rq.dm_idx < r.b) row = r.row0 + (int32_t)(rq.dm_idx - r.a);
+            const StageInfo& st = plan->stages[plan->stage_of[rq.dm_idx]];
+            FoldItem it{};
+            it.row = row;
+            it.n = st.nv;
+            it.dt = (double)st.ds * plan->tsamp;
+            it.T = plan->t_span(rq.dm_idx);
+            it.f = rq.f_hz;
+            it.fdot = rq.fdot_hz_s;
+            it.s1 = mom[row];
+            it.s2 = mom[MAXROWS + row];
+            items.push_back(it);
+            which.push_back(order[k]);
+        }
+        const int64_t ni = (int64_t)items.size();
+        const size_t o_items = 0, o_prof = (ni * sizeof(FoldItem) + 255) / 256 * 256;
+        const size_t o_cnt = o_prof + (size_t)ni * nfreq * nbin * 8, o_chi = o_cnt + (size_t)ni * nfreq * nbin * 8;
+        const size_t o_frq = o_chi + (size_t)ni * nfreq * 8, total = o_frq + (size_t)ni * nfreq * 8;
+        PSS_TRY(ctx->fold_buf.ensure(total));
+        char* fb = (char*)ctx->fold_buf.p;
+        PSS_CUDA(cudaMemcpyAsync(fb + o_items, items.data(), ni * sizeof(FoldItem), cudaMemcpyHostToDevice, s));
+        FoldArgs fa{};
+        fa.series = ser;
+        fa.stride = nv_max;
+        fa.items = (const FoldItem*)(fb + o_items);
+        fa.nbin = nbin;
+        fa.nfreq = nfreq;
+        fa.step_bins = step_bins;
+        fa.prof = (long long*)(fb + o_prof);
+        fa.counts = (long long*)(fb + o_cnt);
+        fa.chi2 = (double*)(fb + o_chi);
+        fa.freq = (double*)(fb + o_frq);
+        PSS_CUDA(launch_fold(fa, ni, s));
+        std::vector<char> host(total - o_prof);
+        PSS_CUDA(cudaMemcpyAsync(host.data(), fb + o_prof, host.size(), cudaMemcpyDeviceToHost, s));
+        PSS_CUDA(cudaStreamSynchronize(s));
+        const long long* hp = (const long long*)host.data();
+        const long long* hc = (const long long*)(host.data() + (o_cnt - o_prof));
+        const double* hchi = (const double*)(host.data() + (o_chi - o_prof));
+        const double* hfrq = (const double*)(host.data() + (o_frq - o_prof));
+        for (int64_t i = 0; i < ni; ++i) {
+            int best = 0;
+            for (int k = 1; k < nfreq; ++k)
+                if (hchi[i * nfreq + k] > hchi[i * nfreq + best]) best = k;
+            const int64_t w = which[i];
+            results[w].f_hz = hfrq[i * nfreq + best];
+            results[w].chi2_red = hchi[i * nfreq + best];
+            results[w].best = best;
+            results[w].reserved = 0;
+            memcpy(profiles + w * nbin, hp + (i * nfreq + best) * nbin, (size_t)nbin * 8);
+            memcpy(counts + w * nbin, hc + (i * nfreq + best) * nbin, (size_t)nbin * 8);
+        }
+        q0 = q;
     }
     return PSS_OK;
 }
@@ -1088,8 +1618,7 @@ pss_status refine_prepare(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc
     // per-channel series (channel-major copy already staged by run_path) and spectra
     const std::vector<int32_t> keep = kept_channels(fil);
     const int32_t ck = (int32_t)keep.size();
-    const int TN = dedisp_tile_samples();
-    const int64_t pitch = ((fil->nsamp + TN + 256) + 63) / 64 * 64;
+    const int64_t pitch = xcm_pitch(*plan, fil);
     PSS_TRY(ctx->series.ensure((size_t)ck * nfft * 4));
     PSS_TRY(ctx->sums.ensure((size_t)ck * 8));
     PSS_TRY(ctx->fftA.ensure((size_t)ck * M * 8));
@@ -1293,8 +1822,8 @@ namespace pss {
 namespace {
 
 size_t ctx_bytes(const pss_ctx* c) {
-    const DevBuf* bufs[] = {&c->fil_dev, &c->xcm, &c->delays_dev, &c->series, &c->sums, &c->fftA, &c->fftB,
-                            &c->spec, &c->plane, &c->cands, &c->counter, &c->taps, &c->ftaps, &c->tapinfo,
+    const DevBuf* bufs[] = {&c->fil_dev, &c->xcm, &c->delays_dev, &c->subu, &c->series, &c->sums, &c->fftA,
+                            &c->fftB, &c->spec, &c->plane, &c->cands, &c->counter, &c->taps, &c->ftaps, &c->tapinfo,
                             &c->errflag, &c->twid};
     size_t t = 0;
     for (const DevBuf* b : bufs) t += b->bytes;
@@ -1527,13 +2056,17 @@ size_t search_footprint(const Plan& plan, const pss_fil_desc* fil, const pss_sea
     auto buf = [](size_t want) { return want ? want + want / 8 + 256 : (size_t)0; };
     const std::vector<int32_t> keep = kept_channels(fil);
     const int64_t ck = (int64_t)keep.size();
-    const int64_t pitch = ((fil->nsamp + dedisp_tile_samples() + 256) + 63) / 64 * 64;
+    const int64_t pitch = xcm_pitch(plan, fil);
     const int nz = nz_of(cfg);
-    size_t t = buf((size_t)file_bytes(fil)) + buf((size_t)ck * pitch + 64) +
-               buf((size_t)(ck + plan.ndm() * ck) * sizeof(int32_t)) + buf(sizeof(int)) +
-               buf((size_t)dev_cap * sizeof(pss_raw_cand)) + buf(sizeof(unsigned long long));
+    size_t tables = (size_t)(ck + plan.ndm() * ck);
+    if (plan.nsub > 0) {
+        const size_t ng = plan.grp_first.size();
+        tables = std::max(tables, (size_t)ck + ng * ck + (size_t)plan.ndm() * plan.nsub + 2 * ng + 2 * plan.nsub + 16);
+    }
+    size_t t = buf((size_t)file_bytes(fil)) + buf((size_t)ck * pitch + 64) + buf(tables * sizeof(int32_t)) +
+               buf(sizeof(int)) + buf((size_t)dev_cap * sizeof(pss_raw_cand)) + buf(sizeof(unsigned long long));
     int64_t nfft_max = 0, total_taps = 0;
-    size_t need_series = 0, need_fft = 0, need_sums = 0, need_plane = 0;
+    size_t need_series = 0, need_fft = 0, need_sums = 0, need_plane = 0, subu = 0;
     std::vector<int64_t> sizes;
     for (const auto& st : plan.stages) {
         nfft_max = std::max<int64_t>(nfft_max, st.nfft);
@@ -1543,6 +2076,11 @@ size_t search_footprint(const Plan& plan, const pss_fil_desc* fil, const pss_sea
             t += buf((size_t)(st.nfft / 2) * sizeof(float2));  // inter-pass twiddles (at most M entries)
         }
         const int64_t B = batch_trials(st.nfft, nz, MODE_SEARCH, st.n_dm);
+        if (plan.nsub > 0) {
+            // stage-1 rows: groups touched by a batch x subbands x (N_v ds + largest D, padded)
+            const int64_t ngb = (B + plan.sub_group - 1) / plan.sub_group + 1;
+            subu = std::max(subu, (size_t)plan.nsub * ngb * ((fil->nsamp + 3) & ~int64_t(3)) * 4);
+        }
         need_series = std::max(need_series, (size_t)B * st.nfft * 4);
         need_sums = std::max(need_sums, (size_t)B * 8);
         need_fft = std::max(need_fft, (size_t)B * (st.nfft / 2) * 8);
@@ -1555,7 +2093,8 @@ size_t search_footprint(const Plan& plan, const pss_fil_desc* fil, const pss_sea
     if (plane_fft_usable(cfg->zmax, cfg->halfwidth_extra, PLANE_FFT_L))
         t += buf((size_t)nz * 2 * PLANE_FFT_L * sizeof(float2));
     t += buf((size_t)nfft_max * sizeof(float2)) + buf(need_series) + buf(need_sums) + 3 * buf(need_fft) +
-         buf(need_plane) + buf((size_t)total_taps * sizeof(float2)) + buf((size_t)5 * nz * sizeof(int32_t));
+         buf(need_plane) + buf((size_t)total_taps * sizeof(float2)) + buf((size_t)5 * nz * sizeof(int32_t)) +
+         buf(subu);
     return t;
 }
 

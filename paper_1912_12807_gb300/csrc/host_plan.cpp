@@ -31,6 +31,18 @@ static int64_t next_pow2(int64_t n) {
     return p;
 }
 
+// N_v and nfft of every stage from the plan's largest delay.
+static pss_status set_lengths(Plan* P) {
+    if (P->nsamp <= P->max_delay) return fail(PSS_EINVAL, "pss_dd_plan: file shorter than the largest dispersion delay");
+    for (auto& si : P->stages) {
+        si.nv = (P->nsamp - P->max_delay) / si.ds;
+        if (si.nv < 1) return fail(PSS_EINVAL, "pss_dd_plan: no valid samples after downsampling");
+        si.nfft = next_pow2(si.nv);
+        if (si.nfft > (int64_t(1) << 24)) return fail(PSS_EINVAL, "pss_dd_plan: series longer than 2^24");
+    }
+    return PSS_OK;
+}
+
 pss_status build_plan(const pss_fil_desc* fil, const pss_dd_stage* st, int nst, Plan* P) {
     if (!fil || !st || nst <= 0) return fail(PSS_EINVAL, "pss_dd_plan: null descriptor or no stages");
     if (fil->nchan <= 0 || fil->nsamp <= 0) return fail(PSS_EINVAL, "pss_dd_plan: nchan and nsamp must be > 0");
@@ -92,14 +104,73 @@ pss_status build_plan(const pss_fil_desc* fil, const pss_dd_stage* st, int nst, 
         }
     }
     P->max_delay = dmax;
-    if (fil->nsamp <= dmax) return fail(PSS_EINVAL, "pss_dd_plan: file shorter than the largest dispersion delay");
-    for (auto& si : P->stages) {
-        si.nv = (fil->nsamp - dmax) / si.ds;
-        if (si.nv < 1) return fail(PSS_EINVAL, "pss_dd_plan: no valid samples after downsampling");
-        si.nfft = next_pow2(si.nv);
-        if (si.nfft > (int64_t(1) << 24)) return fail(PSS_EINVAL, "pss_dd_plan: series longer than 2^24");
+    P->nsub = 0;
+    return set_lengths(P);
+}
+
+// Two-stage (prepsubband) scheme; the paper only says it is faster than one
+// prepdata per DM (Sect. 5).  Subband b = channels [b S, (b+1) S), reference
+// f_b = its highest centre frequency; groups of `group` consecutive trials
+// of one stage, nominal DM = the middle trial's (index first + (n-1)/2);
+//   e_c(g)  = round(((K DM_g) (1/(f_c f_c) - 1/(f_b f_b))) / tsamp),
+//   D_b(i)  = round(((K DM_i) (1/(f_b f_b) - 1/(f_ref f_ref))) / tsamp),
+// halves away from zero; D' = max(D, max_{i,c} e_c(g_i) + D_b(c)(i)).
+pss_status build_subband(Plan* P, int32_t nsub, int32_t group) {
+    const int C = P->nchan;
+    if (nsub < 1 || C % nsub != 0) return fail(PSS_EINVAL, "pss_dd_plan_subband: nsub must divide nchan");
+    if (group < 1 || group > 1024) return fail(PSS_EINVAL, "pss_dd_plan_subband: group must be in [1, 1024]");
+    const int S = C / nsub;
+    P->nsub = nsub;
+    P->sub_group = group;
+    P->sub_S = S;
+    double fref = -1e300;
+    for (int c = 0; c < C; ++c) fref = std::max(fref, P->freqs[c]);
+    P->fsub.assign(nsub, -1e300);
+    for (int c = 0; c < C; ++c) P->fsub[c / S] = std::max(P->fsub[c / S], P->freqs[c]);
+    const int64_t ndm = P->ndm();
+    P->grp_first.clear();
+    P->grp_n.clear();
+    P->grp_dm.clear();
+    P->grp_of.assign(ndm, 0);
+    for (int64_t i = 0; i < ndm;) {
+        int64_t j = i;
+        while (j < ndm && j - i < group && P->stage_of[j] == P->stage_of[i]) ++j;
+        for (int64_t k = i; k < j; ++k) P->grp_of[k] = (int32_t)P->grp_first.size();
+        P->grp_first.push_back(i);
+        P->grp_n.push_back((int32_t)(j - i));
+        P->grp_dm.push_back(P->dms[i + (j - i - 1) / 2]);
+        i = j;
     }
-    return PSS_OK;
+    const int64_t ng = (int64_t)P->grp_first.size();
+    P->sub_e.assign((size_t)ng * C, 0);
+    P->sub_D.assign((size_t)ndm * nsub, 0);
+    std::vector<double> din(C), db(nsub);
+    for (int c = 0; c < C; ++c) {
+        const double fb = P->fsub[c / S];
+        din[c] = 1.0 / (P->freqs[c] * P->freqs[c]) - 1.0 / (fb * fb);
+    }
+    for (int b = 0; b < nsub; ++b) db[b] = 1.0 / (P->fsub[b] * P->fsub[b]) - 1.0 / (fref * fref);
+    for (int64_t g = 0; g < ng; ++g) {
+        const double kd = K_DISP * P->grp_dm[g];
+        for (int c = 0; c < C; ++c) {
+            const double r = round((kd * din[c]) / P->tsamp);
+            if (!(r < 2.0e9)) return fail(PSS_EINVAL, "pss_dd_plan_subband: delay exceeds int32");
+            P->sub_e[(size_t)g * C + c] = (int32_t)r;
+        }
+    }
+    int64_t dmax = P->max_delay;
+    for (int64_t i = 0; i < ndm; ++i) {
+        const double kd = K_DISP * P->dms[i];
+        for (int b = 0; b < nsub; ++b) {
+            const double r = round((kd * db[b]) / P->tsamp);
+            if (!(r < 2.0e9)) return fail(PSS_EINVAL, "pss_dd_plan_subband: delay exceeds int32");
+            P->sub_D[(size_t)i * nsub + b] = (int32_t)r;
+        }
+        const int32_t* e = &P->sub_e[(size_t)P->grp_of[i] * C];
+        for (int c = 0; c < C; ++c) dmax = std::max<int64_t>(dmax, (int64_t)e[c] + P->sub_D[(size_t)i * nsub + c / S]);
+    }
+    P->max_delay = dmax;
+    return set_lengths(P);
 }
 
 // ---- statistics -----------------------------------------------------------

@@ -120,7 +120,20 @@ __global__ void __launch_bounds__(NT) k_dedisp(DedispArgs a, int RW, int CC, uin
     const int gn = min(G, a.nb - g0);
     const int my = g0 + warp;
     const bool active = warp < gn;
-    const int nchunks = (a.ck + CC - 1) / CC;
+    // this CTA's channels: all ck, or subband blockIdx.z's (stage 1 of the two-stage scheme)
+    const uint8_t* xcm = a.xcm;
+    const int32_t* delays = a.delays;
+    int ck = a.ck;
+    int32_t* out_i = a.out_i;
+    const int dstride = a.dstride > 0 ? a.dstride : a.ck;
+    if (a.zsub) {
+        const int2 z = a.zsub[blockIdx.z];
+        xcm += (int64_t)z.x * a.pitch;
+        delays += z.x;
+        ck = z.y;
+        out_i += (int64_t)blockIdx.z * a.zout;
+    }
+    const int nchunks = (ck + CC - 1) / CC;
 
     if (threadIdx.x == 0) {
         mbar_init(S.bar, 1);
@@ -132,17 +145,17 @@ __global__ void __launch_bounds__(NT) k_dedisp(DedispArgs a, int RW, int CC, uin
     // was sized for) is refused rather than read out of bounds
     const int omax = 4 * (RW - 32 * KW);
     bool bad = false;
-    for (int c = threadIdx.x; c < a.ck; c += NT) {
-        const int32_t* dcol = a.delays + (int64_t)g0 * a.ck + c;
+    for (int c = threadIdx.x; c < ck; c += NT) {
+        const int32_t* dcol = delays + (int64_t)g0 * dstride + c;
         int32_t dmin = dcol[0];
-        for (int g = 1; g < gn; ++g) dmin = min(dmin, dcol[(int64_t)g * a.ck]);
+        for (int g = 1; g < gn; ++g) dmin = min(dmin, dcol[(int64_t)g * dstride]);
         const int64_t st = (t0 + dmin) & ~int64_t(15);
         S.rs[c] = (int32_t)(st - t0);
         for (int g = 0; g < gn; ++g) {
-            const int64_t o = t0 + dcol[(int64_t)g * a.ck] - st;
+            const int64_t o = t0 + dcol[(int64_t)g * dstride] - st;
             bad |= (o >= omax);
             // word index into the channel's four copies: copy (o & 3), word (o >> 2)
-            S.offs[g * a.ck + c] = (uint16_t)(bad ? 0 : (o & 3) * RW + (o >> 2));
+            S.offs[g * ck + c] = (uint16_t)(bad ? 0 : (o & 3) * RW + (o >> 2));
         }
     }
     if (__syncthreads_or(bad)) {
@@ -153,14 +166,14 @@ __global__ void __launch_bounds__(NT) k_dedisp(DedispArgs a, int RW, int CC, uin
         // warp 0: one bulk copy per row of the chunk
         if (warp == 0) {
             const int cb = c * CC;
-            const int cn = min(CC, a.ck - cb);
+            const int cn = min(CC, ck - cb);
             if (lane == 0) mbar_expect_tx(S.bar, (uint32_t)(cn * RAWB));
             __syncwarp();
             // order this CTA's earlier generic-proxy reads of the staging area
             // before the bulk copies overwrite it
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             for (int i = lane; i < cn; i += 32) {
-                const uint8_t* src = a.xcm + (int64_t)(cb + i) * a.pitch + t0 + S.rs[cb + i];
+                const uint8_t* src = xcm + (int64_t)(cb + i) * a.pitch + t0 + S.rs[cb + i];
                 bulk_g2s(S.raw + (size_t)i * RAWB, src, (uint32_t)RAWB, S.bar);
             }
         }
@@ -186,7 +199,7 @@ __global__ void __launch_bounds__(NT) k_dedisp(DedispArgs a, int RW, int CC, uin
     int failed_at = -1;
     for (int c = 0; c < nchunks; ++c) {
         const int cb = c * CC;
-        const int cn = min(CC, a.ck - cb);
+        const int cn = min(CC, ck - cb);
         // one warp polls the mbarrier; the others wait at the block barrier (which
         // does not take issue slots), and the barrier passes the staged bytes on
         const bool ok = warp == 0 ? mbar_wait(S.bar, (uint32_t)(c & 1)) : true;
@@ -229,7 +242,7 @@ __global__ void __launch_bounds__(NT) k_dedisp(DedispArgs a, int RW, int CC, uin
             }
         }
         if (active) {
-            const uint16_t* offs = S.offs + warp * a.ck + cb;
+            const uint16_t* offs = S.offs + warp * ck + cb;
 #pragma unroll 4
             for (int i = 0; i < cn; ++i) {
                 const uint32_t* p = S.copies + (size_t)i * 4 * RW + offs[i] + lane;
@@ -271,7 +284,7 @@ __global__ void __launch_bounds__(NT) k_dedisp(DedispArgs a, int RW, int CC, uin
     unsigned long long part = 0ull;
     if (a.ds == 1) {
         float* of = INT_OUT ? nullptr : a.out_f + (int64_t)my * a.out_stride;
-        int32_t* oi = INT_OUT ? a.out_i + (int64_t)my * a.out_stride : nullptr;
+        int32_t* oi = INT_OUT ? out_i + (int64_t)my * a.out_stride : nullptr;
 #pragma unroll
         for (int k = 0; k < KW; ++k) {
             const int64_t j = j0 + 4 * (lane + 32 * k);
@@ -306,7 +319,7 @@ __global__ void __launch_bounds__(NT) k_dedisp(DedispArgs a, int RW, int CC, uin
             unsigned long long acc = 0ull;
             for (int e = 0; e < a.ds; ++e) acc += nat[oo * a.ds + e];
             part += acc;
-            if (INT_OUT) a.out_i[(int64_t)my * a.out_stride + j] = (int32_t)acc;
+            if (INT_OUT) out_i[(int64_t)my * a.out_stride + j] = (int32_t)acc;
             else a.out_f[(int64_t)my * a.out_stride + j] = (float)acc;
         }
     }
@@ -345,7 +358,7 @@ cudaError_t launch_dedisp(const DedispArgs& a, int num_sms, cudaStream_t s) {
     const size_t shm = layout_of(RW, CC, a.ck).total;
     if (shm > 220 * 1024) return cudaErrorInvalidValue;
     const int64_t L = a.nv * a.ds;
-    dim3 grid((unsigned)((L + TN - 1) / TN), (unsigned)((a.nb + G - 1) / G));
+    dim3 grid((unsigned)((L + TN - 1) / TN), (unsigned)((a.nb + G - 1) / G), (unsigned)(a.zsub ? a.nz : 1));
     const bool wide = a.ck > 256;
     if (a.out_i) return wide ? launch_t<true, true>(a, grid, shm, RW, CC, s) : launch_t<true, false>(a, grid, shm, RW, CC, s);
     return wide ? launch_t<false, true>(a, grid, shm, RW, CC, s) : launch_t<false, false>(a, grid, shm, RW, CC, s);

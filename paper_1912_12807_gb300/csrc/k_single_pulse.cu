@@ -1,0 +1,176 @@
+// Single-pulse (boxcar matched-filter) search of dedispersed series: the
+// step after dedispersion in the paper's pipeline (single_pulse_search.py,
+// Sect. 2 step 7; long-period pulsars are found this way, Sect. 5.3).
+//
+// Per trial: mu = S1/N and sigma = sqrt((S2 - S1*S1/N)/N) from the exact
+// integer moments S1 = sum s, S2 = sum s^2; for each boxcar width w,
+// B_w[t] = sum_{k<w} s[t+k] (exact, t <= N - w) is a detection when
+// B_w[t] >= w*mu + thr*sigma*sqrt(w) and it is a local maximum over its
+// own width (strictly above the w - 1 values before it, not below the
+// w - 1 after it).  The FP64 arithmetic is written with round-to-nearest
+// intrinsics in the stated order so that no multiply-add is contracted and
+// the threshold is the same number the host computes.
+//
+// k_sp_moments: one pass over the series, 64-bit integer sums.
+// k_sp_detect: a CTA owns TS samples of one trial; it stages the samples
+// [t0 - wmax + 1, t0 + TS + 2 wmax - 2] in shared memory as a 64-bit
+// prefix sum (so every B_w the tile and its local-maximum windows need is
+// one subtraction), then tests every (t, w).  Detections are appended
+// with an atomic counter; past `cap` they are only counted.
+#include "pss_internal.h"
+
+namespace pss {
+
+namespace {
+
+constexpr int TS = 2048;  // samples per CTA
+constexpr int NT = 256;
+
+__global__ void __launch_bounds__(NT) k_sp_moments(const int32_t* __restrict__ series, int64_t stride, int64_t n,
+                                                   unsigned long long* s1, unsigned long long* s2) {
+    const int b = blockIdx.y;
+    const int32_t* s = series + (int64_t)b * stride;
+    unsigned long long a1 = 0ull, a2 = 0ull;
+    for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT) {
+        const unsigned long long v = (unsigned long long)(uint32_t)s[i];
+        a1 += v;
+        a2 += v * v;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        a1 += __shfl_xor_sync(0xffffffffu, a1, off);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(s1 + b, a1);
+        atomicAdd(s2 + b, a2);
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_sp_detect(const __grid_constant__ SpArgs a) {
+    extern __shared__ __align__(16) long long R[];  // prefix sums relative to `base`
+    __shared__ double s_thr[SP_MAXW];
+    __shared__ long long s_tot[NT];
+    __shared__ int s_ok;
+    const int b = blockIdx.y;
+    const int64_t n = a.n;
+    const int64_t t0 = (int64_t)blockIdx.x * TS;
+    const int32_t* s = a.series + (int64_t)b * a.stride;
+    if (threadIdx.x == 0) {
+        const double fS1 = (double)a.s1[b], fS2 = (double)a.s2[b], fN = (double)n;
+        const double mu = __ddiv_rn(fS1, fN);
+        double var = __ddiv_rn(__dsub_rn(fS2, __ddiv_rn(__dmul_rn(fS1, fS1), fN)), fN);
+        if (!(var > 0.0)) var = 0.0;
+        const double sigma = __dsqrt_rn(var);
+        s_ok = sigma > 0.0;
+        const double ts = __dmul_rn(a.thr, sigma);
+        for (int i = 0; i < a.nw; ++i) {
+            const double w = (double)a.w[i];
+            s_thr[i] = __dadd_rn(__dmul_rn(w, mu), __dmul_rn(ts, __dsqrt_rn(w)));
+        }
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    const int64_t base = max((int64_t)0, t0 - a.wmax + 1);
+    const int64_t last = min(n, t0 + TS + 2 * (int64_t)a.wmax - 2);  // largest prefix index needed
+    const int L = (int)(last - base + 1);                           // R[0 .. L-1]
+    // R[k] = sum_{base <= j < base + k} s[j]: per-thread segment sums, then a scan
+    const int seg = (L + NT - 1) / NT;
+    const int k0 = threadIdx.x * seg;
+    long long acc = 0;
+    for (int k = k0; k < min(k0 + seg, L - 1); ++k) acc += s[base + k];
+    s_tot[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        // exclusive scan of the NT segment totals by one warp (8 per lane)
+        constexpr int PER = NT / 32;
+        long long v[PER], run = 0;
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            v[i] = s_tot[threadIdx.x * PER + i];
+            run += v[i];
+        }
+        long long incl = run;
+        for (int off = 1; off < 32; off <<= 1) {
+            const long long u = __shfl_up_sync(0xffffffffu, incl, off);
+            if (threadIdx.x >= off) incl += u;
+        }
+        long long ex = incl - run;
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const long long t = v[i];
+            s_tot[threadIdx.x * PER + i] = ex;
+            ex += t;
+        }
+    }
+    __syncthreads();
+    acc = s_tot[threadIdx.x];
+    for (int k = k0; k < min(k0 + seg, L); ++k) {
+        R[k] = acc;
+        if (k < L - 1) acc += s[base + k];
+    }
+    __syncthreads();
+    for (int i = 0; i < a.nw; ++i) {
+        const int w = a.w[i];
+        const int64_t tmax = n - w;  // last valid boxcar start
+        if (tmax < t0) continue;
+        const double thr = s_thr[i];
+        const int64_t tend = min(t0 + TS - 1, tmax);
+        for (int64_t t = t0 + threadIdx.x; t <= tend; t += NT) {
+            const long long B = R[t + w - base] - R[t - base];
+            if (!((double)B >= thr)) continue;
+            bool ok = true;
+            const int64_t lo = max((int64_t)0, t - w + 1), hi = min(tmax, t + w - 1);
+            for (int64_t u = lo; u < t && ok; ++u) ok = B > R[u + w - base] - R[u - base];
+            for (int64_t u = t + 1; u <= hi && ok; ++u) ok = B >= R[u + w - base] - R[u - base];
+            if (!ok) continue;
+            const unsigned long long slot = atomicAdd(a.count, 1ull);
+            if ((int64_t)slot < a.cap) {
+                SpRaw e;
+                e.dm_idx = a.dm0 + b;
+                e.w = w;
+                e.t = t;
+                e.B = B;
+                a.out[slot] = e;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+size_t sp_detect_smem(int wmax) { return (size_t)(TS + 3 * wmax) * sizeof(long long); }
+
+cudaError_t launch_single_pulse(const SpArgs& a, unsigned long long* s1, unsigned long long* s2, cudaStream_t s) {
+    if (a.nb <= 0 || a.n <= 0) return cudaSuccess;
+    if (a.nw < 1 || a.nw > SP_MAXW || a.wmax < 1 || a.wmax > SP_MAXWIDTH) return cudaErrorInvalidValue;
+    dim3 gm((unsigned)std::min<int64_t>((a.n + NT - 1) / NT, 64), (unsigned)a.nb);
+    k_sp_moments<<<gm, NT, 0, s>>>(a.series, a.stride, a.n, s1, s2);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t shm = sp_detect_smem(a.wmax);
+    e = allow_smem((const void*)k_sp_detect, shm);
+    if (e != cudaSuccess) return e;
+    dim3 gd((unsigned)((a.n + TS - 1) / TS), (unsigned)a.nb);
+    k_sp_detect<<<gd, NT, shm, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sp_moments(const int32_t* series, int64_t stride, int64_t n, int32_t nb, unsigned long long* s1,
+                              unsigned long long* s2, cudaStream_t s) {
+    if (nb <= 0 || n <= 0) return cudaSuccess;
+    dim3 gm((unsigned)std::min<int64_t>((n + NT - 1) / NT, 64), (unsigned)nb);
+    k_sp_moments<<<gm, NT, 0, s>>>(series, stride, n, s1, s2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sp_detect_only(const SpArgs& a, cudaStream_t s) {
+    if (a.nb <= 0 || a.n <= 0) return cudaSuccess;
+    const size_t shm = sp_detect_smem(a.wmax);
+    cudaError_t e = allow_smem((const void*)k_sp_detect, shm);
+    if (e != cudaSuccess) return e;
+    dim3 gd((unsigned)((a.n + TS - 1) / TS), (unsigned)a.nb);
+    k_sp_detect<<<gd, NT, shm, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace pss

@@ -57,6 +57,7 @@ using namespace pss;
 extern "C" pss_status pss_dedisperse_noalloc(const pss_plan* plan, const pss_fil_desc* fil, const void* data_dev,
                                              int64_t dm_begin, int64_t dm_end, int32_t* out, void* stream) {
     if (!plan || !fil || !data_dev) return fail(PSS_EINVAL, "pss_dedisperse_noalloc: null plan, descriptor or data");
+    if (plan->nsub > 0) return fail(PSS_EINVAL, "pss_dedisperse_noalloc: two-stage (subband) plans are not supported");
     if (fil->nchan != plan->nchan || fil->nsamp != plan->nsamp)
         return fail(PSS_EINVAL, "pss_dedisperse_noalloc: descriptor does not match the plan");
     if (fil->nbits != 8 && fil->nbits != 1) return fail(PSS_EINVAL, "pss_dedisperse_noalloc: nbits must be 8 or 1");

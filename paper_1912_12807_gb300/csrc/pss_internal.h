@@ -49,7 +49,16 @@ struct Plan {
     std::vector<double> dms;
     std::vector<int32_t> stage_of;
     std::vector<int32_t> delays;  // [ndm][nchan]
-    int64_t max_delay = 0;
+    int64_t max_delay = 0;        // D (or D' of the two-stage scheme)
+    // two-stage (subband) scheme; nsub == 0: exact shift-and-sum
+    int32_t nsub = 0, sub_group = 0, sub_S = 0;
+    std::vector<double> fsub;        // [nsub] reference frequency of each subband
+    std::vector<int64_t> grp_first;  // [ngroups] first trial of each group
+    std::vector<int32_t> grp_n;      // [ngroups] trials in each group
+    std::vector<double> grp_dm;      // [ngroups] nominal DM
+    std::vector<int32_t> grp_of;     // [ndm] group of each trial
+    std::vector<int32_t> sub_e;      // [ngroups][nchan] within-subband delays at the nominal DM
+    std::vector<int32_t> sub_D;      // [ndm][nsub] subband delays
     int64_t ndm() const { return (int64_t)dms.size(); }
     double t_span(int64_t dm) const {
         const StageInfo& s = stages[stage_of[dm]];
@@ -58,6 +67,9 @@ struct Plan {
 };
 
 pss_status build_plan(const pss_fil_desc* fil, const pss_dd_stage* st, int nst, Plan* out);
+// The two-stage tables on top of a built plan; raises max_delay to D' and
+// recomputes the stage lengths.
+pss_status build_subband(Plan* P, int32_t nsub, int32_t group);
 
 // ---- statistics (host) ----------------------------------------------------
 double log_q(int n, double S);
@@ -135,7 +147,12 @@ struct Ctx {
     int num_sms = 0;
     DevBuf fil_dev;      // uploaded file bytes
     DevBuf xcm;          // channel-major uint8 [Ck][pitch]
-    DevBuf delays_dev;   // int32 [ndm][Ck] (kept channels)
+    DevBuf delays_dev;   // int32 [ndm][Ck] (kept channels), or the two-stage tables
+    DevBuf subu;         // int32 stage-1 subband sums of the two-stage scheme
+    DevBuf sp_series;    // int32 dedispersed series of the single-pulse search
+    DevBuf sp_mom;       // unsigned long long [2][B] moments
+    DevBuf sp_ev;        // SpRaw detections
+    DevBuf fold_buf;     // folding items and outputs
     std::vector<int32_t> delays_host;  // what delays_dev holds (keep list + delays), empty if unknown
     DevBuf series;       // float [B][nfft]
     DevBuf sums;         // unsigned long long [B]
@@ -246,10 +263,96 @@ struct DedispArgs {
     int32_t spread;         // max over groups/channels of (dmax - dmin)
     int* err;               // set to 1 if a bounded wait expires (nullable)
     int32_t chunk_kb;       // shared memory for staged channel chunks (0: default)
+    // two-stage scheme, stage 1: blockIdx.z = subband z sums its own kept
+    // channels zsub[z] = (first, count) (ck is then the largest count and
+    // sizes the launch), its delays start at delays + first with rows of
+    // dstride, and its rows go to out_i + z * zout.  zsub null: one sum over
+    // all ck channels, delay rows of ck.
+    const int2* zsub;
+    int32_t nz;
+    int32_t dstride;
+    int64_t zout;
 };
 int dedisp_tile_samples();
 int dedisp_group_trials();  // consecutive trials sharing one staged tile
 cudaError_t launch_dedisp(const DedispArgs& a, int num_sms, cudaStream_t s);
+
+// Two-stage scheme, stage 2: s_i[t] = sum_b u_{g(i),b}[t + D_b(i)], then the
+// ds boxcar, for the nb trials of a batch (k_subband.cu).
+struct SubsumArgs {
+    const int32_t* u;       // [nsub][group rows][row_stride] stage-1 sums
+    int64_t u_zstride;      // elements between subbands
+    int64_t u_rowstride;    // elements between group rows
+    int64_t u_len;          // valid elements of a row
+    int32_t nsub;
+    const int32_t* D;       // [nb][nsub] subband delays of the batch's trials
+    const int2* grp;        // [group rows] (first trial relative to the tables' start, count)
+    int32_t b0rel;          // the batch's first trial relative to the tables' start
+    int32_t ngrp;
+    int32_t nb;
+    int64_t nv;             // outputs per trial
+    int32_t ds;
+    float* out_f;           // [nb][out_stride] or null
+    int32_t* out_i;         // [nb][out_stride] or null
+    int64_t out_stride;
+    unsigned long long* sums;  // [nb] or null
+    int32_t spread;         // max over group rows and subbands of (D max - D min)
+};
+cudaError_t launch_subsum(const SubsumArgs& a, cudaStream_t s);
+
+// Single-pulse boxcar search (k_single_pulse.cu).
+constexpr int SP_MAXW = 32;         // widths per call
+constexpr int SP_MAXWIDTH = 1024;   // largest width
+struct SpRaw {
+    int32_t dm_idx;
+    int32_t w;
+    int64_t t;
+    int64_t B;
+};
+struct SpArgs {
+    const int32_t* series;  // [nb][stride] exact dedispersed series
+    int64_t stride;
+    int64_t n;              // samples per trial (N_v)
+    int32_t nb;
+    int32_t dm0;            // plan index of trial 0
+    int32_t w[SP_MAXW];
+    int32_t nw, wmax;
+    double thr;
+    const unsigned long long* s1;  // [nb] sum s
+    const unsigned long long* s2;  // [nb] sum s^2
+    SpRaw* out;
+    unsigned long long* count;
+    int64_t cap;
+};
+// moments (into s1, s2, which must be zeroed) then detection
+cudaError_t launch_single_pulse(const SpArgs& a, unsigned long long* s1, unsigned long long* s2, cudaStream_t s);
+// detection alone (moments already in a.s1, a.s2)
+cudaError_t launch_sp_detect_only(const SpArgs& a, cudaStream_t s);
+// exact moments alone: s1[b] += sum s, s2[b] += sum s^2 (zero them first)
+cudaError_t launch_sp_moments(const int32_t* series, int64_t stride, int64_t n, int32_t nb, unsigned long long* s1,
+                              unsigned long long* s2, cudaStream_t s);
+
+// Folding (k_fold.cu): one item per candidate.
+struct FoldItem {
+    int32_t row;       // series row of the candidate's trial
+    int32_t reserved;
+    int64_t n;         // samples of that series
+    double dt, T;      // sample interval, series span (s)
+    double f, fdot;    // candidate frequency (Hz) and drift (Hz/s)
+    unsigned long long s1, s2;  // exact moments of the series
+};
+struct FoldArgs {
+    const int32_t* series;  // [rows][stride]
+    int64_t stride;
+    const FoldItem* items;
+    int32_t nbin, nfreq;
+    double step_bins;
+    long long* prof;        // [items][nfreq][nbin]
+    long long* counts;      // [items][nfreq][nbin]
+    double* chi2;           // [items][nfreq]
+    double* freq;           // [items][nfreq]
+};
+cudaError_t launch_fold(const FoldArgs& a, int64_t nitems, cudaStream_t s);
 
 struct FftArgs {
     const float* series;              // [nb][series_stride] raw sums (float, exact)

@@ -53,13 +53,18 @@ class pss_refine_point(C.Structure):
 REFINE_DTYPE = np.dtype([("dm_idx", "<i4"), ("numharm", "<i4"), ("dm", "<f8"), ("r", "<f8"), ("z", "<f8")])
 RAW_DTYPE = np.dtype([("dm_idx", "<i4"), ("numharm", "<i4"), ("h", "<i4"), ("j", "<i4"), ("power", "<f4"),
                       ("reserved", "<i4")])
+FOLD_REQ_DTYPE = np.dtype([("dm_idx", "<i4"), ("reserved", "<i4"), ("f_hz", "<f8"), ("fdot_hz_s", "<f8")])
+FOLD_RES_DTYPE = np.dtype([("f_hz", "<f8"), ("chi2_red", "<f8"), ("best", "<i4"), ("reserved", "<i4")])
+SP_DTYPE = np.dtype([("dm_idx", "<i4"), ("width", "<i4"), ("t", "<i8"), ("boxsum", "<i8"), ("snr", "<f8")])
+SP_WIDTHS = (1, 2, 3, 4, 6, 9, 14, 20, 30, 45, 70, 100, 150)
 CAND_DTYPE = np.dtype([("dm_idx", "<i4"), ("numharm", "<i4"), ("dm", "<f8"), ("r", "<f8"), ("z", "<f8"),
                        ("f_hz", "<f8"), ("sigma", "<f8"), ("power", "<f4"), ("dm_hits", "<i4"), ("h", "<i4"),
                        ("j", "<i4")], align=True)
 
 # every symbol include/pss.h declares
-EXPORTS = ["pss_ctx_create", "pss_ctx_destroy", "pss_last_error", "pss_version", "pss_dd_plan", "pss_plan_info",
-           "pss_plan_trial_info", "pss_plan_free", "pss_dedisperse", "pss_spectrum", "pss_power_plane",
+EXPORTS = ["pss_ctx_create", "pss_ctx_destroy", "pss_last_error", "pss_version", "pss_dd_plan", "pss_dd_plan_subband",
+           "pss_plan_subband_info", "pss_plan_info",
+           "pss_plan_trial_info", "pss_plan_free", "pss_dedisperse", "pss_single_pulse", "pss_fold", "pss_spectrum", "pss_power_plane",
            "pss_search_raw", "pss_sift", "pss_search_dm_batch", "pss_response", "pss_sigma_of_power",
            "pss_power_threshold", "pss_ctx_profile", "pss_ctx_profile_read", "pss_dedisperse_noalloc",
            "pss_refine_prepare", "pss_refine_eval", "pss_refine_candidates", "pss_batch_create", "pss_batch_run",
@@ -87,10 +92,15 @@ def lib():
         "pss_last_error": (C.c_char_p, []),
         "pss_version": (C.c_char_p, []),
         "pss_dd_plan": (st, [P(pss_fil_desc), P(pss_dd_stage), C.c_int, P(vp)]),
+        "pss_dd_plan_subband": (st, [P(pss_fil_desc), P(pss_dd_stage), C.c_int, i32, i32, P(vp)]),
+        "pss_plan_subband_info": (st, [vp, P(i32), P(i32), P(i64), vp, vp, vp]),
         "pss_plan_info": (st, [vp, P(i64), P(i64), vp, vp]),
         "pss_plan_trial_info": (st, [vp, i64, P(i32), P(i64), P(i64), P(i32)]),
         "pss_plan_free": (None, [vp]),
         "pss_dedisperse": (st, [vp, vp, P(pss_fil_desc), vp, C.c_int, i64, i64, vp, vp]),
+        "pss_single_pulse": (st, [vp, vp, P(pss_fil_desc), vp, C.c_int, i64, i64, vp, i32, C.c_double, vp, i64,
+                                  P(i64), vp]),
+        "pss_fold": (st, [vp, vp, P(pss_fil_desc), vp, C.c_int, vp, i64, i32, i32, C.c_double, vp, vp, vp, vp]),
         "pss_spectrum": (st, [vp, vp, P(pss_fil_desc), vp, C.c_int, P(pss_search_cfg), i64, i64, vp, vp]),
         "pss_power_plane": (st, [vp, vp, P(pss_fil_desc), vp, C.c_int, P(pss_search_cfg), i64, i64, vp, vp]),
         "pss_search_raw": (st, [vp, vp, P(pss_fil_desc), vp, C.c_int, P(pss_search_cfg), i64, i64, vp, i64,
@@ -208,12 +218,20 @@ class Context:
 
 
 class Plan:
-    def __init__(self, desc: FilDesc, stages):
+    """pss_dd_plan, or pss_dd_plan_subband when subband = (nsub, group)."""
+
+    def __init__(self, desc: FilDesc, stages, subband=None):
         self.desc = desc
         self._st = stages_array(stages)
         h = C.c_void_p()
-        _check(lib().pss_dd_plan(C.byref(desc.c), self._st, len(stages), C.byref(h)))
+        if subband is None:
+            _check(lib().pss_dd_plan(C.byref(desc.c), self._st, len(stages), C.byref(h)))
+        else:
+            nsub, group = subband
+            _check(lib().pss_dd_plan_subband(C.byref(desc.c), self._st, len(stages), int(nsub), int(group),
+                                             C.byref(h)))
         self.h = h
+        self.subband = subband
         ndm, dmax = C.c_int64(), C.c_int64()
         _check(lib().pss_plan_info(h, C.byref(ndm), C.byref(dmax), None, None))
         self.ndm, self.max_delay = ndm.value, dmax.value
@@ -227,6 +245,18 @@ class Plan:
         out = np.empty((self.ndm, self.desc.c.nchan), dtype=np.int32)
         _check(lib().pss_plan_info(self.h, None, None, None, out.ctypes.data))
         return out
+
+    def subband_info(self):
+        """dict(nsub, group, group_dm [ngroups], chan_delays [ngroups][nchan],
+        sub_delays [ndm][nsub]) of a two-stage plan (nsub 0 otherwise)."""
+        nsub, group, ng = C.c_int32(), C.c_int32(), C.c_int64()
+        _check(lib().pss_plan_subband_info(self.h, C.byref(nsub), C.byref(group), C.byref(ng), None, None, None))
+        gdm = np.empty(ng.value, dtype=np.float64)
+        e = np.empty((ng.value, self.desc.c.nchan), dtype=np.int32)
+        D = np.empty((self.ndm, nsub.value), dtype=np.int32)
+        _check(lib().pss_plan_subband_info(self.h, None, None, None, gdm.ctypes.data, e.ctypes.data,
+                                           D.ctypes.data))
+        return dict(nsub=nsub.value, group=group.value, group_dm=gdm, chan_delays=e, sub_delays=D)
 
     def trial(self, dm_idx: int):
         s, nv, nfft, ds = C.c_int32(), C.c_int64(), C.c_int64(), C.c_int32()
@@ -304,6 +334,44 @@ def pss_dedisperse_noalloc(plan: Plan, data_dev, dm_begin: int, dm_end: int, out
     _check(lib().pss_dedisperse_noalloc(plan.h, C.byref(plan.desc.c), C.c_void_p(data_dev.data_ptr()), dm_begin,
                                         dm_end, C.c_void_p(out.data_ptr()), _stream(stream)))
     return out[:total]
+
+
+def pss_single_pulse(ctx: Context, plan: Plan, data, dm_begin: int, dm_end: int, widths=SP_WIDTHS,
+                     sigma_thr: float = 6.0, cap: int = 1 << 16, stream=None) -> np.ndarray:
+    """Single-pulse events (SP_DTYPE) of trials [dm_begin, dm_end), sorted by
+    (dm_idx, t); grows `cap` and calls again when it is too small."""
+    p, dev, keep = _data_arg(data)
+    w = np.ascontiguousarray(widths, dtype=np.int32)
+    while True:
+        out = np.zeros(max(cap, 1), dtype=SP_DTYPE)
+        n = C.c_int64()
+        st = lib().pss_single_pulse(ctx.h, plan.h, C.byref(plan.desc.c), p, dev, dm_begin, dm_end,
+                                    w.ctypes.data, len(w), float(sigma_thr), out.ctypes.data, cap, C.byref(n),
+                                    _stream(stream))
+        if st == PSS_ECAP:
+            cap = n.value
+            continue
+        _check(st)
+        return out[: n.value]
+
+
+def pss_fold(ctx: Context, plan: Plan, data, dm_idx, f_hz, fdot_hz_s=None, nbin: int = 64, nfreq: int = 9,
+             step_bins: float = 0.25, stream=None):
+    """Fold candidates (arrays of DM index, frequency, drift): (profiles int64
+    [n][nbin], counts int64 [n][nbin], results FOLD_RES_DTYPE [n])."""
+    dm_idx = np.atleast_1d(np.asarray(dm_idx))
+    n = len(dm_idx)
+    req = np.zeros(n, dtype=FOLD_REQ_DTYPE)
+    req["dm_idx"] = dm_idx
+    req["f_hz"] = f_hz
+    req["fdot_hz_s"] = 0.0 if fdot_hz_s is None else fdot_hz_s
+    prof = np.zeros((n, nbin), dtype=np.int64)
+    cnt = np.zeros((n, nbin), dtype=np.int64)
+    res = np.zeros(n, dtype=FOLD_RES_DTYPE)
+    p, dev, keep = _data_arg(data)
+    _check(lib().pss_fold(ctx.h, plan.h, C.byref(plan.desc.c), p, dev, req.ctypes.data, n, nbin, nfreq,
+                          float(step_bins), prof.ctypes.data, cnt.ctypes.data, res.ctypes.data, _stream(stream)))
+    return prof, cnt, res
 
 
 def pss_spectrum(ctx: Context, plan: Plan, data, cfg: pss_search_cfg, dm_begin: int, dm_end: int, stream=None):

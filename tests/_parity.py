@@ -9,6 +9,7 @@ from oracle import plan as OP
 from oracle import response as OR
 from oracle import spectrum as OS
 from oracle import stats as OST
+from oracle import subband as OSB
 
 # Tolerances (normalised powers; candidate exception band).
 P_RTOL = 1e-4           # |P_gpu - P_ref| <= P_RTOL * max(P_ref, 1)
@@ -19,7 +20,10 @@ TIE_RTOL = 1e-4         # ... as may ones whose local-max test meets a neighbour
 def oracle_plane(x_cm, P: OP.Plan, dm_idx: int, cfg, method="direct"):
     ds = int(P.ds_of[dm_idx])
     nv, nfft = P.nv_nfft(dm_idx)
-    s = OD.dedisperse(x_cm, P.delays[dm_idx], P.max_delay, ds)
+    if P.sub is None:
+        s = OD.dedisperse(x_cm, P.delays[dm_idx], P.max_delay, ds)
+    else:
+        s = OSB.dedisperse_subband(x_cm, P.sub, dm_idx, P.max_delay, ds)
     A = OS.half_spectrum(OS.real_series(s, nfft))
     Ap = OS.whiten(A, cfg.whiten_block)
     plane = OR.power_plane(Ap, cfg.zmax, cfg.dz, cfg.halfwidth_extra, method)

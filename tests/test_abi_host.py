@@ -128,6 +128,46 @@ def test_plan_delay_table_bit_exact(L, wl):
         assert (t["nv"], t["nfft"], t["ds"]) == (nv, nfft, int(op.ds_of[i]))
 
 
+@pytest.mark.parametrize("wl,sub", [("drift", (16, 16)), ("drift", (256, 4)), ("pmps", (8, 24)),
+                                    ("small", (1, 1)), ("small", (4, 7))])
+def test_subband_plan_tables_bit_exact(L, wl, sub):
+    shapes = {
+        "small": (64, 1 << 16, 2e-4, 1500.0, 1200.0, [synth.Stage(0.0, 1.0, 101, 1)]),
+        "drift": (256, 1 << 18, 2e-4, 1050.0, 1450.0, [synth.Stage(0.0, 0.5, 1001, 1)]),
+        "pmps": (96, 1 << 23, 2.5e-4, 1230.0, 1518.0, synth.stages_from_table(
+            [(0.0, 200.0, 0.5, 1), (200.0, 600.0, 1.0, 2), (600.0, 2000.0, 5.0, 4)], True)),
+    }
+    nchan, nsamp, ts, lo, hi, stages = shapes[wl]
+    fch0, foff = synth.band(lo, hi, nchan)
+    if wl == "small":
+        foff = -abs(foff)  # descending band
+        fch0 = 1500.0
+    desc = L.FilDesc(nchan, nsamp, ts, fch0, foff, 8 if wl != "pmps" else 1)
+    p = L.Plan(desc, stages, subband=sub)
+    op = OP.Plan(nchan, nsamp, ts, fch0, foff, stages, subband=sub)
+    info = p.subband_info()
+    assert (info["nsub"], info["group"]) == sub
+    np.testing.assert_array_equal(info["group_dm"], op.sub.grp_dm)
+    np.testing.assert_array_equal(info["chan_delays"], op.sub.e)
+    np.testing.assert_array_equal(info["sub_delays"], op.sub.D)
+    np.testing.assert_array_equal(p.delays(), op.delays)
+    assert p.max_delay == op.max_delay
+    for i in (0, p.ndm // 2, p.ndm - 1):
+        t = p.trial(i)
+        nv, nfft = op.nv_nfft(i)
+        assert (t["nv"], t["nfft"], t["ds"]) == (nv, nfft, int(op.ds_of[i]))
+    # an exact plan reports no subbands
+    assert L.Plan(desc, stages).subband_info()["nsub"] == 0
+
+
+def test_subband_plan_rejects_bad_input(L):
+    desc = L.FilDesc(64, 1 << 14, 2e-4, 1202.34375, 4.6875)
+    for sub in ((6, 4), (0, 4), (8, 0), (8, 2000)):
+        with pytest.raises(L.PssError) as e:
+            L.Plan(desc, [synth.Stage(0.0, 1.0, 10, 1)], subband=sub)
+        assert e.value.status == L.PSS_EINVAL
+
+
 def test_plan_rejects_bad_input(L):
     desc = L.FilDesc(64, 1000, 2e-4, 1202.34375, 4.6875)
     with pytest.raises(L.PssError) as e:
