@@ -414,6 +414,7 @@ pss_status enqueue_dedisp(pss_ctx* ctx, const pss_plan* plan, int32_t ck, int64_
     sa.sums = sums;
     sa.spread = SB.spread2;
     sa.b0rel = (int32_t)(b0 - dm_begin);
+    sa.err = (int*)ctx->errflag.p;
     PSS_CUDA(launch_subsum(sa, s));
     return PSS_OK;
 }
@@ -706,7 +707,7 @@ pss_status setup_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fi
             if (P->sub.on) {
                 d.spread = 0;
                 d.sub = sub_batch(plan, P->sub, P->ck, dm_begin, b0, d.nb, st.nv, st.ds);
-                need_subu = std::max(need_subu, (size_t)plan->nsub * d.sub.ngb * d.sub.stride1 * 4);
+                need_subu = std::max(need_subu, (size_t)plan->nsub * d.sub.ngb * d.sub.stride1 * 4 + subsum_slack_bytes(d.sub.spread2));
             } else {
                 d.spread = delay_spread(hd.data() + (size_t)(b0 - dm_begin) * P->ck, d.nb, P->ck);
             }
@@ -1213,7 +1214,7 @@ pss_status pss_dedisperse(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc
             SubBatch SB;
             if (T.on) {
                 SB = sub_batch(plan, T, ck, dm_begin, b0, nb, st.nv, st.ds);
-                PSS_TRY(ctx->subu.ensure((size_t)plan->nsub * SB.ngb * SB.stride1 * 4));
+                PSS_TRY(ctx->subu.ensure((size_t)plan->nsub * SB.ngb * SB.stride1 * 4 + subsum_slack_bytes(SB.spread2)));
             } else {
                 spread = delay_spread(hd.data() + (size_t)(b0 - dm_begin) * ck, nb, ck);
             }
@@ -1269,7 +1270,7 @@ pss_status pss_single_pulse(pss_ctx* ctx, const pss_plan* plan, const pss_fil_de
             SubBatch SB;
             if (T.on) {
                 SB = sub_batch(plan, T, ck, dm_begin, b0, nb, st.nv, st.ds);
-                PSS_TRY(ctx->subu.ensure((size_t)plan->nsub * SB.ngb * SB.stride1 * 4));
+                PSS_TRY(ctx->subu.ensure((size_t)plan->nsub * SB.ngb * SB.stride1 * 4 + subsum_slack_bytes(SB.spread2)));
             } else {
                 spread = delay_spread(hd.data() + (size_t)(b0 - dm_begin) * ck, nb, ck);
             }
@@ -1405,7 +1406,7 @@ pss_status pss_fold(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil,
             SubBatch SB;
             if (T.on) {
                 SB = sub_batch(plan, T, ck, lo_dm, r.a, nb, st.nv, st.ds);
-                PSS_TRY(ctx->subu.ensure((size_t)plan->nsub * SB.ngb * SB.stride1 * 4));
+                PSS_TRY(ctx->subu.ensure((size_t)plan->nsub * SB.ngb * SB.stride1 * 4 + subsum_slack_bytes(SB.spread2)));
             } else {
                 spread = delay_spread(hd.data() + (size_t)(r.a - lo_dm) * ck, nb, ck);
             }
@@ -2079,7 +2080,8 @@ size_t search_footprint(const Plan& plan, const pss_fil_desc* fil, const pss_sea
         if (plan.nsub > 0) {
             // stage-1 rows: groups touched by a batch x subbands x (N_v ds + largest D, padded)
             const int64_t ngb = (B + plan.sub_group - 1) / plan.sub_group + 1;
-            subu = std::max(subu, (size_t)plan.nsub * ngb * ((fil->nsamp + 3) & ~int64_t(3)) * 4);
+            subu = std::max(subu, (size_t)plan.nsub * ngb * ((fil->nsamp + 3) & ~int64_t(3)) * 4 +
+                                      subsum_slack_bytes((int32_t)plan.max_delay));
         }
         need_series = std::max(need_series, (size_t)B * st.nfft * 4);
         need_sums = std::max(need_sums, (size_t)B * 8);

@@ -24,6 +24,7 @@
 //
 // Every wait on the mbarrier is bounded; on expiry the CTA sets the error
 // flag, waits (bounded) for its copies in flight, and exits without writing.
+#include "bulk.cuh"
 #include "pss_internal.h"
 
 namespace pss {
@@ -34,42 +35,6 @@ constexpr int G = 16;            // DM trials per CTA (one per warp)
 constexpr int KW = 8;            // 32-bit words per lane
 constexpr int TN = 32 * 4 * KW;  // native samples per tile (1024)
 constexpr int NT = 32 * G;
-constexpr int WAIT_LIMIT = 1 << 22;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    const uint32_t a = smem_u32(bar);
-    for (int i = 0; i < WAIT_LIMIT; ++i) {
-        uint32_t ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-            : "=r"(ok)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
 
 __device__ __forceinline__ uint32_t madd(uint32_t x, uint32_t one, uint32_t acc) {
     uint32_t r;

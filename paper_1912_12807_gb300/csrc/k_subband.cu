@@ -7,9 +7,14 @@
 // its 16 warps are 16 trials of the group (more trials: further passes).
 // For every subband the samples [t0 + Dmin_b, t0 + TN + Dmax_b) of the
 // group's row, which all of the group's trials read, are staged once in
-// shared memory with coalesced loads; then each warp adds the row at its
-// own offset D_b(i) - Dmin_b (lane l: samples l + 32 j, consecutive words
-// across lanes).  The sums are exact int32.
+// shared memory by one bulk (TMA engine) copy per row, from the 16-byte
+// boundary at or below t0 + Dmin_b, completed on an mbarrier whose wait is
+// bounded (on expiry the CTA sets the error flag and leaves); then each warp
+// adds the row at its own offset D_b(i) - Dmin_b (lane l: samples l + 32 j,
+// consecutive words across lanes).  The sums are exact int32.  Copies may
+// read up to RW samples past a row's end: the stage-1 buffer carries that
+// much slack after its last row.
+#include "bulk.cuh"
 #include "pss_internal.h"
 
 namespace pss {
@@ -24,8 +29,9 @@ constexpr int MAXSB = 64;       // subbands staged per round
 
 template <bool INT_OUT>
 __global__ void __launch_bounds__(NT) k_subsum(const __grid_constant__ SubsumArgs a, int RW, int SBC) {
-    extern __shared__ __align__(16) int32_t sm[];  // [SBC][RW] staged rows; reused by the ds epilogue
-    __shared__ int32_t s_dmin[MAXSB];
+    extern __shared__ __align__(128) int32_t sm[];  // [SBC][RW] staged rows; reused by the ds epilogue
+    __shared__ int32_t s_dmin[MAXSB], s_lead[MAXSB];
+    __shared__ __align__(8) uint64_t s_bar;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int r = blockIdx.y;
     const int2 gr = a.grp[r];
@@ -34,6 +40,12 @@ __global__ void __launch_bounds__(NT) k_subsum(const __grid_constant__ SubsumArg
     const int64_t t0 = (int64_t)blockIdx.x * TN;
     const int32_t* urow = a.u + (int64_t)r * a.u_rowstride;
     const int64_t j0 = t0 / a.ds;
+    if (threadIdx.x == 0) {
+        mbar_init(&s_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t phase = 0;
     for (int p0 = tlo; p0 < thi; p0 += NW) {
         const int pn = min(NW, thi - p0);
         const int my = p0 + warp;
@@ -47,22 +59,31 @@ __global__ void __launch_bounds__(NT) k_subsum(const __grid_constant__ SubsumArg
                 int32_t dmin = a.D[(int64_t)p0 * a.nsub + sb0 + threadIdx.x];
                 for (int k = 1; k < pn; ++k) dmin = min(dmin, a.D[(int64_t)(p0 + k) * a.nsub + sb0 + threadIdx.x]);
                 s_dmin[threadIdx.x] = dmin;
+                // rows are staged from a 16-byte boundary: `lead` samples before t0 + dmin
+                s_lead[threadIdx.x] = (int32_t)((t0 + dmin) & 3);
             }
             __syncthreads();
-            for (int b = 0; b < sbn; ++b) {
-                const int32_t* src = urow + (int64_t)(sb0 + b) * a.u_zstride;
-                const int64_t base = t0 + s_dmin[b];
-                int32_t* dst = sm + (size_t)b * RW;
-                for (int e = threadIdx.x; e < RW; e += NT) {
-                    const int64_t t = base + e;
-                    dst[e] = t < a.u_len ? __ldg(src + t) : 0;
+            // one bulk copy per subband row of RW samples (the group's window plus alignment slack)
+            if (threadIdx.x == 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect_tx(&s_bar, (uint32_t)(sbn * RW * 4));
+                for (int b = 0; b < sbn; ++b) {
+                    const int64_t st = t0 + s_dmin[b] - s_lead[b];
+                    bulk_g2s(sm + (size_t)b * RW, urow + (int64_t)(sb0 + b) * a.u_zstride + st, (uint32_t)(RW * 4),
+                             &s_bar);
                 }
             }
-            __syncthreads();
+            const bool ok = warp == 0 ? mbar_wait(&s_bar, phase) : true;
+            phase ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0 && a.err) atomicExch(a.err, 1);
+                mbar_wait(&s_bar, phase ^ 1u);  // let the copies in flight land before leaving
+                return;
+            }
             if (active) {
                 const int32_t* drow = a.D + (int64_t)my * a.nsub + sb0;
                 for (int b = 0; b < sbn; ++b) {
-                    const int32_t* row = sm + (size_t)b * RW + (drow[b] - s_dmin[b]) + lane;
+                    const int32_t* row = sm + (size_t)b * RW + (drow[b] - s_dmin[b] + s_lead[b]) + lane;
 #pragma unroll
                     for (int j = 0; j < KJ; ++j) acc[j] += row[32 * j];
                 }
@@ -117,7 +138,8 @@ __global__ void __launch_bounds__(NT) k_subsum(const __grid_constant__ SubsumArg
 cudaError_t launch_subsum(const SubsumArgs& a, cudaStream_t s) {
     if (a.nb <= 0 || a.ngrp <= 0) return cudaSuccess;
     if (a.spread < 0 || a.ds < 1 || a.ds > TN || (TN % a.ds) != 0) return cudaErrorInvalidValue;
-    const int RW = TN + a.spread;
+    // window TN + spread, plus up to 3 samples of alignment lead, in whole 16-byte units
+    const int RW = (TN + a.spread + 3 + 3) & ~3;
     // subbands per staging round: about 96 KiB of rows, at least one
     int SBC = (int)((96 * 1024) / ((size_t)RW * 4));
     SBC = std::max(1, std::min(std::min(SBC, MAXSB), a.nsub));

@@ -297,8 +297,11 @@ struct SubsumArgs {
     int64_t out_stride;
     unsigned long long* sums;  // [nb] or null
     int32_t spread;         // max over group rows and subbands of (D max - D min)
+    int* err;               // set to 1 if a bounded wait expires (nullable)
 };
 cudaError_t launch_subsum(const SubsumArgs& a, cudaStream_t s);
+// bytes past the last stage-1 row that stage 2's staging copies may read
+inline size_t subsum_slack_bytes(int32_t spread) { return (size_t)(1024 + spread + 16) * 4; }
 
 // Single-pulse boxcar search (k_single_pulse.cu).
 constexpr int SP_MAXW = 32;         // widths per call
