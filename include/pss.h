@@ -171,6 +171,24 @@ pss_status pss_ctx_profile_read(pss_ctx* ctx, double* ms, int64_t* launches);
  * Errors: PSS_EINVAL for nsamp <= D, empty stages, bad ds. */
 pss_status pss_dd_plan(const pss_fil_desc* fil, const pss_dd_stage* stages, int nstages,
                        pss_plan** out);
+/* Stage rows of an automatic dedispersion plan for [dm_lo, dm_hi) (the
+ * paper builds its plans with DDplan.py, Sect. 3.1, Tables 2-3; this rule is
+ * this library's, from textbook smearing):
+ *   t_chan(DM) = 8.3e-6 * DM * |foff| / nu^3,  t_bw(d) = 8.3e-6 * d * BW / nu^3
+ * (nu = band centre in GHz, BW = nchan*|foff| MHz, seconds).  A nominal
+ * factor v starts at the smallest power of two with v*tsamp >= tres_s
+ * (at most ds_max) and doubles per row; a row starting at d0 downsamples by
+ * ds = min(v, ds_max), takes the largest step s of 1, 2, 3, 5 x 10^k
+ * (0.01 .. 1000) with t_bw(s/2) <= sqrt((ds*tsamp)^2 + t_chan(d0)^2), and
+ * holds n = ceil((end - d0)/s - 1e-9) >= 1 trials, end = min(max(DM_sw,
+ * d0 + s), dm_hi) with t_chan(DM_sw) = 3.5*v*tsamp; the next row starts at
+ * d0 + n*s.  Uses fil's nchan, tsamp_s, fch0_mhz and foff_mhz.
+ * out: host array of cap rows; n_out: rows written, or needed with PSS_ECAP.
+ * Errors: PSS_EINVAL for a bad descriptor or range, ds_max not a power of
+ * two in [1, 1024]. */
+pss_status pss_dd_plan_auto(const pss_fil_desc* fil, double dm_lo, double dm_hi, double tres_s, int32_t ds_max,
+                            pss_dd_stage* out, int32_t cap, int32_t* n_out);
+
 /* A plan for two-stage (subband) dedispersion, the prepsubband scheme the
  * paper calls faster than one prepdata run per DM (Sect. 5).  Same DM grid
  * as pss_dd_plan; its dedispersion (pss_dedisperse and every search call

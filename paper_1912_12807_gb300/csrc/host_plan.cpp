@@ -5,6 +5,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
+#include <vector>
 #include <string>
 
 #include "pss_internal.h"
@@ -173,6 +175,56 @@ pss_status build_subband(Plan* P, int32_t nsub, int32_t group) {
     return set_lengths(P);
 }
 
+// ---- automatic plan (DDplan-like; the paper's Tables 2-3 come from DDplan.py,
+// Sect. 3.1) ------------------------------------------------------------------
+// Smearing terms (nu = band centre in GHz, widths in MHz, seconds):
+//   t_chan(DM) = 8.3e-6 DM dnu / nu^3,   t_bw(d) = 8.3e-6 d BW / nu^3.
+// Nominal factor v starts at the smallest power of two with v tsamp >= tres
+// (capped at ds_max) and doubles per stage; a stage downsamples by
+// min(v, ds_max), takes the largest listed step s with t_bw(s/2) <=
+// sqrt(ts^2 + t_chan(d0)^2), and runs to where t_chan reaches kappa v tsamp
+// (at least one step, at most dm_hi), kappa = 3.5.
+pss_status auto_plan(const pss_fil_desc* fil, double dm_lo, double dm_hi, double tres, int32_t ds_max,
+                     std::vector<pss_dd_stage>* rows) {
+    static const double kSteps[] = {0.01, 0.02, 0.03, 0.05, 0.1, 0.2, 0.3, 0.5, 1.0, 2.0, 3.0, 5.0, 10.0,
+                                    20.0, 30.0, 50.0, 100.0, 200.0, 300.0, 500.0, 1000.0};
+    const double kappa = 3.5;
+    const int nchan = fil->nchan;
+    const double ctr = fil->fch0_mhz + 0.5 * (double)(nchan - 1) * fil->foff_mhz;
+    const double dnu = fabs(fil->foff_mhz), bw = (double)nchan * fabs(fil->foff_mhz);
+    const double nu = ctr / 1000.0;
+    const double kch = 8.3e-6 * dnu / (nu * nu * nu);
+    const double kbw = 8.3e-6 * bw / (nu * nu * nu);
+    int64_t v = 1;
+    while (v < ds_max && (double)v * fil->tsamp_s < tres) v *= 2;
+    double d0 = dm_lo;
+    rows->clear();
+    while (d0 < dm_hi) {
+        if (rows->size() > 4096) return fail(PSS_EINVAL, "pss_dd_plan_auto: more than 4096 rows");
+        const int64_t ds = std::min<int64_t>(v, ds_max);
+        const double ts = (double)ds * fil->tsamp_s;
+        const double tc = kch * d0;
+        const double T = sqrt(ts * ts + tc * tc);
+        double step = kSteps[0];
+        for (double st : kSteps)
+            if (kbw * (0.5 * st) <= T) step = st;
+        const double dsw = kappa * ((double)v * fil->tsamp_s) / kch;
+        const double end = std::min(std::max(dsw, d0 + step), dm_hi);
+        int64_t n = (int64_t)ceil((end - d0) / step - 1e-9);
+        if (n < 1) n = 1;
+        if (n > (int64_t)1 << 30) return fail(PSS_EINVAL, "pss_dd_plan_auto: too many trials in a row");
+        pss_dd_stage r;
+        r.dm_lo = d0;
+        r.dm_step = step;
+        r.n_dm = (int32_t)n;
+        r.ds = (int32_t)ds;
+        rows->push_back(r);
+        d0 = d0 + (double)n * step;
+        if (v < ((int64_t)1 << 40)) v *= 2;
+    }
+    return PSS_OK;
+}
+
 // ---- statistics -----------------------------------------------------------
 // Noise powers are Exp(1); a sum of n of them is Gamma(n, 1) with tail
 // Q(n, S) = exp(-S) sum_{j<n} S^j / j!.  sigma = -Phi^-1(Q).
@@ -264,6 +316,27 @@ double power_threshold(int n, double sigma) {
 }  // namespace pss
 
 extern "C" const char* pss_last_error(void) { return pss::g_err.c_str(); }
+
+extern "C" pss_status pss_dd_plan_auto(const pss_fil_desc* fil, double dm_lo, double dm_hi, double tres_s,
+                                       int32_t ds_max, pss_dd_stage* out, int32_t cap, int32_t* n_out) {
+    if (!fil || !n_out) return pss::fail(PSS_EINVAL, "pss_dd_plan_auto: null argument");
+    *n_out = 0;
+    if (fil->nchan <= 0 || !(fil->tsamp_s > 0) || !(fil->foff_mhz != 0))
+        return pss::fail(PSS_EINVAL, "pss_dd_plan_auto: bad descriptor");
+    if (!(dm_lo >= 0) || !(dm_hi > dm_lo) || !std::isfinite(dm_hi) || !std::isfinite(tres_s))
+        return pss::fail(PSS_EINVAL, "pss_dd_plan_auto: need 0 <= dm_lo < dm_hi, finite");
+    if (ds_max < 1 || ds_max > 1024 || (ds_max & (ds_max - 1)))
+        return pss::fail(PSS_EINVAL, "pss_dd_plan_auto: ds_max must be a power of two in [1, 1024]");
+    const double ctr = fil->fch0_mhz + 0.5 * (double)(fil->nchan - 1) * fil->foff_mhz;
+    if (!(ctr > 0)) return pss::fail(PSS_EINVAL, "pss_dd_plan_auto: band centre must be > 0");
+    std::vector<pss_dd_stage> rows;
+    pss_status st = pss::auto_plan(fil, dm_lo, dm_hi, tres_s, ds_max, &rows);
+    if (st != PSS_OK) return st;
+    *n_out = (int32_t)rows.size();
+    if ((int32_t)rows.size() > cap) return pss::fail(PSS_ECAP, "pss_dd_plan_auto: more rows than cap");
+    if (!rows.empty()) memcpy(out, rows.data(), rows.size() * sizeof(pss_dd_stage));
+    return PSS_OK;
+}
 
 extern "C" double pss_sigma_of_power(int32_t numharm, double power) {
     if (numharm < 1) return 0.0;

@@ -62,7 +62,7 @@ CAND_DTYPE = np.dtype([("dm_idx", "<i4"), ("numharm", "<i4"), ("dm", "<f8"), ("r
                        ("j", "<i4")], align=True)
 
 # every symbol include/pss.h declares
-EXPORTS = ["pss_ctx_create", "pss_ctx_destroy", "pss_last_error", "pss_version", "pss_dd_plan", "pss_dd_plan_subband",
+EXPORTS = ["pss_ctx_create", "pss_ctx_destroy", "pss_last_error", "pss_version", "pss_dd_plan", "pss_dd_plan_auto", "pss_dd_plan_subband",
            "pss_plan_subband_info", "pss_plan_info",
            "pss_plan_trial_info", "pss_plan_free", "pss_dedisperse", "pss_single_pulse", "pss_fold", "pss_spectrum", "pss_power_plane",
            "pss_search_raw", "pss_sift", "pss_search_dm_batch", "pss_response", "pss_sigma_of_power",
@@ -92,6 +92,7 @@ def lib():
         "pss_last_error": (C.c_char_p, []),
         "pss_version": (C.c_char_p, []),
         "pss_dd_plan": (st, [P(pss_fil_desc), P(pss_dd_stage), C.c_int, P(vp)]),
+        "pss_dd_plan_auto": (st, [P(pss_fil_desc), C.c_double, C.c_double, C.c_double, i32, vp, i32, P(i32)]),
         "pss_dd_plan_subband": (st, [P(pss_fil_desc), P(pss_dd_stage), C.c_int, i32, i32, P(vp)]),
         "pss_plan_subband_info": (st, [vp, P(i32), P(i32), P(i64), vp, vp, vp]),
         "pss_plan_info": (st, [vp, P(i64), P(i64), vp, vp]),
@@ -215,6 +216,21 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def pss_dd_plan_auto(desc: "FilDesc", dm_lo: float, dm_hi: float, tres_s: float = 0.0, ds_max: int = 1024):
+    """Automatic plan rows [(dm_lo, dm_step, n_dm, ds)] for the file shape."""
+    cap = 64
+    while True:
+        out = (pss_dd_stage * cap)()
+        n = C.c_int32()
+        st = lib().pss_dd_plan_auto(C.byref(desc.c), float(dm_lo), float(dm_hi), float(tres_s), int(ds_max), out,
+                                    cap, C.byref(n))
+        if st == PSS_ECAP:
+            cap = n.value
+            continue
+        _check(st)
+        return [(out[i].dm_lo, out[i].dm_step, out[i].n_dm, out[i].ds) for i in range(n.value)]
 
 
 class Plan:

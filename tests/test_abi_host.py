@@ -233,3 +233,24 @@ def test_sift_matches_oracle(L, zmax, min_hits, dz):
         assert abs(g["sigma"] - r["sigma"]) < 1e-9 * r["sigma"]
         assert g["dm"] == op.dms[r["dm_idx"]]
         assert abs(g["f_hz"] - r["r"] / op.t_span(r["dm_idx"])) < 1e-12 * g["f_hz"] + 1e-15
+
+
+@pytest.mark.parametrize("fch0,foff,nchan,ts,lo,hi,tres,dsmax", [
+    (1231.5, 3.0, 96, 250e-6, 0.0, 3896.0, 0.0, 1024),
+    (290.125, 0.25, 200, 100e-6, 0.0, 784.4, 0.8e-3, 128),
+    (1450.0, -1.5625, 256, 2e-4, 3.0, 500.0, 0.0, 1024),
+    (1050.78125, 1.5625, 256, 2e-4, 0.0, 1.0, 1e-3, 4)])
+def test_auto_plan_matches_oracle(L, fch0, foff, nchan, ts, lo, hi, tres, dsmax):
+    from oracle import ddplan as ODP
+    desc = L.FilDesc(nchan, 1 << 20, ts, fch0, foff)
+    got = L.pss_dd_plan_auto(desc, lo, hi, tres, dsmax)
+    ref = ODP.auto_plan(fch0, foff, nchan, ts, lo, hi, tres=tres, ds_max=dsmax)
+    assert got == [(float(a), float(b), int(c), int(d)) for a, b, c, d in ref]
+
+
+def test_auto_plan_rejects_bad_input(L):
+    desc = L.FilDesc(64, 1 << 16, 2e-4, 1200.0, 4.6875)
+    for args in ((10.0, 5.0, 0.0, 8), (-1.0, 5.0, 0.0, 8), (0.0, 5.0, 0.0, 3), (0.0, 5.0, 0.0, 2048)):
+        with pytest.raises(L.PssError) as e:
+            L.pss_dd_plan_auto(desc, *args)
+        assert e.value.status == L.PSS_EINVAL
