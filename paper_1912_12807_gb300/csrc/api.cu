@@ -230,6 +230,7 @@ pss_status setup_input(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* f
     if (!same) {
         PSS_CUDA(cudaStreamSynchronize(s));  // `host` is about to go out of scope
         ctx->delays_host.swap(host);
+        ctx->delays_gen++;
     }
     *ck_out = ck;
     *pitch_out = pitch;
@@ -647,20 +648,73 @@ int64_t batch_trials(int64_t nfft, int nz, Mode mode, int64_t n) {
 // device buffer at its final size, templates and twiddles.  After this the
 // kernel sequence (enqueue_path) allocates nothing and never waits on the
 // host, so it can be captured into a CUDA graph.
+// The last set-up of a context, reused while the request is byte-for-byte
+// the same (plan, file shape and mask, search parameters, trials, mode,
+// capacity, tuning) and the device tables are still the ones uploaded for it:
+// the host tables, batch list and launch sizes are then not rebuilt.
+struct PathCache {
+    std::string key;
+    uint64_t gen = 0;
+    PathSetup P;
+    size_t need[6] = {0, 0, 0, 0, 0, 0};
+};
+
+template <class T>
+void key_put(std::string* k, const T& v) {
+    k->append(reinterpret_cast<const char*>(&v), sizeof(T));
+}
+
+std::string path_key(const pss_plan* plan, const pss_fil_desc* fil, const pss_search_cfg* cfg, int64_t dm_begin,
+                     int64_t dm_end, Mode mode, int64_t dev_cap, int64_t max_b, const Tune& t) {
+    std::string k;
+    key_put(&k, plan->id);
+    key_put(&k, fil->nchan);
+    key_put(&k, fil->nbits);
+    key_put(&k, fil->nsamp);
+    key_put(&k, fil->tsamp_s);
+    key_put(&k, fil->fch0_mhz);
+    key_put(&k, fil->foff_mhz);
+    key_put(&k, fil->layout);
+    if (fil->chan_mask) k.append(reinterpret_cast<const char*>(fil->chan_mask), (size_t)fil->nchan);
+    else k.push_back('\1');
+    key_put(&k, *cfg);
+    key_put(&k, dm_begin);
+    key_put(&k, dm_end);
+    key_put(&k, (int)mode);
+    key_put(&k, dev_cap);
+    key_put(&k, max_b);
+    key_put(&k, t.fft_variant);
+    key_put(&k, t.harm_run);
+    key_put(&k, t.dedisp_kb);
+    key_put(&k, t.whiten_form);
+    key_put(&k, t.fused);
+    key_put(&k, t.plane_form);
+    return k;
+}
+
 pss_status setup_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil, const pss_search_cfg* cfg,
                       int64_t dm_begin, int64_t dm_end, Mode mode, cudaStream_t s, int64_t dev_cap, PathSetup* P,
                       int64_t max_b = 0) {
-    PSS_TRY(setup_input(ctx, plan, fil, dm_begin, dm_end, s, &P->ck, &P->pitch, &P->sub));
-    P->batches.clear();
-    P->harm.clear();
+    std::string key = path_key(plan, fil, cfg, dm_begin, dm_end, mode, dev_cap, max_b, ctx->tune);
+    PathCache* pc = static_cast<PathCache*>(ctx->path_cache.get());
+    const bool hit = pc && pc->gen == ctx->delays_gen && pc->key == key && dm_end > dm_begin;
+    if (hit) {
+        *P = pc->P;
+    } else {
+        PSS_TRY(setup_input(ctx, plan, fil, dm_begin, dm_end, s, &P->ck, &P->pitch, &P->sub));
+    }
+    if (!hit) {
+        P->batches.clear();
+        P->harm.clear();
+    }
     P->dev_cap = dev_cap;
     if (dm_end == dm_begin) return PSS_OK;
     PSS_TRY(ensure_templates(ctx, cfg, s));
     P->nz = nz_of(cfg);
     P->Z = cfg->zmax ? (int)llround(cfg->zmax / cfg->dz) : 0;
     P->nstages = (int)log2((double)cfg->numharm) + 1;
-    const std::vector<int32_t> hd =
-        P->sub.on ? std::vector<int32_t>() : compact_delays(plan, kept_channels(fil), dm_begin, dm_end);
+    const std::vector<int32_t> hd = (hit || P->sub.on) ? std::vector<int32_t>()
+                                                       : compact_delays(plan, kept_channels(fil), dm_begin, dm_end);
     if (mode == MODE_SEARCH) {
         PSS_TRY(ctx->cands.ensure((size_t)dev_cap * sizeof(pss_raw_cand)));
         PSS_TRY(ctx->counter.ensure(sizeof(unsigned long long)));
@@ -677,7 +731,14 @@ pss_status setup_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fi
         if (st.n_dm > 0) PSS_TRY(ensure_passtw(ctx, st.nfft / 2, ctx->tune.fft_variant, s));
     size_t need_series = 0, need_fft = 0, need_sums = 0, need_plane = 0, need_subu = 0;
     int64_t out_off = 0;
-    for (size_t si = 0; si < plan->stages.size(); ++si) {
+    if (hit) {
+        need_series = pc->need[0];
+        need_fft = pc->need[1];
+        need_sums = pc->need[2];
+        need_plane = pc->need[3];
+        need_subu = pc->need[4];
+    }
+    for (size_t si = 0; si < plan->stages.size() && !hit; ++si) {
         const StageInfo& st = plan->stages[si];
         const int64_t lo = std::max<int64_t>(dm_begin, st.first);
         const int64_t hi = std::min<int64_t>(dm_end, st.first + st.n_dm);
@@ -723,6 +784,18 @@ pss_status setup_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fi
     PSS_TRY(ctx->fftB.ensure(need_fft));
     if (mode != MODE_SPECTRUM) PSS_TRY(ctx->spec.ensure(need_fft));
     if (mode == MODE_SEARCH) PSS_TRY(ctx->plane.ensure(need_plane));
+    if (!hit) {
+        auto c = std::make_shared<PathCache>();
+        c->key.swap(key);
+        c->gen = ctx->delays_gen;
+        c->P = *P;
+        c->need[0] = need_series;
+        c->need[1] = need_fft;
+        c->need[2] = need_sums;
+        c->need[3] = need_plane;
+        c->need[4] = need_subu;
+        ctx->path_cache = c;
+    }
     return PSS_OK;
 }
 
@@ -902,10 +975,11 @@ pss_status check_errflag(pss_ctx* ctx, cudaStream_t s) {
     return PSS_OK;
 }
 
-// Trials per DM batch of a pipelined search of n trials: four batches (at
-// least 64 trials each), so that the host sift of all but the last overlaps
-// the device work.
-int64_t pipeline_batch(int64_t n) { return n >= 256 ? (n + 3) / 4 : (n >= 64 ? (n + 1) / 2 : 0); }
+// Trials per DM batch of a pipelined search of n trials: three batches of
+// 30 % and a last one of about 10 % (at least 256 trials in all), so that
+// the host sift of all but the last overlaps the device work and the sift
+// left after the device finishes is short; two batches from 64 trials.
+int64_t pipeline_batch(int64_t n) { return n >= 256 ? (3 * n + 9) / 10 : (n >= 64 ? (n + 1) / 2 : 0); }
 
 // Events and pinned count slots for n DM batches, and a stream for downloads.
 pss_status ensure_snapshots(pss_ctx* ctx, int n) {
@@ -961,7 +1035,15 @@ pss_status drain_batches(pss_ctx* ctx, const pss_plan* plan, const pss_search_cf
                                      (size_t)(cnt - prev) * sizeof(pss_raw_cand), cudaMemcpyDeviceToHost,
                                      ctx->stream2));
             PSS_CUDA(cudaStreamSynchronize(ctx->stream2));
+            const size_t old = surv->size();
             PSS_TRY(sift_within(*plan, *cfg, ctx->raw_pinned, (int64_t)(cnt - prev), surv));
+            if (cfg->zmax == 0) {
+                // keep the survivors ordered by r (stable) while the device works on,
+                // so the across-trial linkage after the last batch needs no sort
+                auto by_r = [](const SiftItem& a, const SiftItem& b) { return a.kr < b.kr; };
+                std::stable_sort(surv->begin() + old, surv->end(), by_r);
+                std::inplace_merge(surv->begin(), surv->begin() + old, surv->end(), by_r);
+            }
         }
         prev = cnt;
     }

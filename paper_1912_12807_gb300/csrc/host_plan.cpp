@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <vector>
 #include <string>
@@ -46,6 +47,8 @@ static pss_status set_lengths(Plan* P) {
 }
 
 pss_status build_plan(const pss_fil_desc* fil, const pss_dd_stage* st, int nst, Plan* P) {
+    static std::atomic<uint64_t> next_id{1};
+    P->id = next_id.fetch_add(1);
     if (!fil || !st || nst <= 0) return fail(PSS_EINVAL, "pss_dd_plan: null descriptor or no stages");
     if (fil->nchan <= 0 || fil->nsamp <= 0) return fail(PSS_EINVAL, "pss_dd_plan: nchan and nsamp must be > 0");
     if (!(fil->tsamp_s > 0)) return fail(PSS_EINVAL, "pss_dd_plan: tsamp_s must be > 0");

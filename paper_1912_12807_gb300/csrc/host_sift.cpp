@@ -77,16 +77,27 @@ Groups link_groups(const std::vector<Item>& it, double /*dz*/) {
     for (int i = 1; i < n && one_row; ++i) one_row = it[i].kz == it[0].kz;
     if (one_row) {
         // all z equal (zmax = 0): sort by r; consecutive items closer than
-        // one bin link, so groups are the runs of the sorted order
+        // one bin link, so groups are the runs of the sorted order (items
+        // that arrive sorted by r, as the pipelined search keeps them, skip
+        // the sort)
         Groups G;
-        std::vector<uint64_t> key(n);
-        for (int i = 0; i < n; ++i) key[i] = ((uint64_t)it[i].kr << 32) | (uint32_t)i;
-        std::sort(key.begin(), key.end());
         G.members.resize(n);
         G.start.push_back(0);
-        for (int p = 0; p < n; ++p) {
-            G.members[p] = (int)(key[p] & 0xFFFFFFFFu);
-            if (p > 0 && (int64_t)(key[p] >> 32) - (int64_t)(key[p - 1] >> 32) > 64) G.start.push_back(p);
+        bool sorted = true;
+        for (int i = 1; i < n && sorted; ++i) sorted = it[i - 1].kr <= it[i].kr;
+        if (sorted) {
+            for (int p = 0; p < n; ++p) {
+                G.members[p] = p;
+                if (p > 0 && it[p].kr - it[p - 1].kr > 64) G.start.push_back(p);
+            }
+        } else {
+            std::vector<uint64_t> key(n);
+            for (int i = 0; i < n; ++i) key[i] = ((uint64_t)it[i].kr << 32) | (uint32_t)i;
+            std::sort(key.begin(), key.end());
+            for (int p = 0; p < n; ++p) {
+                G.members[p] = (int)(key[p] & 0xFFFFFFFFu);
+                if (p > 0 && (int64_t)(key[p] >> 32) - (int64_t)(key[p - 1] >> 32) > 64) G.start.push_back(p);
+            }
         }
         G.start.push_back(n);
         if (n == 0) G.start.resize(1);
@@ -351,17 +362,24 @@ pss_status sift_across(const Plan& P, const pss_search_cfg& cfg, std::vector<Sif
     };
     const Groups G = link_groups(survivors, cfg.dz);
     lap("link");
-    for (int g = 0; g < G.count(); ++g) {
+    // one representative per group, groups in parallel (each writes its own slot)
+    const int ng = G.count();
+    std::vector<pss_cand> reps((size_t)ng);
+    std::vector<char> keep((size_t)ng, 0);
+    parallel_for(ng, 64, [&](int64_t g) {
         const int* mem = G.members.data() + G.start[g];
         const int nm = G.start[g + 1] - G.start[g];
         const int best = pick_rep(survivors, mem, nm, true);
-        std::vector<int32_t> dms;
-        for (int q = 0; q < nm; ++q) dms.push_back(survivors[mem[q]].dm_idx);
-        std::sort(dms.begin(), dms.end());
-        int hits = (int)(std::unique(dms.begin(), dms.end()) - dms.begin());
-        if (hits < cfg.min_dm_hits) continue;
+        int hits = 1;
+        if (nm > 1) {
+            std::vector<int32_t> dms((size_t)nm);
+            for (int q = 0; q < nm; ++q) dms[(size_t)q] = survivors[mem[q]].dm_idx;
+            std::sort(dms.begin(), dms.end());
+            hits = (int)(std::unique(dms.begin(), dms.end()) - dms.begin());
+        }
+        if (hits < cfg.min_dm_hits) return;
         const Item& b = survivors[best];
-        pss_cand c;
+        pss_cand& c = reps[(size_t)g];
         c.dm_idx = b.dm_idx;
         c.numharm = b.n;
         c.dm = P.dms[b.dm_idx];
@@ -373,8 +391,10 @@ pss_status sift_across(const Plan& P, const pss_search_cfg& cfg, std::vector<Sif
         c.dm_hits = hits;
         c.h = b.h;
         c.j = b.j;
-        out->push_back(c);
-    }
+        keep[(size_t)g] = 1;
+    });
+    for (int g = 0; g < ng; ++g)
+        if (keep[(size_t)g]) out->push_back(reps[(size_t)g]);
     lap("reps");
     std::sort(out->begin(), out->end(), [](const pss_cand& a, const pss_cand& b) {
         if (a.dm_idx != b.dm_idx) return a.dm_idx < b.dm_idx;

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <atomic>
 #include <functional>
+#include <memory>
 #include <string>
 #include <thread>
 #include <vector>
@@ -50,6 +51,7 @@ struct Plan {
     std::vector<int32_t> stage_of;
     std::vector<int32_t> delays;  // [ndm][nchan]
     int64_t max_delay = 0;        // D (or D' of the two-stage scheme)
+    uint64_t id = 0;              // unique per plan built in this process
     // two-stage (subband) scheme; nsub == 0: exact shift-and-sum
     int32_t nsub = 0, sub_group = 0, sub_S = 0;
     std::vector<double> fsub;        // [nsub] reference frequency of each subband
@@ -154,6 +156,8 @@ struct Ctx {
     DevBuf sp_ev;        // SpRaw detections
     DevBuf fold_buf;     // folding items and outputs
     std::vector<int32_t> delays_host;  // what delays_dev holds (keep list + delays), empty if unknown
+    uint64_t delays_gen = 0;           // bumped whenever delays_dev is rewritten
+    std::shared_ptr<void> path_cache;  // last search set-up (api.cu), valid while delays_gen matches
     DevBuf series;       // float [B][nfft]
     DevBuf sums;         // unsigned long long [B]
     DevBuf fftA, fftB;   // float2 [B][M]
