@@ -479,7 +479,9 @@ size_t pss_batch_footprint(const pss_batch* b);
  * fft_split: FFT pass-split variant (0 = even split), harm_run: points per
  * lane of the harmonic sum (16 or 8), dedisp_kb: shared memory for staged
  * channel chunks (KiB), whiten_form: whitening median per CTA (0), per
- * warp (1) or by size (-1: per warp up to 2^18 bins), fused: for zmax 0 and nfft 2^18, FFT + whitening + plane in one
+ * warp (1), per pair of warps (2) or the default (-1: the pair form for
+ * blocks of 256-1024 bins, else per CTA), fused: for zmax 0 and nfft 2^18,
+ * FFT + whitening + plane in one
  * thread-block-cluster launch (1) or as separate kernels (0); the fused
  * path is used only where the device can run 16-CTA clusters.  Pointers
  * are nullable. */

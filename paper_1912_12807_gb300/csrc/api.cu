@@ -851,7 +851,7 @@ pss_status enqueue_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* 
             fa.tw = (const float2*)ctx->twid.p;
             fa.twM = ctx->twid_n;
             fa.fft_variant = ctx->tune.fft_variant;
-            fa.whiten_form = ctx->tune.whiten_form >= 0 ? ctx->tune.whiten_form : (M <= (int64_t(1) << 18) ? 1 : 0);
+            fa.whiten_form = ctx->tune.whiten_form >= 0 ? ctx->tune.whiten_form : 2;
             set_passtw(ctx, &fa);
             fa.whiten = 1;
             fa.gains_out = nullptr;
@@ -1148,6 +1148,8 @@ pss_status pss_ctx_create(int device, pss_ctx** out) {
     if (const char* f = getenv("PSS_FUSED")) c->tune.fused = f[0] == '1';
     // PSS_PLANE_FORM=0 / 1: the radix 8-8-8-4 / 16-16-8 overlap-save plane kernel
     if (const char* f = getenv("PSS_PLANE_FORM")) c->tune.plane_form = f[0] == '1';
+    // PSS_WHITEN_FORM=0 / 1 / 2: block per CTA / warp per block / warp pair per block
+    if (const char* f = getenv("PSS_WHITEN_FORM")) c->tune.whiten_form = (f[0] >= '0' && f[0] <= '2') ? f[0] - '0' : -1;
     *out = c;
     return PSS_OK;
 }
@@ -1966,7 +1968,7 @@ pss_status autotune(pss_ctx* ctx, const Plan& plan, const pss_fil_desc* fil, con
             return fail(PSS_EINVAL, "PSS_TUNE value out of range");
         int rad[4];
         if (fft_pass_plan(plan.stages[0].nfft / 2, t.fft_variant, rad) == 0 || (t.harm_run != 8 && t.harm_run != 16) ||
-            t.dedisp_kb < 16 || t.dedisp_kb > 200 || t.whiten_form < -1 || t.whiten_form > 1)
+            t.dedisp_kb < 16 || t.dedisp_kb > 200 || t.whiten_form < -1 || t.whiten_form > 2)
             return fail(PSS_EINVAL, "PSS_TUNE value out of range");
         ctx->tune = t;
         return PSS_OK;
@@ -2033,7 +2035,7 @@ pss_status autotune(pss_ctx* ctx, const Plan& plan, const pss_fil_desc* fil, con
         else ctx->tune.fused = 0;
         if (st == PSS_OK && !ctx->tune.fused) {
             st = sweep(&ctx->tune.fft_variant, fv, 1u << 2, "fft split");
-            if (st == PSS_OK) st = sweep(&ctx->tune.whiten_form, {0, 1}, 1u << 3, "whiten");
+            if (st == PSS_OK) st = sweep(&ctx->tune.whiten_form, {0, 1, 2}, 1u << 3, "whiten");
         } else {
             ctx->tune.whiten_form = 0;  // not used by the fused kernel
         }

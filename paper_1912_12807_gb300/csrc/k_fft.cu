@@ -442,6 +442,40 @@ __global__ void __launch_bounds__(32 * WW) k_whiten_warp(const float2* Zall, int
     whiten_block<VPL>(A, k0, lane, k0 == 0 ? W - 1 : W, s_hist[wq], s_cand[wq], s_cpos[wq], whiten, g, O + k0);
 }
 
+// Pairs of warps per block of W = 64 VPL bins (whiten_block_pair): half the
+// registers per thread of the one-warp form, so twice the warps per SM.
+constexpr int WP = 4;  // pairs per CTA
+
+template <int VPL>
+__global__ void __launch_bounds__(64 * WP) k_whiten_pair(const float2* Zall, int64_t z_stride, int64_t M,
+                                                        float2* out, int64_t out_stride, const float2* tw,
+                                                        int64_t twM, int whiten, float* gains,
+                                                        int64_t gains_stride) {
+    constexpr int W = 64 * VPL;
+    __shared__ uint32_t s_sh[WP][NBIN + 2 * NCAND + 8];
+    const int lane = threadIdx.x & 31, pr = threadIdx.x >> 6, h = (threadIdx.x >> 5) & 1;
+    const int64_t blk = (int64_t)blockIdx.x * WP + pr;
+    if (blk >= M / W) return;  // both warps of a pair leave together
+    const int b = blockIdx.y;
+    const int64_t k0 = blk * W;
+    const float2* Z = Zall + (int64_t)b * z_stride;
+    float2* O = out + (int64_t)b * out_stride;
+    const int64_t wstride = twM / (2 * M);  // exp(-2 pi i k / nfft)
+    float2 A[VPL];
+#pragma unroll
+    for (int i = 0; i < VPL; ++i) {
+        const int64_t k = k0 + h * 32 * VPL + lane + 32 * i;
+        A[i] = r2c_bin(Z[k], Z[(M - k) & (M - 1)], tw[k * wstride], k);
+    }
+    if (!whiten && !gains) {
+#pragma unroll
+        for (int i = 0; i < VPL; ++i) O[k0 + h * 32 * VPL + lane + 32 * i] = A[i];
+        return;
+    }
+    float* g = gains ? gains + (int64_t)b * gains_stride + blk : nullptr;
+    whiten_block_pair<VPL>(A, k0, h, lane, k0 == 0 ? W - 1 : W, s_sh[pr], 1 + pr, whiten, g, O + k0);
+}
+
 // Pass radices of an M-point FFT, M = 2^L: the fewest passes of radix
 // 2^5 .. 2^10 (ceil(L / 10)); variant 0 splits L evenly, larger parts
 // first; variants 1.. are the other splits of L into that many parts within
@@ -545,6 +579,20 @@ cudaError_t launch_fft_whiten(const FftArgs& a, cudaStream_t s, Ctx* prof_ctx) {
     }
     const int W = a.whiten_block;
     if (W < 64 || W > 4096 || (W & (W - 1)) != 0 || M % W != 0) return cudaErrorInvalidValue;
+    if (a.whiten_form == 2 && (W == 1024 || W == 512 || W == 256)) {
+        dim3 g2((unsigned)((M / W + WP - 1) / WP), (unsigned)a.nb);
+        ProfScope ps(prof_ctx, 3, s);
+        if (W == 1024)
+            k_whiten_pair<16><<<g2, 64 * WP, 0, s>>>(in, M, M, a.spec_out, a.spec_stride, a.tw, a.twM, a.whiten,
+                                                     a.gains_out, a.gains_stride);
+        else if (W == 512)
+            k_whiten_pair<8><<<g2, 64 * WP, 0, s>>>(in, M, M, a.spec_out, a.spec_stride, a.tw, a.twM, a.whiten,
+                                                    a.gains_out, a.gains_stride);
+        else
+            k_whiten_pair<4><<<g2, 64 * WP, 0, s>>>(in, M, M, a.spec_out, a.spec_stride, a.tw, a.twM, a.whiten,
+                                                    a.gains_out, a.gains_stride);
+        return cudaGetLastError();
+    }
     if (a.whiten_form == 1 && (W == 1024 || W == 512 || W == 256)) {
         dim3 g2((unsigned)((M / W + WW - 1) / WW), (unsigned)a.nb);
         ProfScope ps(prof_ctx, 3, s);

@@ -138,7 +138,7 @@ struct Tune {
     int fft_variant = 0;   // FFT pass split
     int harm_run = 8;      // harmonic-sum points per lane
     int dedisp_kb = 96;    // dedispersion chunk staging budget
-    int whiten_form = -1;  // whitening kernel form (-1: by size, warp-per-block up to 2^18 bins)
+    int whiten_form = -1;  // whitening kernel form (-1: default, the warp pair per block)
     int fused = 0;         // zmax 0, nfft 2^18: cluster-fused FFT + whitening + plane (where the device allows)
     int plane_form = 1;    // overlap-save plane kernel form (1: radix 16-16-8, 0: radix 8-8-8-4)
 };
@@ -380,7 +380,7 @@ struct FftArgs {
     int64_t gains_stride;
     const float2* ptw[4];             // inter-pass twiddle tables of passes 1.. (fft_pass_plan)
     int32_t fft_variant;              // pass split (fft_pass_plan variant)
-    int32_t whiten_form;              // 0: block-per-CTA median, 1: warp-per-block median
+    int32_t whiten_form;              // 0: block-per-CTA median, 1: warp-per-block, 2: warp pair per block
 };
 cudaError_t launch_twiddles(float2* tw, int64_t n, cudaStream_t s);
 // Radices of the passes of an M-point FFT for split `variant` (0 = default);

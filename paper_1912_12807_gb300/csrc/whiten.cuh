@@ -160,4 +160,131 @@ __device__ __forceinline__ void whiten_block(float2 (&A)[VPL], int64_t k0, int l
     for (int i = 0; i < VPL; ++i) Oblk[lane + 32 * i] = make_float2(A[i].x * scale, A[i].y * scale);
 }
 
+// The same block whitening by a pair of warps (h = 0, 1) that share one
+// histogram: lane l of warp h holds bins k0 + h*32*VPL + l + 32 i.  The
+// selected element, the scale and the output are those of whiten_block on
+// the same 2*32*VPL bins (positions h*32*VPL + l + 32 i order ties the same
+// way).  The pair synchronises with named barrier `bar` (64 threads).
+// sh: NBIN + 2*NCAND + 8 words of shared memory for the pair.
+__device__ __forceinline__ void pair_sync(int bar) { asm volatile("bar.sync %0, 64;" ::"r"(bar) : "memory"); }
+
+template <int VPL>
+__device__ __forceinline__ void whiten_block_pair(float2 (&A)[VPL], int64_t k0, int h, int lane, int m, uint32_t* sh,
+                                                  int bar, int whiten, float* gain_out, float2* Oblk) {
+    uint32_t* hist = sh;
+    uint32_t* cand = sh + NBIN;
+    uint32_t* cpos = cand + NCAND;
+    uint32_t* misc = cpos + NCAND;  // [0] warp-0 total, [1] bin, [2] rank, [3] slots, [4] value, [5] scale bits
+    const int t = h * 32 + lane;     // 0..63
+    auto keyof = [&](int i) -> uint32_t {
+        return (k0 == 0 && t == 0 && i == 0) ? 0xFFFFFFFFu : __float_as_uint(A[i].x * A[i].x + A[i].y * A[i].y);
+    };
+    for (int i = t; i < NBIN; i += 64) hist[i] = 0u;
+    if (t == 0) misc[3] = 0u;
+    pair_sync(bar);
+#pragma unroll
+    for (int i = 0; i < VPL; ++i) {
+        const uint32_t kk = keyof(i);
+        if (kk != 0xFFFFFFFFu) atomicAdd(&hist[kk >> 20], 1u);
+    }
+    pair_sync(bar);
+    const uint32_t rank0 = (uint32_t)((m - 1) / 2);
+    // thread t owns bins [t * BPT, (t+1) * BPT)
+    constexpr int BPT = NBIN / 64;
+    uint32_t tot = 0;
+#pragma unroll 8
+    for (int i = 0; i < BPT; ++i) tot += hist[t * BPT + i];
+    uint32_t incl = tot;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+    }
+    if (h == 0 && lane == 31) misc[0] = incl;
+    pair_sync(bar);
+    if (h == 1) incl += misc[0];
+    const uint32_t before0 = incl - tot;
+    if (rank0 >= before0 && rank0 < incl) {
+        uint32_t before = before0;
+        for (int i = 0; i < BPT; ++i) {
+            const uint32_t c = hist[t * BPT + i];
+            if (rank0 < before + c) {
+                misc[1] = (uint32_t)(t * BPT + i);
+                misc[2] = rank0 - before;
+                break;
+            }
+            before += c;
+        }
+    }
+    pair_sync(bar);
+    const uint32_t bin = misc[1], rank = misc[2];
+    const uint32_t nin = hist[bin];
+    if (nin <= (uint32_t)NCAND) {
+#pragma unroll
+        for (int i = 0; i < VPL; ++i) {
+            const uint32_t kk = keyof(i);
+            if (kk != 0xFFFFFFFFu && (kk >> 20) == bin) {
+                const uint32_t slot = atomicAdd(&misc[3], 1u);
+                cand[slot] = kk;
+                cpos[slot] = (uint32_t)(h * 32 * VPL + lane + 32 * i);
+            }
+        }
+        pair_sync(bar);
+        for (uint32_t c = t; c < nin; c += 64) {
+            const uint32_t v = cand[c], pv = cpos[c];
+            uint32_t r = 0;
+            for (uint32_t q = 0; q < nin; ++q) {
+                const uint32_t u = cand[q];
+                r += (u < v) || (u == v && cpos[q] < pv);
+            }
+            if (r == rank) misc[4] = v;
+        }
+    } else {
+        // many values share the top bits: radix rounds on bits 19..0 (8, 8, 4)
+        uint32_t prefix = bin << 20, mask = 0xFFF00000u, rk = rank;
+#pragma unroll
+        for (int pass = 0; pass < 3; ++pass) {
+            const int shift = pass == 0 ? 12 : (pass == 1 ? 4 : 0);
+            const uint32_t dmask = pass == 2 ? 15u : 255u;
+            pair_sync(bar);
+            for (int i = t; i < 256; i += 64) hist[i] = 0u;
+            pair_sync(bar);
+#pragma unroll
+            for (int i = 0; i < VPL; ++i) {
+                const uint32_t kk = keyof(i);
+                if (kk != 0xFFFFFFFFu && (kk & mask) == prefix) atomicAdd(&hist[(kk >> shift) & dmask], 1u);
+            }
+            pair_sync(bar);
+            if (t == 0) {
+                uint32_t before = 0;
+                for (uint32_t d = 0; d <= dmask; ++d) {
+                    if (rk < before + hist[d]) {
+                        misc[1] = d;
+                        misc[2] = rk - before;
+                        break;
+                    }
+                    before += hist[d];
+                }
+            }
+            pair_sync(bar);
+            prefix |= misc[1] << shift;
+            mask |= dmask << shift;
+            rk = misc[2];
+        }
+        if (t == 0) misc[4] = prefix;
+    }
+    pair_sync(bar);
+    // scale sqrt(ln 2 / med) and gain ln 2 / med in FP64, once per pair (FP64 is slow)
+    if (t == 0) {
+        const float med = __uint_as_float(misc[4]);
+        const double g = med > 0.f ? 0.69314718055994530942 / (double)med : 0.0;
+        misc[5] = __float_as_uint(whiten ? (float)sqrt(g) : 1.f);
+        if (gain_out) *gain_out = (float)g;
+    }
+    pair_sync(bar);
+    const float scale = __uint_as_float(misc[5]);
+#pragma unroll
+    for (int i = 0; i < VPL; ++i) Oblk[h * 32 * VPL + lane + 32 * i] = make_float2(A[i].x * scale, A[i].y * scale);
+}
+
 }  // namespace pss

@@ -195,14 +195,16 @@ def test_alternate_launch_shapes_are_exact(L, ctx, monkeypatch):
     # 16 points per lane in the harmonic sum, a 64 KiB dedispersion chunk budget
     # and the warp-per-block whitening median: the same arithmetic, the same bytes
     for case in (_case_a(1001), _case_b()):
-        monkeypatch.setenv("PSS_TUNE", "0,16,64,1,0")
-        plan = L.Plan(L.FilDesc.of(case.fil), case.stages)
-        b = L.Batch(plan, L.cfg_of(case.cfg))
-        assert b.tuning == {"fft_split": 0, "harm_run": 16, "dedisp_kb": 64, "whiten_form": 1, "fused": 0}
-        got = b.run(case.fil.data)
-        b.close()
-        monkeypatch.delenv("PSS_TUNE")
-        assert _same(got, _alone(L, ctx, case))
+        for pin, form in (("0,16,64,1,0", 1), ("0,8,96,2,0", 2), ("0,8,96,0,0", 0)):
+            # the warp-pair (2) and block (0) whitening forms select the same median
+            monkeypatch.setenv("PSS_TUNE", pin)
+            plan = L.Plan(L.FilDesc.of(case.fil), case.stages)
+            b = L.Batch(plan, L.cfg_of(case.cfg))
+            assert b.tuning["whiten_form"] == form
+            got = b.run(case.fil.data)
+            b.close()
+            monkeypatch.delenv("PSS_TUNE")
+            assert _same(got, _alone(L, ctx, case)), pin
     monkeypatch.setenv("PSS_TUNE", "0,7,64,1")
     with pytest.raises(L.PssError):
         L.Batch(L.Plan(L.FilDesc.of(_case_a().fil), _case_a().stages), L.cfg_of(_case_a().cfg))
@@ -216,7 +218,7 @@ def test_autotuned_batch_and_server(L, ctx, monkeypatch):
     b = L.Batch(plan, cfg)
     t = b.tuning
     assert t["harm_run"] in (8, 16) and t["dedisp_kb"] in (64, 96) and t["fft_split"] >= 0
-    assert t["whiten_form"] in (0, 1)
+    assert t["whiten_form"] in (0, 1, 2)
     got, ref = b.run(a.fil.data), _alone(L, ctx, a)
     # same detections; powers within the parity tolerance of the untuned search
     key = lambda x: set(zip(x["dm_idx"].tolist(), x["numharm"].tolist(), x["h"].tolist(), x["j"].tolist()))
