@@ -1037,6 +1037,14 @@ pss_status drain_batches(pss_ctx* ctx, const pss_plan* plan, const pss_search_cf
             PSS_CUDA(cudaStreamSynchronize(ctx->stream2));
             const size_t old = surv->size();
             PSS_TRY(sift_within(*plan, *cfg, ctx->raw_pinned, (int64_t)(cnt - prev), surv));
+            // sigma of each survivor now, while the device works (the across-trial
+            // representatives need it after the last batch)
+            SiftItem* nw = surv->data() + old;
+            parallel_for((int64_t)(surv->size() - old), 256, [&](int64_t i) {
+                SiftItem& x = nw[i];
+                x.logp = log_q(x.n, (double)x.power);
+                x.sigma = sigma_from_logp(x.logp);
+            });
             if (cfg->zmax == 0) {
                 // keep the survivors ordered by r (stable) while the device works on,
                 // so the across-trial linkage after the last batch needs no sort
