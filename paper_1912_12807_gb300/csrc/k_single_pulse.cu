@@ -17,6 +17,8 @@
 // prefix sum (so every B_w the tile and its local-maximum windows need is
 // one subtraction), then tests every (t, w).  Detections are appended
 // with an atomic counter; past `cap` they are only counted.
+#include <limits.h>
+
 #include "pss_internal.h"
 
 namespace pss {
@@ -48,7 +50,7 @@ __global__ void __launch_bounds__(NT) k_sp_moments(const int32_t* __restrict__ s
 
 __global__ void __launch_bounds__(NT) k_sp_detect(const __grid_constant__ SpArgs a) {
     extern __shared__ __align__(16) long long R[];  // prefix sums relative to `base`
-    __shared__ double s_thr[SP_MAXW];
+    __shared__ long long s_thr[SP_MAXW];  // ceil of the FP64 threshold: B >= thr  <=>  B >= ceil(thr)
     __shared__ long long s_tot[NT];
     __shared__ int s_ok;
     const int b = blockIdx.y;
@@ -65,7 +67,11 @@ __global__ void __launch_bounds__(NT) k_sp_detect(const __grid_constant__ SpArgs
         const double ts = __dmul_rn(a.thr, sigma);
         for (int i = 0; i < a.nw; ++i) {
             const double w = (double)a.w[i];
-            s_thr[i] = __dadd_rn(__dmul_rn(w, mu), __dmul_rn(ts, __dsqrt_rn(w)));
+            const double thr = __dadd_rn(__dmul_rn(w, mu), __dmul_rn(ts, __dsqrt_rn(w)));
+            // B is an integer below 2^53 (exact as a double), so (double)B >= thr
+            // exactly when B >= ceil(thr); the loop then compares integers only
+            const double c = ceil(thr);
+            s_thr[i] = c > 9.0e18 ? LLONG_MAX : (c < -9.0e18 ? LLONG_MIN : (long long)c);
         }
     }
     __syncthreads();
@@ -113,11 +119,11 @@ __global__ void __launch_bounds__(NT) k_sp_detect(const __grid_constant__ SpArgs
         const int w = a.w[i];
         const int64_t tmax = n - w;  // last valid boxcar start
         if (tmax < t0) continue;
-        const double thr = s_thr[i];
+        const long long thr = s_thr[i];
         const int64_t tend = min(t0 + TS - 1, tmax);
         for (int64_t t = t0 + threadIdx.x; t <= tend; t += NT) {
             const long long B = R[t + w - base] - R[t - base];
-            if (!((double)B >= thr)) continue;
+            if (B < thr) continue;
             bool ok = true;
             const int64_t lo = max((int64_t)0, t - w + 1), hi = min(tmax, t + w - 1);
             for (int64_t u = lo; u < t && ok; ++u) ok = B > R[u + w - base] - R[u - base];
