@@ -28,7 +28,7 @@ constexpr int KJ = TN / 32;     // samples per lane
 constexpr int MAXSB = 64;       // subbands staged per round
 
 template <bool INT_OUT>
-__global__ void __launch_bounds__(NT) k_subsum(const __grid_constant__ SubsumArgs a, int RW, int SBC) {
+__global__ void __launch_bounds__(NT, 2) k_subsum(const __grid_constant__ SubsumArgs a, int RW, int SBC) {
     extern __shared__ __align__(128) int32_t sm[];  // [SBC][RW] staged rows; reused by the ds epilogue
     __shared__ int32_t s_dmin[MAXSB], s_lead[MAXSB];
     __shared__ __align__(8) uint64_t s_bar;
