@@ -20,7 +20,8 @@
 //   Gq_c = sum_q A^c_q conj(rho_q), Gz_c = sum_q A^c_q conj(rho_z),
 //   dE/dr = k sum_q 2 Re(conj(rho) rho_q), dE/dz = k sum_q 2 Re(conj(rho) rho_z),
 //   dP/dx = g (2 Re(conj(F) dF/dx) / E - |F|^2 (dE/dx) / E^2).
-// Phases and the response (rho_derivs, response.cuh) are evaluated in FP64;
+// Phases and the response (rho_derivs, response.cuh) are evaluated in FP64
+// (harmonic k's channel phases as the k-th power of the fundamental's);
 // the channel sums accumulate in FP32 and are reduced across the CTA in FP64.
 #include <math.h>
 
@@ -78,7 +79,30 @@ __global__ void __launch_bounds__(NT) k_refine_eval(const __grid_constant__ Refi
     const RefinePt pt = a.pts[p];
     const int64_t M = a.nfft / 2;
     double P = 0.0, gdm = 0.0, gr = 0.0, gz = 0.0;
+    // channel phases exp(i 2 pi (k r) DM dtau_c / T): the fundamental's by
+    // sincospi (FP64), each further harmonic by one FP64 complex product
+    // (phi_ck = k phi_c1), for the CPT channels a thread owns
+    constexpr int CPT = 4;
+    const bool rec = a.ck <= CPT * NT;
+    double e1c[CPT], e1s[CPT], ekc[CPT], eks[CPT];
+#pragma unroll
+    for (int i = 0; i < CPT; ++i) {
+        e1c[i] = 1.0;
+        e1s[i] = 0.0;
+        ekc[i] = 1.0;
+        eks[i] = 0.0;
+        const int c = threadIdx.x + i * NT;
+        if (rec && c < a.ck) sincospi(2.0 * pt.r * pt.dm * a.dtau[c] / a.T, &e1s[i], &e1c[i]);
+    }
     for (int k = 1; k <= pt.numharm; ++k) {
+        if (rec) {
+#pragma unroll
+            for (int i = 0; i < CPT; ++i) {
+                const double c2 = ekc[i] * e1c[i] - eks[i] * e1s[i];
+                eks[i] = ekc[i] * e1s[i] + eks[i] * e1c[i];
+                ekc[i] = c2;
+            }
+        }
         const double rk = k * pt.r, zk = k * pt.z;
         const int m = (int)ceil(fabs(zk) / 2.0) + a.extra;
         if (2 * m > MAXTAP) break;
@@ -103,7 +127,7 @@ __global__ void __launch_bounds__(NT) k_refine_eval(const __grid_constant__ Refi
         const int t_lo = (int)max((int64_t)0, -(k0 - m + 1));
         const int t_hi = (int)min((int64_t)(2 * m), M - (k0 - m + 1));
         float2 F = make_float2(0.f, 0.f), Fdm = F, Fr = F, Fz = F;
-        for (int c = threadIdx.x; c < a.ck; c += NT) {
+        for (int c = threadIdx.x, ci = 0; c < a.ck; c += NT, ++ci) {
             const float2* Ac = a.chan_spec + (int64_t)c * M + (k0 - m + 1);
             float2 G = make_float2(0.f, 0.f), Gq = G, Gz = G;
             for (int t = t_lo; t < t_hi; ++t) {
@@ -119,7 +143,19 @@ __global__ void __launch_bounds__(NT) k_refine_eval(const __grid_constant__ Refi
             // phase exp(i 2 pi rk DM dtau_c / T), FP64
             const double dt = a.dtau[c];
             double sn, cs;
-            sincospi(2.0 * rk * pt.dm * dt / a.T, &sn, &cs);
+            if (rec) {
+                // ci < CPT here; the unrolled select keeps the arrays in registers
+                cs = ekc[0];
+                sn = eks[0];
+#pragma unroll
+                for (int i = 1; i < CPT; ++i)
+                    if (ci == i) {
+                        cs = ekc[i];
+                        sn = eks[i];
+                    }
+            } else {
+                sincospi(2.0 * rk * pt.dm * dt / a.T, &sn, &cs);
+            }
             const float2 e = make_float2((float)cs, (float)sn);
             const float2 eG = make_float2(e.x * G.x - e.y * G.y, e.x * G.y + e.y * G.x);
             F.x += eG.x;

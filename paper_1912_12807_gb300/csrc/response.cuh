@@ -16,7 +16,8 @@
 //    with C + iS = ((1+i)/2) erf(sqrt(pi) (1-i) x / 2) (Abramowitz & Stegun
 //    7.3.22) evaluated by the power series (A&S 7.3.11, 7.3.13) for |x| <= 2
 //    and, above, by the auxiliary functions f, g through the continued
-//    fraction of erfc (A&S 7.1.14), truncated at 60 terms (~1e-15).
+//    fraction of erfc (A&S 7.1.14), truncated at min(60, ceil(220/x^2) + 6)
+//    terms (~1e-15).
 #pragma once
 
 #include <math.h>
@@ -77,7 +78,12 @@ PSS_HD void fresnel_cs(double x, double* C, double* S) {
         const double h = 0.5 * sqrt(M_PI) * ax;
         cplx zeta = {h, -h};
         cplx cf = zeta;
-        for (int k = 60; k >= 1; --k) {
+        // terms needed fall like 1/x^2: ceil(220 / x^2) + 6 (at most 60) agree
+        // with the 60-term value to 2.3e-16 for every x > 2 (checked on a
+        // 7e-4 grid up to x = 60)
+        int nt = (int)ceil(220.0 / (ax * ax)) + 6;
+        if (nt > 60) nt = 60;
+        for (int k = nt; k >= 1; --k) {
             // cf = zeta + (k/2) / cf
             const double den = cf.re * cf.re + cf.im * cf.im;
             const double kk = 0.5 * k;
