@@ -1037,14 +1037,6 @@ pss_status drain_batches(pss_ctx* ctx, const pss_plan* plan, const pss_search_cf
             PSS_CUDA(cudaStreamSynchronize(ctx->stream2));
             const size_t old = surv->size();
             PSS_TRY(sift_within(*plan, *cfg, ctx->raw_pinned, (int64_t)(cnt - prev), surv));
-            // sigma of each survivor now, while the device works (the across-trial
-            // representatives need it after the last batch)
-            SiftItem* nw = surv->data() + old;
-            parallel_for((int64_t)(surv->size() - old), 256, [&](int64_t i) {
-                SiftItem& x = nw[i];
-                x.logp = log_q(x.n, (double)x.power);
-                x.sigma = sigma_from_logp(x.logp);
-            });
             if (cfg->zmax == 0) {
                 // keep the survivors ordered by r (stable) while the device works on,
                 // so the across-trial linkage after the last batch needs no sort
@@ -1355,7 +1347,7 @@ pss_status pss_single_pulse(pss_ctx* ctx, const pss_plan* plan, const pss_fil_de
         int64_t B = std::max<int64_t>(1, std::min<int64_t>(1024, ((int64_t)1 << 28) / st.nv));
         if (T.on && B > plan->sub_group) B = B / plan->sub_group * plan->sub_group;
         PSS_TRY(ctx->sp_series.ensure((size_t)std::min<int64_t>(B, hi - lo) * st.nv * sizeof(int32_t)));
-        PSS_TRY(ctx->sp_mom.ensure((size_t)2 * std::min<int64_t>(B, hi - lo) * sizeof(unsigned long long)));
+        PSS_TRY(ctx->sp_mom.ensure((size_t)(2 + SP_MAXW) * std::min<int64_t>(B, hi - lo) * sizeof(unsigned long long)));
         for (int64_t b0 = lo; b0 < hi; b0 += B) {
             const int32_t nb = (int32_t)std::min<int64_t>(B, hi - b0);
             int32_t spread = 0;
@@ -1385,6 +1377,7 @@ pss_status pss_single_pulse(pss_ctx* ctx, const pss_plan* plan, const pss_fil_de
             sa.thr = sigma_thr;
             sa.s1 = m1;
             sa.s2 = m2;
+            sa.thr_tab = (long long*)(m2 + nb);
             sa.out = (SpRaw*)ctx->sp_ev.p;
             sa.count = (unsigned long long*)ctx->counter.p;
             sa.cap = devcap;

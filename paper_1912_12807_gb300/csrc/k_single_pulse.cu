@@ -12,6 +12,7 @@
 // the threshold is the same number the host computes.
 //
 // k_sp_moments: one pass over the series, 64-bit integer sums.
+// k_sp_thresholds: the integer threshold of every (trial, width), FP64.
 // k_sp_detect: a CTA owns TS samples of one trial; it stages the samples
 // [t0 - wmax + 1, t0 + TS + 2 wmax - 2] in shared memory as a 64-bit
 // prefix sum (so every B_w the tile and its local-maximum windows need is
@@ -48,34 +49,37 @@ __global__ void __launch_bounds__(NT) k_sp_moments(const int32_t* __restrict__ s
     }
 }
 
+// One thread per (trial, width): the integer threshold ceil(w*mu +
+// thr*sigma*sqrt(w)) (B is an integer below 2^53, exact as a double, so
+// (double)B >= thr exactly when B >= ceil(thr)); LLONG_MAX when sigma is 0.
+__global__ void k_sp_thresholds(const __grid_constant__ SpArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.nb * a.nw) return;
+    const int b = i / a.nw, wi = i - b * a.nw;
+    const double fS1 = (double)a.s1[b], fS2 = (double)a.s2[b], fN = (double)a.n;
+    const double mu = __ddiv_rn(fS1, fN);
+    double var = __ddiv_rn(__dsub_rn(fS2, __ddiv_rn(__dmul_rn(fS1, fS1), fN)), fN);
+    if (!(var > 0.0)) var = 0.0;
+    const double sigma = __dsqrt_rn(var);
+    long long t = LLONG_MAX;
+    if (sigma > 0.0) {
+        const double w = (double)a.w[wi];
+        const double thr = __dadd_rn(__dmul_rn(w, mu), __dmul_rn(__dmul_rn(a.thr, sigma), __dsqrt_rn(w)));
+        const double c = ceil(thr);
+        t = c > 9.0e18 ? LLONG_MAX : (c < -9.0e18 ? LLONG_MIN : (long long)c);
+    }
+    a.thr_tab[i] = t;
+}
+
 __global__ void __launch_bounds__(NT) k_sp_detect(const __grid_constant__ SpArgs a) {
     extern __shared__ __align__(16) long long R[];  // prefix sums relative to `base`
-    __shared__ long long s_thr[SP_MAXW];  // ceil of the FP64 threshold: B >= thr  <=>  B >= ceil(thr)
     __shared__ long long s_tot[NT];
-    __shared__ int s_ok;
     const int b = blockIdx.y;
     const int64_t n = a.n;
     const int64_t t0 = (int64_t)blockIdx.x * TS;
     const int32_t* s = a.series + (int64_t)b * a.stride;
-    if (threadIdx.x == 0) {
-        const double fS1 = (double)a.s1[b], fS2 = (double)a.s2[b], fN = (double)n;
-        const double mu = __ddiv_rn(fS1, fN);
-        double var = __ddiv_rn(__dsub_rn(fS2, __ddiv_rn(__dmul_rn(fS1, fS1), fN)), fN);
-        if (!(var > 0.0)) var = 0.0;
-        const double sigma = __dsqrt_rn(var);
-        s_ok = sigma > 0.0;
-        const double ts = __dmul_rn(a.thr, sigma);
-        for (int i = 0; i < a.nw; ++i) {
-            const double w = (double)a.w[i];
-            const double thr = __dadd_rn(__dmul_rn(w, mu), __dmul_rn(ts, __dsqrt_rn(w)));
-            // B is an integer below 2^53 (exact as a double), so (double)B >= thr
-            // exactly when B >= ceil(thr); the loop then compares integers only
-            const double c = ceil(thr);
-            s_thr[i] = c > 9.0e18 ? LLONG_MAX : (c < -9.0e18 ? LLONG_MIN : (long long)c);
-        }
-    }
-    __syncthreads();
-    if (!s_ok) return;
+    const long long* thr_b = a.thr_tab + (int64_t)b * a.nw;
+    if (thr_b[0] == LLONG_MAX) return;  // sigma 0: no detections (uniform over the CTA)
     const int64_t base = max((int64_t)0, t0 - a.wmax + 1);
     const int64_t last = min(n, t0 + TS + 2 * (int64_t)a.wmax - 2);  // largest prefix index needed
     const int L = (int)(last - base + 1);                           // R[0 .. L-1]
@@ -119,7 +123,7 @@ __global__ void __launch_bounds__(NT) k_sp_detect(const __grid_constant__ SpArgs
         const int w = a.w[i];
         const int64_t tmax = n - w;  // last valid boxcar start
         if (tmax < t0) continue;
-        const long long thr = s_thr[i];
+        const long long thr = thr_b[i];
         const int64_t tend = min(t0 + TS - 1, tmax);
         for (int64_t t = t0 + threadIdx.x; t <= tend; t += NT) {
             const long long B = R[t + w - base] - R[t - base];
@@ -152,6 +156,9 @@ cudaError_t launch_single_pulse(const SpArgs& a, unsigned long long* s1, unsigne
     dim3 gm((unsigned)std::min<int64_t>((a.n + NT - 1) / NT, 64), (unsigned)a.nb);
     k_sp_moments<<<gm, NT, 0, s>>>(a.series, a.stride, a.n, s1, s2);
     cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_sp_thresholds<<<(unsigned)((a.nb * a.nw + 127) / 128), 128, 0, s>>>(a);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t shm = sp_detect_smem(a.wmax);
     e = allow_smem((const void*)k_sp_detect, shm);

@@ -327,6 +327,7 @@ struct SpArgs {
     double thr;
     const unsigned long long* s1;  // [nb] sum s
     const unsigned long long* s2;  // [nb] sum s^2
+    long long* thr_tab;     // [nb][nw] integer thresholds (written by the moments launch)
     SpRaw* out;
     unsigned long long* count;
     int64_t cap;
