@@ -1943,6 +1943,8 @@ std::string tune_key(const Plan& plan, const pss_fil_desc* f, const pss_search_c
              f->tsamp_s, f->fch0_mhz, f->foff_mhz, f->layout);
     k += buf;
     for (int i = 0; i < f->nchan; ++i) k += (f->chan_mask && !f->chan_mask[i]) ? '0' : '1';
+    snprintf(buf, sizeof buf, "|sub%d,%d", plan.nsub, plan.sub_group);
+    k += buf;
     for (const auto& st : plan.stages) {
         snprintf(buf, sizeof buf, "|%.17g,%.17g,%d,%d", st.dm_lo, st.dm_step, st.n_dm, st.ds);
         k += buf;
