@@ -120,9 +120,11 @@ def oracle_rate(pool, n_trials, ndm, offset=0):
 
 
 def cpu_baseline_block(value, cores, n, ndm, dt):
+    which = ("%d of the %d DM trials (evenly spaced)" % (n, ndm) if n <= ndm else
+             "%d trial searches cycling evenly over the %d DM trials" % (n, ndm))
     return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d of the %d DM trials (evenly spaced), each searched end to end by the FP64 "
-                      "NumPy oracle in a spawn pool of %d processes; %.1f s wall" % (n, ndm, cores, dt)}
+            "sample": "%s, each searched end to end by the FP64 NumPy oracle in a spawn pool of %d "
+                      "processes; %.1f s wall" % (which, cores, dt)}
 
 
 def _per_step_trials(name, cores):
