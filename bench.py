@@ -411,7 +411,7 @@ def run_ours(args, rank, world, local_rank):
     e2e = max_over_ranks(statistics.mean(e2e_ms), world, dev)
 
     refine = None
-    if wl.cfg.zmax > 0 and rank == 0 and len(cands):
+    if wl.cfg.zmax > 0 and rank == 0 and len(cands) and args.refine_top > 0:
         refine = run_refine(pss, ctx, plan, data_dev, cfg, cands, args.refine_top)
 
     subband = None
