@@ -20,9 +20,12 @@
 //   Gq_c = sum_q A^c_q conj(rho_q), Gz_c = sum_q A^c_q conj(rho_z),
 //   dE/dr = k sum_q 2 Re(conj(rho) rho_q), dE/dz = k sum_q 2 Re(conj(rho) rho_z),
 //   dP/dx = g (2 Re(conj(F) dF/dx) / E - |F|^2 (dE/dx) / E^2).
-// Phases and the response (rho_derivs, response.cuh) are evaluated in FP64
-// (harmonic k's channel phases as the k-th power of the fundamental's);
-// the channel sums accumulate in FP32 and are reduced across the CTA in FP64.
+// Phases are evaluated in FP64 (harmonic k's channel phases as the k-th
+// power of the fundamental's); the response taps (rho_derivs, response.cuh)
+// in FP64 for |kz| < 8 and above that with FP64 phase arguments and FP32
+// magnitudes (rho_derivs_mixed);
+// the phased channel sums per tap (lanes over taps, warps over channel
+// groups) accumulate in FP32 and are reduced across the CTA in FP64.
 #include <math.h>
 
 #include "pss_internal.h"
@@ -51,6 +54,94 @@ __global__ void k_chan_series(const uint8_t* xcm, int64_t pitch, int32_t ck, int
     if ((threadIdx.x & 31) == 0) atomicAdd(sums + c, part);
 }
 
+// ---- response taps for |z| >= RESP_F32_Z, FP32 with FP64 phase arguments ---
+// rho and its derivatives (same formulas as rho_derivs in response.cuh) with
+// every phase argument formed and reduced modulo 2 in FP64 and the rest in
+// FP32.  Above |z| = 8 the integration-by-parts solve for M1, M2 divides by z
+// with |q - z/2| / |z| <= 1 + extra / |z|, so FP32 errors stay near 1e-6 of
+// the taps; below it the FP64 evaluation runs.
+constexpr double RESP_F32_Z = 8.0;
+
+// x mod 2 in [-1, 1], FP64, as a float (an argument for sincospif)
+__device__ __forceinline__ float mod2f(double x) { return (float)(x - 2.0 * rint(0.5 * x)); }
+
+// Fresnel C, S of x as C = sgn (1/2 + oc), S = sgn (1/2 + os), sgn = sign(x):
+// the offsets from 1/2 are what a difference of two same-side values needs.
+__device__ __forceinline__ void fresnel_off(double x, float* sgn, float* oc, float* os) {
+    const double axd = fabs(x);
+    const float ax = (float)axd;
+    *sgn = x < 0 ? -1.f : 1.f;
+    if (ax <= 2.f) {
+        // power series (A&S 7.3.11, 7.3.13), terms (pi/2)^k x^(2k+1) / (k! (2k+1))
+        float t = ax, c = 0.f, sv = 0.f;
+        const float a2 = 1.5707963267948966f * ax * ax;
+        for (int k = 0; k < 40; ++k) {
+            const float term = t / (float)(2 * k + 1);
+            switch (k & 3) {
+                case 0: c += term; break;
+                case 1: sv += term; break;
+                case 2: c -= term; break;
+                default: sv -= term; break;
+            }
+            t *= a2 / (float)(k + 1);
+            if (t < 1e-9f) break;
+        }
+        *oc = c - 0.5f;
+        *os = sv - 0.5f;
+        return;
+    }
+    // continued fraction of erfc (A&S 7.1.14) for the auxiliary functions f, g
+    const float h = 0.88622692545275801f * ax;  // sqrt(pi) / 2 * x
+    float cr = h, ci = -h;
+    int nt = (int)ceilf(220.f / (ax * ax)) + 6;
+    if (nt > 60) nt = 60;
+    for (int k = nt; k >= 1; --k) {
+        const float den = cr * cr + ci * ci;
+        const float kk = 0.5f * (float)k;
+        cr = h + kk * cr / den;
+        ci = -h - kk * ci / den;
+    }
+    const float den = cr * cr + ci * ci;
+    const float Kr = cr / den, Ki = -ci / den;
+    const float fac = 0.28209479177387814f;  // 1 / (2 sqrt(pi))
+    const float g = fac * (Kr - Ki), f = fac * (Kr + Ki);
+    float sn, cs;
+    sincospif(mod2f(0.5 * axd * axd), &sn, &cs);
+    *oc = f * sn - g * cs;
+    *os = -f * cs - g * sn;
+}
+
+__device__ __forceinline__ float2 c_mulf(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ void rho_derivs_mixed(double q, double z, float2* r, float2* rq, float2* rz) {
+    const double sqd = sqrt(2.0 * fabs(z));
+    const double bb = (q - 0.5 * z) / z;
+    float g0, c0, s0, g1, c1, s1;
+    fresnel_off(sqd * bb, &g0, &c0, &s0);
+    fresnel_off(sqd * (1.0 + bb), &g1, &c1, &s1);
+    const float isq = (float)(1.0 / sqd);
+    // C(w1) - C(w0) with the halves taken exactly
+    const float dC = (0.5f * (g1 - g0) + (g1 * c1 - g0 * c0)) * isq;
+    const float dS = (z > 0 ? 1.f : -1.f) * (0.5f * (g1 - g0) + (g1 * s1 - g0 * s0)) * isq;
+    const double qq = q - 0.5 * z;
+    float sn, cs;
+    sincospif(mod2f(-(qq * qq) / z), &sn, &cs);
+    const float2 rho = c_mulf(make_float2(cs, sn), make_float2(dC, dS));
+    float es, ec;
+    sincospif(mod2f(2.0 * q), &es, &ec);
+    const float af = (float)qq, zf = (float)z;
+    const float i2p = 0.15915494309189535f;  // 1 / (2 pi); (x) / (2 pi i) = (x.y, -x.x) / (2 pi)
+    const float2 t1 = make_float2(es * i2p, -(ec - 1.f) * i2p);
+    const float2 M1 = make_float2((t1.x - af * rho.x) / zf, (t1.y - af * rho.y) / zf);
+    const float2 t2 = make_float2((es - rho.y) * i2p, -(ec - rho.x) * i2p);
+    const float2 M2 = make_float2((t2.x - af * M1.x) / zf, (t2.y - af * M1.y) / zf);
+    *r = rho;
+    *rq = make_float2(-6.283185307179586f * M1.y, 6.283185307179586f * M1.x);            // 2 pi i M1
+    *rz = make_float2(-3.141592653589793f * (M2.y - M1.y), 3.141592653589793f * (M2.x - M1.x));  // pi i (M2 - M1)
+}
+
 __device__ __forceinline__ double2 block_sum2(double2 v, double* red) {
     // reduce (x, y) over the CTA; red holds 2 * NT / 32 doubles
     for (int off = 16; off > 0; off >>= 1) {
@@ -75,6 +166,7 @@ __device__ __forceinline__ double2 block_sum2(double2 v, double* red) {
 __global__ void __launch_bounds__(NT) k_refine_eval(const __grid_constant__ RefineArgs a) {
     __shared__ float2 s_r[MAXTAP], s_rq[MAXTAP], s_rz[MAXTAP];
     __shared__ double red[2 * NT / 32];
+    extern __shared__ float4 s_ch[];  // [ck] channel phase e_c and dtau_c e_c of the harmonic
     const int p = blockIdx.x;
     const RefinePt pt = a.pts[p];
     const int64_t M = a.nfft / 2;
@@ -111,14 +203,25 @@ __global__ void __launch_bounds__(NT) k_refine_eval(const __grid_constant__ Refi
         double e0 = 0.0, eq = 0.0, ez = 0.0;
         for (int t = threadIdx.x; t < 2 * m; t += NT) {
             const int64_t q = k0 - m + 1 + t;
-            cplx r, rq, rz;
-            rho_derivs(rk - (double)q, zk, &r, &rq, &rz);
-            s_r[t] = make_float2((float)r.re, (float)-r.im);
-            s_rq[t] = make_float2((float)rq.re, (float)-rq.im);
-            s_rz[t] = make_float2((float)rz.re, (float)-rz.im);
-            e0 += r.re * r.re + r.im * r.im;
-            eq += 2.0 * (r.re * rq.re + r.im * rq.im);
-            ez += 2.0 * (r.re * rz.re + r.im * rz.im);
+            if (fabs(zk) >= RESP_F32_Z) {
+                float2 r, rq, rz;
+                rho_derivs_mixed(rk - (double)q, zk, &r, &rq, &rz);
+                s_r[t] = make_float2(r.x, -r.y);
+                s_rq[t] = make_float2(rq.x, -rq.y);
+                s_rz[t] = make_float2(rz.x, -rz.y);
+                e0 += (double)(r.x * r.x + r.y * r.y);
+                eq += (double)(2.f * (r.x * rq.x + r.y * rq.y));
+                ez += (double)(2.f * (r.x * rz.x + r.y * rz.y));
+            } else {
+                cplx r, rq, rz;
+                rho_derivs(rk - (double)q, zk, &r, &rq, &rz);
+                s_r[t] = make_float2((float)r.re, (float)-r.im);
+                s_rq[t] = make_float2((float)rq.re, (float)-rq.im);
+                s_rz[t] = make_float2((float)rz.re, (float)-rz.im);
+                e0 += r.re * r.re + r.im * r.im;
+                eq += 2.0 * (r.re * rq.re + r.im * rq.im);
+                ez += 2.0 * (r.re * rz.re + r.im * rz.im);
+            }
         }
         const double2 e01 = block_sum2(make_double2(e0, eq), red);
         const double2 ez2 = block_sum2(make_double2(ez, 0.0), red);
@@ -126,21 +229,8 @@ __global__ void __launch_bounds__(NT) k_refine_eval(const __grid_constant__ Refi
         // valid tap range (bins inside [0, M))
         const int t_lo = (int)max((int64_t)0, -(k0 - m + 1));
         const int t_hi = (int)min((int64_t)(2 * m), M - (k0 - m + 1));
-        float2 F = make_float2(0.f, 0.f), Fdm = F, Fr = F, Fz = F;
+        // channel phases e_c = exp(i 2 pi rk DM dtau_c / T) (FP64) and dtau_c e_c, in shared memory
         for (int c = threadIdx.x, ci = 0; c < a.ck; c += NT, ++ci) {
-            const float2* Ac = a.chan_spec + (int64_t)c * M + (k0 - m + 1);
-            float2 G = make_float2(0.f, 0.f), Gq = G, Gz = G;
-            for (int t = t_lo; t < t_hi; ++t) {
-                const float2 x = __ldg(Ac + t);
-                const float2 u = s_r[t], v = s_rq[t], w = s_rz[t];
-                G.x = fmaf(x.x, u.x, fmaf(-x.y, u.y, G.x));
-                G.y = fmaf(x.x, u.y, fmaf(x.y, u.x, G.y));
-                Gq.x = fmaf(x.x, v.x, fmaf(-x.y, v.y, Gq.x));
-                Gq.y = fmaf(x.x, v.y, fmaf(x.y, v.x, Gq.y));
-                Gz.x = fmaf(x.x, w.x, fmaf(-x.y, w.y, Gz.x));
-                Gz.y = fmaf(x.x, w.y, fmaf(x.y, w.x, Gz.y));
-            }
-            // phase exp(i 2 pi rk DM dtau_c / T), FP64
             const double dt = a.dtau[c];
             double sn, cs;
             if (rec) {
@@ -156,22 +246,47 @@ __global__ void __launch_bounds__(NT) k_refine_eval(const __grid_constant__ Refi
             } else {
                 sincospi(2.0 * rk * pt.dm * dt / a.T, &sn, &cs);
             }
-            const float2 e = make_float2((float)cs, (float)sn);
-            const float2 eG = make_float2(e.x * G.x - e.y * G.y, e.x * G.y + e.y * G.x);
-            F.x += eG.x;
-            F.y += eG.y;
-            // i * dphi * eG
-            const float dphi_dm = (float)(2.0 * M_PI * rk * dt / a.T);
-            const float dphi_dr = (float)(2.0 * M_PI * k * pt.dm * dt / a.T);
-            Fdm.x += -dphi_dm * eG.y;
-            Fdm.y += dphi_dm * eG.x;
-            const float2 eGq = make_float2(e.x * Gq.x - e.y * Gq.y, e.x * Gq.y + e.y * Gq.x);
-            Fr.x += -dphi_dr * eG.y + k * eGq.x;
-            Fr.y += dphi_dr * eG.x + k * eGq.y;
-            const float2 eGz = make_float2(e.x * Gz.x - e.y * Gz.y, e.x * Gz.y + e.y * Gz.x);
-            Fz.x += k * eGz.x;
-            Fz.y += k * eGz.y;
+            s_ch[c] = make_float4((float)cs, (float)sn, (float)(dt * cs), (float)(dt * sn));
         }
+        __syncthreads();
+        // F = sum_t u_t H_t, H_t = sum_c e_c A^c_t (u = conj rho); the DM and r
+        // derivatives need H'_t = sum_c dtau_c e_c A^c_t.  Lanes take
+        // consecutive taps (coalesced reads of each channel's spectrum), warps
+        // take channel groups; each warp adds its partial sums into F directly.
+        float2 F = make_float2(0.f, 0.f), Fd = F, Fq = F, Fz = F;
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int cper = (a.ck + NT / 32 - 1) / (NT / 32);
+        const int c0 = warp * cper, c1 = min(a.ck, c0 + cper);
+        const float2* Abase = a.chan_spec + (k0 - m + 1);
+        for (int tb = t_lo; tb < t_hi; tb += 32) {
+            const int t = tb + lane;
+            if (t < t_hi) {
+                float2 H = make_float2(0.f, 0.f), Hd = H;
+                const float2* Ap = Abase + t;
+                for (int c = c0; c < c1; ++c) {
+                    const float2 x = __ldg(Ap + (int64_t)c * M);
+                    const float4 e = s_ch[c];
+                    H.x = fmaf(e.x, x.x, fmaf(-e.y, x.y, H.x));
+                    H.y = fmaf(e.x, x.y, fmaf(e.y, x.x, H.y));
+                    Hd.x = fmaf(e.z, x.x, fmaf(-e.w, x.y, Hd.x));
+                    Hd.y = fmaf(e.z, x.y, fmaf(e.w, x.x, Hd.y));
+                }
+                const float2 u = s_r[t], v = s_rq[t], w = s_rz[t];
+                F.x += u.x * H.x - u.y * H.y;
+                F.y += u.x * H.y + u.y * H.x;
+                Fd.x += u.x * Hd.x - u.y * Hd.y;
+                Fd.y += u.x * Hd.y + u.y * Hd.x;
+                Fq.x += v.x * H.x - v.y * H.y;
+                Fq.y += v.x * H.y + v.y * H.x;
+                Fz.x += w.x * H.x - w.y * H.y;
+                Fz.y += w.x * H.y + w.y * H.x;
+            }
+        }
+        // Fdm = i (2 pi rk / T) sum u H',  Fr = i (2 pi k DM / T) sum u H' + k sum v H,  Fz = k sum w H
+        const float cdm = (float)(2.0 * M_PI * rk / a.T), cdr = (float)(2.0 * M_PI * k * pt.dm / a.T);
+        const float2 Fdm = make_float2(-cdm * Fd.y, cdm * Fd.x);
+        const float2 Fr = make_float2(-cdr * Fd.y + k * Fq.x, cdr * Fd.x + k * Fq.y);
+        Fz = make_float2(k * Fz.x, k * Fz.y);
         const double2 sF = block_sum2(make_double2(F.x, F.y), red);
         const double2 sFdm = block_sum2(make_double2(Fdm.x, Fdm.y), red);
         const double2 sFr = block_sum2(make_double2(Fr.x, Fr.y), red);
@@ -205,7 +320,10 @@ cudaError_t launch_chan_series(const uint8_t* xcm, int64_t pitch, int32_t ck, in
 
 cudaError_t launch_refine_eval(const RefineArgs& a, int64_t n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    k_refine_eval<<<(unsigned)n, NT, 0, s>>>(a);
+    const size_t shm = (size_t)a.ck * sizeof(float4);
+    cudaError_t e = allow_smem((const void*)k_refine_eval, shm);
+    if (e != cudaSuccess) return e;
+    k_refine_eval<<<(unsigned)n, NT, shm, s>>>(a);
     return cudaGetLastError();
 }
 
