@@ -91,18 +91,40 @@ __device__ __forceinline__ void fresnel_off(double x, float* sgn, float* oc, flo
         return;
     }
     // continued fraction of erfc (A&S 7.1.14) for the auxiliary functions f, g
-    const float h = 0.88622692545275801f * ax;  // sqrt(pi) / 2 * x
-    float cr = h, ci = -h;
+    // (forward three-term recurrences as in fresnel_cs: one division)
+    const float h = 0.88622692545275801f * ax;  // sqrt(pi) / 2 * x; zeta = h (1 - i)
     int nt = (int)ceilf(220.f / (ax * ax)) + 6;
     if (nt > 60) nt = 60;
-    for (int k = nt; k >= 1; --k) {
-        const float den = cr * cr + ci * ci;
+    if (ax > 1e4f) nt = 1;  // zeta^2 must stay inside the FP32 range
+    float a1r = h, a1i = -h, a2r = 1.f, a2i = 0.f, b1r = 1.f, b1i = 0.f, b2r = 0.f, b2i = 0.f;
+    for (int k = 1; k <= nt; ++k) {
         const float kk = 0.5f * (float)k;
-        cr = h + kk * cr / den;
-        ci = -h - kk * ci / den;
+        const float ar = h * a1r + h * a1i + kk * a2r, ai = h * a1i - h * a1r + kk * a2i;
+        const float br = h * b1r + h * b1i + kk * b2r, bi = h * b1i - h * b1r + kk * b2i;
+        a2r = a1r;
+        a2i = a1i;
+        a1r = ar;
+        a1i = ai;
+        b2r = b1r;
+        b2i = b1i;
+        b1r = br;
+        b1i = bi;
+        // A, B grow like prod (k/2): rescale both (their ratio is the value) so
+        // that |A|^2 in the final division stays inside the FP32 range
+        if (fabsf(a1r) + fabsf(a1i) > 1e15f) {
+            a1r *= 1e-15f;
+            a1i *= 1e-15f;
+            a2r *= 1e-15f;
+            a2i *= 1e-15f;
+            b1r *= 1e-15f;
+            b1i *= 1e-15f;
+            b2r *= 1e-15f;
+            b2i *= 1e-15f;
+        }
     }
-    const float den = cr * cr + ci * ci;
-    const float Kr = cr / den, Ki = -ci / den;
+    // K = B / A
+    const float den = a1r * a1r + a1i * a1i;
+    const float Kr = (b1r * a1r + b1i * a1i) / den, Ki = (b1i * a1r - b1r * a1i) / den;
     const float fac = 0.28209479177387814f;  // 1 / (2 sqrt(pi))
     const float g = fac * (Kr - Ki), f = fac * (Kr + Ki);
     float sn, cs;

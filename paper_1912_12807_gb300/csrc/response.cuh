@@ -75,22 +75,30 @@ PSS_HD void fresnel_cs(double x, double* C, double* S) {
         }
     } else {
         // zeta = sqrt(pi) (1 - i) x / 2;  K = 1 / (zeta + (1/2)/(zeta + (2/2)/(zeta + ...)))
+        // truncated after nt partial fractions, evaluated forwards with the
+        // three-term recurrences A_k = zeta A_{k-1} + (k/2) A_{k-2} (likewise B),
+        // A_0 = zeta, B_0 = 1, A_{-1} = 1, B_{-1} = 0, so that K = B / A needs one
+        // division (A, B grow like |zeta|^nt: far inside the FP64 range for |x| < 1e40)
         const double h = 0.5 * sqrt(M_PI) * ax;
-        cplx zeta = {h, -h};
-        cplx cf = zeta;
+        const cplx zeta = {h, -h};
         // terms needed fall like 1/x^2: ceil(220 / x^2) + 6 (at most 60) agree
         // with the 60-term value to 2.3e-16 for every x > 2 (checked on a
         // 7e-4 grid up to x = 60)
         int nt = (int)ceil(220.0 / (ax * ax)) + 6;
         if (nt > 60) nt = 60;
-        for (int k = nt; k >= 1; --k) {
-            // cf = zeta + (k/2) / cf
-            const double den = cf.re * cf.re + cf.im * cf.im;
+        cplx A1 = zeta, A2 = {1.0, 0.0}, B1 = {1.0, 0.0}, B2 = {0.0, 0.0};
+        for (int k = 1; k <= nt; ++k) {
             const double kk = 0.5 * k;
-            cf = {zeta.re + kk * cf.re / den, zeta.im - kk * cf.im / den};
+            const cplx A = {zeta.re * A1.re - zeta.im * A1.im + kk * A2.re, zeta.re * A1.im + zeta.im * A1.re + kk * A2.im};
+            const cplx B = {zeta.re * B1.re - zeta.im * B1.im + kk * B2.re, zeta.re * B1.im + zeta.im * B1.re + kk * B2.im};
+            A2 = A1;
+            A1 = A;
+            B2 = B1;
+            B1 = B;
         }
-        const double den = cf.re * cf.re + cf.im * cf.im;
-        const cplx K = {cf.re / den, -cf.im / den};
+        // K = B / A
+        const double den = A1.re * A1.re + A1.im * A1.im;
+        const cplx K = {(B1.re * A1.re + B1.im * A1.im) / den, (B1.im * A1.re - B1.re * A1.im) / den};
         // g + i f = (1 + i) / (2 sqrt(pi)) * K
         const double fac = 0.5 / sqrt(M_PI);
         const double g = fac * (K.re - K.im);
@@ -117,15 +125,24 @@ template <int NM>
 PSS_HD void moments_n(double q, cplx* I) {
     const double a = 2.0 * M_PI * q;
     if (fabs(q) < 0.5 || fabs(a) < 1.5 * NM) {
+        // term m of I_n is t_m / (n + m + 1), t_m = (i a)^m / m!; the
+        // reciprocals 1/(n + m + 1), n < NM, roll along with m (one division
+        // per term instead of 2 NM)
         cplx t = {1.0, 0.0};
-        for (int n = 0; n < NM; ++n) I[n] = {0.0, 0.0};
+        double rc[NM];
+        for (int n = 0; n < NM; ++n) {
+            I[n] = {0.0, 0.0};
+            rc[n] = 1.0 / (n + 1);
+        }
         for (int m = 0; m < 80; ++m) {
             for (int n = 0; n < NM; ++n) {
-                I[n].re += t.re / (n + m + 1);
-                I[n].im += t.im / (n + m + 1);
+                I[n].re += t.re * rc[n];
+                I[n].im += t.im * rc[n];
             }
-            t = c_mul(t, cplx{0.0, a / (m + 1)});
+            t = c_mul(t, cplx{0.0, a * rc[0]});  // rc[0] = 1 / (m + 1)
             if (fabs(t.re) + fabs(t.im) < 1e-18) break;
+            for (int n = 0; n + 1 < NM; ++n) rc[n] = rc[n + 1];
+            rc[NM - 1] = 1.0 / (m + 1 + NM);
         }
         return;
     }
