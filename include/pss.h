@@ -512,6 +512,13 @@ pss_status pss_server_create(int device, size_t hbm_budget_bytes, int max_slots,
  * search cfg; *ticket identifies the result. */
 pss_status pss_submit_file(pss_server* srv, const pss_fil_desc* fil, const void* host_data,
                            const pss_dd_stage* stages, int nstages, const pss_search_cfg* cfg, uint64_t* ticket);
+/* pss_submit_file with a two-stage plan (pss_dd_plan_subband(fil, stages,
+ * nstages, nsub, group)); files of the same shape and plan share prepared
+ * batches as with pss_submit_file.  PSS_EINVAL for nsub <= 0 and for what
+ * pss_dd_plan_subband rejects. */
+pss_status pss_submit_file_subband(pss_server* srv, const pss_fil_desc* fil, const void* host_data,
+                                   const pss_dd_stage* stages, int nstages, int32_t nsub, int32_t group,
+                                   const pss_search_cfg* cfg, uint64_t* ticket);
 /* Wait up to timeout_ms for a ticket's result: PSS_ENOTREADY if timeout_ms
  * is 0 and it is not ready, PSS_ETIMEOUT if the wait expires.  The result is
  * handed over once (free it with pss_result_free). */

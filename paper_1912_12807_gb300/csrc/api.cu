@@ -1378,6 +1378,8 @@ pss_status pss_single_pulse(pss_ctx* ctx, const pss_plan* plan, const pss_fil_de
             sa.s1 = m1;
             sa.s2 = m2;
             sa.thr_tab = (long long*)(m2 + nb);
+            // a sample sums at most 255 (8-bit) or 1 (1-bit) per kept channel and native sample
+            sa.max_value = (long long)ck * (fil->nbits == 8 ? 255 : 1) * st.ds;
             sa.out = (SpRaw*)ctx->sp_ev.p;
             sa.count = (unsigned long long*)ctx->counter.p;
             sa.cap = devcap;

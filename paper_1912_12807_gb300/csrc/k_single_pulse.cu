@@ -14,8 +14,8 @@
 // k_sp_moments: one pass over the series, 64-bit integer sums.
 // k_sp_thresholds: the integer threshold of every (trial, width), FP64.
 // k_sp_detect: a CTA owns TS samples of one trial; it stages the samples
-// [t0 - wmax + 1, t0 + TS + 2 wmax - 2] in shared memory as a 64-bit
-// prefix sum (so every B_w the tile and its local-maximum windows need is
+// [t0 - wmax + 1, t0 + TS + 2 wmax - 2] in shared memory as a prefix sum
+// (32-bit when every sum of the tile fits, else 64-bit) (so every B_w the tile and its local-maximum windows need is
 // one subtraction), then tests every (t, w).  Detections are appended
 // with an atomic counter; past `cap` they are only counted.
 #include <limits.h>
@@ -71,9 +71,13 @@ __global__ void k_sp_thresholds(const __grid_constant__ SpArgs a) {
     a.thr_tab[i] = t;
 }
 
+// T: the prefix-sum type; 32-bit when every window sum of the launch fits
+// (the host checks the bound), else 64-bit.
+template <typename T>
 __global__ void __launch_bounds__(NT) k_sp_detect(const __grid_constant__ SpArgs a) {
-    extern __shared__ __align__(16) long long R[];  // prefix sums relative to `base`
-    __shared__ long long s_tot[NT];
+    extern __shared__ __align__(16) unsigned char sp_raw[];
+    T* R = reinterpret_cast<T*>(sp_raw);  // prefix sums relative to `base`
+    __shared__ T s_tot[NT];
     const int b = blockIdx.y;
     const int64_t n = a.n;
     const int64_t t0 = (int64_t)blockIdx.x * TS;
@@ -86,28 +90,28 @@ __global__ void __launch_bounds__(NT) k_sp_detect(const __grid_constant__ SpArgs
     // R[k] = sum_{base <= j < base + k} s[j]: per-thread segment sums, then a scan
     const int seg = (L + NT - 1) / NT;
     const int k0 = threadIdx.x * seg;
-    long long acc = 0;
+    T acc = 0;
     for (int k = k0; k < min(k0 + seg, L - 1); ++k) acc += s[base + k];
     s_tot[threadIdx.x] = acc;
     __syncthreads();
     if (threadIdx.x < 32) {
         // exclusive scan of the NT segment totals by one warp (8 per lane)
         constexpr int PER = NT / 32;
-        long long v[PER], run = 0;
+        T v[PER], run = 0;
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
             v[i] = s_tot[threadIdx.x * PER + i];
             run += v[i];
         }
-        long long incl = run;
+        T incl = run;
         for (int off = 1; off < 32; off <<= 1) {
-            const long long u = __shfl_up_sync(0xffffffffu, incl, off);
+            const T u = __shfl_up_sync(0xffffffffu, incl, off);
             if (threadIdx.x >= off) incl += u;
         }
-        long long ex = incl - run;
+        T ex = incl - run;
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
-            const long long t = v[i];
+            const T t = v[i];
             s_tot[threadIdx.x * PER + i] = ex;
             ex += t;
         }
@@ -123,10 +127,15 @@ __global__ void __launch_bounds__(NT) k_sp_detect(const __grid_constant__ SpArgs
         const int w = a.w[i];
         const int64_t tmax = n - w;  // last valid boxcar start
         if (tmax < t0) continue;
-        const long long thr = thr_b[i];
+        // a threshold beyond T's range can never be met by a window sum that fits T
+        const long long thr64 = thr_b[i];
+        constexpr long long TMAX = sizeof(T) == 4 ? (long long)INT_MAX : LLONG_MAX;
+        constexpr long long TMIN = sizeof(T) == 4 ? (long long)INT_MIN : LLONG_MIN;
+        if (thr64 > TMAX) continue;
+        const T thr = (T)(thr64 < TMIN ? TMIN : thr64);
         const int64_t tend = min(t0 + TS - 1, tmax);
         for (int64_t t = t0 + threadIdx.x; t <= tend; t += NT) {
-            const long long B = R[t + w - base] - R[t - base];
+            const T B = R[t + w - base] - R[t - base];
             if (B < thr) continue;
             bool ok = true;
             const int64_t lo = max((int64_t)0, t - w + 1), hi = min(tmax, t + w - 1);
@@ -148,7 +157,26 @@ __global__ void __launch_bounds__(NT) k_sp_detect(const __grid_constant__ SpArgs
 
 }  // namespace
 
-size_t sp_detect_smem(int wmax) { return (size_t)(TS + 3 * wmax) * sizeof(long long); }
+size_t sp_detect_smem(int wmax, bool narrow) {
+    return (size_t)(TS + 3 * wmax) * (narrow ? sizeof(int) : sizeof(long long));
+}
+
+// 32-bit prefix sums suffice when the largest sum a tile forms fits
+bool sp_narrow(const SpArgs& a) {
+    return a.max_value >= 0 && (long long)(TS + 3 * a.wmax) * a.max_value < (1ll << 31) - 1;
+}
+
+cudaError_t launch_detect(const SpArgs& a, cudaStream_t s) {
+    const bool narrow = sp_narrow(a);
+    const size_t shm = sp_detect_smem(a.wmax, narrow);
+    const void* k = narrow ? (const void*)k_sp_detect<int> : (const void*)k_sp_detect<long long>;
+    cudaError_t e = allow_smem(k, shm);
+    if (e != cudaSuccess) return e;
+    dim3 gd((unsigned)((a.n + TS - 1) / TS), (unsigned)a.nb);
+    if (narrow) k_sp_detect<int><<<gd, NT, shm, s>>>(a);
+    else k_sp_detect<long long><<<gd, NT, shm, s>>>(a);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_single_pulse(const SpArgs& a, unsigned long long* s1, unsigned long long* s2, cudaStream_t s) {
     if (a.nb <= 0 || a.n <= 0) return cudaSuccess;
@@ -160,12 +188,7 @@ cudaError_t launch_single_pulse(const SpArgs& a, unsigned long long* s1, unsigne
     k_sp_thresholds<<<(unsigned)((a.nb * a.nw + 127) / 128), 128, 0, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t shm = sp_detect_smem(a.wmax);
-    e = allow_smem((const void*)k_sp_detect, shm);
-    if (e != cudaSuccess) return e;
-    dim3 gd((unsigned)((a.n + TS - 1) / TS), (unsigned)a.nb);
-    k_sp_detect<<<gd, NT, shm, s>>>(a);
-    return cudaGetLastError();
+    return launch_detect(a, s);
 }
 
 cudaError_t launch_sp_moments(const int32_t* series, int64_t stride, int64_t n, int32_t nb, unsigned long long* s1,
@@ -178,12 +201,7 @@ cudaError_t launch_sp_moments(const int32_t* series, int64_t stride, int64_t n, 
 
 cudaError_t launch_sp_detect_only(const SpArgs& a, cudaStream_t s) {
     if (a.nb <= 0 || a.n <= 0) return cudaSuccess;
-    const size_t shm = sp_detect_smem(a.wmax);
-    cudaError_t e = allow_smem((const void*)k_sp_detect, shm);
-    if (e != cudaSuccess) return e;
-    dim3 gd((unsigned)((a.n + TS - 1) / TS), (unsigned)a.nb);
-    k_sp_detect<<<gd, NT, shm, s>>>(a);
-    return cudaGetLastError();
+    return launch_detect(a, s);
 }
 
 }  // namespace pss

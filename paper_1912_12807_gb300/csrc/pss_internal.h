@@ -328,6 +328,7 @@ struct SpArgs {
     const unsigned long long* s1;  // [nb] sum s
     const unsigned long long* s2;  // [nb] sum s^2
     long long* thr_tab;     // [nb][nw] integer thresholds (written by the moments launch)
+    long long max_value;    // largest value a series sample can take (-1: unknown)
     SpRaw* out;
     unsigned long long* count;
     int64_t cap;

@@ -123,8 +123,9 @@ struct Request {
 };
 
 std::string shape_key(const pss_fil_desc& f, const std::vector<uint8_t>& mask, const std::vector<pss_dd_stage>& st,
-                      const pss_search_cfg& c) {
+                      const pss_search_cfg& c, int32_t nsub, int32_t group) {
     std::ostringstream o;
+    o << "sub" << nsub << ',' << group << '|';
     o.precision(17);
     o << f.nchan << '/' << f.nbits << '/' << f.nsamp << '/' << f.tsamp_s << '/' << f.fch0_mhz << '/' << f.foff_mhz
       << '/' << f.layout << '|';
@@ -312,9 +313,9 @@ extern "C" pss_status pss_server_create(int device, size_t hbm_budget_bytes, int
     return PSS_OK;
 }
 
-extern "C" pss_status pss_submit_file(pss_server* srv, const pss_fil_desc* fil, const void* host_data,
-                                      const pss_dd_stage* stages, int nstages, const pss_search_cfg* cfg,
-                                      uint64_t* ticket) {
+// nsub == 0: an exact plan; otherwise a two-stage plan (pss_dd_plan_subband)
+static pss_status submit(pss_server* srv, const pss_fil_desc* fil, const void* host_data, const pss_dd_stage* stages,
+                         int nstages, int32_t nsub, int32_t group, const pss_search_cfg* cfg, uint64_t* ticket) {
     if (!srv || !fil || !host_data || !stages || nstages <= 0 || !cfg || !ticket)
         return fail(PSS_EINVAL, "pss_submit_file: null argument");
     Request* r = new Request();
@@ -325,7 +326,8 @@ extern "C" pss_status pss_submit_file(pss_server* srv, const pss_fil_desc* fil, 
     }
     r->stages.assign(stages, stages + nstages);
     r->cfg = *cfg;
-    pss_status st = pss_dd_plan(&r->fil, r->stages.data(), nstages, &r->plan);
+    pss_status st = nsub > 0 ? pss_dd_plan_subband(&r->fil, r->stages.data(), nstages, nsub, group, &r->plan)
+                             : pss_dd_plan(&r->fil, r->stages.data(), nstages, &r->plan);
     if (st != PSS_OK) {
         delete r;
         return st;
@@ -351,7 +353,7 @@ extern "C" pss_status pss_submit_file(pss_server* srv, const pss_fil_desc* fil, 
         delete r;
         return fail(PSS_ENOMEM, "pss_submit_file: cannot copy the file");
     }
-    r->key = shape_key(r->fil, r->mask, r->stages, r->cfg);
+    r->key = shape_key(r->fil, r->mask, r->stages, r->cfg, nsub, group);
     r->t_submit = Clock::now();
     std::lock_guard<std::mutex> lk(srv->mu);
     r->ticket = srv->next_ticket++;
@@ -360,6 +362,19 @@ extern "C" pss_status pss_submit_file(pss_server* srv, const pss_fil_desc* fil, 
     srv->queue.push_back(r);
     srv->cv_work.notify_all();
     return PSS_OK;
+}
+
+extern "C" pss_status pss_submit_file(pss_server* srv, const pss_fil_desc* fil, const void* host_data,
+                                      const pss_dd_stage* stages, int nstages, const pss_search_cfg* cfg,
+                                      uint64_t* ticket) {
+    return submit(srv, fil, host_data, stages, nstages, 0, 0, cfg, ticket);
+}
+
+extern "C" pss_status pss_submit_file_subband(pss_server* srv, const pss_fil_desc* fil, const void* host_data,
+                                              const pss_dd_stage* stages, int nstages, int32_t nsub, int32_t group,
+                                              const pss_search_cfg* cfg, uint64_t* ticket) {
+    if (nsub <= 0) return fail(PSS_EINVAL, "pss_submit_file_subband: nsub must be > 0");
+    return submit(srv, fil, host_data, stages, nstages, nsub, group, cfg, ticket);
 }
 
 extern "C" pss_status pss_poll(pss_server* srv, uint64_t ticket, int timeout_ms, pss_result** out) {

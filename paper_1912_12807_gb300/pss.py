@@ -69,7 +69,8 @@ EXPORTS = ["pss_ctx_create", "pss_ctx_destroy", "pss_last_error", "pss_version",
            "pss_power_threshold", "pss_ctx_profile", "pss_ctx_profile_read", "pss_dedisperse_noalloc",
            "pss_refine_prepare", "pss_refine_eval", "pss_refine_candidates", "pss_batch_create", "pss_batch_run",
            "pss_batch_footprint", "pss_batch_free", "pss_search_footprint", "pss_ctx_take_cands",
-           "pss_batch_take_cands", "pss_batch_tuning", "pss_server_create", "pss_submit_file", "pss_poll",
+           "pss_batch_take_cands", "pss_batch_tuning", "pss_server_create", "pss_submit_file",
+           "pss_submit_file_subband", "pss_poll",
            "pss_result_cands", "pss_result_free", "pss_server_stats", "pss_server_destroy"]
 PROFILE_STAGES = ["unpack", "dedisperse", "fft", "whiten", "plane", "harmsum"]
 
@@ -128,6 +129,8 @@ def lib():
         "pss_server_create": (st, [C.c_int, C.c_size_t, C.c_int, P(vp)]),
         "pss_submit_file": (st, [vp, P(pss_fil_desc), vp, P(pss_dd_stage), C.c_int, P(pss_search_cfg),
                                  P(C.c_uint64)]),
+        "pss_submit_file_subband": (st, [vp, P(pss_fil_desc), vp, P(pss_dd_stage), C.c_int, i32, i32,
+                                         P(pss_search_cfg), P(C.c_uint64)]),
         "pss_poll": (st, [vp, C.c_uint64, C.c_int, P(vp)]),
         "pss_result_cands": (st, [vp, P(vp), P(i64), P(C.c_double)]),
         "pss_result_free": (None, [vp]),
@@ -532,12 +535,17 @@ class Server:
         _check(lib().pss_server_create(int(device), C.c_size_t(int(hbm_budget_bytes)), int(max_slots), C.byref(h)))
         self.h = h
 
-    def submit(self, desc: FilDesc, data, stages, cfg: pss_search_cfg) -> int:
+    def submit(self, desc: FilDesc, data, stages, cfg: pss_search_cfg, subband=None) -> int:
+        """pss_submit_file, or pss_submit_file_subband when subband = (nsub, group)."""
         arr = np.ascontiguousarray(data, dtype=np.uint8)
         st_arr = stages_array(stages)
         t = C.c_uint64()
-        _check(lib().pss_submit_file(self.h, C.byref(desc.c), arr.ctypes.data, st_arr, len(stages), C.byref(cfg),
-                                     C.byref(t)))
+        if subband is None:
+            _check(lib().pss_submit_file(self.h, C.byref(desc.c), arr.ctypes.data, st_arr, len(stages), C.byref(cfg),
+                                         C.byref(t)))
+        else:
+            _check(lib().pss_submit_file_subband(self.h, C.byref(desc.c), arr.ctypes.data, st_arr, len(stages),
+                                                 int(subband[0]), int(subband[1]), C.byref(cfg), C.byref(t)))
         return int(t.value)
 
     def poll(self, ticket: int, timeout_ms: int = -1):

@@ -100,3 +100,10 @@ def test_single_pulse_constant_input_and_errors(L, ctx):
         L.pss_single_pulse(ctx, plan, _dev(fil.data), 0, 4, widths=(2048,))
     with pytest.raises(L.PssError):
         L.pss_single_pulse(ctx, plan, _dev(fil.data), 0, 4, widths=tuple(range(1, 40)))
+
+
+def test_single_pulse_wide_sums(L, ctx):
+    # heavy downsampling: window sums beyond 32 bits, the 64-bit prefix form
+    fil = _bursty(nsamp=1 << 17, seed=14)
+    stages = [synth.Stage(20.0, 5.0, 6, 256)]
+    _compare(L, ctx, fil, stages, (1, 2, 4, 16), 3.0)

@@ -135,3 +135,26 @@ def test_noalloc_refuses_subband_plan(L, small):
     with pytest.raises(L.PssError) as e:
         L.pss_dedisperse_noalloc(plan, _dev(small.fil.data), 0, 4)
     assert e.value.status == L.PSS_EINVAL
+
+
+def test_server_serves_subband_plans(L, small, monkeypatch):
+    # a two-stage request and an exact one of the same file, served together:
+    # each equals its own prepared batch (default launch shapes)
+    monkeypatch.setenv("PSS_AUTOTUNE", "0")
+    fil, cfg = small.fil, L.cfg_of(small.cfg)
+    desc = L.FilDesc.of(fil)
+    refs = {}
+    for sub in (None, (8, 8)):
+        b = L.pss_batch_create(L.Plan(desc, small.stages, subband=sub), cfg)
+        refs[sub] = b.run(fil.data)
+        b.close()
+    srv = L.Server(8 << 30, max_slots=2)
+    try:
+        tickets = {sub: srv.submit(desc, fil.data, small.stages, cfg, subband=sub) for sub in (None, (8, 8))}
+        for sub, t in tickets.items():
+            got, _ = srv.poll(t)
+            assert got.tobytes() == refs[sub].tobytes(), sub
+        with pytest.raises(L.PssError):
+            srv.submit(desc, fil.data, small.stages, cfg, subband=(0, 8))
+    finally:
+        srv.close()
