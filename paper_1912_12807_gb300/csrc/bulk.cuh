@@ -1,5 +1,7 @@
 // Bulk (TMA engine) copies from global to shared memory completed on an
-// mbarrier, with a bounded wait: shared by the dedispersion kernels.
+// mbarrier, with a bounded wait (the dedispersion kernels), and 8-byte
+// asynchronous copies with zero fill (the double-buffered FFT and plane
+// kernels).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -42,5 +44,16 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
+
+// 8-byte global -> shared copy; src_bytes < 8 fills the rest with zeros
+// (src_bytes 0 reads nothing)
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 }  // namespace pss

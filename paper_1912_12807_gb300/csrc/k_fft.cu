@@ -25,6 +25,7 @@
 #include <math.h>
 #include <stdlib.h>
 
+#include "bulk.cuh"
 #include "fft_small.cuh"
 #include "whiten.cuh"
 #include "pss_internal.h"
@@ -221,14 +222,6 @@ __global__ void __launch_bounds__(NT) k_fft_pass(const __grid_constant__ PassArg
 // twiddles of later passes (prefetched into registers one tile ahead), are
 // applied in shared memory once a tile has landed.  Same arithmetic in the
 // same order as k_fft_pass: the results are bit-identical.
-__device__ __forceinline__ void cp_async8(void* dst, const void* src, uint32_t src_bytes) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-                 "l"(src), "r"(src_bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 template <int R>
 __device__ __forceinline__ void issue_tile(const PassArgs& a, int b, int64_t j0, float2* buf) {

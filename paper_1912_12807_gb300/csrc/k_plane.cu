@@ -19,6 +19,9 @@
 // for every (row, parity) multiplies by the FFT of the taps, transforms back
 // and keeps the L - 2 m_max + 1 outputs that the circular wrap does not
 // touch.  About 70 flops per plane value instead of 16 m(z).
+#include <stdlib.h>
+
+#include "bulk.cuh"
 #include "fft_small.cuh"
 #include "pss_internal.h"
 #include "response.cuh"
@@ -163,6 +166,85 @@ __global__ void __launch_bounds__(NT) k_plane_z0(PlaneArgs a) {
         const float r = re[i] * s1, q = im[i] * s1;
         if (kb + i < M) P[kb + i] = make_float2(p0[i], r * r + q * q);
     }
+}
+
+// The same FIR, double-buffered: a CTA walks `tpc` consecutive tiles of one
+// trial and brings tile t+1 into a second shared-memory buffer by
+// asynchronous 8-byte copies (zero-filled outside the spectrum) while it
+// computes tile t.  Same arithmetic and order: bit-identical planes.
+template <int NTAP, int R>
+__global__ void __launch_bounds__(NT) k_plane_z0_db(PlaneArgs a, int tpc) {
+    constexpr int KB0 = NT * R;
+    constexpr int H = NTAP / 2 - 1;
+    constexpr int TW = KB0 + NTAP - 1;
+    constexpr int TWP = TW + TW / 8 + 1;
+    __shared__ float2 tiles[2 * TWP];
+    const int b = blockIdx.y;
+    const int64_t M = a.nfft / 2;
+    const int64_t ntile = (M + KB0 - 1) / KB0;
+    const int64_t tile0 = (int64_t)blockIdx.x * tpc;
+    const int64_t tile1 = min(ntile, tile0 + tpc);
+    const float2* Ap = a.spec + (int64_t)b * a.spec_stride;
+    auto issue = [&](int64_t tt, float2* buf) {
+        const int64_t k0 = tt * KB0;
+        for (int i = threadIdx.x; i < TW; i += NT) {
+            const int64_t k = k0 - H + i;
+            const bool ok = k >= 0 && k < M;
+            cp_async8(buf + i + (i >> 3), ok ? (const void*)(Ap + k) : (const void*)Ap, ok ? 8u : 0u);
+        }
+    };
+    issue(tile0, tiles);
+    cp_async_commit();
+    const float s1 = a.tap_scale[1];
+    float2* P = reinterpret_cast<float2*>(a.plane + (int64_t)b * a.plane_stride);
+    for (int64_t t = tile0; t < tile1; ++t) {
+        const float2* cur = tiles + ((t - tile0) & 1) * TWP;
+        if (t + 1 < tile1) {
+            issue(t + 1, tiles + ((t + 1 - tile0) & 1) * TWP);
+            cp_async_commit();
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        float re[R], im[R], p0[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) re[i] = im[i] = p0[i] = 0.f;
+        const float2* w = cur + threadIdx.x * (R + R / 8);
+#pragma unroll
+        for (int j = 0; j < R + NTAP - 1; ++j) {
+            const float2 x = w[j + (j >> 3)];
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                const int ti = j - i;
+                if (ti >= 0 && ti < NTAP) {
+                    re[i] = fmaf(x.x, z0_tap<NTAP>(ti), re[i]);
+                    im[i] = fmaf(x.y, z0_tap<NTAP>(ti), im[i]);
+                }
+                if (ti == H) p0[i] = x.x * x.x + x.y * x.y;
+            }
+        }
+        const int64_t kb = t * KB0 + (int64_t)threadIdx.x * R;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const float r = re[i] * s1, q = im[i] * s1;
+            if (kb + i < M) P[kb + i] = make_float2(p0[i], r * r + q * q);
+        }
+        __syncthreads();
+    }
+}
+
+// PSS_PLANE_Z0_DB=0 keeps the single-buffered zmax 0 plane; PSS_PLANE_Z0_TPC
+// sets the tiles per CTA of the double-buffered one (default 4).
+int plane_z0_tpc() {
+    static const int v = [] {
+        const char* e = getenv("PSS_PLANE_Z0_DB");
+        if (e && e[0] == '0') return 0;
+        const char* t = getenv("PSS_PLANE_Z0_TPC");
+        const int x = t ? atoi(t) : 4;
+        return x < 1 ? 1 : x;
+    }();
+    return v;
 }
 
 // ---- overlap-save plane ------------------------------------------------------
@@ -476,7 +558,15 @@ cudaError_t launch_plane(const PlaneArgs& a, cudaStream_t s) {
     const int64_t M = a.nfft / 2;
     if (a.zmax == 0 && a.extra == 16) {
         constexpr int R = 8;
-        dim3 grid((unsigned)((M + NT * R - 1) / (NT * R)), (unsigned)a.nb);
+        const int64_t ntile = (M + NT * R - 1) / (NT * R);
+        const int tpc = plane_z0_tpc();
+        if (tpc > 0) {
+            const int64_t per = std::min<int64_t>(tpc, ntile);
+            dim3 grid((unsigned)((ntile + per - 1) / per), (unsigned)a.nb);
+            k_plane_z0_db<32, R><<<grid, NT, 0, s>>>(a, (int)per);
+            return cudaGetLastError();
+        }
+        dim3 grid((unsigned)ntile, (unsigned)a.nb);
         k_plane_z0<32, R><<<grid, NT, 0, s>>>(a);
         return cudaGetLastError();
     }
