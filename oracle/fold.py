@@ -10,9 +10,14 @@ of trial frequencies around the candidate's:
 
 * Sample j of a series with ds-fold downsampling is at t_j = j * dt,
   dt = ds * tsamp.  Its phase at frequency f and drift fdot (Hz/s) is
-  phi_j = f*t_j + (0.5*fdot)*(t_j*t_j), and its bin is
-  min(floor((phi_j - floor(phi_j)) * nbin), nbin - 1) (FP64, in that order;
-  the product can round up to nbin when the fraction is within an ulp of 1).
+  phi_j = f*t_j + (fdot/2)*t_j^2 = j*x + j^2*g cycles, x = f*dt and
+  g = (0.5*fdot)*(dt*dt) (FP64, in that order).  The phase is carried in
+  64-bit fixed point (units of 2^-64 cycle, wrapping modulo one cycle):
+  X = rint((x - floor(x)) * 2^64), Gq = rint((g - floor(g)) * 2^64)
+  (round half to even; both taken modulo 2^64), phase_j = (j*X + j*j*Gq)
+  mod 2^64, and the bin is ((phase_j >> 32) * nbin) >> 32, i.e. the
+  fraction of the cycle times nbin, rounded down, in integers.  (The
+  rounding of X and Gq moves the phase by at most (j + j^2) 2^-65 cycle.)
 * Profile P_b = sum of s_j over the samples of bin b, n_b their number
   (exact integers).
 * Significance: with mu = S1/N and var = (S2 - S1*S1/N)/N of the series
@@ -25,15 +30,28 @@ of trial frequencies around the candidate's:
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
+
+
+MASK64 = (1 << 64) - 1
+
+
+def fixed_point(v: float) -> int:
+    """rint((v - floor(v)) * 2^64) modulo 2^64, round half to even."""
+    fr = v - math.floor(v)
+    return int(round(math.ldexp(fr, 64))) & MASK64
 
 
 def phase_bins(n: int, dt: float, f: float, fdot: float, nbin: int) -> np.ndarray:
     """int64 [n]: the bin of every sample (module docstring)."""
-    t = np.arange(n, dtype=np.float64) * dt
-    phi = f * t + (0.5 * fdot) * (t * t)
-    frac = phi - np.floor(phi)
-    return np.minimum(np.floor(frac * float(nbin)), float(nbin - 1)).astype(np.int64)
+    X = np.uint64(fixed_point(f * dt))
+    G = np.uint64(fixed_point((0.5 * fdot) * (dt * dt)))
+    j = np.arange(n, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        ph = j * X + (j * j) * G          # uint64 arithmetic wraps modulo 2^64
+    return (((ph >> np.uint64(32)) * np.uint64(nbin)) >> np.uint64(32)).astype(np.int64)
 
 
 def fold(s: np.ndarray, dt: float, f: float, fdot: float, nbin: int):

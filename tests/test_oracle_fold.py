@@ -79,3 +79,24 @@ def test_drift_term_realigns_a_chirped_train():
     none = FO.fold_search(s, dt, T, f0, 0.0, 64, 1, 0.0)[2]
     wrong = FO.fold_search(s, dt, T, f0, -fd, 64, 1, 0.0)[2]
     assert good > 3 * none and good > 3 * wrong
+
+
+def test_fixed_point_phase_matches_exact_rational_phase():
+    # the 64-bit fixed-point bins equal floor(frac(f t + fdot t^2 / 2) nbin) of
+    # the exact rational phase, except where that phase lies within the
+    # fixed-point rounding, (j + j^2) 2^-65 cycle, of a bin edge
+    from fractions import Fraction
+    assert FO.fixed_point(0.25) == 1 << 62 and FO.fixed_point(-0.25) == 3 << 62
+    rng = np.random.default_rng(5)
+    for _ in range(5):
+        f, fd, dt, nbin = rng.uniform(0.5, 400), rng.uniform(-3, 3), rng.uniform(1e-4, 1e-3), int(rng.integers(2, 100))
+        n = 3000
+        got = FO.phase_bins(n, dt, f, fd, nbin)
+        x = Fraction(f * dt)
+        g = Fraction(0.5 * fd) * Fraction(dt * dt)
+        for j in range(0, n, 7):
+            ph = (j * x + j * j * g) % 1
+            b = int(ph * nbin)
+            if b != int(got[j]):
+                edge = min(abs(ph * nbin - b), abs(ph * nbin - (b + 1))) / nbin
+                assert edge <= Fraction(j + j * j + 2, 2 ** 64), (j, b, got[j])
