@@ -1,14 +1,17 @@
 // Folding of candidates' dedispersed series on a grid of trial frequencies
 // (the prepfold step, paper Sect. 2 step 6).
 //
-// One CTA folds one (candidate, trial frequency): sample j (t = j dt) has
-// phase phi = f t + (0.5 fdot)(t t) and bin min(floor(frac(phi) nbin),
-// nbin - 1), FP64 with round-to-nearest intrinsics in that order (no
-// contracted multiply-adds), so every sample lands in the bin the host
-// reading assigns it.  Each thread walks a contiguous run of samples and
-// adds a run of equal bins with one shared-memory atomic; the profile and
-// counts are exact integers.  Thread 0 then forms the reduced chi-square
-// against a flat profile, summing the bins in order.
+// One CTA folds one (candidate, trial frequency): sample j has phase
+// j x + j^2 g cycles (x = f dt, g = (fdot/2) dt^2) carried in 64-bit fixed
+// point (X, G: x and g modulo one cycle in units of 2^-64, rounded to
+// nearest even from FP64 values formed with round-to-nearest intrinsics in
+// the host's order), phase_j = j X + j^2 G modulo 2^64, and bin
+// ((phase_j >> 32) nbin) >> 32: integer arithmetic, so every sample lands in
+// the bin the host reading assigns it, with no FP64 per sample.  Each
+// thread walks a contiguous run of samples and adds a run of equal bins with
+// one shared-memory atomic; the profile and counts are exact integers.
+// Thread 0 then forms the reduced chi-square against a flat profile,
+// summing the bins in order.
 #include "pss_internal.h"
 
 namespace pss {
@@ -30,8 +33,13 @@ __global__ void __launch_bounds__(NT) k_fold(const __grid_constant__ FoldArgs a)
     __syncthreads();
     const double f = __dadd_rn(it.f, __dmul_rn(__dsub_rn((double)k, __ddiv_rn((double)(a.nfreq - 1), 2.0)),
                                                __ddiv_rn(a.step_bins, it.T)));
-    const double hfd = __dmul_rn(0.5, it.fdot);
-    const double nb = (double)a.nbin;
+    // per-sample phase step x = f dt and drift g = (fdot / 2) dt^2 in 64-bit
+    // fixed point (2^-64 cycle, modulo one cycle), rounded to nearest even
+    const double x = __dmul_rn(f, it.dt);
+    const double g = __dmul_rn(__dmul_rn(0.5, it.fdot), __dmul_rn(it.dt, it.dt));
+    const unsigned long long X = __double2ull_rn(ldexp(__dsub_rn(x, floor(x)), 64));
+    const unsigned long long G = __double2ull_rn(ldexp(__dsub_rn(g, floor(g)), 64));
+    const unsigned long long nb = (unsigned long long)a.nbin;
     const int32_t* s = a.series + (int64_t)it.row * a.stride;
     const int64_t n = it.n;
     const int64_t per = (n + NT - 1) / NT;
@@ -40,11 +48,9 @@ __global__ void __launch_bounds__(NT) k_fold(const __grid_constant__ FoldArgs a)
     unsigned long long acc = 0ull;
     unsigned int c = 0u;
     for (int64_t j = j0; j < j1; ++j) {
-        const double t = __dmul_rn((double)j, it.dt);
-        const double phi = __dadd_rn(__dmul_rn(f, t), __dmul_rn(hfd, __dmul_rn(t, t)));
-        const double fr = __dsub_rn(phi, floor(phi));
-        int bin = (int)floor(__dmul_rn(fr, nb));
-        bin = min(bin, a.nbin - 1);
+        const unsigned long long ju = (unsigned long long)j;
+        const unsigned long long ph = ju * X + (ju * ju) * G;  // wraps modulo 2^64: one cycle
+        const int bin = (int)(((ph >> 32) * nb) >> 32);
         if (bin != cur) {
             if (c) {
                 atomicAdd(P + cur, acc);
