@@ -376,6 +376,35 @@ def workload_pmps(seed: int = 1004, nsamp: int = 1 << 23, zmax: int = 0,
                     SearchCfg(zmax=zmax, dz=2.0, numharm=16))
 
 
+# The paper's FAST drift-scan plan (Table 3): rows (start, end, step, ds),
+# each row the half-open range [start, end); 979 trials in all.
+TABLE3_ROWS = ((0.0, 31.5, 0.1, 8), (31.5, 62.9, 0.2, 16), (62.9, 139.4, 0.5, 32),
+               (139.4, 278.4, 1.0, 64), (278.4, 556.4, 2.0, 128), (556.4, 784.4, 3.0, 128))
+
+
+def workload_fast(seed: int = 1006, nsamp: int = 1 << 18, zmax: int = 0) -> Workload:
+    """The paper's FAST test file shape (Table 1; timed in Sect. 3.3): 200 channels
+    over 290-340 MHz, 0.2 ms, 2^18 samples, 8-bit, searched with the
+    Table 3 plan (979 trials, ds 8-128).  Five pulsars (P 0.1-0.9 s, so
+    that the channel smearing at these frequencies, tens of ms at the
+    highest DMs, stays below a tenth of the period; DM 10-700; duty 2-8 %;
+    8-30 sigma folded), two narrowband RFI channels and a zero-DM burst;
+    harmonic sums up to 16."""
+    nchan = 200
+    rng = np.random.default_rng(seed + 7)
+    psrs = []
+    for _ in range(5):
+        duty = rng.uniform(0.02, 0.08)
+        amp = rng.uniform(8.0, 30.0) / math.sqrt(nchan * nsamp * duty)
+        psrs.append(Pulsar(rng.uniform(0.1, 0.9), rng.uniform(10.0, 700.0), duty, amp, phase0=rng.uniform()))
+    rfi = tuple(int(c) for c in rng.choice(nchan, 2, replace=False))
+    fil = make_8bit(nchan, nsamp, 2e-4, 290.0, 340.0, psrs, seed, rfi_chans=rfi,
+                    burst_t_s=0.61 * nsamp * 2e-4)
+    return Workload("fast_200ch_2^18_table3_zmax%d" % zmax, fil,
+                    stages_from_table(TABLE3_ROWS, last_inclusive=False),
+                    SearchCfg(zmax=zmax, dz=2.0, numharm=16))
+
+
 def stream_files(n_files: int = 64, seed0: int = 5000, mean_gap_s: float = 26.0,
                  speedup: float = 50.0, max_log2: int = 19, chans=(128, 256, 512, 1024)):
     """A drift-scan stream: n_files files with channel counts drawn from

@@ -111,3 +111,11 @@ def test_file_shape_sizes():
         name, nchan, ts, dur, mb, bits = ln.split()[:6]
         nbytes = int(nchan) * (float(dur) / float(ts)) * int(bits) / 8
         assert abs(nbytes / 1e6 - float(mb)) / float(mb) < 0.15, name
+
+
+def test_fast_workload_uses_table_3():
+    # the FAST-shaped benchmark file is searched with the printed Table 3 plan
+    rr = _rows()["table3"]
+    assert [tuple(r[:4]) for r in rr] == [tuple(map(float, r[:3])) + (r[3],) for r in synth.TABLE3_ROWS]
+    st = synth.stages_from_table(synth.TABLE3_ROWS, last_inclusive=False)
+    assert sum(s.n_dm for s in st) == 979 and [s.ds for s in st] == [8, 16, 32, 64, 128, 128]
