@@ -47,6 +47,7 @@ METRIC = "DM-trials searched/s and files/s vs 26 s realtime; batched vs plain; p
 UNIT = "DM-trials/s"
 REALTIME_S = 26.0
 OLA_L = 2048  # overlap-save segment of the zmax > 0 plane
+BX_MIN = int(os.environ.get("PSS_DEDISP_BX_MIN") or "8")  # rows with ds >= this use the boxcar table (0: none)
 
 WORKLOADS = {
     "driftscan": "driftscan_256ch_2^18_8bit_dm0-500x0.5_1001trials_zmax0_numharm16",
@@ -456,6 +457,12 @@ def run_ours(args, rank, world, local_rank):
         rooflines[st] = roofline_of(st, bound, amount * args.steps, unit, ms_st, n_st, peaks, peak_kind)
         if args.dm_trials is None:
             rooflines[st]["traffic"] = recorded_traffic(name, st)
+    bx_rows = [s.ds for s in wl.stages if BX_MIN > 0 and BX_MIN <= s.ds <= 256]
+    if bx_rows and "dedisperse" in rooflines:
+        rooflines["dedisperse"]["note"] = (
+            "rows with ds %s dedisperse from a per-channel boxcar table (one term per output and channel, "
+            "plus one table build per ds); achieved counts the definition's C x N_v x ds additions"
+            % sorted(set(bx_rows)))
     dominant = max(prof, key=lambda k: prof[k][0])
     launches_per_step = sum(n for _, n in prof.values()) / args.steps
     bi = fil.nbytes()

@@ -223,6 +223,18 @@ pss_status setup_input(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* f
                                  cudaMemcpyHostToDevice, s));
     }
     PSS_TRY(ctx->xcm.ensure((size_t)ck * pitch + 64));
+    // the boxcar table of the downsampled rows (exact plans only)
+    if (plan->nsub == 0) {
+        size_t need_bx = 0;
+        for (const auto& st : plan->stages)
+            if (st.n_dm > 0 && st.first < dm_end && st.first + st.n_dm > dm_begin && bx_use(ctx->tune, st.ds))
+                need_bx = std::max(need_bx, bx_table_bytes(ck, plan->nsamp, st.ds));
+        if (need_bx) {
+            const void* was = ctx->bx.p;
+            PSS_TRY(ctx->bx.ensure(need_bx));
+            if (ctx->bx.p != was) ctx->bx_ds = 0;
+        }
+    }
     if (!ctx->errflag.p) {
         PSS_TRY(ctx->errflag.ensure(sizeof(int)));
         PSS_CUDA(cudaMemsetAsync(ctx->errflag.p, 0, sizeof(int), s));
@@ -264,6 +276,7 @@ pss_status enqueue_prep(pss_ctx* ctx, const pss_fil_desc* fil, const uint8_t* sr
     pa.pitch = pitch;
     ProfScope ps(ctx, 0, s);
     PSS_CUDA(launch_prep(pa, s));
+    ctx->bx_ds = 0;  // the boxcar table no longer matches the channel-major data
     return PSS_OK;
 }
 
@@ -355,6 +368,40 @@ pss_status enqueue_dedisp(pss_ctx* ctx, const pss_plan* plan, int32_t ck, int64_
                           const SubBatch& SB, void* subu, float* out_f, int32_t* out_i, int64_t out_stride,
                           unsigned long long* sums, cudaStream_t s) {
     const int32_t* base = (const int32_t*)ctx->delays_dev.p;
+    // downsampled row: one boxcar table per ds (built once per file and ds), then one term per channel;
+    // a few trials alone do not pay for building the table
+    if (!T.on && bx_use(ctx->tune, st.ds) && ctx->bx.bytes >= bx_table_bytes(ck, plan->nsamp, st.ds) &&
+        (ctx->bx_ds == st.ds || nb >= 16)) {
+        ProfScope ps(ctx, 1, s);
+        if (ctx->bx_ds != st.ds) {
+            BxTableArgs ta{};
+            ta.xcm = (const uint8_t*)ctx->xcm.p;
+            ta.pitch = pitch;
+            ta.ck = ck;
+            ta.nsamp = plan->nsamp;
+            ta.lds = ilog2(st.ds);
+            ta.lmt = ilog2(bx_table_cols(st.ds));
+            ta.mlen = bx_mlen(plan->nsamp, st.ds);
+            ta.mstride = bx_mstride(plan->nsamp, st.ds);
+            ta.table = (uint16_t*)ctx->bx.p;
+            PSS_CUDA(launch_bx_table(ta, s));
+            ctx->bx_ds = st.ds;
+        }
+        BxArgs ba{};
+        ba.table = (const uint16_t*)ctx->bx.p;
+        ba.mstride = bx_mstride(plan->nsamp, st.ds);
+        ba.ck = ck;
+        ba.lds = ilog2(st.ds);
+        ba.delays = base + ck + (b0 - dm_begin) * ck;
+        ba.nb = nb;
+        ba.nv = st.nv;
+        ba.out_f = out_f;
+        ba.out_i = out_i;
+        ba.out_stride = out_stride;
+        ba.sums = sums;
+        PSS_CUDA(launch_dedisp_bx(ba, s));
+        return PSS_OK;
+    }
     if (!T.on) {
         DedispArgs da{};
         da.xcm = (const uint8_t*)ctx->xcm.p;
@@ -1148,6 +1195,8 @@ pss_status pss_ctx_create(int device, pss_ctx** out) {
     if (const char* f = getenv("PSS_FUSED")) c->tune.fused = f[0] == '1';
     // PSS_PLANE_FORM=0 / 1: the radix 8-8-8-4 / 16-16-8 overlap-save plane kernel
     if (const char* f = getenv("PSS_PLANE_FORM")) c->tune.plane_form = f[0] == '1';
+    // PSS_DEDISP_BX_MIN=k: rows with ds >= k use the boxcar-table dedispersion (0: never)
+    if (const char* f = getenv("PSS_DEDISP_BX_MIN")) c->tune.bx_min = std::max(0, atoi(f));
     // PSS_WHITEN_FORM=0 / 1 / 2: block per CTA / warp per block / warp pair per block
     if (const char* f = getenv("PSS_WHITEN_FORM")) c->tune.whiten_form = (f[0] >= '0' && f[0] <= '2') ? f[0] - '0' : -1;
     *out = c;
@@ -1159,7 +1208,7 @@ void pss_ctx_destroy(pss_ctx* c) {
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     DevBuf* bufs[] = {&c->fil_dev, &c->xcm, &c->delays_dev, &c->subu, &c->sp_series, &c->sp_mom, &c->sp_ev,
-                      &c->fold_buf, &c->series, &c->sums, &c->fftA, &c->fftB,
+                      &c->fold_buf, &c->bx, &c->series, &c->sums, &c->fftA, &c->fftB,
                       &c->spec, &c->plane, &c->cands, &c->counter, &c->taps, &c->ftaps, &c->tapinfo, &c->errflag,
                       &c->twid, &c->chan_spec, &c->refine_gains, &c->refine_dtau, &c->refine_pts, &c->refine_out};
     for (DevBuf* b : bufs) b->release();
@@ -1910,7 +1959,7 @@ namespace pss {
 namespace {
 
 size_t ctx_bytes(const pss_ctx* c) {
-    const DevBuf* bufs[] = {&c->fil_dev, &c->xcm, &c->delays_dev, &c->subu, &c->series, &c->sums, &c->fftA,
+    const DevBuf* bufs[] = {&c->fil_dev, &c->xcm, &c->delays_dev, &c->subu, &c->bx, &c->series, &c->sums, &c->fftA,
                             &c->fftB, &c->spec, &c->plane, &c->cands, &c->counter, &c->taps, &c->ftaps, &c->tapinfo,
                             &c->errflag, &c->twid};
     size_t t = 0;
@@ -2156,11 +2205,12 @@ size_t search_footprint(const Plan& plan, const pss_fil_desc* fil, const pss_sea
     size_t t = buf((size_t)file_bytes(fil)) + buf((size_t)ck * pitch + 64) + buf(tables * sizeof(int32_t)) +
                buf(sizeof(int)) + buf((size_t)dev_cap * sizeof(pss_raw_cand)) + buf(sizeof(unsigned long long));
     int64_t nfft_max = 0, total_taps = 0;
-    size_t need_series = 0, need_fft = 0, need_sums = 0, need_plane = 0, subu = 0;
+    size_t need_series = 0, need_fft = 0, need_sums = 0, need_plane = 0, subu = 0, bx = 0;
     std::vector<int64_t> sizes;
     for (const auto& st : plan.stages) {
         nfft_max = std::max<int64_t>(nfft_max, st.nfft);
         if (st.n_dm <= 0) continue;
+        if (plan.nsub == 0 && bx_use(Tune{}, st.ds)) bx = std::max(bx, bx_table_bytes((int32_t)ck, plan.nsamp, st.ds));
         if (std::find(sizes.begin(), sizes.end(), st.nfft) == sizes.end()) {
             sizes.push_back(st.nfft);
             t += buf((size_t)(st.nfft / 2) * sizeof(float2));  // inter-pass twiddles (at most M entries)
@@ -2185,7 +2235,7 @@ size_t search_footprint(const Plan& plan, const pss_fil_desc* fil, const pss_sea
         t += buf((size_t)nz * 2 * PLANE_FFT_L * sizeof(float2));
     t += buf((size_t)nfft_max * sizeof(float2)) + buf(need_series) + buf(need_sums) + 3 * buf(need_fft) +
          buf(need_plane) + buf((size_t)total_taps * sizeof(float2)) + buf((size_t)5 * nz * sizeof(int32_t)) +
-         buf(subu);
+         buf(subu) + buf(bx);
     return t;
 }
 

@@ -141,6 +141,7 @@ struct Tune {
     int whiten_form = -1;  // whitening kernel form (-1: default, the warp pair per block)
     int fused = 0;         // zmax 0, nfft 2^18: cluster-fused FFT + whitening + plane (where the device allows)
     int plane_form = 1;    // overlap-save plane kernel form (1: radix 16-16-8, 0: radix 8-8-8-4)
+    int bx_min = 8;        // rows with ds >= bx_min (and <= 256) dedisperse from the boxcar table (0: never)
 };
 
 struct Ctx {
@@ -155,6 +156,8 @@ struct Ctx {
     DevBuf sp_mom;       // unsigned long long [2][B] moments
     DevBuf sp_ev;        // SpRaw detections
     DevBuf fold_buf;     // folding items and outputs
+    DevBuf bx;           // uint16 boxcar table of the downsampled rows
+    int bx_ds = 0;       // the ds the table holds for the current channel-major file (0: none)
     std::vector<int32_t> delays_host;  // what delays_dev holds (keep list + delays), empty if unknown
     uint64_t delays_gen = 0;           // bumped whenever delays_dev is rewritten
     std::shared_ptr<void> path_cache;  // last search set-up (api.cu), valid while delays_gen matches
@@ -304,6 +307,53 @@ struct SubsumArgs {
     int* err;               // set to 1 if a bounded wait expires (nullable)
 };
 cudaError_t launch_subsum(const SubsumArgs& a, cudaStream_t s);
+
+// Dedispersion of downsampled rows from a per-channel boxcar table
+// (k_dedisp_bx.cu): Wt[c][p][m] = sum_{k<ds} x[c][m ds + p + k] (uint16,
+// rows of mstride; ds a power of two), then
+// s_ds[j] = sum_c Wt[c][d_c mod ds][d_c div ds + j].
+constexpr int BX_MAX_DS = 256;  // 255 * ds fits 16 bits
+struct BxTableArgs {
+    const uint8_t* xcm;
+    int64_t pitch;
+    int32_t ck;
+    int64_t nsamp;
+    int32_t lds;       // ds = 2^lds
+    int32_t lmt;       // table columns per CTA: 2^lmt = bx_table_cols(ds)
+    int64_t mlen;      // columns per phase row: ceil(nsamp / ds)
+    int64_t mstride;   // elements between phase rows (>= mlen)
+    uint16_t* table;   // [ck][ds][mstride]
+};
+struct BxArgs {
+    const uint16_t* table;
+    int64_t mstride;
+    int32_t ck;
+    int32_t lds;            // ds = 2^lds
+    const int32_t* delays;  // [nb][ck]
+    int32_t nb;
+    int64_t nv;
+    float* out_f;           // [nb][out_stride] or null
+    int32_t* out_i;         // [nb][out_stride] or null
+    int64_t out_stride;
+    unsigned long long* sums;  // [nb] or null
+};
+int bx_table_cols(int ds);
+// columns per phase row and the row stride (16-byte rows)
+inline int64_t bx_mlen(int64_t nsamp, int ds) { return (nsamp + ds - 1) / ds; }
+inline int64_t bx_mstride(int64_t nsamp, int ds) { return (bx_mlen(nsamp, ds) + 7) & ~int64_t(7); }
+inline size_t bx_table_bytes(int32_t ck, int64_t nsamp, int ds) {
+    return (size_t)ck * (size_t)ds * (size_t)bx_mstride(nsamp, ds) * sizeof(uint16_t);
+}
+inline bool bx_use(const Tune& t, int ds) {
+    return t.bx_min > 0 && ds >= t.bx_min && ds >= 2 && ds <= BX_MAX_DS && (ds & (ds - 1)) == 0;
+}
+inline int ilog2(int v) {
+    int l = 0;
+    while ((1 << (l + 1)) <= v) ++l;
+    return l;
+}
+cudaError_t launch_bx_table(const BxTableArgs& a, cudaStream_t s);
+cudaError_t launch_dedisp_bx(const BxArgs& a, cudaStream_t s);
 // bytes past the last stage-1 row that stage 2's staging copies may read
 inline size_t subsum_slack_bytes(int32_t spread) { return (size_t)(1024 + spread + 16) * 4; }
 

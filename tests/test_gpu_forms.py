@@ -41,3 +41,34 @@ def test_fft_and_plane_forms_are_bit_identical(tmp_path, nsamp):
     a = _run(tmp_path, {"PSS_FFT_DB": "0", "PSS_PLANE_Z0_DB": "0"}, nsamp, "single")
     b = _run(tmp_path, {"PSS_FFT_DB": "1", "PSS_FFT_TPC": "3", "PSS_PLANE_Z0_TPC": "3"}, nsamp, "double")
     assert a.shape == b.shape and a.tobytes() == b.tobytes()
+
+
+CHILD_DD = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, {root!r})
+from paper_1912_12807_gb300 import pss, synth
+fil = synth.make_8bit(48, 40000, 2e-4, 1200.0, 1500.0, [synth.Pulsar(0.01, 30.0, 0.05, 0.5)], seed=11)
+stages = [synth.Stage(0.0, 2.0, 5, 1), synth.Stage(10.0, 2.0, 4, 2), synth.Stage(18.0, 3.0, 3, 4),
+          synth.Stage(27.0, 4.0, 9, 8), synth.Stage(63.0, 5.0, 17, 16), synth.Stage(148.0, 20.0, 3, 128),
+          synth.Stage(208.0, 30.0, 2, 256), synth.Stage(268.0, 40.0, 2, 512)]
+ctx = pss.Context(0)
+plan = pss.Plan(pss.FilDesc.of(fil), stages)
+d = torch.from_numpy(fil.data).cuda()
+a = pss.pss_dedisperse(ctx, plan, d, 0, plan.ndm).cpu().numpy()
+b = pss.pss_dedisperse(ctx, plan, d, 7, 30).cpu().numpy()
+np.save({out!r}, np.concatenate([a.ravel(), b.ravel()]))
+"""
+
+
+def test_dedisp_boxcar_table_and_direct_forms_are_identical(tmp_path):
+    # rows with ds in [PSS_DEDISP_BX_MIN, 256] dedisperse from the boxcar table; 0 turns it off
+    outs = []
+    for tag, v in (("direct", "0"), ("table2", "2"), ("default", None)):
+        out = str(tmp_path / ("dd_%s.npy" % tag))
+        env = dict(os.environ)
+        env.pop("PSS_DEDISP_BX_MIN", None)
+        if v is not None:
+            env["PSS_DEDISP_BX_MIN"] = v
+        subprocess.run([sys.executable, "-c", CHILD_DD.format(root=ROOT, out=out)], env=env, check=True, timeout=600)
+        outs.append(np.load(out))
+    assert outs[0].tobytes() == outs[1].tobytes() == outs[2].tobytes()
