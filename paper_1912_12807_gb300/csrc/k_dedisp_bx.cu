@@ -18,7 +18,8 @@
 //
 // k_dedisp_bx: a CTA owns GW consecutive trials (one warp each) and a tile
 // of TJ output samples; the lanes of a warp turn 32 channels' delays into
-// table offsets at once (one division each) and pass them round by shuffle.
+// table offsets at once (ds is a power of two: a shift and a mask each) and
+// pass them round by shuffle.
 // Adjacent trials mostly share a channel's phase row and offset, so their
 // warps read the same lines through L1.
 #include "pss_internal.h"
@@ -28,7 +29,7 @@ namespace pss {
 namespace {
 
 constexpr int TB_NT = 256;     // table builder threads
-constexpr int TB_SPAN = 8192;  // native samples per table-builder CTA (about)
+constexpr int TB_SPAN = 8192;  // native samples per table-builder CTA, plus a tail of ds
 constexpr int GW = 8;          // trials (warps) per dedispersion CTA
 constexpr int KJ = 8;          // outputs per lane
 constexpr int TJ = 32 * KJ;    // outputs per tile
