@@ -266,7 +266,10 @@ def stage_work(plan, wl, fil_nbytes):
     """Algorithmic work of one step per profiled stage: (bound, amount, unit).
 
     dedisperse: kept channels x output samples x ds additions (each output
-    sample sums one 8-bit sample per channel per native sample);
+    sample sums one 8-bit sample per channel per native sample), two 16-bit
+    SWAR additions per 32-bit add; rows that dedisperse from the boxcar table
+    add one 16-bit table term per channel and output sample with one 32-bit
+    add, counted as the two SWAR slots it takes; bxtable: the table builds;
     unpack: file read + channel-major write; fft: every pass reads and writes
     8 bytes per complex point; whiten: spectrum read + write; plane: for
     zmax 0 the spectrum read + plane write, for zmax > 0 the flops of the
@@ -283,7 +286,10 @@ def stage_work(plan, wl, fil_nbytes):
         t = plan.trial(i)
         nv, nfft, ds = t["nv"], t["nfft"], t["ds"]
         M = nfft // 2
-        adds += float(wl.fil.nchan) * nv * ds
+        if BX_MIN > 0 and BX_MIN <= ds <= 256:
+            adds += 2.0 * wl.fil.nchan * nv  # one 32-bit add per table term: two SWAR add slots
+        else:
+            adds += float(wl.fil.nchan) * nv * ds
         passes = max(1, int(math.ceil(math.log2(M) / 10)))
         fft_b += passes * 2 * 8.0 * M
         whiten_b += 2 * 8.0 * M
@@ -303,8 +309,16 @@ def stage_work(plan, wl, fil_nbytes):
                     z = -cfg.zmax + j * cfg.dz
                     m = int(math.ceil(abs(z) / 2)) + cfg.halfwidth_extra
                     plane_flops += 2 * (2 * m) * 8.0 * M
+    # boxcar-table builds (rows with ds in [BX_MIN, 256]): one per distinct ds, reading the
+    # channel-major bytes and writing the uint16 table of C x ds x ceil(N/ds) (rows of 8)
+    C, N = wl.fil.nchan, wl.fil.nsamp
+    bx_b = 0.0
+    for ds in sorted({s.ds for s in wl.stages if s.n_dm > 0 and BX_MIN > 0 and BX_MIN <= s.ds <= 256}):
+        mstride = ((N + ds - 1) // ds + 7) // 8 * 8
+        bx_b += float(C) * N + 2.0 * C * ds * mstride
     return {"unpack": ("hbm", 2.0 * fil_nbytes, "bytes"),
             "dedisperse": ("alu", adds, "channel-adds"),
+            "bxtable": ("hbm", bx_b, "bytes"),
             "fft": ("hbm", fft_b, "bytes"),
             "whiten": ("hbm", whiten_b, "bytes"),
             "plane": ("hbm", plane_b, "bytes") if cfg.zmax == 0 else ("alu", plane_flops, "flops"),
@@ -460,8 +474,8 @@ def run_ours(args, rank, world, local_rank):
     bx_rows = [s.ds for s in wl.stages if BX_MIN > 0 and BX_MIN <= s.ds <= 256]
     if bx_rows and "dedisperse" in rooflines:
         rooflines["dedisperse"]["note"] = (
-            "rows with ds %s dedisperse from a per-channel boxcar table (one term per output and channel, "
-            "plus one table build per ds); achieved counts the definition's C x N_v x ds additions"
+            "rows with ds %s dedisperse from a per-channel boxcar table built once per ds (stage bxtable): "
+            "one table term per output and channel, a 32-bit add counted as two 16-bit SWAR slots"
             % sorted(set(bx_rows)))
     dominant = max(prof, key=lambda k: prof[k][0])
     launches_per_step = sum(n for _, n in prof.values()) / args.steps

@@ -149,14 +149,16 @@ const char* pss_version(void);
 /* Per-stage device-time accounting (tracing).  While enabled, every kernel
  * launch of the search path is bracketed by CUDA events on the stream it is
  * launched on.  Stages: 0 unpack/transpose, 1 dedisperse, 2 FFT passes,
- * 3 R2C + whitening, 4 f-fdot plane, 5 harmonic sum + compaction.
+ * 3 R2C + whitening, 4 f-fdot plane, 5 harmonic sum + compaction,
+ * 6 boxcar-table builds of the downsampled rows (dedispersion of a row
+ * with ds 8-256 is then stage 1).
  * pss_ctx_profile(ctx, 1) enables and resets; (ctx, 0) disables.
  * pss_ctx_profile_read synchronises the recorded events and returns the
  * summed milliseconds and launch counts of each stage (arrays of
  * PSS_NPROF_STAGES), then resets the records.  The paper reports only
  * whole-pipeline wall-clock times (Table 4, Fig. 1); this has no
  * counterpart there. */
-#define PSS_NPROF_STAGES 6
+#define PSS_NPROF_STAGES 7
 pss_status pss_ctx_profile(pss_ctx* ctx, int enable);
 pss_status pss_ctx_profile_read(pss_ctx* ctx, double* ms, int64_t* launches);
 

@@ -372,8 +372,8 @@ pss_status enqueue_dedisp(pss_ctx* ctx, const pss_plan* plan, int32_t ck, int64_
     // a few trials alone do not pay for building the table
     if (!T.on && bx_use(ctx->tune, st.ds) && ctx->bx.bytes >= bx_table_bytes(ck, plan->nsamp, st.ds) &&
         (ctx->bx_ds == st.ds || nb >= 16)) {
-        ProfScope ps(ctx, 1, s);
         if (ctx->bx_ds != st.ds) {
+            ProfScope pt(ctx, 6, s);
             BxTableArgs ta{};
             ta.xcm = (const uint8_t*)ctx->xcm.p;
             ta.pitch = pitch;
@@ -387,6 +387,7 @@ pss_status enqueue_dedisp(pss_ctx* ctx, const pss_plan* plan, int32_t ck, int64_
             PSS_CUDA(launch_bx_table(ta, s));
             ctx->bx_ds = st.ds;
         }
+        ProfScope ps(ctx, 1, s);
         BxArgs ba{};
         ba.table = (const uint16_t*)ctx->bx.p;
         ba.mstride = bx_mstride(plan->nsamp, st.ds);

@@ -72,7 +72,7 @@ EXPORTS = ["pss_ctx_create", "pss_ctx_destroy", "pss_last_error", "pss_version",
            "pss_batch_take_cands", "pss_batch_tuning", "pss_server_create", "pss_submit_file",
            "pss_submit_file_subband", "pss_poll",
            "pss_result_cands", "pss_result_free", "pss_server_stats", "pss_server_destroy"]
-PROFILE_STAGES = ["unpack", "dedisperse", "fft", "whiten", "plane", "harmsum"]
+PROFILE_STAGES = ["unpack", "dedisperse", "fft", "whiten", "plane", "harmsum", "bxtable"]
 
 _lib = None
 
