@@ -1,5 +1,6 @@
-"""The benchmark's reference arm on the host cores: one JSON line with the
-keys every arm prints, the oracle's rate in it, and nothing on the GPU."""
+"""Host-side checks of the benchmark: the reference arm's JSON line on the
+host cores (the keys every arm prints, the oracle's rate in it, nothing on
+the GPU), and the algorithmic work it divides by kernel time."""
 import json
 import os
 import subprocess
@@ -25,3 +26,29 @@ def test_reference_arm_prints_one_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_stage_work_counts_table_terms_and_builds():
+    # rows with ds in [8, 256] dedisperse from the boxcar table: one term per channel and
+    # output sample (a 32-bit add, two SWAR slots); one table build per distinct ds
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1912_12807_gb300 import build, pss, synth
+    if not os.path.exists(pss.LIB_PATH):
+        build.build()
+    wl = synth.workload_fast()
+    plan = pss.Plan(pss.FilDesc.of(wl.fil), wl.stages)
+    w = bench.stage_work(plan, wl, wl.fil.nbytes())
+    C, N = wl.fil.nchan, wl.fil.nsamp
+    terms = sum(plan.trial(i)["nv"] for i in range(plan.ndm)) * C
+    assert w["dedisperse"] == ("alu", 2.0 * terms, "channel-adds")
+    dss = sorted({s.ds for s in wl.stages})
+    assert dss == [8, 16, 32, 64, 128]
+    build = sum(C * N + 2 * C * ds * (((N + ds - 1) // ds + 7) // 8 * 8) for ds in dss)
+    assert w["bxtable"] == ("hbm", float(build), "bytes")
+    # a plan of ds 1 rows has no table
+    small = synth.workload_small()
+    p2 = pss.Plan(pss.FilDesc.of(small.fil), small.stages)
+    w2 = bench.stage_work(p2, small, small.fil.nbytes())
+    assert w2["bxtable"][1] == 0.0
+    assert w2["dedisperse"][1] == float(small.fil.nchan) * sum(p2.trial(i)["nv"] for i in range(p2.ndm))
