@@ -2207,11 +2207,13 @@ size_t search_footprint(const Plan& plan, const pss_fil_desc* fil, const pss_sea
                buf(sizeof(int)) + buf((size_t)dev_cap * sizeof(pss_raw_cand)) + buf(sizeof(unsigned long long));
     int64_t nfft_max = 0, total_taps = 0;
     size_t need_series = 0, need_fft = 0, need_sums = 0, need_plane = 0, subu = 0, bx = 0;
+    Tune bx_tune;  // the boxcar-table threshold a new context takes (environment included)
+    if (const char* f = getenv("PSS_DEDISP_BX_MIN")) bx_tune.bx_min = std::max(0, atoi(f));
     std::vector<int64_t> sizes;
     for (const auto& st : plan.stages) {
         nfft_max = std::max<int64_t>(nfft_max, st.nfft);
         if (st.n_dm <= 0) continue;
-        if (plan.nsub == 0 && bx_use(Tune{}, st.ds)) bx = std::max(bx, bx_table_bytes((int32_t)ck, plan.nsamp, st.ds));
+        if (plan.nsub == 0 && bx_use(bx_tune, st.ds)) bx = std::max(bx, bx_table_bytes((int32_t)ck, plan.nsamp, st.ds));
         if (std::find(sizes.begin(), sizes.end(), st.nfft) == sizes.end()) {
             sizes.push_back(st.nfft);
             t += buf((size_t)(st.nfft / 2) * sizeof(float2));  // inter-pass twiddles (at most M entries)
