@@ -47,21 +47,34 @@ CHILD_DD = r"""
 import sys, numpy as np, torch
 sys.path.insert(0, {root!r})
 from paper_1912_12807_gb300 import pss, synth
-fil = synth.make_8bit(48, 40000, 2e-4, 1200.0, 1500.0, [synth.Pulsar(0.01, 30.0, 0.05, 0.5)], seed=11)
-stages = [synth.Stage(0.0, 2.0, 5, 1), synth.Stage(10.0, 2.0, 4, 2), synth.Stage(18.0, 3.0, 3, 4),
-          synth.Stage(27.0, 4.0, 9, 8), synth.Stage(63.0, 5.0, 17, 16), synth.Stage(148.0, 20.0, 3, 128),
-          synth.Stage(208.0, 30.0, 2, 256), synth.Stage(268.0, 40.0, 2, 512)]
+sys.path.insert(0, {tests!r})
+from test_gpu_forms import dd_case
+fil, stages = dd_case()
 ctx = pss.Context(0)
 plan = pss.Plan(pss.FilDesc.of(fil), stages)
 d = torch.from_numpy(fil.data).cuda()
 a = pss.pss_dedisperse(ctx, plan, d, 0, plan.ndm).cpu().numpy()
-b = pss.pss_dedisperse(ctx, plan, d, 7, 30).cpu().numpy()
+b = pss.pss_dedisperse(ctx, plan, d, 40, 95).cpu().numpy()
 np.save({out!r}, np.concatenate([a.ravel(), b.ravel()]))
 """
 
 
+def dd_case():
+    """48 channels x 40000 samples; rows of ds 1 to 512, most with 16 or more
+    trials (a call takes the boxcar table for a row of ds in [PSS_DEDISP_BX_MIN,
+    256] when it has at least 16 of its trials)."""
+    from paper_1912_12807_gb300 import synth
+    fil = synth.make_8bit(48, 40000, 2e-4, 1200.0, 1500.0, [synth.Pulsar(0.01, 30.0, 0.05, 0.5)], seed=11)
+    stages = [synth.Stage(0.0, 2.0, 5, 1), synth.Stage(10.0, 2.0, 16, 2), synth.Stage(42.0, 3.0, 16, 4),
+              synth.Stage(90.0, 4.0, 16, 8), synth.Stage(154.0, 5.0, 17, 16), synth.Stage(239.0, 20.0, 16, 128),
+              synth.Stage(559.0, 30.0, 16, 256), synth.Stage(1039.0, 40.0, 2, 512)]
+    return fil, stages
+
+
 def test_dedisp_boxcar_table_and_direct_forms_are_identical(tmp_path):
     # rows with ds in [PSS_DEDISP_BX_MIN, 256] dedisperse from the boxcar table; 0 turns it off
+    from oracle import dedisperse as OD
+    from oracle import plan as OP
     outs = []
     for tag, v in (("direct", "0"), ("table2", "2"), ("default", None)):
         out = str(tmp_path / ("dd_%s.npy" % tag))
@@ -69,6 +82,20 @@ def test_dedisp_boxcar_table_and_direct_forms_are_identical(tmp_path):
         env.pop("PSS_DEDISP_BX_MIN", None)
         if v is not None:
             env["PSS_DEDISP_BX_MIN"] = v
-        subprocess.run([sys.executable, "-c", CHILD_DD.format(root=ROOT, out=out)], env=env, check=True, timeout=600)
+        child = CHILD_DD.format(root=ROOT, tests=os.path.join(ROOT, "tests"), out=out)
+        subprocess.run([sys.executable, "-c", child], env=env, check=True, timeout=600)
         outs.append(np.load(out))
     assert outs[0].tobytes() == outs[1].tobytes() == outs[2].tobytes()
+    # and the first and last trial of every row equal the oracle's series
+    fil, stages = dd_case()
+    op = OP.Plan.for_file(fil, stages)
+    x = OD.channel_major(fil.data, fil.nchan, 8)
+    off, first = 0, 0
+    for st in stages:
+        for i in range(first, first + st.n_dm):
+            nv, _ = op.nv_nfft(i)
+            if i in (first, first + st.n_dm - 1):
+                ref = OD.dedisperse(x, op.delays[i], op.max_delay, st.ds)
+                np.testing.assert_array_equal(outs[1][off:off + nv], ref, err_msg="DM index %d" % i)
+            off += nv
+        first += st.n_dm
