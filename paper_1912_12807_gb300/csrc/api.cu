@@ -370,7 +370,7 @@ pss_status enqueue_dedisp(pss_ctx* ctx, const pss_plan* plan, int32_t ck, int64_
     const int32_t* base = (const int32_t*)ctx->delays_dev.p;
     // downsampled row: one boxcar table per ds (built once per file and ds), then one term per channel;
     // a few trials alone do not pay for building the table
-    if (!T.on && bx_use(ctx->tune, st.ds) && ctx->bx.bytes >= bx_table_bytes(ck, plan->nsamp, st.ds) &&
+    if (!T.on && bx_use(ctx->tune, st.ds) && ck <= 65535 && ctx->bx.bytes >= bx_table_bytes(ck, plan->nsamp, st.ds) &&
         (ctx->bx_ds == st.ds || nb >= 16)) {
         if (ctx->bx_ds != st.ds) {
             ProfScope pt(ctx, 6, s);
