@@ -49,8 +49,9 @@ def test_struct_layout_matches_binding(L):
 #include <stddef.h>
 #include "pss.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(pss_fil_desc), sizeof(pss_dd_stage), sizeof(pss_search_cfg),
-         sizeof(pss_raw_cand), sizeof(pss_cand), offsetof(pss_cand, power), offsetof(pss_fil_desc, chan_mask));
+  printf("%zu %zu %zu %zu %zu %zu %zu %d\n", sizeof(pss_fil_desc), sizeof(pss_dd_stage), sizeof(pss_search_cfg),
+         sizeof(pss_raw_cand), sizeof(pss_cand), offsetof(pss_cand, power), offsetof(pss_fil_desc, chan_mask),
+         PSS_NPROF_STAGES);
   return 0;
 }
 '''
@@ -62,7 +63,7 @@ int main(void) {
         got = [int(x) for x in subprocess.check_output([exe]).split()]
     want = [C.sizeof(L.pss_fil_desc), C.sizeof(L.pss_dd_stage), C.sizeof(L.pss_search_cfg),
             L.RAW_DTYPE.itemsize, L.CAND_DTYPE.itemsize, L.CAND_DTYPE.fields["power"][1],
-            L.pss_fil_desc.chan_mask.offset]
+            L.pss_fil_desc.chan_mask.offset, len(L.PROFILE_STAGES)]
     assert got == want
 
 
@@ -85,6 +86,20 @@ def test_version_and_no_device_error(L):
     with pytest.raises(L.PssError) as e:
         L.Server(1 << 30, 2)
     assert e.value.status in (L.PSS_ECUDA, L.PSS_EINVAL)
+
+
+def test_search_footprint_counts_the_boxcar_table(L, monkeypatch):
+    # a row of ds 8 dedisperses from a uint16 table of C x ds x ceil(N/ds) (rows of 8)
+    nchan, nsamp, ds = 64, 100000, 8
+    desc = L.FilDesc(nchan, nsamp, 2e-4, *synth.band(1200.0, 1500.0, nchan))
+    plan = L.Plan(desc, [synth.Stage(0.0, 1.0, 40, ds)])
+    cfg = L.search_cfg(zmax=0, numharm=8)
+    monkeypatch.delenv("PSS_DEDISP_BX_MIN", raising=False)
+    on = L.pss_search_footprint(plan, cfg)
+    monkeypatch.setenv("PSS_DEDISP_BX_MIN", "0")
+    off = L.pss_search_footprint(plan, cfg)
+    table = nchan * ds * (((nsamp + ds - 1) // ds + 7) // 8 * 8) * 2
+    assert on - off == table + table // 8 + 256
 
 
 def test_search_footprint_is_host_arithmetic(L):
