@@ -72,3 +72,19 @@ def test_whiten_zero_block():
     A[1500] = 3.0
     Ap = SP.whiten(A, 1024)
     assert np.all(Ap == 0)
+
+
+def test_whiten_single_block_spectrum():
+    # the ds 128 rows of the Table 3 plan: nfft 2048, one block of 1024 bins whose
+    # median excludes the zeroed DC bin (1023 values, lower median index 511)
+    rng = np.random.default_rng(9)
+    y = rng.standard_normal(2048) * 5.0 + 7.0
+    A = SP.half_spectrum(y)
+    assert A.shape[0] == 1024
+    Ap = SP.whiten(A, 1024)
+    p = np.abs(Ap) ** 2
+    assert p[0] == 0
+    assert abs(np.sort(p[1:])[511] - math.log(2.0)) < 1e-12
+    # the scale is the one block's: every bin is multiplied by the same factor
+    ratio = p[1:] / (np.abs(A[1:]) ** 2)
+    assert np.allclose(ratio, ratio[0], rtol=1e-12)
