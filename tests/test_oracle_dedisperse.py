@@ -46,6 +46,26 @@ def test_total_equals_window_sums():
     assert int(s.sum()) == ref
 
 
+def test_wide_downsampling_equals_channel_window_sums():
+    # s_ds[j] = sum_c (x[c][j ds + d_c] + ... + x[c][j ds + d_c + ds - 1]): each
+    # output is one window sum per channel, taken here from per-channel prefix
+    # sums (an order of operations independent of the shift-and-sum)
+    rng = np.random.default_rng(8)
+    C, N, D = 16, 6000, 700
+    x = rng.integers(0, 256, size=(C, N)).astype(np.uint8)
+    d = rng.integers(0, D + 1, size=C)
+    d[0] = D
+    cs = np.concatenate([np.zeros((C, 1), np.int64), np.cumsum(x.astype(np.int64), axis=1)], axis=1)
+    for ds in (8, 64, 256):
+        nv = (N - D) // ds
+        j = np.arange(nv)
+        ref = np.zeros(nv, np.int64)
+        for c in range(C):
+            t = j * ds + d[c]
+            ref += cs[c, t + ds] - cs[c, t]
+        assert np.array_equal(DD.dedisperse(x, d, D, ds), ref)
+
+
 def test_one_bit_unpack_msb_first():
     data = np.array([[0b10000000, 0b00000001], [0b01000000, 0b10000000]], dtype=np.uint8)
     x = DD.channel_major(data, 16, 1)
