@@ -162,6 +162,30 @@ const char* pss_version(void);
 pss_status pss_ctx_profile(pss_ctx* ctx, int enable);
 pss_status pss_ctx_profile_read(pss_ctx* ctx, double* ms, int64_t* launches);
 
+/* Measured instruction throughputs of a device: the denominators of the
+ * integer-arithmetic (dedispersion) and FP32 (template correlation)
+ * rooflines.  Each figure comes from one wave of CTAs (4 per SM, 256
+ * threads) running 8 independent chains of one instruction kind per thread:
+ * add3 = a + b + c (two 32-bit additions), lop3 = (a & b) ^ c, prmt = a
+ * byte permute, imad = a * b + c (integer), ffma = FP32 a * b + c (two
+ * flops), mix = lop3 and imad alternating (both integer pipes busy: the
+ * issue rate), lds = conflict-free 32-bit shared-memory loads (bytes).
+ * *_per_clk_sm: per SM clock (cycles counted by clock64); *_per_s: per
+ * second over the whole device (CUDA events); sm_mhz: the SM clock the
+ * probes ran at.  Allocates a few KiB of device memory and synchronises.
+ * The paper has no counterpart (its timings are whole-pipeline CPU wall
+ * clock, Table 4). */
+typedef struct {
+    int32_t sms;
+    int32_t reserved;
+    double sm_mhz;
+    double add3_per_clk_sm, lop3_per_clk_sm, prmt_per_clk_sm, imad_per_clk_sm;
+    double ffma_flops_per_clk_sm, mix_per_clk_sm, lds_bytes_per_clk_sm;
+    double int32_adds_per_s, lop3_per_s, prmt_per_s, imad_per_s;
+    double fp32_flops_per_s, mix_per_s, lds_bytes_per_s;
+} pss_peaks;
+pss_status pss_measure_peaks(int device, pss_peaks* out);
+
 /* ---- plan (DDplan; Sect. 3.1, Tables 2-3) ------------------------------- */
 
 /* Build the DM grid and the integer delay table of a plan:
@@ -258,7 +282,12 @@ pss_status pss_dedisperse(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc
  *    exits;
  *  - the first call on a device looks up the array's device address (set-up
  *    per device, under the current device); make that first call before any
- *    stream capture;
+ *    stream capture.  The address is kept for the life of the process: a
+ *    caller that resets the device (cudaDeviceReset) invalidates it, and
+ *    must not call this entry point on that device afterwards;
+ *  - every launch's limits are checked on the host before anything is
+ *    enqueued; if a later CUDA step fails, the call waits for `stream` before
+ *    it returns the error, so nothing of it is still running;
  *  - every call shares the one array: calls that overlap on the GPU (other
  *    streams, other host threads) race and corrupt each other's results.
  *    Each call overwrites all of the scratch it reads, so nothing carries
@@ -325,9 +354,15 @@ typedef struct {
  * folds sifted candidates with prepfold, Sect. 2 step 6).  Sample j is at
  * t = j*dt, dt = ds*tsamp; at trial frequency
  *   f_k = f + (k - (nfreq - 1)/2) * (step_bins / T),  k < nfreq,
- * (T = nfft*ds*tsamp of the trial) its phase is phi = f_k*t + (0.5*fdot)*(t*t)
- * and its bin min(floor((phi - floor(phi))*nbin), nbin - 1), FP64 in that
- * order.  P_b / n_b: sum / number of the samples of bin b (exact).  With
+ * (T = nfft*ds*tsamp of the trial) its phase is phi_j = j*x + j*j*g cycles
+ * with x = f_k*dt and g = (0.5*fdot)*(dt*dt) (FP64, in that order), carried
+ * in 64-bit fixed point: X and G are the fractional parts of x and g in
+ * units of 2^-64 cycle (rounded half to even), phase_j = (j*X + j*j*G) mod
+ * 2^64, and the bin is ((phase_j >> 32) * nbin) >> 32.  This is
+ * floor(frac(phi_j) * nbin) except for samples within (j + j*j)*2^-65
+ * cycle of a bin edge (the rounding of X and G); every bin is an exact
+ * integer decision.  P_b / n_b: sum / number of the samples of bin b
+ * (exact).  With
  * mu = S1/N, var = (S2 - S1*S1/N)/N of the series, chi2_red =
  * sum over bins in order with n_b > 0 of d*d/(n_b*var), d = P_b - n_b*mu,
  * divided by (those bins - 1); 0 when var is 0.  The result is the trial
@@ -478,7 +513,9 @@ size_t pss_batch_footprint(const pss_batch* b);
  * changes, and keeps the fastest;
  * the choice is remembered per shape for the life of the process;
  * environment PSS_AUTOTUNE=0 keeps the defaults 0 / 8 / 96 / -1 / 0):
- * fft_split: FFT pass-split variant (0 = even split), harm_run: points per
+ * fft_split: FFT pass-split variant of the first stage's size (0 = even
+ * split; every transform size of a staged plan is tuned on its own, see
+ * pss_batch_fft_split), harm_run: points per
  * lane of the harmonic sum (16 or 8), dedisp_kb: shared memory for staged
  * channel chunks (KiB), whiten_form: whitening median per CTA (0), per
  * warp (1), per pair of warps (2) or the default (-1: the pair form for
@@ -489,6 +526,21 @@ size_t pss_batch_footprint(const pss_batch* b);
  * are nullable. */
 pss_status pss_batch_tuning(const pss_batch* b, int32_t* fft_split, int32_t* harm_run, int32_t* dedisp_kb,
                             int32_t* whiten_form, int32_t* fused);
+/* The FFT pass split the batch runs for nfft-point series (Sect. 2 step 3,
+ * realfft): PSS_EINVAL unless nfft is a power of two >= 128.  Sizes the
+ * plan does not use report 0. */
+pss_status pss_batch_fft_split(const pss_batch* b, int64_t nfft, int32_t* split);
+/* Pass radices of split `split` of the nfft-point real FFT (nfft/2 complex
+ * points in the fewest passes of radix 2^5..2^10; split 0 is the even
+ * split, larger larger parts first; 1.. the other compositions).  npass:
+ * host int32; radices: host int32[4], unused entries 0.  PSS_EINVAL past
+ * the last split of the size, and for nfft not a power of two >= 128. */
+pss_status pss_fft_split_radices(int64_t nfft, int32_t split, int32_t* npass, int32_t* radices);
+/* Pin the FFT pass split a context uses for nfft-point series (what the
+ * autotuner of a prepared batch would choose); every later call on the
+ * context runs it.  The arithmetic is the same transform, only the FP32
+ * rounding order differs.  PSS_EINVAL as pss_fft_split_radices. */
+pss_status pss_ctx_set_fft_split(pss_ctx* ctx, int64_t nfft, int32_t split);
 /* Device bytes a batch for this shape will hold, computed on the host
  * without a device (what the server admits files by).  PSS_EINVAL for the
  * arguments pss_batch_create would reject. */

@@ -227,7 +227,8 @@ pss_status setup_input(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* f
     if (plan->nsub == 0) {
         size_t need_bx = 0;
         for (const auto& st : plan->stages)
-            if (st.n_dm > 0 && st.first < dm_end && st.first + st.n_dm > dm_begin && bx_use(ctx->tune, st.ds))
+            if (st.n_dm > 0 && st.first < dm_end && st.first + st.n_dm > dm_begin && bx_use(ctx->tune, st.ds) &&
+                ck <= 65535)
                 need_bx = std::max(need_bx, bx_table_bytes(ck, plan->nsamp, st.ds));
         if (need_bx) {
             const void* was = ctx->bx.p;
@@ -731,7 +732,7 @@ std::string path_key(const pss_plan* plan, const pss_fil_desc* fil, const pss_se
     key_put(&k, (int)mode);
     key_put(&k, dev_cap);
     key_put(&k, max_b);
-    key_put(&k, t.fft_variant);
+    k.append(reinterpret_cast<const char*>(t.fft_split), sizeof t.fft_split);
     key_put(&k, t.harm_run);
     key_put(&k, t.dedisp_kb);
     key_put(&k, t.whiten_form);
@@ -776,7 +777,7 @@ pss_status setup_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fi
         ctx->twid_n = nfft_max;
     }
     for (const auto& st : plan->stages)
-        if (st.n_dm > 0) PSS_TRY(ensure_passtw(ctx, st.nfft / 2, ctx->tune.fft_variant, s));
+        if (st.n_dm > 0) PSS_TRY(ensure_passtw(ctx, st.nfft / 2, ctx->tune.split_for(st.nfft / 2), s));
     size_t need_series = 0, need_fft = 0, need_sums = 0, need_plane = 0, need_subu = 0;
     int64_t out_off = 0;
     if (hit) {
@@ -898,7 +899,7 @@ pss_status enqueue_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* 
             fa.whiten_block = cfg->whiten_block;
             fa.tw = (const float2*)ctx->twid.p;
             fa.twM = ctx->twid_n;
-            fa.fft_variant = ctx->tune.fft_variant;
+            fa.fft_variant = ctx->tune.split_for(M);
             fa.whiten_form = ctx->tune.whiten_form >= 0 ? ctx->tune.whiten_form : 2;
             set_passtw(ctx, &fa);
             fa.whiten = 1;
@@ -2012,9 +2013,11 @@ std::map<std::string, Tune> g_tuned;
 
 pss_status autotune(pss_ctx* ctx, const Plan& plan, const pss_fil_desc* fil, const pss_search_cfg* cfg) {
     // PSS_TUNE="fft,harm,dedisp,whiten" pins the launch shapes instead (not remembered)
+    // (the fft split applies to every stage's size that has such a split, the even split elsewhere)
     if (const char* pin = getenv("PSS_TUNE")) {
         Tune t;
-        const int got = sscanf(pin, "%d,%d,%d,%d,%d,%d", &t.fft_variant, &t.harm_run, &t.dedisp_kb, &t.whiten_form,
+        int split = 0;
+        const int got = sscanf(pin, "%d,%d,%d,%d,%d,%d", &split, &t.harm_run, &t.dedisp_kb, &t.whiten_form,
                                &t.fused, &t.plane_form);
         if (got < 4)
             return fail(PSS_EINVAL, "PSS_TUNE must be 4 to 6 integers: fft split, harm run, dedisp KiB, whiten form"
@@ -2022,9 +2025,16 @@ pss_status autotune(pss_ctx* ctx, const Plan& plan, const pss_fil_desc* fil, con
         if ((t.fused != 0 && t.fused != 1) || (t.plane_form != 0 && t.plane_form != 1))
             return fail(PSS_EINVAL, "PSS_TUNE value out of range");
         int rad[4];
-        if (fft_pass_plan(plan.stages[0].nfft / 2, t.fft_variant, rad) == 0 || (t.harm_run != 8 && t.harm_run != 16) ||
-            t.dedisp_kb < 16 || t.dedisp_kb > 200 || t.whiten_form < -1 || t.whiten_form > 2)
+        if (split < 0 || fft_pass_plan(plan.stages[0].nfft / 2, split, rad) == 0 ||
+            (t.harm_run != 8 && t.harm_run != 16) || t.dedisp_kb < 16 || t.dedisp_kb > 200 || t.whiten_form < -1 ||
+            t.whiten_form > 2)
             return fail(PSS_EINVAL, "PSS_TUNE value out of range");
+        for (const auto& st : plan.stages) {
+            const int64_t M = st.nfft / 2;
+            int L = 0;
+            while (L < 31 && (int64_t(1) << L) < M) ++L;
+            t.fft_split[L] = (int8_t)(fft_pass_plan(M, split, rad) > 0 ? split : 0);
+        }
         ctx->tune = t;
         return PSS_OK;
     }
@@ -2040,17 +2050,18 @@ pss_status autotune(pss_ctx* ctx, const Plan& plan, const pss_fil_desc* fil, con
         }
     }
     cudaStream_t s = ctx->stream;
-    const int64_t nt = std::min<int64_t>(plan.ndm(), 256);
     const pss_plan* pp = static_cast<const pss_plan*>(&plan);
+    // trials the choices are timed on: the first min(n, 256) of the plan, or of the stage being tuned
+    int64_t tb = 0, te = std::min<int64_t>(plan.ndm(), 256);
     // time of profiler stage `stage` (1 dedisperse, 2 FFT, 3 whiten, 5 harmonic sum) over one
     // warm pass; the kernels of the other stages do not change with the choice being tuned
     auto measure = [&](unsigned stages, float* ms) -> pss_status {
         PathSetup T;
-        PSS_TRY(setup_path(ctx, pp, fil, cfg, 0, nt, MODE_SEARCH, s, kBatchInitialCap, &T));
+        PSS_TRY(setup_path(ctx, pp, fil, cfg, tb, te, MODE_SEARCH, s, kBatchInitialCap, &T));
         const uint8_t* src = (const uint8_t*)ctx->fil_dev.p;
-        PSS_TRY(enqueue_path(ctx, pp, fil, src, cfg, 0, T, MODE_SEARCH, Outputs(), s));
+        PSS_TRY(enqueue_path(ctx, pp, fil, src, cfg, tb, T, MODE_SEARCH, Outputs(), s));
         PSS_TRY(pss_ctx_profile(ctx, 1));
-        PSS_TRY(enqueue_path(ctx, pp, fil, src, cfg, 0, T, MODE_SEARCH, Outputs(), s));
+        PSS_TRY(enqueue_path(ctx, pp, fil, src, cfg, tb, T, MODE_SEARCH, Outputs(), s));
         double st_ms[PSS_NPROF_STAGES];
         int64_t n[PSS_NPROF_STAGES];
         pss_status r = pss_ctx_profile_read(ctx, st_ms, n);
@@ -2061,7 +2072,7 @@ pss_status autotune(pss_ctx* ctx, const Plan& plan, const pss_fil_desc* fil, con
             if (stages & (1u << i)) *ms += (float)st_ms[i];
         return check_errflag(ctx, s);
     };
-    auto sweep = [&](int* field, const std::vector<int>& cands, unsigned stage, const char* what) -> pss_status {
+    auto sweep = [&](auto* field, const std::vector<int>& cands, unsigned stage, const char* what) -> pss_status {
         int best = *field;
         float best_ms = 1e30f;
         for (int v : cands) {
@@ -2079,17 +2090,31 @@ pss_status autotune(pss_ctx* ctx, const Plan& plan, const pss_fil_desc* fil, con
     };
     pss_status st = PSS_OK;
     {
-        // FFT pass splits of the first stage's size
-        std::vector<int> fv;
-        int rad[4];
-        for (int v = 0; v < 6 && fft_pass_plan(plan.stages[0].nfft / 2, v, rad) > 0; ++v) fv.push_back(v);
         // stage bits of the profiler: 1 dedisperse, 2 FFT (and the fused kernel), 3 whiten, 4 plane, 5 harmonic sum
         const bool fusable = cfg->zmax == 0 && plan.stages.size() == 1 && plan.stages[0].nfft == (int64_t(1) << 18) &&
                              cfg->whiten_block == 1024 && cfg->halfwidth_extra == 16 && spec_cluster_usable();
         if (fusable) st = sweep(&ctx->tune.fused, {1, 0}, (1u << 2) | (1u << 3) | (1u << 4), "fused");
         else ctx->tune.fused = 0;
         if (st == PSS_OK && !ctx->tune.fused) {
-            st = sweep(&ctx->tune.fft_variant, fv, 1u << 2, "fft split");
+            // FFT pass splits of every transform size of the plan, each timed on the first
+            // trials of the first stage of that size
+            for (size_t si = 0; si < plan.stages.size() && st == PSS_OK; ++si) {
+                const auto& sg = plan.stages[si];
+                const int64_t M = sg.nfft / 2;
+                bool seen = sg.n_dm == 0;
+                for (size_t sj = 0; sj < si && !seen; ++sj) seen = plan.stages[sj].n_dm > 0 && plan.stages[sj].nfft == sg.nfft;
+                if (seen) continue;
+                std::vector<int> fv;
+                int rad[4];
+                for (int v = 0; v < 6 && fft_pass_plan(M, v, rad) > 0; ++v) fv.push_back(v);
+                int L = 0;
+                while (L < 31 && (int64_t(1) << L) < M) ++L;
+                tb = sg.first;
+                te = sg.first + std::min<int64_t>(sg.n_dm, 256);
+                if (fv.size() > 1) st = sweep(&ctx->tune.fft_split[L], fv, 1u << 2, "fft split");
+            }
+            tb = 0;
+            te = std::min<int64_t>(plan.ndm(), 256);
             if (st == PSS_OK) st = sweep(&ctx->tune.whiten_form, {0, 1, 2}, 1u << 3, "whiten");
         } else {
             ctx->tune.whiten_form = 0;  // not used by the fused kernel
@@ -2213,7 +2238,7 @@ size_t search_footprint(const Plan& plan, const pss_fil_desc* fil, const pss_sea
     for (const auto& st : plan.stages) {
         nfft_max = std::max<int64_t>(nfft_max, st.nfft);
         if (st.n_dm <= 0) continue;
-        if (plan.nsub == 0 && bx_use(bx_tune, st.ds)) bx = std::max(bx, bx_table_bytes((int32_t)ck, plan.nsamp, st.ds));
+        if (plan.nsub == 0 && bx_use(bx_tune, st.ds) && ck <= 65535) bx = std::max(bx, bx_table_bytes((int32_t)ck, plan.nsamp, st.ds));
         if (std::find(sizes.begin(), sizes.end(), st.nfft) == sizes.end()) {
             sizes.push_back(st.nfft);
             t += buf((size_t)(st.nfft / 2) * sizeof(float2));  // inter-pass twiddles (at most M entries)
@@ -2257,11 +2282,51 @@ extern "C" size_t pss_batch_footprint(const pss_batch* b) { return b ? b->footpr
 extern "C" pss_status pss_batch_tuning(const pss_batch* b, int32_t* fft_split, int32_t* harm_run, int32_t* dedisp_kb,
                                        int32_t* whiten_form, int32_t* fused) {
     if (!b) return fail(PSS_EINVAL, "pss_batch_tuning: null batch");
-    if (fft_split) *fft_split = b->ctx->tune.fft_variant;
+    if (fft_split) *fft_split = b->ctx->tune.split_for(b->plan.stages[0].nfft / 2);
     if (harm_run) *harm_run = b->ctx->tune.harm_run;
     if (dedisp_kb) *dedisp_kb = b->ctx->tune.dedisp_kb;
     if (whiten_form) *whiten_form = b->ctx->tune.whiten_form;
     if (fused) *fused = b->ctx->tune.fused;
+    return PSS_OK;
+}
+
+namespace {
+// log2 of an FFT's complex points M = nfft / 2 (nfft a power of two >= 128), or -1
+int split_index(int64_t nfft) {
+    if (nfft < 128 || (nfft & (nfft - 1)) != 0) return -1;
+    int L = 0;
+    while ((int64_t(1) << L) < nfft / 2) ++L;
+    return L < 32 ? L : -1;
+}
+}  // namespace
+
+extern "C" pss_status pss_fft_split_radices(int64_t nfft, int32_t split, int32_t* npass, int32_t* radices) {
+    if (!npass || !radices) return fail(PSS_EINVAL, "pss_fft_split_radices: null argument");
+    *npass = 0;
+    if (split_index(nfft) < 0 || split < 0) return fail(PSS_EINVAL, "pss_fft_split_radices: bad nfft or split");
+    int rad[4] = {0, 0, 0, 0};
+    const int np = fft_pass_plan(nfft / 2, split, rad);
+    if (np == 0) return fail(PSS_EINVAL, "pss_fft_split_radices: no such split for this size");
+    for (int i = 0; i < 4; ++i) radices[i] = i < np ? rad[i] : 0;
+    *npass = np;
+    return PSS_OK;
+}
+
+extern "C" pss_status pss_ctx_set_fft_split(pss_ctx* ctx, int64_t nfft, int32_t split) {
+    if (!ctx) return fail(PSS_EINVAL, "pss_ctx_set_fft_split: null ctx");
+    const int L = split_index(nfft);
+    int rad[4];
+    if (L < 0 || split < 0 || split > 127 || fft_pass_plan(nfft / 2, split, rad) == 0)
+        return fail(PSS_EINVAL, "pss_ctx_set_fft_split: no such split for this size");
+    ctx->tune.fft_split[L] = (int8_t)split;
+    return PSS_OK;
+}
+
+extern "C" pss_status pss_batch_fft_split(const pss_batch* b, int64_t nfft, int32_t* split) {
+    if (!b || !split) return fail(PSS_EINVAL, "pss_batch_fft_split: null argument");
+    const int L = split_index(nfft);
+    if (L < 0) return fail(PSS_EINVAL, "pss_batch_fft_split: bad nfft");
+    *split = b->ctx->tune.fft_split[L];
     return PSS_OK;
 }
 

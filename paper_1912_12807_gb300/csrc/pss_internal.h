@@ -135,7 +135,14 @@ struct DevBuf {
 // Launch-shape choices the autotuner may change (pss_batch_create); the
 // defaults are what untuned calls use.
 struct Tune {
-    int fft_variant = 0;   // FFT pass split
+    // FFT pass split per transform size: fft_split[L] is the variant used for
+    // M = 2^L complex points (0: the even split; see fft_pass_plan)
+    int8_t fft_split[32] = {};
+    int split_for(int64_t M) const {
+        int L = 0;
+        while (L < 31 && (int64_t(1) << L) < M) ++L;
+        return fft_split[L];
+    }
     int harm_run = 8;      // harmonic-sum points per lane
     int dedisp_kb = 96;    // dedispersion chunk staging budget
     int whiten_form = -1;  // whitening kernel form (-1: default, the warp pair per block)
@@ -283,6 +290,10 @@ struct DedispArgs {
 int dedisp_tile_samples();
 int dedisp_group_trials();  // consecutive trials sharing one staged tile
 cudaError_t launch_dedisp(const DedispArgs& a, int num_sms, cudaStream_t s);
+// Whether launch_dedisp accepts a launch of this delay spread and kept-channel
+// count (the host-side checks it makes before launching), so that callers
+// can refuse a request before enqueuing any work.
+bool dedisp_launch_fits(int32_t spread, int32_t ck, int chunk_kb);
 
 // Two-stage scheme, stage 2: s_i[t] = sum_b u_{g(i),b}[t + D_b(i)], then the
 // ds boxcar, for the nb trials of a batch (k_subband.cu).
@@ -438,6 +449,10 @@ cudaError_t launch_twiddles(float2* tw, int64_t n, cudaStream_t s);
 // Radices of the passes of an M-point FFT for split `variant` (0 = default);
 // returns the pass count (<= 3), or 0 past the last variant.
 int fft_pass_plan(int64_t M, int variant, int* rad);
+// Instruction-throughput probes (k_probe.cu): per SM clock and per second for
+// add3, lop3, prmt, imad, ffma (flops), lop3/imad mix, lds (bytes).
+cudaError_t probe_peaks(int sms, cudaStream_t s, uint32_t* sink, unsigned long long* cyc, double per_clk[7],
+                        double per_s[7], double* sm_mhz);
 cudaError_t launch_pass_twiddles(float2* out, const float2* tw, int64_t twM, int R, int64_t Ns, cudaStream_t s);
 cudaError_t launch_fft_whiten(const FftArgs& a, cudaStream_t s, Ctx* prof_ctx);
 

@@ -69,7 +69,8 @@ EXPORTS = ["pss_ctx_create", "pss_ctx_destroy", "pss_last_error", "pss_version",
            "pss_power_threshold", "pss_ctx_profile", "pss_ctx_profile_read", "pss_dedisperse_noalloc",
            "pss_refine_prepare", "pss_refine_eval", "pss_refine_candidates", "pss_batch_create", "pss_batch_run",
            "pss_batch_footprint", "pss_batch_free", "pss_search_footprint", "pss_ctx_take_cands",
-           "pss_batch_take_cands", "pss_batch_tuning", "pss_server_create", "pss_submit_file",
+           "pss_batch_take_cands", "pss_batch_tuning", "pss_batch_fft_split", "pss_fft_split_radices",
+           "pss_ctx_set_fft_split", "pss_measure_peaks", "pss_server_create", "pss_submit_file",
            "pss_submit_file_subband", "pss_poll",
            "pss_result_cands", "pss_result_free", "pss_server_stats", "pss_server_destroy"]
 PROFILE_STAGES = ["unpack", "dedisperse", "fft", "whiten", "plane", "harmsum", "bxtable"]
@@ -125,6 +126,10 @@ def lib():
         "pss_ctx_take_cands": (st, [vp, vp, i64, P(i64)]),
         "pss_batch_take_cands": (st, [vp, vp, i64, P(i64)]),
         "pss_batch_tuning": (st, [vp, P(i32), P(i32), P(i32), P(i32), P(i32)]),
+        "pss_batch_fft_split": (st, [vp, i64, P(i32)]),
+        "pss_fft_split_radices": (st, [i64, i32, P(i32), P(i32)]),
+        "pss_ctx_set_fft_split": (st, [vp, i64, i32]),
+        "pss_measure_peaks": (st, [C.c_int, vp]),
         "pss_search_footprint": (st, [vp, P(pss_fil_desc), P(pss_search_cfg), P(C.c_size_t)]),
         "pss_server_create": (st, [C.c_int, C.c_size_t, C.c_int, P(vp)]),
         "pss_submit_file": (st, [vp, P(pss_fil_desc), vp, P(pss_dd_stage), C.c_int, P(pss_search_cfg),
@@ -483,6 +488,12 @@ class Batch:
         return {"fft_split": f.value, "harm_run": h.value, "dedisp_kb": d.value, "whiten_form": w.value,
                 "fused": u.value}
 
+    def fft_split(self, nfft: int) -> int:
+        """The FFT pass split the batch runs for nfft-point series."""
+        v = C.c_int32()
+        _check(lib().pss_batch_fft_split(self.h, int(nfft), C.byref(v)))
+        return v.value
+
     def run(self, data, cap: int = 1 << 14, timing: bool = False):
         """Sifted candidates of one file (host array or device tensor; a device
         tensor must be complete: the batch copies it on its own stream)."""
@@ -509,6 +520,51 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def pss_fft_split_radices(nfft: int, split: int):
+    """Pass radices of FFT split `split` for nfft-point series, or None past
+    the last split of that size."""
+    n = C.c_int32()
+    rad = (C.c_int32 * 4)()
+    st = lib().pss_fft_split_radices(int(nfft), int(split), C.byref(n), rad)
+    if st == PSS_EINVAL:
+        return None
+    _check(st)
+    return [int(rad[i]) for i in range(n.value)]
+
+
+def pss_fft_splits(nfft: int):
+    """Every pass split of the nfft-point FFT: [(split, radices)]."""
+    out = []
+    for v in range(64):
+        r = pss_fft_split_radices(nfft, v)
+        if r is None:
+            break
+        out.append((v, r))
+    return out
+
+
+PEAKS_FIELDS = ["sm_mhz", "add3_per_clk_sm", "lop3_per_clk_sm", "prmt_per_clk_sm", "imad_per_clk_sm",
+                "ffma_flops_per_clk_sm", "mix_per_clk_sm", "lds_bytes_per_clk_sm", "int32_adds_per_s", "lop3_per_s",
+                "prmt_per_s", "imad_per_s", "fp32_flops_per_s", "mix_per_s", "lds_bytes_per_s"]
+
+
+class pss_peaks(C.Structure):
+    _fields_ = [("sms", C.c_int32), ("reserved", C.c_int32)] + [(n, C.c_double) for n in PEAKS_FIELDS]
+
+
+def pss_measure_peaks(device: int = 0) -> dict:
+    """Measured instruction throughputs of the device (pss_measure_peaks)."""
+    p = pss_peaks()
+    _check(lib().pss_measure_peaks(int(device), C.byref(p)))
+    out = {"sms": int(p.sms)}
+    out.update({n: float(getattr(p, n)) for n in PEAKS_FIELDS})
+    return out
+
+
+def pss_ctx_set_fft_split(ctx: Context, nfft: int, split: int):
+    _check(lib().pss_ctx_set_fft_split(ctx.h, int(nfft), int(split)))
 
 
 def pss_batch_create(plan: Plan, cfg: pss_search_cfg, device: int = 0) -> Batch:

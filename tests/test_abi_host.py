@@ -49,9 +49,9 @@ def test_struct_layout_matches_binding(L):
 #include <stddef.h>
 #include "pss.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %d\n", sizeof(pss_fil_desc), sizeof(pss_dd_stage), sizeof(pss_search_cfg),
+  printf("%zu %zu %zu %zu %zu %zu %zu %d %zu %zu\n", sizeof(pss_fil_desc), sizeof(pss_dd_stage), sizeof(pss_search_cfg),
          sizeof(pss_raw_cand), sizeof(pss_cand), offsetof(pss_cand, power), offsetof(pss_fil_desc, chan_mask),
-         PSS_NPROF_STAGES);
+         PSS_NPROF_STAGES, sizeof(pss_peaks), offsetof(pss_peaks, lds_bytes_per_s));
   return 0;
 }
 '''
@@ -63,7 +63,8 @@ int main(void) {
         got = [int(x) for x in subprocess.check_output([exe]).split()]
     want = [C.sizeof(L.pss_fil_desc), C.sizeof(L.pss_dd_stage), C.sizeof(L.pss_search_cfg),
             L.RAW_DTYPE.itemsize, L.CAND_DTYPE.itemsize, L.CAND_DTYPE.fields["power"][1],
-            L.pss_fil_desc.chan_mask.offset, len(L.PROFILE_STAGES)]
+            L.pss_fil_desc.chan_mask.offset, len(L.PROFILE_STAGES), C.sizeof(L.pss_peaks),
+            L.pss_peaks.lds_bytes_per_s.offset]
     assert got == want
 
 
