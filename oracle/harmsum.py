@@ -77,11 +77,12 @@ def min_half_bin(n: int, t_span: float, f_lo_hz: float) -> int:
 
 
 def raw_candidates(P: np.ndarray, numharm: int, Z: int, thr: dict,
-                   t_span: float, f_lo_hz: float):
-    """List of (n, h, j, S_n) for every stage, in (n, j, h) order."""
+                   t_span: float, f_lo_hz: float, sums: dict = None):
+    """List of (n, h, j, S_n) for every stage, in (n, j, h) order.  `sums`
+    may hold S_n of some stages already computed by harmonic_sum(P, n, Z)."""
     out = []
     for n in harmonic_stages(numharm):
-        S = harmonic_sum(P, n, Z)
+        S = sums[n] if sums is not None and n in sums else harmonic_sum(P, n, Z)
         m = (S >= thr[n]) & local_max(S)
         hmin = min_half_bin(n, t_span, f_lo_hz)
         if hmin > 0:
