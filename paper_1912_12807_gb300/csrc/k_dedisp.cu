@@ -308,20 +308,41 @@ cudaError_t launch_t(const DedispArgs& a, dim3 grid, size_t shm, int RW, int CC,
 int dedisp_tile_samples() { return TN; }
 int dedisp_group_trials() { return G; }
 
-cudaError_t launch_dedisp(const DedispArgs& a, int num_sms, cudaStream_t s) {
-    (void)num_sms;
+namespace {
+// Launch sizes of a spread: words per staged row copy (RW), channels per
+// chunk (CC) and the shared memory; false where the launch is refused.
+bool dedisp_sizes(int32_t spread, int32_t ck, int chunk_kb, int* RW_out, int* CC_out, size_t* shm_out) {
     // staged row: the 256 words a lane sweep reads plus the delay spread and
     // the 16-byte alignment slack, in whole 16-byte chunks
-    int RW = 32 * KW + (15 + a.spread) / 4 + 1;
+    if (spread < 0 || spread > 65535) return false;
+    int RW = 32 * KW + (15 + spread) / 4 + 1;
     RW = (RW + 3) & ~3;
     const size_t per_chan = (size_t)16 * RW + (4 * RW + 16);
-    const int kb = a.chunk_kb > 0 ? a.chunk_kb : 96;  // 96 KiB: two CTAs per SM fit beside the rest
+    const int kb = chunk_kb > 0 ? chunk_kb : 96;  // 96 KiB: two CTAs per SM fit beside the rest
     int CC = (int)(((size_t)kb * 1024) / per_chan);
     if (CC > 32) CC = 32;
     if (CC < 1) CC = 1;
-    if (15 + a.spread > 65535 - 4 * RW) return cudaErrorInvalidValue;  // offsets are 16-bit
-    const size_t shm = layout_of(RW, CC, a.ck).total;
-    if (shm > 220 * 1024) return cudaErrorInvalidValue;
+    if (15 + spread > 65535 - 4 * RW) return false;  // offsets are 16-bit
+    const size_t shm = layout_of(RW, CC, ck).total;
+    if (shm > 220 * 1024) return false;
+    *RW_out = RW;
+    *CC_out = CC;
+    *shm_out = shm;
+    return true;
+}
+}  // namespace
+
+bool dedisp_launch_fits(int32_t spread, int32_t ck, int chunk_kb) {
+    int RW, CC;
+    size_t shm;
+    return dedisp_sizes(spread, ck, chunk_kb, &RW, &CC, &shm);
+}
+
+cudaError_t launch_dedisp(const DedispArgs& a, int num_sms, cudaStream_t s) {
+    (void)num_sms;
+    int RW = 0, CC = 0;
+    size_t shm = 0;
+    if (!dedisp_sizes(a.spread, a.ck, a.chunk_kb, &RW, &CC, &shm)) return cudaErrorInvalidValue;
     const int64_t L = a.nv * a.ds;
     dim3 grid((unsigned)((L + TN - 1) / TN), (unsigned)((a.nb + G - 1) / G), (unsigned)(a.zsub ? a.nz : 1));
     const bool wide = a.ck > 256;

@@ -188,7 +188,9 @@ int bx_table_cols(int ds) { return TB_SPAN / std::max(ds, 1); }
 cudaError_t launch_bx_table(const BxTableArgs& a, cudaStream_t s) {
     if (a.ck <= 0 || a.mlen <= 0) return cudaSuccess;
     const int ds = 1 << a.lds;
-    if (a.lds < 1 || ds > BX_MAX_DS || (1 << a.lmt) != bx_table_cols(ds) || a.mstride < a.mlen || (a.pitch & 15))
+    // grid.y is the channel: at most 65535 rows
+    if (a.lds < 1 || ds > BX_MAX_DS || (1 << a.lmt) != bx_table_cols(ds) || a.mstride < a.mlen || (a.pitch & 15) ||
+        a.ck > 65535)
         return cudaErrorInvalidValue;
     const int L = TB_SPAN + ds;
     const size_t shm = (size_t)((L + 15) & ~15) + (size_t)(L + 1 + (L >> a.lds) + 2) * sizeof(int32_t);

@@ -91,7 +91,6 @@ extern "C" pss_status pss_dedisperse_noalloc(const pss_plan* plan, const pss_fil
     void* base = nullptr;
     int* d_err = nullptr;
     PSS_TRY(scratch_address(dev, &base, &d_err));
-    PSS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), s));
     int32_t* d_keep = (int32_t*)base;
     uint8_t* d_xcm = (uint8_t*)base + table_bytes;
 
@@ -100,21 +99,15 @@ extern "C" pss_status pss_dedisperse_noalloc(const pss_plan* plan, const pss_fil
     for (int64_t i = 0; i < ndm; ++i)
         for (int32_t r = 0; r < ck; ++r)
             host[(size_t)ck * (1 + i) + r] = plan->delays[(size_t)(dm_begin + i) * plan->nchan + keep[r]];
-    PSS_CUDA(cudaMemcpyAsync(d_keep, host.data(), host.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
 
-    PrepArgs pa;
-    pa.src = (const uint8_t*)data_dev;
-    pa.nchan = fil->nchan;
-    pa.nbits = fil->nbits;
-    pa.layout = fil->layout;
-    pa.nsamp = fil->nsamp;
-    pa.keep = d_keep;
-    pa.ck = ck;
-    pa.xcm = d_xcm;
-    pa.pitch = pitch;
-    PSS_CUDA(launch_prep(pa, s));
-
-    int64_t off = 0;
+    // every launch's delay spread, checked against the kernel's limits before any work is enqueued,
+    // so that a refused request leaves nothing running on the stream
+    struct Launch {
+        int64_t b0;
+        int32_t nb, spread;
+        const StageInfo* st;
+    };
+    std::vector<Launch> launches;
     for (size_t si = 0; si < plan->stages.size(); ++si) {
         const StageInfo& st = plan->stages[si];
         const int64_t lo = std::max<int64_t>(dm_begin, st.first);
@@ -134,23 +127,55 @@ extern "C" pss_status pss_dedisperse_noalloc(const pss_plan* plan, const pss_fil
                     }
                     spread = std::max(spread, mx - mn);
                 }
+            if (!dedisp_launch_fits(spread, ck, 0))
+                return fail(PSS_EINVAL, "pss_dedisperse_noalloc: the delay spread of 16 consecutive trials (" +
+                                            std::to_string(spread) + " samples) is too large for the kernel");
+            launches.push_back({b0, nb, spread, &st});
+        }
+    }
+
+    // from the first enqueued operation on, every exit waits for the stream: nothing of this call
+    // may still be writing into `out` or the shared scratch when it returns
+    auto enqueue = [&]() -> pss_status {
+        PSS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+        PSS_CUDA(cudaMemcpyAsync(d_keep, host.data(), host.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+
+        PrepArgs pa;
+        pa.src = (const uint8_t*)data_dev;
+        pa.nchan = fil->nchan;
+        pa.nbits = fil->nbits;
+        pa.layout = fil->layout;
+        pa.nsamp = fil->nsamp;
+        pa.keep = d_keep;
+        pa.ck = ck;
+        pa.xcm = d_xcm;
+        pa.pitch = pitch;
+        PSS_CUDA(launch_prep(pa, s));
+        int64_t off = 0;
+        for (const Launch& l : launches) {
             DedispArgs da{};
             da.xcm = d_xcm;
             da.pitch = pitch;
             da.ck = ck;
-            da.delays = d_keep + (size_t)ck * (1 + (b0 - dm_begin));
-            da.nb = nb;
-            da.nv = st.nv;
-            da.ds = st.ds;
+            da.delays = d_keep + (size_t)ck * (1 + (l.b0 - dm_begin));
+            da.nb = l.nb;
+            da.nv = l.st->nv;
+            da.ds = l.st->ds;
             da.out_f = nullptr;
             da.out_i = out + off;
-            da.out_stride = st.nv;
+            da.out_stride = l.st->nv;
             da.sums = nullptr;
-            da.spread = spread;
+            da.spread = l.spread;
             da.err = d_err;
             PSS_CUDA(launch_dedisp(da, 0, s));
-            off += (int64_t)nb * st.nv;
+            off += (int64_t)l.nb * l.st->nv;
         }
+        return PSS_OK;
+    };
+    const pss_status st = enqueue();
+    if (st != PSS_OK) {
+        cudaStreamSynchronize(s);  // the error is already recorded; this only drains the stream
+        return st;
     }
     int flag = 0;
     PSS_CUDA(cudaMemcpyAsync(&flag, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
