@@ -13,11 +13,13 @@ of trial frequencies around the candidate's:
   phi_j = f*t_j + (fdot/2)*t_j^2 = j*x + j^2*g cycles, x = f*dt and
   g = (0.5*fdot)*(dt*dt) (FP64, in that order).  The phase is carried in
   64-bit fixed point (units of 2^-64 cycle, wrapping modulo one cycle):
-  X = rint((x - floor(x)) * 2^64), Gq = rint((g - floor(g)) * 2^64)
-  (round half to even; both taken modulo 2^64), phase_j = (j*X + j*j*Gq)
-  mod 2^64, and the bin is ((phase_j >> 32) * nbin) >> 32, i.e. the
-  fraction of the cycle times nbin, rounded down, in integers.  (The
-  rounding of X and Gq moves the phase by at most (j + j^2) 2^-65 cycle.)
+  X = rint(x * 2^64) mod 2^64 and Gq = rint(g * 2^64) mod 2^64 (round half
+  to even, on the exact binary values of x and g; a negative value wraps),
+  phase_j = (j*X + j*j*Gq) mod 2^64, and the bin is
+  floor(phase_j * nbin / 2^64), the fraction of the cycle times nbin
+  rounded down, in integers.  The rounding of X and Gq is the only
+  departure from the exact phase j*x + j^2*g: at most (j + j^2) 2^-65
+  cycle.
 * Profile P_b = sum of s_j over the samples of bin b, n_b their number
   (exact integers).
 * Significance: with mu = S1/N and var = (S2 - S1*S1/N)/N of the series
@@ -39,8 +41,10 @@ MASK64 = (1 << 64) - 1
 
 
 def fixed_point(v: float) -> int:
-    """rint((v - floor(v)) * 2^64) modulo 2^64, round half to even."""
-    fr = v - math.floor(v)
+    """rint(v * 2^64) modulo 2^64, round half to even, exactly: v - trunc(v)
+    is exact in FP64 (the integer part is removed without rounding), and so
+    is its scaling by 2^64."""
+    fr = v - math.trunc(v)
     return int(round(math.ldexp(fr, 64))) & MASK64
 
 
@@ -51,7 +55,10 @@ def phase_bins(n: int, dt: float, f: float, fdot: float, nbin: int) -> np.ndarra
     j = np.arange(n, dtype=np.uint64)
     with np.errstate(over="ignore"):
         ph = j * X + (j * j) * G          # uint64 arithmetic wraps modulo 2^64
-    return (((ph >> np.uint64(32)) * np.uint64(nbin)) >> np.uint64(32)).astype(np.int64)
+    # floor(ph * nbin / 2^64) from the two 32-bit halves of ph (no product exceeds 2^42)
+    hi, lo = ph >> np.uint64(32), ph & np.uint64(0xFFFFFFFF)
+    nb = np.uint64(nbin)
+    return ((hi * nb + ((lo * nb) >> np.uint64(32))) >> np.uint64(32)).astype(np.int64)
 
 
 def fold(s: np.ndarray, dt: float, f: float, fdot: float, nbin: int):

@@ -81,22 +81,38 @@ def test_drift_term_realigns_a_chirped_train():
     assert good > 3 * none and good > 3 * wrong
 
 
-def test_fixed_point_phase_matches_exact_rational_phase():
-    # the 64-bit fixed-point bins equal floor(frac(f t + fdot t^2 / 2) nbin) of
-    # the exact rational phase, except where that phase lies within the
-    # fixed-point rounding, (j + j^2) 2^-65 cycle, of a bin edge
+def test_fixed_point_is_the_exact_rounded_fraction():
+    # X = rint(v 2^64) mod 2^64 of the exact binary value of v, for either sign and
+    # for values whose fraction 1 + v (v < 0) FP64 cannot hold
     from fractions import Fraction
     assert FO.fixed_point(0.25) == 1 << 62 and FO.fixed_point(-0.25) == 3 << 62
+    rng = np.random.default_rng(6)
+    vals = [-4e-10, 4e-10, -1e-17, -0.5, 0.5, -3.75, 1234.5678, -1234.5678, 2.0 ** -70, -(2.0 ** -70),
+            1.0 - 2.0 ** -53, -1.0 + 2.0 ** -53] + list(rng.uniform(-5, 5, 50)) + list(rng.uniform(-1e-9, 1e-9, 50))
+    for v in vals:
+        want = int(round((Fraction(v) % 1) * 2 ** 64)) % 2 ** 64
+        assert FO.fixed_point(float(v)) == want, v
+
+
+def test_fixed_point_phase_matches_exact_rational_phase():
+    # the 64-bit fixed-point bins equal floor(frac(j x + j^2 g) nbin) of the exact
+    # rational phase of the FP64 x = f dt and g = (fdot/2) dt^2, except where that
+    # phase lies within the fixed-point rounding, (j + j^2) 2^-65 cycle, of a bin
+    # edge; drifts of both signs, long series, bin counts that are and are not
+    # powers of two
+    from fractions import Fraction
     rng = np.random.default_rng(5)
-    for _ in range(5):
-        f, fd, dt, nbin = rng.uniform(0.5, 400), rng.uniform(-3, 3), rng.uniform(1e-4, 1e-3), int(rng.integers(2, 100))
-        n = 3000
+    for it in range(8):
+        f, dt = rng.uniform(0.5, 400), rng.uniform(1e-4, 1e-3)
+        fd = rng.uniform(-3, 3) if it % 2 else -rng.uniform(1e-3, 0.1)
+        nbin = int(rng.integers(2, 100)) if it < 4 else 64
+        n = 300000
         got = FO.phase_bins(n, dt, f, fd, nbin)
         x = Fraction(f * dt)
-        g = Fraction(0.5 * fd) * Fraction(dt * dt)
-        for j in range(0, n, 7):
+        g = Fraction((0.5 * fd) * (dt * dt))
+        for j in list(range(0, 3000, 7)) + list(range(3000, n, 997)):
             ph = (j * x + j * j * g) % 1
             b = int(ph * nbin)
             if b != int(got[j]):
                 edge = min(abs(ph * nbin - b), abs(ph * nbin - (b + 1))) / nbin
-                assert edge <= Fraction(j + j * j + 2, 2 ** 64), (j, b, got[j])
+                assert edge <= Fraction(j + j * j, 2 ** 65), (it, j, b, got[j])
