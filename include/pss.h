@@ -356,12 +356,12 @@ typedef struct {
  *   f_k = f + (k - (nfreq - 1)/2) * (step_bins / T),  k < nfreq,
  * (T = nfft*ds*tsamp of the trial) its phase is phi_j = j*x + j*j*g cycles
  * with x = f_k*dt and g = (0.5*fdot)*(dt*dt) (FP64, in that order), carried
- * in 64-bit fixed point: X and G are the fractional parts of x and g in
- * units of 2^-64 cycle (rounded half to even), phase_j = (j*X + j*j*G) mod
- * 2^64, and the bin is ((phase_j >> 32) * nbin) >> 32.  This is
- * floor(frac(phi_j) * nbin) except for samples within (j + j*j)*2^-65
- * cycle of a bin edge (the rounding of X and G); every bin is an exact
- * integer decision.  P_b / n_b: sum / number of the samples of bin b
+ * in 64-bit fixed point: X = rint(x * 2^64) and G = rint(g * 2^64) modulo
+ * 2^64 (rounded half to even from the exact binary values of x and g; a
+ * negative g wraps), phase_j = (j*X + j*j*G) mod 2^64, and the bin is
+ * floor(phase_j * nbin / 2^64).  This is floor(frac(phi_j) * nbin) except
+ * for samples within (j + j*j)*2^-65 cycle of a bin edge (the rounding of X
+ * and G); every bin is an exact integer decision.  P_b / n_b: sum / number of the samples of bin b
  * (exact).  With
  * mu = S1/N, var = (S2 - S1*S1/N)/N of the series, chi2_red =
  * sum over bins in order with n_b > 0 of d*d/(n_b*var), d = P_b - n_b*mu,

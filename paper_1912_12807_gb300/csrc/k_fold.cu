@@ -3,11 +3,12 @@
 //
 // One CTA folds one (candidate, trial frequency): sample j has phase
 // j x + j^2 g cycles (x = f dt, g = (fdot/2) dt^2) carried in 64-bit fixed
-// point (X, G: x and g modulo one cycle in units of 2^-64, rounded to
-// nearest even from FP64 values formed with round-to-nearest intrinsics in
-// the host's order), phase_j = j X + j^2 G modulo 2^64, and bin
-// ((phase_j >> 32) nbin) >> 32: integer arithmetic, so every sample lands in
-// the bin the host reading assigns it, with no FP64 per sample.  Each
+// point (X, G: rint(x 2^64), rint(g 2^64) modulo 2^64, rounded to nearest
+// even from the exact binary values of the FP64 x and g formed with
+// round-to-nearest intrinsics in the host's order; a negative g wraps),
+// phase_j = j X + j^2 G modulo 2^64, and bin floor(phase_j nbin / 2^64) (the
+// high word of the 128-bit product): integer arithmetic, so every sample
+// lands in the bin the host reading assigns it, with no FP64 per sample.  Each
 // thread walks a contiguous run of samples and adds a run of equal bins with
 // one shared-memory atomic; the profile and counts are exact integers.
 // Thread 0 then forms the reduced chi-square against a flat profile,
@@ -19,6 +20,15 @@ namespace pss {
 namespace {
 
 constexpr int NT = 256;
+
+// rint(v 2^64) modulo 2^64, round half to even: v - trunc(v) is exact in FP64
+// and lies in (-1, 1), its scaling by 2^64 is exact, and a negative fraction
+// wraps (2^64 - rint(|r| 2^64))
+__device__ __forceinline__ unsigned long long fixed_point(double v) {
+    const double r = __dsub_rn(v, trunc(v));
+    if (r >= 0.0) return __double2ull_rn(ldexp(r, 64));
+    return 0ull - __double2ull_rn(ldexp(-r, 64));
+}
 
 __global__ void __launch_bounds__(NT) k_fold(const __grid_constant__ FoldArgs a) {
     extern __shared__ __align__(16) unsigned long long sm[];  // P [nbin], then n [nbin] (u32)
@@ -37,8 +47,8 @@ __global__ void __launch_bounds__(NT) k_fold(const __grid_constant__ FoldArgs a)
     // fixed point (2^-64 cycle, modulo one cycle), rounded to nearest even
     const double x = __dmul_rn(f, it.dt);
     const double g = __dmul_rn(__dmul_rn(0.5, it.fdot), __dmul_rn(it.dt, it.dt));
-    const unsigned long long X = __double2ull_rn(ldexp(__dsub_rn(x, floor(x)), 64));
-    const unsigned long long G = __double2ull_rn(ldexp(__dsub_rn(g, floor(g)), 64));
+    const unsigned long long X = fixed_point(x);
+    const unsigned long long G = fixed_point(g);
     const unsigned long long nb = (unsigned long long)a.nbin;
     const int32_t* s = a.series + (int64_t)it.row * a.stride;
     const int64_t n = it.n;
@@ -50,7 +60,7 @@ __global__ void __launch_bounds__(NT) k_fold(const __grid_constant__ FoldArgs a)
     for (int64_t j = j0; j < j1; ++j) {
         const unsigned long long ju = (unsigned long long)j;
         const unsigned long long ph = ju * X + (ju * ju) * G;  // wraps modulo 2^64: one cycle
-        const int bin = (int)(((ph >> 32) * nb) >> 32);
+        const int bin = (int)__umul64hi(ph, nb);
         if (bin != cur) {
             if (c) {
                 atomicAdd(P + cur, acc);
