@@ -262,6 +262,15 @@ def recorded_traffic(workload, stage):
     return float(rec["dram_read_bytes"]) + float(rec["dram_write_bytes"])
 
 
+def bx_row(plan, wl, stage):
+    """Whether the library dedisperses a plan stage from the boxcar table when
+    the whole plan is searched in one call: ds in [BX_MIN, 256], an exact
+    plan, at most 65535 kept channels, and at least 16 trials in the row."""
+    st = wl.stages[stage]
+    return (BX_MIN > 0 and BX_MIN <= st.ds <= 256 and st.n_dm >= 16 and wl.fil.nchan <= 65535
+            and not getattr(plan, "subband", None))
+
+
 def stage_work(plan, wl, fil_nbytes):
     """Algorithmic work of one step per profiled stage: (bound, amount, unit).
 
@@ -286,7 +295,7 @@ def stage_work(plan, wl, fil_nbytes):
         t = plan.trial(i)
         nv, nfft, ds = t["nv"], t["nfft"], t["ds"]
         M = nfft // 2
-        if BX_MIN > 0 and BX_MIN <= ds <= 256:
+        if bx_row(plan, wl, t["stage"]):
             adds += 2.0 * wl.fil.nchan * nv  # one 32-bit add per table term: two SWAR add slots
         else:
             adds += float(wl.fil.nchan) * nv * ds
@@ -313,7 +322,7 @@ def stage_work(plan, wl, fil_nbytes):
     # channel-major bytes and writing the uint16 table of C x ds x ceil(N/ds) (rows of 8)
     C, N = wl.fil.nchan, wl.fil.nsamp
     bx_b = 0.0
-    for ds in sorted({s.ds for s in wl.stages if s.n_dm > 0 and BX_MIN > 0 and BX_MIN <= s.ds <= 256}):
+    for ds in sorted({s.ds for k, s in enumerate(wl.stages) if bx_row(plan, wl, k)}):
         mstride = ((N + ds - 1) // ds + 7) // 8 * 8
         bx_b += float(C) * N + 2.0 * C * ds * mstride
     return {"unpack": ("hbm", 2.0 * fil_nbytes, "bytes"),
@@ -325,8 +334,27 @@ def stage_work(plan, wl, fil_nbytes):
             "harmsum": ("hbm", harm_b, "bytes")}
 
 
-def roofline_of(stage, bound, amount, unit, ms, launches, peaks, peak_kind):
-    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+# Instructions per channel-addition at the floor of the SWAR dedispersion loop:
+# per 32-bit word of 4 samples one 128-bit shared-memory load serves 4 words
+# (0.25), two extractions (mask and byte permute) and one three-input add that
+# folds two channels' halves (1.0): 3.25 instructions per 4 channel-additions.
+DEDISP_INSTR_PER_ADD = 3.25 / 4.0
+
+
+def alu_denominators(probe):
+    """Integer and FP32 roofline denominators from the device probes
+    (pss_measure_peaks): the dedispersion ceiling is the smaller of the
+    shared-memory operand bandwidth (every channel-addition reads its 8-bit
+    sample from shared memory once: 1 byte) and the issue rate with the
+    integer and FMA pipes busy over DEDISP_INSTR_PER_ADD instructions."""
+    smem = probe["lds_bytes_per_s"]
+    issue = probe["mix_per_s"] / DEDISP_INSTR_PER_ADD
+    return {"channel_adds_per_s": min(smem, issue), "smem_bound_adds_per_s": smem,
+            "issue_bound_adds_per_s": issue, "int32_adds_per_s": probe["int32_adds_per_s"],
+            "fp32_flops_per_s": probe["fp32_flops_per_s"]}
+
+
+def roofline_of(stage, bound, amount, unit, ms, launches, peaks, peak_kind, alu):
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     per_launch = amount / max(launches, 1)
     t = (ms / max(launches, 1)) / 1e3
@@ -336,19 +364,124 @@ def roofline_of(stage, bound, amount, unit, ms, launches, peaks, peak_kind):
         return {"kernel": stage, "bound": "hbm", "achieved": ach / 1e9, "peak": hbm, "unit": "GB/s",
                 "frac": ach / peak, "traffic": None, "peak_source": "hbm_gbs (%s)" % peak_kind}
     if unit == "channel-adds":
-        # 152 SMs x 64 integer-ALU lanes x 2 sixteen-bit additions per 32-bit add
-        peak = 152 * 64 * 2 * sm_mhz * 1e6
+        peak = alu["channel_adds_per_s"]
         return {"kernel": stage, "bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12,
                 "unit": "T channel-adds/s", "frac": ach / peak, "traffic": None,
-                "peak_source": "derived: 152 SMs x 64 INT lanes x 2 (16-bit SWAR) x %.0f MHz (%s clock)"
-                               % (sm_mhz, peak_kind)}
-    peak = 152 * 128 * 2 * sm_mhz * 1e6  # FP32 FMA lanes
+                "frac_of_int32_add_peak": ach / (2.0 * alu["int32_adds_per_s"]),
+                "peak_source": "measured (pss_measure_peaks): min(shared-memory load bytes/s at 1 byte per "
+                               "channel-add, lop3/imad issue rate / %.4f instructions per channel-add)"
+                               % DEDISP_INSTR_PER_ADD}
+    peak = alu["fp32_flops_per_s"]
     return {"kernel": stage, "bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-            "frac": ach / peak, "traffic": None,
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x %.0f MHz (%s clock)" % (sm_mhz, peak_kind)}
+            "frac": ach / peak, "traffic": None, "peak_source": "measured (pss_measure_peaks): FP32 FMA rate"}
 
 
 # ---------------------------------------------------------------- GPU arm
+def measure_search(pss, wl, name, steps, warmup, local_rank, flush, stream, peaks, peak_kind, alu, world=1,
+                   traffic=True):
+    """One workload through pss_search_dm_batch with the file resident on
+    the device: `steps` steps timed by CUDA events on the launching stream
+    (L2 flushed between them), per-stage device time from the library's
+    profiler, rooflines against the measured peaks, then the same call with
+    the file in pinned host memory (upload and candidate download timed).
+    Returns (result dict, context, plan, cfg, device data, candidates); the
+    caller closes the context."""
+    import torch
+    dev = torch.device("cuda", local_rank)
+    fil = wl.fil
+    ctx = pss.Context(local_rank)
+    plan = pss.Plan(pss.FilDesc.of(fil), wl.stages)
+    cfg = pss.cfg_of(wl.cfg)
+    ndm = plan.ndm
+    data_dev = torch.from_numpy(fil.data).to(dev)
+    data_host = torch.from_numpy(fil.data).pin_memory()
+
+    def step(on_device=True):
+        if on_device:
+            return pss.pss_search_dm_batch(ctx, plan, data_dev, cfg, 0, ndm, stream=stream.cuda_stream)
+        # a numpy view of the pinned tensor: the library uploads it inside the call
+        return pss.pss_search_dm_batch(ctx, plan, data_host.numpy(), cfg, 0, ndm, stream=stream.cuda_stream)
+
+    cands = None
+    for _ in range(warmup):
+        cands = step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ctx.profile(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    barrier()
+    t_wall0 = time.perf_counter()
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        cands = step()
+        ev[k][1].record(stream)
+    barrier()
+    t_wall = time.perf_counter() - t_wall0
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = max_over_ranks(sum(step_ms) / len(step_ms), world, dev)
+
+    e2e_ms = []
+    for k in range(max(1, steps)):
+        flush.fill_((k + 1) & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(on_device=False)
+        t1 = time.perf_counter()
+        e2e_ms.append(1e3 * (t1 - t0))
+    e2e = max_over_ranks(statistics.mean(e2e_ms), world, dev)
+
+    work = stage_work(plan, wl, fil.nbytes())
+    rooflines = {}
+    for st, (ms_st, n_st) in prof.items():
+        if n_st == 0:
+            continue
+        bound, amount, unit = work[st]
+        rooflines[st] = roofline_of(st, bound, amount * steps, unit, ms_st, n_st, peaks, peak_kind, alu)
+        if traffic:
+            rooflines[st]["traffic"] = recorded_traffic(name, st)
+    if "dedisperse" in rooflines:
+        # the same launches against HBM: every trial's FP32 series written once, the
+        # channel-major file read once per launch
+        ms_dd, n_dd = prof["dedisperse"]
+        nv_sum = sum(plan.trial(i)["nv"] for i in range(ndm))
+        dd_bytes = 4.0 * nv_sum * steps + float(fil.nchan) * fil.nsamp * n_dd
+        rooflines["dedisperse"]["hbm_frac"] = (dd_bytes / (ms_dd / 1e3)) / (float(peaks.get("hbm_gbs", 6800.0)) * 1e9)
+        bx_rows = sorted({wl.stages[k].ds for k in range(len(wl.stages)) if bx_row(plan, wl, k)})
+        if bx_rows:
+            rooflines["dedisperse"]["note"] = (
+                "rows with ds %s dedisperse from a per-channel boxcar table built once per ds (stage bxtable): "
+                "one table term per output and channel, a 32-bit add counted as two 16-bit SWAR slots" % bx_rows)
+    dominant = max(prof, key=lambda k: prof[k][0])
+    launches_per_step = sum(n for _, n in prof.values()) / steps
+    bi = fil.nbytes()
+    bo = int(len(cands)) * pss.CAND_DTYPE.itemsize
+    res = {"metric": METRIC, "value": job_value(world, ndm, ms), "unit": UNIT, "steps": steps, "warmup": warmup,
+           "ms_per_step": ms, "config": _config(wl, name, {"dm_trials": ndm}), "files_per_s": world * 1e3 / ms,
+           "s_per_file": ms / 1e3, "realtime_budget_s": REALTIME_S, "realtime_factor": REALTIME_S / (ms / 1e3),
+           "roofline": rooflines[dominant],
+           "e2e": {"value": job_value(world, ndm, e2e), "unit": UNIT, "h2d_bytes_per_step": bi,
+                   "d2h_bytes_per_step": bo, "ms_per_step": e2e},
+           "gpu_launches": int(round(launches_per_step * steps)),
+           "stages_ms_per_step": {k: v[0] / steps for k, v in prof.items()},
+           "stage_launches_per_step": {k: v[1] / steps for k, v in prof.items()},
+           "stage_rooflines": {k: {kk: v[kk] for kk in ("bound", "frac", "achieved", "unit", "hbm_frac")
+                                   if kk in v} for k, v in rooflines.items()},
+           "clocks": clocks.summary(), "wall_s_timed": t_wall, "candidates": int(len(cands))}
+    return res, ctx, plan, cfg, data_dev, cands
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -373,63 +506,16 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
+    peaks, peak_kind = measured_peaks()
+    probe = pss.pss_measure_peaks(local_rank)
+    alu = alu_denominators(probe)
     wl = make_workload(name, n_dm=args.dm_trials, seed_offset=rank)
-    fil = wl.fil
-    ctx = pss.Context(local_rank)
-    plan = pss.Plan(pss.FilDesc.of(fil), wl.stages)
-    cfg = pss.cfg_of(wl.cfg)
-    ndm = plan.ndm
-    data_dev = torch.from_numpy(fil.data).to(dev)
-    data_host = torch.from_numpy(fil.data).pin_memory()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-
-    def step(on_device=True):
-        if on_device:
-            return pss.pss_search_dm_batch(ctx, plan, data_dev, cfg, 0, ndm, stream=stream.cuda_stream)
-        # a numpy view of the pinned tensor: the library uploads it inside the call
-        return pss.pss_search_dm_batch(ctx, plan, data_host.numpy(), cfg, 0, ndm, stream=stream.cuda_stream)
-
-    for _ in range(args.warmup):
-        cands = step()
-    torch.cuda.synchronize()
-
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    # timed region: per-step CUDA events, L2 flushed between steps
-    clocks = ClockSampler(local_rank)
-    clocks.start()
-    ctx.profile(True)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    barrier()
-    t_wall0 = time.perf_counter()
-    for k in range(args.steps):
-        flush.fill_(k & 0xFF)
-        ev[k][0].record(stream)
-        cands = step()
-        ev[k][1].record(stream)
-    barrier()
-    t_wall = time.perf_counter() - t_wall0
-    prof = ctx.profile_read()
-    ctx.profile(False)
-    clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = max_over_ranks(sum(step_ms) / len(step_ms), world, dev)
-
-    # e2e through the same call with the file in pinned host memory
-    e2e_ms = []
-    for k in range(max(1, args.steps)):
-        flush.fill_((k + 1) & 0xFF)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        step(on_device=False)
-        t1 = time.perf_counter()
-        e2e_ms.append(1e3 * (t1 - t0))
-    e2e = max_over_ranks(statistics.mean(e2e_ms), world, dev)
+    head, ctx, plan, cfg, data_dev, cands = measure_search(
+        pss, wl, name, args.steps, args.warmup, local_rank, flush, stream, peaks, peak_kind, alu, world,
+        traffic=args.dm_trials is None)
+    ndm = plan.ndm
 
     refine = None
     if wl.cfg.zmax > 0 and rank == 0 and len(cands) and args.refine_top > 0:
@@ -454,55 +540,79 @@ def run_ours(args, rank, world, local_rank):
         batched = run_batched(pss, plan, cfg, data_dev, ndm, max(3, args.steps), flush)
         if rank == 0:
             served = run_served(pss, name, wl, args, local_rank)
+    ctx.close()
+    del data_dev
+
+    # the other workloads of the benchmark, each a sub-object with its own timing (1 GPU only)
+    extras = {}
+    if rank == 0 and world == 1 and args.extras:
+        for ex in args.extras.split(","):
+            t0 = time.perf_counter()
+            if ex == "stream":
+                extras["stream"] = run_stream(args, local_rank, n_files=args.extra_stream_files)
+            else:
+                extras[ex] = run_extra(pss, ex, args, local_rank, flush, stream, peaks, peak_kind, alu)
+            extras[ex]["bench_wall_s"] = time.perf_counter() - t0
 
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()
         return
-    value = job_value(world, ndm, ms)
-    peaks, peak_kind = measured_peaks()
-    work = stage_work(plan, wl, fil.nbytes())
-    rooflines = {}
-    for st, (ms_st, n_st) in prof.items():
-        if n_st == 0:
-            continue
-        bound, amount, unit = work[st]
-        rooflines[st] = roofline_of(st, bound, amount * args.steps, unit, ms_st, n_st, peaks, peak_kind)
-        if args.dm_trials is None:
-            rooflines[st]["traffic"] = recorded_traffic(name, st)
-    bx_rows = [s.ds for s in wl.stages if BX_MIN > 0 and BX_MIN <= s.ds <= 256]
-    if bx_rows and "dedisperse" in rooflines:
-        rooflines["dedisperse"]["note"] = (
-            "rows with ds %s dedisperse from a per-channel boxcar table built once per ds (stage bxtable): "
-            "one table term per output and channel, a 32-bit add counted as two 16-bit SWAR slots"
-            % sorted(set(bx_rows)))
-    dominant = max(prof, key=lambda k: prof[k][0])
-    launches_per_step = sum(n for _, n in prof.values()) / args.steps
-    bi = fil.nbytes()
-    bo = int(len(cands)) * pss.CAND_DTYPE.itemsize
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": value / PAPER_RATE[name] if name in PAPER_RATE and args.dm_trials is None else None,
-            "dtype": "i32+f32", "data": "synthetic",
-            "config": _config(wl, name, {"dm_trials": ndm}), "files_per_s": world * 1e3 / ms,
-            "s_per_file": ms / 1e3, "realtime_budget_s": REALTIME_S, "realtime_factor": REALTIME_S / (ms / 1e3),
-            "roofline": rooflines[dominant],
-            "e2e": {"value": job_value(world, ndm, e2e), "unit": UNIT, "h2d_bytes_per_step": bi,
-                    "d2h_bytes_per_step": bo, "ms_per_step": e2e},
-            "gpu_launches": int(round(launches_per_step * args.steps)),
-            "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
-            "stage_launches_per_step": {k: v[1] / args.steps for k, v in prof.items()},
-            "stage_rooflines": {k: {"bound": v["bound"], "frac": v["frac"], "achieved": v["achieved"],
-                                    "unit": v["unit"]} for k, v in rooflines.items()},
-            "clocks": clocks.summary(), "wall_s_timed": t_wall, "candidates": int(len(cands)),
-            "batched": batched, "serve": served, "refine": refine, "subband": subband, "single_pulse": single, "fold": folded,
-            "cpu_baseline": cpu}
+    line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": head["value"] / PAPER_RATE[name] if name in PAPER_RATE and args.dm_trials is None else None,
+            "dtype": "i32+f32", "data": "synthetic"}
+    for k in ("config", "files_per_s", "s_per_file", "realtime_budget_s", "realtime_factor", "roofline", "e2e",
+              "gpu_launches", "stages_ms_per_step", "stage_launches_per_step", "stage_rooflines", "clocks",
+              "wall_s_timed", "candidates"):
+        line[k] = head[k]
+    line.update({"batched": batched, "serve": served, "refine": refine, "subband": subband, "single_pulse": single,
+                 "fold": folded, "alu_peaks": {"probe": probe, "denominators": alu}, "cpu_baseline": cpu})
+    line.update(extras)
     print(json.dumps(line), flush=True)
-    ctx.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_extra(pss, ex, args, local_rank, flush, stream, peaks, peak_kind, alu):
+    """A sub-object of the default line: the acceleration file with the
+    refinement of its top 4096 candidates and its prepared batch (accel), the
+    PMPS-shaped file at zmax 0 and 50 (pmps), or the FAST-shaped file with the
+    printed Table 3 plan (fast)."""
+    import torch
+    steps = max(2, args.extra_steps)
+    if ex == "accel":
+        wl = make_workload("accel")
+        res, ctx, plan, cfg, data_dev, cands = measure_search(pss, wl, "accel", steps, 3, local_rank, flush, stream,
+                                                              peaks, peak_kind, alu)
+        if len(cands) and args.refine_top > 0:
+            res["refine"] = run_refine(pss, ctx, plan, data_dev, cfg, cands, args.refine_top)
+        ctx.close()
+        res["batched"] = run_batched(pss, plan, cfg, data_dev, plan.ndm, steps, flush)
+        return res
+    if ex == "pmps":
+        wl = make_workload("pmps")
+        out = {}
+        for z, key in ((0, "zmax0"), (50, "zmax50")):
+            wl.cfg.zmax = z
+            nm = "pmps" if z == 0 else "pmps50"
+            res, ctx, plan, cfg, data_dev, cands = measure_search(pss, wl, nm, steps, 3 if z == 0 else 2, local_rank,
+                                                                  flush, stream, peaks, peak_kind, alu)
+            ctx.close()
+            out[key] = res
+            del data_dev
+            torch.cuda.empty_cache()
+        return out
+    if ex == "fast":
+        wl = make_workload("fast")
+        res, ctx, plan, cfg, data_dev, cands = measure_search(pss, wl, "fast", max(steps, 5), 3, local_rank, flush,
+                                                              stream, peaks, peak_kind, alu)
+        ctx.close()
+        res["vs_paper_cpu_rate"] = res["value"] / PAPER_RATE["fast"]
+        return res
+    raise ValueError(ex)
 
 
 def run_refine(pss, ctx, plan, data_dev, cfg, cands, top, iters=40):
@@ -676,22 +786,21 @@ def run_served(pss, name, wl, args, device):
             "budget_gib": args.serve_budget_gib}
 
 
-def run_stream(args, rank, world, local_rank):
+def run_stream(args, local_rank, n_files=None):
     """Mixed-shape drift-scan stream (128-1024 channels, 2^17-2^19 samples,
     0-3 pulsars, DM 0-500 step 1, zmax 100, numharm 8; Poisson arrivals with
     a 26 s mean replayed faster by --stream-speedup): the plain per-file loop
     (pss_search_dm_batch on host data, one file after another), then the
     request loop (pss_server) saturated (all files queued at once) and paced
-    at the replayed arrival times, with submit-to-result latencies."""
-    import numpy as np
+    at the replayed arrival times, with submit-to-result latencies.  Returns
+    the measurement as a dict (the contract keys included)."""
     import torch
 
     from paper_1912_12807_gb300 import pss, synth
-    if rank != 0:
-        return
+    n_files = n_files or args.stream_files
     torch.cuda.set_device(local_rank)
     t0 = time.perf_counter()
-    files = list(synth.stream_files(args.stream_files, speedup=args.stream_speedup))
+    files = list(synth.stream_files(n_files, speedup=args.stream_speedup))
     t_gen = time.perf_counter() - t0
     ndm = int(sum(st.n_dm for st in files[0][1].stages))
     shapes = sorted({(w.fil.nchan, w.fil.nsamp) for _, w in files})
@@ -735,11 +844,40 @@ def run_stream(args, rank, world, local_rank):
     lat = sorted(srv.poll(t)[1] for t in pending)
     t_paced = time.perf_counter() - tick
     srv.close()
+    # grouped: queued files searched together (pss_search_multi: one launch per stage over a group)
+    grouped = None
+    if args.stream_group > 1:
+        srv = pss.Server(budget, max_slots=args.serve_slots, device=local_rank, max_group=args.stream_group)
+        for t in [srv.submit(d, w.fil.data, stages, cfg) for (_, w), d in zip(files, descs)]:
+            srv.poll(t)
+        t0 = time.perf_counter()
+        ts = [srv.submit(d, w.fil.data, stages, cfg) for (_, w), d in zip(files, descs)]
+        n_grouped = sum(len(srv.poll(t)[0]) for t in ts)
+        t_gsat = time.perf_counter() - t0
+        st_sat = srv.stats()
+        tick = time.perf_counter()
+        pending = []
+        for (ta, w), d in zip(files, descs):
+            while time.perf_counter() < tick + ta:
+                time.sleep(0.001)
+            pending.append(srv.submit(d, w.fil.data, stages, cfg))
+        glat = sorted(srv.poll(t)[1] for t in pending)
+        t_gpaced = time.perf_counter() - tick
+        st_all = srv.stats()
+        srv.close()
+        gp = lambda q: glat[max(0, math.ceil(q / 100.0 * len(glat)) - 1)]
+        grouped = {"max_group": args.stream_group, "slots": args.serve_slots,
+                   "saturated": {"value": len(files) * ndm / t_gsat, "unit": UNIT, "files_per_s": len(files) / t_gsat,
+                                 "s_per_file": t_gsat / len(files)},
+                   "paced": {"p50_ms": 1e3 * gp(50), "p99_ms": 1e3 * gp(99), "max_ms": 1e3 * glat[-1],
+                             "wall_s": t_gpaced},
+                   "groups": st_all["groups"], "grouped_files": st_all["grouped_files"],
+                   "groups_saturated_pass": st_sat["groups"], "candidates": n_grouped}
     clocks.stop()
     pct = lambda q: lat[max(0, math.ceil(q / 100.0 * len(lat)) - 1)]
     n = len(files)
     value = n * ndm / t_sat
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": n, "warmup": n,
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": n, "warmup": n,
             "ms_per_step": 1e3 * t_sat / n, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "i32+f32", "data": "synthetic",
             "config": {"workload": "stream_%dfiles_128-1024ch_2^17-2^19_dm0-500x1_zmax100_numharm8" % n,
@@ -754,8 +892,8 @@ def run_stream(args, rank, world, local_rank):
             "served_paced": {"p50_ms": 1e3 * pct(50), "p99_ms": 1e3 * pct(99), "max_ms": 1e3 * lat[-1],
                              "wall_s": t_paced, "realtime_budget_s": REALTIME_S},
             "candidates": {"plain": n_plain, "served": n_served},
+            "grouped": grouped,
             "clocks": clocks.summary(), "generation_s": t_gen}
-    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -772,12 +910,20 @@ def main():
     ap.add_argument("--stream-files", type=int, default=64)
     ap.add_argument("--refine-top", type=int, default=4096, help="candidates refined after a zmax > 0 search")
     ap.add_argument("--stream-speedup", type=float, default=50.0)
+    ap.add_argument("--stream-group", type=int, default=8,
+                    help="files per group of the grouped server in the stream measurement (1: not measured)")
     ap.add_argument("--fold-top", type=int, default=64, help="sifted candidates folded after the search (0: none)")
     ap.add_argument("--single-pulse", type=int, default=None,
                     help="1: also time the single-pulse search of every trial (default: 1 for the drift-scan workload)")
     ap.add_argument("--subband", default=None,
                     help="'nsub,group' of a two-stage plan searched beside the exact one, or 'none' "
                          "(default: 16,16 for the drift-scan workload, none otherwise)")
+    ap.add_argument("--extras", default=None,
+                    help="comma list of other workloads measured as sub-objects of the default line at N=1 "
+                         "(accel, pmps, stream, fast; default: all four for the drift-scan workload, none otherwise; "
+                         "'' for none)")
+    ap.add_argument("--extra-steps", type=int, default=3, help="timed steps of each extra workload")
+    ap.add_argument("--extra-stream-files", type=int, default=16, help="files of the extra stream measurement")
     ap.add_argument("--dm-trials", type=int, default=None,
                     help="DM trials of a single-stage plan (driftscan/accel); smaller values make profiling cases")
     args = ap.parse_args()
@@ -785,6 +931,8 @@ def main():
         args.subband = "16,16" if args.workload == "driftscan" else "none"
     if args.single_pulse is None:
         args.single_pulse = 1 if args.workload == "driftscan" else 0
+    if args.extras is None:
+        args.extras = "accel,pmps,stream,fast" if args.workload == "driftscan" and args.dm_trials is None else ""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
@@ -792,7 +940,8 @@ def main():
         run_reference(args, rank)
         return
     if args.workload == "stream":
-        run_stream(args, rank, world, local_rank)
+        if rank == 0:
+            print(json.dumps(run_stream(args, local_rank)), flush=True)
         return
     run_ours(args, rank, world, local_rank)
 
