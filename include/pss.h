@@ -146,6 +146,27 @@ const char* pss_last_error(void);
 /* Library version string. */
 const char* pss_version(void);
 
+/* Failure detection.  Every staging-barrier wait of the dedispersion kernels
+ * is bounded: when it runs out the kernel sets an error flag, lets the bulk
+ * copies it has in flight land (with the full bound), and leaves without
+ * writing; the call then returns PSS_ETIMEOUT and the context stays usable.
+ * pss_ctx_set_wait_limit(ctx, polls) with polls > 0 makes those data waits
+ * give up after `polls` non-blocking polls on this context (so that a test
+ * can make them run out); 0 restores the default bound (2^22 blocking
+ * polls).  The limit applies to calls and prepared batches made after it
+ * is set.  The paper has no counterpart (its jobs are OS processes). */
+pss_status pss_ctx_set_wait_limit(pss_ctx* ctx, int32_t polls);
+/* Synchronise `stream` and report (then clear) a bounded-wait failure or a
+ * refused launch of the context's kernels since the last report:
+ * PSS_ETIMEOUT / PSS_EINVAL, else PSS_OK.  The asynchronous calls
+ * (pss_dedisperse) report through this; the calls that synchronise check
+ * the flag themselves and discard their results when it is set. */
+pss_status pss_ctx_check(pss_ctx* ctx, void* stream);
+/* Test hook: the n-th device allocation of the library from now on (any
+ * context) fails as if the device were out of memory, and the call that
+ * made it returns PSS_ENOMEM; n <= 0 turns the hook off. */
+void pss_debug_fail_alloc(int64_t n);
+
 /* Per-stage device-time accounting (tracing).  While enabled, every kernel
  * launch of the search path is bracketed by CUDA events on the stream it is
  * launched on.  Stages: 0 unpack/transpose, 1 dedisperse, 2 FFT passes,
@@ -259,7 +280,9 @@ void pss_plan_free(pss_plan* plan);
  * s_ds[j] = sum_{k<ds} s[j*ds + k] for j < N_v.
  * data: the file bytes (host if data_on_device == 0, else device).
  * out: device int32; trial i's N_v values start at element
- * sum_{dm_begin <= k < i} N_v(k) (rows packed back to back). */
+ * sum_{dm_begin <= k < i} N_v(k) (rows packed back to back).
+ * Asynchronous: a kernel that gives up (a bounded wait that runs out) is
+ * reported by pss_ctx_check or the context's next synchronising call. */
 pss_status pss_dedisperse(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* fil,
                           const void* data, int data_on_device, int64_t dm_begin,
                           int64_t dm_end, int32_t* out, void* stream);
@@ -502,6 +525,41 @@ pss_status pss_batch_create(int device, const pss_plan* plan, const pss_fil_desc
  * time of copy + graph.  Not thread-safe for one batch. */
 pss_status pss_batch_run(pss_batch* b, const void* data, int data_on_device, pss_cand* out, int64_t cap,
                          int64_t* n_out, double* gpu_ms);
+/* ---- several files in one launch per stage (Sect. 2 parallel versions) -- */
+
+/* One file of a group: its plan (exact, not two-stage), descriptor and bytes
+ * (host or device, as the call's data_on_device says). */
+typedef struct {
+    const pss_plan* plan;
+    const pss_fil_desc* fil;
+    const void* data;
+} pss_multi_file;
+
+/* Search nfiles files of any channel count, sample count, bit depth, layout
+ * and DM plan with the same search parameters, as one group: the trials of
+ * every file become rows grouped by transform length, and each batch of rows
+ * is one launch per stage whose kernels walk a device-side work list (the
+ * unpack and dedispersion kernels: items of (file, stage, run of trials,
+ * tile); the FFT, whitening, plane and harmonic-sum kernels: rows carrying
+ * their file, trial, N_v and f_lo cut).  The sequence runs as one captured
+ * CUDA graph (the first group that uses a new transform length on a context
+ * runs eagerly, which loads its kernels).  This replaces the paper's
+ * process-level parallel versions V2/V3 (Sect. 2) for many files at once.
+ * Each file's sifted list is byte-identical to pss_search_dm_batch of that
+ * file alone on a context with the same launch shapes.
+ * out: host [cap], the lists of file 0, 1, ... back to back; counts: host
+ * [nfiles] the length of each; *n_out their total (PSS_ECAP when it exceeds
+ * cap: the context keeps the lists for pss_ctx_take_cands, counts are set).
+ * PSS_EINVAL for a two-stage plan or arguments pss_search_dm_batch would
+ * refuse.  Synchronises `stream`. */
+pss_status pss_search_multi(pss_ctx* ctx, const pss_search_cfg* cfg, const pss_multi_file* files, int32_t nfiles,
+                            int data_on_device, pss_cand* out, int64_t cap, int64_t* counts, int64_t* n_out,
+                            void* stream);
+/* Device bytes pss_search_multi holds for this group (host arithmetic, no
+ * device): what a server admits a group by. */
+pss_status pss_search_multi_footprint(const pss_search_cfg* cfg, const pss_multi_file* files, int32_t nfiles,
+                                      size_t* bytes);
+
 /* The sifted candidates of the batch's last pss_batch_run (kept after
  * PSS_ECAP so that they need not be searched again); errors as
  * pss_ctx_take_cands. */
@@ -562,6 +620,18 @@ void pss_batch_free(pss_batch* b);
 typedef struct pss_server pss_server;
 typedef struct pss_result pss_result;
 pss_status pss_server_create(int device, size_t hbm_budget_bytes, int max_slots, pss_server** out);
+/* pss_server_create with grouping: with max_group > 1 each slot takes the
+ * file at the head of the queue together with the files queued right
+ * behind it (same search parameters, exact plans, at most max_group, while
+ * the group's footprint fits what is left of the budget) and searches them
+ * as one group with pss_search_multi on a context of its own; a two-stage
+ * plan runs alone.  Results (per file, by ticket) are the same bytes as the
+ * file searched alone with the default launch shapes.  max_group 1 is
+ * pss_server_create.  max_group in [1, 1024]. */
+pss_status pss_server_create_grouped(int device, size_t hbm_budget_bytes, int max_slots, int max_group,
+                                     pss_server** out);
+/* Groups a grouped server has run and the files in them. */
+pss_status pss_server_group_stats(pss_server* srv, int64_t* groups, int64_t* files);
 /* Queue a file (host bytes, copied before return) with its plan stages and
  * search cfg; *ticket identifies the result. */
 pss_status pss_submit_file(pss_server* srv, const pss_fil_desc* fil, const void* host_data,

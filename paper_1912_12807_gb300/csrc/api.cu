@@ -18,10 +18,15 @@
 
 namespace pss {
 
+// pss_debug_fail_alloc: device allocations left before one is made to fail (<= 0: none)
+std::atomic<int64_t> g_alloc_countdown{0};
+
 pss_status DevBuf::ensure(size_t want) {
     if (want <= bytes) return PSS_OK;
     release();
     size_t sz = want + want / 8 + 256;
+    if (g_alloc_countdown.load() > 0 && g_alloc_countdown.fetch_sub(1) == 1)
+        return fail(PSS_ENOMEM, "device allocation of " + std::to_string(sz) + " bytes refused (pss_debug_fail_alloc)");
     cudaError_t e = cudaMalloc(&p, sz);
     if (e != cudaSuccess) {
         p = nullptr;
@@ -420,6 +425,7 @@ pss_status enqueue_dedisp(pss_ctx* ctx, const pss_plan* plan, int32_t ck, int64_
         da.spread = spread;
         da.err = (int*)ctx->errflag.p;
         da.chunk_kb = ctx->tune.dedisp_kb;
+        da.wait_polls = ctx->wait_polls;
         ProfScope ps(ctx, 1, s);
         PSS_CUDA(launch_dedisp(da, ctx->num_sms, s));
         return PSS_OK;
@@ -444,6 +450,7 @@ pss_status enqueue_dedisp(pss_ctx* ctx, const pss_plan* plan, int32_t ck, int64_
     da.spread = SB.spread1;
     da.err = (int*)ctx->errflag.p;
     da.chunk_kb = ctx->tune.dedisp_kb;
+    da.wait_polls = ctx->wait_polls;
     PSS_CUDA(launch_dedisp(da, ctx->num_sms, s));
     SubsumArgs sa{};
     sa.u = (const int32_t*)subu;
@@ -458,6 +465,7 @@ pss_status enqueue_dedisp(pss_ctx* ctx, const pss_plan* plan, int32_t ck, int64_
     sa.nb = nb;
     sa.nv = st.nv;
     sa.ds = st.ds;
+    sa.wait_polls = ctx->wait_polls;
     sa.out_f = out_f;
     sa.out_i = out_i;
     sa.out_stride = out_stride;
@@ -1169,7 +1177,464 @@ pss_status search_raw_vec(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc
     return fail(PSS_ECAP, "candidate buffer overflow persisted after resizing");
 }
 
+// ---- multi-file search: one launch per stage over a group of files -------
+//
+// The files of a group may differ in channels, samples, bits, layout and DM
+// plan (exact plans) and share the search parameters.  Their trials become
+// rows grouped by transform length; each length class runs in batches of
+// rows (batch_trials), and every batch is one launch per stage over rows of
+// several files: the work-list dedispersion (items = runs of consecutive
+// trials of one file and stage, one launch per kernel variant: at most 256
+// kept channels or more) into float rows, the FFT passes and whitening with
+// each row's own N_v, the plane, and the harmonic sums with each row's DM
+// index, file index and f_lo cut.  Before the batches, one work-list launch
+// unpacks every file.  The whole sequence is captured into one graph and
+// launched once.  The kernels and their arithmetic are those of the
+// single-file path, so every file's sorted candidate list is byte-identical
+// to a search of that file alone on a context with the same launch shapes.
+
+struct MultiRow {
+    int32_t file, stage;
+    int64_t trial;
+};
+
+struct MultiBatch {
+    int64_t nfft;
+    int32_t nrows;
+    int64_t items_narrow = 0, n_narrow = 0, ctas_narrow = 0;  // byte offset in the work list, count, CTAs
+    int64_t items_wide = 0, n_wide = 0, ctas_wide = 0;
+    size_t shm_narrow = 0, shm_wide = 0;
+    int64_t nv_rows = 0, row_dm = 0, row_file = 0, row_hmin = 0;  // byte offsets
+};
+
+struct MultiSetup {
+    std::vector<int32_t> ck;
+    std::vector<int64_t> pitch, fil_off, xcm_off, tab_off;  // tab_off: int32 elements into the table block
+    int64_t prep_items = 0, prep_ctas = 0;                  // byte offset of the prep items, CTAs
+    int64_t tab_bytes_off = 0;                              // byte offset of the table block
+    std::vector<MultiBatch> batches;
+    std::vector<uint8_t> work;                              // host image of ctx->mf_work
+    size_t fil_bytes = 0, xcm_bytes = 0;
+    size_t need_series = 0, need_sums = 0, need_fft = 0, need_plane = 0;
+    int nz = 1, Z = 0, nstages = 1;
+    float thr[6] = {0, 0, 0, 0, 0, 0};
+};
+
+template <class T>
+int64_t work_put(std::vector<uint8_t>* w, const T* v, size_t n) {
+    const int64_t off = (int64_t)((w->size() + 255) & ~size_t(255));
+    w->resize((size_t)off + n * sizeof(T));
+    if (n) memcpy(w->data() + off, v, n * sizeof(T));
+    return off;
+}
+
+size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
+
+// Host set-up of a group: validation, layouts and the work lists (device
+// pointers are formed from the buffers' addresses, which the caller has
+// sized from a first, sizing-only pass: bases null).
+pss_status multi_setup(const Tune& tune, int* errflag, int32_t wait_polls, const pss_search_cfg* cfg,
+                       const pss_multi_file* files,
+                       int32_t nfiles, const uint8_t* fil_base, const uint8_t* xcm_base, const uint8_t* work_base,
+                       float* series, unsigned long long* sums, MultiSetup* M) {
+    *M = MultiSetup();
+    M->nz = nz_of(cfg);
+    M->Z = cfg->zmax ? (int)llround(cfg->zmax / cfg->dz) : 0;
+    M->nstages = 0;
+    while ((1 << M->nstages) <= cfg->numharm) ++M->nstages;
+    for (int k = 0; k < M->nstages; ++k) M->thr[k] = thr_f32(1 << k, cfg->sigma_thr);
+    std::vector<int32_t> tab;
+    std::vector<PrepItem> prep;
+    for (int32_t f = 0; f < nfiles; ++f) {
+        const pss_plan* plan = files[f].plan;
+        const pss_fil_desc* fil = files[f].fil;
+        const std::vector<int32_t> keep = kept_channels(fil);
+        const int32_t ck = (int32_t)keep.size();
+        const int64_t pitch = xcm_pitch(*plan, fil);
+        M->ck.push_back(ck);
+        M->pitch.push_back(pitch);
+        M->fil_off.push_back((int64_t)M->fil_bytes);
+        M->fil_bytes += align256((size_t)file_bytes(fil));
+        M->xcm_off.push_back((int64_t)M->xcm_bytes);
+        M->xcm_bytes += align256((size_t)ck * pitch + 64);
+        M->tab_off.push_back((int64_t)tab.size());
+        const std::vector<int32_t> hd = compact_delays(plan, keep, 0, plan->ndm());
+        tab.insert(tab.end(), keep.begin(), keep.end());
+        tab.insert(tab.end(), hd.begin(), hd.end());
+        while (tab.size() % 64) tab.push_back(0);  // 256-byte steps
+    }
+    M->tab_bytes_off = work_put(&M->work, tab.data(), tab.size());
+    const int32_t* tab_dev = work_base ? (const int32_t*)(work_base + M->tab_bytes_off) : nullptr;
+    for (int32_t f = 0; f < nfiles; ++f) {
+        PrepItem it{};
+        it.a.src = (fil_base ? fil_base : (const uint8_t*)nullptr) + M->fil_off[f];
+        it.a.nchan = files[f].fil->nchan;
+        it.a.nbits = files[f].fil->nbits;
+        it.a.layout = files[f].fil->layout;
+        it.a.nsamp = files[f].fil->nsamp;
+        it.a.keep = tab_dev ? tab_dev + M->tab_off[f] : nullptr;
+        it.a.ck = M->ck[f];
+        it.a.xcm = (uint8_t*)(xcm_base ? xcm_base : (const uint8_t*)nullptr) + M->xcm_off[f];
+        it.a.pitch = M->pitch[f];
+        it.first = M->prep_ctas;
+        M->prep_ctas += prep_item_ctas(it.a, &it.gx);
+        prep.push_back(it);
+    }
+    M->prep_items = work_put(&M->work, prep.data(), prep.size());
+    // rows by transform length, longest first; within a length, file by file, trial by trial
+    std::map<int64_t, std::vector<MultiRow>, std::greater<int64_t>> classes;
+    for (int32_t f = 0; f < nfiles; ++f) {
+        const Plan& P = *files[f].plan;
+        for (size_t si = 0; si < P.stages.size(); ++si) {
+            const StageInfo& st = P.stages[si];
+            for (int64_t i = st.first; i < st.first + st.n_dm; ++i) classes[st.nfft].push_back({f, (int32_t)si, i});
+        }
+    }
+    for (const auto& kv : classes) {
+        const int64_t nfft = kv.first;
+        const std::vector<MultiRow>& rows = kv.second;
+        const int64_t B = batch_trials(nfft, M->nz, MODE_SEARCH, (int64_t)rows.size());
+        M->need_series = std::max(M->need_series, (size_t)B * nfft * 4);
+        M->need_sums = std::max(M->need_sums, (size_t)B * 8);
+        M->need_fft = std::max(M->need_fft, (size_t)B * (nfft / 2) * 8);
+        M->need_plane = std::max(M->need_plane, (size_t)B * M->nz * nfft * 4);
+        for (size_t r0 = 0; r0 < rows.size(); r0 += (size_t)B) {
+            const size_t r1 = std::min(rows.size(), r0 + (size_t)B);
+            MultiBatch mb;
+            mb.nfft = nfft;
+            mb.nrows = (int32_t)(r1 - r0);
+            std::vector<DedispItem> narrow, wide;
+            std::vector<int64_t> nv_rows;
+            std::vector<int32_t> row_dm, row_file, row_hmin;
+            size_t a = r0;
+            while (a < r1) {
+                size_t e = a + 1;
+                while (e < r1 && rows[e].file == rows[a].file && rows[e].stage == rows[a].stage &&
+                       rows[e].trial == rows[e - 1].trial + 1)
+                    ++e;
+                const int32_t f = rows[a].file;
+                const Plan& P = *files[f].plan;
+                const StageInfo& st = P.stages[rows[a].stage];
+                const int32_t ck = M->ck[f];
+                const int32_t* hd = tab.data() + M->tab_off[f] + ck + (size_t)rows[a].trial * ck;
+                DedispItem it{};
+                it.a.xcm = (const uint8_t*)(xcm_base ? xcm_base : (const uint8_t*)nullptr) + M->xcm_off[f];
+                it.a.pitch = M->pitch[f];
+                it.a.ck = ck;
+                it.a.delays = tab_dev ? tab_dev + M->tab_off[f] + ck + rows[a].trial * ck : nullptr;
+                it.a.nb = (int32_t)(e - a);
+                it.a.nv = st.nv;
+                it.a.ds = st.ds;
+                // (the sizing pass has no buffers yet: any non-null row address passes the checks)
+                it.a.out_f = series ? series + (int64_t)(a - r0) * nfft : reinterpret_cast<float*>(uintptr_t(256));
+                it.a.out_stride = nfft;
+                it.a.sums = sums ? sums + (a - r0) : nullptr;
+                it.a.spread = delay_spread(hd, (int64_t)(e - a), ck);
+                it.a.err = errflag;
+                it.a.chunk_kb = tune.dedisp_kb;
+                it.a.wait_polls = wait_polls;
+                size_t shm = 0;
+                if (!dedisp_item(&it, tune.dedisp_kb, &shm))
+                    return fail(PSS_EINVAL, "pss_search_multi: file " + std::to_string(f) +
+                                                ": a delay spread too large for the dedispersion kernel");
+                const bool w = ck > 256;
+                std::vector<DedispItem>& dst = w ? wide : narrow;
+                int64_t& ctas = w ? mb.ctas_wide : mb.ctas_narrow;
+                size_t& mshm = w ? mb.shm_wide : mb.shm_narrow;
+                it.first = ctas;
+                ctas += (int64_t)it.gx * it.gy;
+                mshm = std::max(mshm, shm);
+                dst.push_back(it);
+                const double T = (double)(st.nfft * (int64_t)st.ds) * P.tsamp;
+                for (size_t r = a; r < e; ++r) {
+                    nv_rows.push_back(st.nv);
+                    row_dm.push_back((int32_t)rows[r].trial);
+                    row_file.push_back(f);
+                    for (int k = 0; k < 8; ++k)
+                        row_hmin.push_back(k < M->nstages ? (int32_t)std::min<double>(
+                                                                ceil((double)(2 << k) * T * cfg->f_lo_hz), 2e9)
+                                                          : 0);
+                }
+                a = e;
+            }
+            mb.n_narrow = (int64_t)narrow.size();
+            mb.n_wide = (int64_t)wide.size();
+            mb.items_narrow = work_put(&M->work, narrow.data(), narrow.size());
+            mb.items_wide = work_put(&M->work, wide.data(), wide.size());
+            mb.nv_rows = work_put(&M->work, nv_rows.data(), nv_rows.size());
+            mb.row_dm = work_put(&M->work, row_dm.data(), row_dm.size());
+            mb.row_file = work_put(&M->work, row_file.data(), row_file.size());
+            mb.row_hmin = work_put(&M->work, row_hmin.data(), row_hmin.size());
+            M->batches.push_back(mb);
+        }
+    }
+    return PSS_OK;
+}
+
+// The kernel sequence of a group (no allocation, no host waits: capturable).
+pss_status multi_enqueue(pss_ctx* ctx, const pss_search_cfg* cfg, const MultiSetup& M, int64_t dev_cap,
+                         cudaStream_t s) {
+    const uint8_t* W = (const uint8_t*)ctx->mf_work.p;
+    PSS_CUDA(cudaMemsetAsync(ctx->counter.p, 0, sizeof(unsigned long long), s));
+    {
+        ProfScope ps(ctx, 0, s);
+        PSS_CUDA(launch_prep_multi((const PrepItem*)(W + M.prep_items), (int)M.ck.size(), M.prep_ctas, s));
+    }
+    for (const MultiBatch& b : M.batches) {
+        const int64_t nfft = b.nfft, Mh = nfft / 2;
+        PSS_CUDA(cudaMemsetAsync(ctx->sums.p, 0, (size_t)b.nrows * 8, s));
+        {
+            ProfScope ps(ctx, 1, s);
+            PSS_CUDA(launch_dedisp_multi((const DedispItem*)(W + b.items_narrow), (int)b.n_narrow, b.ctas_narrow,
+                                         b.shm_narrow, false, s));
+        }
+        if (b.n_wide) {
+            ProfScope ps(ctx, 1, s);
+            PSS_CUDA(launch_dedisp_multi((const DedispItem*)(W + b.items_wide), (int)b.n_wide, b.ctas_wide,
+                                         b.shm_wide, true, s));
+        }
+        FftArgs fa{};
+        fa.series = (const float*)ctx->series.p;
+        fa.series_stride = nfft;
+        fa.sums = (const unsigned long long*)ctx->sums.p;
+        fa.nv = 0;
+        fa.nv_rows = (const int64_t*)(W + b.nv_rows);
+        fa.nfft = nfft;
+        fa.nb = b.nrows;
+        fa.bufA = (float2*)ctx->fftA.p;
+        fa.bufB = (float2*)ctx->fftB.p;
+        fa.spec_out = (float2*)ctx->spec.p;
+        fa.spec_stride = Mh;
+        fa.whiten_block = cfg->whiten_block;
+        fa.tw = (const float2*)ctx->twid.p;
+        fa.twM = ctx->twid_n;
+        fa.fft_variant = ctx->tune.split_for(Mh);
+        fa.whiten_form = ctx->tune.whiten_form >= 0 ? ctx->tune.whiten_form : 2;
+        set_passtw(ctx, &fa);
+        fa.whiten = 1;
+        PSS_CUDA(launch_fft_whiten(fa, s, ctx));
+        PlaneArgs pl{};
+        pl.spec = (const float2*)ctx->spec.p;
+        pl.spec_stride = Mh;
+        pl.nfft = nfft;
+        pl.nb = b.nrows;
+        pl.plane = (float*)ctx->plane.p;
+        pl.plane_stride = (int64_t)M.nz * nfft;
+        pl.zmax = cfg->zmax;
+        pl.dz = cfg->zmax ? cfg->dz : 1.0;
+        pl.extra = cfg->halfwidth_extra;
+        pl.taps = (const float2*)ctx->taps.p;
+        const int32_t* info = (const int32_t*)ctx->tapinfo.p;
+        pl.tap_off = info;
+        pl.tap_m = info + 2 * M.nz;
+        pl.tap_scale = (const float*)(info + 3 * M.nz);
+        pl.ftaps = nullptr;
+        if (ctx->ftap_ok && plane_fft_usable(cfg->zmax, cfg->halfwidth_extra, Mh)) {
+            const int mmax = (cfg->zmax + 1) / 2 + cfg->halfwidth_extra;
+            pl.ftaps = (const float2*)ctx->ftaps.p;
+            pl.fL = PLANE_FFT_L;
+            pl.fM0 = mmax - 1;
+            pl.fV = PLANE_FFT_L - 2 * mmax + 1;
+            pl.tw = (const float2*)ctx->twid.p;
+            pl.twM = ctx->twid_n;
+            pl.nz = M.nz;
+            pl.form = ctx->tune.plane_form;
+            pl.zrow0 = -1;
+            for (int j = 0; j < M.nz; ++j)
+                if (-(double)cfg->zmax + (double)j * pl.dz == 0.0) pl.zrow0 = j;
+        }
+        {
+            ProfScope ps(ctx, 4, s);
+            PSS_CUDA(launch_plane(pl, s));
+        }
+        HarmArgs ha{};
+        for (int k = 0; k < 6; ++k) ha.thr[k] = M.thr[k];
+        ha.run = ctx->tune.harm_run;
+        ha.plane = (const float*)ctx->plane.p;
+        ha.plane_stride = (int64_t)M.nz * nfft;
+        ha.nfft = nfft;
+        ha.nz = M.nz;
+        ha.Z = M.Z;
+        ha.nb = b.nrows;
+        ha.dm0 = 0;
+        ha.nstages = M.nstages;
+        ha.out = (pss_raw_cand*)ctx->cands.p;
+        ha.counter = (unsigned long long*)ctx->counter.p;
+        ha.cap = dev_cap;
+        ha.row_dm = (const int32_t*)(W + b.row_dm);
+        ha.row_file = (const int32_t*)(W + b.row_file);
+        ha.row_hmin = (const int32_t*)(W + b.row_hmin);
+        {
+            ProfScope ps(ctx, 5, s);
+            PSS_CUDA(launch_harm(ha, s));
+        }
+    }
+    return PSS_OK;
+}
+
+// A group's search: upload, set-up, one captured graph, sift file by file.
+pss_status multi_search(pss_ctx* ctx, const pss_search_cfg* cfg, const pss_multi_file* files, int32_t nfiles,
+                        int on_dev, cudaStream_t s, std::vector<pss_cand>* out, std::vector<int64_t>* counts) {
+    if (nfiles < 1 || !files || !cfg) return fail(PSS_EINVAL, "pss_search_multi: no files");
+    for (int32_t f = 0; f < nfiles; ++f) {
+        if (!files[f].plan || !files[f].fil || !files[f].data)
+            return fail(PSS_EINVAL, "pss_search_multi: null plan, descriptor or data of file " + std::to_string(f));
+        if (files[f].plan->nsub > 0)
+            return fail(PSS_EINVAL, "pss_search_multi: two-stage (subband) plans are not supported");
+        PSS_TRY(validate_search(files[f].plan, files[f].fil, cfg));
+    }
+    if (!ctx->errflag.p) {
+        PSS_TRY(ctx->errflag.ensure(sizeof(int)));
+        PSS_CUDA(cudaMemsetAsync(ctx->errflag.p, 0, sizeof(int), s));
+    }
+    // sizing pass, then buffers, then the work lists with real addresses
+    MultiSetup M;
+    PSS_TRY(multi_setup(ctx->tune, (int*)ctx->errflag.p, ctx->wait_polls, cfg, files, nfiles, nullptr, nullptr,
+                        nullptr, nullptr, nullptr, &M));
+    PSS_TRY(ctx->mf_fil.ensure(M.fil_bytes));
+    PSS_TRY(ctx->mf_xcm.ensure(M.xcm_bytes));
+    PSS_TRY(ctx->mf_work.ensure(M.work.size() + 256));
+    PSS_TRY(ctx->series.ensure(M.need_series));
+    PSS_TRY(ctx->sums.ensure(M.need_sums));
+    PSS_TRY(ctx->fftA.ensure(M.need_fft));
+    PSS_TRY(ctx->fftB.ensure(M.need_fft));
+    PSS_TRY(ctx->spec.ensure(M.need_fft));
+    PSS_TRY(ctx->plane.ensure(M.need_plane));
+    PSS_TRY(multi_setup(ctx->tune, (int*)ctx->errflag.p, ctx->wait_polls, cfg, files, nfiles,
+                        (const uint8_t*)ctx->mf_fil.p,
+                        (const uint8_t*)ctx->mf_xcm.p, (const uint8_t*)ctx->mf_work.p, (float*)ctx->series.p,
+                        (unsigned long long*)ctx->sums.p, &M));
+    PSS_TRY(ensure_templates(ctx, cfg, s));
+    int64_t nfft_max = 0;
+    for (const MultiBatch& b : M.batches) nfft_max = std::max(nfft_max, b.nfft);
+    if (ctx->twid_n < nfft_max) {
+        PSS_TRY(ctx->twid.ensure((size_t)nfft_max * sizeof(float2)));
+        PSS_CUDA(launch_twiddles((float2*)ctx->twid.p, nfft_max, s));
+        ctx->twid_n = nfft_max;
+    }
+    for (const MultiBatch& b : M.batches) PSS_TRY(ensure_passtw(ctx, b.nfft / 2, ctx->tune.split_for(b.nfft / 2), s));
+    // inputs and work lists
+    for (int32_t f = 0; f < nfiles; ++f)
+        PSS_CUDA(cudaMemcpyAsync((uint8_t*)ctx->mf_fil.p + M.fil_off[f], files[f].data,
+                                 (size_t)file_bytes(files[f].fil),
+                                 on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    PSS_CUDA(cudaMemcpyAsync(ctx->mf_work.p, M.work.data(), M.work.size(), cudaMemcpyHostToDevice, s));
+    int64_t cap = std::max<int64_t>(kBatchInitialCap, (int64_t)(ctx->cands.bytes / sizeof(pss_raw_cand)));
+    std::vector<pss_raw_cand> raw;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        PSS_TRY(ctx->cands.ensure((size_t)cap * sizeof(pss_raw_cand)));
+        PSS_TRY(ctx->counter.ensure(sizeof(unsigned long long)));
+        // a group whose kernel variants this context has not run yet runs eagerly (the launchers set
+        // kernel attributes and the kernels load on first use); otherwise the sequence is captured into
+        // one graph and launched
+        bool warm = true;
+        for (const MultiBatch& b : M.batches) {
+            const int64_t key = b.nfft * 4 + (b.n_wide ? 2 : 0) + (b.n_narrow ? 1 : 0);
+            if (!ctx->mf_seen.count(key)) warm = false;
+        }
+        unsigned long long cnt = 0;
+        cudaError_t e = cudaSuccess;
+        if (!warm) {
+            PSS_TRY(multi_enqueue(ctx, cfg, M, cap, s));
+            for (const MultiBatch& b : M.batches) ctx->mf_seen.insert(b.nfft * 4 + (b.n_wide ? 2 : 0) + (b.n_narrow ? 1 : 0));
+        } else {
+            // captured on the context's own stream (the caller's may be the legacy default stream,
+            // which cannot capture), launched on the caller's stream after its uploads
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t ge = nullptr;
+            cudaStream_t cs = ctx->stream;
+            PSS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+            pss_status st = multi_enqueue(ctx, cfg, M, cap, cs);
+            e = cudaStreamEndCapture(cs, &g);
+            if (st != PSS_OK) {
+                if (g) cudaGraphDestroy(g);
+                return st;
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&ge, g, 0);
+            if (e == cudaSuccess) e = cudaGraphLaunch(ge, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (ge) cudaGraphExecDestroy(ge);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(e, "pss_search_multi graph");
+        }
+        PSS_CUDA(cudaMemcpyAsync(&cnt, ctx->counter.p, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+        PSS_CUDA(cudaStreamSynchronize(s));
+        ctx->mf_graphs += warm ? 1 : 0;
+        PSS_TRY(check_errflag(ctx, s));
+        if ((int64_t)cnt <= cap) {
+            raw.resize(cnt);
+            if (cnt)
+                PSS_CUDA(cudaMemcpyAsync(raw.data(), ctx->cands.p, cnt * sizeof(pss_raw_cand), cudaMemcpyDeviceToHost,
+                                         s));
+            PSS_CUDA(cudaStreamSynchronize(s));
+            break;
+        }
+        if (attempt == 1) return fail(PSS_ECAP, "pss_search_multi: candidate buffer overflow persisted");
+        cap = (int64_t)cnt + 1024;
+    }
+    // file by file: sort, sift
+    std::vector<std::vector<pss_raw_cand>> per(nfiles);
+    for (const pss_raw_cand& c : raw) {
+        if (c.reserved < 0 || c.reserved >= nfiles) return fail(PSS_EINVAL, "pss_search_multi: bad file tag");
+        pss_raw_cand d = c;
+        d.reserved = 0;
+        per[c.reserved].push_back(d);
+    }
+    out->clear();
+    counts->assign(nfiles, 0);
+    for (int32_t f = 0; f < nfiles; ++f) {
+        sort_raw(&per[f], files[f].plan->ndm());
+        std::vector<pss_cand> v;
+        PSS_TRY(sift(*files[f].plan, *cfg, per[f].data(), (int64_t)per[f].size(), &v));
+        (*counts)[f] = (int64_t)v.size();
+        out->insert(out->end(), v.begin(), v.end());
+    }
+    return PSS_OK;
+}
+
 }  // namespace
+
+// Device bytes a multi-file search of these files holds (host arithmetic):
+// each file's bytes, channel-major copy and delay tables, the work lists,
+// and the per-row buffers of the largest batch of each transform length.
+size_t multi_footprint(const std::vector<const Plan*>& plans, const std::vector<const pss_fil_desc*>& fils,
+                       const pss_search_cfg* cfg) {
+    const int nz = nz_of(cfg);
+    size_t t = 0, work = 0, series = 0, sums = 0, fft = 0, plane = 0;
+    std::map<int64_t, int64_t> rows;
+    int64_t nfft_max = 0;
+    for (size_t f = 0; f < plans.size(); ++f) {
+        const Plan& P = *plans[f];
+        int64_t ck = 0;
+        for (int c = 0; c < fils[f]->nchan; ++c) ck += (!fils[f]->chan_mask || fils[f]->chan_mask[c]) ? 1 : 0;
+        t += align256((size_t)file_bytes(fils[f])) + align256((size_t)ck * xcm_pitch(P, fils[f]) + 64);
+        work += align256((size_t)(ck + P.ndm() * ck) * 4) + 256;
+        for (const auto& st : P.stages)
+            if (st.n_dm > 0) rows[st.nfft] += st.n_dm;
+        // per trial at most one dedispersion item (a run of one trial) and the row arrays
+        work += (size_t)P.ndm() * (sizeof(DedispItem) + 8 + 4 + 4 + 32) + 4096;
+    }
+    for (const auto& kv : rows) {
+        const int64_t nfft = kv.first;
+        const int64_t B = batch_trials(nfft, nz, MODE_SEARCH, kv.second);
+        nfft_max = std::max(nfft_max, nfft);
+        series = std::max(series, (size_t)B * nfft * 4);
+        sums = std::max(sums, (size_t)B * 8);
+        fft = std::max(fft, (size_t)B * (nfft / 2) * 8);
+        plane = std::max(plane, (size_t)B * nz * nfft * 4);
+        t += align256((size_t)(nfft / 2) * sizeof(float2));  // inter-pass twiddles
+    }
+    t += align256(work) + align256(series) + align256(sums) + 3 * align256(fft) + align256(plane) +
+         align256((size_t)kBatchInitialCap * sizeof(pss_raw_cand)) + 256 + align256((size_t)nfft_max * sizeof(float2));
+    const int mmax = (cfg->zmax + 1) / 2 + cfg->halfwidth_extra;
+    t += align256((size_t)nz * 2 * (2 * mmax) * sizeof(float2)) + align256((size_t)5 * nz * sizeof(int32_t));
+    if (cfg->zmax > 0) t += align256((size_t)nz * 2 * PLANE_FFT_L * sizeof(float2));
+    return t;
+}
+
+size_t ctx_device_bytes(const pss_ctx* c);
+
 }  // namespace pss
 
 using namespace pss;
@@ -1210,7 +1675,7 @@ void pss_ctx_destroy(pss_ctx* c) {
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     DevBuf* bufs[] = {&c->fil_dev, &c->xcm, &c->delays_dev, &c->subu, &c->sp_series, &c->sp_mom, &c->sp_ev,
-                      &c->fold_buf, &c->bx, &c->series, &c->sums, &c->fftA, &c->fftB,
+                      &c->fold_buf, &c->bx, &c->mf_fil, &c->mf_xcm, &c->mf_work, &c->series, &c->sums, &c->fftA, &c->fftB,
                       &c->spec, &c->plane, &c->cands, &c->counter, &c->taps, &c->ftaps, &c->tapinfo, &c->errflag,
                       &c->twid, &c->chan_spec, &c->refine_gains, &c->refine_dtau, &c->refine_pts, &c->refine_out};
     for (DevBuf* b : bufs) b->release();
@@ -1226,6 +1691,22 @@ void pss_ctx_destroy(pss_ctx* c) {
     for (auto e : c->prof_pool) cudaEventDestroy(e);
     if (c->stream) cudaStreamDestroy(c->stream);
     delete c;
+}
+
+pss_status pss_ctx_set_wait_limit(pss_ctx* ctx, int32_t polls) {
+    if (!ctx || polls < 0) return fail(PSS_EINVAL, "pss_ctx_set_wait_limit: null ctx or negative polls");
+    ctx->wait_polls = polls;
+    return PSS_OK;
+}
+
+void pss_debug_fail_alloc(int64_t n) { g_alloc_countdown.store(n > 0 ? n : 0); }
+
+pss_status pss_ctx_check(pss_ctx* ctx, void* stream) {
+    if (!ctx) return fail(PSS_EINVAL, "pss_ctx_check: null ctx");
+    PSS_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = pick_stream(ctx, stream);
+    PSS_CUDA(cudaStreamSynchronize(s));
+    return check_errflag(ctx, s);
 }
 
 pss_status pss_ctx_profile(pss_ctx* ctx, int enable) {
@@ -1695,6 +2176,39 @@ pss_status pss_search_dm_batch(pss_ctx* ctx, const pss_plan* plan, const pss_fil
     return take_cands(ctx->last_cands, out, cap, n_out);
 }
 
+pss_status pss_search_multi(pss_ctx* ctx, const pss_search_cfg* cfg, const pss_multi_file* files, int32_t nfiles,
+                            int data_on_device, pss_cand* out, int64_t cap, int64_t* counts, int64_t* n_out,
+                            void* stream) {
+    if (!n_out || !counts) return fail(PSS_EINVAL, "pss_search_multi: null counts or n_out");
+    *n_out = 0;
+    if (!ctx) return fail(PSS_EINVAL, "null ctx");
+    PSS_CUDA(cudaSetDevice(ctx->device));
+    ctx->has_last = false;
+    PSS_TRY(multi_search(ctx, cfg, files, nfiles, data_on_device, pick_stream(ctx, stream), &ctx->last_cands,
+                         &ctx->last_counts));
+    ctx->has_last = true;
+    for (int32_t f = 0; f < nfiles; ++f) counts[f] = ctx->last_counts[f];
+    return take_cands(ctx->last_cands, out, cap, n_out);
+}
+
+pss_status pss_search_multi_footprint(const pss_search_cfg* cfg, const pss_multi_file* files, int32_t nfiles,
+                                      size_t* bytes) {
+    if (!bytes || !cfg || !files || nfiles < 1) return fail(PSS_EINVAL, "pss_search_multi_footprint: null argument");
+    *bytes = 0;
+    std::vector<const Plan*> plans;
+    std::vector<const pss_fil_desc*> fils;
+    for (int32_t f = 0; f < nfiles; ++f) {
+        if (!files[f].plan || !files[f].fil) return fail(PSS_EINVAL, "pss_search_multi_footprint: null plan or descriptor");
+        if (files[f].plan->nsub > 0)
+            return fail(PSS_EINVAL, "pss_search_multi_footprint: two-stage (subband) plans are not supported");
+        PSS_TRY(validate_search(files[f].plan, files[f].fil, cfg));
+        plans.push_back(files[f].plan);
+        fils.push_back(files[f].fil);
+    }
+    *bytes = multi_footprint(plans, fils, cfg);
+    return PSS_OK;
+}
+
 pss_status pss_ctx_take_cands(pss_ctx* ctx, pss_cand* out, int64_t cap, int64_t* n_out) {
     if (!ctx || !n_out) return fail(PSS_EINVAL, "pss_ctx_take_cands: null argument");
     *n_out = 0;
@@ -1963,7 +2477,7 @@ namespace {
 size_t ctx_bytes(const pss_ctx* c) {
     const DevBuf* bufs[] = {&c->fil_dev, &c->xcm, &c->delays_dev, &c->subu, &c->bx, &c->series, &c->sums, &c->fftA,
                             &c->fftB, &c->spec, &c->plane, &c->cands, &c->counter, &c->taps, &c->ftaps, &c->tapinfo,
-                            &c->errflag, &c->twid};
+                            &c->errflag, &c->twid, &c->mf_fil, &c->mf_xcm, &c->mf_work};
     size_t t = 0;
     for (const DevBuf* b : bufs) t += b->bytes;
     for (const auto& p : c->passtw) t += p.buf.bytes;
@@ -2394,3 +2908,7 @@ extern "C" void pss_batch_free(pss_batch* b) {
     }
     delete b;
 }
+
+namespace pss {
+size_t ctx_device_bytes(const pss_ctx* c) { return ctx_bytes(c); }
+}  // namespace pss

@@ -23,8 +23,23 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                  : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Wait for the phase of `parity` to complete: up to WAIT_LIMIT blocking polls
+// (try_wait), or, with test_polls > 0 (a context's short limit for tests),
+// that many non-blocking polls (test_wait); false when they run out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int test_polls = 0) {
     const uint32_t a = smem_u32(bar);
+    if (test_polls > 0) {
+        for (int i = 0; i < test_polls; ++i) {
+            uint32_t ok;
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                : "=r"(ok)
+                : "r"(a), "r"(parity)
+                : "memory");
+            if (ok) return true;
+        }
+        return false;
+    }
     for (int i = 0; i < WAIT_LIMIT; ++i) {
         uint32_t ok;
         asm volatile(

@@ -66,8 +66,10 @@ __host__ __device__ inline Layout layout_of(int RW, int CC, int ck) {
     return L;
 }
 
+// The tile (bx, by, bz) of a launch: time tile bx, trial group by, subband bz.
 template <bool INT_OUT, bool WIDE>
-__global__ void __launch_bounds__(NT) k_dedisp(DedispArgs a, int RW, int CC, uint32_t one) {
+__device__ __forceinline__ void dedisp_tile(const DedispArgs& a, int RW, int CC, uint32_t one, int bx, int by,
+                                            int bz) {
     extern __shared__ __align__(128) uint8_t smraw[];
     const int RAWB = 4 * RW + 16;
     const Layout Lo = layout_of(RW, CC, a.ck);
@@ -80,23 +82,23 @@ __global__ void __launch_bounds__(NT) k_dedisp(DedispArgs a, int RW, int CC, uin
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int64_t t0 = (int64_t)blockIdx.x * TN;
-    const int g0 = blockIdx.y * G;
+    const int64_t t0 = (int64_t)bx * TN;
+    const int g0 = by * G;
     const int gn = min(G, a.nb - g0);
     const int my = g0 + warp;
     const bool active = warp < gn;
-    // this CTA's channels: all ck, or subband blockIdx.z's (stage 1 of the two-stage scheme)
+    // this CTA's channels: all ck, or subband bz's (stage 1 of the two-stage scheme)
     const uint8_t* xcm = a.xcm;
     const int32_t* delays = a.delays;
     int ck = a.ck;
     int32_t* out_i = a.out_i;
     const int dstride = a.dstride > 0 ? a.dstride : a.ck;
     if (a.zsub) {
-        const int2 z = a.zsub[blockIdx.z];
+        const int2 z = a.zsub[bz];
         xcm += (int64_t)z.x * a.pitch;
         delays += z.x;
         ck = z.y;
-        out_i += (int64_t)blockIdx.z * a.zout;
+        out_i += (int64_t)bz * a.zout;
     }
     const int nchunks = (ck + CC - 1) / CC;
 
@@ -167,7 +169,7 @@ __global__ void __launch_bounds__(NT) k_dedisp(DedispArgs a, int RW, int CC, uin
         const int cn = min(CC, ck - cb);
         // one warp polls the mbarrier; the others wait at the block barrier (which
         // does not take issue slots), and the barrier passes the staged bytes on
-        const bool ok = warp == 0 ? mbar_wait(S.bar, (uint32_t)(c & 1)) : true;
+        const bool ok = warp == 0 ? mbar_wait(S.bar, (uint32_t)(c & 1), a.wait_polls) : true;
         if (__syncthreads_or(!ok)) {
             failed_at = c;
             break;
@@ -225,6 +227,7 @@ __global__ void __launch_bounds__(NT) k_dedisp(DedispArgs a, int RW, int CC, uin
     if (failed_at >= 0) {
         if (threadIdx.x == 0 && a.err) atomicExch(a.err, 1);
         // let the copies still in flight land before the CTA's shared memory is released
+        // (always the full bound, whatever limit the data wait had)
         mbar_wait(S.bar, (uint32_t)(failed_at & 1));
         return;
     }
@@ -295,6 +298,30 @@ __global__ void __launch_bounds__(NT) k_dedisp(DedispArgs a, int RW, int CC, uin
     }
 }
 
+template <bool INT_OUT, bool WIDE>
+__global__ void __launch_bounds__(NT) k_dedisp(DedispArgs a, int RW, int CC, uint32_t one) {
+    dedisp_tile<INT_OUT, WIDE>(a, RW, CC, one, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Work-list form: every (file, stage, trial run) of a group of files in one
+// launch.  CTA k takes the item whose CTA range [first, first + gx * gy)
+// holds k (binary search over the items, in order of `first`), and the tile
+// (k - first) of that item's grid, with the item's own staging sizes.
+template <bool WIDE>
+__global__ void __launch_bounds__(NT) k_dedisp_multi(const DedispItem* items, int nitems, uint32_t one) {
+    const int64_t k = blockIdx.x;
+    int lo = 0, hi = nitems - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (items[mid].first <= k) lo = mid;
+        else hi = mid - 1;
+    }
+    const DedispItem& it = items[lo];
+    const int64_t local = k - it.first;
+    const DedispArgs a = it.a;
+    dedisp_tile<false, WIDE>(a, it.RW, it.CC, one, (int)(local % it.gx), (int)(local / it.gx), 0);
+}
+
 template <bool I, bool W>
 cudaError_t launch_t(const DedispArgs& a, dim3 grid, size_t shm, int RW, int CC, cudaStream_t s) {
     cudaError_t e = allow_smem((const void*)k_dedisp<I, W>, shm);
@@ -336,6 +363,31 @@ bool dedisp_launch_fits(int32_t spread, int32_t ck, int chunk_kb) {
     int RW, CC;
     size_t shm;
     return dedisp_sizes(spread, ck, chunk_kb, &RW, &CC, &shm);
+}
+
+bool dedisp_item(DedispItem* it, int chunk_kb, size_t* shm) {
+    const DedispArgs& a = it->a;
+    int RW = 0, CC = 0;
+    if (a.zsub || a.out_i || !a.out_f) return false;  // the work-list form: exact sums into float rows
+    if (!dedisp_sizes(a.spread, a.ck, chunk_kb, &RW, &CC, shm)) return false;
+    it->RW = RW;
+    it->CC = CC;
+    const int64_t L = a.nv * a.ds;
+    it->gx = (int32_t)((L + TN - 1) / TN);
+    it->gy = (a.nb + G - 1) / G;
+    return it->gx > 0 && it->gy > 0;
+}
+
+cudaError_t launch_dedisp_multi(const DedispItem* items, int nitems, int64_t total_ctas, size_t shm, bool wide,
+                                cudaStream_t s) {
+    if (nitems <= 0 || total_ctas <= 0) return cudaSuccess;
+    if (total_ctas > 0x7fffffff || shm > 220 * 1024) return cudaErrorInvalidValue;
+    const void* fn = wide ? (const void*)k_dedisp_multi<true> : (const void*)k_dedisp_multi<false>;
+    cudaError_t e = allow_smem(fn, shm);
+    if (e != cudaSuccess) return e;
+    if (wide) k_dedisp_multi<true><<<(unsigned)total_ctas, NT, shm, s>>>(items, nitems, 1u);
+    else k_dedisp_multi<false><<<(unsigned)total_ctas, NT, shm, s>>>(items, nitems, 1u);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_dedisp(const DedispArgs& a, int num_sms, cudaStream_t s) {

@@ -127,6 +127,7 @@ struct PassArgs {
     int64_t series_stride;
     const unsigned long long* sums;
     int64_t nv;
+    const int64_t* nv_rows;    // first pass: per-row N_v (nullable: every row has nv)
     float2* out;
     int64_t out_stride;
     int64_t M;
@@ -135,6 +136,9 @@ struct PassArgs {
     int64_t twM;
     const float2* ptw;         // later passes: [R][Ns] inter-pass twiddles tw[r k twM / (Ns R)]
 };
+
+// N_v of batch row b (per-row lengths when the rows come from several files)
+__device__ __forceinline__ int64_t row_nv(const PassArgs& a, int b) { return a.nv_rows ? a.nv_rows[b] : a.nv; }
 
 template <int R>
 __global__ void __launch_bounds__(NT) k_fft_pass(const __grid_constant__ PassArgs a) {
@@ -151,7 +155,7 @@ __global__ void __launch_bounds__(NT) k_fft_pass(const __grid_constant__ PassArg
         // mean = sum / N_v in FP64 (once per CTA: FP64 is slow), split as integer + fraction
         __shared__ float s_mu[2];
         if (threadIdx.x == 0) {
-            const double mu = (double)a.sums[b] / (double)a.nv;
+            const double mu = (double)a.sums[b] / (double)row_nv(a, b);
             const double mi = rint(mu);
             s_mu[0] = (float)mi;
             s_mu[1] = (float)(mu - mi);
@@ -159,6 +163,7 @@ __global__ void __launch_bounds__(NT) k_fft_pass(const __grid_constant__ PassArg
         __syncthreads();
         const float mu_i = s_mu[0], mu_f = s_mu[1];
         const float* s = a.series + (int64_t)b * a.series_stride;
+        const int64_t nv = row_nv(a, b);
 #pragma unroll
         for (int e = threadIdx.x; e < R * TJ; e += NT) {
             const int jj = e % TJ, r = e / TJ;
@@ -166,10 +171,10 @@ __global__ void __launch_bounds__(NT) k_fft_pass(const __grid_constant__ PassArg
             float2 x = make_float2(0.f, 0.f);
             if (j < ncol) {
                 const int64_t n = j + (int64_t)r * ncol;
-                if (2 * n + 1 < a.nv) {
+                if (2 * n + 1 < nv) {
                     const float2 v = *reinterpret_cast<const float2*>(s + 2 * n);
                     x = make_float2((v.x - mu_i) - mu_f, (v.y - mu_i) - mu_f);
-                } else if (2 * n < a.nv) {
+                } else if (2 * n < nv) {
                     x.x = (s[2 * n] - mu_i) - mu_f;
                 }
             }
@@ -227,6 +232,7 @@ template <int R>
 __device__ __forceinline__ void issue_tile(const PassArgs& a, int b, int64_t j0, float2* buf) {
     const int64_t ncol = a.M / R;
     if (a.series != nullptr) {
+        const int64_t nv = row_nv(a, b);
         const float* s = a.series + (int64_t)b * a.series_stride;
 #pragma unroll
         for (int i = 0; i < R * TJ / NT; ++i) {
@@ -235,7 +241,7 @@ __device__ __forceinline__ void issue_tile(const PassArgs& a, int b, int64_t j0,
             const int64_t j = j0 + jj;
             const int64_t n = j + (int64_t)r * ncol;
             // both samples, the first only (the odd tail), or none (zeros)
-            const uint32_t nbytes = (j < ncol && 2 * n + 1 < a.nv) ? 8u : ((j < ncol && 2 * n < a.nv) ? 4u : 0u);
+            const uint32_t nbytes = (j < ncol && 2 * n + 1 < nv) ? 8u : ((j < ncol && 2 * n < nv) ? 4u : 0u);
             cp_async8(buf + r * TJP + jj, nbytes ? (const void*)(s + 2 * n) : (const void*)s, nbytes);
         }
     } else {
@@ -284,11 +290,12 @@ __global__ void __launch_bounds__(NT, db_min_blocks<R>()) k_fft_pass_db(const __
     cp_async_commit();
     load_subtables<R>(twt, a.tw, a.twM);
     float mu_i = 0.f, mu_f = 0.f;
+    const int64_t nv_b = first ? row_nv(a, b) : 0;
     if (first) {
         // mean = sum / N_v in FP64 (once per CTA: FP64 is slow), split as integer + fraction
         __shared__ float s_mu[2];
         if (threadIdx.x == 0) {
-            const double mu = (double)a.sums[b] / (double)a.nv;
+            const double mu = (double)a.sums[b] / (double)row_nv(a, b);
             const double mi = rint(mu);
             s_mu[0] = (float)mi;
             s_mu[1] = (float)(mu - mi);
@@ -322,8 +329,8 @@ __global__ void __launch_bounds__(NT, db_min_blocks<R>()) k_fft_pass_db(const __
                 const int64_t n = j + (int64_t)r * ncol;
                 float2 v = make_float2(0.f, 0.f);
                 if (j < ncol) {
-                    if (2 * n + 1 < a.nv) v = make_float2((x.x - mu_i) - mu_f, (x.y - mu_i) - mu_f);
-                    else if (2 * n < a.nv) v.x = (x.x - mu_i) - mu_f;
+                    if (2 * n + 1 < nv_b) v = make_float2((x.x - mu_i) - mu_f, (x.y - mu_i) - mu_f);
+                    else if (2 * n < nv_b) v.x = (x.x - mu_i) - mu_f;
                 }
                 x = v;
             } else {
@@ -733,6 +740,7 @@ cudaError_t launch_fft_whiten(const FftArgs& a, cudaStream_t s, Ctx* prof_ctx) {
     PassArgs p{};
     p.M = M;
     p.nv = a.nv;
+    p.nv_rows = a.nv_rows;
     p.sums = a.sums;
     p.tw = a.tw;
     p.twM = a.twM;

@@ -121,12 +121,12 @@ __device__ __forceinline__ void harm_stage(const HarmArgs& a, const Tile& t, flo
                 const unsigned long long slot = slot0 + __popc(m & ((1u << t.lane) - 1u));
                 if ((int64_t)slot < a.cap) {
                     pss_raw_cand c;
-                    c.dm_idx = a.dm0 + t.b;
+                    c.dm_idx = a.row_dm ? a.row_dm[t.b] : a.dm0 + t.b;
                     c.numharm = n;
                     c.h = h;
                     c.j = j;
                     c.power = s;
-                    c.reserved = 0;
+                    c.reserved = a.row_file ? a.row_file[t.b] : 0;
                     a.out[slot] = c;
                 }
             }
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(NT) k_harm(const __grid_constant__ HarmArgs a)
     for (int q = 0; q < 6; ++q)
         if (threadIdx.x == q) {  // constant indices keep the parameter block out of local memory
             s_thr[q] = a.thr[q];
-            s_hmin[q] = a.hmin[q];
+            s_hmin[q] = a.row_hmin ? a.row_hmin[8 * blockIdx.z + q] : a.hmin[q];
         }
     Tile t;
     t.b = blockIdx.z;
@@ -227,7 +227,7 @@ __device__ __forceinline__ void reg_test(const HarmArgs& a, const float* P, cons
 #pragma unroll
     for (int i = 1; i < R; ++i) mx = fmaxf(mx, acc[i]);
     if (!__any_sync(0xffffffffu, mx >= thr)) return;
-    const int nfft = (int)a.nfft, hmin = a.hmin[SI], nz = a.nz, Z = a.Z;
+    const int nfft = (int)a.nfft, hmin = a.row_hmin ? a.row_hmin[8 * b + SI] : a.hmin[SI], nz = a.nz, Z = a.Z;
 #pragma unroll
     for (int i = 0; i < R; ++i) {
         float left = __shfl_up_sync(0xffffffffu, acc[i], 1);
@@ -253,12 +253,12 @@ __device__ __forceinline__ void reg_test(const HarmArgs& a, const float* P, cons
                 const unsigned long long slot = atomicAdd(a.counter, 1ull);
                 if ((int64_t)slot < a.cap) {
                     pss_raw_cand c;
-                    c.dm_idx = a.dm0 + b;
+                    c.dm_idx = a.row_dm ? a.row_dm[b] : a.dm0 + b;
                     c.numharm = 1 << SI;
                     c.h = h;
                     c.j = j;
                     c.power = s;
-                    c.reserved = 0;
+                    c.reserved = a.row_file ? a.row_file[b] : 0;
                     a.out[slot] = c;
                 }
             }

@@ -73,11 +73,11 @@ __global__ void __launch_bounds__(NT, 2) k_subsum(const __grid_constant__ Subsum
                              &s_bar);
                 }
             }
-            const bool ok = warp == 0 ? mbar_wait(&s_bar, phase) : true;
+            const bool ok = warp == 0 ? mbar_wait(&s_bar, phase, a.wait_polls) : true;
             phase ^= 1u;
             if (__syncthreads_or(!ok)) {
                 if (threadIdx.x == 0 && a.err) atomicExch(a.err, 1);
-                mbar_wait(&s_bar, phase ^ 1u);  // let the copies in flight land before leaving
+                mbar_wait(&s_bar, phase ^ 1u);  // let the copies in flight land before leaving (full bound)
                 return;
             }
             if (active) {

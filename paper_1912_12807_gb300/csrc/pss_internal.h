@@ -10,6 +10,7 @@
 #include <memory>
 #include <string>
 #include <thread>
+#include <set>
 #include <vector>
 
 #include "../../include/pss.h"
@@ -213,6 +214,14 @@ struct Ctx {
     // sifted candidates of the last whole-file search (pss_ctx_take_cands)
     std::vector<pss_cand> last_cands;
     bool has_last = false;
+    // multi-file search (pss_search_multi): the group's file bytes, channel-major
+    // copies, tables and work lists, and the candidate count of each file of
+    // the last group (its lists are in last_cands, file after file)
+    DevBuf mf_fil, mf_xcm, mf_work;
+    std::vector<int64_t> last_counts;
+    std::set<int64_t> mf_seen;   // (transform length, dedispersion variants) the context has run eagerly
+    int32_t wait_polls = 0;      // pss_ctx_set_wait_limit: short staging-barrier waits (tests)
+    int64_t mf_graphs = 0;       // groups run as a captured graph
     // per-stage event timing (pss_ctx_profile)
     bool prof_on = false;
     struct ProfRec {
@@ -244,6 +253,16 @@ struct PrepArgs {
     int64_t pitch;        // bytes per channel-major row (multiple of 64)
 };
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
+// Work-list unpack of several files in one launch: item i covers CTAs
+// [first, first + CTAs of its grid); items in increasing `first`.
+struct PrepItem {
+    PrepArgs a;
+    int32_t gx;      // tiles along time (the grid's x extent)
+    int32_t pad;
+    int64_t first;   // first CTA of the item
+};
+int64_t prep_item_ctas(const PrepArgs& a, int32_t* gx);  // CTAs of one item (sets gx)
+cudaError_t launch_prep_multi(const PrepItem* items, int nitems, int64_t total_ctas, cudaStream_t s);
 
 // Let kernel `fn` launch with as much dynamic shared memory as the device
 // allows next to its static shared memory (error if `shm` exceeds that).
@@ -277,6 +296,7 @@ struct DedispArgs {
     int32_t spread;         // max over groups/channels of (dmax - dmin)
     int* err;               // set to 1 if a bounded wait expires (nullable)
     int32_t chunk_kb;       // shared memory for staged channel chunks (0: default)
+    int32_t wait_polls;     // > 0: the data waits give up after this many non-blocking polls (tests)
     // two-stage scheme, stage 1: blockIdx.z = subband z sums its own kept
     // channels zsub[z] = (first, count) (ck is then the largest count and
     // sizes the launch), its delays start at delays + first with rows of
@@ -294,6 +314,22 @@ cudaError_t launch_dedisp(const DedispArgs& a, int num_sms, cudaStream_t s);
 // count (the host-side checks it makes before launching), so that callers
 // can refuse a request before enqueuing any work.
 bool dedisp_launch_fits(int32_t spread, int32_t ck, int chunk_kb);
+// Work-list dedispersion of several files' trial runs in one launch (exact
+// sums into float rows with per-trial sums; one subband): item i covers CTAs
+// [first, first + gx * gy); items in increasing `first`.
+struct DedispItem {
+    DedispArgs a;
+    int32_t RW, CC;   // staged row words and channels per chunk (dedisp_item)
+    int32_t gx, gy;   // time tiles, groups of trials
+    int64_t first;    // first CTA of the item
+};
+// Fill an item's launch sizes from its arguments (false: the kernel refuses
+// them); *shm: the item's dynamic shared memory.
+bool dedisp_item(DedispItem* it, int chunk_kb, size_t* shm);
+// One launch over items (all with ck <= 256, or all > 256: `wide`); shm the
+// largest item's.
+cudaError_t launch_dedisp_multi(const DedispItem* items, int nitems, int64_t total_ctas, size_t shm, bool wide,
+                                cudaStream_t s);
 
 // Two-stage scheme, stage 2: s_i[t] = sum_b u_{g(i),b}[t + D_b(i)], then the
 // ds boxcar, for the nb trials of a batch (k_subband.cu).
@@ -316,6 +352,7 @@ struct SubsumArgs {
     unsigned long long* sums;  // [nb] or null
     int32_t spread;         // max over group rows and subbands of (D max - D min)
     int* err;               // set to 1 if a bounded wait expires (nullable)
+    int32_t wait_polls;     // > 0: the data waits give up after this many non-blocking polls (tests)
 };
 cudaError_t launch_subsum(const SubsumArgs& a, cudaStream_t s);
 
@@ -429,6 +466,7 @@ struct FftArgs {
     int64_t series_stride;
     const unsigned long long* sums;   // [nb]
     int64_t nv;
+    const int64_t* nv_rows;           // nullable: per-row N_v (rows from several files)
     int64_t nfft;
     int32_t nb;
     float2* bufA;
@@ -541,6 +579,11 @@ struct HarmArgs {
     unsigned long long* counter;
     int64_t cap;
     int32_t run;        // points per lane of the register-blocked kernel (16 or 8; 0: 16)
+    // rows from several files (all nullable): the detection's DM index and file
+    // index of each batch row, and each row's per-stage smallest half-bin [nb][8]
+    const int32_t* row_dm;
+    const int32_t* row_file;
+    const int32_t* row_hmin;
 };
 cudaError_t launch_harm(const HarmArgs& a, cudaStream_t s);
 
@@ -582,4 +625,10 @@ pss_status validate_search(const pss_plan* plan, const pss_fil_desc* fil, const 
 // Device bytes a pss_batch for this shape holds with room for dev_cap raw
 // detections; host arithmetic only.
 size_t search_footprint(const Plan& plan, const pss_fil_desc* fil, const pss_search_cfg* cfg, int64_t dev_cap);
+// Device bytes a multi-file search of these files holds (pss_search_multi);
+// host arithmetic only.
+size_t multi_footprint(const std::vector<const Plan*>& plans, const std::vector<const pss_fil_desc*>& fils,
+                       const pss_search_cfg* cfg);
+// Device bytes a context holds now.
+size_t ctx_device_bytes(const pss_ctx* c);
 }  // namespace pss

@@ -166,6 +166,12 @@ struct pss_server {
     uint64_t clock = 0;
     std::vector<std::thread> workers;
     std::vector<double> latencies;
+    // grouped mode (max_group > 1): each slot searches up to max_group queued
+    // files at once through pss_search_multi on a context of its own; held[i]
+    // is what slot i's context holds on the device
+    int max_group = 1;
+    std::vector<size_t> held;
+    int64_t groups_run = 0, files_grouped = 0;
 
     void finish(Request* r, pss_result* res) {
         res->latency_s = std::chrono::duration<double>(Clock::now() - r->t_submit).count();
@@ -230,6 +236,154 @@ struct pss_server {
             cv_work.wait(lk);
         }
         return nullptr;
+    }
+
+    // Whether r can join a group led by h: an exact plan and the same search parameters.
+    static bool groupable(const Request* h, const Request* r) {
+        const pss_search_cfg &a = h->cfg, &b = r->cfg;
+        return r->plan->nsub == 0 && h->plan->nsub == 0 && a.zmax == b.zmax && a.numharm == b.numharm &&
+               a.dz == b.dz && a.sigma_thr == b.sigma_thr && a.f_lo_hz == b.f_lo_hz &&
+               a.whiten_block == b.whiten_block && a.halfwidth_extra == b.halfwidth_extra &&
+               a.min_dm_hits == b.min_dm_hits;
+    }
+    static size_t group_bytes(const std::vector<Request*>& g) {
+        std::vector<const Plan*> plans;
+        std::vector<const pss_fil_desc*> fils;
+        for (const Request* r : g) {
+            plans.push_back(r->plan);
+            fils.push_back(&r->fil);
+        }
+        return multi_footprint(plans, fils, &g[0]->cfg);
+    }
+
+    // Grouped admission (under `mu`): the head of the queue and the files
+    // queued right behind it that can join it, up to max_group, while the
+    // group's footprint beyond what this slot's context already holds fits in
+    // what is left of the budget.  A file that cannot be grouped (a two-stage
+    // plan) runs alone.  A file whose own footprint exceeds the budget fails
+    // with PSS_ENOMEM.
+    bool admit_group(std::unique_lock<std::mutex>& lk, int wi, std::vector<Request*>* grp, size_t* reserved) {
+        while (!stop) {
+            if (queue.empty()) {
+                cv_work.wait(lk);
+                continue;
+            }
+            Request* h = queue.front();
+            if (h->estimate > budget) {
+                queue.pop_front();
+                lk.unlock();
+                pss_result* res = new pss_result();
+                res->status = PSS_ENOMEM;
+                res->err = "file needs more device memory than the server budget";
+                finish(h, res);
+                delete h;
+                lk.lock();
+                continue;
+            }
+            grp->assign(1, h);
+            size_t fp = h->plan->nsub == 0 ? group_bytes(*grp) : h->estimate;
+            if (h->plan->nsub == 0) {
+                for (size_t i = 1; i < queue.size() && (int)grp->size() < max_group; ++i) {
+                    Request* r = queue[i];
+                    if (!groupable(h, r)) break;  // arrival order is kept
+                    grp->push_back(r);
+                    const size_t f2 = group_bytes(*grp);
+                    const size_t need2 = f2 > held[wi] ? f2 - held[wi] : 0;
+                    if (in_use + need2 > budget) {
+                        grp->pop_back();
+                        break;
+                    }
+                    fp = f2;
+                }
+            }
+            const size_t need = fp > held[wi] ? fp - held[wi] : 0;
+            if (in_use + need <= budget) {
+                for (size_t i = 0; i < grp->size(); ++i) queue.pop_front();
+                in_use += need;
+                *reserved = need;
+                return true;
+            }
+            cv_work.wait(lk);
+        }
+        return false;
+    }
+
+    void worker_grouped(int wi) {
+        cudaSetDevice(device);
+        pss_ctx* ctx = nullptr;
+        const pss_status cst = pss_ctx_create(device, &ctx);
+        const std::string cerr = cst == PSS_OK ? "" : pss_last_error();
+        std::unique_lock<std::mutex> lk(mu);
+        for (;;) {
+            std::vector<Request*> grp;
+            size_t reserved = 0;
+            if (!admit_group(lk, wi, &grp, &reserved)) break;  // stopping
+            lk.unlock();
+            std::vector<pss_result*> res(grp.size());
+            for (auto& r : res) r = new pss_result();
+            try {
+                pss_status st = cst;
+                std::string err = cerr;
+                std::vector<pss_cand> out;
+                std::vector<int64_t> counts(grp.size(), 0);
+                if (st == PSS_OK && grp[0]->plan->nsub > 0) {
+                    // a two-stage plan runs alone through the single-file path
+                    int64_t n = 0;
+                    out.resize(1024);
+                    st = pss_search_dm_batch(ctx, grp[0]->plan, &grp[0]->fil, grp[0]->bytes(), 0, &grp[0]->cfg, 0,
+                                             grp[0]->plan->ndm(), out.data(), (int64_t)out.size(), &n, nullptr);
+                    if (st == PSS_ECAP) {
+                        out.resize((size_t)n);
+                        st = pss_ctx_take_cands(ctx, out.data(), n, &n);
+                    }
+                    out.resize(st == PSS_OK ? (size_t)n : 0);
+                    counts[0] = (int64_t)out.size();
+                } else if (st == PSS_OK) {
+                    std::vector<pss_multi_file> mf(grp.size());
+                    for (size_t i = 0; i < grp.size(); ++i) mf[i] = {grp[i]->plan, &grp[i]->fil, grp[i]->bytes()};
+                    int64_t n = 0;
+                    out.resize(4096);
+                    st = pss_search_multi(ctx, &grp[0]->cfg, mf.data(), (int32_t)grp.size(), 0, out.data(),
+                                          (int64_t)out.size(), counts.data(), &n, nullptr);
+                    if (st == PSS_ECAP) {
+                        out.resize((size_t)n);
+                        st = pss_ctx_take_cands(ctx, out.data(), n, &n);
+                    }
+                    out.resize(st == PSS_OK ? (size_t)n : 0);
+                }
+                if (st != PSS_OK && err.empty()) err = pss_last_error();
+                size_t off = 0;
+                for (size_t i = 0; i < grp.size(); ++i) {
+                    res[i]->status = st;
+                    res[i]->err = err;
+                    if (st == PSS_OK) {
+                        res[i]->cands.assign(out.begin() + (long)off, out.begin() + (long)(off + counts[i]));
+                        off += (size_t)counts[i];
+                    }
+                }
+            } catch (const std::bad_alloc&) {
+                for (auto& r : res) {
+                    r->status = PSS_ENOMEM;
+                    r->err = "host allocation failed";
+                }
+            }
+            {
+                const size_t now = ctx ? ctx_device_bytes(ctx) : 0;
+                std::lock_guard<std::mutex> g(mu);
+                in_use = in_use - reserved - held[wi] + now;
+                held[wi] = now;
+                ++groups_run;
+                files_grouped += (int64_t)grp.size();
+            }
+            for (size_t i = 0; i < grp.size(); ++i) {
+                grp[i]->release_data();
+                finish(grp[i], res[i]);
+                delete grp[i];
+            }
+            lk.lock();
+        }
+        lk.unlock();
+        if (ctx) pss_ctx_destroy(ctx);
     }
 
     void worker(int) {
@@ -298,8 +452,9 @@ struct pss_server {
     }
 };
 
-extern "C" pss_status pss_server_create(int device, size_t hbm_budget_bytes, int max_slots, pss_server** out) {
-    if (!out || max_slots < 1 || max_slots > 64 || hbm_budget_bytes == 0)
+extern "C" pss_status pss_server_create_grouped(int device, size_t hbm_budget_bytes, int max_slots, int max_group,
+                                               pss_server** out) {
+    if (!out || max_slots < 1 || max_slots > 64 || hbm_budget_bytes == 0 || max_group < 1 || max_group > 1024)
         return fail(PSS_EINVAL, "pss_server_create: bad arguments");
     *out = nullptr;
     int n = 0;
@@ -308,9 +463,18 @@ extern "C" pss_status pss_server_create(int device, size_t hbm_budget_bytes, int
     pss_server* s = new pss_server();
     s->device = device;
     s->budget = hbm_budget_bytes;
-    for (int i = 0; i < max_slots; ++i) s->workers.emplace_back([s, i] { s->worker(i); });
+    s->max_group = max_group;
+    s->held.assign((size_t)max_slots, 0);
+    for (int i = 0; i < max_slots; ++i) {
+        if (max_group > 1) s->workers.emplace_back([s, i] { s->worker_grouped(i); });
+        else s->workers.emplace_back([s, i] { s->worker(i); });
+    }
     *out = s;
     return PSS_OK;
+}
+
+extern "C" pss_status pss_server_create(int device, size_t hbm_budget_bytes, int max_slots, pss_server** out) {
+    return pss_server_create_grouped(device, hbm_budget_bytes, max_slots, 1, out);
 }
 
 // nsub == 0: an exact plan; otherwise a two-stage plan (pss_dd_plan_subband)
@@ -423,6 +587,14 @@ extern "C" pss_status pss_server_stats(pss_server* srv, int64_t* completed, doub
     if (p50_s) *p50_s = pct(50.0);
     if (p99_s) *p99_s = pct(99.0);
     if (bytes_in_use) *bytes_in_use = srv->in_use;
+    return PSS_OK;
+}
+
+extern "C" pss_status pss_server_group_stats(pss_server* srv, int64_t* groups, int64_t* files) {
+    if (!srv) return fail(PSS_EINVAL, "pss_server_group_stats: null server");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (groups) *groups = srv->groups_run;
+    if (files) *files = srv->files_grouped;
     return PSS_OK;
 }
 

@@ -70,7 +70,9 @@ EXPORTS = ["pss_ctx_create", "pss_ctx_destroy", "pss_last_error", "pss_version",
            "pss_refine_prepare", "pss_refine_eval", "pss_refine_candidates", "pss_batch_create", "pss_batch_run",
            "pss_batch_footprint", "pss_batch_free", "pss_search_footprint", "pss_ctx_take_cands",
            "pss_batch_take_cands", "pss_batch_tuning", "pss_batch_fft_split", "pss_fft_split_radices",
-           "pss_ctx_set_fft_split", "pss_measure_peaks", "pss_server_create", "pss_submit_file",
+           "pss_ctx_set_fft_split", "pss_measure_peaks", "pss_ctx_set_wait_limit", "pss_debug_fail_alloc",
+           "pss_ctx_check", "pss_search_multi", "pss_search_multi_footprint",
+           "pss_server_create", "pss_server_create_grouped", "pss_server_group_stats", "pss_submit_file",
            "pss_submit_file_subband", "pss_poll",
            "pss_result_cands", "pss_result_free", "pss_server_stats", "pss_server_destroy"]
 PROFILE_STAGES = ["unpack", "dedisperse", "fft", "whiten", "plane", "harmsum", "bxtable"]
@@ -130,8 +132,15 @@ def lib():
         "pss_fft_split_radices": (st, [i64, i32, P(i32), P(i32)]),
         "pss_ctx_set_fft_split": (st, [vp, i64, i32]),
         "pss_measure_peaks": (st, [C.c_int, vp]),
+        "pss_ctx_set_wait_limit": (st, [vp, i32]),
+        "pss_ctx_check": (st, [vp, vp]),
+        "pss_debug_fail_alloc": (None, [i64]),
+        "pss_search_multi": (st, [vp, P(pss_search_cfg), vp, i32, C.c_int, vp, i64, vp, P(i64), vp]),
+        "pss_search_multi_footprint": (st, [P(pss_search_cfg), vp, i32, P(C.c_size_t)]),
         "pss_search_footprint": (st, [vp, P(pss_fil_desc), P(pss_search_cfg), P(C.c_size_t)]),
         "pss_server_create": (st, [C.c_int, C.c_size_t, C.c_int, P(vp)]),
+        "pss_server_create_grouped": (st, [C.c_int, C.c_size_t, C.c_int, C.c_int, P(vp)]),
+        "pss_server_group_stats": (st, [vp, P(i64), P(i64)]),
         "pss_submit_file": (st, [vp, P(pss_fil_desc), vp, P(pss_dd_stage), C.c_int, P(pss_search_cfg),
                                  P(C.c_uint64)]),
         "pss_submit_file_subband": (st, [vp, P(pss_fil_desc), vp, P(pss_dd_stage), C.c_int, i32, i32,
@@ -467,6 +476,62 @@ def pss_search_dm_batch(ctx: Context, plan: Plan, data, cfg: pss_search_cfg, dm_
     return out[: n.value]
 
 
+class pss_multi_file(C.Structure):
+    _fields_ = [("plan", C.c_void_p), ("fil", C.POINTER(pss_fil_desc)), ("data", C.c_void_p)]
+
+
+def _multi_files(files):
+    """ctypes array of pss_multi_file for [(Plan, data)], the data all on the
+    host or all on the device, and the objects to keep alive meanwhile."""
+    arr = (pss_multi_file * len(files))()
+    keep, on_dev = [], None
+    for k, (plan, data) in enumerate(files):
+        p, dev, kp = _data_arg(data)
+        if on_dev is None:
+            on_dev = dev
+        elif on_dev != dev:
+            raise ValueError("pss_search_multi: every file on the host, or every file on the device")
+        keep.append(kp)
+        arr[k].plan = plan.h
+        arr[k].fil = C.pointer(plan.desc.c)
+        arr[k].data = p.value
+    return arr, int(bool(on_dev)), keep
+
+
+def pss_search_multi(ctx: Context, cfg: pss_search_cfg, files, cap: int = 1 << 14, stream=None):
+    """Sifted candidates (CAND_DTYPE) of each of a group of files
+    [(Plan, data)] searched together (pss_search_multi): a list, one array
+    per file."""
+    arr, on_dev, keep = _multi_files(files)
+    if on_dev:
+        import torch
+        torch.cuda.current_stream().synchronize()
+    counts = np.zeros(len(files), dtype=np.int64)
+    n = C.c_int64()
+    out = np.zeros(cap, dtype=CAND_DTYPE)
+    st = lib().pss_search_multi(ctx.h, C.byref(cfg), arr, len(files), on_dev, out.ctypes.data, cap,
+                                counts.ctypes.data, C.byref(n), _stream(stream))
+    if st == PSS_ECAP:  # the context kept the lists: fetch them without searching again
+        out = np.zeros(n.value, dtype=CAND_DTYPE)
+        st = lib().pss_ctx_take_cands(ctx.h, out.ctypes.data, n.value, C.byref(n))
+    _check(st)
+    res, off = [], 0
+    for c in counts:
+        res.append(out[off:off + int(c)])
+        off += int(c)
+    return res
+
+
+def pss_search_multi_footprint(cfg: pss_search_cfg, files) -> int:
+    arr = (pss_multi_file * len(files))()
+    for k, (plan, _) in enumerate(files):
+        arr[k].plan = plan.h
+        arr[k].fil = C.pointer(plan.desc.c)
+    b = C.c_size_t()
+    _check(lib().pss_search_multi_footprint(C.byref(cfg), arr, len(files), C.byref(b)))
+    return int(b.value)
+
+
 class Batch:
     """A search prepared for files of one shape and captured into a CUDA
     graph (pss_batch_*); run() searches one file per call."""
@@ -563,6 +628,18 @@ def pss_measure_peaks(device: int = 0) -> dict:
     return out
 
 
+def pss_ctx_set_wait_limit(ctx: Context, polls: int):
+    _check(lib().pss_ctx_set_wait_limit(ctx.h, int(polls)))
+
+
+def pss_ctx_check(ctx: Context, stream=None):
+    _check(lib().pss_ctx_check(ctx.h, _stream(stream)))
+
+
+def pss_debug_fail_alloc(n: int):
+    lib().pss_debug_fail_alloc(int(n))
+
+
 def pss_ctx_set_fft_split(ctx: Context, nfft: int, split: int):
     _check(lib().pss_ctx_set_fft_split(ctx.h, int(nfft), int(split)))
 
@@ -586,9 +663,12 @@ class Server:
     """Request loop over files (pss_server_*): submit() queues a file and
     returns a ticket; poll() hands over its candidates once."""
 
-    def __init__(self, hbm_budget_bytes: int, max_slots: int = 2, device: int = 0):
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 2, device: int = 0, max_group: int = 1):
+        """max_group > 1: pss_server_create_grouped (queued files searched in
+        groups through pss_search_multi)."""
         h = C.c_void_p()
-        _check(lib().pss_server_create(int(device), C.c_size_t(int(hbm_budget_bytes)), int(max_slots), C.byref(h)))
+        _check(lib().pss_server_create_grouped(int(device), C.c_size_t(int(hbm_budget_bytes)), int(max_slots),
+                                               int(max_group), C.byref(h)))
         self.h = h
 
     def submit(self, desc: FilDesc, data, stages, cfg: pss_search_cfg, subband=None) -> int:
@@ -624,7 +704,10 @@ class Server:
     def stats(self):
         done, p50, p99, used = C.c_int64(), C.c_double(), C.c_double(), C.c_size_t()
         _check(lib().pss_server_stats(self.h, C.byref(done), C.byref(p50), C.byref(p99), C.byref(used)))
-        return dict(completed=done.value, p50_s=p50.value, p99_s=p99.value, bytes_in_use=int(used.value))
+        g, f = C.c_int64(), C.c_int64()
+        _check(lib().pss_server_group_stats(self.h, C.byref(g), C.byref(f)))
+        return dict(completed=done.value, p50_s=p50.value, p99_s=p99.value, bytes_in_use=int(used.value),
+                    groups=g.value, grouped_files=f.value)
 
     def close(self):
         if self.h:
