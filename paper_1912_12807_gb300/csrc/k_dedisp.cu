@@ -118,11 +118,14 @@ __device__ __forceinline__ void dedisp_tile(const DedispArgs& a, int RW, int CC,
         for (int g = 1; g < gn; ++g) dmin = min(dmin, dcol[(int64_t)g * dstride]);
         const int64_t st = (t0 + dmin) & ~int64_t(15);
         S.rs[c] = (int32_t)(st - t0);
+        // the channel's place in its chunk: its four copies start at word (c mod CC) * 4 RW
+        const int base = (c - (c / CC) * CC) * 4 * RW;
         for (int g = 0; g < gn; ++g) {
             const int64_t o = t0 + dcol[(int64_t)g * dstride] - st;
             bad |= (o >= omax);
-            // word index into the channel's four copies: copy (o & 3), word (o >> 2)
-            S.offs[g * ck + c] = (uint16_t)(bad ? 0 : (o & 3) * RW + (o >> 2));
+            // word index into the chunk's copies: copy (o & 3), word (o >> 2) of this channel's
+            // (below CC * 4 * RW <= 51200: the copies fill at most 200 KiB)
+            S.offs[g * ck + c] = (uint16_t)(bad ? 0 : base + (o & 3) * RW + (o >> 2));
         }
     }
     if (__syncthreads_or(bad)) {
@@ -212,7 +215,7 @@ __device__ __forceinline__ void dedisp_tile(const DedispArgs& a, int RW, int CC,
             const uint16_t* offs = S.offs + warp * ck + cb;
 #pragma unroll 4
             for (int i = 0; i < cn; ++i) {
-                const uint32_t* p = S.copies + (size_t)i * 4 * RW + offs[i] + lane;
+                const uint32_t* p = S.copies + offs[i] + lane;
 #pragma unroll
                 for (int k = 0; k < KW; ++k) {
                     const uint32_t w = p[32 * k];
@@ -222,8 +225,10 @@ __device__ __forceinline__ void dedisp_tile(const DedispArgs& a, int RW, int CC,
             }
         }
         since_flush += cn;
-        __syncthreads();
+        // no barrier here: the next chunk's first barrier (after its data wait) also orders this
+        // chunk's reads of the copies before the next expansion overwrites them
     }
+    __syncthreads();  // every warp is done with the copies (the epilogue reuses them)
     if (failed_at >= 0) {
         if (threadIdx.x == 0 && a.err) atomicExch(a.err, 1);
         // let the copies still in flight land before the CTA's shared memory is released

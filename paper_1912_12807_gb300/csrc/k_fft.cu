@@ -408,7 +408,229 @@ cudaError_t run_pass(const PassArgs& p, int nb, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// ---- register-radix form ----------------------------------------------------
+// The same pass with its R-point DFTs split into two or three register
+// sub-stages (radix 4, 8 or 16) whose first reads the columns straight from
+// global memory (mean, padding or inter-pass twiddles applied in registers)
+// and whose last writes the results straight to global memory, so an
+// element crosses shared memory once (two sub-stages) or twice (three)
+// instead of being staged, fixed up, transformed in place and read back.
+// Sub-stage with radix RR and running span ns (Stockham, as in `substage`):
+// butterfly b takes elements b + q R/RR (q < RR) of its column, twiddled by
+// exp(-2 pi i q (b mod ns) / (RR ns)), and writes the RR-point DFT to
+// ((b - b mod ns) RR + b mod ns) + q ns; in the last sub-stage ns RR = R and
+// the result of butterfly b, output q, is frequency b + q R/RR.
+// A CTA owns RT columns; its threads take butterflies column-fastest
+// (coalesced column reads, and writes of later passes), except the last
+// sub-stage of the first pass (Ns = 1), whose outputs are contiguous in
+// frequency: there the threads take butterflies b-fastest.
+template <int R>
+struct RrPlan {
+    // sub-stage radices: first, middle (0: none), last
+    static constexpr int A = (R == 32) ? 4 : (R == 64) ? 8 : (R == 128) ? 16 : (R == 256) ? 16 : (R == 512) ? 8 : 16;
+    static constexpr int B = (R == 512 || R == 1024) ? 8 : 0;
+    static constexpr int C = R / A / (B ? B : 1);
+    static constexpr int RT = (R == 32) ? 32 : (R == 64 || R == 128) ? 16 : 8;  // columns per CTA
+    static constexpr int NTR = (R >= 512) ? 256 : 128;                       // threads
+    static constexpr int RTP = RT + 1;
+    // twiddle entries of the sub-stages after the first: B * A (middle) + C * (R / C)
+    static constexpr int TW = (B ? B * A : 0) + R;
+};
+
+template <int R, int RR, int RT, int NTR>
+__device__ __forceinline__ void rr_mid(float2* buf, const float2* twt, int ns) {
+    constexpr int NB = R / RR * RT;
+    constexpr int PER = (NB + NTR - 1) / NTR;
+    float2 x[PER][RR];
+    int dst[PER];
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int e = threadIdx.x + p * NTR;
+        if (NB % NTR == 0 || e < NB) {
+            const int jj = e % RT, b = e / RT;
+            const int k = b & (ns - 1);
+#pragma unroll
+            for (int q = 0; q < RR; ++q) {
+                x[p][q] = buf[(b + q * (R / RR)) * (RT + 1) + jj];
+                if (q && k) x[p][q] = cmul(x[p][q], twt[q * ns + k]);
+            }
+            dst[p] = ((b - k) * RR + k) * (RT + 1) + jj;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int e = threadIdx.x + p * NTR;
+        if (NB % NTR == 0 || e < NB) {
+            dft_any<RR>(x[p]);
+#pragma unroll
+            for (int q = 0; q < RR; ++q) buf[dst[p] + q * ns * (RT + 1)] = x[p][q];
+        }
+    }
+    __syncthreads();
+}
+
+template <int R, bool FIRST>
+__global__ void __launch_bounds__(RrPlan<R>::NTR) k_fft_pass_rr(const __grid_constant__ PassArgs a) {
+    using P = RrPlan<R>;
+    constexpr int A = P::A, B = P::B, C = P::C, RT = P::RT, RTP = P::RTP, NTR = P::NTR;
+    extern __shared__ float2 sm[];
+    float2* buf = sm;               // [R][RTP]
+    float2* twt = sm + R * RTP;     // middle table [B * A] (q-major), then the last [C * (R / C)]
+    const int b = blockIdx.y;
+    const int64_t ncol = a.M / R;
+    const int64_t j0 = (int64_t)blockIdx.x * RT;
+    // sub-stage twiddle tables from the global table exp(-2 pi i t / twM)
+    {
+        const int64_t tstride = a.twM / R;
+        int off = 0;
+        if constexpr (B != 0) {
+            // middle: ns = A, radix B: exp(-2 pi i q k / (B A)), q < B, k < A
+            for (int i = threadIdx.x; i < B * A; i += NTR) {
+                const int q = i / A, k = i - q * A;
+                twt[i] = a.tw[(int64_t)(q * k * (R / (B * A))) * tstride];
+            }
+            off = B * A;
+        }
+        // last: ns = R / C, radix C: exp(-2 pi i q k / R), q < C, k < R / C
+        for (int i = threadIdx.x; i < R; i += NTR) {
+            const int q = i / (R / C), k = i - q * (R / C);
+            twt[off + i] = a.tw[(int64_t)(q * k) * tstride];
+        }
+    }
+    // first sub-stage: radix A from global memory, ns = 1 (no twiddles inside the DFT)
+    {
+        float mu_i = 0.f, mu_f = 0.f;
+        int64_t nv = 0;
+        if constexpr (FIRST) {
+            __shared__ float s_mu[2];
+            if (threadIdx.x == 0) {
+                // mean = sum / N_v in FP64 (once per CTA), split as integer + fraction
+                const double mu = (double)a.sums[b] / (double)row_nv(a, b);
+                const double mi = rint(mu);
+                s_mu[0] = (float)mi;
+                s_mu[1] = (float)(mu - mi);
+            }
+            __syncthreads();
+            mu_i = s_mu[0];
+            mu_f = s_mu[1];
+            nv = row_nv(a, b);
+        }
+        constexpr int NB = R / A * RT;
+        constexpr int PER = (NB + NTR - 1) / NTR;
+        const float* sr = FIRST ? a.series + (int64_t)b * a.series_stride : nullptr;
+        const float2* in = FIRST ? nullptr : a.in + (int64_t)b * a.in_stride;
+#pragma unroll
+        for (int p = 0; p < PER; ++p) {
+            const int e = threadIdx.x + p * NTR;
+            if (NB % NTR == 0 || e < NB) {
+                const int jj = e % RT, bb = e / RT;
+                const int64_t j = j0 + jj;
+                float2 x[A];
+#pragma unroll
+                for (int q = 0; q < A; ++q) {
+                    const int r = bb + q * (R / A);
+                    float2 v = make_float2(0.f, 0.f);
+                    if (j < ncol) {
+                        const int64_t n = j + (int64_t)r * ncol;
+                        if constexpr (FIRST) {
+                            if (2 * n + 1 < nv) {
+                                const float2 w = *reinterpret_cast<const float2*>(sr + 2 * n);
+                                v = make_float2((w.x - mu_i) - mu_f, (w.y - mu_i) - mu_f);
+                            } else if (2 * n < nv) {
+                                v.x = (sr[2 * n] - mu_i) - mu_f;
+                            }
+                        } else {
+                            v = in[n];
+                            const int64_t k = j % a.Ns;
+                            if (k && r) v = cmul(v, a.ptw[(int64_t)r * a.Ns + k]);
+                        }
+                    }
+                    x[q] = v;
+                }
+                dft_any<A>(x);
+#pragma unroll
+                for (int q = 0; q < A; ++q) buf[(bb * A + q) * RTP + jj] = x[q];
+            }
+        }
+        __syncthreads();
+    }
+    if constexpr (B != 0) rr_mid<R, B, RT, NTR>(buf, twt, A);
+    // last sub-stage: radix C, ns = R / C, straight to global memory
+    {
+        constexpr int NS = R / C;
+        const float2* tl = twt + (B ? B * A : 0);
+        constexpr int NB = R / C * RT;
+        constexpr int PER = (NB + NTR - 1) / NTR;
+        float2* o = a.out + (int64_t)b * a.out_stride;
+        const bool ns1 = a.Ns == 1;
+#pragma unroll
+        for (int p = 0; p < PER; ++p) {
+            const int e = threadIdx.x + p * NTR;
+            if (NB % NTR == 0 || e < NB) {
+                // Ns = 1: butterflies b-fastest (contiguous frequencies); else column-fastest
+                const int jj = ns1 ? e / NS : e % RT;
+                const int bb = ns1 ? e % NS : e / RT;
+                float2 x[C];
+#pragma unroll
+                for (int q = 0; q < C; ++q) {
+                    x[q] = buf[(bb + q * NS) * RTP + jj];
+                    if (q && bb) x[q] = cmul(x[q], tl[q * NS + bb]);
+                }
+                dft_any<C>(x);
+                const int64_t j = j0 + jj;
+                if (j < ncol) {
+                    if (ns1) {
+#pragma unroll
+                        for (int q = 0; q < C; ++q) o[j * R + bb + q * NS] = x[q];
+                    } else {
+                        const int64_t kc = j % a.Ns;
+                        float2* oo = o + (j / a.Ns) * a.Ns * R + kc;
+#pragma unroll
+                        for (int q = 0; q < C; ++q) oo[(int64_t)(bb + q * NS) * a.Ns] = x[q];
+                    }
+                }
+            }
+        }
+    }
+}
+
+// PSS_FFT_RR=0 keeps the shared-memory sub-stage forms; by default the
+// register-radix form runs.
+bool fft_rr() {
+    static const int v = [] {
+        const char* e = getenv("PSS_FFT_RR");
+        return e ? (e[0] == '1' ? 1 : 0) : 1;
+    }();
+    return v == 1;
+}
+
+template <int R>
+cudaError_t run_pass_rr(const PassArgs& p, int nb, cudaStream_t s) {
+    using P = RrPlan<R>;
+    static_assert(P::A * (P::B ? P::B : 1) * P::C == R, "radix plan");
+    const size_t shm = (size_t)(R * P::RTP + P::TW) * sizeof(float2);
+    const void* k = p.series ? (const void*)k_fft_pass_rr<R, true> : (const void*)k_fft_pass_rr<R, false>;
+    cudaError_t e = allow_smem(k, shm);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((p.M / R + P::RT - 1) / P::RT), (unsigned)nb);
+    if (p.series) k_fft_pass_rr<R, true><<<grid, P::NTR, shm, s>>>(p);
+    else k_fft_pass_rr<R, false><<<grid, P::NTR, shm, s>>>(p);
+    return cudaGetLastError();
+}
+
 cudaError_t dispatch_pass(int R, const PassArgs& p, int nb, cudaStream_t s) {
+    if (fft_rr()) {
+        switch (R) {
+            case 32: return run_pass_rr<32>(p, nb, s);
+            case 64: return run_pass_rr<64>(p, nb, s);
+            case 128: return run_pass_rr<128>(p, nb, s);
+            case 256: return run_pass_rr<256>(p, nb, s);
+            case 512: return run_pass_rr<512>(p, nb, s);
+            case 1024: return run_pass_rr<1024>(p, nb, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (R) {
         case 32: return run_pass<32>(p, nb, s);
         case 64: return run_pass<64>(p, nb, s);

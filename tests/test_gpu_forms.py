@@ -1,6 +1,8 @@
 """Alternative kernel forms chosen per process (environment) give the same
-bytes: the double- and single-buffered FFT passes (PSS_FFT_DB) and zmax 0
-plane kernels (PSS_PLANE_Z0_DB)."""
+bytes: the double- and single-buffered FFT passes (PSS_FFT_DB, with the
+shared-memory sub-stage passes, PSS_FFT_RR=0) and zmax 0 plane kernels
+(PSS_PLANE_Z0_DB).  The register-radix FFT passes (PSS_FFT_RR=1, the
+default) round differently: both FFT forms are compared with the oracle."""
 import os
 import subprocess
 import sys
@@ -38,9 +40,29 @@ def _run(tmp_path, env_extra, nsamp, tag):
 
 @pytest.mark.parametrize("nsamp", [1 << 16, (1 << 16) + 12345])
 def test_fft_and_plane_forms_are_bit_identical(tmp_path, nsamp):
-    a = _run(tmp_path, {"PSS_FFT_DB": "0", "PSS_PLANE_Z0_DB": "0"}, nsamp, "single")
-    b = _run(tmp_path, {"PSS_FFT_DB": "1", "PSS_FFT_TPC": "3", "PSS_PLANE_Z0_TPC": "3"}, nsamp, "double")
+    a = _run(tmp_path, {"PSS_FFT_RR": "0", "PSS_FFT_DB": "0", "PSS_PLANE_Z0_DB": "0"}, nsamp, "single")
+    b = _run(tmp_path, {"PSS_FFT_RR": "0", "PSS_FFT_DB": "1", "PSS_FFT_TPC": "3", "PSS_PLANE_Z0_TPC": "3"}, nsamp,
+             "double")
     assert a.shape == b.shape and a.tobytes() == b.tobytes()
+
+
+@pytest.mark.parametrize("nsamp", [1 << 16, (1 << 15) + 777])
+def test_fft_register_and_shared_forms_match_oracle(tmp_path, nsamp):
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from _parity import check_powers, oracle_plane
+    from oracle import dedisperse as OD
+    from oracle import plan as OP
+    from paper_1912_12807_gb300 import synth
+    wl = synth.workload_small(nsamp=nsamp)
+    op = OP.Plan.for_file(wl.fil, wl.stages)
+    x = OD.channel_major(wl.fil.data, wl.fil.nchan, 8)
+    M = op.nv_nfft(0)[1] // 2
+    refs = [np.abs(oracle_plane(x, op, i, wl.cfg)[1]) ** 2 for i in range(40)]
+    for tag, env in (("rr", {"PSS_FFT_RR": "1"}), ("smem", {"PSS_FFT_RR": "0"})):
+        got = _run(tmp_path, env, nsamp, tag)
+        spec = got[: 2 * 40 * M].view(np.complex64)
+        for i in range(40):
+            check_powers(np.abs(spec[i * M:(i + 1) * M]) ** 2, refs[i], "%s form, trial %d" % (tag, i))
 
 
 CHILD_DD = r"""
