@@ -856,7 +856,7 @@ __global__ void __launch_bounds__(32 * WW) k_whiten_warp(const float2* Zall, int
 constexpr int WP = 4;  // pairs per CTA
 
 template <int VPL>
-__global__ void __launch_bounds__(64 * WP) k_whiten_pair(const float2* Zall, int64_t z_stride, int64_t M,
+__global__ void __launch_bounds__(64 * WP, 4) k_whiten_pair(const float2* Zall, int64_t z_stride, int64_t M,
                                                         float2* out, int64_t out_stride, const float2* tw,
                                                         int64_t twM, int whiten, float* gains,
                                                         int64_t gains_stride) {
