@@ -506,35 +506,70 @@ __global__ void __launch_bounds__(F16NT, 4) k_plane_fft16(const __grid_constant_
     __syncthreads();
     const int nz = a.nz;
     float2* P = reinterpret_cast<float2*>(a.plane + (int64_t)b * a.plane_stride);
+    // Per row: the first radix-16 sub-stage (running span 1) takes butterfly b = thread's
+    // elements b + 128 q, which are the thread's own bins X[q]: it runs on the products in
+    // registers; the middle sub-stage runs in shared memory; the last (radix 8, span 256)
+    // reads its inputs and writes the powers of its outputs b + 256 q straight to the plane.
+    // The same operations in the same order as the in-place form (bit-identical output).
     for (int j = 0; j < nz; ++j) {
         const bool zrow0 = (j == a.zrow0);
         const float2* T0 = a.ftaps + (int64_t)j * 2 * L;
         const float2* T1 = T0 + L;
+        {
+            float2 x0[NE], x1[NE];
 #pragma unroll
-        for (int e = 0; e < NE; ++e) {
-            const int i = threadIdx.x + e * F16NT;
-            const float2 y0 = cmul(X[e], __ldg(T0 + i)), y1 = cmul(X[e], __ldg(T1 + i));
-            Y0[fx(i)] = make_float2(y0.x, -y0.y);
-            Y1[fx(i)] = make_float2(y1.x, -y1.y);
-        }
-        __syncthreads();
-        fft2048x2_r16(Y0, Y1, twt);
-        float2* row = P + (int64_t)j * M;
+            for (int e = 0; e < NE; ++e) {
+                const int i = threadIdx.x + e * F16NT;
+                const float2 y0 = cmul(X[e], __ldg(T0 + i)), y1 = cmul(X[e], __ldg(T1 + i));
+                x0[e] = make_float2(y0.x, -y0.y);
+                x1[e] = make_float2(y1.x, -y1.y);
+            }
+            dft_any<16>(x0);
+            dft_any<16>(x1);
 #pragma unroll
-        for (int e = 0; e < NE; ++e) {
-            const int u = threadIdx.x + e * F16NT;
-            const int64_t k = k0 + u;
-            if (u < V && k < M) {
-                const float2 y0 = Y0[fx(u)], y1 = Y1[fx(u)];
-                float p0 = y0.x * y0.x + y0.y * y0.y;
-                if (zrow0) {
-                    const float2 c = Ap[k];
-                    p0 = c.x * c.x + c.y * c.y;
-                }
-                row[k] = make_float2(p0, y1.x * y1.x + y1.y * y1.y);
+            for (int q = 0; q < 16; ++q) {
+                Y0[fx(threadIdx.x * 16 + q)] = x0[q];
+                Y1[fx(threadIdx.x * 16 + q)] = x1[q];
             }
         }
         __syncthreads();
+        fft16_substage2<16, 16>(Y0, Y1, twt + T16A);
+        float2* row = P + (int64_t)j * M;
+        {
+            constexpr int NS = 256, NB = L / 8, PER = NB / F16NT;
+            const float2* tl = twt + T16B;
+#pragma unroll
+            for (int p = 0; p < PER; ++p) {
+                const int bb = threadIdx.x + p * F16NT;  // < NS: its span index k is bb itself
+                float2 x0[8], x1[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    x0[q] = Y0[fx(bb + q * NB)];
+                    x1[q] = Y1[fx(bb + q * NB)];
+                    if (q) {
+                        const float2 w = tl[q * NS + bb];
+                        x0[q] = cmul(x0[q], w);
+                        x1[q] = cmul(x1[q], w);
+                    }
+                }
+                dft_any<8>(x0);
+                dft_any<8>(x1);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int u = bb + q * NS;
+                    const int64_t k = k0 + u;
+                    if (u < V && k < M) {
+                        float p0 = x0[q].x * x0[q].x + x0[q].y * x0[q].y;
+                        if (zrow0) {
+                            const float2 c = Ap[k];
+                            p0 = c.x * c.x + c.y * c.y;
+                        }
+                        row[k] = make_float2(p0, x1[q].x * x1[q].x + x1[q].y * x1[q].y);
+                    }
+                }
+            }
+        }
+        __syncthreads();  // the next row's first sub-stage overwrites Y0 / Y1
     }
 }
 
