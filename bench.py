@@ -910,7 +910,7 @@ def main():
     ap.add_argument("--stream-files", type=int, default=64)
     ap.add_argument("--refine-top", type=int, default=4096, help="candidates refined after a zmax > 0 search")
     ap.add_argument("--stream-speedup", type=float, default=50.0)
-    ap.add_argument("--stream-group", type=int, default=8,
+    ap.add_argument("--stream-group", type=int, default=16,
                     help="files per group of the grouped server in the stream measurement (1: not measured)")
     ap.add_argument("--fold-top", type=int, default=64, help="sifted candidates folded after the search (0: none)")
     ap.add_argument("--single-pulse", type=int, default=None,

@@ -1664,6 +1664,8 @@ pss_status pss_ctx_create(int device, pss_ctx** out) {
     if (const char* f = getenv("PSS_PLANE_FORM")) c->tune.plane_form = f[0] == '1';
     // PSS_DEDISP_BX_MIN=k: rows with ds >= k use the boxcar-table dedispersion (0: never)
     if (const char* f = getenv("PSS_DEDISP_BX_MIN")) c->tune.bx_min = std::max(0, atoi(f));
+    // PSS_DEDISP_KB=k: shared memory (KiB) for the dedispersion kernel's staged channel chunks
+    if (const char* f = getenv("PSS_DEDISP_KB")) c->tune.dedisp_kb = std::min(200, std::max(16, atoi(f)));
     // PSS_WHITEN_FORM=0 / 1 / 2: block per CTA / warp per block / warp pair per block
     if (const char* f = getenv("PSS_WHITEN_FORM")) c->tune.whiten_form = (f[0] >= '0' && f[0] <= '2') ? f[0] - '0' : -1;
     *out = c;

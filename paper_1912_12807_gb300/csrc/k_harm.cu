@@ -17,6 +17,7 @@
 // f >= f_lo cut are compacted with a warp ballot and one atomic per warp;
 // the global counter always counts, so an overflow of `cap` is detected.
 #include <math.h>
+#include <stdlib.h>
 
 #include "pss_internal.h"
 
@@ -290,14 +291,17 @@ __device__ __forceinline__ void reg_stages(const HarmArgs& a, const float* P, fl
 
 constexpr int REG_NT = 128;
 
-template <int NSTAGES, int R>
+template <int NSTAGES, int R, bool ROWS>
 __global__ void __launch_bounds__(REG_NT) k_harm_reg(const __grid_constant__ HarmArgs a) {
     // blocks of consecutive launch order take the same h range of successive
-    // rows, so the harmonic rows they read overlap while they are in L2
+    // rows, so the harmonic rows they read overlap while they are in L2; with
+    // ROWS the warps of a block take consecutive rows of one h range, so the
+    // harmonic rows they share are read through the same L1
     const int lane = threadIdx.x & 31;
-    const int j = blockIdx.x;
+    const int j = ROWS ? blockIdx.x * (REG_NT / 32) + (threadIdx.x >> 5) : blockIdx.x;
+    if (ROWS && j >= a.nz) return;  // no barriers in this kernel
     const int b = blockIdx.z;
-    const int hw = (blockIdx.y * (REG_NT / 32) + (threadIdx.x >> 5)) * 32 * R;
+    const int hw = ROWS ? blockIdx.y * 32 * R : (blockIdx.y * (REG_NT / 32) + (threadIdx.x >> 5)) * 32 * R;
     const float* P = a.plane + (int64_t)b * a.plane_stride;
     float acc[R];
     const float* row = P + j * (int)a.nfft;
@@ -306,18 +310,37 @@ __global__ void __launch_bounds__(REG_NT) k_harm_reg(const __grid_constant__ Har
     reg_stages<0, NSTAGES, R>(a, P, acc, hw, j, lane, b);
 }
 
-template <int R>
-cudaError_t launch_reg(const HarmArgs& a, cudaStream_t s) {
-    dim3 grid((unsigned)a.nz, (unsigned)(a.nfft / (REG_NT * R)), (unsigned)a.nb);
+// 2-D planes: the warps of a block take consecutive plane rows (default; 31.1 -> 28.9 ms on
+// the zmax 200 accel file); PSS_HARM_ROWS=0 keeps one row per block
+bool harm_rows() {
+    static const int v = [] {
+        const char* e = getenv("PSS_HARM_ROWS");
+        return e ? (e[0] == '1' ? 1 : 0) : 1;
+    }();
+    return v == 1;
+}
+
+template <int R, bool ROWS>
+cudaError_t launch_reg_t(const HarmArgs& a, cudaStream_t s) {
+    constexpr int W = REG_NT / 32;
+    dim3 grid(ROWS ? (unsigned)((a.nz + W - 1) / W) : (unsigned)a.nz,
+              ROWS ? (unsigned)(a.nfft / (32 * R)) : (unsigned)(a.nfft / (REG_NT * R)), (unsigned)a.nb);
+    if (grid.y > 65535) return cudaErrorInvalidValue;
     switch (a.nstages) {
-        case 1: k_harm_reg<1, R><<<grid, REG_NT, 0, s>>>(a); break;
-        case 2: k_harm_reg<2, R><<<grid, REG_NT, 0, s>>>(a); break;
-        case 3: k_harm_reg<3, R><<<grid, REG_NT, 0, s>>>(a); break;
-        case 4: k_harm_reg<4, R><<<grid, REG_NT, 0, s>>>(a); break;
-        case 5: k_harm_reg<5, R><<<grid, REG_NT, 0, s>>>(a); break;
+        case 1: k_harm_reg<1, R, ROWS><<<grid, REG_NT, 0, s>>>(a); break;
+        case 2: k_harm_reg<2, R, ROWS><<<grid, REG_NT, 0, s>>>(a); break;
+        case 3: k_harm_reg<3, R, ROWS><<<grid, REG_NT, 0, s>>>(a); break;
+        case 4: k_harm_reg<4, R, ROWS><<<grid, REG_NT, 0, s>>>(a); break;
+        case 5: k_harm_reg<5, R, ROWS><<<grid, REG_NT, 0, s>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+template <int R>
+cudaError_t launch_reg(const HarmArgs& a, cudaStream_t s) {
+    if (a.nz > 1 && harm_rows() && a.nfft / (32 * R) <= 65535) return launch_reg_t<R, true>(a, s);
+    return launch_reg_t<R, false>(a, s);
 }
 
 }  // namespace

@@ -121,3 +121,52 @@ def test_dedisp_boxcar_table_and_direct_forms_are_identical(tmp_path):
                 np.testing.assert_array_equal(outs[1][off:off + nv], ref, err_msg="DM index %d" % i)
             off += nv
         first += st.n_dm
+
+
+CHILD_SEARCH = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, {root!r})
+from paper_1912_12807_gb300 import pss, synth
+sys.path.insert(0, {tests!r})
+from test_gpu_forms import search_cases
+res = []
+for fil, stages, mask in search_cases():
+    ctx = pss.Context(0)
+    plan = pss.Plan(pss.FilDesc.of(fil, chan_mask=mask), stages)
+    cfg = pss.search_cfg(zmax=0, numharm=8)
+    d = torch.from_numpy(fil.data).cuda()
+    spec = pss.pss_spectrum(ctx, plan, d, cfg, 0, plan.ndm).cpu().numpy()
+    raw = pss.pss_search_raw(ctx, plan, d, cfg, 0, plan.ndm)
+    res.append(spec.view(np.float32).ravel())
+    res.append(np.frombuffer(raw.tobytes(), dtype=np.float32))
+    ctx.close()
+np.save({out!r}, np.concatenate(res))
+"""
+
+
+def search_cases():
+    """A masked 8-bit file and a 1-bit file, each with rows of ds 8 to 128 of
+    16 or more trials (the boxcar-table path of the search: float series with
+    per-trial sums)."""
+    from paper_1912_12807_gb300 import synth
+    f8 = synth.make_8bit(64, 1 << 18, 2e-4, 1200.0, 1500.0, [synth.Pulsar(0.05, 40.0, 0.05, 0.6)], seed=21)
+    mask = np.ones(64, dtype=np.uint8)
+    mask[[1, 2, 30, 63]] = 0
+    st8 = [synth.Stage(0.0, 4.0, 16, 8), synth.Stage(64.0, 6.0, 18, 32), synth.Stage(172.0, 10.0, 16, 128)]
+    f1 = synth.make_1bit(96, 1 << 17, 2.5e-4, 1230.0, 1518.0, [synth.Pulsar(0.1, 80.0, 0.05, 0.1)], seed=22)
+    st1 = [synth.Stage(0.0, 5.0, 16, 8), synth.Stage(80.0, 10.0, 20, 16), synth.Stage(280.0, 20.0, 16, 64)]
+    return [(f8, st8, mask), (f1, st1, None)]
+
+
+def test_dedisp_boxcar_table_search_path_is_identical(tmp_path):
+    # the search's float series and per-trial sums through the table equal the direct kernel's:
+    # identical spectra and raw candidates, masked 8-bit and 1-bit files
+    outs = []
+    for tag, v in (("direct", "0"), ("table", "2")):
+        out = str(tmp_path / ("srch_%s.npy" % tag))
+        env = dict(os.environ)
+        env["PSS_DEDISP_BX_MIN"] = v
+        child = CHILD_SEARCH.format(root=ROOT, tests=os.path.join(ROOT, "tests"), out=out)
+        subprocess.run([sys.executable, "-c", child], env=env, check=True, timeout=600)
+        outs.append(np.load(out))
+    assert outs[0].size > 0 and outs[0].tobytes() == outs[1].tobytes()
