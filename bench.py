@@ -280,7 +280,10 @@ def stage_work(plan, wl, fil_nbytes):
     add one 16-bit table term per channel and output sample with one 32-bit
     add, counted as the two SWAR slots it takes; bxtable: the table builds;
     unpack: file read + channel-major write; fft: every pass reads and writes
-    8 bytes per complex point; whiten: spectrum read + write; plane: for
+    8 bytes per complex point; whiten: spectrum read + write (where the
+    whitening and the zmax 0 plane run as one kernel, the stage reads the
+    spectrum and writes the plane: the same bytes, and the plane stage has
+    no launches); plane: for
     zmax 0 the spectrum read + plane write, for zmax > 0 the flops of the
     overlap-save correlation (5 L log2 L per L-point FFT, 6 per complex
     product) or, where the direct form runs, the 8 flops of every complex tap;
@@ -451,6 +454,9 @@ def measure_search(pss, wl, name, steps, warmup, local_rank, flush, stream, peak
         rooflines[st] = roofline_of(st, bound, amount * steps, unit, ms_st, n_st, peaks, peak_kind, alu)
         if traffic:
             rooflines[st]["traffic"] = recorded_traffic(name, st)
+    if "whiten" in rooflines and cfg.zmax == 0 and prof.get("plane", (0.0, 0))[1] == 0:
+        rooflines["whiten"]["note"] = ("whitening and the zmax 0 plane in one kernel (k_whiten_z0, k_z0_seams): "
+                                       "spectrum read, plane written")
     if "dedisperse" in rooflines:
         # the same launches against HBM: every trial's FP32 series written once, the
         # channel-major file read once per launch
@@ -476,7 +482,7 @@ def measure_search(pss, wl, name, steps, warmup, local_rank, flush, stream, peak
            "gpu_launches": int(round(launches_per_step * steps)),
            "stages_ms_per_step": {k: v[0] / steps for k, v in prof.items()},
            "stage_launches_per_step": {k: v[1] / steps for k, v in prof.items()},
-           "stage_rooflines": {k: {kk: v[kk] for kk in ("bound", "frac", "achieved", "unit", "hbm_frac")
+           "stage_rooflines": {k: {kk: v[kk] for kk in ("bound", "frac", "achieved", "unit", "hbm_frac", "note")
                                    if kk in v} for k, v in rooflines.items()},
            "clocks": clocks.summary(), "wall_s_timed": t_wall, "candidates": int(len(cands))}
     return res, ctx, plan, cfg, data_dev, cands

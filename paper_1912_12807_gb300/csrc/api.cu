@@ -693,6 +693,19 @@ struct PathSetup {
 // Trials per batch for a stage of nfft-point spectra: as many as fit in
 // 6 GiB of per-trial buffers (series, three spectra, and the plane when
 // searching), at most 1024 and at most the n trials there are.
+// Whitening and the zmax 0 plane in one kernel (k_whiten_z0; PSS_WHITEN_Z0=0
+// keeps the two kernels): zmax 0 with 2m = 32 taps, warp-pair whitening of
+// 256, 512 or 1024-bin blocks.  The block scales go to the spectrum buffer,
+// which the fused form does not otherwise use.
+bool whiten_z0_usable(const pss_search_cfg* cfg, int whiten_form) {
+    static const bool on = [] {
+        const char* e = getenv("PSS_WHITEN_Z0");
+        return !(e && e[0] == '0');
+    }();
+    const int W = cfg->whiten_block;
+    return on && cfg->zmax == 0 && cfg->halfwidth_extra == 16 && whiten_form == 2 && (W == 256 || W == 512 || W == 1024);
+}
+
 int64_t batch_trials(int64_t nfft, int nz, Mode mode, int64_t n) {
     const size_t per_dm = (size_t)nfft * 4 + (size_t)(nfft / 2) * 8 * 3 +
                           ((mode == MODE_PLANE || mode == MODE_GAINS) ? 0 : (size_t)nz * nfft * 4);
@@ -917,41 +930,50 @@ pss_status enqueue_path(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc* 
                 fa.gains_out = outs.gains + (d.b0 - dm_begin) * (M / cfg->whiten_block);
                 fa.gains_stride = M / cfg->whiten_block;
             }
+            const bool z0 = (mode == MODE_SEARCH || mode == MODE_PLANE) && whiten_z0_usable(cfg, fa.whiten_form);
+            if (z0) {
+                fa.z0_plane = plane_out;
+                fa.z0_plane_stride = (int64_t)P.nz * nfft;
+                fa.z0_scale1 = (const float*)((const int32_t*)ctx->tapinfo.p + 3 * P.nz) + 1;
+                fa.wscale = (float*)ctx->spec.p;
+            }
             PSS_CUDA(launch_fft_whiten(fa, s, ctx));
             if (mode == MODE_SPECTRUM || mode == MODE_GAINS) continue;
-            PlaneArgs pl{};
-            pl.spec = spec;
-            pl.spec_stride = M;
-            pl.nfft = nfft;
-            pl.nb = d.nb;
-            pl.plane = (mode == MODE_PLANE) ? outs.plane + d.out_off : (float*)ctx->plane.p;
-            pl.plane_stride = (int64_t)P.nz * nfft;
-            pl.zmax = cfg->zmax;
-            pl.dz = cfg->zmax ? cfg->dz : 1.0;
-            pl.extra = cfg->halfwidth_extra;
-            pl.taps = (const float2*)ctx->taps.p;
-            const int32_t* info = (const int32_t*)ctx->tapinfo.p;
-            pl.tap_off = info;
-            pl.tap_m = info + 2 * P.nz;
-            pl.tap_scale = (const float*)(info + 3 * P.nz);
-            pl.ftaps = nullptr;
-            if (ctx->ftap_ok && plane_fft_usable(cfg->zmax, cfg->halfwidth_extra, M)) {
-                const int mmax = (cfg->zmax + 1) / 2 + cfg->halfwidth_extra;
-                pl.ftaps = (const float2*)ctx->ftaps.p;
-                pl.fL = PLANE_FFT_L;
-                pl.fM0 = mmax - 1;
-                pl.fV = PLANE_FFT_L - 2 * mmax + 1;
-                pl.tw = (const float2*)ctx->twid.p;
-                pl.twM = ctx->twid_n;
-                pl.nz = P.nz;
-                pl.form = ctx->tune.plane_form;
-                pl.zrow0 = -1;
-                for (int j = 0; j < P.nz; ++j)
-                    if (-(double)cfg->zmax + (double)j * pl.dz == 0.0) pl.zrow0 = j;
-            }
-            {
-                ProfScope ps(ctx, 4, s);
-                PSS_CUDA(launch_plane(pl, s));
+            if (!z0) {
+                PlaneArgs pl{};
+                pl.spec = spec;
+                pl.spec_stride = M;
+                pl.nfft = nfft;
+                pl.nb = d.nb;
+                pl.plane = (mode == MODE_PLANE) ? outs.plane + d.out_off : (float*)ctx->plane.p;
+                pl.plane_stride = (int64_t)P.nz * nfft;
+                pl.zmax = cfg->zmax;
+                pl.dz = cfg->zmax ? cfg->dz : 1.0;
+                pl.extra = cfg->halfwidth_extra;
+                pl.taps = (const float2*)ctx->taps.p;
+                const int32_t* info = (const int32_t*)ctx->tapinfo.p;
+                pl.tap_off = info;
+                pl.tap_m = info + 2 * P.nz;
+                pl.tap_scale = (const float*)(info + 3 * P.nz);
+                pl.ftaps = nullptr;
+                if (ctx->ftap_ok && plane_fft_usable(cfg->zmax, cfg->halfwidth_extra, M)) {
+                    const int mmax = (cfg->zmax + 1) / 2 + cfg->halfwidth_extra;
+                    pl.ftaps = (const float2*)ctx->ftaps.p;
+                    pl.fL = PLANE_FFT_L;
+                    pl.fM0 = mmax - 1;
+                    pl.fV = PLANE_FFT_L - 2 * mmax + 1;
+                    pl.tw = (const float2*)ctx->twid.p;
+                    pl.twM = ctx->twid_n;
+                    pl.nz = P.nz;
+                    pl.form = ctx->tune.plane_form;
+                    pl.zrow0 = -1;
+                    for (int j = 0; j < P.nz; ++j)
+                        if (-(double)cfg->zmax + (double)j * pl.dz == 0.0) pl.zrow0 = j;
+                }
+                {
+                    ProfScope ps(ctx, 4, s);
+                    PSS_CUDA(launch_plane(pl, s));
+                }
             }
         }
         if (mode == MODE_PLANE) continue;
@@ -1412,40 +1434,49 @@ pss_status multi_enqueue(pss_ctx* ctx, const pss_search_cfg* cfg, const MultiSet
         fa.whiten_form = ctx->tune.whiten_form >= 0 ? ctx->tune.whiten_form : 2;
         set_passtw(ctx, &fa);
         fa.whiten = 1;
-        PSS_CUDA(launch_fft_whiten(fa, s, ctx));
-        PlaneArgs pl{};
-        pl.spec = (const float2*)ctx->spec.p;
-        pl.spec_stride = Mh;
-        pl.nfft = nfft;
-        pl.nb = b.nrows;
-        pl.plane = (float*)ctx->plane.p;
-        pl.plane_stride = (int64_t)M.nz * nfft;
-        pl.zmax = cfg->zmax;
-        pl.dz = cfg->zmax ? cfg->dz : 1.0;
-        pl.extra = cfg->halfwidth_extra;
-        pl.taps = (const float2*)ctx->taps.p;
-        const int32_t* info = (const int32_t*)ctx->tapinfo.p;
-        pl.tap_off = info;
-        pl.tap_m = info + 2 * M.nz;
-        pl.tap_scale = (const float*)(info + 3 * M.nz);
-        pl.ftaps = nullptr;
-        if (ctx->ftap_ok && plane_fft_usable(cfg->zmax, cfg->halfwidth_extra, Mh)) {
-            const int mmax = (cfg->zmax + 1) / 2 + cfg->halfwidth_extra;
-            pl.ftaps = (const float2*)ctx->ftaps.p;
-            pl.fL = PLANE_FFT_L;
-            pl.fM0 = mmax - 1;
-            pl.fV = PLANE_FFT_L - 2 * mmax + 1;
-            pl.tw = (const float2*)ctx->twid.p;
-            pl.twM = ctx->twid_n;
-            pl.nz = M.nz;
-            pl.form = ctx->tune.plane_form;
-            pl.zrow0 = -1;
-            for (int j = 0; j < M.nz; ++j)
-                if (-(double)cfg->zmax + (double)j * pl.dz == 0.0) pl.zrow0 = j;
+        const bool z0 = whiten_z0_usable(cfg, fa.whiten_form);
+        if (z0) {
+            fa.z0_plane = (float*)ctx->plane.p;
+            fa.z0_plane_stride = (int64_t)M.nz * nfft;
+            fa.z0_scale1 = (const float*)((const int32_t*)ctx->tapinfo.p + 3 * M.nz) + 1;
+            fa.wscale = (float*)ctx->spec.p;
         }
-        {
-            ProfScope ps(ctx, 4, s);
-            PSS_CUDA(launch_plane(pl, s));
+        PSS_CUDA(launch_fft_whiten(fa, s, ctx));
+        if (!z0) {
+            PlaneArgs pl{};
+            pl.spec = (const float2*)ctx->spec.p;
+            pl.spec_stride = Mh;
+            pl.nfft = nfft;
+            pl.nb = b.nrows;
+            pl.plane = (float*)ctx->plane.p;
+            pl.plane_stride = (int64_t)M.nz * nfft;
+            pl.zmax = cfg->zmax;
+            pl.dz = cfg->zmax ? cfg->dz : 1.0;
+            pl.extra = cfg->halfwidth_extra;
+            pl.taps = (const float2*)ctx->taps.p;
+            const int32_t* info = (const int32_t*)ctx->tapinfo.p;
+            pl.tap_off = info;
+            pl.tap_m = info + 2 * M.nz;
+            pl.tap_scale = (const float*)(info + 3 * M.nz);
+            pl.ftaps = nullptr;
+            if (ctx->ftap_ok && plane_fft_usable(cfg->zmax, cfg->halfwidth_extra, Mh)) {
+                const int mmax = (cfg->zmax + 1) / 2 + cfg->halfwidth_extra;
+                pl.ftaps = (const float2*)ctx->ftaps.p;
+                pl.fL = PLANE_FFT_L;
+                pl.fM0 = mmax - 1;
+                pl.fV = PLANE_FFT_L - 2 * mmax + 1;
+                pl.tw = (const float2*)ctx->twid.p;
+                pl.twM = ctx->twid_n;
+                pl.nz = M.nz;
+                pl.form = ctx->tune.plane_form;
+                pl.zrow0 = -1;
+                for (int j = 0; j < M.nz; ++j)
+                    if (-(double)cfg->zmax + (double)j * pl.dz == 0.0) pl.zrow0 = j;
+            }
+            {
+                ProfScope ps(ctx, 4, s);
+                PSS_CUDA(launch_plane(pl, s));
+            }
         }
         HarmArgs ha{};
         for (int k = 0; k < 6; ++k) ha.thr[k] = M.thr[k];

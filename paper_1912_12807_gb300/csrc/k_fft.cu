@@ -885,6 +885,143 @@ __global__ void __launch_bounds__(64 * WP, 4) k_whiten_pair(const float2* Zall, 
     whiten_block_pair<VPL>(A, k0, h, lane, k0 == 0 ? W - 1 : W, s_sh[pr], 1 + pr, whiten, g, O + k0);
 }
 
+// Whitening and the zmax 0 plane (the 32-tap half-bin interpolation of
+// k_plane_z0) in one pass over the spectrum.  A CTA of WP warp pairs whitens
+// WP consecutive blocks as k_whiten_pair does, stores each block's scale,
+// puts the whitened bins of its range K0 .. K0 + WP W into shared memory
+// (over the pairs' histograms, after a block barrier) and computes the plane
+// values of its range whose windows (bins k - 15 .. k + 16) lie inside the
+// range or reach past an end of the spectrum (zero there).  The 31 values
+// whose windows cross an interior range boundary are left to k_z0_seams.
+// Same operations in the same order as the whitening kernel followed by
+// k_plane_z0 (bit-identical planes); the whitened spectrum never goes to HBM.
+constexpr int Z0TAP = 32;              // 2m taps of the zmax 0 template
+constexpr int Z0H = Z0TAP / 2 - 1;     // taps t = -Z0H .. Z0H + 1 around a bin
+constexpr int Z0R = 8;                 // consecutive outputs per thread and round
+constexpr int SHW = NBIN + 2 * NCAND + 8;
+
+template <int VPL>
+__global__ void __launch_bounds__(64 * WP, 4) k_whiten_z0(const float2* Zall, int64_t z_stride, int64_t M,
+                                                      float* plane, int64_t plane_stride, const float2* tw,
+                                                      int64_t twM, const float* tap_scale1, float* wscale) {
+    constexpr int W = 64 * VPL;
+    constexpr int KB = WP * W;            // bins per CTA
+    constexpr int TW = KB + Z0TAP - 1;    // tile: bins K0 - Z0H .. K0 + KB + Z0H
+    constexpr int TWP = TW + TW / 8 + 1;  // one padding slot every 8 entries
+    constexpr int NTH = 64 * WP;
+    static_assert(2 * TWP <= WP * SHW, "the tile fits in the pairs' whitening scratch");
+    static_assert(KB % Z0R == 0, "whole runs of outputs");
+    __shared__ __align__(16) uint32_t s_raw[WP * SHW];
+    const int lane = threadIdx.x & 31, pr = threadIdx.x >> 6, h = (threadIdx.x >> 5) & 1;
+    const int64_t nblk = M / W;
+    const int64_t blk = (int64_t)blockIdx.x * WP + pr;
+    const bool have = blk < nblk;
+    const int b = blockIdx.y;
+    const int64_t k0 = blk * W;
+    const int64_t K0 = (int64_t)blockIdx.x * KB;
+    const float2* Z = Zall + (int64_t)b * z_stride;
+    const int64_t wstride = twM / (2 * M);  // exp(-2 pi i k / nfft)
+    float2 A[VPL];
+    if (have) {
+#pragma unroll
+        for (int i = 0; i < VPL; ++i) {
+            const int64_t k = k0 + h * 32 * VPL + lane + 32 * i;
+            A[i] = r2c_bin(Z[k], Z[(M - k) & (M - 1)], tw[k * wstride], k);
+        }
+        const float scale = whiten_block_pair<VPL>(A, k0, h, lane, k0 == 0 ? W - 1 : W, s_raw + pr * SHW, 1 + pr, 1,
+                                                   nullptr, nullptr);
+        if (h == 0 && lane == 0) wscale[(int64_t)b * nblk + blk] = scale;
+    }
+    __syncthreads();  // every pair is done with its histogram
+    float2* tile = reinterpret_cast<float2*>(s_raw);
+    if (have) {
+#pragma unroll
+        for (int i = 0; i < VPL; ++i) {
+            const int u = (int)(k0 - K0) + h * 32 * VPL + lane + 32 * i + Z0H;
+            tile[u + (u >> 3)] = A[i];
+        }
+    }
+    for (int u = threadIdx.x; u < TW; u += NTH) {
+        const int64_t k = K0 - Z0H + u;
+        if (k < K0 || k >= K0 + KB || k >= M) tile[u + (u >> 3)] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const float s1 = *tap_scale1;
+    float2* P = reinterpret_cast<float2*>(plane + (int64_t)b * plane_stride);
+    // outputs whose windows cross an interior boundary of the CTA ranges
+    const int64_t lo_ok = K0 > 0 ? K0 + Z0H : K0;
+    const int64_t hi_ok = K0 + KB < M ? K0 + KB - Z0H - 1 : M;
+#pragma unroll 1
+    for (int ub = (int)threadIdx.x * Z0R; ub < KB; ub += NTH * Z0R) {  // ub: tile index of the first window
+        float re[Z0R], im[Z0R], p0[Z0R];
+#pragma unroll
+        for (int i = 0; i < Z0R; ++i) re[i] = im[i] = p0[i] = 0.f;
+        const float2* w = tile + ub + (ub >> 3);
+#pragma unroll
+        for (int j = 0; j < Z0R + Z0TAP - 1; ++j) {
+            const float2 x = w[j + (j >> 3)];
+#pragma unroll
+            for (int i = 0; i < Z0R; ++i) {
+                const int ti = j - i;
+                if (ti >= 0 && ti < Z0TAP) {
+                    re[i] = fmaf(x.x, z0_tap<Z0TAP>(ti), re[i]);
+                    im[i] = fmaf(x.y, z0_tap<Z0TAP>(ti), im[i]);
+                }
+                if (ti == Z0H) p0[i] = x.x * x.x + x.y * x.y;
+            }
+        }
+        const int64_t kb = K0 + ub;
+#pragma unroll
+        for (int i = 0; i < Z0R; ++i) {
+            const int64_t k = kb + i;
+            const float r = re[i] * s1, q = im[i] * s1;
+            if (k >= lo_ok && k < hi_ok) P[k] = make_float2(p0[i], r * r + q * q);
+        }
+    }
+}
+
+// The plane values next to the interior boundaries K = c KB (0 < K < M) of
+// k_whiten_z0's ranges: outputs K - Z0H - 1 .. K + Z0H - 1, one warp per
+// boundary, from the bins K - 2 Z0H - 1 .. K + 2 Z0H re-derived from the half
+// spectrum (r2c_bin) times their blocks' scales.  Same arithmetic and order
+// as k_plane_z0.
+constexpr int SEAM_WARPS = 4;
+
+__global__ void __launch_bounds__(32 * SEAM_WARPS) k_z0_seams(const float2* Zall, int64_t z_stride, int64_t M, int W,
+                                                              int KB, float* plane, int64_t plane_stride,
+                                                              const float2* tw, int64_t twM, const float* tap_scale1,
+                                                              const float* wscale) {
+    constexpr int NW = 2 * Z0TAP - 2;  // bins of the 2 Z0H + 1 windows
+    __shared__ float2 win[SEAM_WARPS][NW];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t K = ((int64_t)blockIdx.x * SEAM_WARPS + warp + 1) * KB;
+    if (K >= M) return;  // no block barrier below
+    const int b = blockIdx.y;
+    const float2* Z = Zall + (int64_t)b * z_stride;
+    const float* sc = wscale + (int64_t)b * (M / W);
+    const int64_t wstride = twM / (2 * M);
+    const int64_t kw = K - 2 * Z0H - 1;  // first bin of the windows (>= 1: K >= KB >= 256)
+    for (int j = lane; j < NW; j += 32) {
+        const int64_t k = kw + j;
+        const float2 a = r2c_bin(Z[k], Z[(M - k) & (M - 1)], tw[k * wstride], k);
+        const float s = sc[k / W];
+        win[warp][j] = make_float2(a.x * s, a.y * s);
+    }
+    __syncwarp();
+    if (lane >= 2 * Z0H + 1) return;
+    float re = 0.f, im = 0.f, p0 = 0.f;
+#pragma unroll
+    for (int ti = 0; ti < Z0TAP; ++ti) {
+        const float2 x = win[warp][lane + ti];
+        re = fmaf(x.x, z0_tap<Z0TAP>(ti), re);
+        im = fmaf(x.y, z0_tap<Z0TAP>(ti), im);
+        if (ti == Z0H) p0 = x.x * x.x + x.y * x.y;
+    }
+    const float s1 = *tap_scale1;
+    const float r = re * s1, q = im * s1;
+    reinterpret_cast<float2*>(plane + (int64_t)b * plane_stride)[K - Z0H - 1 + lane] = make_float2(p0, r * r + q * q);
+}
+
 // Pass radices of an M-point FFT, M = 2^L: the fewest passes of radix
 // 2^5 .. 2^10 (ceil(L / 10)); variant 0 splits L evenly, larger parts
 // first; variants 1.. are the other splits of L into that many parts within
@@ -989,6 +1126,34 @@ cudaError_t launch_fft_whiten(const FftArgs& a, cudaStream_t s, Ctx* prof_ctx) {
     }
     const int W = a.whiten_block;
     if (W < 64 || W > 4096 || (W & (W - 1)) != 0 || M % W != 0) return cudaErrorInvalidValue;
+    if (a.z0_plane && a.whiten && !a.gains_out && (W == 1024 || W == 512 || W == 256)) {
+        // whitening + zmax 0 plane, then the values at the CTA range boundaries
+        if (!a.z0_scale1 || !a.wscale) return cudaErrorInvalidValue;
+        const int KB = WP * W;
+        dim3 g2((unsigned)((M / W + WP - 1) / WP), (unsigned)a.nb);
+        // both kernels are profiled as the whitening stage (the plane stage then has no launches)
+        ProfScope ps(prof_ctx, 3, s);
+        {
+            if (W == 1024)
+                k_whiten_z0<16><<<g2, 64 * WP, 0, s>>>(in, M, M, a.z0_plane, a.z0_plane_stride, a.tw, a.twM,
+                                                       a.z0_scale1, a.wscale);
+            else if (W == 512)
+                k_whiten_z0<8><<<g2, 64 * WP, 0, s>>>(in, M, M, a.z0_plane, a.z0_plane_stride, a.tw, a.twM,
+                                                      a.z0_scale1, a.wscale);
+            else
+                k_whiten_z0<4><<<g2, 64 * WP, 0, s>>>(in, M, M, a.z0_plane, a.z0_plane_stride, a.tw, a.twM,
+                                                      a.z0_scale1, a.wscale);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+        const int64_t nseam = (M - 1) / KB;  // boundaries K = c KB, 0 < K < M
+        if (nseam > 0) {
+            dim3 g3((unsigned)((nseam + SEAM_WARPS - 1) / SEAM_WARPS), (unsigned)a.nb);
+            k_z0_seams<<<g3, 32 * SEAM_WARPS, 0, s>>>(in, M, M, W, KB, a.z0_plane, a.z0_plane_stride, a.tw, a.twM,
+                                                      a.z0_scale1, a.wscale);
+        }
+        return cudaGetLastError();
+    }
     if (a.whiten_form == 2 && (W == 1024 || W == 512 || W == 256)) {
         dim3 g2((unsigned)((M / W + WP - 1) / WP), (unsigned)a.nb);
         ProfScope ps(prof_ctx, 3, s);

@@ -482,6 +482,12 @@ struct FftArgs {
     const float2* ptw[4];             // inter-pass twiddle tables of passes 1.. (fft_pass_plan)
     int32_t fft_variant;              // pass split (fft_pass_plan variant)
     int32_t whiten_form;              // 0: block-per-CTA median, 1: warp-per-block, 2: warp pair per block
+    // nullable: whiten and write the zmax 0 plane (2m = 32 taps) here in one pass
+    // (whitening blocks of 256, 512 or 1024 bins); the spectrum is then not written
+    float* z0_plane;                  // [nb][z0_plane_stride] float2 (|A_k|^2, half-bin power) per bin
+    int64_t z0_plane_stride;
+    const float* z0_scale1;           // the half-bin taps' normalisation (tap_scale[1])
+    float* wscale;                    // [nb][M / whiten_block] scratch: each block's scale
 };
 cudaError_t launch_twiddles(float2* tw, int64_t n, cudaStream_t s);
 // Radices of the passes of an M-point FFT for split `variant` (0 = default);

@@ -165,12 +165,13 @@ __device__ __forceinline__ void whiten_block(float2 (&A)[VPL], int64_t k0, int l
 // selected element, the scale and the output are those of whiten_block on
 // the same 2*32*VPL bins (positions h*32*VPL + l + 32 i order ties the same
 // way).  The pair synchronises with named barrier `bar` (64 threads).
-// sh: NBIN + 2*NCAND + 8 words of shared memory for the pair.
+// sh: NBIN + 2*NCAND + 8 words of shared memory for the pair.  With Oblk
+// null the scaled bins stay in A.  Returns the scale.
 __device__ __forceinline__ void pair_sync(int bar) { asm volatile("bar.sync %0, 64;" ::"r"(bar) : "memory"); }
 
 template <int VPL>
-__device__ __forceinline__ void whiten_block_pair(float2 (&A)[VPL], int64_t k0, int h, int lane, int m, uint32_t* sh,
-                                                  int bar, int whiten, float* gain_out, float2* Oblk) {
+__device__ __forceinline__ float whiten_block_pair(float2 (&A)[VPL], int64_t k0, int h, int lane, int m, uint32_t* sh,
+                                                   int bar, int whiten, float* gain_out, float2* Oblk) {
     uint32_t* hist = sh;
     uint32_t* cand = sh + NBIN;
     uint32_t* cpos = cand + NCAND;
@@ -283,8 +284,14 @@ __device__ __forceinline__ void whiten_block_pair(float2 (&A)[VPL], int64_t k0, 
     }
     pair_sync(bar);
     const float scale = __uint_as_float(misc[5]);
+    if (Oblk) {
 #pragma unroll
-    for (int i = 0; i < VPL; ++i) Oblk[h * 32 * VPL + lane + 32 * i] = make_float2(A[i].x * scale, A[i].y * scale);
+        for (int i = 0; i < VPL; ++i) Oblk[h * 32 * VPL + lane + 32 * i] = make_float2(A[i].x * scale, A[i].y * scale);
+    } else {
+#pragma unroll
+        for (int i = 0; i < VPL; ++i) A[i] = make_float2(A[i].x * scale, A[i].y * scale);
+    }
+    return scale;
 }
 
 }  // namespace pss

@@ -1,7 +1,8 @@
 """Alternative kernel forms chosen per process (environment) give the same
 bytes: the double- and single-buffered FFT passes (PSS_FFT_DB, with the
 shared-memory sub-stage passes, PSS_FFT_RR=0) and zmax 0 plane kernels
-(PSS_PLANE_Z0_DB).  The register-radix FFT passes (PSS_FFT_RR=1, the
+(PSS_PLANE_Z0_DB), and the whitening fused with the zmax 0 plane against
+the two kernels (PSS_WHITEN_Z0).  The register-radix FFT passes (PSS_FFT_RR=1, the
 default) round differently: both FFT forms are compared with the oracle."""
 import os
 import subprocess
@@ -63,6 +64,39 @@ def test_fft_register_and_shared_forms_match_oracle(tmp_path, nsamp):
         spec = got[: 2 * 40 * M].view(np.complex64)
         for i in range(40):
             check_powers(np.abs(spec[i * M:(i + 1) * M]) ** 2, refs[i], "%s form, trial %d" % (tag, i))
+
+
+CHILD_Z0 = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, {root!r})
+from paper_1912_12807_gb300 import pss, synth
+out = []
+for nsamp, W in {cases!r}:
+    wl = synth.workload_small(nsamp=nsamp)
+    ctx = pss.Context(0)
+    plan = pss.Plan(pss.FilDesc.of(wl.fil), wl.stages)
+    cfg = pss.search_cfg(zmax=0, numharm=8, whiten_block=W)
+    d = torch.from_numpy(wl.fil.data).cuda()
+    out.append(pss.pss_power_plane(ctx, plan, d, cfg, 0, 40).cpu().numpy().ravel().view(np.uint8))
+    out.append(pss.pss_search_dm_batch(ctx, plan, d, cfg, 0, plan.ndm).view(np.uint8))
+    ctx.close()
+np.save({out!r}, np.concatenate(out))
+"""
+
+
+def test_whitening_fused_with_zmax0_plane_is_bit_identical(tmp_path):
+    # whitening blocks of 1024, 512 and 256 bins (4 blocks per CTA range: several interior range
+    # boundaries), a ragged series, and a spectrum of two blocks (a CTA with idle warp pairs)
+    cases = [(1 << 16, 1024), ((1 << 16) + 12345, 512), (1 << 15, 256), (3000, 1024)]
+    outs = []
+    for tag, v in (("fused", "1"), ("separate", "0")):
+        out = str(tmp_path / ("z0_%s.npy" % tag))
+        env = dict(os.environ)
+        env["PSS_WHITEN_Z0"] = v
+        subprocess.run([sys.executable, "-c", CHILD_Z0.format(root=ROOT, cases=cases, out=out)], env=env,
+                       check=True, timeout=600)
+        outs.append(np.load(out))
+    assert outs[0].size > 0 and outs[0].tobytes() == outs[1].tobytes()
 
 
 CHILD_DD = r"""
