@@ -1041,11 +1041,8 @@ namespace {
 
 // A kernel's bounded wait expired since the flag was last cleared: report it
 // (and clear it).
-pss_status check_errflag(pss_ctx* ctx, cudaStream_t s) {
-    if (!ctx->errflag.p) return PSS_OK;
-    int flag = 0;
-    PSS_CUDA(cudaMemcpyAsync(&flag, ctx->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-    PSS_CUDA(cudaStreamSynchronize(s));
+// The status a read of the error flag gives (and the flag cleared on s).
+pss_status errflag_status(pss_ctx* ctx, int flag, cudaStream_t s) {
     if (flag) {
         PSS_CUDA(cudaMemsetAsync(ctx->errflag.p, 0, sizeof(int), s));
         if (flag == 1) return fail(PSS_ETIMEOUT, "a kernel's bounded wait on its staging barrier expired; results discarded");
@@ -1054,10 +1051,20 @@ pss_status check_errflag(pss_ctx* ctx, cudaStream_t s) {
     return PSS_OK;
 }
 
+pss_status check_errflag(pss_ctx* ctx, cudaStream_t s) {
+    if (!ctx->errflag.p) return PSS_OK;
+    int flag = 0;
+    PSS_CUDA(cudaMemcpyAsync(&flag, ctx->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PSS_CUDA(cudaStreamSynchronize(s));
+    return errflag_status(ctx, flag, s);
+}
+
 // Trials per DM batch of a pipelined search of n trials: three batches of
 // 30 % and a last one of about 10 % (at least 256 trials in all), so that
 // the host sift of all but the last overlaps the device work and the sift
-// left after the device finishes is short; two batches from 64 trials.
+// left after the device finishes is short; two batches from 64 trials.  (A
+// last batch of 5 % is shorter on the device than the host sift of the
+// batch before it, which then ends later.)
 int64_t pipeline_batch(int64_t n) { return n >= 256 ? (3 * n + 9) / 10 : (n >= 64 ? (n + 1) / 2 : 0); }
 
 // Events and pinned count slots for n DM batches, and a stream for downloads.
@@ -1147,16 +1154,24 @@ pss_status search_pipelined(pss_ctx* ctx, const pss_plan* plan, const pss_fil_de
         PSS_TRY(setup_path(ctx, plan, fil, cfg, dm_begin, dm_end, MODE_SEARCH, s, cap, &P, pipeline_batch(n)));
         const uint8_t* src = nullptr;
         PSS_TRY(upload_input(ctx, fil, data, on_dev, s, &src));
-        PSS_TRY(ensure_snapshots(ctx, (int)P.batches.size()));
+        // one pinned slot per DM batch for its detection count, and one for the error flag
+        const size_t nb = P.batches.size();
+        PSS_TRY(ensure_snapshots(ctx, (int)nb + 1));
         PSS_TRY(enqueue_path(ctx, plan, fil, src, cfg, dm_begin, P, MODE_SEARCH, Outputs(), s, true));
+        if (ctx->errflag.p)
+            PSS_CUDA(cudaMemcpyAsync(ctx->batch_cnt + nb, ctx->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         tm.mark("enqueue");
         std::vector<SiftItem> surv;
         bool overflow = false;
         unsigned long long total = 0;
-        PSS_TRY(drain_batches(ctx, plan, cfg, P.batches.size(), cap, &surv, &overflow, &total));
+        PSS_TRY(drain_batches(ctx, plan, cfg, nb, cap, &surv, &overflow, &total));
         PSS_CUDA(cudaStreamSynchronize(s));
         tm.mark("gpu+within");
-        PSS_TRY(check_errflag(ctx, s));
+        if (ctx->errflag.p) {
+            int flag = 0;
+            memcpy(&flag, ctx->batch_cnt + nb, sizeof(int));
+            PSS_TRY(errflag_status(ctx, flag, s));
+        }
         if (!overflow) {
             PSS_TRY(sift_across(*plan, *cfg, surv, out));
             tm.mark("across");

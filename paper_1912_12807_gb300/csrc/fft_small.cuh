@@ -103,6 +103,12 @@ __host__ __device__ __forceinline__ int fp(int i) {
 // the run number.
 __host__ __device__ __forceinline__ int fx(int i) { return (i & ~15) | ((i & 15) ^ ((i >> 4) & 15)); }
 
+// |x|^2 with a fixed rounding: x.x^2 rounded, then x.y^2 added by one fused
+// multiply-add, so that every kernel forming a power gets the same bits
+// whatever the compiler would otherwise contract.
+__device__ __forceinline__ float pow2(float2 x) { return fmaf(x.y, x.y, __fmul_rn(x.x, x.x)); }
+__device__ __forceinline__ float pow2(float re, float im) { return fmaf(im, im, __fmul_rn(re, re)); }
+
 // Odd half-bin tap i of the z = 0 template with 2m = NTAP taps: the
 // imaginary part of conj(rho(1/2 - t, 0)) with t = i - (m - 1), which is
 // 1 / (pi (t - 1/2)) (its real part is zero), rounded to FP32 at compile time.

@@ -369,15 +369,17 @@ pss_status sift_across(const Plan& P, const pss_search_cfg& cfg, std::vector<Sif
     parallel_for(ng, 64, [&](int64_t g) {
         const int* mem = G.members.data() + G.start[g];
         const int nm = G.start[g + 1] - G.start[g];
-        const int best = pick_rep(survivors, mem, nm, true);
         int hits = 1;
         if (nm > 1) {
-            std::vector<int32_t> dms((size_t)nm);
+            thread_local std::vector<int32_t> dms;  // reused: no allocation per group
+            dms.resize((size_t)nm);
             for (int q = 0; q < nm; ++q) dms[(size_t)q] = survivors[mem[q]].dm_idx;
             std::sort(dms.begin(), dms.end());
             hits = (int)(std::unique(dms.begin(), dms.end()) - dms.begin());
         }
+        // groups seen in too few trials are dropped before any sigma is evaluated
         if (hits < cfg.min_dm_hits) return;
+        const int best = pick_rep(survivors, mem, nm, true);
         const Item& b = survivors[best];
         pss_cand& c = reps[(size_t)g];
         c.dm_idx = b.dm_idx;

@@ -691,7 +691,7 @@ __global__ void __launch_bounds__(256) k_r2c_whiten(const float2* Zall, int64_t 
         float2 a = make_float2(sum.x + wd.y, sum.y - wd.x);  // sum - i * w * dif
         if (k == 0) a = make_float2(0.f, 0.f);
         A[e] = a;
-        const float p = a.x * a.x + a.y * a.y;
+        const float p = pow2(a);
         key[threadIdx.x + e * nt] = (k == 0) ? 0xFFFFFFFFu : __float_as_uint(p);
     }
     if (!whiten && !gains) {
@@ -712,7 +712,9 @@ __global__ void __launch_bounds__(256) k_r2c_whiten(const float2* Zall, int64_t 
     const int BPT = NBIN / nt;
     {
         uint32_t tot = 0;
-        for (int i = 0; i < BPT; ++i) tot += hist[threadIdx.x * BPT + i];
+        // each thread starts at a different bin of its run so that a warp's reads fall in distinct banks
+        const int rot = (int)threadIdx.x / (BPT >= 32 ? 1 : 32 / BPT);
+        for (int i = 0; i < BPT; ++i) tot += hist[threadIdx.x * BPT + ((i + rot) & (BPT - 1))];
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
         uint32_t incl = tot;
         for (int off = 1; off < 32; off <<= 1) {
@@ -898,6 +900,7 @@ __global__ void __launch_bounds__(64 * WP, 4) k_whiten_pair(const float2* Zall, 
 constexpr int Z0TAP = 32;              // 2m taps of the zmax 0 template
 constexpr int Z0H = Z0TAP / 2 - 1;     // taps t = -Z0H .. Z0H + 1 around a bin
 constexpr int Z0R = 8;                 // consecutive outputs per thread and round
+constexpr int Z0S = Z0R == 16 ? 4 : 3; // one padding slot every 2^Z0S tile entries (conflict-free runs)
 constexpr int SHW = NBIN + 2 * NCAND + 8;
 
 template <int VPL>
@@ -906,8 +909,8 @@ __global__ void __launch_bounds__(64 * WP, 4) k_whiten_z0(const float2* Zall, in
                                                       int64_t twM, const float* tap_scale1, float* wscale) {
     constexpr int W = 64 * VPL;
     constexpr int KB = WP * W;            // bins per CTA
-    constexpr int TW = KB + Z0TAP - 1;    // tile: bins K0 - Z0H .. K0 + KB + Z0H
-    constexpr int TWP = TW + TW / 8 + 1;  // one padding slot every 8 entries
+    constexpr int TW = KB + Z0TAP - 1;     // tile: bins K0 - Z0H .. K0 + KB + Z0H
+    constexpr int TWP = TW + (TW >> Z0S) + 1;
     constexpr int NTH = 64 * WP;
     static_assert(2 * TWP <= WP * SHW, "the tile fits in the pairs' whitening scratch");
     static_assert(KB % Z0R == 0, "whole runs of outputs");
@@ -938,12 +941,12 @@ __global__ void __launch_bounds__(64 * WP, 4) k_whiten_z0(const float2* Zall, in
 #pragma unroll
         for (int i = 0; i < VPL; ++i) {
             const int u = (int)(k0 - K0) + h * 32 * VPL + lane + 32 * i + Z0H;
-            tile[u + (u >> 3)] = A[i];
+            tile[u + (u >> Z0S)] = A[i];
         }
     }
     for (int u = threadIdx.x; u < TW; u += NTH) {
         const int64_t k = K0 - Z0H + u;
-        if (k < K0 || k >= K0 + KB || k >= M) tile[u + (u >> 3)] = make_float2(0.f, 0.f);
+        if (k < K0 || k >= K0 + KB || k >= M) tile[u + (u >> Z0S)] = make_float2(0.f, 0.f);
     }
     __syncthreads();
     const float s1 = *tap_scale1;
@@ -956,10 +959,10 @@ __global__ void __launch_bounds__(64 * WP, 4) k_whiten_z0(const float2* Zall, in
         float re[Z0R], im[Z0R], p0[Z0R];
 #pragma unroll
         for (int i = 0; i < Z0R; ++i) re[i] = im[i] = p0[i] = 0.f;
-        const float2* w = tile + ub + (ub >> 3);
+        const float2* w = tile + ub + (ub >> Z0S);
 #pragma unroll
         for (int j = 0; j < Z0R + Z0TAP - 1; ++j) {
-            const float2 x = w[j + (j >> 3)];
+            const float2 x = w[j + (j >> Z0S)];
 #pragma unroll
             for (int i = 0; i < Z0R; ++i) {
                 const int ti = j - i;
@@ -967,7 +970,7 @@ __global__ void __launch_bounds__(64 * WP, 4) k_whiten_z0(const float2* Zall, in
                     re[i] = fmaf(x.x, z0_tap<Z0TAP>(ti), re[i]);
                     im[i] = fmaf(x.y, z0_tap<Z0TAP>(ti), im[i]);
                 }
-                if (ti == Z0H) p0[i] = x.x * x.x + x.y * x.y;
+                if (ti == Z0H) p0[i] = pow2(x);
             }
         }
         const int64_t kb = K0 + ub;
@@ -975,7 +978,7 @@ __global__ void __launch_bounds__(64 * WP, 4) k_whiten_z0(const float2* Zall, in
         for (int i = 0; i < Z0R; ++i) {
             const int64_t k = kb + i;
             const float r = re[i] * s1, q = im[i] * s1;
-            if (k >= lo_ok && k < hi_ok) P[k] = make_float2(p0[i], r * r + q * q);
+            if (k >= lo_ok && k < hi_ok) P[k] = make_float2(p0[i], pow2(r, q));
         }
     }
 }
@@ -1015,11 +1018,11 @@ __global__ void __launch_bounds__(32 * SEAM_WARPS) k_z0_seams(const float2* Zall
         const float2 x = win[warp][lane + ti];
         re = fmaf(x.x, z0_tap<Z0TAP>(ti), re);
         im = fmaf(x.y, z0_tap<Z0TAP>(ti), im);
-        if (ti == Z0H) p0 = x.x * x.x + x.y * x.y;
+        if (ti == Z0H) p0 = pow2(x);
     }
     const float s1 = *tap_scale1;
     const float r = re * s1, q = im * s1;
-    reinterpret_cast<float2*>(plane + (int64_t)b * plane_stride)[K - Z0H - 1 + lane] = make_float2(p0, r * r + q * q);
+    reinterpret_cast<float2*>(plane + (int64_t)b * plane_stride)[K - Z0H - 1 + lane] = make_float2(p0, pow2(r, q));
 }
 
 // Pass radices of an M-point FFT, M = 2^L: the fewest passes of radix

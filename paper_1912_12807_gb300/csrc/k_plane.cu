@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(NT) k_plane(PlaneArgs a) {
         float p0, p1;
         if (z0) {
             const float2 c = w[m - 1];
-            p0 = c.x * c.x + c.y * c.y;
+            p0 = pow2(c);
             float re = 0.f, im = 0.f;
             for (int i = 0; i < 2 * m; ++i) {
                 const float gy = g1[i].y;
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(NT) k_plane(PlaneArgs a) {
             }
             re *= s1;
             im *= s1;
-            p1 = re * re + im * im;
+            p1 = pow2(re, im);
         } else {
             float r0 = 0.f, i0 = 0.f, r1 = 0.f, i1 = 0.f;
             for (int i = 0; i < 2 * m; ++i) {
@@ -114,8 +114,8 @@ __global__ void __launch_bounds__(NT) k_plane(PlaneArgs a) {
                 i1 = fmaf(x.y, v.x, i1);
             }
             r0 *= s0; i0 *= s0; r1 *= s1; i1 *= s1;
-            p0 = r0 * r0 + i0 * i0;
-            p1 = r1 * r1 + i1 * i1;
+            p0 = pow2(r0, i0);
+            p1 = pow2(r1, i1);
         }
         reinterpret_cast<float2*>(P)[k] = make_float2(p0, p1);
     }
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(NT) k_plane_z0(PlaneArgs a) {
                 re[i] = fmaf(x.x, z0_tap<NTAP>(ti), re[i]);
                 im[i] = fmaf(x.y, z0_tap<NTAP>(ti), im[i]);
             }
-            if (ti == H) p0[i] = x.x * x.x + x.y * x.y;
+            if (ti == H) p0[i] = pow2(x);
         }
     }
     float2* P = reinterpret_cast<float2*>(a.plane + (int64_t)b * a.plane_stride);
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(NT) k_plane_z0(PlaneArgs a) {
 #pragma unroll
     for (int i = 0; i < R; ++i) {
         const float r = re[i] * s1, q = im[i] * s1;
-        if (kb + i < M) P[kb + i] = make_float2(p0[i], r * r + q * q);
+        if (kb + i < M) P[kb + i] = make_float2(p0[i], pow2(r, q));
     }
 }
 
@@ -221,14 +221,14 @@ __global__ void __launch_bounds__(NT) k_plane_z0_db(PlaneArgs a, int tpc) {
                     re[i] = fmaf(x.x, z0_tap<NTAP>(ti), re[i]);
                     im[i] = fmaf(x.y, z0_tap<NTAP>(ti), im[i]);
                 }
-                if (ti == H) p0[i] = x.x * x.x + x.y * x.y;
+                if (ti == H) p0[i] = pow2(x);
             }
         }
         const int64_t kb = t * KB0 + (int64_t)threadIdx.x * R;
 #pragma unroll
         for (int i = 0; i < R; ++i) {
             const float r = re[i] * s1, q = im[i] * s1;
-            if (kb + i < M) P[kb + i] = make_float2(p0[i], r * r + q * q);
+            if (kb + i < M) P[kb + i] = make_float2(p0[i], pow2(r, q));
         }
         __syncthreads();
     }
@@ -408,13 +408,13 @@ __global__ void __launch_bounds__(FNT, 3) k_plane_fft(const __grid_constant__ Pl
             const int64_t k = k0 + u;
             if (u < V && k < M) {
                 const float2 y0 = Y0[fp(u)], y1 = Y1[fp(u)];
-                float p0 = y0.x * y0.x + y0.y * y0.y;
+                float p0 = pow2(y0);
                 if (zrow0) {
                     // integer half-bins of the z = 0 row: the raw powers, exactly
                     const float2 c = Ap[k];
-                    p0 = c.x * c.x + c.y * c.y;
+                    p0 = pow2(c);
                 }
-                row[k] = make_float2(p0, y1.x * y1.x + y1.y * y1.y);
+                row[k] = make_float2(p0, pow2(y1));
             }
         }
         __syncthreads();
@@ -559,12 +559,12 @@ __global__ void __launch_bounds__(F16NT, 4) k_plane_fft16(const __grid_constant_
                     const int u = bb + q * NS;
                     const int64_t k = k0 + u;
                     if (u < V && k < M) {
-                        float p0 = x0[q].x * x0[q].x + x0[q].y * x0[q].y;
+                        float p0 = pow2(x0[q]);
                         if (zrow0) {
                             const float2 c = Ap[k];
-                            p0 = c.x * c.x + c.y * c.y;
+                            p0 = pow2(c);
                         }
-                        row[k] = make_float2(p0, x1[q].x * x1[q].x + x1[q].y * x1[q].y);
+                        row[k] = make_float2(p0, pow2(x1[q]));
                     }
                 }
             }

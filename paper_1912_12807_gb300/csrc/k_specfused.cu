@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(FT, 1) k_spec_cluster(const __grid_constant__ 
                     re[i] = fmaf(xv.x, z0_tap<NTAP>(ti), re[i]);
                     im[i] = fmaf(xv.y, z0_tap<NTAP>(ti), im[i]);
                 }
-                if (ti == NTAP / 2 - 1) p0[i] = xv.x * xv.x + xv.y * xv.y;
+                if (ti == NTAP / 2 - 1) p0[i] = pow2(xv);
             }
         }
         float2* P = reinterpret_cast<float2*>(a.plane + (int64_t)b * a.plane_stride);
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(FT, 1) k_spec_cluster(const __grid_constant__ 
 #pragma unroll
         for (int i = 0; i < RUN; ++i) {
             const float rr = re[i] * s1, qq = im[i] * s1;
-            P[kb + i] = make_float2(p0[i], rr * rr + qq * qq);
+            P[kb + i] = make_float2(p0[i], pow2(rr, qq));
         }
     }
 }

@@ -36,7 +36,7 @@ __device__ __forceinline__ void whiten_block(float2 (&A)[VPL], int64_t k0, int l
                                              uint32_t* cand, uint32_t* cpos, int whiten, float* gain_out,
                                              float2* Oblk) {
     auto keyof = [&](int i) -> uint32_t {
-        return (k0 == 0 && lane == 0 && i == 0) ? 0xFFFFFFFFu : __float_as_uint(A[i].x * A[i].x + A[i].y * A[i].y);
+        return (k0 == 0 && lane == 0 && i == 0) ? 0xFFFFFFFFu : __float_as_uint(pow2(A[i]));
     };
     __syncwarp();
     for (int i = lane; i < NBIN; i += 32) hist[i] = 0u;
@@ -52,7 +52,7 @@ __device__ __forceinline__ void whiten_block(float2 (&A)[VPL], int64_t k0, int l
     constexpr int BPL = NBIN / 32;
     uint32_t tot = 0;
 #pragma unroll 8
-    for (int i = 0; i < BPL; ++i) tot += hist[lane * BPL + i];
+    for (int i = 0; i < BPL; ++i) tot += hist[lane * BPL + ((i + lane) & (BPL - 1))];  // rotated: no bank conflicts
     uint32_t incl = tot;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -178,7 +178,7 @@ __device__ __forceinline__ float whiten_block_pair(float2 (&A)[VPL], int64_t k0,
     uint32_t* misc = cpos + NCAND;  // [0] warp-0 total, [1] bin, [2] rank, [3] slots, [4] value, [5] scale bits
     const int t = h * 32 + lane;     // 0..63
     auto keyof = [&](int i) -> uint32_t {
-        return (k0 == 0 && t == 0 && i == 0) ? 0xFFFFFFFFu : __float_as_uint(A[i].x * A[i].x + A[i].y * A[i].y);
+        return (k0 == 0 && t == 0 && i == 0) ? 0xFFFFFFFFu : __float_as_uint(pow2(A[i]));
     };
     for (int i = t; i < NBIN; i += 64) hist[i] = 0u;
     if (t == 0) misc[3] = 0u;
@@ -194,7 +194,7 @@ __device__ __forceinline__ float whiten_block_pair(float2 (&A)[VPL], int64_t k0,
     constexpr int BPT = NBIN / 64;
     uint32_t tot = 0;
 #pragma unroll 8
-    for (int i = 0; i < BPT; ++i) tot += hist[t * BPT + i];
+    for (int i = 0; i < BPT; ++i) tot += hist[t * BPT + ((i + t) & (BPT - 1))];  // rotated: no bank conflicts
     uint32_t incl = tot;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
