@@ -328,7 +328,8 @@ def stage_work(plan, wl, fil_nbytes):
     for ds in sorted({s.ds for k, s in enumerate(wl.stages) if bx_row(plan, wl, k)}):
         mstride = ((N + ds - 1) // ds + 7) // 8 * 8
         bx_b += float(C) * N + 2.0 * C * ds * mstride
-    return {"unpack": ("hbm", 2.0 * fil_nbytes, "bytes"),
+    # unpack: the file read once, one byte per channel and sample written (8x the file for 1-bit data)
+    return {"unpack": ("hbm", float(fil_nbytes) + float(wl.fil.nchan) * wl.fil.nsamp, "bytes"),
             "dedisperse": ("alu", adds, "channel-adds"),
             "bxtable": ("hbm", bx_b, "bytes"),
             "fft": ("hbm", fft_b, "bytes"),

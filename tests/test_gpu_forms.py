@@ -1,8 +1,9 @@
 """Alternative kernel forms chosen per process (environment) give the same
 bytes: the double- and single-buffered FFT passes (PSS_FFT_DB, with the
 shared-memory sub-stage passes, PSS_FFT_RR=0) and zmax 0 plane kernels
-(PSS_PLANE_Z0_DB), and the whitening fused with the zmax 0 plane against
-the two kernels (PSS_WHITEN_Z0).  The register-radix FFT passes (PSS_FFT_RR=1, the
+(PSS_PLANE_Z0_DB), the whitening fused with the zmax 0 plane against
+the two kernels (PSS_WHITEN_Z0), and the unpack kernels for files with
+every channel kept against the tiled one (PSS_PREP_FAST).  The register-radix FFT passes (PSS_FFT_RR=1, the
 default) round differently: both FFT forms are compared with the oracle."""
 import os
 import subprocess
@@ -95,6 +96,38 @@ def test_whitening_fused_with_zmax0_plane_is_bit_identical(tmp_path):
         env["PSS_WHITEN_Z0"] = v
         subprocess.run([sys.executable, "-c", CHILD_Z0.format(root=ROOT, cases=cases, out=out)], env=env,
                        check=True, timeout=600)
+        outs.append(np.load(out))
+    assert outs[0].size > 0 and outs[0].tobytes() == outs[1].tobytes()
+
+
+CHILD_PREP = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, {root!r})
+from paper_1912_12807_gb300 import pss, synth
+out = []
+files = [synth.make_8bit(64, 40000 + 7, 2e-4, 1200.0, 1500.0, [synth.Pulsar(0.02, 30.0, 0.05, 0.5)], seed=5),
+         synth.make_8bit(260, 30000, 2e-4, 1200.0, 1500.0, [], seed=6),
+         synth.make_1bit(96, 50000 + 33, 2.5e-4, 1230.0, 1518.0, [synth.Pulsar(0.02, 100.0, 0.05, 0.1)], seed=7)]
+for fil in files:
+    ctx = pss.Context(0)
+    plan = pss.Plan(pss.FilDesc.of(fil), [synth.Stage(0.0, 2.0, 40, 1)])
+    d = torch.from_numpy(fil.data).cuda()
+    out.append(pss.pss_dedisperse(ctx, plan, d, 0, plan.ndm).cpu().numpy().ravel().view(np.uint8))
+    ctx.close()
+np.save({out!r}, np.concatenate(out))
+"""
+
+
+def test_unpack_forms_are_identical(tmp_path):
+    # 8-bit files of 64 and 260 channels (ragged series) and a 1-bit file of 96 channels: the
+    # register-transpose and ballot unpack kernels against the tiled one, through dedispersion
+    outs = []
+    for tag, v in (("fast", "1"), ("tiled", "0")):
+        out = str(tmp_path / ("prep_%s.npy" % tag))
+        env = dict(os.environ)
+        env["PSS_PREP_FAST"] = v
+        subprocess.run([sys.executable, "-c", CHILD_PREP.format(root=ROOT, out=out)], env=env, check=True,
+                       timeout=600)
         outs.append(np.load(out))
     assert outs[0].size > 0 and outs[0].tobytes() == outs[1].tobytes()
 
