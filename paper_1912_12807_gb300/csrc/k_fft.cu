@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(NT) k_fft_pass(const __grid_constant__ PassArg
             float2 x = make_float2(0.f, 0.f);
             if (j < ncol) {
                 x = in[j + (int64_t)r * ncol];
-                const int64_t k = j % a.Ns;
+                const int64_t k = j & (a.Ns - 1);  // Ns: a power of two
                 // table laid out like the data: consecutive columns read consecutive words
                 if (k && r) x = cmul(x, a.ptw[(int64_t)r * a.Ns + k]);
             }
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(NT) k_fft_pass(const __grid_constant__ PassArg
             const int jj = e % TJ, r = e / TJ;
             const int64_t j = j0 + jj;
             if (j < ncol) {
-                const int64_t k = j % a.Ns;
+                const int64_t k = j & (a.Ns - 1);  // Ns: a power of two
                 o[(j / a.Ns) * a.Ns * R + k + (int64_t)r * a.Ns] = res[r * TJP + jj];
             }
         }
@@ -266,7 +266,7 @@ __device__ __forceinline__ void load_ptw(const PassArgs& a, int64_t j0, float2 (
         const int e = threadIdx.x + i * NT;
         const int jj = e % TJ, r = e / TJ;
         const int64_t j = j0 + jj;
-        const int64_t k = j % a.Ns;
+        const int64_t k = j & (a.Ns - 1);  // Ns: a power of two
         w[i] = (j < ncol && k && r) ? a.ptw[(int64_t)r * a.Ns + k] : make_float2(1.f, 0.f);
     }
 }
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(NT, db_min_blocks<R>()) k_fft_pass_db(const __
                 x = v;
             } else {
                 const int64_t j = j0 + jj;
-                if (j < ncol && (j % a.Ns) && r) x = cmul(x, w[i]);
+                if (j < ncol && (j & (a.Ns - 1)) && r) x = cmul(x, w[i]);
             }
         }
         if constexpr (!FIRST) {
@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(NT, db_min_blocks<R>()) k_fft_pass_db(const __
                 const int jj = e % TJ, r = e / TJ;
                 const int64_t j = j0 + jj;
                 if (j < ncol) {
-                    const int64_t k = j % a.Ns;
+                    const int64_t k = j & (a.Ns - 1);  // Ns: a power of two
                     o[(j / a.Ns) * a.Ns * R + k + (int64_t)r * a.Ns] = res[r * TJP + jj];
                 }
             }
@@ -542,7 +542,7 @@ __global__ void __launch_bounds__(RrPlan<R>::NTR) k_fft_pass_rr(const __grid_con
                             }
                         } else {
                             v = in[n];
-                            const int64_t k = j % a.Ns;
+                            const int64_t k = j & (a.Ns - 1);  // Ns: a power of two
                             if (k && r) v = cmul(v, a.ptw[(int64_t)r * a.Ns + k]);
                         }
                     }
@@ -584,7 +584,7 @@ __global__ void __launch_bounds__(RrPlan<R>::NTR) k_fft_pass_rr(const __grid_con
 #pragma unroll
                         for (int q = 0; q < C; ++q) o[j * R + bb + q * NS] = x[q];
                     } else {
-                        const int64_t kc = j % a.Ns;
+                        const int64_t kc = j & (a.Ns - 1);
                         float2* oo = o + (j / a.Ns) * a.Ns * R + kc;
 #pragma unroll
                         for (int q = 0; q < C; ++q) oo[(int64_t)(bb + q * NS) * a.Ns] = x[q];
