@@ -432,6 +432,9 @@ struct RrPlan {
     static constexpr int C = R / A / (B ? B : 1);
     static constexpr int RT = (R == 32) ? 32 : (R == 64 || R == 128) ? 16 : 8;  // columns per CTA
     static constexpr int NTR = (R >= 512) ? 256 : 128;                       // threads
+    // CTAs per SM the register budget must allow: the counts the compiler reaches by itself,
+    // except radix 128 (the passes of 2^20-2^22-point transforms), held to 48 registers
+    static constexpr int MINB = (R == 32) ? 16 : (R == 64) ? 12 : (R == 128) ? 10 : (R == 256) ? 9 : (R == 512) ? 4 : 2;
     static constexpr int RTP = RT + 1;
     // twiddle entries of the sub-stages after the first: B * A (middle) + C * (R / C)
     static constexpr int TW = (B ? B * A : 0) + R;
@@ -471,7 +474,7 @@ __device__ __forceinline__ void rr_mid(float2* buf, const float2* twt, int ns) {
 }
 
 template <int R, bool FIRST>
-__global__ void __launch_bounds__(RrPlan<R>::NTR) k_fft_pass_rr(const __grid_constant__ PassArgs a) {
+__global__ void __launch_bounds__(RrPlan<R>::NTR, RrPlan<R>::MINB) k_fft_pass_rr(const __grid_constant__ PassArgs a) {
     using P = RrPlan<R>;
     constexpr int A = P::A, B = P::B, C = P::C, RT = P::RT, RTP = P::RTP, NTR = P::NTR;
     extern __shared__ float2 sm[];
