@@ -362,11 +362,13 @@ pss_status sift_across(const Plan& P, const pss_search_cfg& cfg, std::vector<Sif
     };
     const Groups G = link_groups(survivors, cfg.dz);
     lap("link");
-    // one representative per group, groups in parallel (each writes its own slot)
+    // one representative per group, groups in parallel (each writes its own slot); one group
+    // per task: after the within-trial sift the groups are few (about 100 on the drift-scan
+    // file) and the largest span hundreds of trials
     const int ng = G.count();
     std::vector<pss_cand> reps((size_t)ng);
     std::vector<char> keep((size_t)ng, 0);
-    parallel_for(ng, 64, [&](int64_t g) {
+    parallel_for(ng, 1, [&](int64_t g) {
         const int* mem = G.members.data() + G.start[g];
         const int nm = G.start[g + 1] - G.start[g];
         int hits = 1;
