@@ -598,6 +598,208 @@ __global__ void __launch_bounds__(RrPlan<R>::NTR, RrPlan<R>::MINB) k_fft_pass_rr
     }
 }
 
+// ---- register-radix form with staged, double-buffered tiles -----------------
+// The same pass as k_fft_pass_rr, but a CTA walks `tpc` consecutive column
+// tiles of one trial: while it transforms tile t, tile t+1 (and, after the
+// first pass, the tile's inter-pass twiddles, which have the same shape:
+// rows r, columns (j mod Ns) .. + RT) comes into shared memory by
+// asynchronous 8-byte copies (zero-filled past the data).  The first
+// sub-stage reads the landed tile, mean, padding or twiddles applied in
+// registers as k_fft_pass_rr does; the tile's buffer then holds the later
+// sub-stages, and the sub-stage twiddle tables are built once per CTA.
+// Same operations in the same order: bit-identical to k_fft_pass_rr.
+template <int R, bool FIRST>
+struct RrdbPlan {
+    static constexpr int TS = R * RrPlan<R>::RTP;  // float2 per tile buffer
+    static constexpr int NSLOT = FIRST ? 2 : 4;    // tiles x2, and their twiddles x2 after the first pass
+    static constexpr size_t bytes = ((size_t)NSLOT * TS + RrPlan<R>::TW) * sizeof(float2);
+};
+
+template <int R, bool FIRST>
+__global__ void __launch_bounds__(RrPlan<R>::NTR) k_fft_pass_rrdb(const __grid_constant__ PassArgs a, int tpc) {
+    using P = RrPlan<R>;
+    constexpr int A = P::A, B = P::B, C = P::C, RT = P::RT, RTP = P::RTP, NTR = P::NTR;
+    constexpr int TS = RrdbPlan<R, FIRST>::TS;
+    extern __shared__ float2 sm[];
+    float2* twt = sm + RrdbPlan<R, FIRST>::NSLOT * TS;
+    const int b = blockIdx.y;
+    const int64_t ncol = a.M / R;
+    const int64_t ntile = (ncol + RT - 1) / RT;
+    const int64_t tile0 = (int64_t)blockIdx.x * tpc;
+    const int64_t tile1 = min(ntile, tile0 + tpc);
+    const float* sr = FIRST ? a.series + (int64_t)b * a.series_stride : nullptr;
+    const float2* in = FIRST ? nullptr : a.in + (int64_t)b * a.in_stride;
+    const int64_t nv = FIRST ? row_nv(a, b) : 0;
+    // asynchronous copies of tile t (and its twiddles) into slot `slot`
+    auto issue = [&](int64_t t, int slot) {
+        float2* dst = sm + slot * TS;
+        float2* dstw = sm + (2 + slot) * TS;
+        const int64_t j0 = t * RT;
+#pragma unroll 4
+        for (int i = 0; i < (R * RT + NTR - 1) / NTR; ++i) {
+            const int e = threadIdx.x + i * NTR;
+            if ((R * RT) % NTR != 0 && e >= R * RT) break;
+            const int jj = e % RT, r = e / RT;
+            const int64_t j = j0 + jj;
+            const int64_t n = j + (int64_t)r * ncol;
+            if constexpr (FIRST) {
+                // both samples, the first only (the odd tail), or none (zeros)
+                const uint32_t nbytes = (j < ncol && 2 * n + 1 < nv) ? 8u : ((j < ncol && 2 * n < nv) ? 4u : 0u);
+                cp_async8(dst + r * RTP + jj, nbytes ? (const void*)(sr + 2 * n) : (const void*)sr, nbytes);
+            } else {
+                const bool ok = j < ncol;
+                cp_async8(dst + r * RTP + jj, ok ? (const void*)(in + n) : (const void*)in, ok ? 8u : 0u);
+                const int64_t k = j & (a.Ns - 1);  // Ns: a power of two
+                const bool okw = ok && k && r;     // the twiddle is used only there
+                cp_async8(dstw + r * RTP + jj, okw ? (const void*)(a.ptw + (int64_t)r * a.Ns + k) : (const void*)a.ptw,
+                          okw ? 8u : 0u);
+            }
+        }
+    };
+    issue(tile0, 0);
+    cp_async_commit();
+    // sub-stage twiddle tables from the global table exp(-2 pi i t / twM), once per CTA
+    {
+        const int64_t tstride = a.twM / R;
+        int off = 0;
+        if constexpr (B != 0) {
+            for (int i = threadIdx.x; i < B * A; i += NTR) {
+                const int q = i / A, k = i - q * A;
+                twt[i] = a.tw[(int64_t)(q * k * (R / (B * A))) * tstride];
+            }
+            off = B * A;
+        }
+        for (int i = threadIdx.x; i < R; i += NTR) {
+            const int q = i / (R / C), k = i - q * (R / C);
+            twt[off + i] = a.tw[(int64_t)(q * k) * tstride];
+        }
+    }
+    float mu_i = 0.f, mu_f = 0.f;
+    if constexpr (FIRST) {
+        __shared__ float s_mu[2];
+        if (threadIdx.x == 0) {
+            // mean = sum / N_v in FP64 (once per CTA), split as integer + fraction
+            const double mu = (double)a.sums[b] / (double)nv;
+            const double mi = rint(mu);
+            s_mu[0] = (float)mi;
+            s_mu[1] = (float)(mu - mi);
+        }
+        __syncthreads();
+        mu_i = s_mu[0];
+        mu_f = s_mu[1];
+    }
+    float2* o = a.out + (int64_t)b * a.out_stride;
+    for (int64_t t = tile0; t < tile1; ++t) {
+        const int slot = (int)((t - tile0) & 1);
+        float2* buf = sm + slot * TS;
+        const float2* wt = sm + (2 + slot) * TS;
+        if (t + 1 < tile1) {
+            issue(t + 1, slot ^ 1);
+            cp_async_commit();
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();  // tile t has landed (every thread's copies)
+        const int64_t j0 = t * RT;
+        // first sub-stage: radix A from the landed tile, ns = 1
+        {
+            constexpr int NB = R / A * RT;
+            constexpr int PER = (NB + NTR - 1) / NTR;
+            float2 x[PER][A];
+#pragma unroll
+            for (int p = 0; p < PER; ++p) {
+                const int e = threadIdx.x + p * NTR;
+                if (NB % NTR == 0 || e < NB) {
+                    const int jj = e % RT, bb = e / RT;
+                    const int64_t j = j0 + jj;
+#pragma unroll
+                    for (int q = 0; q < A; ++q) {
+                        const int r = bb + q * (R / A);
+                        float2 v = make_float2(0.f, 0.f);
+                        if (j < ncol) {
+                            const float2 w = buf[r * RTP + jj];
+                            if constexpr (FIRST) {
+                                const int64_t n = j + (int64_t)r * ncol;
+                                if (2 * n + 1 < nv) v = make_float2((w.x - mu_i) - mu_f, (w.y - mu_i) - mu_f);
+                                else if (2 * n < nv) v.x = (w.x - mu_i) - mu_f;
+                            } else {
+                                v = w;
+                                const int64_t k = j & (a.Ns - 1);
+                                if (k && r) v = cmul(v, wt[r * RTP + jj]);
+                            }
+                        }
+                        x[p][q] = v;
+                    }
+                    dft_any<A>(x[p]);
+                }
+            }
+            __syncthreads();  // the tile is read: its buffer takes the sub-stage outputs
+#pragma unroll
+            for (int p = 0; p < PER; ++p) {
+                const int e = threadIdx.x + p * NTR;
+                if (NB % NTR == 0 || e < NB) {
+                    const int jj = e % RT, bb = e / RT;
+#pragma unroll
+                    for (int q = 0; q < A; ++q) buf[(bb * A + q) * RTP + jj] = x[p][q];
+                }
+            }
+            __syncthreads();
+        }
+        if constexpr (B != 0) rr_mid<R, B, RT, NTR>(buf, twt, A);
+        // last sub-stage: radix C, ns = R / C, straight to global memory (as k_fft_pass_rr)
+        {
+            constexpr int NS = R / C;
+            const float2* tl = twt + (B ? B * A : 0);
+            constexpr int NB = R / C * RT;
+            constexpr int PER = (NB + NTR - 1) / NTR;
+            const bool ns1 = a.Ns == 1;
+#pragma unroll
+            for (int p = 0; p < PER; ++p) {
+                const int e = threadIdx.x + p * NTR;
+                if (NB % NTR == 0 || e < NB) {
+                    const int jj = ns1 ? e / NS : e % RT;
+                    const int bb = ns1 ? e % NS : e / RT;
+                    float2 x[C];
+#pragma unroll
+                    for (int q = 0; q < C; ++q) {
+                        x[q] = buf[(bb + q * NS) * RTP + jj];
+                        if (q && bb) x[q] = cmul(x[q], tl[q * NS + bb]);
+                    }
+                    dft_any<C>(x);
+                    const int64_t j = j0 + jj;
+                    if (j < ncol) {
+                        if (ns1) {
+#pragma unroll
+                            for (int q = 0; q < C; ++q) o[j * R + bb + q * NS] = x[q];
+                        } else {
+                            const int64_t kc = j & (a.Ns - 1);
+                            float2* oo = o + (j / a.Ns) * a.Ns * R + kc;
+#pragma unroll
+                            for (int q = 0; q < C; ++q) oo[(int64_t)(bb + q * NS) * a.Ns] = x[q];
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();  // the slot is free for the copies of tile t + 2
+    }
+}
+
+// Staged tiles where a CTA's buffers leave room for two CTAs per SM (the first pass up to
+// radix 512, later passes up to radix 256); PSS_FFT_STAGE=0 keeps k_fft_pass_rr everywhere,
+// PSS_FFT_STAGE_TPC sets the tiles per CTA (default 4)
+int fft_stage_tpc() {
+    static const int v = [] {
+        const char* e = getenv("PSS_FFT_STAGE");
+        if (e && e[0] == '0') return 0;
+        const char* t = getenv("PSS_FFT_STAGE_TPC");
+        const int x = t ? atoi(t) : 4;
+        return x < 1 ? 1 : x;
+    }();
+    return v;
+}
+
 // PSS_FFT_RR=0 keeps the shared-memory sub-stage forms; by default the
 // register-radix form runs.
 bool fft_rr() {
@@ -612,6 +814,26 @@ template <int R>
 cudaError_t run_pass_rr(const PassArgs& p, int nb, cudaStream_t s) {
     using P = RrPlan<R>;
     static_assert(P::A * (P::B ? P::B : 1) * P::C == R, "radix plan");
+    const int tpc = fft_stage_tpc();
+    if constexpr (R <= 512) {
+    if (tpc > 0 && (p.series ? R <= 512 : R <= 256)) {
+        const int64_t ntile = (p.M / R + P::RT - 1) / P::RT;
+        const int per = (int)std::max<int64_t>(1, std::min<int64_t>(tpc, ntile));
+        dim3 grid((unsigned)((ntile + per - 1) / per), (unsigned)nb);
+        if (p.series) {
+            constexpr size_t shm = RrdbPlan<R, true>::bytes;
+            cudaError_t e = allow_smem((const void*)k_fft_pass_rrdb<R, true>, shm);
+            if (e != cudaSuccess) return e;
+            k_fft_pass_rrdb<R, true><<<grid, P::NTR, shm, s>>>(p, per);
+        } else {
+            constexpr size_t shm = RrdbPlan<R, false>::bytes;
+            cudaError_t e = allow_smem((const void*)k_fft_pass_rrdb<R, false>, shm);
+            if (e != cudaSuccess) return e;
+            k_fft_pass_rrdb<R, false><<<grid, P::NTR, shm, s>>>(p, per);
+        }
+        return cudaGetLastError();
+    }
+    }
     const size_t shm = (size_t)(R * P::RTP + P::TW) * sizeof(float2);
     const void* k = p.series ? (const void*)k_fft_pass_rr<R, true> : (const void*)k_fft_pass_rr<R, false>;
     cudaError_t e = allow_smem(k, shm);

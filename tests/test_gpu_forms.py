@@ -2,8 +2,10 @@
 bytes: the double- and single-buffered FFT passes (PSS_FFT_DB, with the
 shared-memory sub-stage passes, PSS_FFT_RR=0) and zmax 0 plane kernels
 (PSS_PLANE_Z0_DB), the whitening fused with the zmax 0 plane against
-the two kernels (PSS_WHITEN_Z0), and the unpack kernels for files with
-every channel kept against the tiled one (PSS_PREP_FAST).  The register-radix FFT passes (PSS_FFT_RR=1, the
+the two kernels (PSS_WHITEN_Z0), the unpack kernels for files with
+every channel kept against the tiled one (PSS_PREP_FAST), and the
+register-radix FFT passes with staged double-buffered tiles against the
+unstaged ones (PSS_FFT_STAGE).  The register-radix FFT passes (PSS_FFT_RR=1, the
 default) round differently: both FFT forms are compared with the oracle."""
 import os
 import subprocess
@@ -128,6 +130,40 @@ def test_unpack_forms_are_identical(tmp_path):
         env["PSS_PREP_FAST"] = v
         subprocess.run([sys.executable, "-c", CHILD_PREP.format(root=ROOT, out=out)], env=env, check=True,
                        timeout=600)
+        outs.append(np.load(out))
+    assert outs[0].size > 0 and outs[0].tobytes() == outs[1].tobytes()
+
+
+CHILD_STAGE = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, {root!r})
+from paper_1912_12807_gb300 import pss, synth
+out = []
+for nsamp in {cases!r}:
+    wl = synth.workload_small(nsamp=nsamp)
+    ctx = pss.Context(0)
+    plan = pss.Plan(pss.FilDesc.of(wl.fil), [synth.Stage(0.0, 1.0, 24, 1)])
+    cfg = pss.search_cfg(zmax=0, numharm=8, whiten_block=256)
+    d = torch.from_numpy(wl.fil.data).cuda()
+    out.append(pss.pss_spectrum(ctx, plan, d, cfg, 0, plan.ndm).cpu().numpy().ravel().view(np.uint8))
+    ctx.close()
+np.save({out!r}, np.concatenate(out))
+"""
+
+
+def test_fft_staged_tiles_are_bit_identical(tmp_path):
+    # complex transforms of 2^11 (radix 64 x 32), 2^15 (256 x 128), 2^16 with a ragged series
+    # (256 x 256) and 2^21 (128 x 128 x 128) points: the staged first and later passes against
+    # k_fft_pass_rr
+    cases = [2500, 1 << 16, (1 << 16) + 12345, (1 << 22) + 77]
+    outs = []
+    for tag, v in (("staged", "1"), ("direct", "0")):
+        out = str(tmp_path / ("stage_%s.npy" % tag))
+        env = dict(os.environ)
+        env["PSS_FFT_STAGE"] = v
+        env["PSS_FFT_RR"] = "1"
+        subprocess.run([sys.executable, "-c", CHILD_STAGE.format(root=ROOT, cases=cases, out=out)], env=env,
+                       check=True, timeout=900)
         outs.append(np.load(out))
     assert outs[0].size > 0 and outs[0].tobytes() == outs[1].tobytes()
 
