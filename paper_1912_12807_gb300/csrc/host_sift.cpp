@@ -58,10 +58,11 @@ bool rep_less(const Item& a, const Item& b) {
 // of 64 x 32 units: two items of one cell always link, so a cell is one
 // union-find node, and only the 4 forward-neighbouring cells need pair tests
 // (skipped when their bounding boxes are too far apart or they are already
-// joined).
+// joined; for the cell above or to the right the bounding boxes decide).
+// Cells are found through a hash table (the same groups, in any order).
 struct Cell {
     int64_t cr, cz;
-    int begin, end;  // range in the sorted order
+    int begin, end;  // range of the cell's members in the order
     int64_t r_lo, r_hi, z_lo, z_hi;
 };
 
@@ -104,77 +105,82 @@ Groups link_groups(const std::vector<Item>& it, double /*dz*/) {
         return G;
     }
     auto fdiv = [](int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); };
-    std::vector<int> order(n);
+    // cells in an open-addressing hash table keyed by (cell r, cell z), in order of first
+    // appearance; the groups are the same sets whatever the order of the cells
     std::vector<int64_t> cr(n), cz(n);
-    int64_t cr0 = INT64_MAX, cr1 = INT64_MIN, cz0 = INT64_MAX, cz1 = INT64_MIN;
     for (int i = 0; i < n; ++i) {
         cr[i] = fdiv(it[i].kr, 64);
         cz[i] = fdiv(it[i].kz, 32);
-        cr0 = std::min(cr0, cr[i]);
-        cr1 = std::max(cr1, cr[i]);
-        cz0 = std::min(cz0, cz[i]);
-        cz1 = std::max(cz1, cz[i]);
     }
-    // order by (cell r, cell z, index): one packed 64-bit key when the ranges fit
-    int bz = 1, bi = 1;
-    while ((int64_t(1) << bz) <= cz1 - cz0) ++bz;
-    while ((int64_t(1) << bi) < n) ++bi;
-    int br = 1;
-    while (n > 0 && (int64_t(1) << br) <= cr1 - cr0) ++br;
-    if (n > 0 && br + bz + bi <= 63) {
-        std::vector<uint64_t> key(n);
-        for (int i = 0; i < n; ++i)
-            key[i] = ((uint64_t)(cr[i] - cr0) << (bz + bi)) | ((uint64_t)(cz[i] - cz0) << bi) | (uint64_t)i;
-        std::sort(key.begin(), key.end());
-        for (int p = 0; p < n; ++p) order[p] = (int)(key[p] & ((uint64_t(1) << bi) - 1));
-    } else {
-        std::iota(order.begin(), order.end(), 0);
-        std::sort(order.begin(), order.end(), [&](int a, int b) {
-            if (cr[a] != cr[b]) return cr[a] < cr[b];
-            if (cz[a] != cz[b]) return cz[a] < cz[b];
-            return a < b;
-        });
-    }
+    size_t cap = 16;
+    while (cap < 2 * (size_t)n) cap <<= 1;
+    std::vector<int> table(cap, -1);
     std::vector<Cell> cells;
-    for (int p = 0; p < n;) {
-        int q = p;
-        Cell c{cr[order[p]], cz[order[p]], p, p, INT64_MAX, INT64_MIN, INT64_MAX, INT64_MIN};
-        while (q < n && cr[order[q]] == c.cr && cz[order[q]] == c.cz) {
-            const Item& x = it[order[q]];
-            c.r_lo = std::min(c.r_lo, x.kr);
-            c.r_hi = std::max(c.r_hi, x.kr);
-            c.z_lo = std::min(c.z_lo, x.kz);
-            c.z_hi = std::max(c.z_hi, x.kz);
-            ++q;
+    cells.reserve((size_t)n);
+    auto hash_of = [](int64_t r, int64_t z) {
+        uint64_t h = (uint64_t)r * 0x9E3779B97F4A7C15ull ^ ((uint64_t)z + 0x632BE59BD9B4E019ull) * 0xC2B2AE3D27D4EB4Full;
+        return h ^ (h >> 29);
+    };
+    auto find_cell = [&](int64_t r, int64_t z) -> int {  // -1 if absent
+        for (size_t h = hash_of(r, z) & (cap - 1);; h = (h + 1) & (cap - 1)) {
+            const int c = table[h];
+            if (c < 0) return -1;
+            if (cells[(size_t)c].cr == r && cells[(size_t)c].cz == z) return c;
         }
-        c.end = q;
-        cells.push_back(c);
-        p = q;
+    };
+    std::vector<int> cell_of(n);
+    for (int i = 0; i < n; ++i) {
+        size_t h = hash_of(cr[i], cz[i]) & (cap - 1);
+        int c;
+        for (;; h = (h + 1) & (cap - 1)) {
+            c = table[h];
+            if (c < 0) {
+                c = (int)cells.size();
+                table[h] = c;
+                cells.push_back(Cell{cr[i], cz[i], 0, 0, INT64_MAX, INT64_MIN, INT64_MAX, INT64_MIN});
+                break;
+            }
+            if (cells[(size_t)c].cr == cr[i] && cells[(size_t)c].cz == cz[i]) break;
+        }
+        Cell& C = cells[(size_t)c];
+        ++C.end;  // count for now
+        C.r_lo = std::min(C.r_lo, it[i].kr);
+        C.r_hi = std::max(C.r_hi, it[i].kr);
+        C.z_lo = std::min(C.z_lo, it[i].kz);
+        C.z_hi = std::max(C.z_hi, it[i].kz);
+        cell_of[i] = c;
     }
     const int nc = (int)cells.size();
+    // members of each cell contiguous in `order` (counting sort by cell)
+    {
+        int acc = 0;
+        for (Cell& C : cells) {
+            const int k = C.end;
+            C.begin = acc;
+            C.end = acc;
+            acc += k;
+        }
+    }
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[cells[(size_t)cell_of[i]].end++] = i;
     std::vector<int> par(nc);
     std::iota(par.begin(), par.end(), 0);
-    // forward neighbours (cr, cz+1), (cr+1, cz-1), (cr+1, cz), (cr+1, cz+1):
-    // cells are sorted by (cr, cz), so a cursor into row cr+1 only moves forward
-    int cur = 0;
+    // forward neighbours (cr, cz+1), (cr+1, cz-1), (cr+1, cz), (cr+1, cz+1) of every cell
     for (int a = 0; a < nc; ++a) {
-        const Cell& A = cells[a];
-        int nbr[4] = {-1, -1, -1, -1};
-        if (a + 1 < nc && cells[a + 1].cr == A.cr && cells[a + 1].cz == A.cz + 1) nbr[0] = a + 1;
-        if (cur < a + 1) cur = a + 1;
-        while (cur < nc && (cells[cur].cr < A.cr + 1 || (cells[cur].cr == A.cr + 1 && cells[cur].cz < A.cz - 1))) ++cur;
-        for (int c = cur, d = 1; c < nc && cells[c].cr == A.cr + 1 && cells[c].cz <= A.cz + 1; ++c) {
-            d = (int)(cells[c].cz - A.cz) + 2;  // 1, 2, 3
-            nbr[d] = c;
-        }
-        for (int b : nbr) {
+        const Cell& A = cells[(size_t)a];
+        const int nbr[4] = {find_cell(A.cr, A.cz + 1), find_cell(A.cr + 1, A.cz - 1), find_cell(A.cr + 1, A.cz),
+                            find_cell(A.cr + 1, A.cz + 1)};
+        for (int k = 0; k < 4; ++k) {
+            const int b = nbr[k];
             if (b < 0) continue;
-            const Cell& B = cells[b];
+            const Cell& B = cells[(size_t)b];
             if (find_root(par, a) == find_root(par, b)) continue;
             // bounding-box gap larger than the link distance: no pair can link
             if (B.r_lo - A.r_hi > 64 || A.r_lo - B.r_hi > 64 || B.z_lo - A.z_hi > 32 || A.z_lo - B.z_hi > 32)
                 continue;
-            bool linked = false;
+            // the cell above (k = 0) or to the right (k = 2): the other coordinate differs by less
+            // than a cell for every pair, so the closest pair of the gap's direction links
+            bool linked = k == 0 || k == 2;
             for (int p = A.begin; p < A.end && !linked; ++p) {
                 const Item& x = it[order[p]];
                 for (int q = B.begin; q < B.end; ++q) {
@@ -200,7 +206,7 @@ Groups link_groups(const std::vector<Item>& it, double /*dz*/) {
             slot[r] = ng++;
             cnt.push_back(0);
         }
-        cnt[slot[r]] += cells[c].end - cells[c].begin;
+        cnt[slot[r]] += cells[(size_t)c].end - cells[(size_t)c].begin;
     }
     Groups G;
     G.start.assign(ng + 1, 0);
@@ -209,7 +215,7 @@ Groups link_groups(const std::vector<Item>& it, double /*dz*/) {
     std::vector<int> fill(G.start.begin(), G.start.end() - 1);
     for (int c = 0; c < nc; ++c) {
         const int g = slot[find_root(par, c)];
-        for (int p = cells[c].begin; p < cells[c].end; ++p) G.members[fill[g]++] = order[p];
+        for (int p = cells[(size_t)c].begin; p < cells[(size_t)c].end; ++p) G.members[fill[g]++] = order[p];
     }
     return G;
 }
