@@ -269,15 +269,31 @@ int pick_rep(std::vector<Item>& items, const int* mem, int nm, bool need_sigma) 
 
 void bucket_by_dm(const pss_raw_cand* raw, int64_t n, int64_t ndm, std::vector<int64_t>* order,
                   std::vector<std::pair<int64_t, int64_t>>* buckets) {
-    std::vector<int64_t> cnt((size_t)ndm + 1, 0);
-    for (int64_t i = 0; i < n; ++i) cnt[(size_t)raw[i].dm_idx + 1]++;
-    for (int64_t d = 0; d < ndm; ++d) cnt[(size_t)d + 1] += cnt[(size_t)d];
-    order->assign((size_t)n, 0);
-    std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
-    for (int64_t i = 0; i < n; ++i) (*order)[(size_t)pos[(size_t)raw[i].dm_idx]++] = i;
+    // stable counting sort by DM index over contiguous chunks of the input in parallel: chunk t's
+    // items of trial d follow those of chunks < t (the order of the serial counting sort)
+    const int64_t T = n < (int64_t)1 << 16 ? 1 : std::min<int64_t>(16, n >> 15);
+    std::vector<int64_t> cnt((size_t)(T * ndm), 0);  // [chunk][trial]
+    auto lo_of = [&](int64_t t) { return t * n / T; };
+    parallel_for(T, 1, [&](int64_t t) {
+        int64_t* c = cnt.data() + t * ndm;
+        for (int64_t i = lo_of(t); i < lo_of(t + 1); ++i) c[raw[i].dm_idx]++;
+    });
+    std::vector<int64_t> pos((size_t)(T * ndm));
     buckets->clear();
-    for (int64_t d = 0; d < ndm; ++d)
-        if (cnt[(size_t)d + 1] > cnt[(size_t)d]) buckets->push_back({cnt[(size_t)d], cnt[(size_t)d + 1]});
+    int64_t acc = 0;
+    for (int64_t d = 0; d < ndm; ++d) {
+        const int64_t first = acc;
+        for (int64_t t = 0; t < T; ++t) {
+            pos[(size_t)(t * ndm + d)] = acc;
+            acc += cnt[(size_t)(t * ndm + d)];
+        }
+        if (acc > first) buckets->push_back({first, acc});
+    }
+    order->resize((size_t)n);
+    parallel_for(T, 1, [&](int64_t t) {
+        int64_t* p = pos.data() + t * ndm;
+        for (int64_t i = lo_of(t); i < lo_of(t + 1); ++i) (*order)[(size_t)p[raw[i].dm_idx]++] = i;
+    });
 }
 
 void sort_raw(std::vector<pss_raw_cand>* v, int64_t ndm) {
