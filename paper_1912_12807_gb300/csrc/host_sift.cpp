@@ -384,22 +384,32 @@ pss_status sift_across(const Plan& P, const pss_search_cfg& cfg, std::vector<Sif
     };
     const Groups G = link_groups(survivors, cfg.dz);
     lap("link");
-    // one representative per group, groups in parallel (each writes its own slot); one group
-    // per task: after the within-trial sift the groups are few (about 100 on the drift-scan
-    // file) and the largest span hundreds of trials
+    // one representative per group, groups in parallel (each writes its own slot); tasks of
+    // about ng / 256 groups: one group per task when they are few (about 100 on the drift-scan
+    // file, the largest spanning hundreds of trials), runs of them when they are many (35 k on
+    // the accel file, where single-group tasks contend for the task counter)
     const int ng = G.count();
     std::vector<pss_cand> reps((size_t)ng);
     std::vector<char> keep((size_t)ng, 0);
-    parallel_for(ng, 1, [&](int64_t g) {
+    parallel_for(ng, std::max(1, ng / 256), [&](int64_t g) {
         const int* mem = G.members.data() + G.start[g];
         const int nm = G.start[g + 1] - G.start[g];
         int hits = 1;
         if (nm > 1) {
-            thread_local std::vector<int32_t> dms;  // reused: no allocation per group
-            dms.resize((size_t)nm);
-            for (int q = 0; q < nm; ++q) dms[(size_t)q] = survivors[mem[q]].dm_idx;
-            std::sort(dms.begin(), dms.end());
-            hits = (int)(std::unique(dms.begin(), dms.end()) - dms.begin());
+            // distinct DM trials of the group: a bit per trial, cleared again after the count
+            thread_local std::vector<uint64_t> seen;
+            const size_t words = (size_t)(P.ndm() + 63) / 64;
+            if (seen.size() < words) seen.assign(words, 0);
+            hits = 0;
+            for (int q = 0; q < nm; ++q) {
+                const int32_t d = survivors[mem[q]].dm_idx;
+                const uint64_t bit = 1ull << (d & 63);
+                if (!(seen[(size_t)(d >> 6)] & bit)) {
+                    seen[(size_t)(d >> 6)] |= bit;
+                    ++hits;
+                }
+            }
+            for (int q = 0; q < nm; ++q) seen[(size_t)(survivors[mem[q]].dm_idx >> 6)] = 0;
         }
         // groups seen in too few trials are dropped before any sigma is evaluated
         if (hits < cfg.min_dm_hits) return;
