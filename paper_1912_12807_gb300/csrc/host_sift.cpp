@@ -432,12 +432,27 @@ pss_status sift_across(const Plan& P, const pss_search_cfg& cfg, std::vector<Sif
     for (int g = 0; g < ng; ++g)
         if (keep[(size_t)g]) out->push_back(reps[(size_t)g]);
     lap("reps");
-    std::sort(out->begin(), out->end(), [](const pss_cand& a, const pss_cand& b) {
-        if (a.dm_idx != b.dm_idx) return a.dm_idx < b.dm_idx;
-        if (a.numharm != b.numharm) return a.numharm < b.numharm;
-        if (a.r != b.r) return a.r < b.r;
-        return a.z < b.z;
+    // order by (DM index, numharm, r, z): a counting sort by DM index, then each trial's
+    // candidates sorted in parallel
+    const int64_t nd = P.ndm();
+    std::vector<int64_t> first((size_t)nd + 1, 0);
+    for (const pss_cand& c : *out) first[(size_t)c.dm_idx + 1]++;
+    for (int64_t d = 0; d < nd; ++d) first[(size_t)d + 1] += first[(size_t)d];
+    std::vector<pss_cand> sorted(out->size());
+    {
+        std::vector<int64_t> pos(first.begin(), first.end() - 1);
+        for (const pss_cand& c : *out) sorted[(size_t)pos[(size_t)c.dm_idx]++] = c;
+    }
+    parallel_for(nd, std::max<int64_t>(1, nd / 256), [&](int64_t d) {
+        std::sort(sorted.begin() + first[(size_t)d], sorted.begin() + first[(size_t)d + 1],
+                  [](const pss_cand& a, const pss_cand& b) {
+                      if (a.numharm != b.numharm) return a.numharm < b.numharm;
+                      if (a.r != b.r) return a.r < b.r;
+                      return a.z < b.z;
+                  });
     });
+    out->swap(sorted);
+    lap("sort");
     return PSS_OK;
 }
 
