@@ -1102,7 +1102,8 @@ pss_status ensure_raw_pinned(pss_ctx* ctx, size_t n) {
 // on the later batches.  *overflow: a batch's count passed `cap` (its
 // detections are incomplete; the caller redoes the search larger).
 pss_status drain_batches(pss_ctx* ctx, const pss_plan* plan, const pss_search_cfg* cfg, size_t nbatches,
-                         int64_t cap, std::vector<SiftItem>* surv, bool* overflow, unsigned long long* total) {
+                         int64_t cap, std::vector<SiftItem>* surv, bool* overflow, unsigned long long* total,
+                         SiftLinker* lk = nullptr) {
     *overflow = false;
     unsigned long long prev = 0;
     for (size_t i = 0; i < nbatches; ++i) {
@@ -1129,6 +1130,9 @@ pss_status drain_batches(pss_ctx* ctx, const pss_plan* plan, const pss_search_cf
                 auto by_r = [](const SiftItem& a, const SiftItem& b) { return a.kr < b.kr; };
                 std::stable_sort(surv->begin() + old, surv->end(), by_r);
                 std::inplace_merge(surv->begin(), surv->begin() + old, surv->end(), by_r);
+            } else if (lk) {
+                // 2-D planes: link the batch's survivors to the earlier ones while the device works on
+                lk->add(*surv, old);
             }
         }
         prev = cnt;
@@ -1162,9 +1166,10 @@ pss_status search_pipelined(pss_ctx* ctx, const pss_plan* plan, const pss_fil_de
             PSS_CUDA(cudaMemcpyAsync(ctx->batch_cnt + nb, ctx->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         tm.mark("enqueue");
         std::vector<SiftItem> surv;
+        SiftLinker lk;
         bool overflow = false;
         unsigned long long total = 0;
-        PSS_TRY(drain_batches(ctx, plan, cfg, nb, cap, &surv, &overflow, &total));
+        PSS_TRY(drain_batches(ctx, plan, cfg, nb, cap, &surv, &overflow, &total, &lk));
         PSS_CUDA(cudaStreamSynchronize(s));
         tm.mark("gpu+within");
         if (ctx->errflag.p) {
@@ -1173,7 +1178,7 @@ pss_status search_pipelined(pss_ctx* ctx, const pss_plan* plan, const pss_fil_de
             PSS_TRY(errflag_status(ctx, flag, s));
         }
         if (!overflow) {
-            PSS_TRY(sift_across(*plan, *cfg, surv, out));
+            PSS_TRY(sift_across(*plan, *cfg, surv, out, cfg->zmax ? &lk : nullptr));
             tm.mark("across");
             return PSS_OK;
         }
@@ -2915,10 +2920,11 @@ extern "C" pss_status pss_batch_run(pss_batch* b, const void* data, int data_on_
         if (gpu_ms) cudaEventRecord(e1, s);
         // the within-trial sift of each DM batch runs while the graph does the later ones
         std::vector<SiftItem> surv;
+        SiftLinker lk;
         bool overflow = false;
         unsigned long long total = 0;
         PSS_TRY(drain_batches(ctx, static_cast<const pss_plan*>(&b->plan), &b->cfg, b->P.batches.size(),
-                              b->P.dev_cap, &surv, &overflow, &total));
+                              b->P.dev_cap, &surv, &overflow, &total, &lk));
         PSS_CUDA(cudaStreamSynchronize(s));
         if (gpu_ms) {
             float ms = 0.f;
@@ -2929,7 +2935,7 @@ extern "C" pss_status pss_batch_run(pss_batch* b, const void* data, int data_on_
         }
         PSS_TRY(check_errflag(ctx, s));
         if (!overflow) {
-            PSS_TRY(sift_across(b->plan, b->cfg, surv, &b->last));
+            PSS_TRY(sift_across(b->plan, b->cfg, surv, &b->last, b->cfg.zmax ? &lk : nullptr));
             b->has_last = true;
             return take_cands(b->last, out, cap, n_out);
         }

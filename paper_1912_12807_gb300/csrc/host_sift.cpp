@@ -371,8 +371,112 @@ pss_status sift_within(const Plan& P, const pss_search_cfg& cfg, const pss_raw_c
     return PSS_OK;
 }
 
+namespace {
+int64_t fdiv64(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+uint64_t cell_hash(int64_t r, int64_t z) {
+    uint64_t h = (uint64_t)r * 0x9E3779B97F4A7C15ull ^ ((uint64_t)z + 0x632BE59BD9B4E019ull) * 0xC2B2AE3D27D4EB4Full;
+    return h ^ (h >> 29);
+}
+}  // namespace
+
+int SiftLinker::find_cell(int64_t cr, int64_t cz) const {
+    if (table_.empty()) return -1;
+    const size_t mask = table_.size() - 1;
+    for (size_t h = cell_hash(cr, cz) & mask;; h = (h + 1) & mask) {
+        const int c = table_[h];
+        if (c < 0) return -1;
+        if (cells_[(size_t)c].cr == cr && cells_[(size_t)c].cz == cz) return c;
+    }
+}
+
+int SiftLinker::root(int c) const {
+    while (par_[(size_t)c] != c) {
+        par_[(size_t)c] = par_[(size_t)par_[(size_t)c]];
+        c = par_[(size_t)c];
+    }
+    return c;
+}
+
+void SiftLinker::grow() {
+    size_t cap = table_.empty() ? 1024 : table_.size() * 2;
+    while (cap < 2 * (cells_.size() + 1)) cap *= 2;
+    table_.assign(cap, -1);
+    for (size_t c = 0; c < cells_.size(); ++c)
+        for (size_t h = cell_hash(cells_[c].cr, cells_[c].cz) & (cap - 1);; h = (h + 1) & (cap - 1))
+            if (table_[h] < 0) {
+                table_[h] = (int)c;
+                break;
+            }
+}
+
+void SiftLinker::add(const std::vector<SiftItem>& items, size_t from) {
+    for (size_t i = from; i < items.size(); ++i) {
+        const SiftItem& x = items[i];
+        const int64_t cr = fdiv64(x.kr, 64), cz = fdiv64(x.kz, 32);
+        int c = find_cell(cr, cz);
+        if (c < 0) {
+            if (2 * (cells_.size() + 1) > table_.size()) grow();
+            c = (int)cells_.size();
+            cells_.push_back(LCell{cr, cz, x.kr, x.kr, x.kz, x.kz, {}});
+            par_.push_back(c);
+            const size_t mask = table_.size() - 1;
+            for (size_t h = cell_hash(cr, cz) & mask;; h = (h + 1) & mask)
+                if (table_[h] < 0) {
+                    table_[h] = c;
+                    break;
+                }
+        }
+        LCell& C = cells_[(size_t)c];
+        C.mem.push_back((int)i);
+        C.r_lo = std::min(C.r_lo, x.kr);
+        C.r_hi = std::max(C.r_hi, x.kr);
+        C.z_lo = std::min(C.z_lo, x.kz);
+        C.z_hi = std::max(C.z_hi, x.kz);
+        cell_of_.push_back(c);
+        // the new item's links to the eight neighbouring cells (its own cell's members link to it)
+        for (int dr = -1; dr <= 1; ++dr)
+            for (int dz = -1; dz <= 1; ++dz) {
+                if (dr == 0 && dz == 0) continue;
+                const int b = find_cell(cr + dr, cz + dz);
+                if (b < 0 || root(b) == root(c)) continue;
+                const LCell& B = cells_[(size_t)b];
+                if (B.r_lo - x.kr > 64 || x.kr - B.r_hi > 64 || B.z_lo - x.kz > 32 || x.kz - B.z_hi > 32) continue;
+                for (int q : B.mem) {
+                    const SiftItem& y = items[(size_t)q];
+                    if (std::llabs(x.kr - y.kr) <= 64 && std::llabs(x.kz - y.kz) <= 32) {
+                        const int ra = root(c), rb = root(b);
+                        par_[(size_t)std::max(ra, rb)] = std::min(ra, rb);
+                        break;
+                    }
+                }
+            }
+    }
+}
+
+void SiftLinker::groups(std::vector<int>* start, std::vector<int>* members) const {
+    const int nc = (int)cells_.size();
+    std::vector<int> slot((size_t)nc, -1), cnt;
+    int ng = 0;
+    for (int c = 0; c < nc; ++c) {
+        const int r = root(c);
+        if (slot[(size_t)r] < 0) {
+            slot[(size_t)r] = ng++;
+            cnt.push_back(0);
+        }
+        cnt[(size_t)slot[(size_t)r]] += (int)cells_[(size_t)c].mem.size();
+    }
+    start->assign((size_t)ng + 1, 0);
+    for (int g = 0; g < ng; ++g) (*start)[(size_t)g + 1] = (*start)[(size_t)g] + cnt[(size_t)g];
+    members->resize(cell_of_.size());
+    std::vector<int> fill(start->begin(), start->end() - 1);
+    for (int c = 0; c < nc; ++c) {
+        const int g = slot[(size_t)root(c)];
+        for (int i : cells_[(size_t)c].mem) (*members)[(size_t)fill[(size_t)g]++] = i;
+    }
+}
+
 pss_status sift_across(const Plan& P, const pss_search_cfg& cfg, std::vector<SiftItem>& survivors,
-                       std::vector<pss_cand>* out) {
+                       std::vector<pss_cand>* out, const SiftLinker* linked) {
     out->clear();
     const bool dbg = getenv("PSS_TIMING") != nullptr;
     auto t0 = std::chrono::steady_clock::now();
@@ -382,7 +486,9 @@ pss_status sift_across(const Plan& P, const pss_search_cfg& cfg, std::vector<Sif
         fprintf(stderr, "[pss] sift.%-10s %8.3f ms\n", what, std::chrono::duration<double, std::milli>(t1 - t0).count());
         t0 = t1;
     };
-    const Groups G = link_groups(survivors, cfg.dz);
+    Groups G;
+    if (linked && linked->size() == survivors.size()) linked->groups(&G.start, &G.members);
+    else G = link_groups(survivors, cfg.dz);
     lap("link");
     // one representative per group, groups in parallel (each writes its own slot); tasks of
     // about ng / 256 groups: one group per task when they are few (about 100 on the drift-scan

@@ -122,8 +122,32 @@ struct SiftItem {
 };
 pss_status sift_within(const Plan& P, const pss_search_cfg& cfg, const pss_raw_cand* raw, int64_t n,
                        std::vector<SiftItem>* out);
+// Incremental single linkage of the survivors of 2-D planes (the links of
+// sift_across, whose components do not depend on the order items arrive in):
+// add() links the items [from, size) to those added before; groups() gives
+// the components of all of them (members as item indices).
+class SiftLinker {
+  public:
+    void add(const std::vector<SiftItem>& items, size_t from);
+    void groups(std::vector<int>* start, std::vector<int>* members) const;
+    size_t size() const { return cell_of_.size(); }
+
+  private:
+    struct LCell {
+        int64_t cr, cz;
+        int64_t r_lo, r_hi, z_lo, z_hi;
+        std::vector<int> mem;
+    };
+    int find_cell(int64_t cr, int64_t cz) const;
+    int root(int c) const;
+    void grow();
+    std::vector<LCell> cells_;
+    std::vector<int> table_;   // open addressing: cell index or -1
+    mutable std::vector<int> par_;
+    std::vector<int> cell_of_;  // cell of each item
+};
 pss_status sift_across(const Plan& P, const pss_search_cfg& cfg, std::vector<SiftItem>& survivors,
-                       std::vector<pss_cand>* out);
+                       std::vector<pss_cand>* out, const SiftLinker* linked = nullptr);
 
 // ---- device workspace -----------------------------------------------------
 struct DevBuf {

@@ -266,6 +266,24 @@ def test_search_raw_small_parity(L, ctx, small):
     assert abs(best["f_hz"] - 1 / 0.0333) < 1.0 / (65536 * 2e-4)
 
 
+def test_pipelined_2d_sift_equals_sift_of_raw(L, ctx):
+    # zmax > 0 with 200 trials: the pipelined search links each DM batch's survivors to the
+    # earlier ones while the device works (four batches); its list must be the one-pass sift of
+    # the raw detections, byte for byte (a low threshold gives many linked groups)
+    fil = synth.make_8bit(64, 1 << 15, 2e-4, 1200.0, 1500.0,
+                          [synth.Pulsar(0.01, 60.0, 0.05, 0.6, z_direct=6.0), synth.Pulsar(0.0123, 20.0, 0.05, 0.4)],
+                          seed=17)
+    stages = [synth.Stage(0.0, 0.5, 200, 1)]
+    plan = L.Plan(L.FilDesc.of(fil), stages)
+    cfg = L.search_cfg(zmax=16, dz=2.0, numharm=8, sigma_thr=3.5, whiten_block=256)
+    d = _torch_dev(fil.data)
+    raw = L.pss_search_raw(ctx, plan, d, cfg, 0, plan.ndm, cap=1 << 22)
+    cands = L.pss_search_dm_batch(ctx, plan, d, cfg, 0, plan.ndm, cap=1 << 18)
+    again = L.pss_sift(plan, cfg, raw, cap=1 << 18)
+    assert len(cands) > 10 and len(raw) > 10 * len(cands)
+    assert cands.tobytes() == again.tobytes()
+
+
 def test_search_accel_parity(L, ctx):
     fil = synth.make_8bit(64, 1 << 14, 2e-4, 1200.0, 1500.0,
                           [synth.Pulsar(0.01, 20.0, 0.05, 0.6, z_direct=9.0)], seed=3)
