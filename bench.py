@@ -386,7 +386,8 @@ def measure_search(pss, wl, name, steps, warmup, local_rank, flush, stream, peak
     """One workload through pss_search_dm_batch with the file resident on
     the device: `steps` steps timed by CUDA events on the launching stream
     (L2 flushed between them), per-stage device time from the library's
-    profiler, rooflines against the measured peaks, then the same call with
+    profiler in up to 3 further steps (its events stay out of the timed
+    ones), rooflines against the measured peaks, then the same call with
     the file in pinned host memory (upload and candidate download timed).
     Returns (result dict, context, plan, cfg, device data, candidates); the
     caller closes the context."""
@@ -419,7 +420,6 @@ def measure_search(pss, wl, name, steps, warmup, local_rank, flush, stream, peak
 
     clocks = ClockSampler(local_rank)
     clocks.start()
-    ctx.profile(True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     barrier()
     t_wall0 = time.perf_counter()
@@ -430,11 +430,19 @@ def measure_search(pss, wl, name, steps, warmup, local_rank, flush, stream, peak
         ev[k][1].record(stream)
     barrier()
     t_wall = time.perf_counter() - t_wall0
-    prof = ctx.profile_read()
-    ctx.profile(False)
     clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = max_over_ranks(sum(step_ms) / len(step_ms), world, dev)
+    # the stage breakdown from further steps with the library's per-stage CUDA events on
+    # (kept out of the timed steps: the events are instrumentation, not the search)
+    psteps = max(1, min(steps, 3))
+    ctx.profile(True)
+    for k in range(psteps):
+        flush.fill_(k & 0xFF)
+        step()
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
 
     e2e_ms = []
     for k in range(max(1, steps)):
@@ -452,7 +460,7 @@ def measure_search(pss, wl, name, steps, warmup, local_rank, flush, stream, peak
         if n_st == 0:
             continue
         bound, amount, unit = work[st]
-        rooflines[st] = roofline_of(st, bound, amount * steps, unit, ms_st, n_st, peaks, peak_kind, alu)
+        rooflines[st] = roofline_of(st, bound, amount * psteps, unit, ms_st, n_st, peaks, peak_kind, alu)
         if traffic:
             rooflines[st]["traffic"] = recorded_traffic(name, st)
     if "whiten" in rooflines and cfg.zmax == 0 and prof.get("plane", (0.0, 0))[1] == 0:
@@ -463,7 +471,7 @@ def measure_search(pss, wl, name, steps, warmup, local_rank, flush, stream, peak
         # channel-major file read once per launch
         ms_dd, n_dd = prof["dedisperse"]
         nv_sum = sum(plan.trial(i)["nv"] for i in range(ndm))
-        dd_bytes = 4.0 * nv_sum * steps + float(fil.nchan) * fil.nsamp * n_dd
+        dd_bytes = 4.0 * nv_sum * psteps + float(fil.nchan) * fil.nsamp * n_dd
         rooflines["dedisperse"]["hbm_frac"] = (dd_bytes / (ms_dd / 1e3)) / (float(peaks.get("hbm_gbs", 6800.0)) * 1e9)
         bx_rows = sorted({wl.stages[k].ds for k in range(len(wl.stages)) if bx_row(plan, wl, k)})
         if bx_rows:
@@ -471,7 +479,7 @@ def measure_search(pss, wl, name, steps, warmup, local_rank, flush, stream, peak
                 "rows with ds %s dedisperse from a per-channel boxcar table built once per ds (stage bxtable): "
                 "one table term per output and channel, a 32-bit add counted as two 16-bit SWAR slots" % bx_rows)
     dominant = max(prof, key=lambda k: prof[k][0])
-    launches_per_step = sum(n for _, n in prof.values()) / steps
+    launches_per_step = sum(n for _, n in prof.values()) / psteps
     bi = fil.nbytes()
     bo = int(len(cands)) * pss.CAND_DTYPE.itemsize
     res = {"metric": METRIC, "value": job_value(world, ndm, ms), "unit": UNIT, "steps": steps, "warmup": warmup,
@@ -481,8 +489,8 @@ def measure_search(pss, wl, name, steps, warmup, local_rank, flush, stream, peak
            "e2e": {"value": job_value(world, ndm, e2e), "unit": UNIT, "h2d_bytes_per_step": bi,
                    "d2h_bytes_per_step": bo, "ms_per_step": e2e},
            "gpu_launches": int(round(launches_per_step * steps)),
-           "stages_ms_per_step": {k: v[0] / steps for k, v in prof.items()},
-           "stage_launches_per_step": {k: v[1] / steps for k, v in prof.items()},
+           "stages_ms_per_step": {k: v[0] / psteps for k, v in prof.items()},
+           "stage_launches_per_step": {k: v[1] / psteps for k, v in prof.items()},
            "stage_rooflines": {k: {kk: v[kk] for kk in ("bound", "frac", "achieved", "unit", "hbm_frac", "note")
                                    if kk in v} for k, v in rooflines.items()},
            "clocks": clocks.summary(), "wall_s_timed": t_wall, "candidates": int(len(cands))}
