@@ -786,9 +786,9 @@ __global__ void __launch_bounds__(RrPlan<R>::NTR) k_fft_pass_rrdb(const __grid_c
     }
 }
 
-// Staged tiles where a CTA's buffers leave room for two CTAs per SM (the first pass up to
-// radix 512, later passes up to radix 256); PSS_FFT_STAGE=0 keeps k_fft_pass_rr everywhere,
-// PSS_FFT_STAGE_TPC sets the tiles per CTA (default 4)
+// Staged tiles for the first pass up to radix 512 (PSS_FFT_STAGE_LATER=1: later passes up to
+// radix 256 too); PSS_FFT_STAGE=0 keeps k_fft_pass_rr everywhere, PSS_FFT_STAGE_TPC sets the
+// tiles per CTA (default 4)
 int fft_stage_tpc() {
     static const int v = [] {
         const char* e = getenv("PSS_FFT_STAGE");
@@ -815,8 +815,14 @@ cudaError_t run_pass_rr(const PassArgs& p, int nb, cudaStream_t s) {
     using P = RrPlan<R>;
     static_assert(P::A * (P::B ? P::B : 1) * P::C == R, "radix plan");
     const int tpc = fft_stage_tpc();
+    // later passes stay unstaged by default: their four tile buffers (tiles and twiddles) leave
+    // two CTAs per SM, slower than the unstaged pass (drift-scan FFT 1.33 against 1.46 ms staged)
+    static const bool later = [] {
+        const char* e = getenv("PSS_FFT_STAGE_LATER");
+        return e && e[0] == '1';
+    }();
     if constexpr (R <= 512) {
-    if (tpc > 0 && (p.series ? R <= 512 : R <= 256)) {
+    if (tpc > 0 && (p.series ? R <= 512 : (later && R <= 256))) {
         const int64_t ntile = (p.M / R + P::RT - 1) / P::RT;
         const int per = (int)std::max<int64_t>(1, std::min<int64_t>(tpc, ntile));
         dim3 grid((unsigned)((ntile + per - 1) / per), (unsigned)nb);

@@ -161,6 +161,7 @@ def test_fft_staged_tiles_are_bit_identical(tmp_path):
         out = str(tmp_path / ("stage_%s.npy" % tag))
         env = dict(os.environ)
         env["PSS_FFT_STAGE"] = v
+        env["PSS_FFT_STAGE_LATER"] = v  # every pass staged (the default stages the first only)
         env["PSS_FFT_RR"] = "1"
         subprocess.run([sys.executable, "-c", CHILD_STAGE.format(root=ROOT, cases=cases, out=out)], env=env,
                        check=True, timeout=900)
