@@ -52,3 +52,30 @@ def test_stage_work_counts_table_terms_and_builds():
     w2 = bench.stage_work(p2, small, small.fil.nbytes())
     assert w2["bxtable"][1] == 0.0
     assert w2["dedisperse"][1] == float(small.fil.nchan) * sum(p2.trial(i)["nv"] for i in range(p2.ndm))
+
+
+def test_stage_work_counts_unpack_and_spectrum_bytes():
+    # unpack: the file read once plus one byte per channel and sample written (8x the file for
+    # 1-bit data); FFT: 16 bytes per complex point and pass; whitening (fused with the zmax 0
+    # plane or not): 16 bytes per complex point; zmax 0 plane: 8 M read + 4 nfft written
+    sys.path.insert(0, ROOT)
+    import math
+    import bench
+    from paper_1912_12807_gb300 import build, pss, synth
+    if not os.path.exists(pss.LIB_PATH):
+        build.build()
+    small = synth.workload_small()
+    plan = pss.Plan(pss.FilDesc.of(small.fil), small.stages)
+    w = bench.stage_work(plan, small, small.fil.nbytes())
+    C, N = small.fil.nchan, small.fil.nsamp
+    assert w["unpack"] == ("hbm", float(C * N + C * N), "bytes")
+    Ms = [plan.trial(i)["nfft"] // 2 for i in range(plan.ndm)]
+    assert w["fft"] == ("hbm", float(sum(max(1, math.ceil(math.log2(M) / 10)) * 16 * M for M in Ms)), "bytes")
+    assert w["whiten"] == ("hbm", float(sum(16 * M for M in Ms)), "bytes")
+    assert w["plane"] == ("hbm", float(sum(8 * M + 4 * 2 * M for M in Ms)), "bytes")
+    f1 = synth.make_1bit(96, 1 << 15, 2.5e-4, 1230.0, 1518.0, [], seed=1)
+    wl1 = synth.Workload("one-bit", f1, [synth.Stage(0.0, 1.0, 8, 1)], small.cfg)
+    p1 = pss.Plan(pss.FilDesc.of(f1), wl1.stages)
+    w1 = bench.stage_work(p1, wl1, f1.nbytes())
+    assert f1.nbytes() * 8 == 96 * (1 << 15)
+    assert w1["unpack"] == ("hbm", float(f1.nbytes() + 96 * (1 << 15)), "bytes")
