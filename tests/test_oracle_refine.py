@@ -48,20 +48,32 @@ def test_single_channel_peak_and_zero_gradient_at_tone():
     assert abs(g) < 1e-2 * abs(curv)
 
 
-def test_integer_bins_reduce_to_phased_channel_sum():
-    # z = 0 and integer k r: the response is a delta, E = 1, so
-    # P_h = sum_k gain * |sum_c exp(i phi_ck) A^c_{kr}|^2
-    wl = synth.workload_small(nsamp=1 << 14)
-    cfg = wl.cfg
-    obj = RF.Objective(wl.fil, [synth.Stage(40.0, 1.0, 21, 1)], cfg, dm_idx=10)
-    dm, r = 50.0, 123.0
-    ref = 0.0
-    for k in range(1, 5):
-        rk = k * r
-        phi = 2 * math.pi * rk * dm * obj.dtau / obj.T
-        F = np.sum(np.exp(1j * phi) * obj.Ac[:, int(rk)])
-        ref += obj.gain[int(rk) // cfg.whiten_block] * abs(F) ** 2
-    assert abs(obj(dm, r, 0.0, 4) - ref) < 1e-9 * ref
+def test_dm_phase_adds_a_delayed_tone_coherently():
+    # 32 channels carry one tone at an integer bin r0 of the span, each delayed by the continuous
+    # dispersion delay of DM0 (shift theorem: channel c's bin r0 turns by exp(-2 pi i r0 tau_c / T)).
+    # At z = 0 and an integer bin the response is a delta, so P_1(DM) / P_1(DM0) must be the array
+    # factor |sum_c exp(2 pi i r0 (DM - DM0) dtau_c / T)|^2 / C^2: 1 at DM0 (the phase undoes the
+    # delays), falling off on either side; a sign or scale error in the phase moves the peak.
+    nchan, nsamp, r0, dm0, tsamp = 32, 4096, 1000, 30.0, 2e-4
+    fch0, foff = synth.band(1200.0, 1500.0, nchan)
+    cfg = synth.SearchCfg(zmax=0, numharm=1, whiten_block=64)
+    stages = [synth.Stage(0.0, 1e-4, 2, 1)]  # delays that round to 0 samples: N_v = nfft = nsamp
+    zero = synth.Filterbank(nchan, nsamp, tsamp, fch0, foff, 8, np.zeros((nsamp, nchan), np.uint8), [])
+    dtau = RF.Objective(zero, stages, cfg, dm_idx=0).dtau  # seconds of delay per unit DM, per channel
+    T = nsamp * tsamp
+    t = np.arange(nsamp)[:, None] * tsamp
+    # seeded noise keeps the whitening block medians above 0 (the rounding error of the tone alone
+    # repeats every 512 samples and leaves most bins of a block empty)
+    noise = np.random.default_rng(5).normal(0.0, 2.0, (nsamp, nchan))
+    x = 128 + 100 * np.cos(2 * np.pi * r0 * (t - dm0 * dtau[None, :]) / T) + noise
+    fil = synth.Filterbank(nchan, nsamp, tsamp, fch0, foff, 8, np.clip(np.rint(x), 0, 255).astype(np.uint8), [])
+    obj = RF.Objective(fil, stages, cfg, dm_idx=0)
+    assert obj.nv == obj.nfft == nsamp and abs(obj.T - T) < 1e-12
+    peak = obj(dm0, float(r0), 0.0, 1)
+    for ddm in (0.05, -0.05, 0.2, -0.3, 0.5, 2 * dm0):
+        af = abs(np.sum(np.exp(2j * np.pi * r0 * ddm * dtau / T))) ** 2 / nchan ** 2
+        assert abs(obj(dm0 + ddm, float(r0), 0.0, 1) / peak - af) < 1e-3, ddm
+    assert obj(-dm0, float(r0), 0.0, 1) < 0.05 * peak
 
 
 def test_dispersed_pulsar_prefers_its_dm():
