@@ -450,6 +450,18 @@ pss_status pss_search_raw(pss_ctx* ctx, const pss_plan* plan, const pss_fil_desc
 pss_status pss_sift(const pss_plan* plan, const pss_search_cfg* cfg, const pss_raw_cand* raw,
                     int64_t n_raw, pss_cand* out, int64_t cap, int64_t* n_out);
 
+/* The same sift done the way a pipelined search does it, host only: the raw
+ * detections of DM batch b (dm_idx in [dm_bounds[b], dm_bounds[b+1]),
+ * b < nbatches; dm_bounds has nbatches + 1 non-decreasing entries) are sifted
+ * within their trials batch by batch, the survivors kept ordered by r
+ * (zmax 0) or linked to the earlier batches' (zmax > 0), and the across-trial
+ * step runs once at the end.  Detections outside every batch are ignored.
+ * The result equals pss_sift of the detections inside the batches (single
+ * linkage does not depend on the order).  Same output contract as pss_sift. */
+pss_status pss_sift_in_batches(const pss_plan* plan, const pss_search_cfg* cfg, const pss_raw_cand* raw,
+                               int64_t n_raw, const int64_t* dm_bounds, int32_t nbatches, pss_cand* out,
+                               int64_t cap, int64_t* n_out);
+
 /* The whole search of DM trials [dm_begin, dm_end) of one file:
  * pss_search_raw followed by pss_sift.  out: host, cap entries.  The sifted
  * list is also kept in the context (until its next search), so that after

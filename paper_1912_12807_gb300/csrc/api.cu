@@ -1096,6 +1096,25 @@ pss_status ensure_raw_pinned(pss_ctx* ctx, size_t n) {
     return PSS_OK;
 }
 
+// The host side of one finished DM batch of a pipelined search: its raw
+// detections sifted within their trials and the survivors added to `surv`;
+// for one-row planes (zmax 0) the survivors stay ordered by r (stable merge),
+// so the across-trial linkage after the last batch needs no sort; for 2-D
+// planes they are linked to the earlier ones (`lk`).
+pss_status absorb_batch(const pss_plan* plan, const pss_search_cfg* cfg, const pss_raw_cand* raw, int64_t n,
+                        std::vector<SiftItem>* surv, SiftLinker* lk) {
+    const size_t old = surv->size();
+    PSS_TRY(sift_within(*plan, *cfg, raw, n, surv));
+    if (cfg->zmax == 0) {
+        auto by_r = [](const SiftItem& a, const SiftItem& b) { return a.kr < b.kr; };
+        std::stable_sort(surv->begin() + old, surv->end(), by_r);
+        std::inplace_merge(surv->begin(), surv->begin() + old, surv->end(), by_r);
+    } else if (lk) {
+        lk->add(*surv, old);
+    }
+    return PSS_OK;
+}
+
 // After the kernels of a search were enqueued with per-batch snapshots:
 // wait for each DM batch in turn, download its detections on the second
 // stream and run the within-trial sift on the host while the device works
@@ -1122,18 +1141,8 @@ pss_status drain_batches(pss_ctx* ctx, const pss_plan* plan, const pss_search_cf
                                      (size_t)(cnt - prev) * sizeof(pss_raw_cand), cudaMemcpyDeviceToHost,
                                      ctx->stream2));
             PSS_CUDA(cudaStreamSynchronize(ctx->stream2));
-            const size_t old = surv->size();
-            PSS_TRY(sift_within(*plan, *cfg, ctx->raw_pinned, (int64_t)(cnt - prev), surv));
-            if (cfg->zmax == 0) {
-                // keep the survivors ordered by r (stable) while the device works on,
-                // so the across-trial linkage after the last batch needs no sort
-                auto by_r = [](const SiftItem& a, const SiftItem& b) { return a.kr < b.kr; };
-                std::stable_sort(surv->begin() + old, surv->end(), by_r);
-                std::inplace_merge(surv->begin(), surv->begin() + old, surv->end(), by_r);
-            } else if (lk) {
-                // 2-D planes: link the batch's survivors to the earlier ones while the device works on
-                lk->add(*surv, old);
-            }
+            // the batch's within-trial sift and hand-over while the device works on the later batches
+            PSS_TRY(absorb_batch(plan, cfg, ctx->raw_pinned, (int64_t)(cnt - prev), surv, lk));
         }
         prev = cnt;
     }
@@ -2210,6 +2219,35 @@ pss_status pss_sift(const pss_plan* plan, const pss_search_cfg* cfg, const pss_r
     if ((int64_t)v.size() > cap) return fail(PSS_ECAP, "pss_sift: output capacity too small");
     if (!v.empty()) {
         if (!out) return fail(PSS_EINVAL, "pss_sift: null out");
+        memcpy(out, v.data(), v.size() * sizeof(pss_cand));
+    }
+    return PSS_OK;
+}
+
+pss_status pss_sift_in_batches(const pss_plan* plan, const pss_search_cfg* cfg, const pss_raw_cand* raw,
+                               int64_t n_raw, const int64_t* dm_bounds, int32_t nbatches, pss_cand* out, int64_t cap,
+                               int64_t* n_out) {
+    if (!plan || !cfg || !n_out || (n_raw > 0 && !raw) || nbatches < 1 || !dm_bounds)
+        return fail(PSS_EINVAL, "pss_sift_in_batches: null argument or no batch");
+    *n_out = 0;
+    if (cfg->zmax > 0 && !(cfg->dz > 0)) return fail(PSS_EINVAL, "pss_sift_in_batches: dz must be > 0");
+    for (int32_t b = 0; b < nbatches; ++b)
+        if (dm_bounds[b] > dm_bounds[b + 1]) return fail(PSS_EINVAL, "pss_sift_in_batches: DM bounds must not decrease");
+    std::vector<SiftItem> surv;
+    SiftLinker lk;
+    std::vector<pss_raw_cand> part;
+    for (int32_t b = 0; b < nbatches; ++b) {
+        part.clear();
+        for (int64_t i = 0; i < n_raw; ++i)
+            if (raw[i].dm_idx >= dm_bounds[b] && raw[i].dm_idx < dm_bounds[b + 1]) part.push_back(raw[i]);
+        PSS_TRY(absorb_batch(plan, cfg, part.data(), (int64_t)part.size(), &surv, &lk));
+    }
+    std::vector<pss_cand> v;
+    PSS_TRY(sift_across(*plan, *cfg, surv, &v, cfg->zmax ? &lk : nullptr));
+    *n_out = (int64_t)v.size();
+    if ((int64_t)v.size() > cap) return fail(PSS_ECAP, "pss_sift_in_batches: output capacity too small");
+    if (!v.empty()) {
+        if (!out) return fail(PSS_EINVAL, "pss_sift_in_batches: null out");
         memcpy(out, v.data(), v.size() * sizeof(pss_cand));
     }
     return PSS_OK;

@@ -65,7 +65,7 @@ CAND_DTYPE = np.dtype([("dm_idx", "<i4"), ("numharm", "<i4"), ("dm", "<f8"), ("r
 EXPORTS = ["pss_ctx_create", "pss_ctx_destroy", "pss_last_error", "pss_version", "pss_dd_plan", "pss_dd_plan_auto", "pss_dd_plan_subband",
            "pss_plan_subband_info", "pss_plan_info",
            "pss_plan_trial_info", "pss_plan_free", "pss_dedisperse", "pss_single_pulse", "pss_fold", "pss_spectrum", "pss_power_plane",
-           "pss_search_raw", "pss_sift", "pss_search_dm_batch", "pss_response", "pss_sigma_of_power",
+           "pss_search_raw", "pss_sift", "pss_sift_in_batches", "pss_search_dm_batch", "pss_response", "pss_sigma_of_power",
            "pss_power_threshold", "pss_ctx_profile", "pss_ctx_profile_read", "pss_dedisperse_noalloc",
            "pss_refine_prepare", "pss_refine_eval", "pss_refine_candidates", "pss_batch_create", "pss_batch_run",
            "pss_batch_footprint", "pss_batch_free", "pss_search_footprint", "pss_ctx_take_cands",
@@ -111,6 +111,7 @@ def lib():
         "pss_search_raw": (st, [vp, vp, P(pss_fil_desc), vp, C.c_int, P(pss_search_cfg), i64, i64, vp, i64,
                                 P(i64), vp]),
         "pss_sift": (st, [vp, P(pss_search_cfg), vp, i64, vp, i64, P(i64)]),
+        "pss_sift_in_batches": (st, [vp, P(pss_search_cfg), vp, i64, vp, i32, vp, i64, P(i64)]),
         "pss_search_dm_batch": (st, [vp, vp, P(pss_fil_desc), vp, C.c_int, P(pss_search_cfg), i64, i64, vp, i64,
                                      P(i64), vp]),
         "pss_response": (st, [vp, vp, vp, i64, vp]),
@@ -455,6 +456,21 @@ def pss_sift(plan: Plan, cfg: pss_search_cfg, raw: np.ndarray, cap: int = 1 << 1
     while True:
         out = np.zeros(cap, dtype=CAND_DTYPE)
         st = lib().pss_sift(plan.h, C.byref(cfg), raw.ctypes.data, raw.shape[0], out.ctypes.data, cap, C.byref(n))
+        if st == PSS_ECAP:
+            cap = n.value
+            continue
+        _check(st)
+        return out[: n.value]
+
+
+def pss_sift_in_batches(plan: Plan, cfg: pss_search_cfg, raw: np.ndarray, dm_bounds, cap: int = 1 << 14) -> np.ndarray:
+    raw = np.ascontiguousarray(raw, dtype=RAW_DTYPE)
+    bounds = np.ascontiguousarray(dm_bounds, dtype=np.int64)
+    n = C.c_int64()
+    while True:
+        out = np.zeros(cap, dtype=CAND_DTYPE)
+        st = lib().pss_sift_in_batches(plan.h, C.byref(cfg), raw.ctypes.data, raw.shape[0], bounds.ctypes.data,
+                                       len(bounds) - 1, out.ctypes.data, cap, C.byref(n))
         if st == PSS_ECAP:
             cap = n.value
             continue

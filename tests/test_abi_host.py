@@ -251,6 +251,31 @@ def test_sift_matches_oracle(L, zmax, min_hits, dz):
         assert abs(g["f_hz"] - r["r"] / op.t_span(r["dm_idx"])) < 1e-12 * g["f_hz"] + 1e-15
 
 
+@pytest.mark.parametrize("zmax,min_hits,dz", [(0, 1, 2.0), (0, 3, 2.0), (20, 1, 2.0), (20, 2, 2.0), (6, 2, 0.3)])
+def test_sift_in_batches_equals_one_pass(L, zmax, min_hits, dz):
+    # the pipelined search's host sift (trials sifted batch by batch, survivors merged in r order
+    # for zmax 0 or linked batch by batch for zmax > 0, across-trial step at the end) gives the
+    # one-pass sift's list, whatever the arrival order; dense lists make many groups span batches
+    rng = np.random.default_rng(100 + zmax + min_hits)
+    nchan, nsamp, ndm = 64, 1 << 14, 40
+    fch0, foff = synth.band(1200.0, 1500.0, nchan)
+    p = L.Plan(L.FilDesc(nchan, nsamp, 2e-4, fch0, foff), [synth.Stage(0.0, 1.0, ndm, 1)])
+    nz = int(round(2 * zmax / dz)) + 1 if zmax else 1
+    raw = _random_raw(rng, ndm, 120, 8192, nz)
+    raw = raw[rng.permutation(len(raw))]
+    cfg = L.search_cfg(zmax=zmax, dz=dz, numharm=8, min_dm_hits=min_hits)
+    ref = L.pss_sift(p, cfg, raw)
+    assert len(ref) > 0
+    for bounds in ([0, ndm], [0, 12, 24, 36, ndm], [0, 1, 5, 5, 30, ndm]):
+        got = L.pss_sift_in_batches(p, cfg, raw, bounds)
+        assert got.tobytes() == ref.tobytes(), bounds
+    # detections outside every batch are left out
+    part = L.pss_sift_in_batches(p, cfg, raw, [0, 20])
+    assert part.tobytes() == L.pss_sift(p, cfg, raw[raw["dm_idx"] < 20]).tobytes()
+    with pytest.raises(L.PssError):
+        L.pss_sift_in_batches(p, cfg, raw, [10, 5])
+
+
 @pytest.mark.parametrize("fch0,foff,nchan,ts,lo,hi,tres,dsmax", [
     (1231.5, 3.0, 96, 250e-6, 0.0, 3896.0, 0.0, 1024),
     (290.125, 0.25, 200, 100e-6, 0.0, 784.4, 0.8e-3, 128),
