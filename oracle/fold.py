@@ -48,6 +48,14 @@ def fixed_point(v: float) -> int:
     return int(round(math.ldexp(fr, 64))) & MASK64
 
 
+def bin_of_phase(ph: np.ndarray, nbin: int) -> np.ndarray:
+    """int64: floor(ph * nbin / 2^64) of uint64 phases, exactly, from the two
+    32-bit halves of ph (nbin <= 2^10, so no product exceeds 2^42)."""
+    hi, lo = ph >> np.uint64(32), ph & np.uint64(0xFFFFFFFF)
+    nb = np.uint64(nbin)
+    return ((hi * nb + ((lo * nb) >> np.uint64(32))) >> np.uint64(32)).astype(np.int64)
+
+
 def phase_bins(n: int, dt: float, f: float, fdot: float, nbin: int) -> np.ndarray:
     """int64 [n]: the bin of every sample (module docstring)."""
     X = np.uint64(fixed_point(f * dt))
@@ -55,10 +63,7 @@ def phase_bins(n: int, dt: float, f: float, fdot: float, nbin: int) -> np.ndarra
     j = np.arange(n, dtype=np.uint64)
     with np.errstate(over="ignore"):
         ph = j * X + (j * j) * G          # uint64 arithmetic wraps modulo 2^64
-    # floor(ph * nbin / 2^64) from the two 32-bit halves of ph (no product exceeds 2^42)
-    hi, lo = ph >> np.uint64(32), ph & np.uint64(0xFFFFFFFF)
-    nb = np.uint64(nbin)
-    return ((hi * nb + ((lo * nb) >> np.uint64(32))) >> np.uint64(32)).astype(np.int64)
+    return bin_of_phase(ph, nbin)
 
 
 def fold(s: np.ndarray, dt: float, f: float, fdot: float, nbin: int):

@@ -70,3 +70,15 @@ def test_band_centre_and_width():
     assert [r[3] for r in rows] == [8, 16, 32, 64, 128, 128] and rows[-1][1] > rows[-2][1]
     ctr, dnu, bw = DP.band(340.0 - 0.125, -0.25, 200)   # descending order, same band
     assert (ctr, dnu, bw) == (315.0, 0.25, 50.0)
+
+
+def test_no_listed_step_fits_takes_the_smallest():
+    # a wide low-frequency band sampled at 0.1 us: even the smallest listed
+    # step smears by more than the resolution at DM 0, so the first row takes
+    # that smallest step
+    fch0, foff, nchan, ts = 200.0, 1.0, 200, 1e-7
+    ctr, dnu, bw = DP.band(fch0, foff, nchan)
+    nu = ctr / 1e3
+    assert 8.3e-6 * (DP.STEPS[0] / 2) * bw / nu ** 3 > ts
+    rows = DP.auto_plan(fch0, foff, nchan, ts, 0.0, 1.0)
+    assert rows[0][1] == DP.STEPS[0] and rows[0][3] == 1

@@ -116,3 +116,35 @@ def test_fixed_point_phase_matches_exact_rational_phase():
             if b != int(got[j]):
                 edge = min(abs(ph * nbin - b), abs(ph * nbin - (b + 1))) / nbin
                 assert edge <= Fraction(j + j * j, 2 ** 65), (it, j, b, got[j])
+
+
+def test_bin_of_phase_is_the_exact_floor_at_every_bin_edge():
+    # floor(ph * nbin / 2^64) in exact integers: at the first phase of every bin,
+    # one unit below it, and at random phases
+    rng = np.random.default_rng(12)
+    for nbin in (2, 3, 7, 64, 100, 1000, 1024):
+        edges = [-(-(m << 64) // nbin) for m in range(1, nbin)]   # ceil(m 2^64 / nbin)
+        ph = edges + [e - 1 for e in edges] + [0, (1 << 64) - 1]
+        ph += [int(v) for v in rng.integers(0, 1 << 63, 200, dtype=np.uint64)]
+        ph += [int(v) | (1 << 63) for v in rng.integers(0, 1 << 63, 200, dtype=np.uint64)]
+        got = FO.bin_of_phase(np.array(ph, dtype=np.uint64), nbin)
+        assert got.tolist() == [(p * nbin) >> 64 for p in ph], nbin
+
+
+def test_reduced_chi2_by_hand():
+    # s = 0, 2, 0, 2, ... folded at half the sample rate: even samples fall in
+    # bin 0, odd ones in bin nbin/2.  mu = 1, var = 1; each used bin holds 4
+    # samples with d = -4 and +4, so chi2 = 16/4 + 16/4 = 8 over 2 used bins:
+    # chi2_red = 8 / (2 - 1), whatever the number of empty bins.
+    s = np.array([0, 2] * 4)
+    for nbin in (2, 4, 16):
+        P, n = FO.fold(s, 1.0, 0.5, 0.0, nbin)
+        assert n.tolist() == [4 if b in (0, nbin // 2) else 0 for b in range(nbin)]
+        assert FO.chi2_red(P, n, 1.0, 1.0) == 8.0
+
+
+def test_equal_trials_keep_the_first():
+    # a constant series has var 0, so every trial scores 0 and the first wins
+    dt, T = 1e-3, 1.0
+    k, fk, c, _, _ = FO.fold_search(np.full(500, 7), dt, T, 5.0, 0.0, 16, 5, 1.0)
+    assert (k, c) == (0, 0.0) and fk == 5.0 - 2.0

@@ -110,6 +110,21 @@ def test_threshold_table():
     for n, v in {1: 20.7368, 2: 23.9538, 4: 29.1688, 8: 37.8435, 16: 52.6057}.items():
         assert abs(thr[n] - v) < 2e-4
         assert abs(ST.sigma_of(n, thr[n]) - 6.0) < 1e-9
+    # the stages double: a 16-harmonic search sums 1, 2, 4, 8 and 16 harmonics, no others
+    assert sorted(thr) == [1, 2, 4, 8, 16]
+    for bad in (0, 3, 12):
+        with pytest.raises(ValueError):
+            ST.harmonic_stages(bad)
+
+
+def test_threshold_is_inclusive():
+    # a peak whose S_1 equals the threshold exactly is a candidate; one ulp below is not
+    thr = {1: 25.0}
+    for v, want in ((25.0, [(1, 300, 0)]), (np.nextafter(25.0, 0.0), [])):
+        P = np.full((1, 1024), 1.0)
+        P[0, 300] = v
+        c = HS.raw_candidates(P, 1, 0, thr, 10.0, 0.0)
+        assert [(n, h, j) for n, h, j, _ in c] == want
 
 
 def test_min_half_bin():

@@ -96,8 +96,25 @@ def test_no_delay_near_half(wl):
     assert frac.min() > 1e-9
 
 
+def test_channel_centres_tile_the_band():
+    # fch0 is the centre of channel 0 (the filterbank header's first-channel
+    # frequency), so a descending 3-channel header reads back unchanged ...
+    assert P.channel_freqs(3, 1400.0, -1.0).tolist() == [1400.0, 1399.0, 1398.0]
+    # ... and n channels of width |foff| laid from the band's lower edge have
+    # their edges at lo + c * width: the first starts at lo, the last ends at hi
+    for lo, hi, n in ((1200.0, 1500.0, 64), (1050.0, 1450.0, 256), (290.0, 340.0, 200)):
+        f = P.channel_freqs(n, *synth.band(lo, hi, n))
+        w = (hi - lo) / n
+        np.testing.assert_allclose(f - w / 2, lo + np.arange(n) * w, rtol=0, atol=1e-9)
+        np.testing.assert_allclose(f + w / 2, lo + np.arange(1, n + 1) * w, rtol=0, atol=1e-9)
+
+
 def test_stage_lengths():
     assert P.stage_lengths(1 << 18, 4455, 1) == (262144 - 4455, 1 << 18)
+    # a valid length that is already a power of two is transformed unpadded
+    assert P.stage_lengths((1 << 18) + 4455, 4455, 1) == (1 << 18, 1 << 18)
+    assert P.stage_lengths((1 << 18) * 4 + 7, 7, 4) == (1 << 18, 1 << 18)
+    assert P.stage_lengths((1 << 18) + 4456, 4455, 1) == ((1 << 18) + 1, 1 << 19)
     assert P.stage_lengths(1 << 23, 7453, 4) == ((8388608 - 7453) // 4, 1 << 21)
     with pytest.raises(ValueError):
         P.stage_lengths(100, 100, 1)

@@ -24,6 +24,9 @@ def _rho_fresnel(q, z):
 def test_z0_is_sinc(q):
     ref = complex(math.cos(math.pi * q), math.sin(math.pi * q)) * (np.sinc(q))
     assert abs(R.rho_quad(q, 0.0) - ref) < 1e-13
+    # the closed form rho() takes at z = 0 is the same function as the quadrature
+    assert abs(R.rho(q, 0.0) - R.rho_quad(q, 0.0)) < 1e-13
+    assert abs(R.rho(q + 0.25, 0.0) - R.rho_quad(q + 0.25, 0.0)) < 1e-13
 
 
 @pytest.mark.parametrize("q,z", [(0.0, 1.0), (0.5, -2.0), (3.5, 10.0), (-40.0, 150.0), (60.5, -200.0), (116.0, 200.0)])

@@ -92,3 +92,50 @@ def test_pruning_keeps_the_strongest_non_overlapping():
 
 def test_constant_series_has_no_events():
     assert SP.search_series(np.full(1000, 77), SP.DEFAULT_WIDTHS, 3.0) == []
+
+
+def _mean_zero_series(spikes, n_minus, N, seed):
+    # n_minus samples of -1 at random places away from the spikes, zeros elsewhere:
+    # S1 = 0 exactly when the spikes sum to n_minus, so mu = 0 in FP64
+    s = np.zeros(N, dtype=np.int64)
+    for t, v in spikes.items():
+        s[t] = v
+    free = [t for t in range(N) if all(abs(t - u) > 8 for u in spikes)]
+    s[np.random.default_rng(seed).choice(free, n_minus, replace=False)] = -1
+    assert s.sum() == 0
+    return s
+
+
+def test_a_boxcar_exactly_at_the_threshold_is_detected():
+    # 100 samples with S1 = 0 and S2 = 400: mu = 0 and sigma = 2 exactly, so at
+    # 5 sigma the one-sample threshold is exactly 10, and a spike of 10 meets it
+    vals = [10] + [-3] * 4 + [-1] * 65 + [1] + [3] * 22 + [0] * 7
+    s = np.array(vals, dtype=np.int64)
+    rest = s[1:].copy()
+    np.random.default_rng(3).shuffle(rest)
+    s = np.concatenate([rest[:50], [10], rest[50:]])
+    mu, sigma = SP.moments(s)
+    assert (mu, sigma) == (0.0, 2.0) and SP.threshold(1, mu, sigma, 5.0) == 10.0
+    assert SP.detections(s, (1,), 5.0) == [(50, 1, 10)]
+    assert SP.detections(s, (1,), math.nextafter(5.0, 6.0)) == []
+
+
+def test_a_plateau_is_detected_at_its_first_sample():
+    # three samples of 10 make two equal neighbouring two-sample boxcars of 20:
+    # the left one beats everything to its right (>=) and the right one does
+    # not beat it (>), so exactly one event, at the left
+    s = _mean_zero_series({100: 10, 101: 10, 102: 10}, 30, 400, 4)
+    assert [(t, w) for t, w, _ in SP.detections(s, (2,), 6.0)] == [(100, 2)]
+
+
+def test_equal_snr_keeps_the_narrower_pulse():
+    # 4, 8, 4 around t = 200 with mu = 0: the one-sample boxcar 8 and the
+    # four-sample boxcar 16 (t = 198) have the same S/N 8/sigma = 16/(2 sigma)
+    # in FP64; they overlap, and the tie goes to the smaller width, after
+    # which the one-sample events at 199 and 201 no longer overlap anything kept
+    s = _mean_zero_series({199: 4, 200: 8, 201: 4}, 16, 400, 5)
+    mu, sigma = SP.moments(s)
+    assert mu == 0.0 and SP.snr(8, 1, mu, sigma) == SP.snr(16, 4, mu, sigma)
+    assert (198, 4, 16) in SP.detections(s, (1, 4), 6.0)
+    ev = SP.search_series(s, (1, 4), 6.0)
+    assert [(t, w, B) for t, w, B, _ in ev] == [(199, 1, 4), (200, 1, 8), (201, 1, 4)]

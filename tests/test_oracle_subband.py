@@ -64,6 +64,24 @@ def test_single_sum_brute_force():
         assert SB.dedisperse_subband(x, sb.sub, i, sb.max_delay, ds, mask).tolist() == ref
 
 
+def test_combined_delay_above_the_exact_maximum_bounds_the_valid_length():
+    # With groups of one, e_c + D_b rounds twice: 64 channels in 8 subbands,
+    # DM 0-11.4 in steps of 0.6 reach a combined delay of 59 samples where the
+    # exact table's largest delay is 58.  The valid length then follows from
+    # 59, and every trial still reads inside the file.
+    fch0, foff = synth.band(1200.0, 1500.0, 64)
+    nsamp = 400
+    ex, sb = _plans(64, nsamp, 2e-4, fch0, foff, [synth.Stage(0.0, 0.6, 20, 1)], (8, 1))
+    assert ex.max_delay == 58 and sb.sub.max_comb == 59 and sb.max_delay == 59
+    assert sb.lengths[0] == (nsamp - 59, 512)
+    x = _file(64, nsamp, 9)
+    for i in range(len(sb.dms)):
+        comb = sb.sub.combined_delays(i)
+        assert comb.max() <= sb.max_delay
+        want = sum(x[c, int(comb[c]):int(comb[c]) + nsamp - 59].astype(np.int64) for c in range(64))
+        assert np.array_equal(SB.dedisperse_subband(x, sb.sub, i, sb.max_delay, 1), want), i
+
+
 def test_groups_and_nominal_dms():
     _, sb = _plans(32, 3000, 5e-4, 1200.0, 3.0, STAGES, (8, 4))
     g = sb.sub
