@@ -107,3 +107,44 @@ def test_single_pulse_wide_sums(L, ctx):
     fil = _bursty(nsamp=1 << 17, seed=14)
     stages = [synth.Stage(20.0, 5.0, 6, 256)]
     _compare(L, ctx, fil, stages, (1, 2, 4, 16), 3.0)
+
+
+def _tie_file(spikes, seed, N=8192, nchan=64, base=100):
+    # Channel 0 carries base + x[t], the other channels base: at DM 0 the
+    # trial's series is nchan*base + x[t].  x is +-2 noise plus the given
+    # samples, with sum 0 and square sum 4N, so mu = nchan*base and sigma = 2
+    # come out exactly in FP64 and the ties below are exact.
+    rng = np.random.default_rng(seed)
+    x = np.zeros(N, np.int64)
+    tot = (4 * N - sum(v * v for v in spikes.values())) // 4
+    diff = -sum(spikes.values()) // 2
+    n_plus = (tot + diff) // 2
+    pos = rng.permutation(np.array([t for t in range(N) if t not in spikes]))
+    x[pos[:n_plus]] = 2
+    x[pos[n_plus:tot]] = -2
+    for t, v in spikes.items():
+        x[t] = v
+    assert x.sum() == 0 and (x * x).sum() == 4 * N
+    data = np.full((N, nchan), base, np.uint8)
+    data[:, 0] = base + x
+    fch0, foff = synth.band(1200.0, 1500.0, nchan)
+    return synth.Filterbank(nchan, N, 2e-4, fch0, foff, 8, data, [])
+
+
+def test_single_pulse_exact_ties(L, ctx):
+    stages = [synth.Stage(0.0, 1.0, 1, 1)]
+    # a one-sample boxcar exactly at 5 sigma (6400 + 10) is an event; a threshold
+    # 1e-9 sigma higher (a threshold above 6410 after rounding) leaves none
+    fil = _tie_file({4000: 10}, 7)
+    got = _compare(L, ctx, fil, stages, (1,), 5.0)
+    assert [(int(g["t"]), int(g["width"]), int(g["boxsum"])) for g in got] == [(4000, 1, 6410)]
+    assert len(_compare(L, ctx, fil, stages, (1,), 5.0 + 1e-9)) == 0
+    # three equal samples make two equal two-sample boxcars: one event, at the first
+    fil = _tie_file({3000: 10, 3001: 10, 3002: 10}, 8)
+    got = _compare(L, ctx, fil, stages, (2,), 4.0)
+    assert [(int(g["t"]), int(g["width"])) for g in got] == [(3000, 2)]
+    # 4, 8, 4 between zeros: the one-sample boxcar 8 and the four-sample boxcar 16
+    # have the same S/N 4; they overlap and the narrower one is kept
+    fil = _tie_file({4998: 0, 4999: 0, 5000: 4, 5001: 8, 5002: 4, 5003: 0, 5004: 0}, 9)
+    got = _compare(L, ctx, fil, stages, (1, 4), 3.0)
+    assert [(int(g["t"]), int(g["width"]), float(g["snr"])) for g in got] == [(5001, 1, 4.0)]
