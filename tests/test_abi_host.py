@@ -251,6 +251,37 @@ def test_sift_matches_oracle(L, zmax, min_hits, dz):
         assert abs(g["f_hz"] - r["r"] / op.t_span(r["dm_idx"])) < 1e-12 * g["f_hz"] + 1e-15
 
 
+@pytest.mark.parametrize("zmax,min_hits,dz", [(0, 2, 2.0), (20, 1, 2.0), (6, 3, 0.3)])
+def test_sift_ties_and_long_chains_match_oracle(L, zmax, min_hits, dz):
+    # three distinct powers make exact sigma ties between members of one group
+    # (representative by lower n, then r, z, DM), and h in [0, 60) chains most
+    # detections into a few long groups spanning many bins and every DM
+    rng = np.random.default_rng(7 + zmax)
+    nchan, nsamp, ndm = 64, 1 << 14, 10
+    fch0, foff = synth.band(1200.0, 1500.0, nchan)
+    stages = [synth.Stage(0.0, 1.0, ndm, 1)]
+    p = L.Plan(L.FilDesc(nchan, nsamp, 2e-4, fch0, foff), stages)
+    nz = int(round(2 * zmax / dz)) + 1 if zmax else 1
+    Z = int(round(zmax / dz))
+    raw = _random_raw(rng, ndm, 60, 8192, nz)
+    raw["h"] = rng.integers(0, 60, len(raw))
+    raw["power"] = rng.choice(np.array([30.0, 45.0, 60.0], np.float32), len(raw))
+    raw = raw[rng.permutation(len(raw))]
+    cfg = L.search_cfg(zmax=zmax, dz=dz, numharm=8, min_dm_hits=min_hits)
+    got = L.pss_sift(p, cfg, raw)
+    by_dm = {}
+    for c in raw:
+        n, h, j = int(c["numharm"]), int(c["h"]), int(c["j"])
+        r, z = OS.fundamental(n, h, j, Z, dz)
+        by_dm.setdefault(int(c["dm_idx"]), []).append(dict(
+            dm_idx=int(c["dm_idx"]), numharm=n, h=h, j=j, r=r, z=z, zq=OS.zq(n, j, Z), power=float(c["power"]),
+            sigma=OST.sigma_of(n, float(c["power"]))))
+    ref = OS.sift(by_dm, dz, min_hits)
+    assert 0 < len(ref) < len(raw) // 10
+    assert [(int(g["dm_idx"]), int(g["numharm"]), int(g["h"]), int(g["j"]), int(g["dm_hits"])) for g in got] == \
+           [(r["dm_idx"], r["numharm"], r["h"], r["j"], r["dm_hits"]) for r in ref]
+
+
 @pytest.mark.parametrize("zmax,min_hits,dz", [(0, 1, 2.0), (0, 3, 2.0), (20, 1, 2.0), (20, 2, 2.0), (6, 2, 0.3)])
 def test_sift_in_batches_equals_one_pass(L, zmax, min_hits, dz):
     # the pipelined search's host sift (trials sifted batch by batch, survivors merged in r order
